@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Benchmark: TV-superiorized CG reconstructions per second on GB300.
+
+One step = one complete solve of the hot path to the stopping threshold: the
+projector A and backprojector A^T (2 + 2 passes per S-CG loop body), the TV
+subgradient and TV trial passes of the perturbation step, the CG scalars and
+vector updates, and the eps test -- on one batch (one problem) of seeded
+synthetic input already resident in HBM.
+
+Default workload: 512x512 ellipse phantom (20 ellipses), 720 angles x 725
+bins, noise sigma = 0.5 % of max(Ax), eps = 1.05 * L sigma^2 / 2, FP32
+storage/arithmetic with FP64 reductions and scalars, variant S-CG.  The
+problem state (~20 MB) fits in L2, so the L2 is flushed (a 512 MiB write)
+before every timed step, outside the step's event pair.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle instead, on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1709_04912_gb300 import inputs  # noqa: E402
+
+METRIC = "S-CG recon/s at fixed eps"
+UNIT = "recon/s"
+OPS_PER_NNZ = 7           # FP32 lane operations per nonzero ray-pixel weight
+WORKLOADS = {w.name: w for w in (inputs.SINGLE_512, inputs.SMALL_FP64, inputs.MIXED_1024,
+                                  inputs.PAPER_512)}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--variant", default="S-CG")
+    ap.add_argument("--workload", default=inputs.SINGLE_512.name, choices=sorted(WORKLOADS))
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--gamma0-rel", type=float, default=0.05)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def nnz_of(work) -> int:
+    """Exact number of nonzero ray-pixel weights of A (one count per angle)."""
+    n, na, nb = work.n, work.n_angles, work.n_bins
+    idx = np.arange(n) - 0.5 * (n - 1)
+    yc, xc = np.meshgrid(idx, idx, indexing="ij")
+    total = 0
+    for a in range(na):
+        if a == 0:
+            c, s = 1.0, 0.0
+        elif 2 * a == na:
+            c, s = 0.0, 1.0
+        else:
+            c, s = math.cos(math.pi * a / na), math.sin(math.pi * a / na)
+        m, mn = max(abs(c), abs(s)), min(abs(c), abs(s))
+        hs = 0.5 * (m + mn)
+        cb = (xc * c + yc * s + 0.5 * (nb - 1)).ravel()
+        if mn == 0.0:       # closed window of half-width 1/2 (edge rays count for both pixels)
+            lo = np.ceil(cb - 0.5)
+            hi = np.floor(cb + 0.5)
+        else:               # open window (cb - hs, cb + hs)
+            lo = np.floor(cb - hs) + 1
+            hi = np.ceil(cb + hs) - 1
+        lo = np.maximum(lo, 0)
+        hi = np.minimum(hi, nb - 1)
+        total += int(np.sum(np.maximum(hi - lo + 1, 0)))
+    return total
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args, work, rank, world):
+    """The FP64 CPU oracle on bounded samples of the same workload."""
+    if rank != 0:
+        return 0
+    import oracle
+    variant = args.variant
+    kw = dict(variant=variant, gamma0_rel=args.gamma0_rel)
+    if variant in ("CG", "PCG"):
+        kw["perturb"] = "none"
+    prob = inputs.make_problem(work, args.seed, oracle.project)
+    # iteration count to eps: one full oracle solve (untimed; also the warm-up)
+    _, full, _ = oracle.solve(prob.y, work.n, eps=prob.eps, max_iter=work.max_iter, **kw)
+    iters = max(full["iters"], 1)
+    samples = []
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.solve(prob.y, work.n, eps=prob.eps, max_iter=0, **kw)
+        t1 = time.perf_counter()
+        oracle.solve(prob.y, work.n, eps=prob.eps, max_iter=1, **kw)
+        t2 = time.perf_counter()
+        t_setup = t1 - t0
+        t_body = max((t2 - t1) - t_setup, 0.0)
+        if step >= args.warmup:
+            samples.append(t_setup + iters * t_body)
+    t_solve = float(np.mean(samples))
+    value = 1.0 / t_solve
+    cores = oracle.num_threads()
+    sample = (f"per step: oracle {variant} set-up alone and set-up + 1 loop body on the full "
+              f"workload; solve time = set-up + {iters} bodies (the oracle's own iteration "
+              f"count to eps)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_solve,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": work.name, "variant": variant,
+                                            "n": work.n, "n_angles": work.n_angles,
+                                            "n_bins": work.n_bins, "eps": prob.eps},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args, work, rank, local_rank, world):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1709_04912_gb300 import scg
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    scg.load()
+    variant = args.variant
+    kw = dict(gamma0_rel=args.gamma0_rel, max_iter=work.max_iter)
+    if variant in ("CG", "PCG"):
+        kw["perturb"] = "none"
+
+    def gpu_project(x, na, nb):
+        xt = torch.tensor(x, dtype=torch.float32, device=dev)
+        return scg.scg_project(xt, na, nb).double().cpu().numpy()
+
+    prob = inputs.make_problem(work, args.seed + rank, gpu_project)
+    y = torch.tensor(prob.y, dtype=torch.float32, device=dev)
+    out = torch.empty((work.n, work.n), dtype=torch.float32, device=dev)
+    nbytes = scg.solve_workspace_bytes(work.n, work.n_angles, work.n_bins, variant, scg.F32)
+    wsp = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def solve():
+        return scg.scg_solve(y, work.n, variant, prob.eps, out=out, work=wsp, **kw)
+
+    for _ in range(args.warmup):
+        r = solve()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    ms = []
+    launches = 0
+    results = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = solve()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        launches += r.kernel_launches
+        results.append(r)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t_total = sum(ms) / 1e3
+    if world > 1:
+        tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt.item())
+    value = args.steps * world / t_total
+    last = results[-1]
+
+    # end to end through the public API with host buffers: pinned y in, x out
+    e2e = None
+    if not args.no_e2e:
+        y_host = torch.tensor(prob.y, dtype=torch.float32).pin_memory()
+        x_host = torch.empty((work.n, work.n), dtype=torch.float32).pin_memory()
+        y_dev = torch.empty_like(y)
+        t_e2e = 0.0
+        for q in range(args.warmup + args.steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            y_dev.copy_(y_host, non_blocking=True)
+            rr = scg.scg_solve(y_dev, work.n, variant, prob.eps, out=out, work=wsp, **kw)
+            x_host.copy_(out, non_blocking=True)
+            torch.cuda.synchronize()
+            if q >= args.warmup:
+                t_e2e += time.perf_counter() - t0
+        e2e = {"value": args.steps / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": int(y_host.numel() * 4),
+               "d2h_bytes_per_step": int(x_host.numel() * 4 + 64)}
+
+    # dominant kernels timed alone (CUDA events on the launching stream)
+    peaks, peak_kind = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    nnz = nnz_of(work)
+    xk = out.clone()
+    rk = torch.randn((work.n_angles, work.n_bins), dtype=torch.float32, device=dev)
+
+    def time_op(fn, reps=20):
+        for _ in range(3):
+            fn()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(reps)]
+        for a, b in evs:
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return float(np.mean([a.elapsed_time(b) for a, b in evs]))
+
+    yk = torch.empty_like(y)
+    gk = torch.empty_like(out)
+    t_proj = time_op(lambda: scg.scg_project(xk, work.n_angles, work.n_bins, out=yk))
+    t_back = time_op(lambda: scg.scg_backproject(rk, work.n, out=gk))
+    clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_ops = sms * 128 * clock_mhz * 1e6 / 1e12          # T lane-ops/s
+    dom = "backproject" if t_back >= t_proj else "project"
+    t_dom = max(t_back, t_proj)
+    achieved = OPS_PER_NNZ * nnz / (t_dom * 1e-3) / 1e12
+    bytes_pass = 4 * (work.J + 2 * work.L)
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        try:
+            import hashlib
+            src = open(os.path.join(ROOT, "paper_1709_04912_gb300", "csrc", "kernels.cu"), "rb").read()
+            tj = json.load(open(tpath))
+            ent = tj.get(f"{dom}:{work.name}")
+            if ent and ent.get("kernels_sha1") == hashlib.sha1(src).hexdigest():
+                traffic = ent.get("bytes_per_launch")
+        except (OSError, ValueError):
+            traffic = None
+    roofline = {"bound": "alu", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak_ops,
+                "unit": "Top/s (FP32 lane ops)", "frac": achieved / peak_ops, "traffic": traffic,
+                "peak_source": f"{sms} SMs x 128 FP32 lanes x {clock_mhz:.0f} MHz ({peak_kind} clock)",
+                "ops_per_launch": OPS_PER_NNZ * nnz, "nnz": nnz,
+                "ms_per_launch": {"project": t_proj, "backproject": t_back},
+                "hbm_gbs_algorithmic": {"project": bytes_pass / (t_proj * 1e-3) / 1e9,
+                                        "backproject": bytes_pass / (t_back * 1e-3) / 1e9,
+                                        "peak": peaks.get("hbm_gbs")}}
+
+    # CPU baseline: the oracle on a bounded sample of the same workload
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        okw = dict(variant=variant, gamma0_rel=args.gamma0_rel)
+        if variant in ("CG", "PCG"):
+            okw["perturb"] = "none"
+        t0 = time.perf_counter()
+        oracle.solve(prob.y, work.n, eps=prob.eps, max_iter=0, **okw)
+        t1 = time.perf_counter()
+        oracle.solve(prob.y, work.n, eps=prob.eps, max_iter=1, **okw)
+        t2 = time.perf_counter()
+        t_setup = t1 - t0
+        t_body = max((t2 - t1) - t_setup, 0.0)
+        t_solve = t_setup + max(last.iters, 1) * t_body
+        cpu = {"value": 1.0 / t_solve, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": (f"oracle {variant} set-up alone and set-up + 1 loop body on the same "
+                          f"workload ({t2 - t0:.1f} s of CPU work), extrapolated to "
+                          f"{max(last.iters, 1)} bodies (this run's GPU iteration count)")}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": work.name, "variant": variant, "n": work.n,
+                           "n_angles": work.n_angles, "n_bins": work.n_bins, "eps": prob.eps,
+                           "iters": last.iters, "status": last.status, "tv_final": last.tv_final,
+                           "f_final": last.f_final, "l2": "flushed (512 MiB write) before each step",
+                           "per_gpu_problems": 1, "parallelism": f"replicas x{world}"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clk,
+                "step_ms": ms}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    rank, local_rank, world = dist_env()
+    work = WORKLOADS[args.workload]
+    if world > 1:
+        import torch.distributed as dist
+        if args.impl == "reference":
+            if rank != 0:
+                return 0
+        else:
+            dist.init_process_group("nccl", init_method="env://")
+    if args.impl == "reference":
+        return run_reference(args, work, rank, world)
+    return run_ours(args, work, rank, local_rank, world)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,202 @@
+/*
+ * scg.h -- C ABI of libscg, a GB300 (sm_103a) implementation of the
+ * total-variation-superiorized conjugate gradient methods of Zibetti, Lin and
+ * Herman ("Total Variation Superiorized Conjugate Gradient Method for Image
+ * Reconstruction") for least-squares parallel-beam CT.
+ *
+ * Problem (Sec. 1, Eq. LS1):  find x minimising f(x) = 1/2 ||y - A x||^2,
+ * stopping as soon as f <= eps, with total variation (TV) as the secondary
+ * criterion that the superiorized variants lower along the way.
+ *
+ * Geometry (Sec. 4: parallel beam, angles uniform over [0, 180) degrees; the
+ * precise conventions below are this library's, the paper states none):
+ *   image   N x N unit pixels centred on the origin, row-major, pixel (i, j)
+ *           (row i, column j) centred at xc = j - (N-1)/2, yc = i - (N-1)/2;
+ *   angles  theta_a = pi * a / n_angles, a = 0 .. n_angles-1;
+ *   bins    unit width, centres s_b = b - (n_bins-1)/2;
+ *   rays    ray (a, b) is the line xc cos(theta_a) + yc sin(theta_a) = s_b;
+ *   data    sinogram row-major [angle][bin];
+ *   A       A[(a,b),(i,j)] = exact length of ray (a,b) inside pixel (i,j); a
+ *           ray running along a pixel edge gives half its length to each of
+ *           the two pixels it separates.
+ *
+ * Element types follow scg_precision: double for SCG_F64, float for SCG_F32.
+ *
+ * Memory: every array argument is a DEVICE pointer owned by the caller, except
+ * where a comment says "host".  Entry points that need scratch take a device
+ * workspace (16-byte aligned) whose size the matching *_workspace_bytes query
+ * returns; the library itself never allocates device memory.  Workspace
+ * contents do not need to be initialised and must not be shared by calls that
+ * may run at the same time.
+ *
+ * Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  Operator
+ * calls are asynchronous and stream-ordered.  scg_solve returns when the solve
+ * has finished (it reads the device's stop flag).
+ *
+ * Errors: every entry point returns an int status (scg_status).  Nothing
+ * prints, aborts or throws; scg_strerror() names a code.  Invalid arguments
+ * are rejected before any launch.
+ */
+#ifndef SCG_H
+#define SCG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SCG_OK = 0,               /* finished; for solves: f(output) <= eps         */
+    SCG_WARN_MAX_ITER = 1,    /* solve stopped at max_iter with f > eps          */
+    SCG_ERR_INVALID = -1,     /* bad geometry/size/pointer/parameter             */
+    SCG_ERR_CUDA = -2,        /* a CUDA runtime call failed                      */
+    SCG_ERR_WORKSPACE = -3,   /* workspace too small or misaligned               */
+    SCG_ERR_BREAKDOWN = -4,   /* zero or non-finite CG denominator               */
+    SCG_ERR_UNSUPPORTED = -5  /* precision/variant combination not available     */
+} scg_status;
+
+/* The seven algorithms of the paper. */
+typedef enum {
+    SCG_CG = 0,       /* Algorithm 1 (steps: CG-STEP, Algorithm 2)               */
+    SCG_PCG = 1,      /* Algorithm 3 (steps: PCG-STEP, Algorithm 4)              */
+    SCG_S_CG = 2,     /* Algorithm 7 (steps: CG-PR-STEP, Algorithm 8)            */
+    SCG_S_CG_CD = 3,  /* Algorithm 9 (steps: CG-CD-STEP, Algorithm 10)           */
+    SCG_S_CG_K = 4,   /* Algorithm 5 (calls CG-K, Algorithm 6)                   */
+    SCG_S_PCG = 5,    /* Algorithm 13 (steps: PCG-PR-STEP, Algorithm 14)         */
+    SCG_S_PCG_K = 6   /* Algorithm 11 (calls PCG-K, Algorithm 12)                */
+} scg_variant;
+
+typedef enum {
+    SCG_F64 = 0,      /* FP64 storage and arithmetic                             */
+    SCG_F32 = 1       /* FP32 storage and arithmetic, FP64 reductions/scalars    */
+} scg_precision;
+
+typedef enum {
+    SCG_PERTURB_NONE = 0,   /* no superiorization step (x_{k+1/2} = x_k)          */
+    SCG_PERTURB_GAMMA = 1   /* gamma_l = gamma0 a^l with TV acceptance (Sec. 3)   */
+} scg_perturb;
+
+typedef struct {
+    int n;            /* image side N (J = N*N pixels), 2 <= N <= 8192          */
+    int n_angles;     /* number of projection angles, 1 <= n_angles <= 16384    */
+    int n_bins;       /* detector bins per angle, 1 <= n_bins <= 16384          */
+} scg_geometry;
+
+/* Solver parameters (Sec. 3 and Sec. 4).  scg_default_params() fills the
+ * defaults named below. */
+typedef struct {
+    int perturb;         /* scg_perturb; default SCG_PERTURB_GAMMA              */
+    double gamma0;       /* > 0: gamma_0 of Eq. gamma_sequence.  <= 0: gamma_0 =
+                            gamma0_rel * ||x|| of the first image that is
+                            perturbed (default 0)                                */
+    double gamma0_rel;   /* default 0.05                                         */
+    double a;            /* gamma_l = gamma_0 a^l; 0 < a < 1; default 0.975 (Sec. 4) */
+    int max_trials;      /* TV-acceptance trials per perturbation; default 32     */
+    int K;               /* CG-K/PCG-K inner steps (S-CG-K, S-PCG-K); default 2   */
+    int k_inclusive;     /* 1: the printed loop "while k <= K" (K+1 steps); default 0 */
+    double mu;           /* filter offset of c(w); <= 0 selects 2*pi/P (default)  */
+    double filter_gain;  /* scale of c(w); default 1                              */
+    int max_iter;        /* cap on loop bodies; default 100                       */
+} scg_params;
+
+typedef struct {
+    int iters;           /* loop bodies executed                                   */
+    int k_final;         /* the algorithm's counter k when it stopped              */
+    int status;          /* scg_status of the solve                                */
+    double f_final;      /* f(output), from the device's FP64 reduction            */
+    double tv_final;     /* TV(output)                                             */
+    long long ell;       /* index l of the gamma sequence after the last trial     */
+    double gamma0_used;  /* gamma_0 in force at exit (0 if never fixed)            */
+    int kernel_launches; /* kernels this call enqueued (graph nodes counted per
+                            launch of the loop-body graph)                       */
+    int body_launches;   /* loop-body graph launches (bodies after the stop flag
+                            return at once)                                      */
+} scg_result;
+
+/* Solver state, for exact checkpoint/resume and for single-step checks.  The
+ * vectors are caller-owned device arrays of N*N elements (NULL when a variant
+ * does not use them):
+ *   CG, PCG:        x = x_k, p = p_k, g = g_k, delta = delta_k
+ *   S-CG, S-PCG:    x = x_k, x_half = x_{k-1/2}, p = p_{k-1}, h = h_{k-1}
+ *   S-CG-CD:        x = x_k, x_half = x_{k-1/2}, p = p_{k-1}, g = g_{k-1}
+ *   S-CG-K, S-PCG-K: x = x_k, x_half = x_{k-1/2}
+ * (Appendix, Propositions on h_{k-1} and p_{k-1}: this tuple determines the
+ * continuation of Algorithm 7.) */
+typedef struct {
+    int valid;           /* set to 1 on export; must be 1 to resume               */
+    int k;
+    long long ell;
+    double gamma0;
+    int gamma_fixed;
+    double delta;
+    void* x;
+    void* x_half;
+    void* p;
+    void* h;
+    void* g;
+} scg_state;
+
+/* Per-iteration trace row written by scg_solve (host array of
+ * trace_rows * SCG_TRACE_FIELDS doubles): k, f(x_{k-1/2}) tested at the top of
+ * the loop body, TV(x_k), TV(x_{k+1/2}), trials, accepted (1/0, -1 = no
+ * perturbation attempted), l after the trials, accepted gamma, alpha, beta,
+ * smallest relative TV margin of the trials, f(x_{k+1/2}). */
+#define SCG_TRACE_FIELDS 12
+
+const char* scg_strerror(int status);
+void scg_default_params(scg_params* p);
+
+/* Bytes of device workspace for the operator entry points below. */
+size_t scg_op_workspace_bytes(const scg_geometry* g, int precision);
+
+/* y = A x (Eq. LS1's system matrix; the ray-driven forward projector).
+ * x: N*N image, y: n_angles*n_bins sinogram (both device). */
+int scg_project(const scg_geometry* g, int precision, const void* x, void* y,
+                void* work, size_t work_bytes, void* stream);
+
+/* x = A^T r (the backprojection in every step of Algorithms 1-14; pixel-driven
+ * gather that evaluates the same weights as scg_project, no atomics). */
+int scg_backproject(const scg_geometry* g, int precision, const void* r, void* x,
+                    void* work, size_t work_bytes, void* stream);
+
+/* *tv_out (device double) = TV(x), the secondary criterion: isotropic forward
+ * differences over the (N-1)^2 interior terms (the paper names TV without a
+ * formula; Sec. 1).  Summed in FP64. */
+int scg_tv(int n, int precision, const void* x, double* tv_out,
+           void* work, size_t work_bytes, void* stream);
+
+/* grad = a subgradient of TV at x (terms with zero norm contribute 0) and
+ * *tv_out = TV(x); the nonascending direction of the perturbation step is
+ * -grad/||grad|| (Sec. 1, Eq. superiorization). */
+int scg_tv_grad(int n, int precision, const void* x, void* grad, double* tv_out,
+                void* work, size_t work_bytes, void* stream);
+
+/* out = F^T C F r row by row: the filtering part of the preconditioner
+ * z = A^T F^T C F (A x - y) of Sec. 3, c(w) = (|w| + mu)(0.54 + 0.46 cos w) on a
+ * unitary DFT of each row zero-padded to P = 2^ceil(log2(2 n_bins)).
+ * mu <= 0 selects 2*pi/P. */
+int scg_filter(const scg_geometry* g, int precision, double mu, double gain,
+               const void* r, void* out, void* work, size_t work_bytes, void* stream);
+
+/* Bytes of device workspace for scg_solve with this geometry and variant. */
+size_t scg_solve_workspace_bytes(const scg_geometry* g, int variant, int precision);
+
+/* Run one solver of the paper from x0 (NULL = zeros) to f <= eps or max_iter.
+ *   y      n_angles*n_bins data (device); x_out  N*N output (device): for the
+ *          superiorized variants x_{k-1/2}, for CG/PCG x_k (their last steps).
+ *   res    host; filled on return.  trace: host, NULL or trace_rows rows.
+ *   resume NULL, or a state exported by an earlier call with the same
+ *          geometry/variant/precision (its vectors are read, not kept).
+ *   final  NULL, or a state whose vector pointers are filled on return.
+ * Blocking: returns after the device has finished.  Returns res->status. */
+int scg_solve(const scg_geometry* g, int variant, int precision, const scg_params* prm,
+              double eps, const void* y, const void* x0, void* x_out,
+              void* work, size_t work_bytes, scg_result* res,
+              double* trace, int trace_rows,
+              const scg_state* resume, scg_state* final_state, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

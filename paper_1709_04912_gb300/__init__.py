@@ -7,12 +7,3 @@ workloads.  Nothing here falls back to the CPU: if the CUDA library is
 missing, every call raises.
 """
 from . import inputs  # noqa: F401
-
-__all__ = ["inputs", "scg"]
-
-
-def __getattr__(name):
-    if name == "scg":
-        from . import scg as _scg
-        return _scg
-    raise AttributeError(name)

@@ -1,0 +1,539 @@
+// kernels.cu -- the CUDA kernels of the TV-superiorized CG hot path.
+//
+//   k_project      ray-driven forward projector A (Eq. LS1), fused residual
+//                  epilogue r = Ax - y and FP64 sum of squares (f of Sec. 1)
+//   k_backproject  pixel-driven gather A^T (1 or 2 right-hand sides), fused
+//                  FP64 inner products of Algorithms 2/4/8/10/14
+//   k_vec          CG vector updates (p' = -g' + beta p, x' = x + alpha p,
+//                  g' = g + alpha h), perturbation apply, projector views
+//   k_tvgrad       TV, TV subgradient, ||dTV||^2, ||x||^2 (optionally fused
+//                  with x_{k+1} = x_{k+1/2} + alpha p')
+//   k_trial        TV of several trial points x + gamma_l v in one pass
+//                  (Eq. gamma_sequence, acceptance TV(z) <= TV(x))
+//   k_sino_axpy    recursive residual r' = r + alpha A p (CG/PCG)
+//   k_filter       row filter of the preconditioner (Sec. 3) as a Toeplitz
+//                  product with taps h = IDFT(c)
+//   k_taps         the taps, in FP64
+// No kernel uses atomics on data; reductions are deterministic.
+#include "scg_kernels.h"
+
+namespace scg {
+
+template <typename T>
+__device__ __forceinline__ Item decode_item(const Prob<T>* probs, const Item* items, int kind) {
+    if (items) return items[blockIdx.x];
+    const Prob<T>& P = probs[0];
+    Item it;
+    it.prob = 0;
+    it.local = blockIdx.x;
+    if (kind == 0) { it.u = blockIdx.x / P.ray_blocks; it.v = blockIdx.x % P.ray_blocks; }
+    else if (kind == 1) { it.u = blockIdx.x / P.tiles_x; it.v = blockIdx.x % P.tiles_x; }
+    else { it.u = blockIdx.x / P.filt_blocks; it.v = blockIdx.x % P.filt_blocks; }
+    return it;
+}
+
+// ---------------------------------------------------------------------------
+// Forward projector.  One thread per ray (a, b), kRayBlock consecutive bins of
+// one angle per block, so the sinogram writes are coalesced.  The ray is walked
+// along its driving axis (columns when |sin| >= |cos|, else rows); at each
+// step the two pixels whose centres lie within one pixel of the crossing are
+// the only ones the chord can touch ((m+n)/2m <= 1), and both are read from the
+// view whose lines run across the driving axis, so a warp's 32 rays read one
+// short contiguous span.
+template <typename T>
+__global__ void __launch_bounds__(kRayBlock)
+k_project(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int dst_sel,
+          int mode, int step) {
+    const Item it = decode_item(probs, items, 0);
+    const Prob<T>& P = probs[it.prob];
+    if (P.st->done) return;
+    const int N = P.n, nb = P.nb, S = P.S;
+    const int a = it.u;
+    const int b = it.v * kRayBlock + threadIdx.x;
+    const Angle<T> g = P.ang[a];
+    const T off_n = P.off_n;
+    T acc = T(0);
+    if (b < nb) {
+        const T sb = T(b) - P.off_b;
+        // crossing coordinate along the non-driving axis: c*(t) = c0 + t*slope
+        const T inv = g.inv_drive;
+        T slope, c0;
+        const T* V;
+        if (g.col_driven) { slope = -g.c * inv; c0 = sb * inv + off_n * (g.c * inv + T(1)); V = P.view_cm; }
+        else              { slope = -g.s * inv; c0 = sb * inv + off_n * (g.s * inv + T(1)); V = P.view_rm; }
+        int tlo = 0, thi = N - 1;
+        const T lo_c = T(-1.5), hi_c = T(N) + T(0.5);
+        if (tabs(slope) < T(1e-6)) {
+            if (!(c0 >= lo_c && c0 <= hi_c)) thi = -1;
+        } else {
+            T t1 = (lo_c - c0) / slope, t2 = (hi_c - c0) / slope;
+            T lo = tmax(tmin(t1, t2), T(-1)), hi = tmin(tmax(t1, t2), T(N));
+            tlo = max(0, (int)tfloor(lo));
+            thi = min(N - 1, (int)tfloor(hi) + 1);
+        }
+        if (g.col_driven) {
+            for (int j = tlo; j <= thi; ++j) {
+                const T xcc = mul_rn(T(j) - off_n, g.c);
+                const T cs = fma_rn(T(j), slope, c0);
+                int i0 = (int)tfloor(cs);
+                i0 = min(max(i0, -kPad), N + kPad - 2);
+                const T yc0 = T(i0) - off_n;
+                const T d0 = sub_rn(sb, ray_offset(xcc, yc0, g.s));
+                const T d1 = sub_rn(sb, ray_offset(xcc, yc0 + T(1), g.s));
+                const T* line = V + (size_t)j * S + kPad + i0;
+                acc = fma(chord(d0, g), __ldg(line), acc);
+                acc = fma(chord(d1, g), __ldg(line + 1), acc);
+            }
+        } else {
+            for (int i = tlo; i <= thi; ++i) {
+                const T yc = T(i) - off_n;
+                const T cs = fma_rn(T(i), slope, c0);
+                int j0 = (int)tfloor(cs);
+                j0 = min(max(j0, -kPad), N + kPad - 2);
+                const T xc0 = T(j0) - off_n;
+                const T d0 = sub_rn(sb, ray_offset(mul_rn(xc0, g.c), yc, g.s));
+                const T d1 = sub_rn(sb, ray_offset(mul_rn(xc0 + T(1), g.c), yc, g.s));
+                const T* line = V + (size_t)i * S + kPad + j0;
+                acc = fma(chord(d0, g), __ldg(line), acc);
+                acc = fma(chord(d1, g), __ldg(line + 1), acc);
+            }
+        }
+    }
+    double v[1] = {0.0};
+    if (b < nb) {
+        T out = acc;
+        if (mode == PROJ_RESIDUAL) out = acc - P.y[(size_t)a * nb + b];
+        if (mode == PROJ_PLAIN_OUT) P.sino[dst_sel][(size_t)a * nb + b] = out;
+        else P.sino[dst_sel][(size_t)a * P.SB + kSPad + b] = out;
+        v[0] = (double)out * (double)out;
+    }
+    if (step != FIN_NONE) reduce_and_finalize<T, 1>(v, P, it.local, P.cnt_ray, step);
+}
+
+// ---------------------------------------------------------------------------
+// Backprojector: one thread per pixel, all angles; the two candidate bins of
+// each angle are the only ones within (m+n)/2 <= 1/sqrt(2) of the pixel's
+// projected centre.  The weights are computed exactly as in k_project, so the
+// pair is matched to the last bit of every weight.
+template <typename T, int NRHS>
+__global__ void __launch_bounds__(kTileThreads)
+k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int src0,
+              int src1, int dst0, int dst1, int step) {
+    const Item it = decode_item(probs, items, 1);
+    const Prob<T>& P = probs[it.prob];
+    if (P.st->done) return;
+    const int N = P.n, na = P.na, nb = P.nb, SB = P.SB;
+    const int i = it.u * kTileH + threadIdx.x / kTileW;
+    const int j = it.v * kTileW + threadIdx.x % kTileW;
+    const bool in = (i < N) && (j < N);
+    const T xc = T(j) - P.off_n, yc = T(i) - P.off_n, off_b = P.off_b;
+    const T* R0 = P.sino[src0] + kSPad;
+    const T* R1 = NRHS == 2 ? P.sino[src1] + kSPad : nullptr;
+    T acc0 = T(0), acc1 = T(0);
+    if (in) {
+        for (int a = 0; a < na; ++a) {
+            const Angle<T> g = P.ang[a];
+            const T p = ray_offset(mul_rn(xc, g.c), yc, g.s);
+            int b0 = (int)tfloor(p + off_b);
+            b0 = min(max(b0, -kSPad), nb + kSPad - 2);
+            const T sb0 = T(b0) - off_b;
+            const T w0 = chord(sub_rn(sb0, p), g);
+            const T w1 = chord(sub_rn(sb0 + T(1), p), g);
+            const size_t o = (size_t)a * SB + b0;
+            acc0 = fma(w0, __ldg(R0 + o), acc0);
+            acc0 = fma(w1, __ldg(R0 + o + 1), acc0);
+            if (NRHS == 2) {
+                acc1 = fma(w0, __ldg(R1 + o), acc1);
+                acc1 = fma(w1, __ldg(R1 + o + 1), acc1);
+            }
+        }
+    }
+    const size_t idx = (size_t)i * N + j;
+    if (in) {
+        P.img[dst0][idx] = acc0;
+        if (NRHS == 2) P.img[dst1][idx] = acc1;
+    }
+    if (step == FIN_NONE) return;
+    double v[3] = {0.0, 0.0, 0.0};
+    if (in) {
+        const double g0 = (double)acc0, g1 = (double)acc1;
+        if (step == FIN_BETA) {
+            const double h = (double)P.img[IB_H][idx];
+            v[0] = (NRHS == 2 ? g1 : g0) * h;       // g'^T h  (z'^T h)
+            v[1] = g0 * g0;                          // ||g'||^2
+            v[2] = g0 * (double)P.img[IB_P][idx];    // g'^T p
+        } else if (step == FIN_ALPHA || step == FIN_CG_ALPHA) {
+            v[0] = (double)P.img[IB_P][idx] * g0;    // p^T h
+        } else if (step == FIN_CG_DELTA) {
+            v[0] = g0 * g0;                          // ||g||^2
+            v[1] = g0 * g1;                          // g^T z
+        }
+    }
+    reduce_and_finalize<T, 3>(v, P, it.local, P.cnt_img, step);
+}
+
+// ---------------------------------------------------------------------------
+// Write one tile of an image into both projector views.  `val` is this
+// thread's pixel value (ignored outside the image).
+template <typename T>
+__device__ __forceinline__ void write_views(const Prob<T>& P, int ti, int tj, T val, bool in) {
+    __shared__ T tile[kTileH][kTileW + 1];
+    const int ty = threadIdx.x / kTileW, tx = threadIdx.x % kTileW;
+    const int i = ti * kTileH + ty, j = tj * kTileW + tx;
+    if (in) P.view_rm[(size_t)i * P.S + kPad + j] = val;
+    tile[ty][tx] = val;
+    __syncthreads();
+    const int jj = threadIdx.x / kTileH, ii = threadIdx.x % kTileH;
+    const int i2 = ti * kTileH + ii, j2 = tj * kTileW + jj;
+    if (i2 < P.n && j2 < P.n) P.view_cm[(size_t)j2 * P.S + kPad + i2] = tile[ii][jj];
+}
+
+// Elementwise operations on one image tile (see VecOp).
+template <typename T>
+__global__ void __launch_bounds__(kTileThreads)
+k_vec(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int op, int sel, int step) {
+    const Item it = decode_item(probs, items, 1);
+    const Prob<T>& P = probs[it.prob];
+    const DevState& st = *P.st;
+    if (st.done) return;
+    const int N = P.n;
+    const int i = it.u * kTileH + threadIdx.x / kTileW;
+    const int j = it.v * kTileW + threadIdx.x % kTileW;
+    const bool in = (i < N) && (j < N);
+    const size_t idx = (size_t)i * N + j;
+    double v[2] = {0.0, 0.0};
+    T val = T(0);
+    switch (op) {
+    case VEC_INIT: {            // X = XH = x0 (AUX, or zeros), views of X
+        const T* src = P.img[IB_AUX];
+        if (in) {
+            val = src ? src[idx] : T(0);
+            P.img[IB_X][idx] = val;
+            if (P.img[IB_XH]) P.img[IB_XH][idx] = val;
+        }
+        write_views(P, it.u, it.v, val, in);
+        break;
+    }
+    case VEC_VIEWS: {           // views of img[sel]
+        if (in) val = P.img[sel][idx];
+        write_views(P, it.u, it.v, val, in);
+        break;
+    }
+    case VEC_PERTURB: {         // x_{k+1/2} = x_k + coef * dTV(x_k), views
+        const T coef = (T)st.coef;
+        if (in) {
+            const T x = P.img[IB_X][idx];
+            val = (st.accepted == 1) ? fma_rn(coef, P.img[IB_TVG][idx], x) : x;
+            P.img[IB_XH][idx] = val;
+        }
+        write_views(P, it.u, it.v, val, in);
+        break;
+    }
+    case VEC_FORM_P: {          // p' = -d + beta p (d = g' or z'), views; S0 = g'^T p'
+        const T beta = (T)st.beta;
+        if (in) {
+            const T d = P.img[sel][idx];
+            val = fma(beta, P.img[IB_P][idx], -d);
+            P.img[IB_P][idx] = val;
+            v[0] = (double)P.img[IB_G][idx] * (double)val;
+        }
+        write_views(P, it.u, it.v, val, in);
+        break;
+    }
+    case VEC_FORM_P0: {         // p_0 = -d (first direction), views; S0 = g^T p_0
+        if (in) {
+            val = -P.img[sel][idx];
+            P.img[IB_P][idx] = val;
+            v[0] = (double)P.img[IB_G][idx] * (double)val;
+        }
+        write_views(P, it.u, it.v, val, in);
+        break;
+    }
+    case VEC_FORM_P_NOVIEW: {   // p' = -d + beta p without views (last CG-K step unused)
+        const T beta = (T)st.beta;
+        if (in) {
+            const T d = P.img[sel][idx];
+            val = fma(beta, P.img[IB_P][idx], -d);
+            P.img[IB_P][idx] = val;
+            v[0] = (double)P.img[IB_G][idx] * (double)val;
+        }
+        break;
+    }
+    case VEC_CG_UPDATE: {       // x' = base + alpha p, g' = g + alpha h; S0 = ||g'||^2, S1 = g'^T z
+        const T alpha = (T)st.alpha;
+        if (in) {
+            const T base = P.img[sel][idx];
+            P.img[IB_X][idx] = fma(alpha, P.img[IB_P][idx], base);
+            const T gn = fma(alpha, P.img[IB_H][idx], P.img[IB_G][idx]);
+            P.img[IB_G][idx] = gn;
+            v[0] = (double)gn * (double)gn;
+            if (P.img[IB_Z]) v[1] = (double)gn * (double)P.img[IB_Z][idx];
+        }
+        break;
+    }
+    case VEC_DOTS_RESUME: {     // S0 = p^T h, S1 = g^T p
+        if (in) {
+            const double p = (double)P.img[IB_P][idx];
+            if (P.img[IB_H]) v[0] = p * (double)P.img[IB_H][idx];
+            if (P.img[IB_G]) v[1] = p * (double)P.img[IB_G][idx];
+        }
+        break;
+    }
+    default:
+        break;
+    }
+    if (step != FIN_NONE) reduce_and_finalize<T, 2>(v, P, it.local, P.cnt_img, step);
+}
+
+// ---------------------------------------------------------------------------
+// TV stencil.  TV(x) = sum over interior (i,j) of ||(x[i+1,j]-x[i,j], x[i,j+1]-x[i,j])||;
+// the subgradient at (i,j) collects the unit vectors of the terms (i,j),
+// (i-1,j) and (i,j-1) (terms of zero norm contribute 0).  With fuse_update the
+// tile first forms x_{k+1} = x_{k+1/2} + alpha p' (written to X) and takes the
+// stencil of that.  src selects the image when not fused; write_grad = 0 only
+// sums TV.
+template <typename T>
+__global__ void __launch_bounds__(kTileThreads)
+k_tvgrad(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int src,
+         int fuse_update, int write_grad, int step) {
+    const Item it = decode_item(probs, items, 1);
+    const Prob<T>& P = probs[it.prob];
+    const DevState& st = *P.st;
+    if (st.done) return;
+    __shared__ T xs[kTileH + 2][kTileW + 3];
+    __shared__ T tu[kTileH + 1][kTileW + 2];
+    __shared__ T tv[kTileH + 1][kTileW + 2];
+    const int N = P.n;
+    const int i0 = it.u * kTileH - 1, j0 = it.v * kTileW - 1;     // smem origin
+    const T alpha = (T)st.alpha;
+    const T* XH = P.img[IB_XH];
+    const T* PP = P.img[IB_P];
+    const T* SRC = P.img[src];
+    for (int q = threadIdx.x; q < (kTileH + 2) * (kTileW + 2); q += kTileThreads) {
+        const int ii = q / (kTileW + 2), jj = q % (kTileW + 2);
+        const int gi = i0 + ii, gj = j0 + jj;
+        T val = T(0);
+        if (gi >= 0 && gi < N && gj >= 0 && gj < N) {
+            const size_t g = (size_t)gi * N + gj;
+            val = fuse_update ? fma(alpha, PP[g], XH[g]) : SRC[g];
+        }
+        xs[ii][jj] = val;
+    }
+    __syncthreads();
+    const int ty = threadIdx.x / kTileW, tx = threadIdx.x % kTileW;
+    // terms for smem rows 0..kTileH (global i0..i0+kTileH), cols 0..kTileW
+    double tvsum = 0.0;
+    for (int q = threadIdx.x; q < (kTileH + 1) * (kTileW + 1); q += kTileThreads) {
+        const int ii = q / (kTileW + 1), jj = q % (kTileW + 1);
+        const int gi = i0 + ii, gj = j0 + jj;
+        T a = T(0), c = T(0);
+        if (gi >= 0 && gi < N - 1 && gj >= 0 && gj < N - 1) {
+            const T x0 = xs[ii][jj];
+            const T du = xs[ii + 1][jj] - x0, dv = xs[ii][jj + 1] - x0;
+            const T nrm = tsqrt(du * du + dv * dv);
+            if (nrm > T(0)) { a = du / nrm; c = dv / nrm; }
+        }
+        tu[ii][jj] = a;
+        tv[ii][jj] = c;
+    }
+    __syncthreads();
+    const int i = i0 + 1 + ty, j = j0 + 1 + tx;
+    const bool in = (i < N) && (j < N);
+    double v[3] = {0.0, 0.0, 0.0};
+    if (in) {
+        const size_t g = (size_t)i * N + j;
+        const T x = xs[ty + 1][tx + 1];
+        if (fuse_update) P.img[IB_X][g] = x;
+        if (i < N - 1 && j < N - 1) {         // this tile's own term (i, j)
+            const T du = xs[ty + 2][tx + 1] - x, dv = xs[ty + 1][tx + 2] - x;
+            tvsum = (double)tsqrt(du * du + dv * dv);
+        }
+        const T gr = -(tu[ty + 1][tx + 1] + tv[ty + 1][tx + 1]) + tu[ty][tx + 1] + tv[ty + 1][tx];
+        if (write_grad) P.img[IB_TVG][g] = gr;
+        v[0] = tvsum;
+        v[1] = (double)gr * (double)gr;
+        v[2] = (double)x * (double)x;
+    }
+    if (step != FIN_NONE) reduce_and_finalize<T, 3>(v, P, it.local, P.cnt_img, step);
+}
+
+// ---------------------------------------------------------------------------
+// kTrials trial points z_t = x + coef_t * dTV(x) (coef_t = -gamma_{l+t}/||dTV||)
+// and x itself, their TVs summed in one pass over x and dTV.  The accepted
+// point is later formed by k_vec(VEC_PERTURB) with the same coefficient and
+// the same fma, so the stored x_{k+1/2} is exactly the point that was tested.
+template <typename T>
+__global__ void __launch_bounds__(kTileThreads)
+k_trial(const Prob<T>* __restrict__ probs, const Item* __restrict__ items) {
+    const Item it = decode_item(probs, items, 1);
+    const Prob<T>& P = probs[it.prob];
+    const DevState& st = *P.st;
+    if (st.done || st.accepted != 0) return;
+    const int N = P.n;
+    const int i = it.u * kTileH + threadIdx.x / kTileW;
+    const int j = it.v * kTileW + threadIdx.x % kTileW;
+    double v[kTrials + 1];
+#pragma unroll
+    for (int t = 0; t <= kTrials; ++t) v[t] = 0.0;
+    if (i < N - 1 && j < N - 1) {
+        const T* X = P.img[IB_X];
+        const T* G = P.img[IB_TVG];
+        const size_t g0 = (size_t)i * N + j;
+        const T x0 = X[g0], xu = X[g0 + N], xv = X[g0 + 1];
+        const T q0 = G[g0], qu = G[g0 + N], qv = G[g0 + 1];
+#pragma unroll
+        for (int t = 0; t < kTrials; ++t) {
+            const T c = (T)st.trial_coef[t];
+            const T z0 = fma_rn(c, q0, x0), zu = fma_rn(c, qu, xu), zv = fma_rn(c, qv, xv);
+            const T du = zu - z0, dv = zv - z0;
+            v[t] = (double)tsqrt(du * du + dv * dv);
+        }
+        const T du = xu - x0, dv = xv - x0;
+        v[kTrials] = (double)tsqrt(du * du + dv * dv);
+    }
+    reduce_and_finalize<T, kTrials + 1>(v, P, it.local, P.cnt_img, FIN_TRIAL);
+}
+
+// ---------------------------------------------------------------------------
+// r' = r + alpha q on the sinogram views; S0 = ||r'||^2.
+template <typename T>
+__global__ void __launch_bounds__(kRayBlock)
+k_sino_axpy(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int step) {
+    const Item it = decode_item(probs, items, 0);
+    const Prob<T>& P = probs[it.prob];
+    const DevState& st = *P.st;
+    if (st.done) return;
+    const int a = it.u, b = it.v * kRayBlock + threadIdx.x;
+    double v[1] = {0.0};
+    if (b < P.nb) {
+        const size_t o = (size_t)a * P.SB + kSPad + b;
+        const T r = fma((T)st.alpha, P.sino[SB_Q][o], P.sino[SB_R][o]);
+        P.sino[SB_R][o] = r;
+        v[0] = (double)r * (double)r;
+    }
+    reduce_and_finalize<T, 1>(v, P, it.local, P.cnt_ray, step);
+}
+
+// ---------------------------------------------------------------------------
+// Row filter: w[a,b] = sum_b' h[b - b'] r[a,b'], the zero-padded circular
+// convolution of Sec. 3's filter restricted to the row (P >= 2 nb, so nothing
+// wraps).  One block per (row, 128 outputs); the row and the taps are staged
+// in shared memory.
+template <typename T>
+__global__ void __launch_bounds__(kFilterBlock)
+k_filter(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int src, int dst,
+         int plain) {
+    const Item it = decode_item(probs, items, 2);
+    const Prob<T>& P = probs[it.prob];
+    if (P.st->done) return;
+    extern __shared__ unsigned char smem_raw[];
+    T* row = reinterpret_cast<T*>(smem_raw);
+    T* taps = row + P.nb;
+    const int nb = P.nb, a = it.u;
+    const T* R = plain ? P.sino[src] + (size_t)a * nb : P.sino[src] + (size_t)a * P.SB + kSPad;
+    for (int q = threadIdx.x; q < nb; q += blockDim.x) row[q] = R[q];
+    for (int q = threadIdx.x; q < 2 * nb - 1; q += blockDim.x) taps[q] = P.taps[q];
+    __syncthreads();
+    const int b = it.v * kFilterBlock + threadIdx.x;
+    if (b >= nb) return;
+    // taps[nb - 1 + k] = h[k]
+    const T* tb = taps + (nb - 1) + b;
+    T acc0 = T(0), acc1 = T(0);
+    int q = 0;
+    for (; q + 1 < nb; q += 2) {
+        acc0 = fma(tb[-q], row[q], acc0);
+        acc1 = fma(tb[-q - 1], row[q + 1], acc1);
+    }
+    if (q < nb) acc0 = fma(tb[-q], row[q], acc0);
+    const T out = acc0 + acc1;
+    if (plain) P.sino[dst][(size_t)a * nb + b] = out;
+    else P.sino[dst][(size_t)a * P.SB + kSPad + b] = out;
+}
+
+// Taps h[k] = gain/P * sum_m c(w_m) cos(2 pi m k / P), k = 0..nb-1, stored
+// symmetrically; one block per k, FP64.
+template <typename T>
+__global__ void k_taps(T* taps, int nb, int P, double mu, double gain) {
+    const int k = blockIdx.x;
+    double acc = 0.0;
+    for (int m = threadIdx.x; m < P; m += blockDim.x) {
+        const double w = (m <= P / 2) ? 2.0 * M_PI * m / P : 2.0 * M_PI * (m - P) / P;
+        const double c = (fabs(w) + mu) * (0.54 + 0.46 * cos(w));
+        const long long mk = ((long long)m * k) % P;
+        acc += c * cos(2.0 * M_PI * (double)mk / (double)P);
+    }
+    __shared__ double red[32];
+    double v[1] = {acc};
+    block_sum<1>(v, red);
+    if (threadIdx.x == 0) {
+        const T h = (T)(gain * v[0] / (double)P);
+        taps[nb - 1 + k] = h;
+        taps[nb - 1 - k] = h;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers.
+template <typename T>
+void launch_project(const Prob<T>* d, const Item* items, int grid, int dst, int mode, int step,
+                    cudaStream_t s) {
+    k_project<T><<<grid, kRayBlock, 0, s>>>(d, items, dst, mode, step);
+}
+template <typename T>
+void launch_backproject(const Prob<T>* d, const Item* items, int grid, int nrhs, int src0,
+                        int src1, int dst0, int dst1, int step, cudaStream_t s) {
+    if (nrhs == 2) k_backproject<T, 2><<<grid, kTileThreads, 0, s>>>(d, items, src0, src1, dst0, dst1, step);
+    else k_backproject<T, 1><<<grid, kTileThreads, 0, s>>>(d, items, src0, src1, dst0, dst1, step);
+}
+template <typename T>
+void launch_vec(const Prob<T>* d, const Item* items, int grid, int op, int sel, int step,
+                cudaStream_t s) {
+    k_vec<T><<<grid, kTileThreads, 0, s>>>(d, items, op, sel, step);
+}
+template <typename T>
+void launch_tvgrad(const Prob<T>* d, const Item* items, int grid, int src, int fuse,
+                   int write_grad, int step, cudaStream_t s) {
+    k_tvgrad<T><<<grid, kTileThreads, 0, s>>>(d, items, src, fuse, write_grad, step);
+}
+template <typename T>
+void launch_trial(const Prob<T>* d, const Item* items, int grid, cudaStream_t s) {
+    k_trial<T><<<grid, kTileThreads, 0, s>>>(d, items);
+}
+template <typename T>
+void launch_sino_axpy(const Prob<T>* d, const Item* items, int grid, int step, cudaStream_t s) {
+    k_sino_axpy<T><<<grid, kRayBlock, 0, s>>>(d, items, step);
+}
+template <typename T>
+cudaError_t launch_filter(const Prob<T>* d, const Item* items, int grid, int max_nb, int src,
+                          int dst, int plain, cudaStream_t s) {
+    size_t smem = (size_t)(3 * max_nb) * sizeof(T);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_filter<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_filter<T><<<grid, kFilterBlock, smem, s>>>(d, items, src, dst, plain);
+    return cudaSuccess;
+}
+template <typename T>
+void launch_taps(T* taps, int nb, int P, double mu, double gain, cudaStream_t s) {
+    k_taps<T><<<nb, 256, 0, s>>>(taps, nb, P, mu, gain);
+}
+
+#define SCG_INSTANTIATE(T)                                                                        \
+    template void launch_project<T>(const Prob<T>*, const Item*, int, int, int, int, cudaStream_t); \
+    template void launch_backproject<T>(const Prob<T>*, const Item*, int, int, int, int, int, int, \
+                                        int, cudaStream_t);                                       \
+    template void launch_vec<T>(const Prob<T>*, const Item*, int, int, int, int, cudaStream_t);     \
+    template void launch_tvgrad<T>(const Prob<T>*, const Item*, int, int, int, int, int,          \
+                                   cudaStream_t);                                                 \
+    template void launch_trial<T>(const Prob<T>*, const Item*, int, cudaStream_t);                \
+    template void launch_sino_axpy<T>(const Prob<T>*, const Item*, int, int, cudaStream_t);       \
+    template cudaError_t launch_filter<T>(const Prob<T>*, const Item*, int, int, int, int, int,   \
+                                          cudaStream_t);                                          \
+    template void launch_taps<T>(T*, int, int, double, double, cudaStream_t);
+
+SCG_INSTANTIATE(float)
+SCG_INSTANTIATE(double)
+
+}  // namespace scg

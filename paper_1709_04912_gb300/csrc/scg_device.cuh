@@ -1,0 +1,446 @@
+// scg_device.cuh -- device-side data structures, the ray-pixel weight, the
+// deterministic FP64 block reductions and the solver state machine shared by
+// every kernel of libscg.
+//
+// Layout in HBM (one "problem" = one reconstruction):
+//   image vectors      N*N, row-major, element type T (float or double)
+//   projector views    two zero-padded copies of the image being projected:
+//                      row-major lines (view_rm[i*S + kPad + j]) for angles
+//                      whose rays are walked row by row, and column-major lines
+//                      (view_cm[j*S + kPad + i]) for angles walked column by
+//                      column, so that the lanes of a warp (consecutive rays)
+//                      read one contiguous span of a line.
+//   sinogram views     [angle][kSPad + bin] rows of stride SB with zero pads,
+//                      so the backprojector's two candidate bins never need a
+//                      bounds test.
+//   partials           kSlots doubles per work item, summed in a fixed order
+//                      by the last item of a launch (no atomics on data).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "scg.h"
+
+namespace scg {
+
+constexpr int kPad = 2;          // zero elements on each side of an image-view line
+constexpr int kSPad = 1;         // zero elements on each side of a sinogram-view row
+constexpr int kSlots = 8;        // FP64 partial sums per work item
+constexpr int kTrials = 7;       // TV trial candidates per pass (+1 baseline slot)
+constexpr int kTileW = 32;       // image tile width (pixels) = one warp
+constexpr int kTileH = 8;        // image tile height
+constexpr int kTileThreads = kTileW * kTileH;
+constexpr int kRayBlock = 128;   // rays per projector work item
+constexpr int kFilterBlock = 128;// output bins per filter work item
+
+enum ImgBuf { IB_X = 0, IB_XH, IB_P, IB_H, IB_G, IB_Z, IB_TVG, IB_AUX, IB_COUNT };
+enum SinoBuf { SB_R = 0, SB_Q, SB_W, SB_COUNT };
+
+// Per-angle constants of the ray-pixel weight (host computes them in FP64).
+//   m = max(|c|,|s|), n = min(|c|,|s|); the chord of a ray through a unit pixel
+//   at signed distance d from its centre is
+//     T(d) = min(1/m, max(0, ((m+n)/2 - |d|) / (m n)))
+//   and, for axis-aligned rays (n = 0), T(d) = min(1, max(0, 1 - |d|)), which
+//   on the half-integer distances that occur there gives 1, 1/2 (a ray on an
+//   edge, shared by two pixels) or 0.
+template <typename T>
+struct Angle {
+    T c, s;        // cos, sin (exact 0/1 at theta = 0, pi/2)
+    T inv_m;       // plateau height 1/m
+    T inv_mn;      // ramp slope
+    T hs_mn;       // ramp offset
+    T inv_drive;   // 1/s for column-walked angles, 1/c for row-walked ones
+    int col_driven;
+    int pad_;
+};
+
+// Work item of a launch over many problems (batched mode).  Single-problem
+// launches pass items = nullptr and decode (u, v) from blockIdx.
+struct Item {
+    int prob;      // problem index
+    int u, v;      // projector: angle, bin block; image: tile row, tile column; filter: row, block
+    int local;     // index of this item among the problem's items of this kind
+};
+
+// Trace row fields (SCG_TRACE_FIELDS).
+enum { TR_K = 0, TR_FTEST, TR_TV_BEFORE, TR_TV_AFTER, TR_TRIALS, TR_ACCEPTED, TR_ELL,
+       TR_GAMMA, TR_ALPHA, TR_BETA, TR_MARGIN, TR_F_AFTER, TR_NF };
+
+// Device-resident solver state: every scalar of Algorithms 1-14 lives here
+// and is only ever written by the finalising block of a reduction.
+struct DevState {
+    double eps;
+    double f_half;          // f at the point tested next: f(x_{k+1/2}) (S-variants), f(x_k) (CG)
+    double pTh;             // p_{k-1}^T h_{k-1}
+    double gTp;             // g_{k-1}^T p_{k-1} (S-CG-CD)
+    double delta;           // CG/PCG delta_k
+    double alpha, beta, num, gg;
+    double tv_x, gnorm2, xnorm2;
+    double gamma0, gamma0_rel, a;
+    double coef;            // applied perturbation: x_{k+1/2} = x_k + coef * dTV(x_k)
+    double trial_coef[kTrials];
+    double margin;
+    double f_final, tv_final;
+    long long ell;
+    int k, iters, max_iter, done, status;
+    int perturb, gamma_fixed, max_trials, trials, accepted;
+    int in_init, variant, inner_stop, family;
+};
+
+enum Family { FAM_CG = 0, FAM_S_PR = 1, FAM_S_K = 2 };
+
+template <typename T>
+struct Prob {
+    int n, na, nb;
+    int S;                  // image-view line stride (elements)
+    int SB;                 // sinogram-view row stride (elements)
+    int cnt_ray, cnt_img, cnt_row;   // items per launch kind
+    int tiles_x;            // image tiles per row of tiles
+    int ray_blocks;         // projector items per angle
+    int filt_blocks;        // filter items per row
+    int P;                  // filter length (power of two >= 2 nb)
+    T off_n, off_b;         // (N-1)/2, (nb-1)/2
+    const Angle<T>* ang;
+    const T* y;             // data [na][nb]
+    T* img[IB_COUNT];
+    T* sino[SB_COUNT];
+    T* view_rm;
+    T* view_cm;
+    const T* taps;          // Toeplitz filter taps h[-(nb-1) .. nb-1]
+    double* partials;
+    unsigned* counter;
+    DevState* st;
+    double* trace;
+    int trace_rows;
+    int pad_;
+};
+
+// ---------------------------------------------------------------------------
+// Rounding-explicit arithmetic.  The projector and the backprojector must
+// evaluate bit-identical weights; spelling every operation out keeps the
+// compiler from contracting them differently in the two kernels.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float tmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double tmin(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float tmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double tmax(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float tabs(float a) { return fabsf(a); }
+__device__ __forceinline__ double tabs(double a) { return fabs(a); }
+__device__ __forceinline__ float tfloor(float a) { return floorf(a); }
+__device__ __forceinline__ double tfloor(double a) { return floor(a); }
+__device__ __forceinline__ float tsqrt(float a) { return sqrtf(a); }
+__device__ __forceinline__ double tsqrt(double a) { return sqrt(a); }
+
+// Distance between ray (sb) and pixel centre (xc, yc) along the detector:
+// d = s_b - (yc*sin + xc*cos), evaluated in this exact order everywhere.
+template <typename T>
+__device__ __forceinline__ T ray_offset(T xcc /* = mul_rn(xc, c) */, T yc, T s) {
+    return fma_rn(yc, s, xcc);
+}
+
+// Chord length T(d) (see Angle).
+template <typename T>
+__device__ __forceinline__ T chord(T d, const Angle<T>& g) {
+    T t = fma_rn(-tabs(d), g.inv_mn, g.hs_mn);
+    return tmin(g.inv_m, tmax(T(0), t));
+}
+
+// ---------------------------------------------------------------------------
+// Block reductions (FP64, fixed order).
+template <int NS>
+__device__ __forceinline__ void block_sum(double (&v)[NS], double* smem /* >= 32*NS */) {
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < NS; ++k) smem[warp * NS + k] = v[k];
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NS; ++k) v[k] = (lane < nwarps) ? smem[lane * NS + k] : 0.0;
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+        }
+    }
+}
+
+template <typename T> __device__ void finalize(int step, const Prob<T>& P, const double* S);
+
+// Publish this item's partial sums; the block that completes the problem's
+// last item sums all partials in item order and runs the step's finaliser.
+// Must be called by every thread of the block (uniform control flow).
+template <typename T, int NS>
+__device__ void reduce_and_finalize(double (&v)[NS], const Prob<T>& P, int local, int total,
+                                    int step) {
+    __shared__ double red[32 * kSlots];
+    __shared__ unsigned s_last;
+    block_sum<NS>(v, red);
+    if (threadIdx.x == 0) {
+        double* dst = P.partials + (size_t)local * kSlots;
+#pragma unroll
+        for (int k = 0; k < NS; ++k) dst[k] = v[k];
+        __threadfence();
+        unsigned prev = atomicAdd(P.counter, 1u);
+        s_last = (prev + 1u == (unsigned)total);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double acc[NS];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) acc[k] = 0.0;
+    for (int it = threadIdx.x; it < total; it += blockDim.x) {
+        const double* src = P.partials + (size_t)it * kSlots;
+#pragma unroll
+        for (int k = 0; k < NS; ++k) acc[k] += __ldcg(src + k);
+    }
+    block_sum<NS>(acc, red);
+    if (threadIdx.x == 0) {
+        *P.counter = 0u;
+        double S[kSlots];
+#pragma unroll
+        for (int k = 0; k < kSlots; ++k) S[k] = k < NS ? acc[k] : 0.0;
+        finalize<T>(step, P, S);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Solver state machine.  Step codes name the reduction that just finished.
+enum Step {
+    FIN_NONE = 0,
+    FIN_F,            // residual projection: f = S0/2 at the point just projected
+    FIN_BETA,         // gradient backprojection (S-variants): S0 = g'^T h (or z'^T h), S1 = ||g'||^2
+    FIN_NUM,          // new direction formed: S0 = g'^T p'
+    FIN_ALPHA,        // h' backprojection: S0 = p'^T h'  ->  alpha = -g'^T p' / p'^T h'
+    FIN_END,          // TV gradient of the new iterate: S0 = TV, S1 = ||dTV||^2, S2 = ||x||^2
+    FIN_TRIAL,        // trial pass: S0..S6 = TV of candidates, S7 = TV(x)
+    FIN_CG_DELTA,     // CG(-K) start: S0 = ||g||^2, S1 = g^T z
+    FIN_CG_ALPHA,     // CG-STEP: S0 = p^T h -> alpha = delta / p^T h
+    FIN_CG_F,         // recursive residual: f = S0/2
+    FIN_CG_BETA,      // CG-STEP: S0 = ||g'||^2, S1 = g'^T z' -> beta = delta'/delta
+    FIN_CG_END,       // CG/PCG end of loop body (no sums)
+    FIN_RESUME,       // resumed state: S0 = p^T h, S1 = g^T p
+    FIN_TV,           // standalone TV: S0 -> trace slot 0
+    FIN_FINAL_F,      // f of the output
+    FIN_FINAL_TV      // TV of the output
+};
+
+__device__ __forceinline__ bool finite_pos(double v) { return v > 0.0 && isfinite(v); }
+
+template <typename T>
+__device__ __forceinline__ double* trace_row(const Prob<T>& P, int it) {
+    if (P.trace == nullptr || it < 0 || it >= P.trace_rows) return nullptr;
+    return P.trace + (size_t)it * TR_NF;
+}
+
+// Finish a loop body: the algorithm's k <- k+1.
+template <typename T>
+__device__ void end_body(const Prob<T>& P) {
+    DevState& st = *P.st;
+    st.k += 1;
+    st.iters += 1;
+}
+
+template <typename T>
+__device__ void set_trial_coefs(const Prob<T>& P) {
+    DevState& st = *P.st;
+    double inv = 1.0 / sqrt(st.gnorm2);
+    for (int t = 0; t < kTrials; ++t)
+        st.trial_coef[t] = -st.gamma0 * pow(st.a, (double)(st.ell + t)) * inv;
+}
+
+// Top of the while loop: test f(x_{k-1/2}) > eps (f(x_k) for CG/PCG) and the
+// iteration cap, open the trace row and prepare the perturbation of x_k.
+template <typename T>
+__device__ void top_of_loop(const Prob<T>& P) {
+    DevState& st = *P.st;
+    if (st.done) return;
+    if (!(st.f_half > st.eps)) { st.done = 1; st.status = SCG_OK; return; }
+    if (st.iters >= st.max_iter) { st.done = 1; st.status = SCG_WARN_MAX_ITER; return; }
+    double* row = trace_row(P, st.iters);
+    if (row) {
+        for (int q = 0; q < TR_NF; ++q) row[q] = 0.0;
+        row[TR_K] = st.k;
+        row[TR_FTEST] = st.f_half;
+        row[TR_TV_BEFORE] = st.tv_x;
+        row[TR_ACCEPTED] = -1.0;
+        row[TR_MARGIN] = __longlong_as_double(0x7ff0000000000000LL);
+    }
+    st.trials = 0;
+    st.margin = __longlong_as_double(0x7ff0000000000000LL);
+    st.coef = 0.0;
+    if (st.family != FAM_CG && st.perturb == SCG_PERTURB_GAMMA && st.gnorm2 > 0.0) {
+        if (!st.gamma_fixed) {
+            st.gamma0 = st.gamma0_rel * sqrt(st.xnorm2);
+            st.gamma_fixed = 1;
+        }
+        st.accepted = 0;              // trials pending
+        set_trial_coefs(P);
+    } else {
+        st.accepted = -1;             // no perturbation this k
+        if (row) { row[TR_TV_AFTER] = st.tv_x; row[TR_ELL] = (double)st.ell; }
+    }
+}
+
+template <typename T>
+__device__ void breakdown(const Prob<T>& P) {
+    DevState& st = *P.st;
+    st.done = 1;
+    st.status = SCG_ERR_BREAKDOWN;
+    end_body(P);
+}
+
+template <typename T>
+__device__ void finalize(int step, const Prob<T>& P, const double* S) {
+    DevState& st = *P.st;
+    double* row = trace_row(P, st.iters);
+    switch (step) {
+    case FIN_F:
+        st.f_half = 0.5 * S[0];
+        if (!st.in_init) {
+            if (row) row[TR_F_AFTER] = st.f_half;
+            // f(x_{k+1/2}) <= eps ends the loop at the next test; the rest of
+            // this step only produces x_{k+1}, which is never used.
+            if (!(st.f_half > st.eps)) { st.done = 1; st.status = SCG_OK; end_body(P); }
+        }
+        break;
+    case FIN_BETA: {
+        st.gg = S[1];
+        if (st.in_init) { st.beta = 0.0; break; }
+        if (st.variant == SCG_S_CG_CD) {
+            if (S[1] == 0.0) st.beta = 0.0;
+            else if (!(st.gTp < 0.0) || !isfinite(st.gTp)) { breakdown(P); break; }
+            else st.beta = -S[1] / st.gTp;               // beta = -||g'||^2 / g^T p
+        } else {
+            st.beta = S[0] / st.pTh;                     // beta = g'^T h / p^T h (z'^T h for S-PCG)
+        }
+        if (row) row[TR_BETA] = st.beta;
+        break;
+    }
+    case FIN_NUM:
+        st.num = S[0];                                   // g'^T p'
+        if (st.variant == SCG_S_CG_CD) st.gTp = S[0];
+        break;
+    case FIN_ALPHA:
+        if (finite_pos(S[0])) st.alpha = -st.num / S[0]; // alpha = -g'^T p' / p'^T h'
+        else if (st.gg == 0.0) st.alpha = 0.0;
+        else { breakdown(P); break; }
+        st.pTh = S[0];
+        if (row && !st.in_init) row[TR_ALPHA] = st.alpha;
+        break;
+    case FIN_END:
+        st.tv_x = S[0];
+        st.gnorm2 = S[1];
+        st.xnorm2 = S[2];
+        if (st.in_init) st.in_init = 0;
+        else end_body(P);
+        top_of_loop(P);
+        break;
+    case FIN_TRIAL: {
+        const double base = S[kTrials];
+        int valid = st.max_trials - st.trials;
+        if (valid > kTrials) valid = kTrials;
+        int acc = -1;
+        for (int t = 0; t < valid; ++t) {
+            double rel = fabs(S[t] - base) / (base > 0.0 ? base : 1.0);
+            if (rel < st.margin) st.margin = rel;
+            if (S[t] <= base) { acc = t; break; }
+        }
+        if (acc >= 0) {
+            st.coef = st.trial_coef[acc];
+            st.ell += acc + 1;
+            st.trials += acc + 1;
+            st.accepted = 1;
+            if (row) {
+                row[TR_TRIALS] = st.trials;
+                row[TR_ACCEPTED] = 1.0;
+                row[TR_GAMMA] = st.gamma0 * pow(st.a, (double)(st.ell - 1));
+                row[TR_TV_AFTER] = S[acc];
+                row[TR_ELL] = (double)st.ell;
+                row[TR_MARGIN] = st.margin;
+            }
+        } else {
+            st.ell += valid;
+            st.trials += valid;
+            if (st.trials >= st.max_trials) {
+                st.accepted = 2;                         // gave up: x_{k+1/2} = x_k
+                st.coef = 0.0;
+                if (row) {
+                    row[TR_TRIALS] = st.trials;
+                    row[TR_ACCEPTED] = 0.0;
+                    row[TR_TV_AFTER] = base;
+                    row[TR_ELL] = (double)st.ell;
+                    row[TR_MARGIN] = st.margin;
+                }
+            } else {
+                set_trial_coefs(P);
+            }
+        }
+        break;
+    }
+    case FIN_CG_DELTA:
+        st.delta = (st.variant == SCG_PCG || st.variant == SCG_S_PCG_K) ? S[1] : S[0];
+        st.inner_stop = 0;
+        break;
+    case FIN_CG_ALPHA:
+        if (st.inner_stop) { st.alpha = 0.0; break; }
+        if (finite_pos(S[0])) { st.alpha = st.delta / S[0]; }       // alpha = delta / p^T h
+        else if (st.delta == 0.0) {
+            st.alpha = 0.0;
+            st.inner_stop = 1;
+            if (st.family == FAM_CG) { st.done = 1; st.status = SCG_OK; }
+        } else { breakdown(P); break; }
+        if (row && st.family == FAM_CG) row[TR_ALPHA] = st.alpha;
+        break;
+    case FIN_CG_F:
+        st.f_half = 0.5 * S[0];
+        break;
+    case FIN_CG_BETA: {
+        if (st.inner_stop) { st.beta = 0.0; break; }
+        double dn = (st.variant == SCG_PCG || st.variant == SCG_S_PCG_K) ? S[1] : S[0];
+        st.beta = dn / st.delta;                         // beta = delta' / delta
+        st.delta = dn;
+        if (row && st.family == FAM_CG) row[TR_BETA] = st.beta;
+        break;
+    }
+    case FIN_CG_END:
+        if (st.in_init) st.in_init = 0;
+        else end_body(P);
+        top_of_loop(P);
+        break;
+    case FIN_RESUME:
+        st.pTh = S[0];
+        st.gTp = S[1];
+        break;
+    case FIN_TV:
+        if (P.trace) P.trace[0] = S[0];
+        break;
+    case FIN_FINAL_F:
+        st.f_final = 0.5 * S[0];
+        break;
+    case FIN_FINAL_TV:
+        st.tv_final = S[0];
+        break;
+    default:
+        break;
+    }
+}
+
+}  // namespace scg

@@ -1,0 +1,43 @@
+// scg_kernels.h -- host-side launchers of the kernels in kernels.cu.
+#pragma once
+
+#include "scg_device.cuh"
+
+namespace scg {
+
+enum ProjMode { PROJ_PLAIN = 0, PROJ_RESIDUAL = 1, PROJ_PLAIN_OUT = 2 };
+
+enum VecOp {
+    VEC_INIT = 0,          // X = XH = x0 (AUX or zeros); views
+    VEC_VIEWS = 1,         // views of img[sel]
+    VEC_PERTURB = 2,       // XH = X + coef * TVG; views
+    VEC_FORM_P = 3,        // P = -img[sel] + beta P; views; S0 = G^T P
+    VEC_FORM_P0 = 4,       // P = -img[sel]; views; S0 = G^T P
+    VEC_FORM_P_NOVIEW = 5, // P = -img[sel] + beta P
+    VEC_CG_UPDATE = 6,     // X = img[sel] + alpha P; G += alpha H; S0 = ||G||^2, S1 = G^T Z
+    VEC_DOTS_RESUME = 7    // S0 = P^T H, S1 = G^T P
+};
+
+template <typename T>
+void launch_project(const Prob<T>* d, const Item* items, int grid, int dst, int mode, int step,
+                    cudaStream_t s);
+template <typename T>
+void launch_backproject(const Prob<T>* d, const Item* items, int grid, int nrhs, int src0,
+                        int src1, int dst0, int dst1, int step, cudaStream_t s);
+template <typename T>
+void launch_vec(const Prob<T>* d, const Item* items, int grid, int op, int sel, int step,
+                cudaStream_t s);
+template <typename T>
+void launch_tvgrad(const Prob<T>* d, const Item* items, int grid, int src, int fuse,
+                   int write_grad, int step, cudaStream_t s);
+template <typename T>
+void launch_trial(const Prob<T>* d, const Item* items, int grid, cudaStream_t s);
+template <typename T>
+void launch_sino_axpy(const Prob<T>* d, const Item* items, int grid, int step, cudaStream_t s);
+template <typename T>
+cudaError_t launch_filter(const Prob<T>* d, const Item* items, int grid, int max_nb, int src,
+                          int dst, int plain, cudaStream_t s);
+template <typename T>
+void launch_taps(T* taps, int nb, int P, double mu, double gain, cudaStream_t s);
+
+}  // namespace scg

@@ -1,0 +1,320 @@
+"""Thin ctypes binding of libscg (``include/scg.h``), with the same entry-point
+names.  It only marshals arguments: tensors must already live on a CUDA
+device, workspaces are allocated through PyTorch, and every step of the
+method runs in the library's CUDA kernels.  There is no CPU fallback: if the
+library cannot be loaded every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+from . import build as _build
+
+F64, F32 = 0, 1
+VARIANTS = {"CG": 0, "PCG": 1, "S-CG": 2, "S-CG-CD": 3, "S-CG-K": 4, "S-PCG": 5, "S-PCG-K": 6}
+PERTURB = {"none": 0, "gamma": 1}
+STATUS = {0: "ok", 1: "max_iter", -1: "invalid", -2: "cuda", -3: "workspace", -4: "breakdown",
+          -5: "unsupported"}
+TRACE_FIELDS = ("k", "f_test", "tv_before", "tv_after", "trials", "accepted", "ell",
+                "gamma", "alpha", "beta", "margin", "f_after")
+
+
+class ScgError(RuntimeError):
+    pass
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("n_angles", ctypes.c_int), ("n_bins", ctypes.c_int)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("perturb", ctypes.c_int), ("gamma0", ctypes.c_double),
+                ("gamma0_rel", ctypes.c_double), ("a", ctypes.c_double),
+                ("max_trials", ctypes.c_int), ("K", ctypes.c_int), ("k_inclusive", ctypes.c_int),
+                ("mu", ctypes.c_double), ("filter_gain", ctypes.c_double),
+                ("max_iter", ctypes.c_int)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("k_final", ctypes.c_int), ("status", ctypes.c_int),
+                ("f_final", ctypes.c_double), ("tv_final", ctypes.c_double),
+                ("ell", ctypes.c_longlong), ("gamma0_used", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int), ("body_launches", ctypes.c_int)]
+
+
+class State(ctypes.Structure):
+    _fields_ = [("valid", ctypes.c_int), ("k", ctypes.c_int), ("ell", ctypes.c_longlong),
+                ("gamma0", ctypes.c_double), ("gamma_fixed", ctypes.c_int),
+                ("delta", ctypes.c_double), ("x", ctypes.c_void_p), ("x_half", ctypes.c_void_p),
+                ("p", ctypes.c_void_p), ("h", ctypes.c_void_p), ("g", ctypes.c_void_p)]
+
+
+STATE_VECTORS = ("x", "x_half", "p", "h", "g")
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True):
+    """Load libscg.so (building it first when sources are newer)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_needed else _build.LIB
+    if not os.path.exists(path):
+        raise ScgError(f"libscg not built: {path}")
+    L = ctypes.CDLL(path)
+    vp, sz, i, d = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_double
+    gp = ctypes.POINTER(Geometry)
+    L.scg_strerror.restype = ctypes.c_char_p
+    L.scg_strerror.argtypes = [i]
+    L.scg_default_params.argtypes = [ctypes.POINTER(Params)]
+    L.scg_op_workspace_bytes.restype = sz
+    L.scg_op_workspace_bytes.argtypes = [gp, i]
+    L.scg_solve_workspace_bytes.restype = sz
+    L.scg_solve_workspace_bytes.argtypes = [gp, i, i]
+    L.scg_project.argtypes = [gp, i, vp, vp, vp, sz, vp]
+    L.scg_backproject.argtypes = [gp, i, vp, vp, vp, sz, vp]
+    L.scg_tv.argtypes = [i, i, vp, vp, vp, sz, vp]
+    L.scg_tv_grad.argtypes = [i, i, vp, vp, vp, vp, sz, vp]
+    L.scg_filter.argtypes = [gp, i, d, d, vp, vp, vp, sz, vp]
+    L.scg_solve.argtypes = [gp, i, i, ctypes.POINTER(Params), d, vp, vp, vp, vp, sz,
+                            ctypes.POINTER(Result), ctypes.POINTER(ctypes.c_double), i,
+                            ctypes.POINTER(State), ctypes.POINTER(State), vp]
+    for name in ("scg_project", "scg_backproject", "scg_tv", "scg_tv_grad", "scg_filter", "scg_solve"):
+        getattr(L, name).restype = i
+    _lib = L
+    return L
+
+
+def _check(rc: int, what: str, ok=(0,)):
+    if rc not in ok:
+        msg = load().scg_strerror(rc).decode()
+        raise ScgError(f"{what} failed: {rc} ({msg})")
+
+
+def _prec(t: torch.Tensor) -> int:
+    if t.dtype == torch.float64:
+        return F64
+    if t.dtype == torch.float32:
+        return F32
+    raise ScgError(f"unsupported dtype {t.dtype}")
+
+
+def _dev_ptr(t: torch.Tensor, name: str) -> int:
+    if not t.is_cuda:
+        raise ScgError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ScgError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+_workspaces: dict = {}
+
+
+def workspace(nbytes: int, device, tag: str) -> torch.Tensor:
+    """Cached device workspace (one per tag and device)."""
+    key = (tag, str(device))
+    w = _workspaces.get(key)
+    if w is None or w.numel() < nbytes:
+        w = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+        _workspaces[key] = w
+    return w
+
+
+def geometry(n: int, n_angles: int, n_bins: int) -> Geometry:
+    return Geometry(int(n), int(n_angles), int(n_bins))
+
+
+def op_workspace_bytes(n: int, n_angles: int, n_bins: int, precision: int) -> int:
+    g = geometry(n, n_angles, n_bins)
+    return int(load().scg_op_workspace_bytes(ctypes.byref(g), precision))
+
+
+def solve_workspace_bytes(n: int, n_angles: int, n_bins: int, variant: str, precision: int) -> int:
+    g = geometry(n, n_angles, n_bins)
+    return int(load().scg_solve_workspace_bytes(ctypes.byref(g), VARIANTS[variant], precision))
+
+
+def scg_project(x: torch.Tensor, n_angles: int, n_bins: int, out: torch.Tensor | None = None):
+    """y = A x on the device (x: N x N)."""
+    n = x.shape[-1]
+    prec = _prec(x)
+    if out is None:
+        out = torch.empty((n_angles, n_bins), dtype=x.dtype, device=x.device)
+    g = geometry(n, n_angles, n_bins)
+    nb = load().scg_op_workspace_bytes(ctypes.byref(g), prec)
+    w = workspace(nb, x.device, "op")
+    rc = load().scg_project(ctypes.byref(g), prec, _dev_ptr(x, "x"), _dev_ptr(out, "y"),
+                            w.data_ptr(), w.numel(), _stream(x.device))
+    _check(rc, "scg_project")
+    return out
+
+
+def scg_backproject(r: torch.Tensor, n: int, out: torch.Tensor | None = None):
+    """x = A^T r on the device (r: n_angles x n_bins)."""
+    na, nbins = r.shape
+    prec = _prec(r)
+    if out is None:
+        out = torch.empty((n, n), dtype=r.dtype, device=r.device)
+    g = geometry(n, na, nbins)
+    nb = load().scg_op_workspace_bytes(ctypes.byref(g), prec)
+    w = workspace(nb, r.device, "op")
+    rc = load().scg_backproject(ctypes.byref(g), prec, _dev_ptr(r, "r"), _dev_ptr(out, "x"),
+                                w.data_ptr(), w.numel(), _stream(r.device))
+    _check(rc, "scg_backproject")
+    return out
+
+
+def scg_tv(x: torch.Tensor) -> torch.Tensor:
+    """TV(x) as a 0-d float64 device tensor."""
+    n = x.shape[-1]
+    prec = _prec(x)
+    out = torch.zeros((), dtype=torch.float64, device=x.device)
+    g = geometry(n, 1, 1)
+    nb = load().scg_op_workspace_bytes(ctypes.byref(g), prec)
+    w = workspace(nb, x.device, "op")
+    rc = load().scg_tv(n, prec, _dev_ptr(x, "x"), out.data_ptr(), w.data_ptr(), w.numel(),
+                       _stream(x.device))
+    _check(rc, "scg_tv")
+    return out
+
+
+def scg_tv_grad(x: torch.Tensor):
+    """(subgradient of TV at x, TV(x) as a 0-d float64 device tensor)."""
+    n = x.shape[-1]
+    prec = _prec(x)
+    out = torch.zeros((), dtype=torch.float64, device=x.device)
+    grad = torch.empty_like(x)
+    g = geometry(n, 1, 1)
+    nb = load().scg_op_workspace_bytes(ctypes.byref(g), prec)
+    w = workspace(nb, x.device, "op")
+    rc = load().scg_tv_grad(n, prec, _dev_ptr(x, "x"), grad.data_ptr(), out.data_ptr(),
+                            w.data_ptr(), w.numel(), _stream(x.device))
+    _check(rc, "scg_tv_grad")
+    return grad, out
+
+
+def scg_filter(r: torch.Tensor, mu: float = 0.0, gain: float = 1.0) -> torch.Tensor:
+    """Row filter F^T C F r of the preconditioner."""
+    na, nbins = r.shape
+    prec = _prec(r)
+    out = torch.empty_like(r)
+    g = geometry(2, na, nbins)
+    nb = load().scg_op_workspace_bytes(ctypes.byref(g), prec)
+    w = workspace(nb, r.device, "op")
+    rc = load().scg_filter(ctypes.byref(g), prec, float(mu), float(gain), _dev_ptr(r, "r"),
+                           out.data_ptr(), w.data_ptr(), w.numel(), _stream(r.device))
+    _check(rc, "scg_filter")
+    return out
+
+
+def default_params(**kw) -> dict:
+    p = Params()
+    load().scg_default_params(ctypes.byref(p))
+    d = {name: getattr(p, name) for name, _ in Params._fields_}
+    d["perturb"] = "gamma" if d["perturb"] == 1 else "none"
+    d.update(kw)
+    return d
+
+
+def _params(d: dict) -> Params:
+    return Params(PERTURB[d["perturb"]], float(d["gamma0"]), float(d["gamma0_rel"]), float(d["a"]),
+                  int(d["max_trials"]), int(d["K"]), int(d["k_inclusive"]), float(d["mu"]),
+                  float(d["filter_gain"]), int(d["max_iter"]))
+
+
+@dataclass
+class SolveResult:
+    x: torch.Tensor
+    iters: int
+    k_final: int
+    status: str
+    status_code: int
+    f_final: float
+    tv_final: float
+    ell: int
+    gamma0_used: float
+    kernel_launches: int = 0
+    body_launches: int = 0
+    trace: object = None
+    state: dict | None = None
+
+
+def scg_solve(y: torch.Tensor, n: int, variant: str = "S-CG", eps: float = 1.0, x0=None,
+              trace: bool = False, resume: dict | None = None, want_state: bool = False,
+              out: torch.Tensor | None = None, work: torch.Tensor | None = None, **params):
+    """Run one solver on the device.  ``y`` is the n_angles x n_bins sinogram.
+
+    ``resume``/``want_state`` carry the state dict of ``include/scg.h``'s
+    scg_state (vectors as N x N device tensors)."""
+    import numpy as np
+
+    L = load()
+    na, nbins = y.shape
+    prec = _prec(y)
+    g = geometry(n, na, nbins)
+    p = _params(default_params(**params))
+    nbytes = L.scg_solve_workspace_bytes(ctypes.byref(g), VARIANTS[variant], prec)
+    if work is None:
+        work = workspace(nbytes, y.device, "solve")
+    if out is None:
+        out = torch.empty((n, n), dtype=y.dtype, device=y.device)
+    x0p = None
+    if x0 is not None:
+        x0 = x0.to(dtype=y.dtype).contiguous()
+        x0p = _dev_ptr(x0, "x0")
+    res = Result()
+    rows = max(int(p.max_iter), 1)
+    tr = np.zeros((rows, len(TRACE_FIELDS))) if trace else None
+    trp = tr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if trace else None
+    keep = []
+    rs = None
+    if resume is not None:
+        R = State()
+        R.valid = 1
+        R.k = int(resume["k"])
+        R.ell = int(resume["ell"])
+        R.gamma0 = float(resume["gamma0"])
+        R.gamma_fixed = int(resume["gamma_fixed"])
+        R.delta = float(resume.get("delta", 0.0))
+        for name in STATE_VECTORS:
+            v = resume.get(name)
+            if v is not None:
+                v = v.to(device=y.device, dtype=y.dtype).contiguous()
+                keep.append(v)
+                setattr(R, name, v.data_ptr())
+        rs = ctypes.byref(R)
+    fs = None
+    fs_t = {}
+    if want_state:
+        F = State()
+        for name in STATE_VECTORS:
+            fs_t[name] = torch.zeros((n, n), dtype=y.dtype, device=y.device)
+            setattr(F, name, fs_t[name].data_ptr())
+        fs = F
+    rc = L.scg_solve(ctypes.byref(g), VARIANTS[variant], prec, ctypes.byref(p), float(eps),
+                     _dev_ptr(y, "y"), x0p, _dev_ptr(out, "x_out"), work.data_ptr(), work.numel(),
+                     ctypes.byref(res), trp, rows if trace else 0, rs,
+                     ctypes.byref(fs) if fs is not None else None, _stream(y.device))
+    _check(rc, "scg_solve", ok=(0, 1, -4))
+    out_res = SolveResult(out, res.iters, res.k_final, STATUS.get(res.status, str(res.status)),
+                          res.status, res.f_final, res.tv_final, res.ell, res.gamma0_used,
+                          res.kernel_launches, res.body_launches)
+    if trace:
+        out_res.trace = tr[: min(res.iters, rows)].copy()
+    if want_state:
+        st = dict(k=fs.k, ell=fs.ell, gamma0=fs.gamma0, gamma_fixed=fs.gamma_fixed, delta=fs.delta)
+        st.update(fs_t)
+        out_res.state = st
+    return out_res

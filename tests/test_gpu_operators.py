@@ -1,0 +1,144 @@
+"""GPU <-> oracle parity of the operators, through the C ABI.
+
+A (ray-driven projector), A^T (pixel-driven backprojector), TV, its
+subgradient and the preconditioner's row filter, on seeded inputs.  Small
+cases (several tiles plus ragged tails, axis-aligned and diagonal angles, odd
+and even sizes) are compared element by element; the full-size workloads are
+compared on sampled rays/pixels that the oracle evaluates one by one.
+
+Tolerances: relative L2 <= 1e-5 for FP32 (FP32 geometry and accumulation over
+at most ~2N weights per ray; the measured error is ~1e-7), <= 1e-12 for FP64.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1709_04912_gb300 import inputs, scg
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+TOL = {torch.float32: 1e-5, torch.float64: 1e-12}
+
+CASES = [
+    (64, 90, 95),       # the FP64 workload's shape
+    (77, 33, 110),      # ragged tiles (N % 32, N % 8 != 0), bins % 128 != 0
+    (130, 181, 185),    # several tiles and ray blocks, odd angle count
+    (33, 4, 47),        # angles 0, 45, 90, 135 degrees only
+    (40, 1, 57),        # a single angle (theta = 0: every ray on pixel edges)
+    (2, 3, 3),          # smallest image
+]
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def image(n, seed):
+    x = inputs.ellipse_phantom(n, 8, seed)
+    return x + 0.1 * inputs.normal(seed, "img", n * n).reshape(n, n)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    assert torch.cuda.is_available()
+    return scg.load()
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("n,na,nb", CASES)
+def test_project_matches_oracle(n, na, nb, dtype):
+    x = image(n, n + na)
+    ref = oracle.project(x, na, nb)
+    got = scg.scg_project(torch.tensor(x, dtype=dtype, device=DEV), na, nb).cpu().numpy()
+    assert rel(got, ref) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("n,na,nb", CASES)
+def test_backproject_matches_oracle(n, na, nb, dtype):
+    r = inputs.normal(7 * n + na, "sino", na * nb).reshape(na, nb)
+    ref = oracle.backproject(r, n)
+    got = scg.scg_backproject(torch.tensor(r, dtype=dtype, device=DEV), n).cpu().numpy()
+    assert rel(got, ref) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("n,na,nb", [(64, 90, 95), (130, 181, 185)])
+def test_pair_is_adjoint_in_fp32(n, na, nb):
+    x = torch.tensor(image(n, 3), dtype=torch.float32, device=DEV)
+    r = torch.tensor(inputs.normal(9, "r", na * nb).reshape(na, nb), dtype=torch.float32, device=DEV)
+    ax = scg.scg_project(x, na, nb).double()
+    atr = scg.scg_backproject(r, n).double()
+    lhs = float((ax * r.double()).sum())
+    rhs = float((x.double() * atr).sum())
+    assert abs(lhs - rhs) <= 1e-6 * (abs(lhs) + 1e-12)
+
+
+def test_pair_uses_identical_weights():
+    # dense A from unit images and dense A^T from unit sinograms, both in FP32:
+    # every weight the backprojector uses is the projector's (matched pair)
+    n, na, nb = 8, 12, 12
+    A = np.zeros((na * nb, n * n))
+    for q in range(n * n):
+        e = torch.zeros(n * n, dtype=torch.float32, device=DEV)
+        e[q] = 1
+        A[:, q] = scg.scg_project(e.view(n, n), na, nb).cpu().numpy().ravel()
+    AT = np.zeros((n * n, na * nb))
+    for q in range(na * nb):
+        e = torch.zeros(na * nb, dtype=torch.float32, device=DEV)
+        e[q] = 1
+        AT[:, q] = scg.scg_backproject(e.view(na, nb), n).cpu().numpy().ravel()
+    assert np.max(np.abs(A - AT.T)) <= 2e-6
+    assert np.mean(A == AT.T) > 0.999
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("n", [2, 7, 64, 77, 130])
+def test_tv_and_subgradient_match_oracle(n, dtype):
+    x = image(n, n)
+    tv_ref, g_ref = oracle.tv_grad(x)
+    xt = torch.tensor(x, dtype=dtype, device=DEV)
+    grad, tv = scg.scg_tv_grad(xt)
+    tv_only = float(scg.scg_tv(xt))
+    tol = 1e-6 if dtype == torch.float32 else 1e-12
+    assert abs(float(tv) - tv_ref) <= tol * max(tv_ref, 1e-12)
+    assert tv_only == float(tv)
+    assert rel(grad.cpu().numpy(), g_ref) <= (1e-5 if dtype == torch.float32 else 1e-12)
+
+
+def test_tv_of_constant_is_zero_on_device():
+    grad, tv = scg.scg_tv_grad(torch.full((50, 50), 2.5, device=DEV))
+    assert float(tv) == 0.0 and float(grad.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("na,nb,mu,gain", [(5, 95, 0.0, 1.0), (3, 130, 0.02, 2.0), (2, 725, 0.0, 1.0)])
+def test_filter_matches_oracle(na, nb, mu, gain, dtype):
+    r = inputs.normal(nb, "f", na * nb).reshape(na, nb)
+    ref = oracle.filter_rows(r, mu, gain)
+    got = scg.scg_filter(torch.tensor(r, dtype=dtype, device=DEV), mu, gain).cpu().numpy()
+    assert rel(got, ref) <= (1e-5 if dtype == torch.float32 else 1e-11)
+
+
+@pytest.mark.parametrize("work", [inputs.SINGLE_512, inputs.MIXED_1024], ids=lambda w: w.name)
+def test_full_size_operators_on_sampled_outputs(work):
+    n, na, nb = work.n, work.n_angles, work.n_bins
+    x = inputs.ellipse_phantom(n, work.n_ellipses, 0)
+    y = scg.scg_project(torch.tensor(x, dtype=torch.float32, device=DEV), na, nb).cpu().numpy()
+    rng = np.random.default_rng(1)
+    a = rng.integers(0, na, 300)
+    b = rng.integers(0, nb, 300)
+    a[:4] = [0, na // 2, na // 4, na - 1]          # axis-aligned and diagonal angles
+    ref = oracle.project_rays(x, na, nb, a, b)
+    assert rel(y[a, b], ref) <= 1e-5
+    r = inputs.normal(2, "r", na * nb).reshape(na, nb)
+    g = scg.scg_backproject(torch.tensor(r, dtype=torch.float32, device=DEV), n).cpu().numpy()
+    i = rng.integers(0, n, 200)
+    j = rng.integers(0, n, 200)
+    i[:2] = [0, n - 1]
+    j[:2] = [0, n - 1]
+    refp = oracle.backproject_pixels(r, n, i, j)
+    assert rel(g[i, j], refp) <= 1e-5

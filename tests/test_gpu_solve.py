@@ -1,0 +1,181 @@
+"""GPU <-> oracle parity of whole solves and single loop bodies, through the
+C ABI (scg_solve).
+
+* FP64, the 64x64 / 90 x 95 workload, every variant: same iteration count,
+  same status, same perturbation decisions (trials, accepted, l) and output x
+  within 1e-9 relative L2 (the oracle's own sensitivity to a 1e-13 data
+  perturbation on this workload is <= 5e-11).
+* FP32, same workload: same decisions where the oracle's TV margin exceeds
+  1e-5, output within 2e-4 relative L2 (FP32 rounding ~6e-8 amplified by the
+  solve's conditioning; measured values are printed).
+* One loop body from a state the oracle exported (k = 4): every vector of the
+  new state within 1e-5 (FP32) / 1e-11 (FP64).
+* Resume from an exported GPU state is bit-exact.
+* Edge cases: f(x0) <= eps (no iteration), max_iter = 0, x0 != 0, no
+  perturbation (S-CG reproduces CG's first iterates).
+* Full-size 512x512 / 720 x 725 S-CG: f(output) <= eps checked with the
+  oracle's A, lower TV than CG at the same eps.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1709_04912_gb300 import inputs, scg
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+VARIANTS = ["CG", "PCG", "S-CG", "S-CG-CD", "S-CG-K", "S-PCG", "S-PCG-K"]
+DECISION = [4, 5, 6]          # trace columns: trials, accepted, l
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def kw_for(variant, prob, **extra):
+    kw = dict(variant=variant, eps=prob.eps, gamma0_rel=0.05, max_iter=100)
+    if variant in ("CG", "PCG"):
+        kw["perturb"] = "none"
+    kw.update(extra)
+    return kw
+
+
+@pytest.fixture(scope="module")
+def small():
+    return inputs.make_problem(inputs.SMALL_FP64, 0, oracle.project)
+
+
+def gpu_solve(prob, dtype, **kw):
+    y = torch.tensor(prob.y, dtype=dtype, device=DEV)
+    variant = kw.pop("variant")
+    eps = kw.pop("eps")
+    x0 = kw.pop("x0", None)
+    if x0 is not None:
+        x0 = torch.tensor(x0, dtype=dtype, device=DEV)
+    return scg.scg_solve(y, prob.work.n, variant, eps, x0=x0, trace=True, **kw)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_fp64_whole_solve_matches_oracle(small, variant):
+    kw = kw_for(variant, small)
+    xo, ro, to = oracle.solve(small.y, small.work.n, **kw)
+    r = gpu_solve(small, torch.float64, **kw)
+    assert r.status == ro["status"] and r.iters == ro["iters"] and r.k_final == ro["k_final"]
+    assert r.ell == ro["ell"]
+    np.testing.assert_array_equal(r.trace[:, DECISION], to[:, DECISION])
+    assert rel(r.x.cpu().numpy(), xo) <= 1e-9
+    assert r.f_final == pytest.approx(ro["f_final"], rel=1e-9)
+    assert r.tv_final == pytest.approx(ro["tv_final"], rel=1e-9)
+    # trace values the oracle also records (the last row's alpha/beta belong
+    # to a step whose result is never used; the device skips that step)
+    np.testing.assert_allclose(r.trace[:, 1:4], to[:, 1:4], rtol=1e-9)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_fp32_whole_solve_matches_oracle(small, variant):
+    kw = kw_for(variant, small)
+    xo, ro, to = oracle.solve(small.y, small.work.n, **kw)
+    r = gpu_solve(small, torch.float32, **kw)
+    err = rel(r.x.cpu().numpy(), xo)
+    print(f"{variant}: iters gpu {r.iters} oracle {ro['iters']}  rel L2 {err:.2e}  "
+          f"tv {r.tv_final:.4f}/{ro['tv_final']:.4f}")
+    assert r.status == ro["status"]
+    robust = np.all(to[:, 10] > 1e-5)                 # no near-tie TV decision
+    if robust:
+        assert r.iters == ro["iters"]
+        np.testing.assert_array_equal(r.trace[:, DECISION], to[:, DECISION])
+        assert err <= 2e-4
+    assert r.f_final <= small.eps
+    assert r.tv_final == pytest.approx(ro["tv_final"], rel=1e-3)
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-11), (torch.float32, 1e-5)])
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_single_loop_body_from_oracle_state(small, variant, dtype, tol):
+    # run the oracle to the top of loop body 4, export its state; take one
+    # body on both sides from that state and compare the new states
+    kw = kw_for(variant, small, eps=small.eps * 1e-3)
+    _, r1, _, st = oracle.solve(small.y, small.work.n, max_iter=4, want_state=True, **kw)
+    assert r1["status"] == "max_iter"
+    xo, ro, to, st_o = oracle.solve(small.y, small.work.n, max_iter=1, resume=st, want_state=True, **kw)
+    resume = dict(st)
+    for name in scg.STATE_VECTORS:
+        resume[name] = torch.tensor(st[name], dtype=dtype, device=DEV)
+    r = gpu_solve(small, dtype, max_iter=1, resume=resume, want_state=True, **kw)
+    assert r.iters == 1 and r.status == "max_iter"
+    np.testing.assert_array_equal(r.trace[:, DECISION], to[:, DECISION])
+    assert r.state["k"] == st_o["k"] and r.state["ell"] == st_o["ell"]
+    used = {"CG": ("x", "p", "g"), "PCG": ("x", "p", "g"), "S-CG": ("x", "x_half", "p", "h"),
+            "S-PCG": ("x", "x_half", "p", "h"), "S-CG-CD": ("x", "x_half", "p", "g"),
+            "S-CG-K": ("x", "x_half"), "S-PCG-K": ("x", "x_half")}[variant]
+    for name in used:
+        e = rel(r.state[name].cpu().numpy(), st_o[name])
+        assert e <= tol, (name, e)
+    if variant in ("CG", "PCG"):
+        assert r.state["delta"] == pytest.approx(st_o["delta"], rel=max(tol, 1e-10) * 10)
+
+
+@pytest.mark.parametrize("variant", ["S-CG", "S-CG-CD", "S-PCG-K", "CG"])
+def test_resume_from_gpu_state_is_exact(small, variant):
+    kw = kw_for(variant, small, eps=small.eps * 1e-3)
+    full = gpu_solve(small, torch.float32, max_iter=7, **kw)
+    a = gpu_solve(small, torch.float32, max_iter=3, want_state=True, **kw)
+    b = gpu_solve(small, torch.float32, max_iter=4, resume=a.state, **kw)
+    assert a.iters + b.iters == full.iters
+    assert b.ell == full.ell
+    if variant == "CG":
+        # the recursive residual restarts from a fresh A x_k - y on resume
+        assert rel(b.x.cpu().numpy(), full.x.cpu().numpy()) <= 1e-5
+    else:
+        assert torch.equal(b.x, full.x)
+
+
+def test_eps_already_met_runs_no_iteration(small):
+    r = gpu_solve(small, torch.float32, variant="S-CG", eps=1e30)
+    assert r.iters == 0 and r.status == "ok" and float(r.x.abs().max()) == 0.0
+
+
+def test_max_iter_zero(small):
+    r = gpu_solve(small, torch.float64, variant="S-CG-CD", eps=small.eps, max_iter=0)
+    xo, ro, _ = oracle.solve(small.y, small.work.n, variant="S-CG-CD", eps=small.eps, max_iter=0)
+    assert r.status == "max_iter" == ro["status"] and r.iters == 0
+    assert rel(r.x.cpu().numpy(), xo) <= 1e-12
+
+
+@pytest.mark.parametrize("variant", ["S-CG", "S-PCG-K", "CG"])
+def test_nonzero_start(small, variant):
+    x0 = 0.5 * small.x_true + 0.01
+    kw = kw_for(variant, small)
+    xo, ro, _ = oracle.solve(small.y, small.work.n, x0=x0, **kw)
+    r = gpu_solve(small, torch.float64, x0=x0, **kw)
+    assert r.iters == ro["iters"]
+    assert rel(r.x.cpu().numpy(), xo) <= 1e-9
+
+
+def test_unperturbed_s_cg_equals_cg_on_device(small):
+    kw = dict(eps=small.eps * 1e-3, perturb="none")
+    cg = gpu_solve(small, torch.float64, variant="CG", max_iter=4, **kw)
+    s = gpu_solve(small, torch.float64, variant="S-CG", max_iter=3, **kw)
+    # S-CG's output after 3 bodies is x_{3+1/2} = x_3 (no perturbation); CG's after 4... compare x_3
+    cg3 = gpu_solve(small, torch.float64, variant="CG", max_iter=3, **kw)
+    assert rel(s.x.cpu().numpy(), cg3.x.cpu().numpy()) <= 1e-10
+    assert cg.iters == 4
+
+
+def test_full_size_single_solve_properties():
+    work = inputs.SINGLE_512
+    prob = inputs.make_problem(work, 0, oracle.project)
+    y = torch.tensor(prob.y, dtype=torch.float32, device=DEV)
+    s = scg.scg_solve(y, work.n, "S-CG", prob.eps, gamma0_rel=0.05, trace=True)
+    c = scg.scg_solve(y, work.n, "CG", prob.eps, perturb="none")
+    assert s.status == "ok" and c.status == "ok"
+    x = s.x.cpu().numpy().astype(np.float64)
+    f = 0.5 * np.sum((prob.y - oracle.project(x, work.n_angles, work.n_bins)) ** 2)
+    assert f <= prob.eps * (1 + 1e-5)
+    assert f == pytest.approx(s.f_final, rel=1e-5)
+    assert s.tv_final < c.tv_final
+    acc = s.trace[:, 5] == 1
+    assert np.all(s.trace[acc, 3] <= s.trace[acc, 2])
