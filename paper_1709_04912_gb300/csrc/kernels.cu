@@ -35,11 +35,11 @@ __device__ __forceinline__ Item decode_item(const Prob<T>* probs, const Item* it
 // ---------------------------------------------------------------------------
 // Forward projector.  One thread per ray (a, b), kRayBlock consecutive bins of
 // one angle per block, so the sinogram writes are coalesced.  The ray is walked
-// along its driving axis (columns when |sin| >= |cos|, else rows); at each
-// step the two pixels whose centres lie within one pixel of the crossing are
-// the only ones the chord can touch ((m+n)/2m <= 1), and both are read from the
-// view whose lines run across the driving axis, so a warp's 32 rays read one
-// short contiguous span.
+// along its driving axis (columns when |sin| >= |cos|, else rows); in each
+// column (row) strip its chord is 1/m and falls on the two pixels nearest the
+// crossing, split u : (1-u) by one saturating FMA of the crossing's fractional
+// part (see Angle).  Both pixels are read from the view whose lines run across
+// the driving axis, so a warp's 32 rays read one short contiguous span.
 template <typename T>
 __global__ void __launch_bounds__(kRayBlock)
 k_project(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int dst_sel,
@@ -51,53 +51,51 @@ k_project(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int
     const int a = it.u;
     const int b = it.v * kRayBlock + threadIdx.x;
     const Angle<T> g = P.ang[a];
-    const T off_n = P.off_n;
     T acc = T(0);
     if (b < nb) {
         const T sb = T(b) - P.off_b;
-        // crossing coordinate along the non-driving axis: c*(t) = c0 + t*slope
-        const T inv = g.inv_drive;
-        T slope, c0;
-        const T* V;
-        if (g.col_driven) { slope = -g.c * inv; c0 = sb * inv + off_n * (g.c * inv + T(1)); V = P.view_cm; }
-        else              { slope = -g.s * inv; c0 = sb * inv + off_n * (g.s * inv + T(1)); V = P.view_rm; }
+        // crossing on the non-driving axis at driving index t: c*(t) = c0 + t * slope
+        const T slope = g.slope;
+        const T c0 = fma(sb, g.inv_drive, g.c0_off);
+        const T* V = g.col_driven ? P.view_cm : P.view_rm;
         int tlo = 0, thi = N - 1;
         const T lo_c = T(-1.5), hi_c = T(N) + T(0.5);
         if (tabs(slope) < T(1e-6)) {
             if (!(c0 >= lo_c && c0 <= hi_c)) thi = -1;
         } else {
-            T t1 = (lo_c - c0) / slope, t2 = (hi_c - c0) / slope;
-            T lo = tmax(tmin(t1, t2), T(-1)), hi = tmin(tmax(t1, t2), T(N));
+            const T t1 = (lo_c - c0) / slope, t2 = (hi_c - c0) / slope;
+            const T lo = tmax(tmin(t1, t2), T(-1)), hi = tmin(tmax(t1, t2), T(N));
             tlo = max(0, (int)tfloor(lo));
             thi = min(N - 1, (int)tfloor(hi) + 1);
         }
-        if (g.col_driven) {
-            for (int j = tlo; j <= thi; ++j) {
-                const T xcc = mul_rn(T(j) - off_n, g.c);
-                const T cs = fma_rn(T(j), slope, c0);
-                int i0 = (int)tfloor(cs);
-                i0 = min(max(i0, -kPad), N + kPad - 2);
-                const T yc0 = T(i0) - off_n;
-                const T d0 = sub_rn(sb, ray_offset(xcc, yc0, g.s));
-                const T d1 = sub_rn(sb, ray_offset(xcc, yc0 + T(1), g.s));
-                const T* line = V + (size_t)j * S + kPad + i0;
-                acc = fma(chord(d0, g), __ldg(line), acc);
-                acc = fma(chord(d1, g), __ldg(line + 1), acc);
-            }
-        } else {
-            for (int i = tlo; i <= thi; ++i) {
-                const T yc = T(i) - off_n;
-                const T cs = fma_rn(T(i), slope, c0);
-                int j0 = (int)tfloor(cs);
-                j0 = min(max(j0, -kPad), N + kPad - 2);
-                const T xc0 = T(j0) - off_n;
-                const T d0 = sub_rn(sb, ray_offset(mul_rn(xc0, g.c), yc, g.s));
-                const T d1 = sub_rn(sb, ray_offset(mul_rn(xc0 + T(1), g.c), yc, g.s));
-                const T* line = V + (size_t)i * S + kPad + j0;
-                acc = fma(chord(d0, g), __ldg(line), acc);
-                acc = fma(chord(d1, g), __ldg(line + 1), acc);
-            }
+        const T k2 = g.k2, h2 = g.h2;
+        const T* line = V + (size_t)tlo * S + kPad;
+        T tf = T(tlo);
+        T acc0 = T(0), acc1 = T(0);
+        int t = tlo;
+        for (; t + 1 <= thi; t += 2) {
+            const T cs0 = fma(tf, slope, c0);
+            const T cs1 = fma(tf + T(1), slope, c0);
+            const T fl0 = tfloor(cs0), fl1 = tfloor(cs1);
+            const int i0 = min(max((int)fl0, -kPad), N + kPad - 2);
+            const int i1 = min(max((int)fl1, -kPad), N + kPad - 2);
+            const T a0 = __ldg(line + i0), b0 = __ldg(line + i0 + 1);
+            const T a1 = __ldg(line + S + i1), b1 = __ldg(line + S + i1 + 1);
+            const T u0 = sat(fma(fl0 - cs0, k2, h2));
+            const T u1 = sat(fma(fl1 - cs1, k2, h2));
+            acc0 += fma(u0, a0 - b0, b0);
+            acc1 += fma(u1, a1 - b1, b1);
+            line += 2 * S;
+            tf += T(2);
         }
+        if (t <= thi) {
+            const T cs0 = fma(tf, slope, c0);
+            const T fl0 = tfloor(cs0);
+            const int i0 = min(max((int)fl0, -kPad), N + kPad - 2);
+            const T a0 = __ldg(line + i0), b0 = __ldg(line + i0 + 1);
+            acc0 += fma(sat(fma(fl0 - cs0, k2, h2)), a0 - b0, b0);
+        }
+        acc = (acc0 + acc1) * g.inv_m;
     }
     double v[1] = {0.0};
     if (b < nb) {
@@ -111,10 +109,10 @@ k_project(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int
 }
 
 // ---------------------------------------------------------------------------
-// Backprojector: one thread per pixel, all angles; the two candidate bins of
-// each angle are the only ones within (m+n)/2 <= 1/sqrt(2) of the pixel's
-// projected centre.  The weights are computed exactly as in k_project, so the
-// pair is matched to the last bit of every weight.
+// Backprojector: one thread per pixel, all angles.  A pixel whose centre
+// projects to bin coordinate cb can only meet bins floor(cb) and floor(cb)+1
+// ((m+n)/2 <= 1/sqrt(2)); their weights are two saturating FMAs of the
+// fractional part (see Angle).  The angle table is staged in shared memory.
 template <typename T, int NRHS>
 __global__ void __launch_bounds__(kTileThreads)
 k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int src0,
@@ -122,6 +120,8 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
     const Item it = decode_item(probs, items, 1);
     const Prob<T>& P = probs[it.prob];
     if (P.st->done) return;
+    constexpr int kChunk = 128;
+    __shared__ Angle<T> tab[kChunk];
     const int N = P.n, na = P.na, nb = P.nb, SB = P.SB;
     const int i = it.u * kTileH + threadIdx.x / kTileW;
     const int j = it.v * kTileW + threadIdx.x % kTileW;
@@ -130,21 +130,29 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
     const T* R0 = P.sino[src0] + kSPad;
     const T* R1 = NRHS == 2 ? P.sino[src1] + kSPad : nullptr;
     T acc0 = T(0), acc1 = T(0);
-    if (in) {
-        for (int a = 0; a < na; ++a) {
-            const Angle<T> g = P.ang[a];
-            const T p = ray_offset(mul_rn(xc, g.c), yc, g.s);
-            int b0 = (int)tfloor(p + off_b);
-            b0 = min(max(b0, -kSPad), nb + kSPad - 2);
-            const T sb0 = T(b0) - off_b;
-            const T w0 = chord(sub_rn(sb0, p), g);
-            const T w1 = chord(sub_rn(sb0 + T(1), p), g);
-            const size_t o = (size_t)a * SB + b0;
-            acc0 = fma(w0, __ldg(R0 + o), acc0);
-            acc0 = fma(w1, __ldg(R0 + o + 1), acc0);
-            if (NRHS == 2) {
-                acc1 = fma(w0, __ldg(R1 + o), acc1);
-                acc1 = fma(w1, __ldg(R1 + o + 1), acc1);
+    for (int a0 = 0; a0 < na; a0 += kChunk) {
+        const int cnt = min(kChunk, na - a0);
+        __syncthreads();
+        for (int q = threadIdx.x; q < cnt; q += blockDim.x) tab[q] = P.ang[a0 + q];
+        __syncthreads();
+        if (in) {
+            const T* r0 = R0 + (size_t)a0 * SB;
+            const T* r1 = NRHS == 2 ? R1 + (size_t)a0 * SB : nullptr;
+#pragma unroll 4
+            for (int q = 0; q < cnt; ++q) {
+                const Angle<T>& g = tab[q];
+                const T cb = fma(yc, g.s, fma(xc, g.c, off_b));
+                const T fl = tfloor(cb);
+                const T fr = cb - fl;
+                const int b0 = min(max((int)fl, -kSPad), nb + kSPad - 2);
+                const T w0 = sat(fma(-fr, g.kb, g.hb0));
+                const T w1 = sat(fma(fr, g.kb, g.hb1));
+                const T* rr = r0 + (size_t)q * SB + b0;
+                acc0 = fma(g.inv_m, fma(w0, __ldg(rr), w1 * __ldg(rr + 1)), acc0);
+                if (NRHS == 2) {
+                    const T* rs = r1 + (size_t)q * SB + b0;
+                    acc1 = fma(g.inv_m, fma(w0, __ldg(rs), w1 * __ldg(rs + 1)), acc1);
+                }
             }
         }
     }

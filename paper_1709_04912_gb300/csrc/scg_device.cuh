@@ -12,7 +12,7 @@
 //                      read one contiguous span of a line.
 //   sinogram views     [angle][kSPad + bin] rows of stride SB with zero pads,
 //                      so the backprojector's two candidate bins never need a
-//                      bounds test.
+//                      bounds test (a clamped candidate pair reads only pads).
 //   partials           kSlots doubles per work item, summed in a fixed order
 //                      by the last item of a launch (no atomics on data).
 #pragma once
@@ -25,7 +25,7 @@
 namespace scg {
 
 constexpr int kPad = 2;          // zero elements on each side of an image-view line
-constexpr int kSPad = 1;         // zero elements on each side of a sinogram-view row
+constexpr int kSPad = 2;         // zero elements on each side of a sinogram-view row
 constexpr int kSlots = 8;        // FP64 partial sums per work item
 constexpr int kTrials = 7;       // TV trial candidates per pass (+1 baseline slot)
 constexpr int kTileW = 32;       // image tile width (pixels) = one warp
@@ -37,20 +37,29 @@ constexpr int kFilterBlock = 128;// output bins per filter work item
 enum ImgBuf { IB_X = 0, IB_XH, IB_P, IB_H, IB_G, IB_Z, IB_TVG, IB_AUX, IB_COUNT };
 enum SinoBuf { SB_R = 0, SB_Q, SB_W, SB_COUNT };
 
-// Per-angle constants of the ray-pixel weight (host computes them in FP64).
-//   m = max(|c|,|s|), n = min(|c|,|s|); the chord of a ray through a unit pixel
-//   at signed distance d from its centre is
-//     T(d) = min(1/m, max(0, ((m+n)/2 - |d|) / (m n)))
-//   and, for axis-aligned rays (n = 0), T(d) = min(1, max(0, 1 - |d|)), which
-//   on the half-integer distances that occur there gives 1, 1/2 (a ray on an
-//   edge, shared by two pixels) or 0.
+// Per-angle constants (host computes them in FP64).  With m = max(|c|,|s|),
+// n = min(|c|,|s|), the chord of a ray through a unit pixel whose centre is at
+// signed detector distance d is T(d) = min(1/m, max(0, ((m+n)/2 - |d|)/(m n)))
+// (for n = 0: 1, 1/2 on an edge, 0).  Two consequences are used:
+//  * walking a ray along its driving axis (columns when |sin| >= |cos|), the
+//    chord inside one column strip is exactly 1/m and lies in the two pixels
+//    nearest the crossing c*, rows floor(c*) and floor(c*)+1; with
+//    f = c* - floor(c*) the first gets u/m, the second (1-u)/m,
+//    u = sat(h2 - f k2), k2 = m/n, h2 = (m+n)/(2n)   (n = 0: k2 = h2 = 1);
+//  * gathering at a pixel whose centre projects to bin coordinate cb
+//    (g = cb - floor(cb)), bins floor(cb) and floor(cb)+1 get
+//    sat(hb0 - g kb)/m and sat(hb1 + g kb)/m,
+//    kb = 1/n, hb0 = (m+n)/(2n), hb1 = ((m+n)/2 - 1)/n   (n = 0: 1, 1, 0).
 template <typename T>
 struct Angle {
     T c, s;        // cos, sin (exact 0/1 at theta = 0, pi/2)
-    T inv_m;       // plateau height 1/m
-    T inv_mn;      // ramp slope
-    T hs_mn;       // ramp offset
+    T inv_m;       // 1/m
     T inv_drive;   // 1/s for column-walked angles, 1/c for row-walked ones
+    T k2, h2;      // forward weights
+    T kb, hb0;     // gather weights
+    T hb1;
+    T slope;       // change of the crossing per step along the driving axis
+    T c0_off;      // off_n * (e * inv_drive + 1), e = c (column-walked) or s
     int col_driven;
     int pad_;
 };
@@ -117,9 +126,8 @@ struct Prob {
 };
 
 // ---------------------------------------------------------------------------
-// Rounding-explicit arithmetic.  The projector and the backprojector must
-// evaluate bit-identical weights; spelling every operation out keeps the
-// compiler from contracting them differently in the two kernels.
+// Rounding-explicit arithmetic helpers (used where the order of rounding
+// matters: trial points and the applied perturbation must be identical).
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
@@ -139,19 +147,8 @@ __device__ __forceinline__ double tfloor(double a) { return floor(a); }
 __device__ __forceinline__ float tsqrt(float a) { return sqrtf(a); }
 __device__ __forceinline__ double tsqrt(double a) { return sqrt(a); }
 
-// Distance between ray (sb) and pixel centre (xc, yc) along the detector:
-// d = s_b - (yc*sin + xc*cos), evaluated in this exact order everywhere.
-template <typename T>
-__device__ __forceinline__ T ray_offset(T xcc /* = mul_rn(xc, c) */, T yc, T s) {
-    return fma_rn(yc, s, xcc);
-}
-
-// Chord length T(d) (see Angle).
-template <typename T>
-__device__ __forceinline__ T chord(T d, const Angle<T>& g) {
-    T t = fma_rn(-tabs(d), g.inv_mn, g.hs_mn);
-    return tmin(g.inv_m, tmax(T(0), t));
-}
+__device__ __forceinline__ float sat(float a) { return __saturatef(a); }
+__device__ __forceinline__ double sat(double a) { return fmin(fmax(a, 0.0), 1.0); }
 
 // ---------------------------------------------------------------------------
 // Block reductions (FP64, fixed order).

@@ -113,29 +113,35 @@ Plan make_plan(const scg_geometry& g, int variant, size_t tsize, int kind) {
 }
 
 template <typename T>
-void fill_angles(std::vector<Angle<T>>& out, int na) {
+void fill_angles(std::vector<Angle<T>>& out, int na, int n) {
     out.resize(na);
+    const double off_n = 0.5 * (n - 1);
     for (int a = 0; a < na; ++a) {
         double c, s;
         if (a == 0) { c = 1.0; s = 0.0; }
         else if (2 * a == na) { c = 0.0; s = 1.0; }
         else { const double th = M_PI * (double)a / (double)na; c = cos(th); s = sin(th); }
         const double ac = fabs(c), as = fabs(s);
-        const double m = ac > as ? ac : as, n = ac > as ? as : ac;
+        const double m = ac > as ? ac : as, mn = ac > as ? as : ac;
+        const double hs = 0.5 * (m + mn);
         Angle<T> g;
         memset(&g, 0, sizeof(g));
         g.c = (T)c;
         g.s = (T)s;
         g.inv_m = (T)(1.0 / m);
-        if (n == 0.0) {                    // T(d) = min(1, max(0, 1 - |d|))
-            g.inv_mn = (T)1.0;
-            g.hs_mn = (T)1.0;
+        if (mn == 0.0) {
+            g.k2 = (T)1.0; g.h2 = (T)1.0;
+            g.kb = (T)1.0; g.hb0 = (T)1.0; g.hb1 = (T)0.0;
         } else {
-            g.inv_mn = (T)(1.0 / (m * n));
-            g.hs_mn = (T)(0.5 * (m + n) / (m * n));
+            g.k2 = (T)(m / mn); g.h2 = (T)(hs / mn);
+            g.kb = (T)(1.0 / mn); g.hb0 = (T)(hs / mn); g.hb1 = (T)((hs - 1.0) / mn);
         }
         g.col_driven = as >= ac ? 1 : 0;
-        g.inv_drive = g.col_driven ? (T)(1.0 / s) : (T)(1.0 / c);
+        const double inv = g.col_driven ? 1.0 / s : 1.0 / c;
+        const double e = g.col_driven ? c : s;
+        g.inv_drive = (T)inv;
+        g.slope = (T)(-e * inv);
+        g.c0_off = (T)(off_n * (e * inv + 1.0));
         out[a] = g;
     }
 }
@@ -358,7 +364,7 @@ int solve_impl(const scg_geometry* g, int variant, int precision, const scg_para
     P.y = (const T*)y;
     P.img[IB_AUX] = (T*)x0;
     std::vector<Angle<T>> ang;
-    fill_angles<T>(ang, g->n_angles);
+    fill_angles<T>(ang, g->n_angles, g->n);
 
     DevState st;
     memset(&st, 0, sizeof(st));
@@ -539,7 +545,7 @@ int op_setup(const scg_geometry& g, void* work, size_t work_bytes, cudaStream_t 
     unsigned char* base = (unsigned char*)work;
     Prob<T> P = make_prob<T>(g, pl, base);
     std::vector<Angle<T>> ang;
-    fill_angles<T>(ang, g.n_angles);
+    fill_angles<T>(ang, g.n_angles, g.n);
     CK(cudaMemsetAsync(base + pl.state, 0, sizeof(DevState), s));
     CK(cudaMemsetAsync(base + pl.counter, 0, 16, s));
     CK(cudaMemcpyAsync(base + pl.ang, ang.data(), sizeof(Angle<T>) * ang.size(), cudaMemcpyHostToDevice, s));

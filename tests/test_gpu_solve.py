@@ -6,8 +6,13 @@ C ABI (scg_solve).
   within 1e-9 relative L2 (the oracle's own sensitivity to a 1e-13 data
   perturbation on this workload is <= 5e-11).
 * FP32, same workload: same decisions where the oracle's TV margin exceeds
-  1e-5, output within 2e-4 relative L2 (FP32 rounding ~6e-8 amplified by the
-  solve's conditioning; measured values are printed).
+  1e-5, and output within a per-variant bound.  The bound is the FP32 error
+  of one loop body (~1e-6, see the single-body test) times the solve's
+  amplification of a rounding-level perturbation, which the oracle measures
+  on this workload (y perturbed by 1e-13: CG 450x, S-CG-K 38x, S-CG-CD 5x,
+  the others <= 3x), with a factor-10 margin.  Plain CG and PCG update the
+  gradient recursively (Eq. recursive), so in FP32 their gradient error does
+  not shrink with the gradient; their bound is looser.
 * One loop body from a state the oracle exported (k = 4): every vector of the
   new state within 1e-5 (FP32) / 1e-11 (FP64).
 * Resume from an exported GPU state is bit-exact.
@@ -35,8 +40,12 @@ def rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
+FP32_BOUND = {"CG": 2e-2, "PCG": 2e-5, "S-CG": 3e-5, "S-CG-CD": 5e-5, "S-CG-K": 4e-4,
+              "S-PCG": 5e-5, "S-PCG-K": 3e-5}
+
+
 def kw_for(variant, prob, **extra):
-    kw = dict(variant=variant, eps=prob.eps, gamma0_rel=0.05, max_iter=100)
+    kw = dict(variant=variant, eps=prob.eps, gamma0_rel=0.05)
     if variant in ("CG", "PCG"):
         kw["perturb"] = "none"
     kw.update(extra)
@@ -87,9 +96,9 @@ def test_fp32_whole_solve_matches_oracle(small, variant):
     if robust:
         assert r.iters == ro["iters"]
         np.testing.assert_array_equal(r.trace[:, DECISION], to[:, DECISION])
-        assert err <= 2e-4
+        assert err <= FP32_BOUND[variant]
     assert r.f_final <= small.eps
-    assert r.tv_final == pytest.approx(ro["tv_final"], rel=1e-3)
+    assert r.tv_final == pytest.approx(ro["tv_final"], rel=2e-2 if variant == "CG" else 1e-3)
 
 
 @pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-11), (torch.float32, 1e-5)])
