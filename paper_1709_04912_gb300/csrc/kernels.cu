@@ -14,6 +14,7 @@
 //   k_filter       row filter of the preconditioner (Sec. 3) as a Toeplitz
 //                  product with taps h = IDFT(c)
 //   k_taps         the taps, in FP64
+//   k_sino_pairs   a caller's plain sinogram into the pair layout
 // No kernel uses atomics on data; reductions are deterministic.
 #include "scg_kernels.h"
 
@@ -36,164 +37,243 @@ __device__ __forceinline__ Item decode_item(const Prob<T>* probs, const Item* it
 // Forward projector.  One thread per ray (a, b), kRayBlock consecutive bins of
 // one angle per block, so the sinogram writes are coalesced.  The ray is walked
 // along its driving axis (columns when |sin| >= |cos|, else rows); in each
-// column (row) strip its chord is 1/m and falls on the two pixels nearest the
-// crossing, split u : (1-u) by one saturating FMA of the crossing's fractional
-// part (see Angle).  Both pixels are read from the view whose lines run across
-// the driving axis, so a warp's 32 rays read one short contiguous span.
+// strip its chord is 1/m and falls on the two pixels nearest the crossing,
+// split u : (1-u) by one saturating FMA of the crossing's fractional part (see
+// Angle).  The two pixels are one pair-layout load from the view whose lines
+// run across the driving axis.  The crossing c*(t) = c0 + t*slope is kept as
+// floor(c0) (integer, from FP64) plus an FP32 remainder, so its rounding
+// error scales with t*|slope| and not with the image size.
+// Walk of one ray: sum over driving index t in [tlo, thi] of the strip chord
+// split between the pair of pixels at the crossing.
+template <typename T>
+__device__ __forceinline__ T walk_ray(const typename Vec2<T>::type* line, int S, int tlo, int thi,
+                                      double c0d, const Angle<T>& g, unsigned top);
+
+// FP32: the crossing in 32.32 fixed point, so every increment is exact; the
+// high word is floor(c*), the fraction's top 23 bits become a float in [1, 2)
+// by an OR into the mantissa.
+template <>
+__device__ __forceinline__ float walk_ray<float>(const float2* line, int S, int tlo, int thi,
+                                                 double c0d, const Angle<float>& g, unsigned top) {
+    long long C = __double2ll_rn((c0d + (double)tlo * g.slope_d) * 4294967296.0);
+    const long long SL = g.slope_fx;
+    const float k2 = g.k2, h2 = g.h2;
+    line += (size_t)tlo * S;
+    float au = 0.f, ay = 0.f, bu = 0.f, by = 0.f;
+    int t = tlo;
+    for (; t + 1 <= thi; t += 2) {
+        const long long C1 = C + SL;
+        const unsigned s0 = min((unsigned)((int)(C >> 32) + kPad), top);
+        const unsigned s1 = min((unsigned)((int)(C1 >> 32) + kPad), top);
+        const float f0 = __int_as_float(0x3F800000 | ((unsigned)C >> 9)) - 1.0f;
+        const float f1 = __int_as_float(0x3F800000 | ((unsigned)C1 >> 9)) - 1.0f;
+        const float2 v0 = __ldg(line + s0);
+        const float2 v1 = __ldg(line + S + s1);
+        au = fmaf(__saturatef(fmaf(-f0, k2, h2)), v0.x - v0.y, au);
+        ay += v0.y;
+        bu = fmaf(__saturatef(fmaf(-f1, k2, h2)), v1.x - v1.y, bu);
+        by += v1.y;
+        C = C1 + SL;
+        line += 2 * S;
+    }
+    if (t <= thi) {
+        const unsigned s0 = min((unsigned)((int)(C >> 32) + kPad), top);
+        const float f0 = __int_as_float(0x3F800000 | ((unsigned)C >> 9)) - 1.0f;
+        const float2 v0 = __ldg(line + s0);
+        au = fmaf(__saturatef(fmaf(-f0, k2, h2)), v0.x - v0.y, au);
+        ay += v0.y;
+    }
+    return (au + bu) + (ay + by);
+}
+
+// FP64: the crossing as an integer base plus an FP64 remainder.
+template <>
+__device__ __forceinline__ double walk_ray<double>(const double2* line, int S, int tlo, int thi,
+                                                   double c0d, const Angle<double>& g, unsigned top) {
+    const double c0i = floor(c0d);
+    const double c0f = c0d - c0i;
+    const int cbase = (int)c0i + kPad;
+    double acc = 0.0;
+    line += (size_t)tlo * S;
+    for (int t = tlo; t <= thi; ++t, line += S) {
+        const double cs = fma((double)t, g.slope_d, c0f);
+        const double fl = floor(cs);
+        const unsigned sl = min((unsigned)((int)fl + cbase), top);
+        const double2 v = __ldg(line + sl);
+        acc += fma(sat(fma(fl - cs, g.k2, g.h2)), v.x - v.y, v.y);
+    }
+    return acc;
+}
+
+// Forward projector.  One thread per ray (a, b), kRayBlock consecutive bins of
+// one angle per block, so the sinogram writes are coalesced.  The ray is walked
+// along its driving axis (columns when |sin| >= |cos|, else rows); in each
+// strip its chord is 1/m and falls on the two pixels nearest the crossing,
+// split u : (1-u) by one saturating FMA of the crossing's fractional part (see
+// Angle).  The two pixels are one pair-layout load from the view whose lines
+// run across the driving axis.
 template <typename T>
 __global__ void __launch_bounds__(kRayBlock)
 k_project(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int dst_sel,
           int mode, int step) {
+    using T2 = typename Vec2<T>::type;
     const Item it = decode_item(probs, items, 0);
     const Prob<T>& P = probs[it.prob];
     if (P.st->done) return;
-    const int N = P.n, nb = P.nb, S = P.S;
+    const int N = P.n, nb = P.nb;
     const int a = it.u;
     const int b = it.v * kRayBlock + threadIdx.x;
     const Angle<T> g = P.ang[a];
     T acc = T(0);
     if (b < nb) {
-        const T sb = T(b) - P.off_b;
         // crossing on the non-driving axis at driving index t: c*(t) = c0 + t * slope
-        const T slope = g.slope;
-        const T c0 = fma(sb, g.inv_drive, g.c0_off);
-        const T* V = g.col_driven ? P.view_cm : P.view_rm;
+        const double c0d = fma((double)b - 0.5 * (double)(nb - 1), g.inv_d, g.c0_off_d);
+        // driving range: crossings within [-1.5, N + 0.5] (pixels touched lie in [0, N))
         int tlo = 0, thi = N - 1;
-        const T lo_c = T(-1.5), hi_c = T(N) + T(0.5);
-        if (tabs(slope) < T(1e-6)) {
-            if (!(c0 >= lo_c && c0 <= hi_c)) thi = -1;
+        const double lo_c = -1.5, hi_c = (double)N + 0.5;
+        if (fabs(g.slope_d) < 1e-6) {
+            if (!(c0d >= lo_c && c0d <= hi_c)) thi = -1;
         } else {
-            const T t1 = (lo_c - c0) / slope, t2 = (hi_c - c0) / slope;
-            const T lo = tmax(tmin(t1, t2), T(-1)), hi = tmin(tmax(t1, t2), T(N));
-            tlo = max(0, (int)tfloor(lo));
-            thi = min(N - 1, (int)tfloor(hi) + 1);
+            const double t1 = (lo_c - c0d) / g.slope_d, t2 = (hi_c - c0d) / g.slope_d;
+            const double lo = fmax(fmin(t1, t2), -1.0), hi = fmin(fmax(t1, t2), (double)N);
+            tlo = max(0, (int)floor(lo));
+            thi = min(N - 1, (int)floor(hi) + 1);
         }
-        const T k2 = g.k2, h2 = g.h2;
-        const T* line = V + (size_t)tlo * S + kPad;
-        T tf = T(tlo);
-        T acc0 = T(0), acc1 = T(0);
-        int t = tlo;
-        for (; t + 1 <= thi; t += 2) {
-            const T cs0 = fma(tf, slope, c0);
-            const T cs1 = fma(tf + T(1), slope, c0);
-            const T fl0 = tfloor(cs0), fl1 = tfloor(cs1);
-            const int i0 = min(max((int)fl0, -kPad), N + kPad - 2);
-            const int i1 = min(max((int)fl1, -kPad), N + kPad - 2);
-            const T a0 = __ldg(line + i0), b0 = __ldg(line + i0 + 1);
-            const T a1 = __ldg(line + S + i1), b1 = __ldg(line + S + i1 + 1);
-            const T u0 = sat(fma(fl0 - cs0, k2, h2));
-            const T u1 = sat(fma(fl1 - cs1, k2, h2));
-            acc0 += fma(u0, a0 - b0, b0);
-            acc1 += fma(u1, a1 - b1, b1);
-            line += 2 * S;
-            tf += T(2);
-        }
-        if (t <= thi) {
-            const T cs0 = fma(tf, slope, c0);
-            const T fl0 = tfloor(cs0);
-            const int i0 = min(max((int)fl0, -kPad), N + kPad - 2);
-            const T a0 = __ldg(line + i0), b0 = __ldg(line + i0 + 1);
-            acc0 += fma(sat(fma(fl0 - cs0, k2, h2)), a0 - b0, b0);
-        }
-        acc = (acc0 + acc1) * g.inv_m;
+        const T2* V = g.col_driven ? P.view_cm : P.view_rm;
+        acc = walk_ray<T>(V, P.S, tlo, thi, c0d, g, (unsigned)(N + 2 * kPad - 2)) * g.inv_m;
     }
     double v[1] = {0.0};
     if (b < nb) {
         T out = acc;
         if (mode == PROJ_RESIDUAL) out = acc - P.y[(size_t)a * nb + b];
-        if (mode == PROJ_PLAIN_OUT) P.sino[dst_sel][(size_t)a * nb + b] = out;
-        else P.sino[dst_sel][(size_t)a * P.SB + kSPad + b] = out;
+        if (mode == PROJ_PLAIN_OUT) P.user_out[(size_t)a * nb + b] = out;
+        else store_pair<T>(P.sino[dst_sel] + (size_t)a * P.SB + kSPad, b, out);
         v[0] = (double)out * (double)out;
     }
     if (step != FIN_NONE) reduce_and_finalize<T, 1>(v, P, it.local, P.cnt_ray, step);
 }
 
 // ---------------------------------------------------------------------------
-// Backprojector: one thread per pixel, all angles.  A pixel whose centre
-// projects to bin coordinate cb can only meet bins floor(cb) and floor(cb)+1
-// ((m+n)/2 <= 1/sqrt(2)); their weights are two saturating FMAs of the
-// fractional part (see Angle).  The angle table is staged in shared memory.
+// Backprojector: two pixels per thread (rows ty and ty + kTileH/2 of a
+// kTileW x kTileH tile), all angles.  A pixel whose centre projects to bin
+// coordinate cb can only meet bins floor(cb) and floor(cb)+1 ((m+n)/2 <=
+// 1/sqrt(2)); their weights are two saturating FMAs of cb's fractional part
+// (see Angle), and the two bins are one pair-layout load.  The projection of
+// the tile's first pixel is computed once per angle in FP64 and split into
+// integer + fraction; each pixel adds only its small in-tile offset in FP32.
 template <typename T, int NRHS>
-__global__ void __launch_bounds__(kTileThreads)
+__global__ void __launch_bounds__(kBackThreads)
 k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int src0,
               int src1, int dst0, int dst1, int step) {
+    using T2 = typename Vec2<T>::type;
     const Item it = decode_item(probs, items, 1);
     const Prob<T>& P = probs[it.prob];
     if (P.st->done) return;
     constexpr int kChunk = 128;
-    __shared__ Angle<T> tab[kChunk];
+    constexpr int kHalf = kTileH / 2;
+    struct Row { T c, s, kb, hb0, hb1, inv_m, frac; int base; };
+    __shared__ Row tab[kChunk];
     const int N = P.n, na = P.na, nb = P.nb, SB = P.SB;
-    const int i = it.u * kTileH + threadIdx.x / kTileW;
-    const int j = it.v * kTileW + threadIdx.x % kTileW;
-    const bool in = (i < N) && (j < N);
-    const T xc = T(j) - P.off_n, yc = T(i) - P.off_n, off_b = P.off_b;
-    const T* R0 = P.sino[src0] + kSPad;
-    const T* R1 = NRHS == 2 ? P.sino[src1] + kSPad : nullptr;
-    T acc0 = T(0), acc1 = T(0);
+    const int ti0 = it.u * kTileH, tj0 = it.v * kTileW;
+    const int tx = threadIdx.x % kTileW, ty = threadIdx.x / kTileW;
+    const int i1 = ti0 + ty, i2 = ti0 + ty + kHalf, j = tj0 + tx;
+    const bool in1 = (i1 < N) && (j < N), in2 = (i2 < N) && (j < N);
+    const T dj = T(tx), di1 = T(ty), di2 = T(ty + kHalf);
+    const double xc0 = (double)tj0 - (double)P.off_n, yc0 = (double)ti0 - (double)P.off_n;
+    const unsigned top = (unsigned)(nb + 2 * kSPad - 2);
+    const T2* R0 = P.sino[src0];
+    const T2* R1 = NRHS == 2 ? P.sino[src1] : nullptr;
+    T a1 = T(0), a2 = T(0), b1 = T(0), b2 = T(0);
     for (int a0 = 0; a0 < na; a0 += kChunk) {
         const int cnt = min(kChunk, na - a0);
         __syncthreads();
-        for (int q = threadIdx.x; q < cnt; q += blockDim.x) tab[q] = P.ang[a0 + q];
+        for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+            const Angle<T> g = P.ang[a0 + q];
+            const double cbt = (double)P.off_b + xc0 * g.c_d + yc0 * g.s_d;
+            const double fl = floor(cbt);
+            Row r;
+            r.c = g.c; r.s = g.s; r.kb = g.kb; r.hb0 = g.hb0; r.hb1 = g.hb1; r.inv_m = g.inv_m;
+            r.frac = (T)(cbt - fl);
+            r.base = (int)fl + kSPad;
+            tab[q] = r;
+        }
         __syncthreads();
-        if (in) {
-            const T* r0 = R0 + (size_t)a0 * SB;
-            const T* r1 = NRHS == 2 ? R1 + (size_t)a0 * SB : nullptr;
-#pragma unroll 4
+        if (in1) {
+            const T2* r0 = R0 + (size_t)a0 * SB;
+            const T2* r1 = NRHS == 2 ? R1 + (size_t)a0 * SB : nullptr;
+#pragma unroll 2
             for (int q = 0; q < cnt; ++q) {
-                const Angle<T>& g = tab[q];
-                const T cb = fma(yc, g.s, fma(xc, g.c, off_b));
-                const T fl = tfloor(cb);
-                const T fr = cb - fl;
-                const int b0 = min(max((int)fl, -kSPad), nb + kSPad - 2);
-                const T w0 = sat(fma(-fr, g.kb, g.hb0));
-                const T w1 = sat(fma(fr, g.kb, g.hb1));
-                const T* rr = r0 + (size_t)q * SB + b0;
-                acc0 = fma(g.inv_m, fma(w0, __ldg(rr), w1 * __ldg(rr + 1)), acc0);
+                const Row& g = tab[q];
+                const T djc = dj * g.c;
+                const T v1 = g.frac + fma(di1, g.s, djc);
+                const T v2 = g.frac + fma(di2, g.s, djc);
+                int q1, q2;
+                const T f1 = v1 - floor_split(v1, q1);
+                const T f2 = v2 - floor_split(v2, q2);
+                const unsigned s1 = min((unsigned)(q1 + g.base), top);
+                const unsigned s2 = min((unsigned)(q2 + g.base), top);
+                const T w10 = sat(fma(-f1, g.kb, g.hb0)), w11 = sat(fma(f1, g.kb, g.hb1));
+                const T w20 = sat(fma(-f2, g.kb, g.hb0)), w21 = sat(fma(f2, g.kb, g.hb1));
+                const T2 e1 = __ldg(r0 + (size_t)q * SB + s1);
+                const T2 e2 = __ldg(r0 + (size_t)q * SB + s2);
+                a1 = fma(g.inv_m, fma(w10, e1.x, w11 * e1.y), a1);
+                a2 = fma(g.inv_m, fma(w20, e2.x, w21 * e2.y), a2);
                 if (NRHS == 2) {
-                    const T* rs = r1 + (size_t)q * SB + b0;
-                    acc1 = fma(g.inv_m, fma(w0, __ldg(rs), w1 * __ldg(rs + 1)), acc1);
+                    const T2 z1 = __ldg(r1 + (size_t)q * SB + s1);
+                    const T2 z2 = __ldg(r1 + (size_t)q * SB + s2);
+                    b1 = fma(g.inv_m, fma(w10, z1.x, w11 * z1.y), b1);
+                    b2 = fma(g.inv_m, fma(w20, z2.x, w21 * z2.y), b2);
                 }
             }
         }
     }
-    const size_t idx = (size_t)i * N + j;
-    if (in) {
-        P.img[dst0][idx] = acc0;
-        if (NRHS == 2) P.img[dst1][idx] = acc1;
+    const size_t idx1 = (size_t)i1 * N + j, idx2 = (size_t)i2 * N + j;
+    if (in1) {
+        P.img[dst0][idx1] = a1;
+        if (NRHS == 2) P.img[dst1][idx1] = b1;
+    }
+    if (in2) {
+        P.img[dst0][idx2] = a2;
+        if (NRHS == 2) P.img[dst1][idx2] = b2;
     }
     if (step == FIN_NONE) return;
     double v[3] = {0.0, 0.0, 0.0};
-    if (in) {
-        const double g0 = (double)acc0, g1 = (double)acc1;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const bool in = h ? in2 : in1;
+        if (!in) continue;
+        const size_t idx = h ? idx2 : idx1;
+        const double g0 = (double)(h ? a2 : a1), g1 = (double)(h ? b2 : b1);
         if (step == FIN_BETA) {
-            const double h = (double)P.img[IB_H][idx];
-            v[0] = (NRHS == 2 ? g1 : g0) * h;       // g'^T h  (z'^T h)
-            v[1] = g0 * g0;                          // ||g'||^2
-            v[2] = g0 * (double)P.img[IB_P][idx];    // g'^T p
+            const double hh = (double)P.img[IB_H][idx];
+            v[0] += (NRHS == 2 ? g1 : g0) * hh;      // g'^T h  (z'^T h)
+            v[1] += g0 * g0;                         // ||g'||^2
+            v[2] += g0 * (double)P.img[IB_P][idx];   // g'^T p
         } else if (step == FIN_ALPHA || step == FIN_CG_ALPHA) {
-            v[0] = (double)P.img[IB_P][idx] * g0;    // p^T h
+            v[0] += (double)P.img[IB_P][idx] * g0;   // p^T h
         } else if (step == FIN_CG_DELTA) {
-            v[0] = g0 * g0;                          // ||g||^2
-            v[1] = g0 * g1;                          // g^T z
+            v[0] += g0 * g0;                         // ||g||^2
+            v[1] += g0 * g1;                         // g^T z
         }
     }
     reduce_and_finalize<T, 3>(v, P, it.local, P.cnt_img, step);
 }
 
 // ---------------------------------------------------------------------------
-// Write one tile of an image into both projector views.  `val` is this
-// thread's pixel value (ignored outside the image).
+// Write one tile of an image into both projector views (pair layout: each
+// element is written into its own slot and the previous slot's second half).
+// `val` is this thread's pixel value (ignored outside the image).
 template <typename T>
 __device__ __forceinline__ void write_views(const Prob<T>& P, int ti, int tj, T val, bool in) {
     __shared__ T tile[kTileH][kTileW + 1];
     const int ty = threadIdx.x / kTileW, tx = threadIdx.x % kTileW;
     const int i = ti * kTileH + ty, j = tj * kTileW + tx;
-    if (in) P.view_rm[(size_t)i * P.S + kPad + j] = val;
+    if (in) store_pair<T>(P.view_rm + (size_t)i * P.S + kPad, j, val);
     tile[ty][tx] = val;
     __syncthreads();
     const int jj = threadIdx.x / kTileH, ii = threadIdx.x % kTileH;
     const int i2 = ti * kTileH + ii, j2 = tj * kTileW + jj;
-    if (i2 < P.n && j2 < P.n) P.view_cm[(size_t)j2 * P.S + kPad + i2] = tile[ii][jj];
+    if (i2 < P.n && j2 < P.n) store_pair<T>(P.view_cm + (size_t)j2 * P.S + kPad, i2, tile[ii][jj]);
 }
 
 // Elementwise operations on one image tile (see VecOp).
@@ -414,12 +494,24 @@ k_sino_axpy(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, i
     const int a = it.u, b = it.v * kRayBlock + threadIdx.x;
     double v[1] = {0.0};
     if (b < P.nb) {
-        const size_t o = (size_t)a * P.SB + kSPad + b;
-        const T r = fma((T)st.alpha, P.sino[SB_Q][o], P.sino[SB_R][o]);
-        P.sino[SB_R][o] = r;
+        const size_t o = (size_t)a * P.SB + kSPad;
+        // reads the first half of slot b, writes it and the second half of
+        // slot b-1: no other thread touches those words
+        const T r = fma((T)st.alpha, P.sino[SB_Q][o + b].x, P.sino[SB_R][o + b].x);
+        store_pair<T>(P.sino[SB_R] + o, b, r);
         v[0] = (double)r * (double)r;
     }
     reduce_and_finalize<T, 1>(v, P, it.local, P.cnt_ray, step);
+}
+
+// Caller's plain sinogram [na][nb] into the pair view sino[dst].
+template <typename T>
+__global__ void __launch_bounds__(kRayBlock)
+k_sino_pairs(const Prob<T>* __restrict__ probs, int dst) {
+    const Prob<T>& P = probs[0];
+    const int a = blockIdx.x / P.ray_blocks, b = (blockIdx.x % P.ray_blocks) * kRayBlock + threadIdx.x;
+    if (b < P.nb)
+        store_pair<T>(P.sino[dst] + (size_t)a * P.SB + kSPad, b, P.user_in[(size_t)a * P.nb + b]);
 }
 
 // ---------------------------------------------------------------------------
@@ -438,8 +530,13 @@ k_filter(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int 
     T* row = reinterpret_cast<T*>(smem_raw);
     T* taps = row + P.nb;
     const int nb = P.nb, a = it.u;
-    const T* R = plain ? P.sino[src] + (size_t)a * nb : P.sino[src] + (size_t)a * P.SB + kSPad;
-    for (int q = threadIdx.x; q < nb; q += blockDim.x) row[q] = R[q];
+    if (plain) {
+        const T* R = P.user_in + (size_t)a * nb;
+        for (int q = threadIdx.x; q < nb; q += blockDim.x) row[q] = R[q];
+    } else {
+        const typename Vec2<T>::type* R = P.sino[src] + (size_t)a * P.SB + kSPad;
+        for (int q = threadIdx.x; q < nb; q += blockDim.x) row[q] = R[q].x;
+    }
     for (int q = threadIdx.x; q < 2 * nb - 1; q += blockDim.x) taps[q] = P.taps[q];
     __syncthreads();
     const int b = it.v * kFilterBlock + threadIdx.x;
@@ -454,8 +551,8 @@ k_filter(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int 
     }
     if (q < nb) acc0 = fma(tb[-q], row[q], acc0);
     const T out = acc0 + acc1;
-    if (plain) P.sino[dst][(size_t)a * nb + b] = out;
-    else P.sino[dst][(size_t)a * P.SB + kSPad + b] = out;
+    if (plain) P.user_out[(size_t)a * nb + b] = out;
+    else store_pair<T>(P.sino[dst] + (size_t)a * P.SB + kSPad, b, out);
 }
 
 // Taps h[k] = gain/P * sum_m c(w_m) cos(2 pi m k / P), k = 0..nb-1, stored
@@ -490,8 +587,12 @@ void launch_project(const Prob<T>* d, const Item* items, int grid, int dst, int 
 template <typename T>
 void launch_backproject(const Prob<T>* d, const Item* items, int grid, int nrhs, int src0,
                         int src1, int dst0, int dst1, int step, cudaStream_t s) {
-    if (nrhs == 2) k_backproject<T, 2><<<grid, kTileThreads, 0, s>>>(d, items, src0, src1, dst0, dst1, step);
-    else k_backproject<T, 1><<<grid, kTileThreads, 0, s>>>(d, items, src0, src1, dst0, dst1, step);
+    if (nrhs == 2) k_backproject<T, 2><<<grid, kBackThreads, 0, s>>>(d, items, src0, src1, dst0, dst1, step);
+    else k_backproject<T, 1><<<grid, kBackThreads, 0, s>>>(d, items, src0, src1, dst0, dst1, step);
+}
+template <typename T>
+void launch_sino_pairs(const Prob<T>* d, int grid, int dst, cudaStream_t s) {
+    k_sino_pairs<T><<<grid, kRayBlock, 0, s>>>(d, dst);
 }
 template <typename T>
 void launch_vec(const Prob<T>* d, const Item* items, int grid, int op, int sel, int step,
@@ -539,7 +640,8 @@ void launch_taps(T* taps, int nb, int P, double mu, double gain, cudaStream_t s)
     template void launch_sino_axpy<T>(const Prob<T>*, const Item*, int, int, cudaStream_t);       \
     template cudaError_t launch_filter<T>(const Prob<T>*, const Item*, int, int, int, int, int,   \
                                           cudaStream_t);                                          \
-    template void launch_taps<T>(T*, int, int, double, double, cudaStream_t);
+    template void launch_taps<T>(T*, int, int, double, double, cudaStream_t);                    \
+    template void launch_sino_pairs<T>(const Prob<T>*, int, int, cudaStream_t);
 
 SCG_INSTANTIATE(float)
 SCG_INSTANTIATE(double)

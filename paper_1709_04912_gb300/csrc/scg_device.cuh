@@ -4,15 +4,18 @@
 //
 // Layout in HBM (one "problem" = one reconstruction):
 //   image vectors      N*N, row-major, element type T (float or double)
-//   projector views    two zero-padded copies of the image being projected:
-//                      row-major lines (view_rm[i*S + kPad + j]) for angles
-//                      whose rays are walked row by row, and column-major lines
+//   projector views    two zero-padded copies of the image being projected, in
+//                      "pair" layout (slot q of a line holds elements q and
+//                      q+1, so the two pixels a ray meets in one strip are one
+//                      aligned 8-byte load): row-major lines
+//                      (view_rm[i*S + kPad + j]) for angles whose rays are
+//                      walked row by row, column-major lines
 //                      (view_cm[j*S + kPad + i]) for angles walked column by
-//                      column, so that the lanes of a warp (consecutive rays)
-//                      read one contiguous span of a line.
-//   sinogram views     [angle][kSPad + bin] rows of stride SB with zero pads,
-//                      so the backprojector's two candidate bins never need a
-//                      bounds test (a clamped candidate pair reads only pads).
+//                      column, so the lanes of a warp (consecutive rays) read
+//                      one short contiguous span of a line.
+//   sinogram views     [angle][kSPad + bin] rows of SB pairs with zero pads, so
+//                      the backprojector's two candidate bins are one load and
+//                      never need a bounds test (a clamped pair reads pads).
 //   partials           kSlots doubles per work item, summed in a fixed order
 //                      by the last item of a launch (no atomics on data).
 #pragma once
@@ -31,6 +34,7 @@ constexpr int kTrials = 7;       // TV trial candidates per pass (+1 baseline sl
 constexpr int kTileW = 32;       // image tile width (pixels) = one warp
 constexpr int kTileH = 8;        // image tile height
 constexpr int kTileThreads = kTileW * kTileH;
+constexpr int kBackThreads = kTileThreads / 2;   // backprojector: two pixels per thread
 constexpr int kRayBlock = 128;   // rays per projector work item
 constexpr int kFilterBlock = 128;// output bins per filter work item
 
@@ -46,6 +50,7 @@ enum SinoBuf { SB_R = 0, SB_Q, SB_W, SB_COUNT };
 //    nearest the crossing c*, rows floor(c*) and floor(c*)+1; with
 //    f = c* - floor(c*) the first gets u/m, the second (1-u)/m,
 //    u = sat(h2 - f k2), k2 = m/n, h2 = (m+n)/(2n)   (n = 0: k2 = h2 = 1);
+//    the FP32 walk carries c* in 32.32 fixed point (exact increments);
 //  * gathering at a pixel whose centre projects to bin coordinate cb
 //    (g = cb - floor(cb)), bins floor(cb) and floor(cb)+1 get
 //    sat(hb0 - g kb)/m and sat(hb1 + g kb)/m,
@@ -54,14 +59,16 @@ template <typename T>
 struct Angle {
     T c, s;        // cos, sin (exact 0/1 at theta = 0, pi/2)
     T inv_m;       // 1/m
-    T inv_drive;   // 1/s for column-walked angles, 1/c for row-walked ones
     T k2, h2;      // forward weights
     T kb, hb0;     // gather weights
     T hb1;
     T slope;       // change of the crossing per step along the driving axis
-    T c0_off;      // off_n * (e * inv_drive + 1), e = c (column-walked) or s
     int col_driven;
-    int pad_;
+    double c_d, s_d;          // cos, sin in FP64 (tile origins of the gather)
+    double inv_d;             // 1/s (column-walked) or 1/c, FP64
+    double c0_off_d;          // off_n * (e * inv + 1), e = c (column-walked) or s
+    double slope_d;
+    long long slope_fx;       // slope in 32.32 fixed point (FP32 forward walk)
 };
 
 // Work item of a launch over many problems (batched mode).  Single-problem
@@ -99,8 +106,13 @@ struct DevState {
 
 enum Family { FAM_CG = 0, FAM_S_PR = 1, FAM_S_K = 2 };
 
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+
 template <typename T>
 struct Prob {
+    using T2 = typename Vec2<T>::type;
     int n, na, nb;
     int S;                  // image-view line stride (elements)
     int SB;                 // sinogram-view row stride (elements)
@@ -113,9 +125,11 @@ struct Prob {
     const Angle<T>* ang;
     const T* y;             // data [na][nb]
     T* img[IB_COUNT];
-    T* sino[SB_COUNT];
-    T* view_rm;
-    T* view_cm;
+    T2* sino[SB_COUNT];     // pair views of the sinogram-sized vectors
+    T2* view_rm;
+    T2* view_cm;
+    const T* user_in;       // caller's plain sinogram (operator entry points)
+    T* user_out;
     const T* taps;          // Toeplitz filter taps h[-(nb-1) .. nb-1]
     double* partials;
     unsigned* counter;
@@ -149,6 +163,29 @@ __device__ __forceinline__ double tsqrt(double a) { return sqrt(a); }
 
 __device__ __forceinline__ float sat(float a) { return __saturatef(a); }
 __device__ __forceinline__ double sat(double a) { return fmin(fmax(a, 0.0), 1.0); }
+
+// floor(v) as value and integer without the conversion pipe: adding 1.5*2^23
+// with round-toward-minus-infinity leaves floor(v) in the low mantissa bits
+// (valid for |v| < 2^22; every caller stays below 2^14).
+__device__ __forceinline__ float floor_split(float v, int& i) {
+    const float t = __fadd_rd(v, 12582912.0f);
+    i = __float_as_int(t) - 0x4B400000;
+    return t - 12582912.0f;
+}
+__device__ __forceinline__ double floor_split(double v, int& i) {
+    const double f = floor(v);
+    i = (int)f;
+    return f;
+}
+
+// Store element b of a pair-layout row (row points at the slot of element 0):
+// slot b holds (e[b], e[b+1]), so e[b] is written twice.
+template <typename T>
+__device__ __forceinline__ void store_pair(typename Vec2<T>::type* row, int b, T v) {
+    T* e = reinterpret_cast<T*>(row);
+    e[2 * b] = v;
+    e[2 * b - 1] = v;
+}
 
 // ---------------------------------------------------------------------------
 // Block reductions (FP64, fixed order).

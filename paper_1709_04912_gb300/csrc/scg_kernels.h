@@ -39,5 +39,7 @@ cudaError_t launch_filter(const Prob<T>* d, const Item* items, int grid, int max
                           int dst, int plain, cudaStream_t s);
 template <typename T>
 void launch_taps(T* taps, int nb, int P, double mu, double gain, cudaStream_t s);
+template <typename T>
+void launch_sino_pairs(const Prob<T>* d, int grid, int dst, cudaStream_t s);
 
 }  // namespace scg

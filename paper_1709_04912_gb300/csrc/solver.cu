@@ -64,8 +64,8 @@ Plan make_plan(const scg_geometry& g, int variant, size_t tsize, int kind) {
     Plan p;
     memset(&p, 0, sizeof(p));
     const int N = g.n, na = g.n_angles, nb = g.n_bins;
-    p.S = round_up4(N + 2 * kPad);
-    p.SB = round_up4(nb + 2 * kSPad);
+    p.S = round_up4(N + 2 * kPad);          // pairs per view line
+    p.SB = round_up4(nb + 2 * kSPad);       // pairs per sinogram-view row
     p.ray_blocks = (nb + kRayBlock - 1) / kRayBlock;
     p.tiles_x = (N + kTileW - 1) / kTileW;
     p.cnt_ray = na * p.ray_blocks;
@@ -84,9 +84,9 @@ Plan make_plan(const scg_geometry& g, int variant, size_t tsize, int kind) {
     if (p.cnt_row > maxcnt) maxcnt = p.cnt_row;
     p.partials = take(sizeof(double) * kSlots * (size_t)maxcnt);
     p.counter = take(sizeof(unsigned) * 4);
-    p.view_rm = take(tsize * (size_t)N * p.S);
-    p.view_cm = take(tsize * (size_t)N * p.S);
-    const size_t sino_bytes = tsize * (size_t)na * p.SB;
+    p.view_rm = take(2 * tsize * (size_t)N * p.S);
+    p.view_cm = take(2 * tsize * (size_t)N * p.S);
+    const size_t sino_bytes = 2 * tsize * (size_t)na * p.SB;
     for (int q = 0; q < IB_COUNT; ++q) p.img[q] = (size_t)-1;
     for (int q = 0; q < SB_COUNT; ++q) p.sino[q] = (size_t)-1;
     if (kind == PLAN_OP) {
@@ -139,9 +139,13 @@ void fill_angles(std::vector<Angle<T>>& out, int na, int n) {
         g.col_driven = as >= ac ? 1 : 0;
         const double inv = g.col_driven ? 1.0 / s : 1.0 / c;
         const double e = g.col_driven ? c : s;
-        g.inv_drive = (T)inv;
         g.slope = (T)(-e * inv);
-        g.c0_off = (T)(off_n * (e * inv + 1.0));
+        g.c_d = c;
+        g.s_d = s;
+        g.inv_d = inv;
+        g.c0_off_d = off_n * (e * inv + 1.0);
+        g.slope_d = -e * inv;
+        g.slope_fx = llrint(g.slope_d * 4294967296.0);
         out[a] = g;
     }
 }
@@ -168,10 +172,11 @@ Prob<T> make_prob(const scg_geometry& g, const Plan& pl, unsigned char* base) {
     P.taps = reinterpret_cast<const T*>(base + pl.taps);
     for (int q = 0; q < IB_COUNT; ++q)
         P.img[q] = pl.img[q] == (size_t)-1 ? nullptr : reinterpret_cast<T*>(base + pl.img[q]);
+    using T2 = typename Vec2<T>::type;
     for (int q = 0; q < SB_COUNT; ++q)
-        P.sino[q] = pl.sino[q] == (size_t)-1 ? nullptr : reinterpret_cast<T*>(base + pl.sino[q]);
-    P.view_rm = reinterpret_cast<T*>(base + pl.view_rm);
-    P.view_cm = reinterpret_cast<T*>(base + pl.view_cm);
+        P.sino[q] = pl.sino[q] == (size_t)-1 ? nullptr : reinterpret_cast<T2*>(base + pl.sino[q]);
+    P.view_rm = reinterpret_cast<T2*>(base + pl.view_rm);
+    P.view_cm = reinterpret_cast<T2*>(base + pl.view_cm);
     P.partials = reinterpret_cast<double*>(base + pl.partials);
     P.counter = reinterpret_cast<unsigned*>(base + pl.counter);
     P.st = reinterpret_cast<DevState*>(base + pl.state);
@@ -567,10 +572,10 @@ int project_impl(const scg_geometry& g, const void* x, void* y, void* work, size
     int rc = op_setup<T>(g, work, wb, s, &pl, &P);
     if (rc) return rc;
     unsigned char* base = (unsigned char*)work;
-    CK(cudaMemsetAsync(base + pl.view_rm, 0, sizeof(T) * (size_t)g.n * pl.S, s));
-    CK(cudaMemsetAsync(base + pl.view_cm, 0, sizeof(T) * (size_t)g.n * pl.S, s));
+    CK(cudaMemsetAsync(base + pl.view_rm, 0, 2 * sizeof(T) * (size_t)g.n * pl.S, s));
+    CK(cudaMemsetAsync(base + pl.view_cm, 0, 2 * sizeof(T) * (size_t)g.n * pl.S, s));
     P.img[IB_AUX] = (T*)x;
-    P.sino[SB_Q] = (T*)y;
+    P.user_out = (T*)y;
     rc = upload_prob<T>(P, pl, work, s);
     if (rc) return rc;
     const Prob<T>* d = reinterpret_cast<const Prob<T>*>(base + pl.prob);
@@ -587,14 +592,13 @@ int backproject_impl(const scg_geometry& g, const void* r, void* x, void* work, 
     int rc = op_setup<T>(g, work, wb, s, &pl, &P);
     if (rc) return rc;
     unsigned char* base = (unsigned char*)work;
-    T* R = reinterpret_cast<T*>(base + pl.sino[SB_R]);
-    CK(cudaMemsetAsync(R, 0, sizeof(T) * (size_t)g.n_angles * pl.SB, s));
-    CK(cudaMemcpy2DAsync(R + kSPad, sizeof(T) * pl.SB, r, sizeof(T) * g.n_bins, sizeof(T) * g.n_bins,
-                         g.n_angles, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(base + pl.sino[SB_R], 0, 2 * sizeof(T) * (size_t)g.n_angles * pl.SB, s));
     P.img[IB_AUX] = (T*)x;
+    P.user_in = (const T*)r;
     rc = upload_prob<T>(P, pl, work, s);
     if (rc) return rc;
     const Prob<T>* d = reinterpret_cast<const Prob<T>*>(base + pl.prob);
+    launch_sino_pairs<T>(d, pl.cnt_ray, SB_R, s);
     launch_backproject<T>(d, nullptr, pl.cnt_img, 1, SB_R, SB_R, IB_AUX, IB_AUX, FIN_NONE, s);
     CK(cudaGetLastError());
     return SCG_OK;
@@ -629,8 +633,8 @@ int filter_impl(const scg_geometry& g, double mu, double gain, const void* r, vo
     if (rc) return rc;
     if ((size_t)(3 * g.n_bins) * sizeof(T) > 227 * 1024) return SCG_ERR_UNSUPPORTED;
     unsigned char* base = (unsigned char*)work;
-    P.sino[SB_R] = (T*)r;
-    P.sino[SB_W] = (T*)out;
+    P.user_in = (const T*)r;
+    P.user_out = (T*)out;
     rc = upload_prob<T>(P, pl, work, s);
     if (rc) return rc;
     const double mu_eff = mu > 0.0 ? mu : 2.0 * M_PI / pl.P;

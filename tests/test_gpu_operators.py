@@ -66,6 +66,16 @@ def test_backproject_matches_oracle(n, na, nb, dtype):
     assert rel(got, ref) <= TOL[dtype]
 
 
+@pytest.mark.parametrize("n,na,nb", [(256, 360, 363), (300, 257, 190)])
+def test_project_random_sign_image(n, na, nb):
+    # zero-mean input: every ray sum cancels, exposing geometric rounding
+    # (including rays that miss part of the image: 190 bins < sqrt(2) * 300)
+    x = inputs.normal(n, "zm", n * n).reshape(n, n)
+    ref = oracle.project(x, na, nb)
+    got = scg.scg_project(torch.tensor(x, dtype=torch.float32, device=DEV), na, nb).cpu().numpy()
+    assert rel(got, ref) <= 1e-5
+
+
 @pytest.mark.parametrize("n,na,nb", [(64, 90, 95), (130, 181, 185)])
 def test_pair_is_adjoint_in_fp32(n, na, nb):
     x = torch.tensor(image(n, 3), dtype=torch.float32, device=DEV)
@@ -129,7 +139,7 @@ def test_filter_matches_oracle(na, nb, mu, gain, dtype):
 @pytest.mark.parametrize("work", [inputs.SINGLE_512, inputs.MIXED_1024], ids=lambda w: w.name)
 def test_full_size_operators_on_sampled_outputs(work):
     n, na, nb = work.n, work.n_angles, work.n_bins
-    x = inputs.ellipse_phantom(n, work.n_ellipses, 0)
+    x = inputs.normal(n, "zm", n * n).reshape(n, n)     # zero mean: cancelling ray sums
     y = scg.scg_project(torch.tensor(x, dtype=torch.float32, device=DEV), na, nb).cpu().numpy()
     rng = np.random.default_rng(1)
     a = rng.integers(0, na, 300)
