@@ -43,66 +43,50 @@ __device__ __forceinline__ Item decode_item(const Prob<T>* probs, const Item* it
 // run across the driving axis.  The crossing c*(t) = c0 + t*slope is kept as
 // floor(c0) (integer, from FP64) plus an FP32 remainder, so its rounding
 // error scales with t*|slope| and not with the image size.
-// Walk of one ray: sum over driving index t in [tlo, thi] of the strip chord
-// split between the pair of pixels at the crossing.
-template <typename T>
-__device__ __forceinline__ T walk_ray(const typename Vec2<T>::type* line, int S, int tlo, int thi,
-                                      double c0d, const Angle<T>& g, unsigned top);
-
-// FP32: the crossing in 32.32 fixed point, so every increment is exact; the
-// high word is floor(c*), the fraction's top 23 bits become a float in [1, 2)
-// by an OR into the mantissa.
-template <>
-__device__ __forceinline__ float walk_ray<float>(const float2* line, int S, int tlo, int thi,
-                                                 double c0d, const Angle<float>& g, unsigned top) {
-    long long C = __double2ll_rn((c0d + (double)tlo * g.slope_d) * 4294967296.0);
-    const long long SL = g.slope_fx;
-    const float k2 = g.k2, h2 = g.h2;
+// Walk of one ray over driving indices [tlo, thi]: the strip chord split
+// between the pair of pixels at the crossing (sum of u*(e0-e1) + e1).
+// FP32: the crossing c* in 32.32 fixed point C, so every increment is exact;
+// the high word is floor(c*), the fraction's top 23 bits become a float in
+// [1, 2) by an OR into the mantissa.
+__device__ __forceinline__ float walk_ray_f32(const float2* line, int S, int tlo, int thi,
+                                              long long C, long long SL, float k2, float h2,
+                                              unsigned top) {
     line += (size_t)tlo * S;
-    float au = 0.f, ay = 0.f, bu = 0.f, by = 0.f;
+    float u0 = 0.f, u1 = 0.f, y0 = 0.f, y1 = 0.f;
     int t = tlo;
-    for (; t + 1 <= thi; t += 2) {
-        const long long C1 = C + SL;
-        const unsigned s0 = min((unsigned)((int)(C >> 32) + kPad), top);
-        const unsigned s1 = min((unsigned)((int)(C1 >> 32) + kPad), top);
-        const float f0 = __int_as_float(0x3F800000 | ((unsigned)C >> 9)) - 1.0f;
-        const float f1 = __int_as_float(0x3F800000 | ((unsigned)C1 >> 9)) - 1.0f;
-        const float2 v0 = __ldg(line + s0);
-        const float2 v1 = __ldg(line + S + s1);
-        au = fmaf(__saturatef(fmaf(-f0, k2, h2)), v0.x - v0.y, au);
-        ay += v0.y;
-        bu = fmaf(__saturatef(fmaf(-f1, k2, h2)), v1.x - v1.y, bu);
-        by += v1.y;
-        C = C1 + SL;
-        line += 2 * S;
+    for (; t + 3 <= thi; t += 4) {
+        const long long Ca = C, Cb = C + SL, Cc = C + 2 * SL, Cd = C + 3 * SL;
+        const unsigned sa = min((unsigned)((int)(Ca >> 32) + kPad), top);
+        const unsigned sb = min((unsigned)((int)(Cb >> 32) + kPad), top);
+        const unsigned sc = min((unsigned)((int)(Cc >> 32) + kPad), top);
+        const unsigned sd = min((unsigned)((int)(Cd >> 32) + kPad), top);
+        const float2 va = __ldg(line + sa);
+        const float2 vb = __ldg(line + S + sb);
+        const float2 vc = __ldg(line + 2 * S + sc);
+        const float2 vd = __ldg(line + 3 * S + sd);
+        const float fa = __int_as_float(0x3F800000 | ((unsigned)Ca >> 9)) - 1.0f;
+        const float fb = __int_as_float(0x3F800000 | ((unsigned)Cb >> 9)) - 1.0f;
+        const float fc = __int_as_float(0x3F800000 | ((unsigned)Cc >> 9)) - 1.0f;
+        const float fd = __int_as_float(0x3F800000 | ((unsigned)Cd >> 9)) - 1.0f;
+        u0 = fmaf(__saturatef(fmaf(-fa, k2, h2)), va.x - va.y, u0);
+        u1 = fmaf(__saturatef(fmaf(-fb, k2, h2)), vb.x - vb.y, u1);
+        u0 = fmaf(__saturatef(fmaf(-fc, k2, h2)), vc.x - vc.y, u0);
+        u1 = fmaf(__saturatef(fmaf(-fd, k2, h2)), vd.x - vd.y, u1);
+        y0 += va.y + vc.y;
+        y1 += vb.y + vd.y;
+        C += 4 * SL;
+        line += 4 * S;
     }
-    if (t <= thi) {
-        const unsigned s0 = min((unsigned)((int)(C >> 32) + kPad), top);
-        const float f0 = __int_as_float(0x3F800000 | ((unsigned)C >> 9)) - 1.0f;
-        const float2 v0 = __ldg(line + s0);
-        au = fmaf(__saturatef(fmaf(-f0, k2, h2)), v0.x - v0.y, au);
-        ay += v0.y;
+    for (; t <= thi; ++t) {
+        const unsigned sa = min((unsigned)((int)(C >> 32) + kPad), top);
+        const float2 va = __ldg(line + sa);
+        const float fa = __int_as_float(0x3F800000 | ((unsigned)C >> 9)) - 1.0f;
+        u0 = fmaf(__saturatef(fmaf(-fa, k2, h2)), va.x - va.y, u0);
+        y0 += va.y;
+        C += SL;
+        line += S;
     }
-    return (au + bu) + (ay + by);
-}
-
-// FP64: the crossing as an integer base plus an FP64 remainder.
-template <>
-__device__ __forceinline__ double walk_ray<double>(const double2* line, int S, int tlo, int thi,
-                                                   double c0d, const Angle<double>& g, unsigned top) {
-    const double c0i = floor(c0d);
-    const double c0f = c0d - c0i;
-    const int cbase = (int)c0i + kPad;
-    double acc = 0.0;
-    line += (size_t)tlo * S;
-    for (int t = tlo; t <= thi; ++t, line += S) {
-        const double cs = fma((double)t, g.slope_d, c0f);
-        const double fl = floor(cs);
-        const unsigned sl = min((unsigned)((int)fl + cbase), top);
-        const double2 v = __ldg(line + sl);
-        acc += fma(sat(fma(fl - cs, g.k2, g.h2)), v.x - v.y, v.y);
-    }
-    return acc;
+    return (u0 + u1) + (y0 + y1);
 }
 
 // Forward projector.  One thread per ray (a, b), kRayBlock consecutive bins of
@@ -111,41 +95,77 @@ __device__ __forceinline__ double walk_ray<double>(const double2* line, int S, i
 // strip its chord is 1/m and falls on the two pixels nearest the crossing,
 // split u : (1-u) by one saturating FMA of the crossing's fractional part (see
 // Angle).  The two pixels are one pair-layout load from the view whose lines
-// run across the driving axis.
+// run across the driving axis.  Crossing at driving index t:
+// c*(t) = c0 + t*slope, c0 = (b - (nb-1)/2) * inv_drive + c0_off.
+template <typename T>
+__device__ __forceinline__ T project_ray(const Prob<T>& P, const Angle<T>& g, int b);
+
+template <>
+__device__ __forceinline__ float project_ray<float>(const Prob<float>& P, const Angle<float>& g, int b) {
+    const int N = P.n, B2 = 2 * b - (P.nb - 1);           // 2 (b - (nb-1)/2)
+    // driving range in FP32 (conservative by one strip): crossings in [-2.5, N + 1.5]
+    const float c0f = fmaf(0.5f * (float)B2, g.inv_drive, g.c0_off);
+    int tlo = 0, thi = N - 1;
+    if (g.inv_slope == 0.f) {
+        if (!(c0f >= -2.5f && c0f <= (float)N + 1.5f)) thi = -1;
+    } else {
+        const float t1 = (-2.5f - c0f) * g.inv_slope, t2 = ((float)N + 1.5f - c0f) * g.inv_slope;
+        const float lo = fmaxf(fminf(t1, t2), -1.f), hi = fminf(fmaxf(t1, t2), (float)N);
+        tlo = max(0, (int)floorf(lo));
+        thi = min(N - 1, (int)floorf(hi) + 1);
+    }
+    // exact crossing in 32.32 fixed point
+    const long long C0 = (((long long)B2 * g.inv_fx) >> 1) + g.c0_off_fx;
+    const long long C = C0 + (long long)tlo * g.slope_fx;
+    const float2* V = g.col_driven ? P.view_cm : P.view_rm;
+    return walk_ray_f32(V, P.S, tlo, thi, C, g.slope_fx, g.k2, g.h2,
+                        (unsigned)(N + 2 * kPad - 2)) * g.inv_m;
+}
+
+template <>
+__device__ __forceinline__ double project_ray<double>(const Prob<double>& P, const Angle<double>& g, int b) {
+    const int N = P.n;
+    const double c0d = fma((double)b - 0.5 * (double)(P.nb - 1), g.inv_d, g.c0_off_d);
+    int tlo = 0, thi = N - 1;
+    if (g.slope_d == 0.0) {
+        if (!(c0d >= -1.5 && c0d <= (double)N + 0.5)) thi = -1;
+    } else {
+        const double t1 = (-1.5 - c0d) / g.slope_d, t2 = ((double)N + 0.5 - c0d) / g.slope_d;
+        const double lo = fmax(fmin(t1, t2), -1.0), hi = fmin(fmax(t1, t2), (double)N);
+        tlo = max(0, (int)floor(lo));
+        thi = min(N - 1, (int)floor(hi) + 1);
+    }
+    const double c0i = floor(c0d);
+    const double c0f = c0d - c0i;
+    const int cbase = (int)c0i + kPad;
+    const unsigned top = (unsigned)(N + 2 * kPad - 2);
+    const double2* line = (g.col_driven ? P.view_cm : P.view_rm) + (size_t)tlo * P.S;
+    double acc = 0.0;
+    for (int t = tlo; t <= thi; ++t, line += P.S) {
+        const double cs = fma((double)t, g.slope_d, c0f);
+        const double fl = floor(cs);
+        const unsigned sl = min((unsigned)((int)fl + cbase), top);
+        const double2 v = __ldg(line + sl);
+        acc += fma(sat(fma(fl - cs, g.k2, g.h2)), v.x - v.y, v.y);
+    }
+    return acc * g.inv_m;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kRayBlock)
 k_project(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int dst_sel,
           int mode, int step) {
-    using T2 = typename Vec2<T>::type;
     const Item it = decode_item(probs, items, 0);
     const Prob<T>& P = probs[it.prob];
     if (P.st->done) return;
-    const int N = P.n, nb = P.nb;
+    const int nb = P.nb;
     const int a = it.u;
     const int b = it.v * kRayBlock + threadIdx.x;
     const Angle<T> g = P.ang[a];
-    T acc = T(0);
-    if (b < nb) {
-        // crossing on the non-driving axis at driving index t: c*(t) = c0 + t * slope
-        const double c0d = fma((double)b - 0.5 * (double)(nb - 1), g.inv_d, g.c0_off_d);
-        // driving range: crossings within [-1.5, N + 0.5] (pixels touched lie in [0, N))
-        int tlo = 0, thi = N - 1;
-        const double lo_c = -1.5, hi_c = (double)N + 0.5;
-        if (fabs(g.slope_d) < 1e-6) {
-            if (!(c0d >= lo_c && c0d <= hi_c)) thi = -1;
-        } else {
-            const double t1 = (lo_c - c0d) / g.slope_d, t2 = (hi_c - c0d) / g.slope_d;
-            const double lo = fmax(fmin(t1, t2), -1.0), hi = fmin(fmax(t1, t2), (double)N);
-            tlo = max(0, (int)floor(lo));
-            thi = min(N - 1, (int)floor(hi) + 1);
-        }
-        const T2* V = g.col_driven ? P.view_cm : P.view_rm;
-        acc = walk_ray<T>(V, P.S, tlo, thi, c0d, g, (unsigned)(N + 2 * kPad - 2)) * g.inv_m;
-    }
     double v[1] = {0.0};
     if (b < nb) {
-        T out = acc;
-        if (mode == PROJ_RESIDUAL) out = acc - P.y[(size_t)a * nb + b];
+        T out = project_ray<T>(P, g, b);
+        if (mode == PROJ_RESIDUAL) out = out - P.y[(size_t)a * nb + b];
         if (mode == PROJ_PLAIN_OUT) P.user_out[(size_t)a * nb + b] = out;
         else store_pair<T>(P.sino[dst_sel] + (size_t)a * P.SB + kSPad, b, out);
         v[0] = (double)out * (double)out;
@@ -158,74 +178,152 @@ k_project(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int
 // kTileW x kTileH tile), all angles.  A pixel whose centre projects to bin
 // coordinate cb can only meet bins floor(cb) and floor(cb)+1 ((m+n)/2 <=
 // 1/sqrt(2)); their weights are two saturating FMAs of cb's fractional part
-// (see Angle), and the two bins are one pair-layout load.  The projection of
-// the tile's first pixel is computed once per angle in FP64 and split into
-// integer + fraction; each pixel adds only its small in-tile offset in FP32.
+// (see Angle), and the two bins are one pair-layout load.
+//
+// Angles are processed in chunks (16 in FP32, 8 in FP64).  For each angle the band of
+// sinogram pairs the tile can touch (<= 31|c| + 7|s| + 4 < kBand slots) is
+// copied into shared memory with cp.async, double-buffered so the next
+// chunk's copies overlap this chunk's arithmetic; parts of a band beyond the
+// detector are zero-filled by the copy itself, so the inner loop needs no
+// bounds test.  The projection of the tile's first pixel comes from 32.32
+// fixed point (FP64 in the FP64 kernel), split into integer + fraction; each
+// pixel adds only its small in-tile offset.
+constexpr int kBand = 48;
+template <typename T> struct BpChunk { static constexpr int value = 16; };
+template <> struct BpChunk<double> { static constexpr int value = 8; };   // 48 KB static limit
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+template <typename T>
+struct BpRow {
+    T c, s, kb, hb0, hb1, inv_m, frac;
+    int rel;       // band index of floor(projection of the tile origin)
+    int s_lo;      // first slot of the band in the sinogram row
+};
+
+// Tile origin projection (integer part and fraction) for one angle.
+template <typename T>
+__device__ __forceinline__ void tile_origin(const Angle<T>& g, int X2, int Y2, int nb, int& I, T& F);
+template <>
+__device__ __forceinline__ void tile_origin<float>(const Angle<float>& g, int X2, int Y2, int nb, int& I,
+                                                   float& F) {
+    // off_b + xc0 c + yc0 s with xc0 = X2/2, yc0 = Y2/2, in 32.32 fixed point
+    const long long cb = ((long long)(nb - 1) << 31) + (((long long)X2 * g.c_fx + (long long)Y2 * g.s_fx) >> 1);
+    I = (int)(cb >> 32);
+    F = __int_as_float(0x3F800000 | ((unsigned)cb >> 9)) - 1.0f;
+}
+template <>
+__device__ __forceinline__ void tile_origin<double>(const Angle<double>& g, int X2, int Y2, int nb, int& I,
+                                                    double& F) {
+    const double cb = 0.5 * (double)(nb - 1) + 0.5 * (double)X2 * g.c_d + 0.5 * (double)Y2 * g.s_d;
+    const double fl = floor(cb);
+    I = (int)fl;
+    F = cb - fl;
+}
+
 template <typename T, int NRHS>
 __global__ void __launch_bounds__(kBackThreads)
 k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int src0,
               int src1, int dst0, int dst1, int step) {
     using T2 = typename Vec2<T>::type;
+    constexpr int kSlotsPerSeg = 16 / (int)sizeof(T2);
+    constexpr int kSegs = kBand / kSlotsPerSeg;       // 16-byte copies per band
+    constexpr int kHalf = kTileH / 2;
+    constexpr int kBpChunk = BpChunk<T>::value;
     const Item it = decode_item(probs, items, 1);
     const Prob<T>& P = probs[it.prob];
     if (P.st->done) return;
-    constexpr int kChunk = 128;
-    constexpr int kHalf = kTileH / 2;
-    struct Row { T c, s, kb, hb0, hb1, inv_m, frac; int base; };
-    __shared__ Row tab[kChunk];
+    __shared__ BpRow<T> rows[2][kBpChunk];
+    __shared__ __align__(16) T2 band[2][NRHS][kBpChunk][kBand];
     const int N = P.n, na = P.na, nb = P.nb, SB = P.SB;
     const int ti0 = it.u * kTileH, tj0 = it.v * kTileW;
     const int tx = threadIdx.x % kTileW, ty = threadIdx.x / kTileW;
     const int i1 = ti0 + ty, i2 = ti0 + ty + kHalf, j = tj0 + tx;
     const bool in1 = (i1 < N) && (j < N), in2 = (i2 < N) && (j < N);
     const T dj = T(tx), di1 = T(ty), di2 = T(ty + kHalf);
-    const double xc0 = (double)tj0 - (double)P.off_n, yc0 = (double)ti0 - (double)P.off_n;
-    const unsigned top = (unsigned)(nb + 2 * kSPad - 2);
-    const T2* R0 = P.sino[src0];
-    const T2* R1 = NRHS == 2 ? P.sino[src1] : nullptr;
-    T a1 = T(0), a2 = T(0), b1 = T(0), b2 = T(0);
-    for (int a0 = 0; a0 < na; a0 += kChunk) {
-        const int cnt = min(kChunk, na - a0);
-        __syncthreads();
-        for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
-            const Angle<T> g = P.ang[a0 + q];
-            const double cbt = (double)P.off_b + xc0 * g.c_d + yc0 * g.s_d;
-            const double fl = floor(cbt);
-            Row r;
+    const int X2 = 2 * tj0 - (N - 1), Y2 = 2 * ti0 - (N - 1);
+    const T2* R[2] = {P.sino[src0], NRHS == 2 ? P.sino[src1] : P.sino[src0]};
+    const int nchunks = (na + kBpChunk - 1) / kBpChunk;
+
+    auto stage_rows = [&](int ch) {
+        const int q = threadIdx.x;
+        const int a = ch * kBpChunk + q;
+        if (q < kBpChunk && a < na) {
+            const Angle<T> g = P.ang[a];
+            int I;
+            T F;
+            tile_origin<T>(g, X2, Y2, nb, I, F);
+            const int lo = (int)tfloor(T(kTileW - 1) * tmin(g.c, T(0))) - 1;
+            const int s_lo = (I + kSPad + lo) & ~(kSlotsPerSeg - 1);
+            BpRow<T> r;
             r.c = g.c; r.s = g.s; r.kb = g.kb; r.hb0 = g.hb0; r.hb1 = g.hb1; r.inv_m = g.inv_m;
-            r.frac = (T)(cbt - fl);
-            r.base = (int)fl + kSPad;
-            tab[q] = r;
+            r.frac = F;
+            r.rel = I + kSPad - s_lo;
+            r.s_lo = s_lo;
+            rows[ch & 1][q] = r;
         }
+    };
+    auto stage_copy = [&](int ch) {
+        const int a0 = ch * kBpChunk;
+        const int cnt = min(kBpChunk, na - a0);
+        for (int sg = threadIdx.x; sg < NRHS * cnt * kSegs; sg += blockDim.x) {
+            const int h = sg / (cnt * kSegs);
+            const int rem = sg - h * cnt * kSegs;
+            const int q = rem / kSegs, k = rem - q * kSegs;
+            const int slot = rows[ch & 1][q].s_lo + k * kSlotsPerSeg;
+            const T2* row = R[h] + (size_t)(a0 + q) * SB;
+            const bool ok = slot >= 0 && slot + kSlotsPerSeg <= SB;
+            cp_async16(&band[ch & 1][h][q][k * kSlotsPerSeg], ok ? row + slot : row, ok ? 16 : 0);
+        }
+        cp_async_commit();
+    };
+
+    T a1 = T(0), a2 = T(0), b1 = T(0), b2 = T(0);
+    stage_rows(0);
+    __syncthreads();
+    stage_copy(0);
+    for (int ch = 0; ch < nchunks; ++ch) {
+        const bool more = ch + 1 < nchunks;
+        if (more) stage_rows(ch + 1);
         __syncthreads();
+        if (more) { stage_copy(ch + 1); cp_async_wait<1>(); }
+        else cp_async_wait<0>();
+        __syncthreads();
+        const int cnt = min(kBpChunk, na - ch * kBpChunk);
+        const int buf = ch & 1;
         if (in1) {
-            const T2* r0 = R0 + (size_t)a0 * SB;
-            const T2* r1 = NRHS == 2 ? R1 + (size_t)a0 * SB : nullptr;
-#pragma unroll 2
+#pragma unroll 4
             for (int q = 0; q < cnt; ++q) {
-                const Row& g = tab[q];
+                const BpRow<T>& g = rows[buf][q];
                 const T djc = dj * g.c;
                 const T v1 = g.frac + fma(di1, g.s, djc);
                 const T v2 = g.frac + fma(di2, g.s, djc);
                 int q1, q2;
                 const T f1 = v1 - floor_split(v1, q1);
                 const T f2 = v2 - floor_split(v2, q2);
-                const unsigned s1 = min((unsigned)(q1 + g.base), top);
-                const unsigned s2 = min((unsigned)(q2 + g.base), top);
+                const unsigned k1 = min((unsigned)(q1 + g.rel), (unsigned)(kBand - 2));
+                const unsigned k2 = min((unsigned)(q2 + g.rel), (unsigned)(kBand - 2));
                 const T w10 = sat(fma(-f1, g.kb, g.hb0)), w11 = sat(fma(f1, g.kb, g.hb1));
                 const T w20 = sat(fma(-f2, g.kb, g.hb0)), w21 = sat(fma(f2, g.kb, g.hb1));
-                const T2 e1 = __ldg(r0 + (size_t)q * SB + s1);
-                const T2 e2 = __ldg(r0 + (size_t)q * SB + s2);
+                const T2 e1 = band[buf][0][q][k1];
+                const T2 e2 = band[buf][0][q][k2];
                 a1 = fma(g.inv_m, fma(w10, e1.x, w11 * e1.y), a1);
                 a2 = fma(g.inv_m, fma(w20, e2.x, w21 * e2.y), a2);
                 if (NRHS == 2) {
-                    const T2 z1 = __ldg(r1 + (size_t)q * SB + s1);
-                    const T2 z2 = __ldg(r1 + (size_t)q * SB + s2);
+                    const T2 z1 = band[buf][NRHS - 1][q][k1];
+                    const T2 z2 = band[buf][NRHS - 1][q][k2];
                     b1 = fma(g.inv_m, fma(w10, z1.x, w11 * z1.y), b1);
                     b2 = fma(g.inv_m, fma(w20, z2.x, w21 * z2.y), b2);
                 }
             }
         }
+        __syncthreads();
     }
     const size_t idx1 = (size_t)i1 * N + j, idx2 = (size_t)i2 * N + j;
     if (in1) {

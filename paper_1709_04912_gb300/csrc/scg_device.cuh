@@ -50,7 +50,8 @@ enum SinoBuf { SB_R = 0, SB_Q, SB_W, SB_COUNT };
 //    nearest the crossing c*, rows floor(c*) and floor(c*)+1; with
 //    f = c* - floor(c*) the first gets u/m, the second (1-u)/m,
 //    u = sat(h2 - f k2), k2 = m/n, h2 = (m+n)/(2n)   (n = 0: k2 = h2 = 1);
-//    the FP32 walk carries c* in 32.32 fixed point (exact increments);
+//    the FP32 walk carries c* in 32.32 fixed point (exact increments, no
+//    FP64 anywhere in the FP32 kernels);
 //  * gathering at a pixel whose centre projects to bin coordinate cb
 //    (g = cb - floor(cb)), bins floor(cb) and floor(cb)+1 get
 //    sat(hb0 - g kb)/m and sat(hb1 + g kb)/m,
@@ -63,12 +64,14 @@ struct Angle {
     T kb, hb0;     // gather weights
     T hb1;
     T slope;       // change of the crossing per step along the driving axis
+    T inv_drive;   // 1/s (column-walked) or 1/c
+    T c0_off;      // off_n * (e * inv_drive + 1), e = c (column-walked) or s
+    T inv_slope;   // 1/slope (0 when slope = 0)
     int col_driven;
-    double c_d, s_d;          // cos, sin in FP64 (tile origins of the gather)
-    double inv_d;             // 1/s (column-walked) or 1/c, FP64
-    double c0_off_d;          // off_n * (e * inv + 1), e = c (column-walked) or s
-    double slope_d;
-    long long slope_fx;       // slope in 32.32 fixed point (FP32 forward walk)
+    double c_d, s_d;          // FP64 copies (FP64 kernels)
+    double inv_d, c0_off_d, slope_d;
+    long long c_fx, s_fx;     // 32.32 fixed point (FP32 kernels)
+    long long inv_fx, c0_off_fx, slope_fx;
 };
 
 // Work item of a launch over many problems (batched mode).  Single-problem

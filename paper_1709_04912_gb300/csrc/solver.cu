@@ -139,13 +139,22 @@ void fill_angles(std::vector<Angle<T>>& out, int na, int n) {
         g.col_driven = as >= ac ? 1 : 0;
         const double inv = g.col_driven ? 1.0 / s : 1.0 / c;
         const double e = g.col_driven ? c : s;
-        g.slope = (T)(-e * inv);
+        const double slope = -e * inv, c0_off = off_n * (e * inv + 1.0);
+        g.slope = (T)slope;
+        g.inv_drive = (T)inv;
+        g.c0_off = (T)c0_off;
+        g.inv_slope = slope == 0.0 ? (T)0 : (T)(1.0 / slope);
         g.c_d = c;
         g.s_d = s;
         g.inv_d = inv;
-        g.c0_off_d = off_n * (e * inv + 1.0);
-        g.slope_d = -e * inv;
-        g.slope_fx = llrint(g.slope_d * 4294967296.0);
+        g.c0_off_d = c0_off;
+        g.slope_d = slope;
+        const double two32 = 4294967296.0;
+        g.c_fx = llrint(c * two32);
+        g.s_fx = llrint(s * two32);
+        g.inv_fx = llrint(inv * two32);
+        g.c0_off_fx = llrint(c0_off * two32);
+        g.slope_fx = llrint(slope * two32);
         out[a] = g;
     }
 }
