@@ -29,7 +29,8 @@ __device__ __forceinline__ Item decode_item(const Prob<T>* probs, const Item* it
     it.local = blockIdx.x;
     if (kind == 0) { it.u = blockIdx.x / P.ray_blocks; it.v = blockIdx.x % P.ray_blocks; }
     else if (kind == 1) { it.u = blockIdx.x / P.tiles_x; it.v = blockIdx.x % P.tiles_x; }
-    else { it.u = blockIdx.x / P.filt_blocks; it.v = blockIdx.x % P.filt_blocks; }
+    else if (kind == 2) { it.u = blockIdx.x / P.filt_blocks; it.v = blockIdx.x % P.filt_blocks; }
+    else { it.u = blockIdx.x / P.proj_blocks; it.v = blockIdx.x % P.proj_blocks; }
     return it;
 }
 
@@ -151,26 +152,30 @@ __device__ __forceinline__ double project_ray<double>(const Prob<double>& P, con
     return acc * g.inv_m;
 }
 
+// One block: kProjAngles adjacent angles x kProjRays consecutive bins; each
+// warp walks 32 rays of one angle.  Rays of neighbouring angles cross the
+// image almost together, so the warps of a block read nearly the same view
+// spans and most of those reads hit L1.
 template <typename T>
-__global__ void __launch_bounds__(kRayBlock)
+__global__ void __launch_bounds__(kProjThreads)
 k_project(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int dst_sel,
           int mode, int step) {
-    const Item it = decode_item(probs, items, 0);
+    const Item it = decode_item(probs, items, 3);
     const Prob<T>& P = probs[it.prob];
     if (P.st->done) return;
     const int nb = P.nb;
-    const int a = it.u;
-    const int b = it.v * kRayBlock + threadIdx.x;
-    const Angle<T> g = P.ang[a];
+    const int a = it.u * kProjAngles + threadIdx.x / kProjRays;
+    const int b = it.v * kProjRays + threadIdx.x % kProjRays;
     double v[1] = {0.0};
-    if (b < nb) {
+    if (a < P.na && b < nb) {
+        const Angle<T> g = P.ang[a];
         T out = project_ray<T>(P, g, b);
         if (mode == PROJ_RESIDUAL) out = out - P.y[(size_t)a * nb + b];
         if (mode == PROJ_PLAIN_OUT) P.user_out[(size_t)a * nb + b] = out;
         else store_pair<T>(P.sino[dst_sel] + (size_t)a * P.SB + kSPad, b, out);
         v[0] = (double)out * (double)out;
     }
-    if (step != FIN_NONE) reduce_and_finalize<T, 1>(v, P, it.local, P.cnt_ray, step);
+    if (step != FIN_NONE) reduce_and_finalize<T, 1>(v, P, it.local, P.cnt_proj, step);
 }
 
 // ---------------------------------------------------------------------------
@@ -680,7 +685,7 @@ __global__ void k_taps(T* taps, int nb, int P, double mu, double gain) {
 template <typename T>
 void launch_project(const Prob<T>* d, const Item* items, int grid, int dst, int mode, int step,
                     cudaStream_t s) {
-    k_project<T><<<grid, kRayBlock, 0, s>>>(d, items, dst, mode, step);
+    k_project<T><<<grid, kProjThreads, 0, s>>>(d, items, dst, mode, step);
 }
 template <typename T>
 void launch_backproject(const Prob<T>* d, const Item* items, int grid, int nrhs, int src0,

@@ -35,7 +35,10 @@ constexpr int kTileW = 32;       // image tile width (pixels) = one warp
 constexpr int kTileH = 8;        // image tile height
 constexpr int kTileThreads = kTileW * kTileH;
 constexpr int kBackThreads = kTileThreads / 2;   // backprojector: two pixels per thread
-constexpr int kRayBlock = 128;   // rays per projector work item
+constexpr int kRayBlock = 128;   // rays per sinogram-row work item (axpy, pairs)
+constexpr int kProjAngles = 4;   // projector block: adjacent angles ...
+constexpr int kProjRays = 64;    // ... x consecutive rays (they read nearly the same image spans)
+constexpr int kProjThreads = kProjAngles * kProjRays;
 constexpr int kFilterBlock = 128;// output bins per filter work item
 
 enum ImgBuf { IB_X = 0, IB_XH, IB_P, IB_H, IB_G, IB_Z, IB_TVG, IB_AUX, IB_COUNT };
@@ -120,6 +123,7 @@ struct Prob {
     int S;                  // image-view line stride (elements)
     int SB;                 // sinogram-view row stride (elements)
     int cnt_ray, cnt_img, cnt_row;   // items per launch kind
+    int cnt_proj, proj_blocks;       // projector items; bin blocks per angle group
     int tiles_x;            // image tiles per row of tiles
     int ray_blocks;         // projector items per angle
     int filt_blocks;        // filter items per row

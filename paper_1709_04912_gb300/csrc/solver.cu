@@ -56,6 +56,7 @@ struct Plan {
     size_t sino[SB_COUNT];
     size_t total;
     int S, SB, cnt_ray, cnt_img, cnt_row, tiles_x, ray_blocks, filt_blocks, P;
+    int cnt_proj, proj_blocks;
 };
 
 enum PlanKind { PLAN_OP = 0, PLAN_SOLVE = 1 };
@@ -72,6 +73,8 @@ Plan make_plan(const scg_geometry& g, int variant, size_t tsize, int kind) {
     p.cnt_img = ((N + kTileH - 1) / kTileH) * p.tiles_x;
     p.filt_blocks = (nb + kFilterBlock - 1) / kFilterBlock;
     p.cnt_row = na * p.filt_blocks;
+    p.proj_blocks = (nb + kProjRays - 1) / kProjRays;
+    p.cnt_proj = ((na + kProjAngles - 1) / kProjAngles) * p.proj_blocks;
     p.P = filter_length(nb);
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, kAlign); return o; };
@@ -82,6 +85,7 @@ Plan make_plan(const scg_geometry& g, int variant, size_t tsize, int kind) {
     p.taps = take(tsize * (2 * (size_t)nb - 1));
     int maxcnt = p.cnt_ray > p.cnt_img ? p.cnt_ray : p.cnt_img;
     if (p.cnt_row > maxcnt) maxcnt = p.cnt_row;
+    if (p.cnt_proj > maxcnt) maxcnt = p.cnt_proj;
     p.partials = take(sizeof(double) * kSlots * (size_t)maxcnt);
     p.counter = take(sizeof(unsigned) * 4);
     p.view_rm = take(2 * tsize * (size_t)N * p.S);
@@ -174,6 +178,8 @@ Prob<T> make_prob(const scg_geometry& g, const Plan& pl, unsigned char* base) {
     P.tiles_x = pl.tiles_x;
     P.ray_blocks = pl.ray_blocks;
     P.filt_blocks = pl.filt_blocks;
+    P.cnt_proj = pl.cnt_proj;
+    P.proj_blocks = pl.proj_blocks;
     P.P = pl.P;
     P.off_n = (T)(0.5 * (g.n - 1));
     P.off_b = (T)(0.5 * (g.n_bins - 1));
@@ -204,10 +210,10 @@ Prob<T> make_prob(const scg_geometry& g, const Plan& pl, unsigned char* base) {
 template <typename T>
 struct Runner {
     const Prob<T>* d;
-    int g_ray, g_img, g_row, nb;
+    int g_ray, g_img, g_row, g_proj, nb;
     cudaStream_t s;
     int launches;
-    void project(int dst, int mode, int step) { ++launches; launch_project<T>(d, nullptr, g_ray, dst, mode, step, s); }
+    void project(int dst, int mode, int step) { ++launches; launch_project<T>(d, nullptr, g_proj, dst, mode, step, s); }
     void back1(int src, int dst, int step) { ++launches; launch_backproject<T>(d, nullptr, g_img, 1, src, src, dst, dst, step, s); }
     void back2(int s0, int s1, int d0, int d1, int step) { ++launches; launch_backproject<T>(d, nullptr, g_img, 2, s0, s1, d0, d1, step, s); }
     void vec(int op, int sel, int step) { ++launches; launch_vec<T>(d, nullptr, g_img, op, sel, step, s); }
@@ -414,7 +420,7 @@ int solve_impl(const scg_geometry* g, int variant, int precision, const scg_para
         if (smem > 227 * 1024) return SCG_ERR_UNSUPPORTED;
     }
     Runner<T> R{reinterpret_cast<const Prob<T>*>(base + pl.prob), pl.cnt_ray, pl.cnt_img, pl.cnt_row,
-                g->n_bins, s, 0};
+                pl.cnt_proj, g->n_bins, s, 0};
     Program pg;
     pg.variant = variant;
     pg.trial_passes = prm->perturb == SCG_PERTURB_GAMMA ? (prm->max_trials + kTrials - 1) / kTrials : 0;
@@ -589,7 +595,7 @@ int project_impl(const scg_geometry& g, const void* x, void* y, void* work, size
     if (rc) return rc;
     const Prob<T>* d = reinterpret_cast<const Prob<T>*>(base + pl.prob);
     launch_vec<T>(d, nullptr, pl.cnt_img, VEC_VIEWS, IB_AUX, FIN_NONE, s);
-    launch_project<T>(d, nullptr, pl.cnt_ray, SB_Q, PROJ_PLAIN_OUT, FIN_NONE, s);
+    launch_project<T>(d, nullptr, pl.cnt_proj, SB_Q, PROJ_PLAIN_OUT, FIN_NONE, s);
     CK(cudaGetLastError());
     return SCG_OK;
 }
