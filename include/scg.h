@@ -92,7 +92,8 @@ typedef struct {
                             perturbed (default 0)                                */
     double gamma0_rel;   /* default 0.05                                         */
     double a;            /* gamma_l = gamma_0 a^l; 0 < a < 1; default 0.975 (Sec. 4) */
-    int max_trials;      /* TV-acceptance trials per perturbation; default 32     */
+    int max_trials;      /* TV-acceptance trials per perturbation; default 31 (one
+                            pass of the trial kernel evaluates 31 candidates)   */
     int K;               /* CG-K/PCG-K inner steps (S-CG-K, S-PCG-K); default 2   */
     int k_inclusive;     /* 1: the printed loop "while k <= K" (K+1 steps); default 0 */
     double mu;           /* filter offset of c(w); <= 0 selects 2*pi/P (default)  */

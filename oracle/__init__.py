@@ -261,7 +261,7 @@ def norm_A(n: int, n_angles: int, n_bins: int, iters: int = 50) -> float:
 
 def default_params(**kw) -> dict:
     p = dict(variant="S-CG", eps=1.0, perturb="gamma", gamma0=0.0, gamma0_rel=0.05,
-             a=0.975, max_trials=32, eta0=0.0, K=2, k_inclusive=0, mu=0.0,
+             a=0.975, max_trials=31, eta0=0.0, K=2, k_inclusive=0, mu=0.0,
              filter_gain=1.0, filter_identity=0, max_iter=100)
     p.update(kw)
     return p

@@ -35,69 +35,71 @@ __device__ __forceinline__ Item decode_item(const Prob<T>* probs, const Item* it
 }
 
 // ---------------------------------------------------------------------------
-// Forward projector.  One thread per ray (a, b), kRayBlock consecutive bins of
-// one angle per block, so the sinogram writes are coalesced.  The ray is walked
-// along its driving axis (columns when |sin| >= |cos|, else rows); in each
-// strip its chord is 1/m and falls on the two pixels nearest the crossing,
-// split u : (1-u) by one saturating FMA of the crossing's fractional part (see
-// Angle).  The two pixels are one pair-layout load from the view whose lines
-// run across the driving axis.  The crossing c*(t) = c0 + t*slope is kept as
-// floor(c0) (integer, from FP64) plus an FP32 remainder, so its rounding
-// error scales with t*|slope| and not with the image size.
-// Walk of one ray over driving indices [tlo, thi]: the strip chord split
-// between the pair of pixels at the crossing (sum of u*(e0-e1) + e1).
-// FP32: the crossing c* in 32.32 fixed point C, so every increment is exact;
-// the high word is floor(c*), the fraction's top 23 bits become a float in
-// [1, 2) by an OR into the mantissa.
+// Forward projector.  One thread per ray (a, b); a block holds kProjAngles
+// adjacent angles x kProjRays consecutive bins, so sinogram writes are
+// coalesced and the block's warps read nearly the same image spans.  The ray
+// is walked along its driving axis (columns when |sin| >= |cos|, else rows);
+// in each strip its chord is 1/m and falls on the two pixels nearest the
+// crossing, split u : (1-u) by one saturating FMA of the crossing's
+// fractional part (see Angle).  The two pixels are one pair-layout load from
+// the view whose lines run across the driving axis.  Crossing at driving
+// index t: c*(t) = c0 + t*slope, c0 = (b - (nb-1)/2) * inv_drive + c0_off.
+//
+// FP32 walk: c* is carried in 32.32 fixed point C, so every increment is
+// exact; the high word is floor(c*) and the fraction's top 23 bits become a
+// float in [1, 2) by an OR into the mantissa.
+__device__ __forceinline__ float2 ld_pair(const float2* line, long long C, unsigned top) {
+    return __ldg(line + min((unsigned)((int)(C >> 32) + kPad), top));
+}
+__device__ __forceinline__ float frac_of(long long C) {
+    return __int_as_float(0x3F800000 | ((unsigned)C >> 9)) - 1.0f;
+}
+__device__ __forceinline__ void strip(float2 v, long long C, float k2, float h2, float& u, float& y) {
+    u = fmaf(__saturatef(fmaf(-frac_of(C), k2, h2)), v.x - v.y, u);
+    y += v.y;
+}
+
+// The walk is software-pipelined: the loads of the next four strips are in
+// flight while the current four are summed.
 __device__ __forceinline__ float walk_ray_f32(const float2* line, int S, int tlo, int thi,
                                               long long C, long long SL, float k2, float h2,
                                               unsigned top) {
     line += (size_t)tlo * S;
+    const int n = thi - tlo + 1;
     float u0 = 0.f, u1 = 0.f, y0 = 0.f, y1 = 0.f;
-    int t = tlo;
-    for (; t + 3 <= thi; t += 4) {
-        const long long Ca = C, Cb = C + SL, Cc = C + 2 * SL, Cd = C + 3 * SL;
-        const unsigned sa = min((unsigned)((int)(Ca >> 32) + kPad), top);
-        const unsigned sb = min((unsigned)((int)(Cb >> 32) + kPad), top);
-        const unsigned sc = min((unsigned)((int)(Cc >> 32) + kPad), top);
-        const unsigned sd = min((unsigned)((int)(Cd >> 32) + kPad), top);
-        const float2 va = __ldg(line + sa);
-        const float2 vb = __ldg(line + S + sb);
-        const float2 vc = __ldg(line + 2 * S + sc);
-        const float2 vd = __ldg(line + 3 * S + sd);
-        const float fa = __int_as_float(0x3F800000 | ((unsigned)Ca >> 9)) - 1.0f;
-        const float fb = __int_as_float(0x3F800000 | ((unsigned)Cb >> 9)) - 1.0f;
-        const float fc = __int_as_float(0x3F800000 | ((unsigned)Cc >> 9)) - 1.0f;
-        const float fd = __int_as_float(0x3F800000 | ((unsigned)Cd >> 9)) - 1.0f;
-        u0 = fmaf(__saturatef(fmaf(-fa, k2, h2)), va.x - va.y, u0);
-        u1 = fmaf(__saturatef(fmaf(-fb, k2, h2)), vb.x - vb.y, u1);
-        u0 = fmaf(__saturatef(fmaf(-fc, k2, h2)), vc.x - vc.y, u0);
-        u1 = fmaf(__saturatef(fmaf(-fd, k2, h2)), vd.x - vd.y, u1);
-        y0 += va.y + vc.y;
-        y1 += vb.y + vd.y;
-        C += 4 * SL;
+    int t = 0;
+    if (n >= 4) {
+        long long Ca = C, Cb = C + SL, Cc = C + 2 * SL, Cd = C + 3 * SL;
+        float2 va = ld_pair(line, Ca, top), vb = ld_pair(line + S, Cb, top);
+        float2 vc = ld_pair(line + 2 * S, Cc, top), vd = ld_pair(line + 3 * S, Cd, top);
+        for (t = 4; t + 4 <= n; t += 4) {
+            const float2* nl = line + 4 * S;
+            const long long Na = Cd + SL, Nb = Cd + 2 * SL, Nc = Cd + 3 * SL, Nd = Cd + 4 * SL;
+            const float2 wa = ld_pair(nl, Na, top), wb = ld_pair(nl + S, Nb, top);
+            const float2 wc = ld_pair(nl + 2 * S, Nc, top), wd = ld_pair(nl + 3 * S, Nd, top);
+            strip(va, Ca, k2, h2, u0, y0);
+            strip(vb, Cb, k2, h2, u1, y1);
+            strip(vc, Cc, k2, h2, u0, y0);
+            strip(vd, Cd, k2, h2, u1, y1);
+            va = wa; vb = wb; vc = wc; vd = wd;
+            Ca = Na; Cb = Nb; Cc = Nc; Cd = Nd;
+            line = nl;
+        }
+        strip(va, Ca, k2, h2, u0, y0);
+        strip(vb, Cb, k2, h2, u1, y1);
+        strip(vc, Cc, k2, h2, u0, y0);
+        strip(vd, Cd, k2, h2, u1, y1);
+        C = Cd + SL;
         line += 4 * S;
     }
-    for (; t <= thi; ++t) {
-        const unsigned sa = min((unsigned)((int)(C >> 32) + kPad), top);
-        const float2 va = __ldg(line + sa);
-        const float fa = __int_as_float(0x3F800000 | ((unsigned)C >> 9)) - 1.0f;
-        u0 = fmaf(__saturatef(fmaf(-fa, k2, h2)), va.x - va.y, u0);
-        y0 += va.y;
+    for (; t < n; ++t) {
+        strip(ld_pair(line, C, top), C, k2, h2, u0, y0);
         C += SL;
         line += S;
     }
     return (u0 + u1) + (y0 + y1);
 }
 
-// Forward projector.  One thread per ray (a, b), kRayBlock consecutive bins of
-// one angle per block, so the sinogram writes are coalesced.  The ray is walked
-// along its driving axis (columns when |sin| >= |cos|, else rows); in each
-// strip its chord is 1/m and falls on the two pixels nearest the crossing,
-// split u : (1-u) by one saturating FMA of the crossing's fractional part (see
-// Angle).  The two pixels are one pair-layout load from the view whose lines
-// run across the driving axis.  Crossing at driving index t:
-// c*(t) = c0 + t*slope, c0 = (b - (nb-1)/2) * inv_drive + c0_off.
 template <typename T>
 __device__ __forceinline__ T project_ray(const Prob<T>& P, const Angle<T>& g, int b);
 
@@ -556,33 +558,84 @@ k_tvgrad(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int 
 template <typename T>
 __global__ void __launch_bounds__(kTileThreads)
 k_trial(const Prob<T>* __restrict__ probs, const Item* __restrict__ items) {
+    constexpr int NS = kTrials + 1;                 // 31 candidates + x itself
+    constexpr int NW = kTileThreads / 32;
     const Item it = decode_item(probs, items, 1);
     const Prob<T>& P = probs[it.prob];
     const DevState& st = *P.st;
     if (st.done || st.accepted != 0) return;
+    __shared__ double wsum[NW][NS];
+    __shared__ double coef_s[kTrials];
+    __shared__ unsigned s_last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x < kTrials) coef_s[threadIdx.x] = st.trial_coef[threadIdx.x];
+    __syncthreads();
     const int N = P.n;
     const int i = it.u * kTileH + threadIdx.x / kTileW;
     const int j = it.v * kTileW + threadIdx.x % kTileW;
-    double v[kTrials + 1];
-#pragma unroll
-    for (int t = 0; t <= kTrials; ++t) v[t] = 0.0;
-    if (i < N - 1 && j < N - 1) {
+    const bool in = (i < N - 1) && (j < N - 1);
+    T x0 = T(0), xu = T(0), xv = T(0), q0 = T(0), qu = T(0), qv = T(0);
+    if (in) {
         const T* X = P.img[IB_X];
         const T* G = P.img[IB_TVG];
         const size_t g0 = (size_t)i * N + j;
-        const T x0 = X[g0], xu = X[g0 + N], xv = X[g0 + 1];
-        const T q0 = G[g0], qu = G[g0 + N], qv = G[g0 + 1];
-#pragma unroll
-        for (int t = 0; t < kTrials; ++t) {
-            const T c = (T)st.trial_coef[t];
-            const T z0 = fma_rn(c, q0, x0), zu = fma_rn(c, qu, xu), zv = fma_rn(c, qv, xv);
-            const T du = zu - z0, dv = zv - z0;
-            v[t] = (double)tsqrt(du * du + dv * dv);
-        }
-        const T du = xu - x0, dv = xv - x0;
-        v[kTrials] = (double)tsqrt(du * du + dv * dv);
+        x0 = X[g0]; xu = X[g0 + N]; xv = X[g0 + 1];
+        q0 = G[g0]; qu = G[g0 + N]; qv = G[g0 + 1];
     }
-    reduce_and_finalize<T, kTrials + 1>(v, P, it.local, P.cnt_img, FIN_TRIAL);
+#pragma unroll
+    for (int grp = 0; grp < NS / 8; ++grp) {
+        double v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int t = grp * 8 + k;
+            T du, dv;
+            if (t < kTrials) {
+                const T c = (T)coef_s[t];
+                const T z0 = fma_rn(c, q0, x0), zu = fma_rn(c, qu, xu), zv = fma_rn(c, qv, xv);
+                du = zu - z0; dv = zv - z0;
+            } else {
+                du = xu - x0; dv = xv - x0;
+            }
+            v[k] = in ? (double)tsqrt(du * du + dv * dv) : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) wsum[warp][grp * 8 + k] = v[k];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < NS) {
+        double b = 0.0;
+        for (int w = 0; w < NW; ++w) b += wsum[w][threadIdx.x];
+        P.partials[(size_t)it.local * kSlots + threadIdx.x] = b;
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(P.counter, 1u) + 1u == (unsigned)P.cnt_img);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // last block: slot = tid % NS, items tid / NS, tid / NS + NW, ... (fixed order)
+    const int slot = threadIdx.x % NS, lane_grp = threadIdx.x / NS;
+    double acc = 0.0;
+    for (int q = lane_grp; q < P.cnt_img; q += NW) acc += __ldcg(P.partials + (size_t)q * kSlots + slot);
+    wsum[lane_grp][slot] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *P.counter = 0u;
+        double S[NS];
+        for (int t = 0; t < NS; ++t) {
+            double sum = 0.0;
+            for (int w = 0; w < NW; ++w) sum += wsum[w][t];
+            S[t] = sum;
+        }
+        finalize<T>(FIN_TRIAL, P, S);
+    }
 }
 
 // ---------------------------------------------------------------------------

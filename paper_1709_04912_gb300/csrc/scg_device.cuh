@@ -29,8 +29,8 @@ namespace scg {
 
 constexpr int kPad = 2;          // zero elements on each side of an image-view line
 constexpr int kSPad = 2;         // zero elements on each side of a sinogram-view row
-constexpr int kSlots = 8;        // FP64 partial sums per work item
-constexpr int kTrials = 7;       // TV trial candidates per pass (+1 baseline slot)
+constexpr int kSlots = 32;       // FP64 partial sums per work item (at most)
+constexpr int kTrials = 31;      // TV trial candidates per pass (+1 baseline slot)
 constexpr int kTileW = 32;       // image tile width (pixels) = one warp
 constexpr int kTileH = 8;        // image tile height
 constexpr int kTileThreads = kTileW * kTileH;
@@ -230,7 +230,7 @@ template <typename T> __device__ void finalize(int step, const Prob<T>& P, const
 template <typename T, int NS>
 __device__ void reduce_and_finalize(double (&v)[NS], const Prob<T>& P, int local, int total,
                                     int step) {
-    __shared__ double red[32 * kSlots];
+    __shared__ double red[32 * NS];
     __shared__ unsigned s_last;
     block_sum<NS>(v, red);
     if (threadIdx.x == 0) {
@@ -255,9 +255,9 @@ __device__ void reduce_and_finalize(double (&v)[NS], const Prob<T>& P, int local
     block_sum<NS>(acc, red);
     if (threadIdx.x == 0) {
         *P.counter = 0u;
-        double S[kSlots];
+        double S[NS < 4 ? 4 : NS];
 #pragma unroll
-        for (int k = 0; k < kSlots; ++k) S[k] = k < NS ? acc[k] : 0.0;
+        for (int k = 0; k < (NS < 4 ? 4 : NS); ++k) S[k] = k < NS ? acc[k] : 0.0;
         finalize<T>(step, P, S);
     }
 }
@@ -302,9 +302,12 @@ __device__ void end_body(const Prob<T>& P) {
 template <typename T>
 __device__ void set_trial_coefs(const Prob<T>& P) {
     DevState& st = *P.st;
-    double inv = 1.0 / sqrt(st.gnorm2);
-    for (int t = 0; t < kTrials; ++t)
-        st.trial_coef[t] = -st.gamma0 * pow(st.a, (double)(st.ell + t)) * inv;
+    // coef_t = -gamma0 a^(l+t) / ||dTV||, t = 0 .. kTrials-1
+    double c = -st.gamma0 * pow(st.a, (double)st.ell) / sqrt(st.gnorm2);
+    for (int t = 0; t < kTrials; ++t) {
+        st.trial_coef[t] = c;
+        c *= st.a;
+    }
 }
 
 // Top of the while loop: test f(x_{k-1/2}) > eps (f(x_k) for CG/PCG) and the

@@ -686,7 +686,7 @@ void scg_default_params(scg_params* p) {
     p->gamma0 = 0.0;
     p->gamma0_rel = 0.05;
     p->a = 0.975;
-    p->max_trials = 32;
+    p->max_trials = 31;
     p->K = 2;
     p->k_inclusive = 0;
     p->mu = 0.0;
