@@ -236,6 +236,7 @@ def run_ours(args, work, rank, local_rank, world):
     ms = []
     launches = 0
     results = []
+    torch.cuda.nvtx.range_push("timed")
     for _ in range(args.steps):
         flush.fill_(1)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -248,6 +249,7 @@ def run_ours(args, work, rank, local_rank, world):
         launches += r.kernel_launches
         results.append(r)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     clk = clocks.stop()
     t_total = sum(ms) / 1e3
     if world > 1:
@@ -360,7 +362,7 @@ def run_ours(args, work, rank, local_rank, world):
                            "f_final": last.f_final, "l2": "flushed (512 MiB write) before each step",
                            "per_gpu_problems": 1, "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches, "clocks": clk,
+                "gpu_launches": launches, "device_loop": bool(last.device_loop), "clocks": clk,
                 "step_ms": ms}
         print(json.dumps(line), flush=True)
     return 0

@@ -94,11 +94,12 @@ typedef struct {
     double a;            /* gamma_l = gamma_0 a^l; 0 < a < 1; default 0.975 (Sec. 4) */
     int max_trials;      /* TV-acceptance trials per perturbation; default 31 (one
                             pass of the trial kernel evaluates 31 candidates)   */
-    int K;               /* CG-K/PCG-K inner steps (S-CG-K, S-PCG-K); default 2   */
+    int K;               /* CG-K/PCG-K inner steps (S-CG-K, S-PCG-K), 1 .. 1000;
+                            default 2                                             */
     int k_inclusive;     /* 1: the printed loop "while k <= K" (K+1 steps); default 0 */
     double mu;           /* filter offset of c(w); <= 0 selects 2*pi/P (default)  */
     double filter_gain;  /* scale of c(w); default 1                              */
-    int max_iter;        /* cap on loop bodies; default 100                       */
+    int max_iter;        /* cap on loop bodies, 0 .. 10^7; default 100             */
 } scg_params;
 
 typedef struct {
@@ -111,8 +112,10 @@ typedef struct {
     double gamma0_used;  /* gamma_0 in force at exit (0 if never fixed)            */
     int kernel_launches; /* kernels this call enqueued (graph nodes counted per
                             launch of the loop-body graph)                       */
-    int body_launches;   /* loop-body graph launches (bodies after the stop flag
-                            return at once)                                      */
+    int body_launches;   /* loop bodies started (with the polled loop, bodies
+                            launched after the stop flag return at once)         */
+    int device_loop;     /* 1: the loop ran as one CUDA graph whose conditional
+                            node the device steers; 0: host-polled graph launches */
 } scg_result;
 
 /* Solver state, for exact checkpoint/resume and for single-step checks.  The

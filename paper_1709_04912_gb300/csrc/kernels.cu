@@ -734,6 +734,22 @@ __global__ void k_taps(T* taps, int nb, int P, double mu, double gain) {
 }
 
 // ---------------------------------------------------------------------------
+// Loop condition of the device-driven while loop (one thread): continue while
+// the solver has not stopped, and never past max_bodies bodies, so the loop
+// ends even if the stop flag were never set.
+__global__ void k_loop_cond(DevState* st, cudaGraphConditionalHandle h) {
+    if (threadIdx.x != 0) return;
+    unsigned more = st->done ? 0u : 1u;
+    if (st->bodies >= st->max_bodies) more = 0u;
+    st->bodies += (int)more;
+    cudaGraphSetConditional(h, more);
+}
+
+void launch_loop_cond(DevState* st, cudaGraphConditionalHandle h, cudaStream_t s) {
+    k_loop_cond<<<1, 32, 0, s>>>(st, h);
+}
+
+// ---------------------------------------------------------------------------
 // Host launchers.
 template <typename T>
 void launch_project(const Prob<T>* d, const Item* items, int grid, int dst, int mode, int step,

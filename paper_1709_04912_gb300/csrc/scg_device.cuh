@@ -108,6 +108,7 @@ struct DevState {
     int k, iters, max_iter, done, status;
     int perturb, gamma_fixed, max_trials, trials, accepted;
     int in_init, variant, inner_stop, family;
+    int bodies, max_bodies;  // loop bodies started by the device loop, and its hard cap
 };
 
 enum Family { FAM_CG = 0, FAM_S_PR = 1, FAM_S_K = 2 };

@@ -41,5 +41,6 @@ template <typename T>
 void launch_taps(T* taps, int nb, int P, double mu, double gain, cudaStream_t s);
 template <typename T>
 void launch_sino_pairs(const Prob<T>* d, int grid, int dst, cudaStream_t s);
+void launch_loop_cond(DevState* st, cudaGraphConditionalHandle h, cudaStream_t s);
 
 }  // namespace scg

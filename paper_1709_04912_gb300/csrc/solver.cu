@@ -333,6 +333,7 @@ struct GraphKey {
 struct BodyGraph {
     cudaGraphExec_t exec;
     int kernels;
+    bool device_loop;    // whole while loop in one graph (conditional node)
 };
 
 std::mutex g_mu;
@@ -439,69 +440,123 @@ int solve_impl(const scg_geometry* g, int variant, int precision, const scg_para
     }
     CK(cudaGetLastError());
 
-    // the loop body as one CUDA graph, cached per workspace and program
+    // The while loop.  Preferred: one CUDA graph holding the whole loop as a
+    // conditional WHILE node whose condition a one-thread kernel sets on the
+    // device after every body (no host round trip per iteration).  Fallback:
+    // one graph per body, launched in batches and polled one batch ahead.
     GraphKey key{dev, work, precision, variant, pg.trial_passes, pg.ksteps, g->n, g->n_angles, g->n_bins};
-    cudaGraphExec_t exec = nullptr;
-    int body_kernels = 0;
+    BodyGraph bg{nullptr, 0, false};
     {
         std::lock_guard<std::mutex> lk(g_mu);
         auto it = g_graphs.find(key);
-        if (it != g_graphs.end()) { exec = it->second.exec; body_kernels = it->second.kernels; }
+        if (it != g_graphs.end()) bg = it->second;
     }
-    if (!exec) {
+    DevState* dst_mut = reinterpret_cast<DevState*>(base + pl.state);
+    if (!bg.exec) {
         cudaStream_t cap;
         CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-        CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
         Runner<T> RC = R;
         RC.s = cap;
         RC.launches = 0;
-        run_body<T>(RC, pg);
-        body_kernels = RC.launches;
-        cudaGraph_t graph;
-        cudaError_t e = cudaStreamEndCapture(cap, &graph);
+        // device loop
+        cudaGraph_t g0 = nullptr;
+        bool ok = cudaGraphCreate(&g0, 0) == cudaSuccess;
+        cudaGraphConditionalHandle h = 0;
+        if (ok) ok = cudaGraphConditionalHandleCreate(&h, g0, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+        cudaGraph_t tmp = nullptr;
+        if (ok) ok = cudaStreamBeginCaptureToGraph(cap, g0, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            launch_loop_cond(dst_mut, h, cap);
+            ok = cudaStreamEndCapture(cap, &tmp) == cudaSuccess;
+        }
+        cudaGraphNode_t pre = nullptr;
+        size_t nn = 1;
+        if (ok) ok = cudaGraphGetNodes(g0, &pre, &nn) == cudaSuccess && nn == 1;
+        alignas(cudaGraphNodeParams) unsigned char npbuf[sizeof(cudaGraphNodeParams)];
+        memset(npbuf, 0, sizeof(npbuf));
+        cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(npbuf);
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t wnode = nullptr;
+        if (ok) ok = cudaGraphAddNode(&wnode, g0, &pre, nullptr, 1, &np) == cudaSuccess;
+        if (ok) {
+            cudaGraph_t body = np.conditional.phGraph_out[0];
+            ok = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (ok) {
+                run_body<T>(RC, pg);
+                launch_loop_cond(dst_mut, h, cap);
+                ok = cudaStreamEndCapture(cap, &tmp) == cudaSuccess;
+            }
+        }
+        if (ok) ok = cudaGraphInstantiate(&bg.exec, g0, 0) == cudaSuccess;
+        if (g0) cudaGraphDestroy(g0);
+        if (ok) {
+            bg.kernels = RC.launches;
+            bg.device_loop = true;
+        } else {
+            cudaGetLastError();                     // clear, and fall back
+            bg.exec = nullptr;
+            RC.launches = 0;
+            CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+            run_body<T>(RC, pg);
+            cudaGraph_t graph;
+            cudaError_t e = cudaStreamEndCapture(cap, &graph);
+            if (e != cudaSuccess) { cudaStreamDestroy(cap); return SCG_ERR_CUDA; }
+            e = cudaGraphInstantiate(&bg.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) { cudaStreamDestroy(cap); return SCG_ERR_CUDA; }
+            bg.kernels = RC.launches;
+            bg.device_loop = false;
+        }
         cudaStreamDestroy(cap);
-        if (e != cudaSuccess) return SCG_ERR_CUDA;
-        e = cudaGraphInstantiate(&exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (e != cudaSuccess) return SCG_ERR_CUDA;
         std::lock_guard<std::mutex> lk(g_mu);
-        g_graphs[key] = BodyGraph{exec, body_kernels};
+        g_graphs[key] = bg;
     }
 
-    // loop bodies, polled one batch ahead
     const DevState* dst = reinterpret_cast<const DevState*>(base + pl.state);
     const int max_bodies = prm->max_iter + 2;
-    int launched = 0, polled = 0;
-    cudaEvent_t evs[2];
-    CK(cudaEventCreateWithFlags(&evs[0], cudaEventDisableTiming));
-    CK(cudaEventCreateWithFlags(&evs[1], cudaEventDisableTiming));
-    int chunk = 2;
-    bool finished = false;
-    int pending = -1;
-    while (!finished) {
-        if (launched < max_bodies) {
-            int cnt = chunk;
-            if (launched + cnt > max_bodies) cnt = max_bodies - launched;
-            for (int q = 0; q < cnt; ++q) CK(cudaGraphLaunch(exec, s));
-            launched += cnt;
-            const int slot = polled & 1;
-            CK(cudaMemcpyAsync(pinned + slot, &dst->done, sizeof(int), cudaMemcpyDeviceToHost, s));
-            CK(cudaEventRecord(evs[slot], s));
-            if (chunk < 8) chunk *= 2;
+    int launched = 0;
+    if (bg.device_loop) {
+        int mb[2] = {0, max_bodies};                // bodies, max_bodies
+        CK(cudaMemcpyAsync(&dst_mut->bodies, mb, sizeof(mb), cudaMemcpyHostToDevice, s));
+        CK(cudaGraphLaunch(bg.exec, s));
+    } else {
+        // loop bodies, polled one batch ahead
+        int polled = 0;
+        cudaEvent_t evs[2];
+        CK(cudaEventCreateWithFlags(&evs[0], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&evs[1], cudaEventDisableTiming));
+        int chunk = 2;
+        bool finished = false;
+        int pending = -1;
+        while (!finished) {
+            if (launched < max_bodies) {
+                int cnt = chunk;
+                if (launched + cnt > max_bodies) cnt = max_bodies - launched;
+                for (int q = 0; q < cnt; ++q) CK(cudaGraphLaunch(bg.exec, s));
+                launched += cnt;
+                const int slot = polled & 1;
+                CK(cudaMemcpyAsync(pinned + slot, &dst->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+                CK(cudaEventRecord(evs[slot], s));
+                if (chunk < 8) chunk *= 2;
+            }
+            if (pending >= 0) {
+                CK(cudaEventSynchronize(evs[pending & 1]));
+                if (pinned[pending & 1]) finished = true;
+            }
+            pending = polled;
+            ++polled;
+            if (launched >= max_bodies && !finished) {
+                CK(cudaEventSynchronize(evs[pending & 1]));
+                finished = true;
+            }
         }
-        if (pending >= 0) {
-            CK(cudaEventSynchronize(evs[pending & 1]));
-            if (pinned[pending & 1]) finished = true;
-        }
-        pending = polled;
-        ++polled;
-        if (launched >= max_bodies && !finished) {
-            CK(cudaEventSynchronize(evs[pending & 1]));
-            finished = true;
-        }
+        cudaEventDestroy(evs[0]);
+        cudaEventDestroy(evs[1]);
     }
-    cudaEventDestroy(evs[0]);
-    cudaEventDestroy(evs[1]);
+    const int body_kernels = bg.kernels;
 
     // output, f and TV of the output
     const int out_sel = fam == FAM_CG ? IB_X : IB_XH;
@@ -542,8 +597,14 @@ int solve_impl(const scg_geometry* g, int variant, int precision, const scg_para
     res->tv_final = hs.tv_final;
     res->ell = hs.ell;
     res->gamma0_used = hs.gamma0;
-    res->body_launches = launched;
-    res->kernel_launches = R.launches + launched * body_kernels;
+    if (bg.device_loop) {
+        res->body_launches = hs.bodies;
+        res->kernel_launches = R.launches + 1 + hs.bodies * (body_kernels + 1);
+    } else {
+        res->body_launches = launched;
+        res->kernel_launches = R.launches + launched * body_kernels;
+    }
+    res->device_loop = bg.device_loop ? 1 : 0;
     if (final_state) {
         final_state->valid = 1;
         final_state->k = hs.k;
@@ -756,7 +817,8 @@ int scg_solve(const scg_geometry* g, int variant, int precision, const scg_param
               scg_state* final_state, void* stream) {
     if (!valid_geometry(g) || !prm || !y || !x_out || !work || !res) return SCG_ERR_INVALID;
     if (variant < SCG_CG || variant > SCG_S_PCG_K) return SCG_ERR_INVALID;
-    if (!(eps > 0.0) || !isfinite(eps) || prm->max_iter < 0 || prm->max_trials < 1 || prm->K < 1 ||
+    if (!(eps > 0.0) || !isfinite(eps) || prm->max_iter < 0 || prm->max_iter > 10000000 ||
+        prm->max_trials < 1 || prm->max_trials > 100000 || prm->K < 1 || prm->K > 1000 ||
         !(prm->a > 0.0 && prm->a < 1.0) || !(prm->filter_gain > 0.0))
         return SCG_ERR_INVALID;
     if (prm->perturb != SCG_PERTURB_NONE && prm->perturb != SCG_PERTURB_GAMMA) return SCG_ERR_INVALID;

@@ -43,7 +43,8 @@ class Result(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("k_final", ctypes.c_int), ("status", ctypes.c_int),
                 ("f_final", ctypes.c_double), ("tv_final", ctypes.c_double),
                 ("ell", ctypes.c_longlong), ("gamma0_used", ctypes.c_double),
-                ("kernel_launches", ctypes.c_int), ("body_launches", ctypes.c_int)]
+                ("kernel_launches", ctypes.c_int), ("body_launches", ctypes.c_int),
+                ("device_loop", ctypes.c_int)]
 
 
 class State(ctypes.Structure):
@@ -247,6 +248,7 @@ class SolveResult:
     gamma0_used: float
     kernel_launches: int = 0
     body_launches: int = 0
+    device_loop: int = 0
     trace: object = None
     state: dict | None = None
 
@@ -310,7 +312,7 @@ def scg_solve(y: torch.Tensor, n: int, variant: str = "S-CG", eps: float = 1.0, 
     _check(rc, "scg_solve", ok=(0, 1, -4))
     out_res = SolveResult(out, res.iters, res.k_final, STATUS.get(res.status, str(res.status)),
                           res.status, res.f_final, res.tv_final, res.ell, res.gamma0_used,
-                          res.kernel_launches, res.body_launches)
+                          res.kernel_launches, res.body_launches, res.device_loop)
     if trace:
         out_res.trace = tr[: min(res.iters, rows)].copy()
     if want_state:
