@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--gamma0-rel", type=float, default=0.05)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="run the while loop as host-polled per-body graphs (same kernels); "
+                         "lets a profiler list every kernel launch")
     return ap.parse_args()
 
 
@@ -207,7 +210,7 @@ def run_ours(args, work, rank, local_rank, world):
     dev = torch.device("cuda", local_rank)
     scg.load()
     variant = args.variant
-    kw = dict(gamma0_rel=args.gamma0_rel, max_iter=work.max_iter)
+    kw = dict(gamma0_rel=args.gamma0_rel, max_iter=work.max_iter, host_loop=int(args.host_loop))
     if variant in ("CG", "PCG"):
         kw["perturb"] = "none"
 

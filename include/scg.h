@@ -100,6 +100,11 @@ typedef struct {
     double mu;           /* filter offset of c(w); <= 0 selects 2*pi/P (default)  */
     double filter_gain;  /* scale of c(w); default 1                              */
     int max_iter;        /* cap on loop bodies, 0 .. 10^7; default 100             */
+    int host_loop;       /* 0 (default): the while loop runs as one CUDA graph
+                            with a conditional node steered by the device.
+                            1: one graph per loop body, launched in batches
+                            and polled by the host (same kernels; for tools
+                            that profile kernels one launch at a time)          */
 } scg_params;
 
 typedef struct {

@@ -48,54 +48,54 @@ __device__ __forceinline__ Item decode_item(const Prob<T>* probs, const Item* it
 // FP32 walk: c* is carried in 32.32 fixed point C, so every increment is
 // exact; the high word is floor(c*) and the fraction's top 23 bits become a
 // float in [1, 2) by an OR into the mantissa.
-__device__ __forceinline__ float2 ld_pair(const float2* line, long long C, unsigned top) {
-    return __ldg(line + min((unsigned)((int)(C >> 32) + kPad), top));
-}
-__device__ __forceinline__ float frac_of(long long C) {
-    return __int_as_float(0x3F800000 | ((unsigned)C >> 9)) - 1.0f;
-}
-__device__ __forceinline__ void strip(float2 v, long long C, float k2, float h2, float& u, float& y) {
-    u = fmaf(__saturatef(fmaf(-frac_of(C), k2, h2)), v.x - v.y, u);
+// D carries the view element index of the pair at the crossing in its high
+// word (line t*S, pad kPad, floor(c*)) and the crossing's fraction in its low
+// word; adding DL = slope + S (both in 32.32) steps to the next strip.
+__device__ __forceinline__ void strip(const float2* view, long long D, float k2, float h2p,
+                                      float& u, float& y) {
+    const float2 v = __ldg(view + (int)(D >> 32));
+    const float f1 = __int_as_float(0x3F800000 | ((unsigned)D >> 9));   // 1 + fraction
+    u = fmaf(__saturatef(fmaf(-f1, k2, h2p)), v.x - v.y, u);
     y += v.y;
 }
 
 // The walk is software-pipelined: the loads of the next four strips are in
-// flight while the current four are summed.
-__device__ __forceinline__ float walk_ray_f32(const float2* line, int S, int tlo, int thi,
-                                              long long C, long long SL, float k2, float h2,
-                                              unsigned top) {
-    line += (size_t)tlo * S;
-    const int n = thi - tlo + 1;
+// flight while the current four are summed.  Every index read lies inside the
+// view because [tlo, thi] holds exactly the strips whose crossing satisfies
+// -1 <= floor(c*) <= N-1 (kPad >= 1).
+__device__ __forceinline__ float walk_ray_f32(const float2* view, int n, long long D, long long DL,
+                                              float k2, float h2p) {
     float u0 = 0.f, u1 = 0.f, y0 = 0.f, y1 = 0.f;
     int t = 0;
     if (n >= 4) {
-        long long Ca = C, Cb = C + SL, Cc = C + 2 * SL, Cd = C + 3 * SL;
-        float2 va = ld_pair(line, Ca, top), vb = ld_pair(line + S, Cb, top);
-        float2 vc = ld_pair(line + 2 * S, Cc, top), vd = ld_pair(line + 3 * S, Cd, top);
+        long long Da = D, Db = D + DL, Dc = D + 2 * DL, Dd = D + 3 * DL;
+        float2 va = __ldg(view + (int)(Da >> 32)), vb = __ldg(view + (int)(Db >> 32));
+        float2 vc = __ldg(view + (int)(Dc >> 32)), vd = __ldg(view + (int)(Dd >> 32));
         for (t = 4; t + 4 <= n; t += 4) {
-            const float2* nl = line + 4 * S;
-            const long long Na = Cd + SL, Nb = Cd + 2 * SL, Nc = Cd + 3 * SL, Nd = Cd + 4 * SL;
-            const float2 wa = ld_pair(nl, Na, top), wb = ld_pair(nl + S, Nb, top);
-            const float2 wc = ld_pair(nl + 2 * S, Nc, top), wd = ld_pair(nl + 3 * S, Nd, top);
-            strip(va, Ca, k2, h2, u0, y0);
-            strip(vb, Cb, k2, h2, u1, y1);
-            strip(vc, Cc, k2, h2, u0, y0);
-            strip(vd, Cd, k2, h2, u1, y1);
+            const long long Na = Dd + DL, Nb = Dd + 2 * DL, Nc = Dd + 3 * DL, Nd = Dd + 4 * DL;
+            const float2 wa = __ldg(view + (int)(Na >> 32)), wb = __ldg(view + (int)(Nb >> 32));
+            const float2 wc = __ldg(view + (int)(Nc >> 32)), wd = __ldg(view + (int)(Nd >> 32));
+#define SCG_STRIP(V_, D_, U_, Y_)                                                                 \
+    U_ = fmaf(__saturatef(fmaf(-__int_as_float(0x3F800000 | ((unsigned)(D_) >> 9)), k2, h2p)),    \
+              V_.x - V_.y, U_);                                                                   \
+    Y_ += V_.y;
+            SCG_STRIP(va, Da, u0, y0)
+            SCG_STRIP(vb, Db, u1, y1)
+            SCG_STRIP(vc, Dc, u0, y0)
+            SCG_STRIP(vd, Dd, u1, y1)
             va = wa; vb = wb; vc = wc; vd = wd;
-            Ca = Na; Cb = Nb; Cc = Nc; Cd = Nd;
-            line = nl;
+            Da = Na; Db = Nb; Dc = Nc; Dd = Nd;
         }
-        strip(va, Ca, k2, h2, u0, y0);
-        strip(vb, Cb, k2, h2, u1, y1);
-        strip(vc, Cc, k2, h2, u0, y0);
-        strip(vd, Cd, k2, h2, u1, y1);
-        C = Cd + SL;
-        line += 4 * S;
+        SCG_STRIP(va, Da, u0, y0)
+        SCG_STRIP(vb, Db, u1, y1)
+        SCG_STRIP(vc, Dc, u0, y0)
+        SCG_STRIP(vd, Dd, u1, y1)
+#undef SCG_STRIP
+        D = Dd + DL;
     }
     for (; t < n; ++t) {
-        strip(ld_pair(line, C, top), C, k2, h2, u0, y0);
-        C += SL;
-        line += S;
+        strip(view, D, k2, h2p, u0, y0);
+        D += DL;
     }
     return (u0 + u1) + (y0 + y1);
 }
@@ -103,26 +103,42 @@ __device__ __forceinline__ float walk_ray_f32(const float2* line, int S, int tlo
 template <typename T>
 __device__ __forceinline__ T project_ray(const Prob<T>& P, const Angle<T>& g, int b);
 
+// Strips t in [0, N) whose crossing C(t) = C0 + t*SL (32.32) has floor in
+// [-1, N-1]: a FP32 estimate, then corrected exactly in integer arithmetic.
+__device__ __forceinline__ void walk_range(long long C0, long long SL, int N, float c0f, float inv_slope,
+                                           int& tlo, int& thi) {
+    const long long lo = -(1LL << 32), hi = (long long)N << 32;   // valid: lo <= C < hi
+    auto ok = [&](int t) { const long long C = C0 + (long long)t * SL; return C >= lo && C < hi; };
+    if (SL == 0) {
+        tlo = 0;
+        thi = (C0 >= lo && C0 < hi) ? N - 1 : -1;
+        return;
+    }
+    const float ta = (-1.f - c0f) * inv_slope, tb = ((float)N - c0f) * inv_slope;
+    tlo = max(0, min(N, (int)floorf(fminf(ta, tb))));
+    thi = min(N - 1, max(-1, (int)floorf(fmaxf(ta, tb)) + 1));
+    for (int q = 0; q < 3 && tlo <= thi && !ok(tlo); ++q) ++tlo;
+    for (int q = 0; q < 3 && tlo > 0 && ok(tlo - 1); ++q) --tlo;
+    for (int q = 0; q < 3 && thi >= tlo && !ok(thi); ++q) --thi;
+    for (int q = 0; q < 3 && thi < N - 1 && ok(thi + 1); ++q) ++thi;
+    // after the corrections every t in [tlo, thi] is valid (the valid set is
+    // an interval and both ends were checked); anything left unconfirmed is
+    // dropped rather than read out of range
+    if (tlo > thi || !ok(tlo) || !ok(thi)) { tlo = 0; thi = -1; }
+}
+
 template <>
 __device__ __forceinline__ float project_ray<float>(const Prob<float>& P, const Angle<float>& g, int b) {
     const int N = P.n, B2 = 2 * b - (P.nb - 1);           // 2 (b - (nb-1)/2)
-    // driving range in FP32 (conservative by one strip): crossings in [-2.5, N + 1.5]
-    const float c0f = fmaf(0.5f * (float)B2, g.inv_drive, g.c0_off);
-    int tlo = 0, thi = N - 1;
-    if (g.inv_slope == 0.f) {
-        if (!(c0f >= -2.5f && c0f <= (float)N + 1.5f)) thi = -1;
-    } else {
-        const float t1 = (-2.5f - c0f) * g.inv_slope, t2 = ((float)N + 1.5f - c0f) * g.inv_slope;
-        const float lo = fmaxf(fminf(t1, t2), -1.f), hi = fminf(fmaxf(t1, t2), (float)N);
-        tlo = max(0, (int)floorf(lo));
-        thi = min(N - 1, (int)floorf(hi) + 1);
-    }
-    // exact crossing in 32.32 fixed point
     const long long C0 = (((long long)B2 * g.inv_fx) >> 1) + g.c0_off_fx;
-    const long long C = C0 + (long long)tlo * g.slope_fx;
+    const float c0f = fmaf(0.5f * (float)B2, g.inv_drive, g.c0_off);
+    int tlo, thi;
+    walk_range(C0, g.slope_fx, N, c0f, g.inv_slope, tlo, thi);
+    if (thi < tlo) return 0.f;
+    const long long S32 = (long long)P.S << 32;
+    const long long D = C0 + (long long)tlo * g.slope_fx + (long long)tlo * S32 + ((long long)kPad << 32);
     const float2* V = g.col_driven ? P.view_cm : P.view_rm;
-    return walk_ray_f32(V, P.S, tlo, thi, C, g.slope_fx, g.k2, g.h2,
-                        (unsigned)(N + 2 * kPad - 2)) * g.inv_m;
+    return walk_ray_f32(V, thi - tlo + 1, D, g.slope_fx + S32, g.k2, g.h2p) * g.inv_m;
 }
 
 template <>
@@ -208,10 +224,9 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
 template <typename T>
-struct BpRow {
+struct __align__(16) BpRow {   // read with two 16-byte shared loads (FP32)
     T c, s, kb, hb0, hb1, inv_m, frac;
     int rel;       // band index of floor(projection of the tile origin)
-    int s_lo;      // first slot of the band in the sinogram row
 };
 
 // Tile origin projection (integer part and fraction) for one angle.
@@ -247,6 +262,7 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
     const Prob<T>& P = probs[it.prob];
     if (P.st->done) return;
     __shared__ BpRow<T> rows[2][kBpChunk];
+    __shared__ int slo[2][kBpChunk];            // first slot of each band in its sinogram row
     __shared__ __align__(16) T2 band[2][NRHS][kBpChunk][kBand];
     const int N = P.n, na = P.na, nb = P.nb, SB = P.SB;
     const int ti0 = it.u * kTileH, tj0 = it.v * kTileW;
@@ -272,8 +288,8 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
             r.c = g.c; r.s = g.s; r.kb = g.kb; r.hb0 = g.hb0; r.hb1 = g.hb1; r.inv_m = g.inv_m;
             r.frac = F;
             r.rel = I + kSPad - s_lo;
-            r.s_lo = s_lo;
             rows[ch & 1][q] = r;
+            slo[ch & 1][q] = s_lo;
         }
     };
     auto stage_copy = [&](int ch) {
@@ -283,7 +299,7 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
             const int h = sg / (cnt * kSegs);
             const int rem = sg - h * cnt * kSegs;
             const int q = rem / kSegs, k = rem - q * kSegs;
-            const int slot = rows[ch & 1][q].s_lo + k * kSlotsPerSeg;
+            const int slot = slo[ch & 1][q] + k * kSlotsPerSeg;
             const T2* row = R[h] + (size_t)(a0 + q) * SB;
             const bool ok = slot >= 0 && slot + kSlotsPerSeg <= SB;
             cp_async16(&band[ch & 1][h][q][k * kSlotsPerSeg], ok ? row + slot : row, ok ? 16 : 0);

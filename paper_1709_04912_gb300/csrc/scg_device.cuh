@@ -64,6 +64,7 @@ struct Angle {
     T c, s;        // cos, sin (exact 0/1 at theta = 0, pi/2)
     T inv_m;       // 1/m
     T k2, h2;      // forward weights
+    T h2p;         // h2 + k2 (weight from a fraction f1 = f + 1 in [1, 2))
     T kb, hb0;     // gather weights
     T hb1;
     T slope;       // change of the crossing per step along the driving axis

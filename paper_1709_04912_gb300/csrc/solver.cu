@@ -134,10 +134,10 @@ void fill_angles(std::vector<Angle<T>>& out, int na, int n) {
         g.s = (T)s;
         g.inv_m = (T)(1.0 / m);
         if (mn == 0.0) {
-            g.k2 = (T)1.0; g.h2 = (T)1.0;
+            g.k2 = (T)1.0; g.h2 = (T)1.0; g.h2p = (T)2.0;
             g.kb = (T)1.0; g.hb0 = (T)1.0; g.hb1 = (T)0.0;
         } else {
-            g.k2 = (T)(m / mn); g.h2 = (T)(hs / mn);
+            g.k2 = (T)(m / mn); g.h2 = (T)(hs / mn); g.h2p = (T)(hs / mn + m / mn);
             g.kb = (T)(1.0 / mn); g.hb0 = (T)(hs / mn); g.hb1 = (T)((hs - 1.0) / mn);
         }
         g.col_driven = as >= ac ? 1 : 0;
@@ -323,10 +323,11 @@ void run_resume(Runner<T>& R, const Program& pg) {
 struct GraphKey {
     int dev;
     const void* work;
-    int prec, variant, trial_passes, ksteps, n, na, nb;
+    int prec, variant, trial_passes, ksteps, n, na, nb, host_loop;
     bool operator<(const GraphKey& o) const {
-        return std::tie(dev, work, prec, variant, trial_passes, ksteps, n, na, nb) <
-               std::tie(o.dev, o.work, o.prec, o.variant, o.trial_passes, o.ksteps, o.n, o.na, o.nb);
+        return std::tie(dev, work, prec, variant, trial_passes, ksteps, n, na, nb, host_loop) <
+               std::tie(o.dev, o.work, o.prec, o.variant, o.trial_passes, o.ksteps, o.n, o.na, o.nb,
+                        o.host_loop);
     }
 };
 
@@ -444,7 +445,8 @@ int solve_impl(const scg_geometry* g, int variant, int precision, const scg_para
     // conditional WHILE node whose condition a one-thread kernel sets on the
     // device after every body (no host round trip per iteration).  Fallback:
     // one graph per body, launched in batches and polled one batch ahead.
-    GraphKey key{dev, work, precision, variant, pg.trial_passes, pg.ksteps, g->n, g->n_angles, g->n_bins};
+    GraphKey key{dev, work, precision, variant, pg.trial_passes, pg.ksteps, g->n, g->n_angles, g->n_bins,
+                 prm->host_loop ? 1 : 0};
     BodyGraph bg{nullptr, 0, false};
     {
         std::lock_guard<std::mutex> lk(g_mu);
@@ -460,7 +462,7 @@ int solve_impl(const scg_geometry* g, int variant, int precision, const scg_para
         RC.launches = 0;
         // device loop
         cudaGraph_t g0 = nullptr;
-        bool ok = cudaGraphCreate(&g0, 0) == cudaSuccess;
+        bool ok = !prm->host_loop && cudaGraphCreate(&g0, 0) == cudaSuccess;
         cudaGraphConditionalHandle h = 0;
         if (ok) ok = cudaGraphConditionalHandleCreate(&h, g0, 1, cudaGraphCondAssignDefault) == cudaSuccess;
         cudaGraph_t tmp = nullptr;
@@ -753,6 +755,7 @@ void scg_default_params(scg_params* p) {
     p->mu = 0.0;
     p->filter_gain = 1.0;
     p->max_iter = 100;
+    p->host_loop = 0;
 }
 
 size_t scg_op_workspace_bytes(const scg_geometry* g, int precision) {
@@ -822,6 +825,7 @@ int scg_solve(const scg_geometry* g, int variant, int precision, const scg_param
         !(prm->a > 0.0 && prm->a < 1.0) || !(prm->filter_gain > 0.0))
         return SCG_ERR_INVALID;
     if (prm->perturb != SCG_PERTURB_NONE && prm->perturb != SCG_PERTURB_GAMMA) return SCG_ERR_INVALID;
+    if (prm->host_loop != 0 && prm->host_loop != 1) return SCG_ERR_INVALID;
     if (resume && resume->valid != 1) return SCG_ERR_INVALID;
     if (!valid_prec(precision)) return SCG_ERR_UNSUPPORTED;
     memset(res, 0, sizeof(*res));

@@ -36,7 +36,7 @@ class Params(ctypes.Structure):
                 ("gamma0_rel", ctypes.c_double), ("a", ctypes.c_double),
                 ("max_trials", ctypes.c_int), ("K", ctypes.c_int), ("k_inclusive", ctypes.c_int),
                 ("mu", ctypes.c_double), ("filter_gain", ctypes.c_double),
-                ("max_iter", ctypes.c_int)]
+                ("max_iter", ctypes.c_int), ("host_loop", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -232,7 +232,7 @@ def default_params(**kw) -> dict:
 def _params(d: dict) -> Params:
     return Params(PERTURB[d["perturb"]], float(d["gamma0"]), float(d["gamma0_rel"]), float(d["a"]),
                   int(d["max_trials"]), int(d["K"]), int(d["k_inclusive"]), float(d["mu"]),
-                  float(d["filter_gain"]), int(d["max_iter"]))
+                  float(d["filter_gain"]), int(d["max_iter"]), int(d["host_loop"]))
 
 
 @dataclass

@@ -188,3 +188,15 @@ def test_full_size_single_solve_properties():
     assert s.tv_final < c.tv_final
     acc = s.trace[:, 5] == 1
     assert np.all(s.trace[acc, 3] <= s.trace[acc, 2])
+
+
+@pytest.mark.parametrize("variant", ["S-CG", "CG", "S-PCG-K"])
+def test_device_loop_and_host_loop_agree(small, variant):
+    # the same kernels driven by the conditional-graph loop and by host-polled
+    # per-body graphs give bit-identical results
+    kw = kw_for(variant, small)
+    d = gpu_solve(small, torch.float32, host_loop=0, **kw)
+    h = gpu_solve(small, torch.float32, host_loop=1, **kw)
+    assert d.device_loop == 1 and h.device_loop == 0
+    assert d.iters == h.iters and d.status == h.status
+    assert torch.equal(d.x, h.x)
