@@ -16,6 +16,8 @@
 //   k_taps         the taps, in FP64
 //   k_sino_pairs   a caller's plain sinogram into the pair layout
 // No kernel uses atomics on data; reductions are deterministic.
+#include <type_traits>
+
 #include "scg_kernels.h"
 
 namespace scg {
@@ -175,7 +177,7 @@ __device__ __forceinline__ double project_ray<double>(const Prob<double>& P, con
 // image almost together, so the warps of a block read nearly the same view
 // spans and most of those reads hit L1.
 template <typename T>
-__global__ void __launch_bounds__(kProjThreads)
+__global__ void __launch_bounds__(kProjThreads, 5)
 k_project(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int dst_sel,
           int mode, int step) {
     const Item it = decode_item(probs, items, 3);
@@ -223,30 +225,23 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-template <typename T>
-struct __align__(16) BpRow {   // read with two 16-byte shared loads (FP32)
-    T c, s, kb, hb0, hb1, inv_m, frac;
-    int rel;       // band index of floor(projection of the tile origin)
+// Per-angle row of the FP32 gather (two 16-byte shared loads).
+struct __align__(16) BpRowF {
+    int base;        // band index of the tile origin's projection, in 8.24 fixed point
+    int c24, s24;    // cos, sin in 8.24
+    float kb, hb0p, hb1p, inv_m;
+    int pad_;
+};
+// Per-angle row of the FP64 gather.
+struct __align__(16) BpRowD {
+    double c, s, kb, hb0, hb1, inv_m, frac;
+    int rel;
 };
 
-// Tile origin projection (integer part and fraction) for one angle.
-template <typename T>
-__device__ __forceinline__ void tile_origin(const Angle<T>& g, int X2, int Y2, int nb, int& I, T& F);
-template <>
-__device__ __forceinline__ void tile_origin<float>(const Angle<float>& g, int X2, int Y2, int nb, int& I,
-                                                   float& F) {
-    // off_b + xc0 c + yc0 s with xc0 = X2/2, yc0 = Y2/2, in 32.32 fixed point
-    const long long cb = ((long long)(nb - 1) << 31) + (((long long)X2 * g.c_fx + (long long)Y2 * g.s_fx) >> 1);
-    I = (int)(cb >> 32);
-    F = __int_as_float(0x3F800000 | ((unsigned)cb >> 9)) - 1.0f;
-}
-template <>
-__device__ __forceinline__ void tile_origin<double>(const Angle<double>& g, int X2, int Y2, int nb, int& I,
-                                                    double& F) {
-    const double cb = 0.5 * (double)(nb - 1) + 0.5 * (double)X2 * g.c_d + 0.5 * (double)Y2 * g.s_d;
-    const double fl = floor(cb);
-    I = (int)fl;
-    F = cb - fl;
+// Tile origin projection (integer part I and fraction) for one angle:
+// off_b + xc0 c + yc0 s with xc0 = X2/2, yc0 = Y2/2, in 32.32 fixed point.
+__device__ __forceinline__ long long tile_origin_fx(const Angle<float>& g, int X2, int Y2, int nb) {
+    return ((long long)(nb - 1) << 31) + (((long long)X2 * g.c_fx + (long long)Y2 * g.s_fx) >> 1);
 }
 
 template <typename T, int NRHS>
@@ -254,6 +249,8 @@ __global__ void __launch_bounds__(kBackThreads)
 k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int src0,
               int src1, int dst0, int dst1, int step) {
     using T2 = typename Vec2<T>::type;
+    using Row = typename std::conditional<std::is_same<T, float>::value, BpRowF, BpRowD>::type;
+    constexpr bool kF32 = std::is_same<T, float>::value;
     constexpr int kSlotsPerSeg = 16 / (int)sizeof(T2);
     constexpr int kSegs = kBand / kSlotsPerSeg;       // 16-byte copies per band
     constexpr int kHalf = kTileH / 2;
@@ -261,7 +258,7 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
     const Item it = decode_item(probs, items, 1);
     const Prob<T>& P = probs[it.prob];
     if (P.st->done) return;
-    __shared__ BpRow<T> rows[2][kBpChunk];
+    __shared__ Row rows[2][kBpChunk];
     __shared__ int slo[2][kBpChunk];            // first slot of each band in its sinogram row
     __shared__ __align__(16) T2 band[2][NRHS][kBpChunk][kBand];
     const int N = P.n, na = P.na, nb = P.nb, SB = P.SB;
@@ -269,7 +266,6 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
     const int tx = threadIdx.x % kTileW, ty = threadIdx.x / kTileW;
     const int i1 = ti0 + ty, i2 = ti0 + ty + kHalf, j = tj0 + tx;
     const bool in1 = (i1 < N) && (j < N), in2 = (i2 < N) && (j < N);
-    const T dj = T(tx), di1 = T(ty), di2 = T(ty + kHalf);
     const int X2 = 2 * tj0 - (N - 1), Y2 = 2 * ti0 - (N - 1);
     const T2* R[2] = {P.sino[src0], NRHS == 2 ? P.sino[src1] : P.sino[src0]};
     const int nchunks = (na + kBpChunk - 1) / kBpChunk;
@@ -279,30 +275,47 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
         const int a = ch * kBpChunk + q;
         if (q < kBpChunk && a < na) {
             const Angle<T> g = P.ang[a];
-            int I;
-            T F;
-            tile_origin<T>(g, X2, Y2, nb, I, F);
+            // band: slots the tile can touch, from floor(projection of the origin)
+            // + floor((kTileW-1) min(c, 0)) - 1, rounded down to a 16-byte boundary
             const int lo = (int)tfloor(T(kTileW - 1) * tmin(g.c, T(0))) - 1;
-            const int s_lo = (I + kSPad + lo) & ~(kSlotsPerSeg - 1);
-            BpRow<T> r;
-            r.c = g.c; r.s = g.s; r.kb = g.kb; r.hb0 = g.hb0; r.hb1 = g.hb1; r.inv_m = g.inv_m;
-            r.frac = F;
-            r.rel = I + kSPad - s_lo;
-            rows[ch & 1][q] = r;
-            slo[ch & 1][q] = s_lo;
+            if constexpr (kF32) {
+                const long long cb = tile_origin_fx(g, X2, Y2, nb);
+                const int I = (int)(cb >> 32);
+                const int s_lo = (I + kSPad + lo) & ~(kSlotsPerSeg - 1);
+                BpRowF r;
+                // 8.24: integer part = band index of floor(cb), fraction = cb's
+                r.base = ((I + kSPad - s_lo) << 24) | (int)((unsigned)cb >> 8);
+                r.c24 = g.c24; r.s24 = g.s24;
+                r.kb = g.kb; r.hb0p = g.hb0p; r.hb1p = g.hb1p; r.inv_m = g.inv_m;
+                r.pad_ = 0;
+                rows[ch & 1][q] = r;
+                slo[ch & 1][q] = s_lo;
+            } else {
+                const double cbt = 0.5 * (double)(nb - 1) + 0.5 * (double)X2 * g.c_d + 0.5 * (double)Y2 * g.s_d;
+                const double fl = floor(cbt);
+                const int I = (int)fl;
+                const int s_lo = (I + kSPad + lo) & ~(kSlotsPerSeg - 1);
+                BpRowD r;
+                r.c = g.c; r.s = g.s; r.kb = g.kb; r.hb0 = g.hb0; r.hb1 = g.hb1; r.inv_m = g.inv_m;
+                r.frac = cbt - fl;
+                r.rel = I + kSPad - s_lo;
+                rows[ch & 1][q] = r;
+                slo[ch & 1][q] = s_lo;
+            }
         }
     };
     auto stage_copy = [&](int ch) {
         const int a0 = ch * kBpChunk;
         const int cnt = min(kBpChunk, na - a0);
-        for (int sg = threadIdx.x; sg < NRHS * cnt * kSegs; sg += blockDim.x) {
-            const int h = sg / (cnt * kSegs);
-            const int rem = sg - h * cnt * kSegs;
-            const int q = rem / kSegs, k = rem - q * kSegs;
-            const int slot = slo[ch & 1][q] + k * kSlotsPerSeg;
-            const T2* row = R[h] + (size_t)(a0 + q) * SB;
-            const bool ok = slot >= 0 && slot + kSlotsPerSeg <= SB;
-            cp_async16(&band[ch & 1][h][q][k * kSlotsPerSeg], ok ? row + slot : row, ok ? 16 : 0);
+#pragma unroll
+        for (int h = 0; h < NRHS; ++h) {
+            for (int sg = threadIdx.x; sg < cnt * kSegs; sg += blockDim.x) {
+                const int q = sg / kSegs, k = sg - q * kSegs;
+                const int slot = slo[ch & 1][q] + k * kSlotsPerSeg;
+                const T2* row = R[h] + (size_t)(a0 + q) * SB;
+                const bool ok = slot >= 0 && slot + kSlotsPerSeg <= SB;
+                cp_async16(&band[ch & 1][h][q][k * kSlotsPerSeg], ok ? row + slot : row, ok ? 16 : 0);
+            }
         }
         cp_async_commit();
     };
@@ -321,28 +334,55 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
         const int cnt = min(kBpChunk, na - ch * kBpChunk);
         const int buf = ch & 1;
         if (in1) {
+            if constexpr (kF32) {
 #pragma unroll 4
-            for (int q = 0; q < cnt; ++q) {
-                const BpRow<T>& g = rows[buf][q];
-                const T djc = dj * g.c;
-                const T v1 = g.frac + fma(di1, g.s, djc);
-                const T v2 = g.frac + fma(di2, g.s, djc);
-                int q1, q2;
-                const T f1 = v1 - floor_split(v1, q1);
-                const T f2 = v2 - floor_split(v2, q2);
-                const unsigned k1 = min((unsigned)(q1 + g.rel), (unsigned)(kBand - 2));
-                const unsigned k2 = min((unsigned)(q2 + g.rel), (unsigned)(kBand - 2));
-                const T w10 = sat(fma(-f1, g.kb, g.hb0)), w11 = sat(fma(f1, g.kb, g.hb1));
-                const T w20 = sat(fma(-f2, g.kb, g.hb0)), w21 = sat(fma(f2, g.kb, g.hb1));
-                const T2 e1 = band[buf][0][q][k1];
-                const T2 e2 = band[buf][0][q][k2];
-                a1 = fma(g.inv_m, fma(w10, e1.x, w11 * e1.y), a1);
-                a2 = fma(g.inv_m, fma(w20, e2.x, w21 * e2.y), a2);
-                if (NRHS == 2) {
-                    const T2 z1 = band[buf][NRHS - 1][q][k1];
-                    const T2 z2 = band[buf][NRHS - 1][q][k2];
-                    b1 = fma(g.inv_m, fma(w10, z1.x, w11 * z1.y), b1);
-                    b2 = fma(g.inv_m, fma(w20, z2.x, w21 * z2.y), b2);
+                for (int q = 0; q < cnt; ++q) {
+                    const BpRowF g = rows[buf][q];
+                    // 8.24 position of both pixels in band coordinates (always > 0)
+                    const int p1 = g.base + tx * g.c24 + ty * g.s24;
+                    const int p2 = p1 + kHalf * g.s24;
+                    // 1 + fraction as a float in [1, 2)
+                    const float f1 = __int_as_float(0x3F800000 | (((unsigned)p1 & 0xFFFFFFu) >> 1));
+                    const float f2 = __int_as_float(0x3F800000 | (((unsigned)p2 & 0xFFFFFFu) >> 1));
+                    const float w10 = __saturatef(fmaf(-f1, g.kb, g.hb0p)), w11 = __saturatef(fmaf(f1, g.kb, g.hb1p));
+                    const float w20 = __saturatef(fmaf(-f2, g.kb, g.hb0p)), w21 = __saturatef(fmaf(f2, g.kb, g.hb1p));
+                    const float2* bq = reinterpret_cast<const float2*>(&band[buf][0][q][0]);
+                    const float2 e1 = bq[p1 >> 24];
+                    const float2 e2 = bq[p2 >> 24];
+                    a1 = fmaf(g.inv_m, fmaf(w10, e1.x, w11 * e1.y), a1);
+                    a2 = fmaf(g.inv_m, fmaf(w20, e2.x, w21 * e2.y), a2);
+                    if (NRHS == 2) {
+                        const float2* zq = reinterpret_cast<const float2*>(&band[buf][NRHS - 1][q][0]);
+                        const float2 z1 = zq[p1 >> 24];
+                        const float2 z2 = zq[p2 >> 24];
+                        b1 = fmaf(g.inv_m, fmaf(w10, z1.x, w11 * z1.y), b1);
+                        b2 = fmaf(g.inv_m, fmaf(w20, z2.x, w21 * z2.y), b2);
+                    }
+                }
+            } else {
+                const T dj = T(tx), di1 = T(ty), di2 = T(ty + kHalf);
+                for (int q = 0; q < cnt; ++q) {
+                    const BpRowD& g = *reinterpret_cast<const BpRowD*>(&rows[buf][q]);
+                    const T djc = dj * g.c;
+                    const T v1 = g.frac + fma(di1, g.s, djc);
+                    const T v2 = g.frac + fma(di2, g.s, djc);
+                    int q1, q2;
+                    const T f1 = v1 - floor_split(v1, q1);
+                    const T f2 = v2 - floor_split(v2, q2);
+                    const unsigned k1 = min((unsigned)(q1 + g.rel), (unsigned)(kBand - 2));
+                    const unsigned k2 = min((unsigned)(q2 + g.rel), (unsigned)(kBand - 2));
+                    const T w10 = sat(fma(-f1, g.kb, g.hb0)), w11 = sat(fma(f1, g.kb, g.hb1));
+                    const T w20 = sat(fma(-f2, g.kb, g.hb0)), w21 = sat(fma(f2, g.kb, g.hb1));
+                    const T2 e1 = band[buf][0][q][k1];
+                    const T2 e2 = band[buf][0][q][k2];
+                    a1 = fma(g.inv_m, fma(w10, e1.x, w11 * e1.y), a1);
+                    a2 = fma(g.inv_m, fma(w20, e2.x, w21 * e2.y), a2);
+                    if (NRHS == 2) {
+                        const T2 z1 = band[buf][NRHS - 1][q][k1];
+                        const T2 z2 = band[buf][NRHS - 1][q][k2];
+                        b1 = fma(g.inv_m, fma(w10, z1.x, w11 * z1.y), b1);
+                        b2 = fma(g.inv_m, fma(w20, z2.x, w21 * z2.y), b2);
+                    }
                 }
             }
         }

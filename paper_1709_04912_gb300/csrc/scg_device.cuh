@@ -75,6 +75,8 @@ struct Angle {
     double c_d, s_d;          // FP64 copies (FP64 kernels)
     double inv_d, c0_off_d, slope_d;
     long long c_fx, s_fx;     // 32.32 fixed point (FP32 kernels)
+    int c24, s24;             // cos, sin in 8.24 fixed point (in-tile offsets of the gather)
+    T hb0p, hb1p;             // hb0 + kb, hb1 - kb (gather weights from g1 = g + 1 in [1, 2))
     long long inv_fx, c0_off_fx, slope_fx;
 };
 
