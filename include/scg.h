@@ -175,6 +175,22 @@ int scg_backproject(const scg_geometry* g, int precision, const void* r, void* x
 int scg_tv(int n, int precision, const void* x, double* tv_out,
            void* work, size_t work_bytes, void* stream);
 
+/* *tv_out (device double) = TV(x), exactly as scg_tv computes it, but with no
+ * workspace argument: for callers that cannot allocate device memory (a
+ * plug-in inside a host program whose memory pool owns the device, a real-time
+ * loop that forbids allocator calls, a fixed memory budget set at start-up).
+ * The paper has no counterpart; this is an interface convenience.
+ * Scratch lives in one array of about 1 MiB that the library defines in device
+ * memory; every GPU that loads the library holds it until the process exits.
+ * Limits and behaviour:
+ *   n must be 2 .. 1024 (larger n returns SCG_ERR_UNSUPPORTED);
+ *   allocates nothing (no cudaMalloc/cudaFree, no allocating library call);
+ *   the first call on a device looks up the array's device address with that
+ *   device current -- make that first call before any stream capture;
+ *   all calls share the array: calls that may overlap on the GPU (e.g. from
+ *   two streams at once) race and give undefined results. */
+int scg_tv_static(int n, int precision, const void* x, double* tv_out, void* stream);
+
 /* grad = a subgradient of TV at x (terms with zero norm contribute 0) and
  * *tv_out = TV(x); the nonascending direction of the perturbation step is
  * -grad/||grad|| (Sec. 1, Eq. superiorization). */
