@@ -186,14 +186,15 @@ k_project(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int
     const int nb = P.nb;
     const int a = it.u * kProjAngles + threadIdx.x / kProjRays;
     const int b = it.v * kProjRays + threadIdx.x % kProjRays;
-    double v[1] = {0.0};
+    Acc<T> v[1];
+    acc_zero(v[0]);
     if (a < P.na && b < nb) {
         const Angle<T> g = P.ang[a];
         T out = project_ray<T>(P, g, b);
         if (mode == PROJ_RESIDUAL) out = out - P.y[(size_t)a * nb + b];
         if (mode == PROJ_PLAIN_OUT) P.user_out[(size_t)a * nb + b] = out;
         else store_pair<T>(P.sino[dst_sel] + (size_t)a * P.SB + kSPad, b, out);
-        v[0] = (double)out * (double)out;
+        v[0] = acc_prod(out, out);
     }
     if (step != FIN_NONE) reduce_and_finalize<T, 1>(v, P, it.local, P.cnt_proj, step);
 }
@@ -398,23 +399,23 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
         if (NRHS == 2) P.img[dst1][idx2] = b2;
     }
     if (step == FIN_NONE) return;
-    double v[3] = {0.0, 0.0, 0.0};
+    Acc<T> v[3];
+    acc_zero(v[0]); acc_zero(v[1]); acc_zero(v[2]);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const bool in = h ? in2 : in1;
         if (!in) continue;
         const size_t idx = h ? idx2 : idx1;
-        const double g0 = (double)(h ? a2 : a1), g1 = (double)(h ? b2 : b1);
+        const T g0 = h ? a2 : a1, g1 = h ? b2 : b1;
         if (step == FIN_BETA) {
-            const double hh = (double)P.img[IB_H][idx];
-            v[0] += (NRHS == 2 ? g1 : g0) * hh;      // g'^T h  (z'^T h)
-            v[1] += g0 * g0;                         // ||g'||^2
-            v[2] += g0 * (double)P.img[IB_P][idx];   // g'^T p
+            v[0] = acc_add(v[0], acc_prod(NRHS == 2 ? g1 : g0, P.img[IB_H][idx]));  // g'^T h (z'^T h)
+            v[1] = acc_add(v[1], acc_prod(g0, g0));                                 // ||g'||^2
+            v[2] = acc_add(v[2], acc_prod(g0, P.img[IB_P][idx]));                   // g'^T p
         } else if (step == FIN_ALPHA || step == FIN_CG_ALPHA) {
-            v[0] += (double)P.img[IB_P][idx] * g0;   // p^T h
+            v[0] = acc_add(v[0], acc_prod(P.img[IB_P][idx], g0));                   // p^T h
         } else if (step == FIN_CG_DELTA) {
-            v[0] += g0 * g0;                         // ||g||^2
-            v[1] += g0 * g1;                         // g^T z
+            v[0] = acc_add(v[0], acc_prod(g0, g0));                                 // ||g||^2
+            v[1] = acc_add(v[1], acc_prod(g0, g1));                                 // g^T z
         }
     }
     reduce_and_finalize<T, 3>(v, P, it.local, P.cnt_img, step);
@@ -450,7 +451,9 @@ k_vec(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int op,
     const int j = it.v * kTileW + threadIdx.x % kTileW;
     const bool in = (i < N) && (j < N);
     const size_t idx = (size_t)i * N + j;
-    double v[2] = {0.0, 0.0};
+    Acc<T> v[2];
+    acc_zero(v[0]);
+    acc_zero(v[1]);
     T val = T(0);
     switch (op) {
     case VEC_INIT: {            // X = XH = x0 (AUX, or zeros), views of X
@@ -484,7 +487,7 @@ k_vec(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int op,
             const T d = P.img[sel][idx];
             val = fma(beta, P.img[IB_P][idx], -d);
             P.img[IB_P][idx] = val;
-            v[0] = (double)P.img[IB_G][idx] * (double)val;
+            v[0] = acc_prod(P.img[IB_G][idx], val);
         }
         write_views(P, it.u, it.v, val, in);
         break;
@@ -493,7 +496,7 @@ k_vec(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int op,
         if (in) {
             val = -P.img[sel][idx];
             P.img[IB_P][idx] = val;
-            v[0] = (double)P.img[IB_G][idx] * (double)val;
+            v[0] = acc_prod(P.img[IB_G][idx], val);
         }
         write_views(P, it.u, it.v, val, in);
         break;
@@ -504,7 +507,7 @@ k_vec(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int op,
             const T d = P.img[sel][idx];
             val = fma(beta, P.img[IB_P][idx], -d);
             P.img[IB_P][idx] = val;
-            v[0] = (double)P.img[IB_G][idx] * (double)val;
+            v[0] = acc_prod(P.img[IB_G][idx], val);
         }
         break;
     }
@@ -515,16 +518,16 @@ k_vec(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int op,
             P.img[IB_X][idx] = fma(alpha, P.img[IB_P][idx], base);
             const T gn = fma(alpha, P.img[IB_H][idx], P.img[IB_G][idx]);
             P.img[IB_G][idx] = gn;
-            v[0] = (double)gn * (double)gn;
-            if (P.img[IB_Z]) v[1] = (double)gn * (double)P.img[IB_Z][idx];
+            v[0] = acc_prod(gn, gn);
+            if (P.img[IB_Z]) v[1] = acc_prod(gn, P.img[IB_Z][idx]);
         }
         break;
     }
     case VEC_DOTS_RESUME: {     // S0 = p^T h, S1 = g^T p
         if (in) {
-            const double p = (double)P.img[IB_P][idx];
-            if (P.img[IB_H]) v[0] = p * (double)P.img[IB_H][idx];
-            if (P.img[IB_G]) v[1] = p * (double)P.img[IB_G][idx];
+            const T p = P.img[IB_P][idx];
+            if (P.img[IB_H]) v[0] = acc_prod(p, P.img[IB_H][idx]);
+            if (P.img[IB_G]) v[1] = acc_prod(p, P.img[IB_G][idx]);
         }
         break;
     }
@@ -571,7 +574,6 @@ k_tvgrad(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int 
     __syncthreads();
     const int ty = threadIdx.x / kTileW, tx = threadIdx.x % kTileW;
     // terms for smem rows 0..kTileH (global i0..i0+kTileH), cols 0..kTileW
-    double tvsum = 0.0;
     for (int q = threadIdx.x; q < (kTileH + 1) * (kTileW + 1); q += kTileThreads) {
         const int ii = q / (kTileW + 1), jj = q % (kTileW + 1);
         const int gi = i0 + ii, gj = j0 + jj;
@@ -588,20 +590,20 @@ k_tvgrad(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int 
     __syncthreads();
     const int i = i0 + 1 + ty, j = j0 + 1 + tx;
     const bool in = (i < N) && (j < N);
-    double v[3] = {0.0, 0.0, 0.0};
+    Acc<T> v[3];
+    acc_zero(v[0]); acc_zero(v[1]); acc_zero(v[2]);
     if (in) {
         const size_t g = (size_t)i * N + j;
         const T x = xs[ty + 1][tx + 1];
         if (fuse_update) P.img[IB_X][g] = x;
         if (i < N - 1 && j < N - 1) {         // this tile's own term (i, j)
             const T du = xs[ty + 2][tx + 1] - x, dv = xs[ty + 1][tx + 2] - x;
-            tvsum = (double)tsqrt(du * du + dv * dv);
+            v[0] = acc_val(tsqrt(du * du + dv * dv));
         }
         const T gr = -(tu[ty + 1][tx + 1] + tv[ty + 1][tx + 1]) + tu[ty][tx + 1] + tv[ty + 1][tx];
         if (write_grad) P.img[IB_TVG][g] = gr;
-        v[0] = tvsum;
-        v[1] = (double)gr * (double)gr;
-        v[2] = (double)x * (double)x;
+        v[1] = acc_prod(gr, gr);
+        v[2] = acc_prod(x, x);
     }
     if (step != FIN_NONE) reduce_and_finalize<T, 3>(v, P, it.local, P.cnt_img, step);
 }
@@ -614,17 +616,18 @@ k_tvgrad(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int 
 template <typename T>
 __global__ void __launch_bounds__(kTileThreads)
 k_trial(const Prob<T>* __restrict__ probs, const Item* __restrict__ items) {
+    using A = Acc<T>;
     constexpr int NS = kTrials + 1;                 // 31 candidates + x itself
     constexpr int NW = kTileThreads / 32;
     const Item it = decode_item(probs, items, 1);
     const Prob<T>& P = probs[it.prob];
     const DevState& st = *P.st;
     if (st.done || st.accepted != 0) return;
-    __shared__ double wsum[NW][NS];
-    __shared__ double coef_s[kTrials];
+    __shared__ A wsum[NW][NS];
+    __shared__ T coef_s[kTrials];
     __shared__ unsigned s_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x < kTrials) coef_s[threadIdx.x] = st.trial_coef[threadIdx.x];
+    if (threadIdx.x < kTrials) coef_s[threadIdx.x] = (T)st.trial_coef[threadIdx.x];
     __syncthreads();
     const int N = P.n;
     const int i = it.u * kTileH + threadIdx.x / kTileW;
@@ -640,24 +643,24 @@ k_trial(const Prob<T>* __restrict__ probs, const Item* __restrict__ items) {
     }
 #pragma unroll
     for (int grp = 0; grp < NS / 8; ++grp) {
-        double v[8];
+        A v[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const int t = grp * 8 + k;
             T du, dv;
             if (t < kTrials) {
-                const T c = (T)coef_s[t];
+                const T c = coef_s[t];
                 const T z0 = fma_rn(c, q0, x0), zu = fma_rn(c, qu, xu), zv = fma_rn(c, qv, xv);
                 du = zu - z0; dv = zv - z0;
             } else {
                 du = xu - x0; dv = xv - x0;
             }
-            v[k] = in ? (double)tsqrt(du * du + dv * dv) : 0.0;
+            v[k] = acc_val(in ? tsqrt(du * du + dv * dv) : T(0));
         }
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+            for (int o = 16; o > 0; o >>= 1) v[k] = acc_add(v[k], acc_shfl_down(v[k], o));
         }
         if (lane == 0) {
 #pragma unroll
@@ -665,10 +668,11 @@ k_trial(const Prob<T>* __restrict__ probs, const Item* __restrict__ items) {
         }
     }
     __syncthreads();
+    A* parts = reinterpret_cast<A*>(P.partials);
     if (threadIdx.x < NS) {
-        double b = 0.0;
-        for (int w = 0; w < NW; ++w) b += wsum[w][threadIdx.x];
-        P.partials[(size_t)it.local * kSlots + threadIdx.x] = b;
+        A b = wsum[0][threadIdx.x];
+        for (int w = 1; w < NW; ++w) b = acc_add(b, wsum[w][threadIdx.x]);
+        parts[(size_t)it.local * kSlots + threadIdx.x] = b;
         __threadfence();
     }
     __syncthreads();
@@ -678,17 +682,29 @@ k_trial(const Prob<T>* __restrict__ probs, const Item* __restrict__ items) {
     __threadfence();
     // last block: slot = tid % NS, items tid / NS, tid / NS + NW, ... (fixed order)
     const int slot = threadIdx.x % NS, lane_grp = threadIdx.x / NS;
-    double acc = 0.0;
-    for (int q = lane_grp; q < P.cnt_img; q += NW) acc += __ldcg(P.partials + (size_t)q * kSlots + slot);
+    A acc;
+    acc_zero(acc);
+    for (int q = lane_grp; q < P.cnt_img; q += NW) {
+        const A* src = parts + (size_t)q * kSlots + slot;
+        A x;
+        if constexpr (std::is_same<A, double>::value) {
+            x = __ldcg(reinterpret_cast<const double*>(src));
+        } else {
+            const float2 w = __ldcg(reinterpret_cast<const float2*>(src));
+            x.hi = w.x;
+            x.lo = w.y;
+        }
+        acc = acc_add(acc, x);
+    }
     wsum[lane_grp][slot] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
         *P.counter = 0u;
         double S[NS];
         for (int t = 0; t < NS; ++t) {
-            double sum = 0.0;
-            for (int w = 0; w < NW; ++w) sum += wsum[w][t];
-            S[t] = sum;
+            A sum = wsum[0][t];
+            for (int w = 1; w < NW; ++w) sum = acc_add(sum, wsum[w][t]);
+            S[t] = acc_to_double(sum);
         }
         finalize<T>(FIN_TRIAL, P, S);
     }
@@ -704,14 +720,15 @@ k_sino_axpy(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, i
     const DevState& st = *P.st;
     if (st.done) return;
     const int a = it.u, b = it.v * kRayBlock + threadIdx.x;
-    double v[1] = {0.0};
+    Acc<T> v[1];
+    acc_zero(v[0]);
     if (b < P.nb) {
         const size_t o = (size_t)a * P.SB + kSPad;
         // reads the first half of slot b, writes it and the second half of
         // slot b-1: no other thread touches those words
         const T r = fma((T)st.alpha, P.sino[SB_Q][o + b].x, P.sino[SB_R][o + b].x);
         store_pair<T>(P.sino[SB_R] + o, b, r);
-        v[0] = (double)r * (double)r;
+        v[0] = acc_prod(r, r);
     }
     reduce_and_finalize<T, 1>(v, P, it.local, P.cnt_ray, step);
 }
@@ -781,7 +798,7 @@ __global__ void k_taps(T* taps, int nb, int P, double mu, double gain) {
     }
     __shared__ double red[32];
     double v[1] = {acc};
-    block_sum<1>(v, red);
+    block_sum<double, 1>(v, red);
     if (threadIdx.x == 0) {
         const T h = (T)(gain * v[0] / (double)P);
         taps[nb - 1 + k] = h;

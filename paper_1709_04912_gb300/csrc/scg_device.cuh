@@ -23,6 +23,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "scg.h"
 
 namespace scg {
@@ -199,13 +201,64 @@ __device__ __forceinline__ void store_pair(typename Vec2<T>::type* row, int b, T
 }
 
 // ---------------------------------------------------------------------------
-// Block reductions (FP64, fixed order).
-template <int NS>
-__device__ __forceinline__ void block_sum(double (&v)[NS], double* smem /* >= 32*NS */) {
+// Reductions.  FP64 arithmetic is slow on this GPU, so the FP32 kernels carry
+// their partial sums as double-float pairs (hi + lo, FP32 each): products are
+// split exactly with an FMA, and sums use the error-free TwoSum, which keeps
+// about 48 bits -- FP64-quality sums without FP64 instructions.  Only the
+// finalising thread converts to double.  The FP64 kernels use doubles.
+// Every sum runs in a fixed order, so results do not depend on scheduling.
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fsub_rn(s, a.hi);
+    const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    const float lo = __fadd_rn(err, __fadd_rn(a.lo, b.lo));
+    const float hi = __fadd_rn(s, lo);
+    DF r;
+    r.hi = hi;
+    r.lo = __fsub_rn(lo, __fsub_rn(hi, s));
+    return r;
+}
+
+template <typename T> struct AccOf;
+template <> struct AccOf<float> { using type = DF; };
+template <> struct AccOf<double> { using type = double; };
+template <typename T> using Acc = typename AccOf<T>::type;
+
+__device__ __forceinline__ void acc_zero(DF& a) { a.hi = 0.f; a.lo = 0.f; }
+__device__ __forceinline__ void acc_zero(double& a) { a = 0.0; }
+// exact product of two FP32 values as a pair
+__device__ __forceinline__ DF acc_prod(float a, float b) {
+    DF r;
+    r.hi = __fmul_rn(a, b);
+    r.lo = __fmaf_rn(a, b, -r.hi);
+    return r;
+}
+__device__ __forceinline__ double acc_prod(double a, double b) { return a * b; }
+__device__ __forceinline__ DF acc_val(float a) { DF r; r.hi = a; r.lo = 0.f; return r; }
+__device__ __forceinline__ double acc_val(double a) { return a; }
+__device__ __forceinline__ DF acc_add(DF a, DF b) { return df_add(a, b); }
+__device__ __forceinline__ double acc_add(double a, double b) { return a + b; }
+__device__ __forceinline__ DF acc_shfl_down(DF a, int o) {
+    DF r;
+    r.hi = __shfl_down_sync(0xffffffffu, a.hi, o);
+    r.lo = __shfl_down_sync(0xffffffffu, a.lo, o);
+    return r;
+}
+__device__ __forceinline__ double acc_shfl_down(double a, int o) { return __shfl_down_sync(0xffffffffu, a, o); }
+__device__ __forceinline__ double acc_to_double(DF a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ double acc_to_double(double a) { return a; }
+
+// Block sum of NS accumulators; the result is valid in thread 0.
+template <typename A, int NS>
+__device__ __forceinline__ void block_sum(A (&v)[NS], A* smem /* >= 32*NS */) {
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+        for (int o = 16; o > 0; o >>= 1) v[k] = acc_add(v[k], acc_shfl_down(v[k], o));
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = (blockDim.x + 31) >> 5;
@@ -217,11 +270,14 @@ __device__ __forceinline__ void block_sum(double (&v)[NS], double* smem /* >= 32
     __syncthreads();
     if (warp == 0) {
 #pragma unroll
-        for (int k = 0; k < NS; ++k) v[k] = (lane < nwarps) ? smem[lane * NS + k] : 0.0;
+        for (int k = 0; k < NS; ++k) {
+            if (lane < nwarps) v[k] = smem[lane * NS + k];
+            else acc_zero(v[k]);
+        }
 #pragma unroll
         for (int k = 0; k < NS; ++k) {
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+            for (int o = 16; o > 0; o >>= 1) v[k] = acc_add(v[k], acc_shfl_down(v[k], o));
         }
     }
 }
@@ -231,14 +287,17 @@ template <typename T> __device__ void finalize(int step, const Prob<T>& P, const
 // Publish this item's partial sums; the block that completes the problem's
 // last item sums all partials in item order and runs the step's finaliser.
 // Must be called by every thread of the block (uniform control flow).
+// Partials are stored as the accumulator type (8 bytes either way).
 template <typename T, int NS>
-__device__ void reduce_and_finalize(double (&v)[NS], const Prob<T>& P, int local, int total,
+__device__ void reduce_and_finalize(Acc<T> (&v)[NS], const Prob<T>& P, int local, int total,
                                     int step) {
-    __shared__ double red[32 * NS];
+    using A = Acc<T>;
+    __shared__ A red[32 * NS];
     __shared__ unsigned s_last;
-    block_sum<NS>(v, red);
+    block_sum<A, NS>(v, red);
+    A* parts = reinterpret_cast<A*>(P.partials);
     if (threadIdx.x == 0) {
-        double* dst = P.partials + (size_t)local * kSlots;
+        A* dst = parts + (size_t)local * kSlots;
 #pragma unroll
         for (int k = 0; k < NS; ++k) dst[k] = v[k];
         __threadfence();
@@ -248,20 +307,30 @@ __device__ void reduce_and_finalize(double (&v)[NS], const Prob<T>& P, int local
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    double acc[NS];
+    A acc[NS];
 #pragma unroll
-    for (int k = 0; k < NS; ++k) acc[k] = 0.0;
+    for (int k = 0; k < NS; ++k) acc_zero(acc[k]);
     for (int it = threadIdx.x; it < total; it += blockDim.x) {
-        const double* src = P.partials + (size_t)it * kSlots;
+        const A* src = parts + (size_t)it * kSlots;
 #pragma unroll
-        for (int k = 0; k < NS; ++k) acc[k] += __ldcg(src + k);
+        for (int k = 0; k < NS; ++k) {
+            A x;
+            if constexpr (sizeof(A) == 8 && !std::is_same<A, double>::value) {
+                const float2 w = __ldcg(reinterpret_cast<const float2*>(src + k));
+                x.hi = w.x;
+                x.lo = w.y;
+            } else {
+                x = __ldcg(reinterpret_cast<const double*>(src + k));
+            }
+            acc[k] = acc_add(acc[k], x);
+        }
     }
-    block_sum<NS>(acc, red);
+    block_sum<A, NS>(acc, red);
     if (threadIdx.x == 0) {
         *P.counter = 0u;
         double S[NS < 4 ? 4 : NS];
 #pragma unroll
-        for (int k = 0; k < (NS < 4 ? 4 : NS); ++k) S[k] = k < NS ? acc[k] : 0.0;
+        for (int k = 0; k < (NS < 4 ? 4 : NS); ++k) S[k] = k < NS ? acc_to_double(acc[k]) : 0.0;
         finalize<T>(step, P, S);
     }
 }
