@@ -196,7 +196,7 @@ k_project(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int
         else store_pair<T>(P.sino[dst_sel] + (size_t)a * P.SB + kSPad, b, out);
         v[0] = acc_prod(out, out);
     }
-    if (step != FIN_NONE) reduce_and_finalize<T, 1>(v, P, it.local, P.cnt_proj, step);
+    if (step != FIN_NONE) reduce_and_finalize<T, 1, true>(v, P, it.local, P.cnt_proj, step);
 }
 
 // ---------------------------------------------------------------------------
@@ -605,7 +605,7 @@ k_tvgrad(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int 
         v[1] = acc_prod(gr, gr);
         v[2] = acc_prod(x, x);
     }
-    if (step != FIN_NONE) reduce_and_finalize<T, 3>(v, P, it.local, P.cnt_img, step);
+    if (step != FIN_NONE) reduce_and_finalize<T, 3, true>(v, P, it.local, P.cnt_img, step);
 }
 
 // ---------------------------------------------------------------------------
@@ -658,10 +658,7 @@ k_trial(const Prob<T>* __restrict__ probs, const Item* __restrict__ items) {
             v[k] = acc_val(in ? tsqrt(du * du + dv * dv) : T(0));
         }
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v[k] = acc_add(v[k], acc_shfl_down(v[k], o));
-        }
+        for (int k = 0; k < 8; ++k) v[k] = warp_sum<true>(v[k]);
         if (lane == 0) {
 #pragma unroll
             for (int k = 0; k < 8; ++k) wsum[warp][grp * 8 + k] = v[k];
@@ -730,7 +727,7 @@ k_sino_axpy(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, i
         store_pair<T>(P.sino[SB_R] + o, b, r);
         v[0] = acc_prod(r, r);
     }
-    reduce_and_finalize<T, 1>(v, P, it.local, P.cnt_ray, step);
+    reduce_and_finalize<T, 1, true>(v, P, it.local, P.cnt_ray, step);
 }
 
 // Caller's plain sinogram [na][nb] into the pair view sino[dst].

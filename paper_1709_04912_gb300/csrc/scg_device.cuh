@@ -252,14 +252,33 @@ __device__ __forceinline__ double acc_shfl_down(double a, int o) { return __shfl
 __device__ __forceinline__ double acc_to_double(DF a) { return (double)a.hi + (double)a.lo; }
 __device__ __forceinline__ double acc_to_double(double a) { return a; }
 
+// Warp-level step of a block sum.  Sums of non-negative terms (squares, TV
+// terms) may take it in plain FP32: a 32-term tree sum of non-negative
+// values is accurate to ~3e-7 relative, and those errors average out over the
+// thousands of warps that the double-float stages then add exactly.  Signed
+// dot products keep double-float throughout.
+template <bool kPositive, typename A>
+__device__ __forceinline__ A warp_sum(A v) {
+    if constexpr (kPositive && std::is_same<A, DF>::value) {
+        float h = v.hi + v.lo;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) h += __shfl_down_sync(0xffffffffu, h, o);
+        A r;
+        r.hi = h;
+        r.lo = 0.f;
+        return r;
+    } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = acc_add(v, acc_shfl_down(v, o));
+        return v;
+    }
+}
+
 // Block sum of NS accumulators; the result is valid in thread 0.
-template <typename A, int NS>
+template <typename A, int NS, bool kPositive = false>
 __device__ __forceinline__ void block_sum(A (&v)[NS], A* smem /* >= 32*NS */) {
 #pragma unroll
-    for (int k = 0; k < NS; ++k) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[k] = acc_add(v[k], acc_shfl_down(v[k], o));
-    }
+    for (int k = 0; k < NS; ++k) v[k] = warp_sum<kPositive>(v[k]);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = (blockDim.x + 31) >> 5;
     __syncthreads();
@@ -288,13 +307,13 @@ template <typename T> __device__ void finalize(int step, const Prob<T>& P, const
 // last item sums all partials in item order and runs the step's finaliser.
 // Must be called by every thread of the block (uniform control flow).
 // Partials are stored as the accumulator type (8 bytes either way).
-template <typename T, int NS>
+template <typename T, int NS, bool kPositive = false>
 __device__ void reduce_and_finalize(Acc<T> (&v)[NS], const Prob<T>& P, int local, int total,
                                     int step) {
     using A = Acc<T>;
     __shared__ A red[32 * NS];
     __shared__ unsigned s_last;
-    block_sum<A, NS>(v, red);
+    block_sum<A, NS, kPositive>(v, red);
     A* parts = reinterpret_cast<A*>(P.partials);
     if (threadIdx.x == 0) {
         A* dst = parts + (size_t)local * kSlots;
