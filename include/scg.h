@@ -221,6 +221,32 @@ int scg_solve(const scg_geometry* g, int variant, int precision, const scg_param
               double* trace, int trace_rows,
               const scg_state* resume, scg_state* final_state, void* stream);
 
+/* One problem of a batched solve: its geometry, threshold and buffers (device
+ * pointers as for scg_solve; x0 may be NULL). */
+typedef struct {
+    scg_geometry geometry;
+    double eps;
+    const void* y;
+    const void* x0;
+    void* x_out;
+} scg_problem;
+
+/* Bytes of device workspace for scg_solve_batch with these problems. */
+size_t scg_batch_workspace_bytes(const scg_problem* problems, int count, int variant, int precision);
+
+/* Solve `count` independent problems (each its own geometry, eps, data) with
+ * one variant, precision and parameter set, advancing them together: every
+ * kernel launch covers the work items of all problems, each problem keeps its
+ * own device-resident state and stops on its own test, and the loop runs until
+ * every problem has stopped (Sec. 3's algorithms, batched; the paper solves
+ * one problem at a time).  Each problem's output equals what scg_solve gives
+ * for it alone, bit for bit.  results: host array of `count`.  Blocking.
+ * Returns SCG_OK when every problem ended with f <= eps, else the first
+ * problem's non-OK status (each result carries its own). */
+int scg_solve_batch(const scg_problem* problems, int count, int variant, int precision,
+                    const scg_params* prm, void* work, size_t work_bytes, scg_result* results,
+                    void* stream);
+
 #ifdef __cplusplus
 }
 #endif

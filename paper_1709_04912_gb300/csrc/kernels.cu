@@ -819,6 +819,44 @@ void launch_loop_cond(DevState* st, cudaGraphConditionalHandle h, cudaStream_t s
     k_loop_cond<<<1, 32, 0, s>>>(st, h);
 }
 
+// Set every problem's stop flag (used around the final kernels of a batch).
+template <typename T>
+__global__ void k_set_done(const Prob<T>* probs, int count, int value) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) probs[i].st->done = value;
+}
+template <typename T>
+void launch_set_done(const Prob<T>* d, int count, int value, cudaStream_t s) {
+    k_set_done<T><<<(count + 127) / 128, 128, 0, s>>>(d, count, value);
+}
+template void launch_set_done<float>(const Prob<float>*, int, int, cudaStream_t);
+template void launch_set_done<double>(const Prob<double>*, int, int, cudaStream_t);
+
+// Batched loop condition: continue while any problem is still running, and
+// never past max_bodies bodies.
+template <typename T>
+__global__ void k_loop_cond_batch(const Prob<T>* probs, BatchState* bs, cudaGraphConditionalHandle h) {
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < bs->count; i += blockDim.x)
+        if (!probs[i].st->done) atomicOr(&any, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned more = any ? 1u : 0u;
+        if (bs->bodies >= bs->max_bodies) more = 0u;
+        bs->bodies += (int)more;
+        cudaGraphSetConditional(h, more);
+    }
+}
+
+template <typename T>
+void launch_loop_cond_batch(const Prob<T>* d, BatchState* bs, cudaGraphConditionalHandle h, cudaStream_t s) {
+    k_loop_cond_batch<T><<<1, 256, 0, s>>>(d, bs, h);
+}
+template void launch_loop_cond_batch<float>(const Prob<float>*, BatchState*, cudaGraphConditionalHandle, cudaStream_t);
+template void launch_loop_cond_batch<double>(const Prob<double>*, BatchState*, cudaGraphConditionalHandle, cudaStream_t);
+
 // ---------------------------------------------------------------------------
 // Host launchers.
 template <typename T>

@@ -118,6 +118,11 @@ struct DevState {
 
 enum Family { FAM_CG = 0, FAM_S_PR = 1, FAM_S_K = 2 };
 
+// Loop bookkeeping of a batched solve (the problems' own states are DevState).
+struct BatchState {
+    int bodies, max_bodies, count, pad_;
+};
+
 template <typename T> struct Vec2;
 template <> struct Vec2<float> { using type = float2; };
 template <> struct Vec2<double> { using type = double2; };

@@ -42,5 +42,9 @@ void launch_taps(T* taps, int nb, int P, double mu, double gain, cudaStream_t s)
 template <typename T>
 void launch_sino_pairs(const Prob<T>* d, int grid, int dst, cudaStream_t s);
 void launch_loop_cond(DevState* st, cudaGraphConditionalHandle h, cudaStream_t s);
+template <typename T>
+void launch_set_done(const Prob<T>* d, int count, int value, cudaStream_t s);
+template <typename T>
+void launch_loop_cond_batch(const Prob<T>* d, BatchState* bs, cudaGraphConditionalHandle h, cudaStream_t s);
 
 }  // namespace scg

@@ -211,20 +211,26 @@ Prob<T> make_prob(const scg_geometry& g, const Plan& pl, unsigned char* base) {
     } while (0)
 
 // Kernel launch sequence helper for one problem.
+// Kernel launch sequence helper: one problem (item lists null, blocks decode
+// their item from blockIdx) or a batch (explicit item lists over problems).
 template <typename T>
 struct Runner {
     const Prob<T>* d;
     int g_ray, g_img, g_row, g_proj, nb;
     cudaStream_t s;
     int launches;
-    void project(int dst, int mode, int step) { ++launches; launch_project<T>(d, nullptr, g_proj, dst, mode, step, s); }
-    void back1(int src, int dst, int step) { ++launches; launch_backproject<T>(d, nullptr, g_img, 1, src, src, dst, dst, step, s); }
-    void back2(int s0, int s1, int d0, int d1, int step) { ++launches; launch_backproject<T>(d, nullptr, g_img, 2, s0, s1, d0, d1, step, s); }
-    void vec(int op, int sel, int step) { ++launches; launch_vec<T>(d, nullptr, g_img, op, sel, step, s); }
-    void tvgrad(int src, int fuse, int wg, int step) { ++launches; launch_tvgrad<T>(d, nullptr, g_img, src, fuse, wg, step, s); }
-    void trial() { ++launches; launch_trial<T>(d, nullptr, g_img, s); }
-    void axpy(int step) { ++launches; launch_sino_axpy<T>(d, nullptr, g_ray, step, s); }
-    void filter(int src, int dst) { ++launches; launch_filter<T>(d, nullptr, g_row, nb, src, dst, 0, s); }
+    const Item* i_ray = nullptr;
+    const Item* i_img = nullptr;
+    const Item* i_row = nullptr;
+    const Item* i_proj = nullptr;
+    void project(int dst, int mode, int step) { ++launches; launch_project<T>(d, i_proj, g_proj, dst, mode, step, s); }
+    void back1(int src, int dst, int step) { ++launches; launch_backproject<T>(d, i_img, g_img, 1, src, src, dst, dst, step, s); }
+    void back2(int s0, int s1, int d0, int d1, int step) { ++launches; launch_backproject<T>(d, i_img, g_img, 2, s0, s1, d0, d1, step, s); }
+    void vec(int op, int sel, int step) { ++launches; launch_vec<T>(d, i_img, g_img, op, sel, step, s); }
+    void tvgrad(int src, int fuse, int wg, int step) { ++launches; launch_tvgrad<T>(d, i_img, g_img, src, fuse, wg, step, s); }
+    void trial() { ++launches; launch_trial<T>(d, i_img, g_img, s); }
+    void axpy(int step) { ++launches; launch_sino_axpy<T>(d, i_ray, g_ray, step, s); }
+    void filter(int src, int dst) { ++launches; launch_filter<T>(d, i_row, g_row, nb, src, dst, 0, s); }
 };
 
 struct Program {
@@ -727,6 +733,271 @@ int filter_impl(const scg_geometry& g, double mu, double gain, const void* r, vo
     return SCG_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Batched solves.  Workspace: [BatchState][an always-stopped DevState][Prob x
+// capacity][item lists for the projector, image-tile, sinogram-row and
+// filter-row kinds][one single-solve region per problem].  Items carry
+// (problem, u, v, local) with local the index the problem's own single-solve
+// launch would give, so each problem's reductions add in exactly the order of
+// a solve of that problem alone.
+//
+// The problem capacity and the item-list lengths are rounded up to a few
+// steps per octave, and the padding items name a placeholder problem whose
+// state is permanently stopped (its blocks return at once).  The captured loop
+// graph then depends only on those rounded sizes, so batches of different
+// geometry mixes reuse it.
+enum { K_PROJ = 0, K_IMG = 1, K_RAY = 2, K_ROW = 3, K_COUNT = 4 };
+
+int round_up_bucket(int n) {
+    if (n <= 16) return n;
+    int lg = 31 - __builtin_clz((unsigned)n);
+    const int step = 1 << (lg - 3);                 // 8 steps per octave: <= 12.5 % padding
+    return (n + step - 1) / step * step;
+}
+
+struct BatchPlan {
+    size_t state, dummy, probs, items[K_COUNT];
+    int n_items[K_COUNT], cap_items[K_COUNT];
+    int cap_probs;
+    std::vector<size_t> region;
+    std::vector<Plan> plans;
+    size_t total;
+    int nb_cap;
+};
+
+BatchPlan make_batch_plan(const scg_problem* pr, int count, int variant, size_t tsize) {
+    BatchPlan b;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, kAlign); return o; };
+    b.state = take(sizeof(BatchState));
+    b.dummy = take(sizeof(DevState));
+    b.cap_probs = round_up_bucket(count + 1);
+    b.probs = take(sizeof(Prob<double>) * (size_t)b.cap_probs);
+    for (int k = 0; k < K_COUNT; ++k) b.n_items[k] = 0;
+    int max_nb = 1;
+    b.plans.resize(count);
+    for (int i = 0; i < count; ++i) {
+        b.plans[i] = make_plan(pr[i].geometry, variant, tsize, PLAN_SOLVE);
+        b.n_items[K_PROJ] += b.plans[i].cnt_proj;
+        b.n_items[K_IMG] += b.plans[i].cnt_img;
+        b.n_items[K_RAY] += b.plans[i].cnt_ray;
+        b.n_items[K_ROW] += b.plans[i].cnt_row;
+        if (pr[i].geometry.n_bins > max_nb) max_nb = pr[i].geometry.n_bins;
+    }
+    b.nb_cap = (max_nb + 127) / 128 * 128;
+    for (int k = 0; k < K_COUNT; ++k) {
+        b.cap_items[k] = round_up_bucket(b.n_items[k]);
+        b.items[k] = take(sizeof(Item) * (size_t)b.cap_items[k]);
+    }
+    b.region.resize(count);
+    for (int i = 0; i < count; ++i) b.region[i] = take(b.plans[i].total);
+    b.total = off;
+    return b;
+}
+
+struct BatchKey {
+    int dev;
+    const void* work;
+    int prec, variant, trial_passes, ksteps, cap_probs, nb_cap;
+    int cap_items[K_COUNT];
+    bool operator<(const BatchKey& o) const {
+        return std::tie(dev, work, prec, variant, trial_passes, ksteps, cap_probs, nb_cap, cap_items[0],
+                        cap_items[1], cap_items[2], cap_items[3]) <
+               std::tie(o.dev, o.work, o.prec, o.variant, o.trial_passes, o.ksteps, o.cap_probs, o.nb_cap,
+                        o.cap_items[0], o.cap_items[1], o.cap_items[2], o.cap_items[3]);
+    }
+};
+std::map<BatchKey, BodyGraph> g_batch_graphs;
+
+template <typename T>
+int batch_impl(const scg_problem* pr, int count, int variant, int precision, const scg_params* prm,
+               void* work, size_t work_bytes, scg_result* results, cudaStream_t user_stream) {
+    const BatchPlan bp = make_batch_plan(pr, count, variant, sizeof(T));
+    if (work_bytes < bp.total || ((uintptr_t)work & 15u)) return SCG_ERR_WORKSPACE;
+    if (uses_filter(variant) && (size_t)(3 * bp.nb_cap) * sizeof(T) > 227 * 1024) return SCG_ERR_UNSUPPORTED;
+    unsigned char* base = (unsigned char*)work;
+    const int fam = family_of(variant);
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    cudaStream_t s;
+    int* pinned = nullptr;
+    CK(side_stream(dev, &s, &pinned));
+    cudaEvent_t ev;
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    CK(cudaEventRecord(ev, user_stream));
+    CK(cudaStreamWaitEvent(s, ev, 0));
+
+    std::vector<Prob<T>> probs(bp.cap_probs);
+    memset(probs.data(), 0, sizeof(Prob<T>) * probs.size());
+    std::vector<std::vector<Item>> items(K_COUNT);
+    for (int k = 0; k < K_COUNT; ++k) items[k].reserve(bp.cap_items[k]);
+    CK(cudaMemsetAsync(base, 0, bp.total, s));
+    for (int i = 0; i < count; ++i) {
+        const Plan& pl = bp.plans[i];
+        unsigned char* rb = base + bp.region[i];
+        Prob<T> P = make_prob<T>(pr[i].geometry, pl, rb);
+        P.y = (const T*)pr[i].y;
+        P.img[IB_AUX] = (T*)pr[i].x0;
+        probs[i] = P;
+        for (int q = 0; q < pl.cnt_proj; ++q) items[K_PROJ].push_back(Item{i, q / pl.proj_blocks, q % pl.proj_blocks, q});
+        for (int q = 0; q < pl.cnt_img; ++q) items[K_IMG].push_back(Item{i, q / pl.tiles_x, q % pl.tiles_x, q});
+        for (int q = 0; q < pl.cnt_ray; ++q) items[K_RAY].push_back(Item{i, q / pl.ray_blocks, q % pl.ray_blocks, q});
+        for (int q = 0; q < pl.cnt_row; ++q) items[K_ROW].push_back(Item{i, q / pl.filt_blocks, q % pl.filt_blocks, q});
+        DevState st;
+        memset(&st, 0, sizeof(st));
+        st.eps = pr[i].eps;
+        st.max_iter = prm->max_iter;
+        st.perturb = prm->perturb;
+        st.gamma0 = prm->gamma0 > 0.0 ? prm->gamma0 : 0.0;
+        st.gamma_fixed = prm->gamma0 > 0.0 ? 1 : 0;
+        st.gamma0_rel = prm->gamma0_rel;
+        st.a = prm->a;
+        st.max_trials = prm->max_trials;
+        st.variant = variant;
+        st.family = fam;
+        st.in_init = 1;
+        st.k = (fam == FAM_S_PR) ? 1 : 0;
+        CK(cudaMemcpyAsync(rb + pl.state, &st, sizeof(st), cudaMemcpyHostToDevice, s));
+        std::vector<Angle<T>> ang;
+        fill_angles<T>(ang, pr[i].geometry.n_angles, pr[i].geometry.n);
+        CK(cudaMemcpyAsync(rb + pl.ang, ang.data(), sizeof(Angle<T>) * ang.size(), cudaMemcpyHostToDevice, s));
+        if (uses_filter(variant)) {
+            const double mu = prm->mu > 0.0 ? prm->mu : 2.0 * M_PI / pl.P;
+            launch_taps<T>(reinterpret_cast<T*>(rb + pl.taps), pr[i].geometry.n_bins, pl.P, mu, prm->filter_gain, s);
+        }
+        // (pageable host sources are staged before cudaMemcpyAsync returns,
+        // so st and ang may be reused for the next problem)
+    }
+    // placeholder problem for the padding items: stopped for good
+    DevState stopped;
+    memset(&stopped, 0, sizeof(stopped));
+    stopped.done = 1;
+    CK(cudaMemcpyAsync(base + bp.dummy, &stopped, sizeof(stopped), cudaMemcpyHostToDevice, s));
+    for (int i = count; i < bp.cap_probs; ++i) probs[i].st = reinterpret_cast<DevState*>(base + bp.dummy);
+    for (int k = 0; k < K_COUNT; ++k)
+        while ((int)items[k].size() < bp.cap_items[k]) items[k].push_back(Item{count, 0, 0, 0});
+    BatchState bs{0, prm->max_iter + 2, count, 0};
+    CK(cudaMemcpyAsync(base + bp.state, &bs, sizeof(bs), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(base + bp.probs, probs.data(), sizeof(Prob<T>) * bp.cap_probs, cudaMemcpyHostToDevice, s));
+    for (int k = 0; k < K_COUNT; ++k)
+        if (bp.cap_items[k])
+            CK(cudaMemcpyAsync(base + bp.items[k], items[k].data(), sizeof(Item) * bp.cap_items[k],
+                               cudaMemcpyHostToDevice, s));
+    const Prob<T>* d = reinterpret_cast<const Prob<T>*>(base + bp.probs);
+    Runner<T> R{d, bp.cap_items[K_RAY], bp.cap_items[K_IMG], bp.cap_items[K_ROW], bp.cap_items[K_PROJ],
+                bp.nb_cap, s, 0};
+    R.i_ray = reinterpret_cast<const Item*>(base + bp.items[K_RAY]);
+    R.i_img = reinterpret_cast<const Item*>(base + bp.items[K_IMG]);
+    R.i_row = reinterpret_cast<const Item*>(base + bp.items[K_ROW]);
+    R.i_proj = reinterpret_cast<const Item*>(base + bp.items[K_PROJ]);
+    Program pg;
+    pg.variant = variant;
+    pg.trial_passes = prm->perturb == SCG_PERTURB_GAMMA ? (prm->max_trials + kTrials - 1) / kTrials : 0;
+    pg.ksteps = prm->K + (prm->k_inclusive ? 1 : 0);
+    run_init<T>(R, pg);
+    CK(cudaGetLastError());
+
+    BatchState* bsd = reinterpret_cast<BatchState*>(base + bp.state);
+    BatchKey key{dev, work, precision, variant, pg.trial_passes, pg.ksteps, bp.cap_probs, bp.nb_cap,
+                 {bp.cap_items[0], bp.cap_items[1], bp.cap_items[2], bp.cap_items[3]}};
+    BodyGraph bg{nullptr, 0, false};
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_batch_graphs.find(key);
+        if (it != g_batch_graphs.end()) bg = it->second;
+    }
+    if (!bg.exec) {
+        cudaStream_t cap;
+        CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        Runner<T> RC = R;
+        RC.s = cap;
+        RC.launches = 0;
+        cudaGraph_t g0 = nullptr;
+        bool ok = cudaGraphCreate(&g0, 0) == cudaSuccess;
+        cudaGraphConditionalHandle h = 0;
+        if (ok) ok = cudaGraphConditionalHandleCreate(&h, g0, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+        cudaGraph_t tmp = nullptr;
+        if (ok) ok = cudaStreamBeginCaptureToGraph(cap, g0, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            launch_loop_cond_batch<T>(d, bsd, h, cap);
+            ok = cudaStreamEndCapture(cap, &tmp) == cudaSuccess;
+        }
+        cudaGraphNode_t pre = nullptr;
+        size_t nn = 1;
+        if (ok) ok = cudaGraphGetNodes(g0, &pre, &nn) == cudaSuccess && nn == 1;
+        alignas(cudaGraphNodeParams) unsigned char npbuf[sizeof(cudaGraphNodeParams)];
+        memset(npbuf, 0, sizeof(npbuf));
+        cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(npbuf);
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t wnode = nullptr;
+        if (ok) ok = cudaGraphAddNode(&wnode, g0, &pre, nullptr, 1, &np) == cudaSuccess;
+        if (ok) {
+            cudaGraph_t body = np.conditional.phGraph_out[0];
+            ok = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (ok) {
+                run_body<T>(RC, pg);
+                launch_loop_cond_batch<T>(d, bsd, h, cap);
+                ok = cudaStreamEndCapture(cap, &tmp) == cudaSuccess;
+            }
+        }
+        if (ok) ok = cudaGraphInstantiate(&bg.exec, g0, 0) == cudaSuccess;
+        if (g0) cudaGraphDestroy(g0);
+        cudaStreamDestroy(cap);
+        if (!ok) { cudaGetLastError(); return SCG_ERR_CUDA; }
+        bg.kernels = RC.launches;
+        bg.device_loop = true;
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_batch_graphs[key] = bg;
+    }
+    CK(cudaGraphLaunch(bg.exec, s));
+
+    // outputs, f and TV of every output
+    const int out_sel = fam == FAM_CG ? IB_X : IB_XH;
+    for (int i = 0; i < count; ++i) {
+        const size_t J = (size_t)pr[i].geometry.n * pr[i].geometry.n;
+        CK(cudaMemcpyAsync(pr[i].x_out, probs[i].img[out_sel], sizeof(T) * J, cudaMemcpyDeviceToDevice, s));
+    }
+    launch_set_done<T>(d, count, 0, s);
+    R.tvgrad(out_sel, 0, 0, FIN_FINAL_TV);
+    if (fam == FAM_CG) {
+        R.vec(VEC_VIEWS, IB_X, FIN_NONE);
+        R.project(SB_Q, PROJ_RESIDUAL, FIN_FINAL_F);
+    }
+    CK(cudaGetLastError());
+    std::vector<DevState> hs(count);
+    for (int i = 0; i < count; ++i)
+        CK(cudaMemcpyAsync(&hs[i], base + bp.region[i] + bp.plans[i].state, sizeof(DevState),
+                           cudaMemcpyDeviceToHost, s));
+    BatchState hb;
+    CK(cudaMemcpyAsync(&hb, bsd, sizeof(hb), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaEventRecord(ev, s));
+    CK(cudaStreamWaitEvent(user_stream, ev, 0));
+    cudaEventDestroy(ev);
+
+    int rc = SCG_OK;
+    const int launches = R.launches + 1 + hb.bodies * (bg.kernels + 1);
+    for (int i = 0; i < count; ++i) {
+        scg_result& r = results[i];
+        memset(&r, 0, sizeof(r));
+        r.iters = hs[i].iters;
+        r.k_final = hs[i].k;
+        r.status = hs[i].status;
+        r.f_final = fam == FAM_CG ? hs[i].f_final : hs[i].f_half;
+        r.tv_final = hs[i].tv_final;
+        r.ell = hs[i].ell;
+        r.gamma0_used = hs[i].gamma0;
+        r.body_launches = hb.bodies;
+        r.kernel_launches = launches;
+        r.device_loop = 1;
+        if (rc == SCG_OK && r.status != SCG_OK) rc = r.status;
+    }
+    return rc;
+}
+
 bool valid_prec(int p) { return p == SCG_F32 || p == SCG_F64; }
 size_t tsize_of(int p) { return p == SCG_F64 ? sizeof(double) : sizeof(float); }
 
@@ -840,6 +1111,40 @@ int scg_solve(const scg_geometry* g, int variant, int precision, const scg_param
                  : solve_impl<float>(g, variant, precision, prm, eps, y, x0, x_out, work, work_bytes,
                                      res, trace, trace_rows, resume, final_state, s);
     if (rc < 0 && rc != SCG_ERR_BREAKDOWN) res->status = rc;
+    return rc;
+}
+
+size_t scg_batch_workspace_bytes(const scg_problem* problems, int count, int variant, int precision) {
+    if (!problems || count < 1 || count > 65536 || !valid_prec(precision) || variant < SCG_CG ||
+        variant > SCG_S_PCG_K)
+        return 0;
+    for (int i = 0; i < count; ++i)
+        if (!valid_geometry(&problems[i].geometry)) return 0;
+    return make_batch_plan(problems, count, variant, tsize_of(precision)).total;
+}
+
+int scg_solve_batch(const scg_problem* problems, int count, int variant, int precision,
+                    const scg_params* prm, void* work, size_t work_bytes, scg_result* results,
+                    void* stream) {
+    if (!problems || count < 1 || count > 65536 || !prm || !work || !results) return SCG_ERR_INVALID;
+    if (variant < SCG_CG || variant > SCG_S_PCG_K) return SCG_ERR_INVALID;
+    if (prm->max_iter < 0 || prm->max_iter > 10000000 || prm->max_trials < 1 || prm->max_trials > 100000 ||
+        prm->K < 1 || prm->K > 1000 || !(prm->a > 0.0 && prm->a < 1.0) || !(prm->filter_gain > 0.0))
+        return SCG_ERR_INVALID;
+    if (prm->perturb != SCG_PERTURB_NONE && prm->perturb != SCG_PERTURB_GAMMA) return SCG_ERR_INVALID;
+    if (prm->host_loop != 0) return SCG_ERR_UNSUPPORTED;
+    for (int i = 0; i < count; ++i) {
+        const scg_problem& p = problems[i];
+        if (!valid_geometry(&p.geometry) || !p.y || !p.x_out || !(p.eps > 0.0) || !isfinite(p.eps))
+            return SCG_ERR_INVALID;
+    }
+    if (!valid_prec(precision)) return SCG_ERR_UNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = precision == SCG_F64
+                 ? batch_impl<double>(problems, count, variant, precision, prm, work, work_bytes, results, s)
+                 : batch_impl<float>(problems, count, variant, precision, prm, work, work_bytes, results, s);
+    if (rc < 0 && rc != SCG_ERR_BREAKDOWN)
+        for (int i = 0; i < count; ++i) results[i].status = rc;
     return rc;
 }
 

@@ -47,6 +47,11 @@ class Result(ctypes.Structure):
                 ("device_loop", ctypes.c_int)]
 
 
+class Problem(ctypes.Structure):
+    _fields_ = [("geometry", Geometry), ("eps", ctypes.c_double), ("y", ctypes.c_void_p),
+                ("x0", ctypes.c_void_p), ("x_out", ctypes.c_void_p)]
+
+
 class State(ctypes.Structure):
     _fields_ = [("valid", ctypes.c_int), ("k", ctypes.c_int), ("ell", ctypes.c_longlong),
                 ("gamma0", ctypes.c_double), ("gamma_fixed", ctypes.c_int),
@@ -88,7 +93,12 @@ def load(build_if_needed: bool = True):
     L.scg_solve.argtypes = [gp, i, i, ctypes.POINTER(Params), d, vp, vp, vp, vp, sz,
                             ctypes.POINTER(Result), ctypes.POINTER(ctypes.c_double), i,
                             ctypes.POINTER(State), ctypes.POINTER(State), vp]
-    for name in ("scg_project", "scg_backproject", "scg_tv", "scg_tv_grad", "scg_filter", "scg_solve"):
+    pp = ctypes.POINTER(Problem)
+    L.scg_batch_workspace_bytes.restype = sz
+    L.scg_batch_workspace_bytes.argtypes = [pp, i, i, i]
+    L.scg_solve_batch.argtypes = [pp, i, i, i, ctypes.POINTER(Params), vp, sz, ctypes.POINTER(Result), vp]
+    for name in ("scg_project", "scg_backproject", "scg_tv", "scg_tv_grad", "scg_filter", "scg_solve",
+                 "scg_solve_batch"):
         getattr(L, name).restype = i
     _lib = L
     return L
@@ -320,3 +330,58 @@ def scg_solve(y: torch.Tensor, n: int, variant: str = "S-CG", eps: float = 1.0, 
         st.update(fs_t)
         out_res.state = st
     return out_res
+
+
+def _problems(ys, ns, eps, x0s, outs):
+    arr = (Problem * len(ys))()
+    for q, (y, n, e, x0, out) in enumerate(zip(ys, ns, eps, x0s, outs)):
+        na, nbins = y.shape
+        arr[q].geometry = geometry(n, na, nbins)
+        arr[q].eps = float(e)
+        arr[q].y = _dev_ptr(y, "y")
+        arr[q].x0 = _dev_ptr(x0, "x0") if x0 is not None else None
+        arr[q].x_out = _dev_ptr(out, "x_out")
+    return arr
+
+
+def batch_workspace_bytes(shapes, variant: str = "S-CG", dtype=torch.float32) -> int:
+    """Workspace bytes of scg_solve_batch for problems of shapes (n, n_angles, n_bins)."""
+    arr = (Problem * len(shapes))()
+    for q, (n, na, nbins) in enumerate(shapes):
+        arr[q].geometry = geometry(n, na, nbins)
+    prec = F64 if dtype == torch.float64 else F32
+    return int(load().scg_batch_workspace_bytes(arr, len(shapes), VARIANTS[variant], prec))
+
+
+def scg_solve_batch(ys, ns, variant: str = "S-CG", eps=1.0, x0s=None, outs=None,
+                    work: torch.Tensor | None = None, **params):
+    """Solve independent problems together (scg_solve_batch).  ``ys``: list of
+    n_angles x n_bins device sinograms of one dtype; ``ns``: image sides;
+    ``eps``: one threshold or one per problem.  Returns one SolveResult each."""
+    L = load()
+    count = len(ys)
+    if count == 0:
+        return []
+    dev, dt = ys[0].device, ys[0].dtype
+    prec = _prec(ys[0])
+    if any(y.dtype != dt or y.device != dev for y in ys):
+        raise ScgError("all sinograms must share one dtype and device")
+    eps = list(eps) if isinstance(eps, (list, tuple)) else [eps] * count
+    x0s = [None] * count if x0s is None else [None if x is None else x.to(dtype=dt).contiguous()
+                                              for x in x0s]
+    if outs is None:
+        outs = [torch.empty((n, n), dtype=dt, device=dev) for n in ns]
+    arr = _problems(ys, ns, eps, x0s, outs)
+    nbytes = L.scg_batch_workspace_bytes(arr, count, VARIANTS[variant], prec)
+    if nbytes == 0:
+        raise ScgError("scg_batch_workspace_bytes rejected the problems")
+    if work is None or work.numel() < nbytes:
+        work = workspace(nbytes, dev, "batch")
+    p = _params(default_params(**params))
+    res = (Result * count)()
+    rc = L.scg_solve_batch(arr, count, VARIANTS[variant], prec, ctypes.byref(p), work.data_ptr(),
+                           work.numel(), res, _stream(dev))
+    _check(rc, "scg_solve_batch", ok=(0, 1, -4))
+    return [SolveResult(outs[q], r.iters, r.k_final, STATUS.get(r.status, str(r.status)), r.status,
+                        r.f_final, r.tv_final, r.ell, r.gamma0_used, r.kernel_launches,
+                        r.body_launches, r.device_loop) for q, r in enumerate(res)]

@@ -6,6 +6,7 @@ import os
 import re
 
 import pytest
+import torch
 
 from paper_1709_04912_gb300 import build as scg_build
 from paper_1709_04912_gb300 import scg
@@ -75,3 +76,32 @@ def test_invalid_arguments_rejected_before_any_launch(lib):
     p2 = scg._params(scg.default_params(a=1.5))
     assert lib.scg_solve(ctypes.byref(g), 2, scg.F32, ctypes.byref(p2), 1.0, fake, None, fake, fake,
                          1 << 30, ctypes.byref(res), None, 0, None, None, None) == -1
+
+
+def test_batch_workspace_query_and_validation(lib):
+    shapes = [(64, 90, 95), (77, 33, 110), (130, 181, 185)]
+    b = scg.batch_workspace_bytes(shapes, "S-CG", torch.float32)
+    # at least the sum of the solo workspaces (plus descriptors and item lists)
+    solo = sum(lib.scg_solve_workspace_bytes(ctypes.byref(scg.geometry(*s)), 2, scg.F32) for s in shapes)
+    assert b >= solo
+    assert scg.batch_workspace_bytes(shapes + [(1, 90, 95)], "S-CG", torch.float32) == 0
+    arr = (scg.Problem * 2)()
+    for q in range(2):
+        arr[q].geometry = scg.geometry(64, 90, 95)
+        arr[q].eps = 1.0
+        arr[q].y = 256
+        arr[q].x_out = 512
+    assert lib.scg_batch_workspace_bytes(arr, 0, 2, scg.F32) == 0
+    assert lib.scg_batch_workspace_bytes(arr, 2, 9, scg.F32) == 0
+    p = scg._params(scg.default_params())
+    res = (scg.Result * 2)()
+    fake = ctypes.c_void_p(256)
+    assert lib.scg_solve_batch(arr, 0, 2, scg.F32, ctypes.byref(p), fake, 1 << 30, res, None) == -1
+    arr[1].eps = 0.0
+    assert lib.scg_solve_batch(arr, 2, 2, scg.F32, ctypes.byref(p), fake, 1 << 30, res, None) == -1
+    arr[1].eps = 1.0
+    arr[1].y = None
+    assert lib.scg_solve_batch(arr, 2, 2, scg.F32, ctypes.byref(p), fake, 1 << 30, res, None) == -1
+    arr[1].y = 256
+    hl = scg._params(scg.default_params(host_loop=1))
+    assert lib.scg_solve_batch(arr, 2, 2, scg.F32, ctypes.byref(hl), fake, 1 << 30, res, None) == -5
