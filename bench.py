@@ -54,6 +54,16 @@ def parse():
     ap.add_argument("--gamma0-rel", type=float, default=0.05)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mode", default="single", choices=["single", "batch", "serving"],
+                    help="single: the headline solve; batch: uneven batch through scg_solve_batch "
+                         "vs the same solves one by one; serving: Poisson request stream through "
+                         "the continuous-batching server")
+    ap.add_argument("--batch", type=int, default=256, help="problems in --mode batch")
+    ap.add_argument("--rate", type=float, default=50.0, help="requests/s in --mode serving")
+    ap.add_argument("--duration", type=float, default=20.0, help="measured seconds in --mode serving")
+    ap.add_argument("--serve-warmup", type=float, default=5.0, help="warm-up seconds in --mode serving")
+    ap.add_argument("--max-active", type=int, default=64)
+    ap.add_argument("--pool-gb", type=float, default=16.0)
     ap.add_argument("--host-loop", action="store_true",
                     help="run the while loop as host-polled per-body graphs (same kernels); "
                          "lets a profiler list every kernel launch")
@@ -371,6 +381,191 @@ def run_ours(args, work, rank, local_rank, world):
     return 0
 
 
+# ---------------------------------------------------------------------------
+def _gpu_problems(works, seed, dev):
+    import torch
+
+    from paper_1709_04912_gb300 import scg
+
+    def gpu_project(x, na, nb):
+        xt = torch.tensor(x, dtype=torch.float32, device=dev)
+        return scg.scg_project(xt, na, nb).double().cpu().numpy()
+
+    probs = [inputs.make_problem(w, seed + q, gpu_project) for q, w in enumerate(works)]
+    ys = [torch.tensor(p.y, dtype=torch.float32, device=dev) for p in probs]
+    return probs, ys
+
+
+def run_batch(args, rank, local_rank, world):
+    """Uneven batch (sizes {128..768}^2, 60..720 angles, 1 % noise): the whole
+    batch through scg_solve_batch, against the same problems solved one by one
+    with scg_solve.  Results are bit-identical both ways."""
+    import torch
+
+    from paper_1709_04912_gb300 import scg
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    scg.load()
+    variant = args.variant
+    kw = dict(gamma0_rel=args.gamma0_rel, max_iter=100)
+    if variant in ("CG", "PCG"):
+        kw["perturb"] = "none"
+    works = inputs.batch_workloads(args.batch, args.seed + rank)
+    probs, ys = _gpu_problems(works, 1000 * (args.seed + rank), dev)
+    ns = [w.n for w in works]
+    eps = [p.eps for p in probs]
+    outs = [torch.empty((n, n), dtype=torch.float32, device=dev) for n in ns]
+    nbytes = scg.batch_workspace_bytes([(w.n, w.n_angles, w.n_bins) for w in works], variant, torch.float32)
+    wsp = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def batch():
+        return scg.scg_solve_batch(ys, ns, variant, eps, outs=outs, work=wsp, **kw)
+
+    for _ in range(args.warmup):
+        rb = batch()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    ms = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rb = batch()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    t_batch = float(np.mean(ms)) / 1e3
+    # the same problems one by one (warm first: one graph per geometry)
+    wsolo = torch.empty(max(scg.solve_workspace_bytes(w.n, w.n_angles, w.n_bins, variant, scg.F32)
+                            for w in works), dtype=torch.uint8, device=dev)
+    for q in range(len(works)):
+        scg.scg_solve(ys[q], ns[q], variant, eps[q], out=outs[q], work=wsolo, **kw)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    same = True
+    for q in range(len(works)):
+        r = scg.scg_solve(ys[q], ns[q], variant, eps[q], out=outs[q], work=wsolo, **kw)
+        same = same and r.iters == rb[q].iters and r.tv_final == rb[q].tv_final
+    e1.record(stream)
+    e1.synchronize()
+    t_solo = e0.elapsed_time(e1) / 1e3
+    if rank == 0:
+        line = {"metric": "batched recon/s", "value": len(works) * world / t_batch, "unit": UNIT,
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * t_batch, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"uneven_batch{len(works)}", "variant": variant,
+                           "sizes": "N in {128,...,768}, angles in {60,...,720}, bins ceil(sqrt2 N)",
+                           "workspace_bytes": nbytes, "parallelism": f"replicas x{world}",
+                           "total_iters": int(sum(r.iters for r in rb)),
+                           "body_launches": rb[0].body_launches},
+                "solo": {"value": len(works) / t_solo, "unit": UNIT, "ms": 1e3 * t_solo,
+                         "same_iters_and_tv": bool(same)},
+                "speedup_vs_solo": t_solo / t_batch, "clocks": clk, "step_ms": ms}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serving(args, rank, local_rank, world):
+    """Poisson stream of few-view requests (N ~ U{128..1024 step 64}, 30..180
+    angles, eps factor U[1.02, 1.2], 1 % noise) through the continuous-batching
+    server; latency is arrival to completion on the host clock."""
+    import torch
+
+    from paper_1709_04912_gb300 import scg
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    scg.load()
+    variant = args.variant
+    kw = dict(gamma0_rel=args.gamma0_rel, max_iter=100)
+    if variant in ("CG", "PCG"):
+        kw["perturb"] = "none"
+    uniq = inputs.serving_workloads(64, args.seed + rank)
+    probs, ys = _gpu_problems(uniq, 5000 * (args.seed + rank), dev)
+    outs = [torch.empty((w.n, w.n), dtype=torch.float32, device=dev) for w in uniq]
+    srv = scg.Server(variant, torch.float32, pool_bytes=int(args.pool_gb * (1 << 30)),
+                     max_active=args.max_active, device=dev, **kw)
+
+    def submit(q, tag):
+        u = q % len(uniq)
+        srv.submit(ys[u], uniq[u].n, probs[u].eps, out=outs[u], tag=tag)
+
+    # saturated throughput: 2 x 64 requests at once (first pass also warms graphs)
+    sat = []
+    for rep in range(2):
+        t0 = time.perf_counter()
+        for q in range(2 * len(uniq)):
+            submit(q, q)
+        got = 0
+        while got < 2 * len(uniq):
+            got += len(srv.step())
+        sat.append(2 * len(uniq) / (time.perf_counter() - t0))
+    # solo: the same requests one by one through scg_solve
+    wsolo = torch.empty(max(scg.solve_workspace_bytes(w.n, w.n_angles, w.n_bins, variant, scg.F32)
+                            for w in uniq), dtype=torch.uint8, device=dev)
+    for q in range(len(uniq)):
+        scg.scg_solve(ys[q], uniq[q].n, variant, probs[q].eps, out=outs[q], work=wsolo, **kw)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for q in range(len(uniq)):
+        scg.scg_solve(ys[q], uniq[q].n, variant, probs[q].eps, out=outs[q], work=wsolo, **kw)
+    torch.cuda.synchronize()
+    solo = len(uniq) / (time.perf_counter() - t0)
+    # the Poisson stream
+    total = args.serve_warmup + args.duration
+    arrivals = inputs.poisson_arrivals(int(args.rate * total * 1.5) + 16, args.rate, args.seed + 7)
+    arrivals = arrivals[arrivals < total]
+    lat, done_t = {}, {}
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    t_start = time.perf_counter()
+    nxt = 0
+    steps = 0
+    while True:
+        now = time.perf_counter() - t_start
+        while nxt < len(arrivals) and arrivals[nxt] <= now:
+            submit(nxt, 100000 + nxt)
+            nxt += 1
+        queued, active = srv.pending()
+        if queued == 0 and active == 0:
+            if nxt >= len(arrivals):
+                break
+            time.sleep(max(0.0, min(arrivals[nxt] - now, 0.01)))
+            continue
+        for tag, r in srv.step():
+            q = tag - 100000
+            t = time.perf_counter() - t_start
+            done_t[q] = t
+            lat[q] = t - arrivals[q]
+        steps += 1
+    clk = clocks.stop()
+    srv.close()
+    window = [q for q in lat if args.serve_warmup <= arrivals[q] < total]
+    served = [q for q in window]
+    L = np.array([lat[q] for q in served]) * 1e3 if served else np.array([float("nan")])
+    t_end = max(done_t[q] for q in served) if served else total
+    thr = len(served) / max(t_end - args.serve_warmup, 1e-9)
+    if rank == 0:
+        line = {"metric": "served recon/s (Poisson)", "value": thr * world, "unit": UNIT, "n_gpus": world,
+                "steps": steps, "warmup": 0, "ms_per_step": None, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "serving_poisson", "variant": variant, "rate": args.rate,
+                           "duration_s": args.duration, "warmup_s": args.serve_warmup,
+                           "requests": len(served), "max_active": args.max_active,
+                           "pool_gb": args.pool_gb,
+                           "sizes": "N ~ U{128..1024 step 64}, 30..180 angles, eps 1.02-1.2 x noise floor"},
+                "latency_ms": {"p50": float(np.percentile(L, 50)), "p99": float(np.percentile(L, 99)),
+                               "mean": float(np.mean(L))},
+                "saturated_recon_per_s": max(sat), "solo_recon_per_s": solo, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     rank, local_rank, world = dist_env()
@@ -384,6 +579,10 @@ def main():
             dist.init_process_group("nccl", init_method="env://")
     if args.impl == "reference":
         return run_reference(args, work, rank, world)
+    if args.mode == "batch":
+        return run_batch(args, rank, local_rank, world)
+    if args.mode == "serving":
+        return run_serving(args, rank, local_rank, world)
     return run_ours(args, work, rank, local_rank, world)
 
 

@@ -20,7 +20,8 @@
  *           ray running along a pixel edge gives half its length to each of
  *           the two pixels it separates.
  *
- * Element types follow scg_precision: double for SCG_F64, float for SCG_F32.
+ * Element types follow scg_precision: double for SCG_F64, float for SCG_F32,
+ * IEEE binary16 for SCG_F16, bfloat16 for SCG_BF16.
  *
  * Memory: every array argument is a DEVICE pointer owned by the caller, except
  * where a comment says "host".  Entry points that need scratch take a device
@@ -69,7 +70,17 @@ typedef enum {
 
 typedef enum {
     SCG_F64 = 0,      /* FP64 storage and arithmetic                             */
-    SCG_F32 = 1       /* FP32 storage and arithmetic, FP64 reductions/scalars    */
+    SCG_F32 = 1,      /* FP32 storage and arithmetic, FP64 reductions/scalars    */
+    SCG_F16 = 2,      /* binary16 storage of every image and sinogram vector,
+                         FP32 arithmetic, FP64-quality reductions, FP64 scalars;
+                         solves run on the scaled system c A x ~ c y (c a power of
+                         two near 1/sqrt(n_angles N), which leaves the iterates
+                         unchanged) so that no vector leaves binary16's range;
+                         the operator entry points apply A unscaled.  Solves:
+                         the superiorized variants only -- CG and PCG update
+                         g and r recursively (Algorithms 2, 4), which an 11-
+                         or 8-bit mantissa cannot carry (SCG_ERR_UNSUPPORTED) */
+    SCG_BF16 = 3      /* as SCG_F16 with bfloat16 storage                        */
 } scg_precision;
 
 typedef enum {
@@ -246,6 +257,66 @@ size_t scg_batch_workspace_bytes(const scg_problem* problems, int count, int var
 int scg_solve_batch(const scg_problem* problems, int count, int variant, int precision,
                     const scg_params* prm, void* work, size_t work_bytes, scg_result* results,
                     void* stream);
+
+/* ---- Serving: continuous batching over a request stream ------------------
+ *
+ * A server holds a set of resident requests in a caller-owned device pool and
+ * advances all of them together, one launch per kernel of the loop body over
+ * the work items of every resident request (as scg_solve_batch does).  A
+ * request joins at the next step after it is submitted, once a slot and pool
+ * memory are free (admission in submission order, by the bytes its state
+ * needs), keeps its whole solver state in the pool while it runs, and leaves
+ * the step after it stops, freeing its memory.  Each result equals what
+ * scg_solve gives for the same request alone, bit for bit.  The paper solves
+ * one problem at a time; serving is this library's. */
+typedef struct scg_server scg_server;       /* opaque */
+
+typedef struct {
+    int variant;            /* one SCG_* variant for every request */
+    int precision;          /* an scg_precision */
+    scg_params params;      /* shared by every request (eps is per request); host_loop must be 0 */
+    void* pool;             /* caller-owned device memory for resident states and work lists,
+                               16-byte aligned; must outlive the server */
+    size_t pool_bytes;
+    int max_active;         /* most requests resident at once, 1..65535 */
+    int bodies_per_step;    /* loop bodies each resident request advances per step, >= 1 */
+} scg_server_config;
+
+typedef struct {
+    unsigned long long tag; /* the tag given to scg_server_submit */
+    scg_result result;      /* as scg_solve's; x_out has been written */
+} scg_completion;
+
+/* Pool bytes one resident request of this geometry holds (its state, vectors
+ * and work items); 0 on invalid arguments. */
+size_t scg_server_footprint(const scg_geometry* g, int variant, int precision);
+
+/* Create a server (host memory only; the pool is not touched until the first
+ * step).  *out receives the handle.  Returns SCG_ERR_INVALID on bad
+ * arguments. */
+int scg_server_create(const scg_server_config* cfg, scg_server** out);
+
+/* Queue one request.  The problem's buffers (y, x0, x_out) are device
+ * pointers that must stay valid until its completion is returned.  Returns
+ * SCG_ERR_INVALID on bad arguments, SCG_ERR_WORKSPACE if its footprint can
+ * never fit the pool.  Host-only; does not block. */
+int scg_server_submit(scg_server* srv, const scg_problem* req, unsigned long long tag);
+
+/* One step: admit queued requests that fit (in submission order; a request
+ * that does not fit yet waits, and so do the ones behind it), advance every
+ * resident request by bodies_per_step loop bodies, finish the ones that
+ * stopped and write up to max_done completions to done[] (*n_done gets the
+ * count; completions beyond max_done are kept for the next step).  Blocking:
+ * returns after the device has finished the step; the completed outputs are
+ * ordered before later work on `stream`. */
+int scg_server_step(scg_server* srv, void* stream, scg_completion* done, int max_done, int* n_done);
+
+/* Requests queued (not yet admitted) and resident. */
+int scg_server_pending(const scg_server* srv, int* queued, int* active);
+
+/* Destroy the server (pending requests are dropped).  The pool is the
+ * caller's to free afterwards. */
+int scg_server_destroy(scg_server* srv);
 
 #ifdef __cplusplus
 }

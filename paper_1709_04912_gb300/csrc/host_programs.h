@@ -1,0 +1,408 @@
+// host_programs.h -- host-side pieces shared by the solve, batch and serving
+// entry points: the per-problem workspace plan, the angle table, the device
+// problem descriptor, the per-variant kernel programs (Algorithms 1-14) and
+// the work-item lists of batched launches.
+#pragma once
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "scg_kernels.h"
+
+namespace scg {
+namespace host {
+
+constexpr int kMaxTraceRows = 4096;
+constexpr size_t kAlign = 256;
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+inline int round_up4(int v) { return (v + 3) / 4 * 4; }
+
+inline bool valid_geometry(const scg_geometry* g) {
+    return g && g->n >= 2 && g->n <= 8192 && g->n_angles >= 1 && g->n_angles <= 16384 &&
+           g->n_bins >= 1 && g->n_bins <= 16384;
+}
+
+inline int filter_length(int nb) {
+    int P = 1;
+    while (P < 2 * nb) P *= 2;
+    return P;
+}
+
+inline int family_of(int v) {
+    if (v == SCG_CG || v == SCG_PCG) return FAM_CG;
+    if (v == SCG_S_CG_K || v == SCG_S_PCG_K) return FAM_S_K;
+    return FAM_S_PR;
+}
+
+inline bool uses_filter(int v) { return v == SCG_PCG || v == SCG_S_PCG || v == SCG_S_PCG_K; }
+
+inline bool valid_prec(int p) { return p == SCG_F32 || p == SCG_F64 || p == SCG_F16 || p == SCG_BF16; }
+// bytes of one stored element, and of one arithmetic value
+inline size_t elem_size(int p) { return p == SCG_F64 ? 8 : p == SCG_F32 ? 4 : 2; }
+inline size_t calc_size(int p) { return p == SCG_F64 ? 8 : 4; }
+template <typename T> constexpr int prec_of();
+template <> constexpr int prec_of<float>() { return SCG_F32; }
+template <> constexpr int prec_of<double>() { return SCG_F64; }
+template <> constexpr int prec_of<__half>() { return SCG_F16; }
+template <> constexpr int prec_of<__nv_bfloat16>() { return SCG_BF16; }
+
+// Half and bfloat16 storage serve the superiorized variants, whose gradient
+// is recomputed from x in every loop body.  CG and PCG update g and r
+// recursively (g' = g + alpha h, Algorithms 2 and 4): with an 8- or 11-bit
+// mantissa the cancellation in that update loses the gradient.
+inline bool solve_supported(int variant, int precision) {
+    if (precision == SCG_F32 || precision == SCG_F64) return true;
+    return variant != SCG_CG && variant != SCG_PCG;
+}
+
+// Scale c of the system a solve works on: c A x ~ c y, f scaled by c^2.  CG's
+// iterates do not change when A and y are scaled together, and a power of two
+// scales every value exactly, so this only moves magnitudes: for half storage
+// A^T (A x - y) grows with n_angles * N and would overflow at 1024^2 / 1440
+// angles.  c = 2^-round(log2(sqrt(n_angles N))) keeps the residual, gradient
+// and direction vectors near 1.  FP32 and FP64 solve the unscaled system.
+inline double system_scale(const scg_geometry& g, int precision) {
+    if (precision == SCG_F32 || precision == SCG_F64) return 1.0;
+    const double e = 0.5 * log2((double)g.n_angles * (double)g.n);
+    return ldexp(1.0, -(int)llround(e));
+}
+
+// Workspace plan: byte offsets of every segment.
+struct Plan {
+    size_t state, prob, ang, taps, partials, counter, trace;
+    size_t img[IB_COUNT];
+    size_t view_rm, view_cm;
+    size_t sino[SB_COUNT];
+    size_t total;
+    int S, SB, cnt_ray, cnt_img, cnt_row, tiles_x, ray_blocks, filt_blocks, P;
+    int cnt_proj, proj_blocks;
+};
+
+enum PlanKind { PLAN_OP = 0, PLAN_SOLVE = 1 };
+
+inline Plan make_plan(const scg_geometry& g, int variant, int precision, int kind) {
+    const size_t tsize = elem_size(precision), csize = calc_size(precision);
+    Plan p;
+    memset(&p, 0, sizeof(p));
+    const int N = g.n, na = g.n_angles, nb = g.n_bins;
+    p.S = round_up4(N + 2 * kPad);          // pairs per view line
+    p.SB = round_up4(nb + 2 * kSPad);       // pairs per sinogram-view row
+    p.ray_blocks = (nb + kRayBlock - 1) / kRayBlock;
+    p.tiles_x = (N + kTileW - 1) / kTileW;
+    p.cnt_ray = na * p.ray_blocks;
+    p.cnt_img = ((N + kTileH - 1) / kTileH) * p.tiles_x;
+    p.filt_blocks = (nb + kFilterBlock - 1) / kFilterBlock;
+    p.cnt_row = na * p.filt_blocks;
+    p.proj_blocks = (nb + kProjRays - 1) / kProjRays;
+    p.cnt_proj = ((na + kProjAngles - 1) / kProjAngles) * p.proj_blocks;
+    p.P = filter_length(nb);
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, kAlign); return o; };
+    const size_t J = (size_t)N * N;
+    p.state = take(sizeof(DevState));
+    p.prob = take(sizeof(Prob<double>));
+    p.ang = take(sizeof(Angle<double>) * na);
+    p.taps = take(csize * (2 * (size_t)nb - 1));
+    int maxcnt = p.cnt_ray > p.cnt_img ? p.cnt_ray : p.cnt_img;
+    if (p.cnt_row > maxcnt) maxcnt = p.cnt_row;
+    if (p.cnt_proj > maxcnt) maxcnt = p.cnt_proj;
+    p.partials = take(sizeof(double) * kSlots * (size_t)maxcnt);
+    p.counter = take(sizeof(unsigned) * 4);
+    p.view_rm = take(2 * tsize * (size_t)N * p.S);
+    p.view_cm = take(2 * tsize * (size_t)N * p.S);
+    const size_t sino_bytes = 2 * tsize * (size_t)na * p.SB;
+    for (int q = 0; q < IB_COUNT; ++q) p.img[q] = (size_t)-1;
+    for (int q = 0; q < SB_COUNT; ++q) p.sino[q] = (size_t)-1;
+    if (kind == PLAN_OP) {
+        p.trace = (size_t)-1;
+        p.sino[SB_R] = take(sino_bytes);
+    } else {
+        p.trace = take(sizeof(double) * TR_NF * kMaxTraceRows);
+        const int fam = family_of(variant);
+        p.img[IB_X] = take(tsize * J);
+        p.img[IB_P] = take(tsize * J);
+        p.img[IB_H] = take(tsize * J);
+        p.img[IB_G] = take(tsize * J);
+        if (fam != FAM_CG) {
+            p.img[IB_XH] = take(tsize * J);
+            p.img[IB_TVG] = take(tsize * J);
+        }
+        if (uses_filter(variant)) p.img[IB_Z] = take(tsize * J);
+        p.sino[SB_R] = take(sino_bytes);
+        p.sino[SB_Q] = take(sino_bytes);
+        if (uses_filter(variant)) p.sino[SB_W] = take(sino_bytes);
+    }
+    p.total = off;
+    return p;
+}
+
+// Per-angle constants; `scale` multiplies every chord (1/m), i.e. A -> scale A.
+template <typename T>
+void fill_angles(std::vector<Angle<T>>& out, int na, int n, double scale = 1.0) {
+    out.resize(na);
+    const double off_n = 0.5 * (n - 1);
+    for (int a = 0; a < na; ++a) {
+        double c, s;
+        if (a == 0) { c = 1.0; s = 0.0; }
+        else if (2 * a == na) { c = 0.0; s = 1.0; }
+        else { const double th = M_PI * (double)a / (double)na; c = cos(th); s = sin(th); }
+        const double ac = fabs(c), as = fabs(s);
+        const double m = ac > as ? ac : as, mn = ac > as ? as : ac;
+        const double hs = 0.5 * (m + mn);
+        Angle<T> g;
+        memset(&g, 0, sizeof(g));
+        g.c = (T)c;
+        g.s = (T)s;
+        g.inv_m = (T)(scale / m);
+        if (mn == 0.0) {
+            g.k2 = (T)1.0; g.h2 = (T)1.0; g.h2p = (T)2.0;
+            g.kb = (T)1.0; g.hb0 = (T)1.0; g.hb1 = (T)0.0;
+            g.hb0p = (T)2.0; g.hb1p = (T)-1.0;
+        } else {
+            g.k2 = (T)(m / mn); g.h2 = (T)(hs / mn); g.h2p = (T)(hs / mn + m / mn);
+            g.kb = (T)(1.0 / mn); g.hb0 = (T)(hs / mn); g.hb1 = (T)((hs - 1.0) / mn);
+            g.hb0p = (T)(hs / mn + 1.0 / mn); g.hb1p = (T)((hs - 1.0) / mn - 1.0 / mn);
+        }
+        g.c24 = (int)llrint(c * 16777216.0);
+        g.s24 = (int)llrint(s * 16777216.0);
+        g.col_driven = as >= ac ? 1 : 0;
+        const double inv = g.col_driven ? 1.0 / s : 1.0 / c;
+        const double e = g.col_driven ? c : s;
+        const double slope = -e * inv, c0_off = off_n * (e * inv + 1.0);
+        g.slope = (T)slope;
+        g.inv_drive = (T)inv;
+        g.c0_off = (T)c0_off;
+        g.inv_slope = slope == 0.0 ? (T)0 : (T)(1.0 / slope);
+        g.c_d = c;
+        g.s_d = s;
+        g.inv_d = inv;
+        g.c0_off_d = c0_off;
+        g.slope_d = slope;
+        const double two32 = 4294967296.0;
+        g.c_fx = llrint(c * two32);
+        g.s_fx = llrint(s * two32);
+        g.inv_fx = llrint(inv * two32);
+        g.c0_off_fx = llrint(c0_off * two32);
+        g.slope_fx = llrint(slope * two32);
+        out[a] = g;
+    }
+}
+
+template <typename T>
+Prob<T> make_prob(const scg_geometry& g, const Plan& pl, unsigned char* base, double scale = 1.0) {
+    using E = typename Tr<T>::S;
+    using E2 = typename Tr<T>::S2;
+    using C = typename Tr<T>::C;
+    Prob<T> P;
+    memset(&P, 0, sizeof(P));
+    P.n = g.n;
+    P.na = g.n_angles;
+    P.nb = g.n_bins;
+    P.S = pl.S;
+    P.SB = pl.SB;
+    P.cnt_ray = pl.cnt_ray;
+    P.cnt_img = pl.cnt_img;
+    P.cnt_row = pl.cnt_row;
+    P.tiles_x = pl.tiles_x;
+    P.ray_blocks = pl.ray_blocks;
+    P.filt_blocks = pl.filt_blocks;
+    P.cnt_proj = pl.cnt_proj;
+    P.proj_blocks = pl.proj_blocks;
+    P.P = pl.P;
+    P.off_n = (C)(0.5 * (g.n - 1));
+    P.off_b = (C)(0.5 * (g.n_bins - 1));
+    P.y_scale = (C)scale;
+    P.ang = reinterpret_cast<const Angle<C>*>(base + pl.ang);
+    P.taps = reinterpret_cast<const C*>(base + pl.taps);
+    for (int q = 0; q < IB_COUNT; ++q)
+        P.img[q] = pl.img[q] == (size_t)-1 ? nullptr : reinterpret_cast<E*>(base + pl.img[q]);
+    for (int q = 0; q < SB_COUNT; ++q)
+        P.sino[q] = pl.sino[q] == (size_t)-1 ? nullptr : reinterpret_cast<E2*>(base + pl.sino[q]);
+    P.view_rm = reinterpret_cast<E2*>(base + pl.view_rm);
+    P.view_cm = reinterpret_cast<E2*>(base + pl.view_cm);
+    P.partials = reinterpret_cast<double*>(base + pl.partials);
+    P.counter = reinterpret_cast<unsigned*>(base + pl.counter);
+    P.st = reinterpret_cast<DevState*>(base + pl.state);
+    P.trace = pl.trace == (size_t)-1 ? nullptr : reinterpret_cast<double*>(base + pl.trace);
+    P.trace_rows = pl.trace == (size_t)-1 ? 0 : kMaxTraceRows;
+    return P;
+}
+
+#define CK(call)                                   \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) return SCG_ERR_CUDA; \
+    } while (0)
+
+// Kernel launch sequence helper: one problem (item lists null, blocks decode
+// their item from blockIdx) or a batch (explicit item lists over problems).
+template <typename T>
+struct Runner {
+    const Prob<T>* d;
+    int g_ray, g_img, g_row, g_proj, nb;
+    cudaStream_t s;
+    int launches;
+    const Item* i_ray = nullptr;
+    const Item* i_img = nullptr;
+    const Item* i_row = nullptr;
+    const Item* i_proj = nullptr;
+    void project(int dst, int mode, int step) { ++launches; launch_project<T>(d, i_proj, g_proj, dst, mode, step, s); }
+    void back1(int src, int dst, int step) { ++launches; launch_backproject<T>(d, i_img, g_img, 1, src, src, dst, dst, step, s); }
+    void back2(int s0, int s1, int d0, int d1, int step) { ++launches; launch_backproject<T>(d, i_img, g_img, 2, s0, s1, d0, d1, step, s); }
+    void vec(int op, int sel, int step) { ++launches; launch_vec<T>(d, i_img, g_img, op, sel, step, s); }
+    void tvgrad(int src, int fuse, int wg, int step) { ++launches; launch_tvgrad<T>(d, i_img, g_img, src, fuse, wg, step, s); }
+    void trial() { ++launches; launch_trial<T>(d, i_img, g_img, s); }
+    void axpy(int step) { ++launches; launch_sino_axpy<T>(d, i_ray, g_ray, step, s); }
+    void filter(int src, int dst) { ++launches; launch_filter<T>(d, i_row, g_row, nb, src, dst, 0, s); }
+};
+
+struct Program {
+    int variant, trial_passes, ksteps;
+};
+
+// The algorithms' set-up steps (before the first loop test).
+template <typename T>
+void run_init(Runner<T>& R, const Program& pg) {
+    const int v = pg.variant, fam = family_of(v);
+    const bool pre = uses_filter(v);
+    const int dsel = pre ? IB_Z : IB_G;
+    R.vec(VEC_INIT, 0, FIN_NONE);                      // x_{1/2} = x0 (S-CG family), x_{-1/2} = x0 (S-K)
+    R.project(SB_R, PROJ_RESIDUAL, FIN_F);             // r = A x0 - y, f(x0)
+    if (fam == FAM_S_K) {
+        R.tvgrad(IB_X, 0, 1, FIN_END);                 // TV and dTV of x_0; first loop test
+        return;
+    }
+    if (pre) R.filter(SB_R, SB_W);
+    if (fam == FAM_CG) {
+        if (pre) R.back2(SB_R, SB_W, IB_G, IB_Z, FIN_CG_DELTA);   // g0 = A^T r, z0 = M g0
+        else R.back1(SB_R, IB_G, FIN_CG_DELTA);                    // g0 = A^T r
+        R.vec(VEC_FORM_P0, dsel, FIN_CG_END);          // p0 = -g0 (-z0); first loop test
+        return;
+    }
+    if (pre) R.back2(SB_R, SB_W, IB_G, IB_Z, FIN_BETA);
+    else R.back1(SB_R, IB_G, FIN_BETA);                // g0 = A^T (A x0 - y)
+    R.vec(VEC_FORM_P0, dsel, FIN_NUM);                 // p0 = -g0 (-z0), g0^T p0
+    R.project(SB_Q, PROJ_PLAIN, FIN_NONE);             // A p0
+    R.back1(SB_Q, IB_H, FIN_ALPHA);                    // h0 = A^T A p0, alpha
+    R.tvgrad(IB_X, 1, 1, FIN_END);                     // x1 = x0 + alpha p0 (+ dTV(x1)); k = 1; loop test
+}
+
+// One loop body of the variant's while loop.
+template <typename T>
+void run_body(Runner<T>& R, const Program& pg) {
+    const int v = pg.variant, fam = family_of(v);
+    const bool pre = uses_filter(v);
+    const int dsel = pre ? IB_Z : IB_G;
+    if (fam == FAM_CG) {                               // CG-STEP / PCG-STEP
+        R.project(SB_Q, PROJ_PLAIN, FIN_NONE);         // A p
+        R.back1(SB_Q, IB_H, FIN_CG_ALPHA);             // h = A^T A p, alpha = delta / p^T h
+        R.axpy(FIN_CG_F);                              // r' = r + alpha A p, f(x')
+        if (pre) {
+            R.filter(SB_R, SB_W);
+            R.back1(SB_W, IB_Z, FIN_NONE);             // z' = M g'
+        }
+        R.vec(VEC_CG_UPDATE, IB_X, FIN_CG_BETA);       // x' = x + alpha p, g' = g + alpha h, beta
+        R.vec(VEC_FORM_P, dsel, FIN_CG_END);           // p' = -g' (-z') + beta p; k = k+1; loop test
+        return;
+    }
+    for (int t = 0; t < pg.trial_passes; ++t) R.trial();  // TV trials of x_k + gamma_l v
+    R.vec(VEC_PERTURB, 0, FIN_NONE);                   // x_{k+1/2} = perturbed(x_k)
+    R.project(SB_R, PROJ_RESIDUAL, FIN_F);             // A x_{k+1/2} - y, f(x_{k+1/2})
+    if (pre) R.filter(SB_R, SB_W);
+    if (fam == FAM_S_K) {                              // CG-K / PCG-K from x_{k+1/2}
+        if (pre) R.back2(SB_R, SB_W, IB_G, IB_Z, FIN_CG_DELTA);
+        else R.back1(SB_R, IB_G, FIN_CG_DELTA);
+        R.vec(VEC_FORM_P0, dsel, FIN_NONE);
+        for (int q = 0; q < pg.ksteps; ++q) {
+            R.project(SB_Q, PROJ_PLAIN, FIN_NONE);
+            R.back1(SB_Q, IB_H, FIN_CG_ALPHA);
+            if (pre) {
+                R.axpy(FIN_NONE);
+                R.filter(SB_R, SB_W);
+                R.back1(SB_W, IB_Z, FIN_NONE);
+            }
+            R.vec(VEC_CG_UPDATE, q == 0 ? IB_XH : IB_X, FIN_CG_BETA);
+            if (q + 1 < pg.ksteps) R.vec(VEC_FORM_P, dsel, FIN_NONE);
+        }
+        R.tvgrad(IB_X, 0, 1, FIN_END);                 // dTV(x_{k+1}); k = k+1; loop test
+        return;
+    }
+    // CG-PR-STEP / CG-CD-STEP / PCG-PR-STEP
+    if (pre) R.back2(SB_R, SB_W, IB_G, IB_Z, FIN_BETA);   // g', z' = M g'
+    else R.back1(SB_R, IB_G, FIN_BETA);                // g' = A^T (A x - y), beta
+    R.vec(VEC_FORM_P, dsel, FIN_NUM);                  // p' = -g' (-z') + beta p, g'^T p'
+    R.project(SB_Q, PROJ_PLAIN, FIN_NONE);             // A p'
+    R.back1(SB_Q, IB_H, FIN_ALPHA);                    // h' = A^T A p', alpha
+    R.tvgrad(IB_X, 1, 1, FIN_END);                     // x' = x + alpha p' (+ dTV); k = k+1; loop test
+}
+
+// Resume from an imported state: recompute f at the tested point, the dots
+// the next step needs, and dTV(x_k); then take the loop test.
+template <typename T>
+void run_resume(Runner<T>& R, const Program& pg) {
+    const int fam = family_of(pg.variant);
+    if (fam == FAM_CG) {
+        R.vec(VEC_VIEWS, IB_X, FIN_NONE);
+        R.project(SB_R, PROJ_RESIDUAL, FIN_F);         // r_k = A x_k - y, f(x_k)
+        R.vec(VEC_VIEWS, IB_P, FIN_CG_END);            // loop test
+        return;
+    }
+    R.vec(VEC_VIEWS, IB_XH, FIN_NONE);
+    R.project(SB_R, PROJ_RESIDUAL, FIN_F);             // f(x_{k-1/2})
+    if (fam == FAM_S_PR) R.vec(VEC_DOTS_RESUME, 0, FIN_RESUME);   // p^T h, g^T p
+    R.tvgrad(IB_X, 0, 1, FIN_END);                     // dTV(x_k); loop test
+}
+
+// Initial device state of one solve.
+inline DevState initial_state(const scg_params* prm, double eps, int variant) {
+    DevState st;
+    memset(&st, 0, sizeof(st));
+    const int fam = family_of(variant);
+    st.eps = eps;
+    st.max_iter = prm->max_iter;
+    st.perturb = prm->perturb;
+    st.gamma0 = prm->gamma0 > 0.0 ? prm->gamma0 : 0.0;
+    st.gamma_fixed = prm->gamma0 > 0.0 ? 1 : 0;
+    st.gamma0_rel = prm->gamma0_rel;
+    st.a = prm->a;
+    st.max_trials = prm->max_trials;
+    st.variant = variant;
+    st.family = fam;
+    st.in_init = 1;
+    st.k = (fam == FAM_S_PR) ? 1 : 0;
+    return st;
+}
+
+inline Program make_program(const scg_params* prm, int variant) {
+    Program pg;
+    pg.variant = variant;
+    pg.trial_passes = prm->perturb == SCG_PERTURB_GAMMA ? (prm->max_trials + kTrials - 1) / kTrials : 0;
+    pg.ksteps = prm->K + (prm->k_inclusive ? 1 : 0);
+    return pg;
+}
+
+// Work items of batched launches, one list per launch kind.  A problem's
+// items keep the (u, v) and block index (local) of its own single-problem
+// launch, so its reductions add in the single-problem order.
+enum { K_PROJ = 0, K_IMG = 1, K_RAY = 2, K_ROW = 3, K_COUNT = 4 };
+
+inline void append_items(const Plan& pl, int prob, std::vector<Item>* lists) {
+    for (int q = 0; q < pl.cnt_proj; ++q) lists[K_PROJ].push_back(Item{prob, q / pl.proj_blocks, q % pl.proj_blocks, q});
+    for (int q = 0; q < pl.cnt_img; ++q) lists[K_IMG].push_back(Item{prob, q / pl.tiles_x, q % pl.tiles_x, q});
+    for (int q = 0; q < pl.cnt_ray; ++q) lists[K_RAY].push_back(Item{prob, q / pl.ray_blocks, q % pl.ray_blocks, q});
+    for (int q = 0; q < pl.cnt_row; ++q) lists[K_ROW].push_back(Item{prob, q / pl.filt_blocks, q % pl.filt_blocks, q});
+}
+
+// List lengths rounded up to eight steps per octave (<= 12.5 % padding), so
+// launches captured for one mix of problems serve other mixes.
+inline int round_up_bucket(int n) {
+    if (n <= 16) return n;
+    int lg = 31 - __builtin_clz((unsigned)n);
+    const int step = 1 << (lg - 3);
+    return (n + step - 1) / step * step;
+}
+
+}  // namespace host
+}  // namespace scg

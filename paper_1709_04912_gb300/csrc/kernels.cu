@@ -53,9 +53,10 @@ __device__ __forceinline__ Item decode_item(const Prob<T>* probs, const Item* it
 // D carries the view element index of the pair at the crossing in its high
 // word (line t*S, pad kPad, floor(c*)) and the crossing's fraction in its low
 // word; adding DL = slope + S (both in 32.32) steps to the next strip.
-__device__ __forceinline__ void strip(const float2* view, long long D, float k2, float h2p,
+template <typename V2>
+__device__ __forceinline__ void strip(const V2* view, long long D, float k2, float h2p,
                                       float& u, float& y) {
-    const float2 v = __ldg(view + (int)(D >> 32));
+    const float2 v = to_c2(__ldg(view + (int)(D >> 32)));
     const float f1 = __int_as_float(0x3F800000 | ((unsigned)D >> 9));   // 1 + fraction
     u = fmaf(__saturatef(fmaf(-f1, k2, h2p)), v.x - v.y, u);
     y += v.y;
@@ -65,18 +66,19 @@ __device__ __forceinline__ void strip(const float2* view, long long D, float k2,
 // flight while the current four are summed.  Every index read lies inside the
 // view because [tlo, thi] holds exactly the strips whose crossing satisfies
 // -1 <= floor(c*) <= N-1 (kPad >= 1).
-__device__ __forceinline__ float walk_ray_f32(const float2* view, int n, long long D, long long DL,
+template <typename V2>
+__device__ __forceinline__ float walk_ray_f32(const V2* view, int n, long long D, long long DL,
                                               float k2, float h2p) {
     float u0 = 0.f, u1 = 0.f, y0 = 0.f, y1 = 0.f;
     int t = 0;
     if (n >= 4) {
         long long Da = D, Db = D + DL, Dc = D + 2 * DL, Dd = D + 3 * DL;
-        float2 va = __ldg(view + (int)(Da >> 32)), vb = __ldg(view + (int)(Db >> 32));
-        float2 vc = __ldg(view + (int)(Dc >> 32)), vd = __ldg(view + (int)(Dd >> 32));
+        float2 va = to_c2(__ldg(view + (int)(Da >> 32))), vb = to_c2(__ldg(view + (int)(Db >> 32)));
+        float2 vc = to_c2(__ldg(view + (int)(Dc >> 32))), vd = to_c2(__ldg(view + (int)(Dd >> 32)));
         for (t = 4; t + 4 <= n; t += 4) {
             const long long Na = Dd + DL, Nb = Dd + 2 * DL, Nc = Dd + 3 * DL, Nd = Dd + 4 * DL;
-            const float2 wa = __ldg(view + (int)(Na >> 32)), wb = __ldg(view + (int)(Nb >> 32));
-            const float2 wc = __ldg(view + (int)(Nc >> 32)), wd = __ldg(view + (int)(Nd >> 32));
+            const float2 wa = to_c2(__ldg(view + (int)(Na >> 32))), wb = to_c2(__ldg(view + (int)(Nb >> 32)));
+            const float2 wc = to_c2(__ldg(view + (int)(Nc >> 32))), wd = to_c2(__ldg(view + (int)(Nd >> 32)));
 #define SCG_STRIP(V_, D_, U_, Y_)                                                                 \
     U_ = fmaf(__saturatef(fmaf(-__int_as_float(0x3F800000 | ((unsigned)(D_) >> 9)), k2, h2p)),    \
               V_.x - V_.y, U_);                                                                   \
@@ -102,8 +104,6 @@ __device__ __forceinline__ float walk_ray_f32(const float2* view, int n, long lo
     return (u0 + u1) + (y0 + y1);
 }
 
-template <typename T>
-__device__ __forceinline__ T project_ray(const Prob<T>& P, const Angle<T>& g, int b);
 
 // Strips t in [0, N) whose crossing C(t) = C0 + t*SL (32.32) has floor in
 // [-1, N-1]: a FP32 estimate, then corrected exactly in integer arithmetic.
@@ -129,8 +129,9 @@ __device__ __forceinline__ void walk_range(long long C0, long long SL, int N, fl
     if (tlo > thi || !ok(tlo) || !ok(thi)) { tlo = 0; thi = -1; }
 }
 
-template <>
-__device__ __forceinline__ float project_ray<float>(const Prob<float>& P, const Angle<float>& g, int b) {
+// FP32 arithmetic (float, half and bfloat16 storage).
+template <typename T>
+__device__ __forceinline__ float project_ray_f32(const Prob<T>& P, const Angle<float>& g, int b) {
     const int N = P.n, B2 = 2 * b - (P.nb - 1);           // 2 (b - (nb-1)/2)
     const long long C0 = (((long long)B2 * g.inv_fx) >> 1) + g.c0_off_fx;
     const float c0f = fmaf(0.5f * (float)B2, g.inv_drive, g.c0_off);
@@ -139,12 +140,11 @@ __device__ __forceinline__ float project_ray<float>(const Prob<float>& P, const 
     if (thi < tlo) return 0.f;
     const long long S32 = (long long)P.S << 32;
     const long long D = C0 + (long long)tlo * g.slope_fx + (long long)tlo * S32 + ((long long)kPad << 32);
-    const float2* V = g.col_driven ? P.view_cm : P.view_rm;
+    const auto* V = g.col_driven ? P.view_cm : P.view_rm;
     return walk_ray_f32(V, thi - tlo + 1, D, g.slope_fx + S32, g.k2, g.h2p) * g.inv_m;
 }
 
-template <>
-__device__ __forceinline__ double project_ray<double>(const Prob<double>& P, const Angle<double>& g, int b) {
+__device__ __forceinline__ double project_ray_f64(const Prob<double>& P, const Angle<double>& g, int b) {
     const int N = P.n;
     const double c0d = fma((double)b - 0.5 * (double)(P.nb - 1), g.inv_d, g.c0_off_d);
     int tlo = 0, thi = N - 1;
@@ -172,6 +172,12 @@ __device__ __forceinline__ double project_ray<double>(const Prob<double>& P, con
     return acc * g.inv_m;
 }
 
+template <typename T>
+__device__ __forceinline__ typename Tr<T>::C project_ray(const Prob<T>& P, const Angle<typename Tr<T>::C>& g, int b) {
+    if constexpr (std::is_same<T, double>::value) return project_ray_f64(P, g, b);
+    else return project_ray_f32(P, g, b);
+}
+
 // One block: kProjAngles adjacent angles x kProjRays consecutive bins; each
 // warp walks 32 rays of one angle.  Rays of neighbouring angles cross the
 // image almost together, so the warps of a block read nearly the same view
@@ -186,13 +192,15 @@ k_project(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int
     const int nb = P.nb;
     const int a = it.u * kProjAngles + threadIdx.x / kProjRays;
     const int b = it.v * kProjRays + threadIdx.x % kProjRays;
+    using C = typename Tr<T>::C;
     Acc<T> v[1];
     acc_zero(v[0]);
     if (a < P.na && b < nb) {
-        const Angle<T> g = P.ang[a];
-        T out = project_ray<T>(P, g, b);
-        if (mode == PROJ_RESIDUAL) out = out - P.y[(size_t)a * nb + b];
-        if (mode == PROJ_PLAIN_OUT) P.user_out[(size_t)a * nb + b] = out;
+        const Angle<C> g = P.ang[a];
+        C out = project_ray<T>(P, g, b);
+        // (y_scale is 1 except for half/bfloat16 storage; the product is exact)
+        if (mode == PROJ_RESIDUAL) out = out - to_c(P.y[(size_t)a * nb + b]) * P.y_scale;
+        if (mode == PROJ_PLAIN_OUT) P.user_out[(size_t)a * nb + b] = to_s<typename Tr<T>::S>(out);
         else store_pair<T>(P.sino[dst_sel] + (size_t)a * P.SB + kSPad, b, out);
         v[0] = acc_prod(out, out);
     }
@@ -215,7 +223,7 @@ k_project(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int
 // fixed point (FP64 in the FP64 kernel), split into integer + fraction; each
 // pixel adds only its small in-tile offset.
 constexpr int kBand = 48;
-template <typename T> struct BpChunk { static constexpr int value = 16; };
+template <typename T> struct BpChunk { static constexpr int value = 16; };   // FP32 arithmetic
 template <> struct BpChunk<double> { static constexpr int value = 8; };   // 48 KB static limit
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
@@ -249,10 +257,11 @@ template <typename T, int NRHS>
 __global__ void __launch_bounds__(kBackThreads)
 k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int src0,
               int src1, int dst0, int dst1, int step) {
-    using T2 = typename Vec2<T>::type;
-    using Row = typename std::conditional<std::is_same<T, float>::value, BpRowF, BpRowD>::type;
-    constexpr bool kF32 = std::is_same<T, float>::value;
-    constexpr int kSlotsPerSeg = 16 / (int)sizeof(T2);
+    using S2 = typename Tr<T>::S2;
+    using C = typename Tr<T>::C;
+    using Row = typename std::conditional<std::is_same<C, float>::value, BpRowF, BpRowD>::type;
+    constexpr bool kF32 = std::is_same<C, float>::value;
+    constexpr int kSlotsPerSeg = 16 / (int)sizeof(S2);
     constexpr int kSegs = kBand / kSlotsPerSeg;       // 16-byte copies per band
     constexpr int kHalf = kTileH / 2;
     constexpr int kBpChunk = BpChunk<T>::value;
@@ -261,24 +270,24 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
     if (P.st->done) return;
     __shared__ Row rows[2][kBpChunk];
     __shared__ int slo[2][kBpChunk];            // first slot of each band in its sinogram row
-    __shared__ __align__(16) T2 band[2][NRHS][kBpChunk][kBand];
+    __shared__ __align__(16) S2 band[2][NRHS][kBpChunk][kBand];
     const int N = P.n, na = P.na, nb = P.nb, SB = P.SB;
     const int ti0 = it.u * kTileH, tj0 = it.v * kTileW;
     const int tx = threadIdx.x % kTileW, ty = threadIdx.x / kTileW;
     const int i1 = ti0 + ty, i2 = ti0 + ty + kHalf, j = tj0 + tx;
     const bool in1 = (i1 < N) && (j < N), in2 = (i2 < N) && (j < N);
     const int X2 = 2 * tj0 - (N - 1), Y2 = 2 * ti0 - (N - 1);
-    const T2* R[2] = {P.sino[src0], NRHS == 2 ? P.sino[src1] : P.sino[src0]};
+    const S2* R[2] = {P.sino[src0], NRHS == 2 ? P.sino[src1] : P.sino[src0]};
     const int nchunks = (na + kBpChunk - 1) / kBpChunk;
 
     auto stage_rows = [&](int ch) {
         const int q = threadIdx.x;
         const int a = ch * kBpChunk + q;
         if (q < kBpChunk && a < na) {
-            const Angle<T> g = P.ang[a];
+            const Angle<C> g = P.ang[a];
             // band: slots the tile can touch, from floor(projection of the origin)
             // + floor((kTileW-1) min(c, 0)) - 1, rounded down to a 16-byte boundary
-            const int lo = (int)tfloor(T(kTileW - 1) * tmin(g.c, T(0))) - 1;
+            const int lo = (int)tfloor(C(kTileW - 1) * tmin(g.c, C(0))) - 1;
             if constexpr (kF32) {
                 const long long cb = tile_origin_fx(g, X2, Y2, nb);
                 const int I = (int)(cb >> 32);
@@ -313,7 +322,7 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
             for (int sg = threadIdx.x; sg < cnt * kSegs; sg += blockDim.x) {
                 const int q = sg / kSegs, k = sg - q * kSegs;
                 const int slot = slo[ch & 1][q] + k * kSlotsPerSeg;
-                const T2* row = R[h] + (size_t)(a0 + q) * SB;
+                const S2* row = R[h] + (size_t)(a0 + q) * SB;
                 const bool ok = slot >= 0 && slot + kSlotsPerSeg <= SB;
                 cp_async16(&band[ch & 1][h][q][k * kSlotsPerSeg], ok ? row + slot : row, ok ? 16 : 0);
             }
@@ -321,7 +330,7 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
         cp_async_commit();
     };
 
-    T a1 = T(0), a2 = T(0), b1 = T(0), b2 = T(0);
+    C a1 = C(0), a2 = C(0), b1 = C(0), b2 = C(0);
     stage_rows(0);
     __syncthreads();
     stage_copy(0);
@@ -347,40 +356,40 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
                     const float f2 = __int_as_float(0x3F800000 | (((unsigned)p2 & 0xFFFFFFu) >> 1));
                     const float w10 = __saturatef(fmaf(-f1, g.kb, g.hb0p)), w11 = __saturatef(fmaf(f1, g.kb, g.hb1p));
                     const float w20 = __saturatef(fmaf(-f2, g.kb, g.hb0p)), w21 = __saturatef(fmaf(f2, g.kb, g.hb1p));
-                    const float2* bq = reinterpret_cast<const float2*>(&band[buf][0][q][0]);
-                    const float2 e1 = bq[p1 >> 24];
-                    const float2 e2 = bq[p2 >> 24];
+                    const S2* bq = &band[buf][0][q][0];
+                    const float2 e1 = to_c2(bq[p1 >> 24]);
+                    const float2 e2 = to_c2(bq[p2 >> 24]);
                     a1 = fmaf(g.inv_m, fmaf(w10, e1.x, w11 * e1.y), a1);
                     a2 = fmaf(g.inv_m, fmaf(w20, e2.x, w21 * e2.y), a2);
                     if (NRHS == 2) {
-                        const float2* zq = reinterpret_cast<const float2*>(&band[buf][NRHS - 1][q][0]);
-                        const float2 z1 = zq[p1 >> 24];
-                        const float2 z2 = zq[p2 >> 24];
+                        const S2* zq = &band[buf][NRHS - 1][q][0];
+                        const float2 z1 = to_c2(zq[p1 >> 24]);
+                        const float2 z2 = to_c2(zq[p2 >> 24]);
                         b1 = fmaf(g.inv_m, fmaf(w10, z1.x, w11 * z1.y), b1);
                         b2 = fmaf(g.inv_m, fmaf(w20, z2.x, w21 * z2.y), b2);
                     }
                 }
             } else {
-                const T dj = T(tx), di1 = T(ty), di2 = T(ty + kHalf);
+                const double dj = double(tx), di1 = double(ty), di2 = double(ty + kHalf);
                 for (int q = 0; q < cnt; ++q) {
                     const BpRowD& g = *reinterpret_cast<const BpRowD*>(&rows[buf][q]);
-                    const T djc = dj * g.c;
-                    const T v1 = g.frac + fma(di1, g.s, djc);
-                    const T v2 = g.frac + fma(di2, g.s, djc);
+                    const double djc = dj * g.c;
+                    const double v1 = g.frac + fma(di1, g.s, djc);
+                    const double v2 = g.frac + fma(di2, g.s, djc);
                     int q1, q2;
-                    const T f1 = v1 - floor_split(v1, q1);
-                    const T f2 = v2 - floor_split(v2, q2);
+                    const double f1 = v1 - floor_split(v1, q1);
+                    const double f2 = v2 - floor_split(v2, q2);
                     const unsigned k1 = min((unsigned)(q1 + g.rel), (unsigned)(kBand - 2));
                     const unsigned k2 = min((unsigned)(q2 + g.rel), (unsigned)(kBand - 2));
-                    const T w10 = sat(fma(-f1, g.kb, g.hb0)), w11 = sat(fma(f1, g.kb, g.hb1));
-                    const T w20 = sat(fma(-f2, g.kb, g.hb0)), w21 = sat(fma(f2, g.kb, g.hb1));
-                    const T2 e1 = band[buf][0][q][k1];
-                    const T2 e2 = band[buf][0][q][k2];
+                    const double w10 = sat(fma(-f1, g.kb, g.hb0)), w11 = sat(fma(f1, g.kb, g.hb1));
+                    const double w20 = sat(fma(-f2, g.kb, g.hb0)), w21 = sat(fma(f2, g.kb, g.hb1));
+                    const double2 e1 = to_c2(band[buf][0][q][k1]);
+                    const double2 e2 = to_c2(band[buf][0][q][k2]);
                     a1 = fma(g.inv_m, fma(w10, e1.x, w11 * e1.y), a1);
                     a2 = fma(g.inv_m, fma(w20, e2.x, w21 * e2.y), a2);
                     if (NRHS == 2) {
-                        const T2 z1 = band[buf][NRHS - 1][q][k1];
-                        const T2 z2 = band[buf][NRHS - 1][q][k2];
+                        const double2 z1 = to_c2(band[buf][NRHS - 1][q][k1]);
+                        const double2 z2 = to_c2(band[buf][NRHS - 1][q][k2]);
                         b1 = fma(g.inv_m, fma(w10, z1.x, w11 * z1.y), b1);
                         b2 = fma(g.inv_m, fma(w20, z2.x, w21 * z2.y), b2);
                     }
@@ -389,14 +398,17 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
         }
         __syncthreads();
     }
+    using S = typename Tr<T>::S;
     const size_t idx1 = (size_t)i1 * N + j, idx2 = (size_t)i2 * N + j;
+    // the dots below use the stored (rounded) values
+    a1 = rnd<T>(a1); a2 = rnd<T>(a2); b1 = rnd<T>(b1); b2 = rnd<T>(b2);
     if (in1) {
-        P.img[dst0][idx1] = a1;
-        if (NRHS == 2) P.img[dst1][idx1] = b1;
+        P.img[dst0][idx1] = to_s<S>(a1);
+        if (NRHS == 2) P.img[dst1][idx1] = to_s<S>(b1);
     }
     if (in2) {
-        P.img[dst0][idx2] = a2;
-        if (NRHS == 2) P.img[dst1][idx2] = b2;
+        P.img[dst0][idx2] = to_s<S>(a2);
+        if (NRHS == 2) P.img[dst1][idx2] = to_s<S>(b2);
     }
     if (step == FIN_NONE) return;
     Acc<T> v[3];
@@ -406,13 +418,13 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
         const bool in = h ? in2 : in1;
         if (!in) continue;
         const size_t idx = h ? idx2 : idx1;
-        const T g0 = h ? a2 : a1, g1 = h ? b2 : b1;
+        const C g0 = h ? a2 : a1, g1 = h ? b2 : b1;
         if (step == FIN_BETA) {
-            v[0] = acc_add(v[0], acc_prod(NRHS == 2 ? g1 : g0, P.img[IB_H][idx]));  // g'^T h (z'^T h)
-            v[1] = acc_add(v[1], acc_prod(g0, g0));                                 // ||g'||^2
-            v[2] = acc_add(v[2], acc_prod(g0, P.img[IB_P][idx]));                   // g'^T p
+            v[0] = acc_add(v[0], acc_prod(NRHS == 2 ? g1 : g0, to_c(P.img[IB_H][idx])));  // g'^T h (z'^T h)
+            v[1] = acc_add(v[1], acc_prod(g0, g0));                                       // ||g'||^2
+            v[2] = acc_add(v[2], acc_prod(g0, to_c(P.img[IB_P][idx])));                   // g'^T p
         } else if (step == FIN_ALPHA || step == FIN_CG_ALPHA) {
-            v[0] = acc_add(v[0], acc_prod(P.img[IB_P][idx], g0));                   // p^T h
+            v[0] = acc_add(v[0], acc_prod(to_c(P.img[IB_P][idx]), g0));                   // p^T h
         } else if (step == FIN_CG_DELTA) {
             v[0] = acc_add(v[0], acc_prod(g0, g0));                                 // ||g||^2
             v[1] = acc_add(v[1], acc_prod(g0, g1));                                 // g^T z
@@ -426,8 +438,8 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
 // element is written into its own slot and the previous slot's second half).
 // `val` is this thread's pixel value (ignored outside the image).
 template <typename T>
-__device__ __forceinline__ void write_views(const Prob<T>& P, int ti, int tj, T val, bool in) {
-    __shared__ T tile[kTileH][kTileW + 1];
+__device__ __forceinline__ void write_views(const Prob<T>& P, int ti, int tj, typename Tr<T>::C val, bool in) {
+    __shared__ typename Tr<T>::C tile[kTileH][kTileW + 1];
     const int ty = threadIdx.x / kTileW, tx = threadIdx.x % kTileW;
     const int i = ti * kTileH + ty, j = tj * kTileW + tx;
     if (in) store_pair<T>(P.view_rm + (size_t)i * P.S + kPad, j, val);
@@ -451,83 +463,87 @@ k_vec(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int op,
     const int j = it.v * kTileW + threadIdx.x % kTileW;
     const bool in = (i < N) && (j < N);
     const size_t idx = (size_t)i * N + j;
+    using C = typename Tr<T>::C;
+    using S = typename Tr<T>::S;
+    // every value written is rounded to storage first (rnd: identity for
+    // float/double), and the dots use the stored value
     Acc<T> v[2];
     acc_zero(v[0]);
     acc_zero(v[1]);
-    T val = T(0);
+    C val = C(0);
     switch (op) {
     case VEC_INIT: {            // X = XH = x0 (AUX, or zeros), views of X
-        const T* src = P.img[IB_AUX];
+        const S* src = P.img[IB_AUX];
         if (in) {
-            val = src ? src[idx] : T(0);
-            P.img[IB_X][idx] = val;
-            if (P.img[IB_XH]) P.img[IB_XH][idx] = val;
+            val = src ? to_c(src[idx]) : C(0);
+            P.img[IB_X][idx] = to_s<S>(val);
+            if (P.img[IB_XH]) P.img[IB_XH][idx] = to_s<S>(val);
         }
         write_views(P, it.u, it.v, val, in);
         break;
     }
     case VEC_VIEWS: {           // views of img[sel]
-        if (in) val = P.img[sel][idx];
+        if (in) val = to_c(P.img[sel][idx]);
         write_views(P, it.u, it.v, val, in);
         break;
     }
     case VEC_PERTURB: {         // x_{k+1/2} = x_k + coef * dTV(x_k), views
-        const T coef = (T)st.coef;
+        const C coef = (C)st.coef;
         if (in) {
-            const T x = P.img[IB_X][idx];
-            val = (st.accepted == 1) ? fma_rn(coef, P.img[IB_TVG][idx], x) : x;
-            P.img[IB_XH][idx] = val;
+            const C x = to_c(P.img[IB_X][idx]);
+            val = (st.accepted == 1) ? rnd<T>(fma_rn(coef, to_c(P.img[IB_TVG][idx]), x)) : x;
+            P.img[IB_XH][idx] = to_s<S>(val);
         }
         write_views(P, it.u, it.v, val, in);
         break;
     }
     case VEC_FORM_P: {          // p' = -d + beta p (d = g' or z'), views; S0 = g'^T p'
-        const T beta = (T)st.beta;
+        const C beta = (C)st.beta;
         if (in) {
-            const T d = P.img[sel][idx];
-            val = fma(beta, P.img[IB_P][idx], -d);
-            P.img[IB_P][idx] = val;
-            v[0] = acc_prod(P.img[IB_G][idx], val);
+            const C d = to_c(P.img[sel][idx]);
+            val = rnd<T>(fma(beta, to_c(P.img[IB_P][idx]), -d));
+            P.img[IB_P][idx] = to_s<S>(val);
+            v[0] = acc_prod(to_c(P.img[IB_G][idx]), val);
         }
         write_views(P, it.u, it.v, val, in);
         break;
     }
     case VEC_FORM_P0: {         // p_0 = -d (first direction), views; S0 = g^T p_0
         if (in) {
-            val = -P.img[sel][idx];
-            P.img[IB_P][idx] = val;
-            v[0] = acc_prod(P.img[IB_G][idx], val);
+            val = -to_c(P.img[sel][idx]);
+            P.img[IB_P][idx] = to_s<S>(val);
+            v[0] = acc_prod(to_c(P.img[IB_G][idx]), val);
         }
         write_views(P, it.u, it.v, val, in);
         break;
     }
     case VEC_FORM_P_NOVIEW: {   // p' = -d + beta p without views (last CG-K step unused)
-        const T beta = (T)st.beta;
+        const C beta = (C)st.beta;
         if (in) {
-            const T d = P.img[sel][idx];
-            val = fma(beta, P.img[IB_P][idx], -d);
-            P.img[IB_P][idx] = val;
-            v[0] = acc_prod(P.img[IB_G][idx], val);
+            const C d = to_c(P.img[sel][idx]);
+            val = rnd<T>(fma(beta, to_c(P.img[IB_P][idx]), -d));
+            P.img[IB_P][idx] = to_s<S>(val);
+            v[0] = acc_prod(to_c(P.img[IB_G][idx]), val);
         }
         break;
     }
     case VEC_CG_UPDATE: {       // x' = base + alpha p, g' = g + alpha h; S0 = ||g'||^2, S1 = g'^T z
-        const T alpha = (T)st.alpha;
+        const C alpha = (C)st.alpha;
         if (in) {
-            const T base = P.img[sel][idx];
-            P.img[IB_X][idx] = fma(alpha, P.img[IB_P][idx], base);
-            const T gn = fma(alpha, P.img[IB_H][idx], P.img[IB_G][idx]);
-            P.img[IB_G][idx] = gn;
+            const C base = to_c(P.img[sel][idx]);
+            P.img[IB_X][idx] = to_s<S>(fma(alpha, to_c(P.img[IB_P][idx]), base));
+            const C gn = rnd<T>(fma(alpha, to_c(P.img[IB_H][idx]), to_c(P.img[IB_G][idx])));
+            P.img[IB_G][idx] = to_s<S>(gn);
             v[0] = acc_prod(gn, gn);
-            if (P.img[IB_Z]) v[1] = acc_prod(gn, P.img[IB_Z][idx]);
+            if (P.img[IB_Z]) v[1] = acc_prod(gn, to_c(P.img[IB_Z][idx]));
         }
         break;
     }
     case VEC_DOTS_RESUME: {     // S0 = p^T h, S1 = g^T p
         if (in) {
-            const T p = P.img[IB_P][idx];
-            if (P.img[IB_H]) v[0] = acc_prod(p, P.img[IB_H][idx]);
-            if (P.img[IB_G]) v[1] = acc_prod(p, P.img[IB_G][idx]);
+            const C p = to_c(P.img[IB_P][idx]);
+            if (P.img[IB_H]) v[0] = acc_prod(p, to_c(P.img[IB_H][idx]));
+            if (P.img[IB_G]) v[1] = acc_prod(p, to_c(P.img[IB_G][idx]));
         }
         break;
     }
@@ -552,22 +568,25 @@ k_tvgrad(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int 
     const Prob<T>& P = probs[it.prob];
     const DevState& st = *P.st;
     if (st.done) return;
-    __shared__ T xs[kTileH + 2][kTileW + 3];
-    __shared__ T tu[kTileH + 1][kTileW + 2];
-    __shared__ T tv[kTileH + 1][kTileW + 2];
+    using C = typename Tr<T>::C;
+    using S = typename Tr<T>::S;
+    __shared__ C xs[kTileH + 2][kTileW + 3];
+    __shared__ C tu[kTileH + 1][kTileW + 2];
+    __shared__ C tv[kTileH + 1][kTileW + 2];
     const int N = P.n;
     const int i0 = it.u * kTileH - 1, j0 = it.v * kTileW - 1;     // smem origin
-    const T alpha = (T)st.alpha;
-    const T* XH = P.img[IB_XH];
-    const T* PP = P.img[IB_P];
-    const T* SRC = P.img[src];
+    const C alpha = (C)st.alpha;
+    const S* XH = P.img[IB_XH];
+    const S* PP = P.img[IB_P];
+    const S* SRC = P.img[src];
     for (int q = threadIdx.x; q < (kTileH + 2) * (kTileW + 2); q += kTileThreads) {
         const int ii = q / (kTileW + 2), jj = q % (kTileW + 2);
         const int gi = i0 + ii, gj = j0 + jj;
-        T val = T(0);
+        C val = C(0);
         if (gi >= 0 && gi < N && gj >= 0 && gj < N) {
             const size_t g = (size_t)gi * N + gj;
-            val = fuse_update ? fma(alpha, PP[g], XH[g]) : SRC[g];
+            // the fused x_{k+1} is rounded to storage: the stencil sees the stored x
+            val = fuse_update ? rnd<T>(fma(alpha, to_c(PP[g]), to_c(XH[g]))) : to_c(SRC[g]);
         }
         xs[ii][jj] = val;
     }
@@ -577,12 +596,12 @@ k_tvgrad(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int 
     for (int q = threadIdx.x; q < (kTileH + 1) * (kTileW + 1); q += kTileThreads) {
         const int ii = q / (kTileW + 1), jj = q % (kTileW + 1);
         const int gi = i0 + ii, gj = j0 + jj;
-        T a = T(0), c = T(0);
+        C a = C(0), c = C(0);
         if (gi >= 0 && gi < N - 1 && gj >= 0 && gj < N - 1) {
-            const T x0 = xs[ii][jj];
-            const T du = xs[ii + 1][jj] - x0, dv = xs[ii][jj + 1] - x0;
-            const T nrm = tsqrt(du * du + dv * dv);
-            if (nrm > T(0)) { a = du / nrm; c = dv / nrm; }
+            const C x0 = xs[ii][jj];
+            const C du = xs[ii + 1][jj] - x0, dv = xs[ii][jj + 1] - x0;
+            const C nrm = tsqrt(du * du + dv * dv);
+            if (nrm > C(0)) { a = du / nrm; c = dv / nrm; }
         }
         tu[ii][jj] = a;
         tv[ii][jj] = c;
@@ -594,14 +613,14 @@ k_tvgrad(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int 
     acc_zero(v[0]); acc_zero(v[1]); acc_zero(v[2]);
     if (in) {
         const size_t g = (size_t)i * N + j;
-        const T x = xs[ty + 1][tx + 1];
-        if (fuse_update) P.img[IB_X][g] = x;
+        const C x = xs[ty + 1][tx + 1];
+        if (fuse_update) P.img[IB_X][g] = to_s<S>(x);
         if (i < N - 1 && j < N - 1) {         // this tile's own term (i, j)
-            const T du = xs[ty + 2][tx + 1] - x, dv = xs[ty + 1][tx + 2] - x;
+            const C du = xs[ty + 2][tx + 1] - x, dv = xs[ty + 1][tx + 2] - x;
             v[0] = acc_val(tsqrt(du * du + dv * dv));
         }
-        const T gr = -(tu[ty + 1][tx + 1] + tv[ty + 1][tx + 1]) + tu[ty][tx + 1] + tv[ty + 1][tx];
-        if (write_grad) P.img[IB_TVG][g] = gr;
+        const C gr = rnd<T>(-(tu[ty + 1][tx + 1] + tv[ty + 1][tx + 1]) + tu[ty][tx + 1] + tv[ty + 1][tx]);
+        if (write_grad) P.img[IB_TVG][g] = to_s<S>(gr);
         v[1] = acc_prod(gr, gr);
         v[2] = acc_prod(x, x);
     }
@@ -617,6 +636,8 @@ template <typename T>
 __global__ void __launch_bounds__(kTileThreads)
 k_trial(const Prob<T>* __restrict__ probs, const Item* __restrict__ items) {
     using A = Acc<T>;
+    using C = typename Tr<T>::C;
+    using S = typename Tr<T>::S;
     constexpr int NS = kTrials + 1;                 // 31 candidates + x itself
     constexpr int NW = kTileThreads / 32;
     const Item it = decode_item(probs, items, 1);
@@ -624,22 +645,22 @@ k_trial(const Prob<T>* __restrict__ probs, const Item* __restrict__ items) {
     const DevState& st = *P.st;
     if (st.done || st.accepted != 0) return;
     __shared__ A wsum[NW][NS];
-    __shared__ T coef_s[kTrials];
+    __shared__ C coef_s[kTrials];
     __shared__ unsigned s_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x < kTrials) coef_s[threadIdx.x] = (T)st.trial_coef[threadIdx.x];
+    if (threadIdx.x < kTrials) coef_s[threadIdx.x] = (C)st.trial_coef[threadIdx.x];
     __syncthreads();
     const int N = P.n;
     const int i = it.u * kTileH + threadIdx.x / kTileW;
     const int j = it.v * kTileW + threadIdx.x % kTileW;
     const bool in = (i < N - 1) && (j < N - 1);
-    T x0 = T(0), xu = T(0), xv = T(0), q0 = T(0), qu = T(0), qv = T(0);
+    C x0 = C(0), xu = C(0), xv = C(0), q0 = C(0), qu = C(0), qv = C(0);
     if (in) {
-        const T* X = P.img[IB_X];
-        const T* G = P.img[IB_TVG];
+        const S* X = P.img[IB_X];
+        const S* G = P.img[IB_TVG];
         const size_t g0 = (size_t)i * N + j;
-        x0 = X[g0]; xu = X[g0 + N]; xv = X[g0 + 1];
-        q0 = G[g0]; qu = G[g0 + N]; qv = G[g0 + 1];
+        x0 = to_c(X[g0]); xu = to_c(X[g0 + N]); xv = to_c(X[g0 + 1]);
+        q0 = to_c(G[g0]); qu = to_c(G[g0 + N]); qv = to_c(G[g0 + 1]);
     }
 #pragma unroll
     for (int grp = 0; grp < NS / 8; ++grp) {
@@ -647,15 +668,17 @@ k_trial(const Prob<T>* __restrict__ probs, const Item* __restrict__ items) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const int t = grp * 8 + k;
-            T du, dv;
+            C du, dv;
             if (t < kTrials) {
-                const T c = coef_s[t];
-                const T z0 = fma_rn(c, q0, x0), zu = fma_rn(c, qu, xu), zv = fma_rn(c, qv, xv);
+                // trial points as they would be stored (VEC_PERTURB rounds the same way)
+                const C c = coef_s[t];
+                const C z0 = rnd<T>(fma_rn(c, q0, x0)), zu = rnd<T>(fma_rn(c, qu, xu)),
+                        zv = rnd<T>(fma_rn(c, qv, xv));
                 du = zu - z0; dv = zv - z0;
             } else {
                 du = xu - x0; dv = xv - x0;
             }
-            v[k] = acc_val(in ? tsqrt(du * du + dv * dv) : T(0));
+            v[k] = acc_val(in ? tsqrt(du * du + dv * dv) : C(0));
         }
 #pragma unroll
         for (int k = 0; k < 8; ++k) v[k] = warp_sum<true>(v[k]);
@@ -723,7 +746,8 @@ k_sino_axpy(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, i
         const size_t o = (size_t)a * P.SB + kSPad;
         // reads the first half of slot b, writes it and the second half of
         // slot b-1: no other thread touches those words
-        const T r = fma((T)st.alpha, P.sino[SB_Q][o + b].x, P.sino[SB_R][o + b].x);
+        using C = typename Tr<T>::C;
+        const C r = rnd<T>(fma((C)st.alpha, to_c(P.sino[SB_Q][o + b].x), to_c(P.sino[SB_R][o + b].x)));
         store_pair<T>(P.sino[SB_R] + o, b, r);
         v[0] = acc_prod(r, r);
     }
@@ -737,7 +761,7 @@ k_sino_pairs(const Prob<T>* __restrict__ probs, int dst) {
     const Prob<T>& P = probs[0];
     const int a = blockIdx.x / P.ray_blocks, b = (blockIdx.x % P.ray_blocks) * kRayBlock + threadIdx.x;
     if (b < P.nb)
-        store_pair<T>(P.sino[dst] + (size_t)a * P.SB + kSPad, b, P.user_in[(size_t)a * P.nb + b]);
+        store_pair<T>(P.sino[dst] + (size_t)a * P.SB + kSPad, b, to_c(P.user_in[(size_t)a * P.nb + b]));
 }
 
 // ---------------------------------------------------------------------------
@@ -752,32 +776,33 @@ k_filter(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int 
     const Item it = decode_item(probs, items, 2);
     const Prob<T>& P = probs[it.prob];
     if (P.st->done) return;
+    using C = typename Tr<T>::C;
     extern __shared__ unsigned char smem_raw[];
-    T* row = reinterpret_cast<T*>(smem_raw);
-    T* taps = row + P.nb;
+    C* row = reinterpret_cast<C*>(smem_raw);
+    C* taps = row + P.nb;
     const int nb = P.nb, a = it.u;
     if (plain) {
-        const T* R = P.user_in + (size_t)a * nb;
-        for (int q = threadIdx.x; q < nb; q += blockDim.x) row[q] = R[q];
+        const typename Tr<T>::S* R = P.user_in + (size_t)a * nb;
+        for (int q = threadIdx.x; q < nb; q += blockDim.x) row[q] = to_c(R[q]);
     } else {
-        const typename Vec2<T>::type* R = P.sino[src] + (size_t)a * P.SB + kSPad;
-        for (int q = threadIdx.x; q < nb; q += blockDim.x) row[q] = R[q].x;
+        const typename Tr<T>::S2* R = P.sino[src] + (size_t)a * P.SB + kSPad;
+        for (int q = threadIdx.x; q < nb; q += blockDim.x) row[q] = to_c(R[q].x);
     }
     for (int q = threadIdx.x; q < 2 * nb - 1; q += blockDim.x) taps[q] = P.taps[q];
     __syncthreads();
     const int b = it.v * kFilterBlock + threadIdx.x;
     if (b >= nb) return;
     // taps[nb - 1 + k] = h[k]
-    const T* tb = taps + (nb - 1) + b;
-    T acc0 = T(0), acc1 = T(0);
+    const C* tb = taps + (nb - 1) + b;
+    C acc0 = C(0), acc1 = C(0);
     int q = 0;
     for (; q + 1 < nb; q += 2) {
         acc0 = fma(tb[-q], row[q], acc0);
         acc1 = fma(tb[-q - 1], row[q + 1], acc1);
     }
     if (q < nb) acc0 = fma(tb[-q], row[q], acc0);
-    const T out = acc0 + acc1;
-    if (plain) P.user_out[(size_t)a * nb + b] = out;
+    const C out = acc0 + acc1;
+    if (plain) P.user_out[(size_t)a * nb + b] = to_s<typename Tr<T>::S>(out);
     else store_pair<T>(P.sino[dst] + (size_t)a * P.SB + kSPad, b, out);
 }
 
@@ -829,8 +854,22 @@ template <typename T>
 void launch_set_done(const Prob<T>* d, int count, int value, cudaStream_t s) {
     k_set_done<T><<<(count + 127) / 128, 128, 0, s>>>(d, count, value);
 }
-template void launch_set_done<float>(const Prob<float>*, int, int, cudaStream_t);
-template void launch_set_done<double>(const Prob<double>*, int, int, cudaStream_t);
+
+// Serving: stop flags of the listed problem slots, gathered (out[i] = done of
+// slots[i]) or set (done = value).
+template <typename T>
+__global__ void k_slots_done(const Prob<T>* probs, const int* slots, int count, int* out, int set, int value) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    DevState* st = probs[slots[i]].st;
+    if (set) st->done = value;
+    else out[i] = st->done;
+}
+template <typename T>
+void launch_slots_done(const Prob<T>* d, const int* slots, int count, int* out, int set, int value,
+                       cudaStream_t s) {
+    if (count > 0) k_slots_done<T><<<(count + 127) / 128, 128, 0, s>>>(d, slots, count, out, set, value);
+}
 
 // Batched loop condition: continue while any problem is still running, and
 // never past max_bodies bodies.
@@ -854,8 +893,6 @@ template <typename T>
 void launch_loop_cond_batch(const Prob<T>* d, BatchState* bs, cudaGraphConditionalHandle h, cudaStream_t s) {
     k_loop_cond_batch<T><<<1, 256, 0, s>>>(d, bs, h);
 }
-template void launch_loop_cond_batch<float>(const Prob<float>*, BatchState*, cudaGraphConditionalHandle, cudaStream_t);
-template void launch_loop_cond_batch<double>(const Prob<double>*, BatchState*, cudaGraphConditionalHandle, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Host launchers.
@@ -895,7 +932,7 @@ void launch_sino_axpy(const Prob<T>* d, const Item* items, int grid, int step, c
 template <typename T>
 cudaError_t launch_filter(const Prob<T>* d, const Item* items, int grid, int max_nb, int src,
                           int dst, int plain, cudaStream_t s) {
-    size_t smem = (size_t)(3 * max_nb) * sizeof(T);
+    size_t smem = (size_t)(3 * max_nb) * sizeof(typename Tr<T>::C);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_filter<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
@@ -920,10 +957,17 @@ void launch_taps(T* taps, int nb, int P, double mu, double gain, cudaStream_t s)
     template void launch_sino_axpy<T>(const Prob<T>*, const Item*, int, int, cudaStream_t);       \
     template cudaError_t launch_filter<T>(const Prob<T>*, const Item*, int, int, int, int, int,   \
                                           cudaStream_t);                                          \
-    template void launch_taps<T>(T*, int, int, double, double, cudaStream_t);                    \
-    template void launch_sino_pairs<T>(const Prob<T>*, int, int, cudaStream_t);
+    template void launch_sino_pairs<T>(const Prob<T>*, int, int, cudaStream_t);                   \
+    template void launch_set_done<T>(const Prob<T>*, int, int, cudaStream_t);                     \
+    template void launch_slots_done<T>(const Prob<T>*, const int*, int, int*, int, int, cudaStream_t); \
+    template void launch_loop_cond_batch<T>(const Prob<T>*, BatchState*, cudaGraphConditionalHandle, \
+                                            cudaStream_t);
 
 SCG_INSTANTIATE(float)
 SCG_INSTANTIATE(double)
+SCG_INSTANTIATE(__half)
+SCG_INSTANTIATE(__nv_bfloat16)
+template void launch_taps<float>(float*, int, int, double, double, cudaStream_t);
+template void launch_taps<double>(double*, int, int, double, double, cudaStream_t);
 
 }  // namespace scg

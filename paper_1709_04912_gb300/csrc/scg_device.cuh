@@ -3,7 +3,9 @@
 // every kernel of libscg.
 //
 // Layout in HBM (one "problem" = one reconstruction):
-//   image vectors      N*N, row-major, element type T (float or double)
+//   image vectors      N*N, row-major, element type S: float or double, or
+//                      half / bfloat16 storage with FP32 arithmetic
+//                      (Tr<T> below gives S and the arithmetic type C)
 //   projector views    two zero-padded copies of the image being projected, in
 //                      "pair" layout (slot q of a line holds elements q and
 //                      q+1, so the two pixels a ray meets in one strip are one
@@ -20,6 +22,8 @@
 //                      by the last item of a launch (no atomics on data).
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -127,9 +131,51 @@ template <typename T> struct Vec2;
 template <> struct Vec2<float> { using type = float2; };
 template <> struct Vec2<double> { using type = double2; };
 
+// Storage type S (and its pair S2) and arithmetic type C of a precision T:
+// float and double compute in themselves; half and bfloat16 are storage
+// formats whose values every kernel widens to FP32 on load and rounds to
+// nearest on store (reductions stay double-float, scalars FP64).
+template <typename T> struct Tr {
+    using S = T;
+    using S2 = typename Vec2<T>::type;
+    using C = T;
+};
+template <> struct Tr<__half> {
+    using S = __half;
+    using S2 = __half2;
+    using C = float;
+};
+template <> struct Tr<__nv_bfloat16> {
+    using S = __nv_bfloat16;
+    using S2 = __nv_bfloat162;
+    using C = float;
+};
+
+__device__ __forceinline__ float to_c(float v) { return v; }
+__device__ __forceinline__ double to_c(double v) { return v; }
+__device__ __forceinline__ float to_c(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_c(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float2 to_c2(float2 v) { return v; }
+__device__ __forceinline__ double2 to_c2(double2 v) { return v; }
+__device__ __forceinline__ float2 to_c2(__half2 v) { return __half22float2(v); }
+__device__ __forceinline__ float2 to_c2(__nv_bfloat162 v) { return __bfloat1622float2(v); }
+template <typename S> __device__ __forceinline__ S to_s(typename Tr<S>::C v);
+template <> __device__ __forceinline__ float to_s<float>(float v) { return v; }
+template <> __device__ __forceinline__ double to_s<double>(double v) { return v; }
+template <> __device__ __forceinline__ __half to_s<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 to_s<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+// v rounded to the storage format and widened back (identity for float/double)
+template <typename T>
+__device__ __forceinline__ typename Tr<T>::C rnd(typename Tr<T>::C v) {
+    if constexpr (std::is_same<typename Tr<T>::S, typename Tr<T>::C>::value) return v;
+    else return to_c(to_s<typename Tr<T>::S>(v));
+}
+
 template <typename T>
 struct Prob {
-    using T2 = typename Vec2<T>::type;
+    using elem_t = typename Tr<T>::S;     // storage element
+    using pair_t = typename Tr<T>::S2;    // storage pair
+    using calc_t = typename Tr<T>::C;     // arithmetic
     int n, na, nb;
     int S;                  // image-view line stride (elements)
     int SB;                 // sinogram-view row stride (elements)
@@ -139,16 +185,17 @@ struct Prob {
     int ray_blocks;         // projector items per angle
     int filt_blocks;        // filter items per row
     int P;                  // filter length (power of two >= 2 nb)
-    T off_n, off_b;         // (N-1)/2, (nb-1)/2
-    const Angle<T>* ang;
-    const T* y;             // data [na][nb]
-    T* img[IB_COUNT];
-    T2* sino[SB_COUNT];     // pair views of the sinogram-sized vectors
-    T2* view_rm;
-    T2* view_cm;
-    const T* user_in;       // caller's plain sinogram (operator entry points)
-    T* user_out;
-    const T* taps;          // Toeplitz filter taps h[-(nb-1) .. nb-1]
+    calc_t off_n, off_b;    // (N-1)/2, (nb-1)/2
+    calc_t y_scale;         // scale c of the solved system c A x ~ c y (a power of two; see Angle.inv_m)
+    const Angle<calc_t>* ang;
+    const elem_t* y;        // data [na][nb]
+    elem_t* img[IB_COUNT];
+    pair_t* sino[SB_COUNT]; // pair views of the sinogram-sized vectors
+    pair_t* view_rm;
+    pair_t* view_cm;
+    const elem_t* user_in;  // caller's plain sinogram (operator entry points)
+    elem_t* user_out;
+    const calc_t* taps;     // Toeplitz filter taps h[-(nb-1) .. nb-1]
     double* partials;
     unsigned* counter;
     DevState* st;
@@ -199,10 +246,12 @@ __device__ __forceinline__ double floor_split(double v, int& i) {
 // Store element b of a pair-layout row (row points at the slot of element 0):
 // slot b holds (e[b], e[b+1]), so e[b] is written twice.
 template <typename T>
-__device__ __forceinline__ void store_pair(typename Vec2<T>::type* row, int b, T v) {
-    T* e = reinterpret_cast<T*>(row);
-    e[2 * b] = v;
-    e[2 * b - 1] = v;
+__device__ __forceinline__ void store_pair(typename Tr<T>::S2* row, int b, typename Tr<T>::C v) {
+    using S = typename Tr<T>::S;
+    S* e = reinterpret_cast<S*>(row);
+    const S w = to_s<S>(v);
+    e[2 * b] = w;
+    e[2 * b - 1] = w;
 }
 
 // ---------------------------------------------------------------------------
@@ -231,6 +280,8 @@ __device__ __forceinline__ DF df_add(DF a, DF b) {
 template <typename T> struct AccOf;
 template <> struct AccOf<float> { using type = DF; };
 template <> struct AccOf<double> { using type = double; };
+template <> struct AccOf<__half> { using type = DF; };
+template <> struct AccOf<__nv_bfloat16> { using type = DF; };
 template <typename T> using Acc = typename AccOf<T>::type;
 
 __device__ __forceinline__ void acc_zero(DF& a) { a.hi = 0.f; a.lo = 0.f; }

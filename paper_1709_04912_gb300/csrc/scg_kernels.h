@@ -45,6 +45,9 @@ void launch_loop_cond(DevState* st, cudaGraphConditionalHandle h, cudaStream_t s
 template <typename T>
 void launch_set_done(const Prob<T>* d, int count, int value, cudaStream_t s);
 template <typename T>
+void launch_slots_done(const Prob<T>* d, const int* slots, int count, int* out, int set, int value,
+                       cudaStream_t s);
+template <typename T>
 void launch_loop_cond_batch(const Prob<T>* d, BatchState* bs, cudaGraphConditionalHandle h, cudaStream_t s);
 
 }  // namespace scg

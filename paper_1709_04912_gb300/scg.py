@@ -14,7 +14,7 @@ import torch
 
 from . import build as _build
 
-F64, F32 = 0, 1
+F64, F32, F16, BF16 = 0, 1, 2, 3
 VARIANTS = {"CG": 0, "PCG": 1, "S-CG": 2, "S-CG-CD": 3, "S-CG-K": 4, "S-PCG": 5, "S-PCG-K": 6}
 PERTURB = {"none": 0, "gamma": 1}
 STATUS = {0: "ok", 1: "max_iter", -1: "invalid", -2: "cuda", -3: "workspace", -4: "breakdown",
@@ -50,6 +50,16 @@ class Result(ctypes.Structure):
 class Problem(ctypes.Structure):
     _fields_ = [("geometry", Geometry), ("eps", ctypes.c_double), ("y", ctypes.c_void_p),
                 ("x0", ctypes.c_void_p), ("x_out", ctypes.c_void_p)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("precision", ctypes.c_int), ("params", Params),
+                ("pool", ctypes.c_void_p), ("pool_bytes", ctypes.c_size_t),
+                ("max_active", ctypes.c_int), ("bodies_per_step", ctypes.c_int)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_ulonglong), ("result", Result)]
 
 
 class State(ctypes.Structure):
@@ -97,8 +107,16 @@ def load(build_if_needed: bool = True):
     L.scg_batch_workspace_bytes.restype = sz
     L.scg_batch_workspace_bytes.argtypes = [pp, i, i, i]
     L.scg_solve_batch.argtypes = [pp, i, i, i, ctypes.POINTER(Params), vp, sz, ctypes.POINTER(Result), vp]
+    L.scg_server_footprint.restype = sz
+    L.scg_server_footprint.argtypes = [gp, i, i]
+    L.scg_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
+    L.scg_server_submit.argtypes = [vp, pp, ctypes.c_ulonglong]
+    L.scg_server_step.argtypes = [vp, vp, ctypes.POINTER(Completion), i, ctypes.POINTER(i)]
+    L.scg_server_pending.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i)]
+    L.scg_server_destroy.argtypes = [vp]
     for name in ("scg_project", "scg_backproject", "scg_tv", "scg_tv_grad", "scg_filter", "scg_solve",
-                 "scg_solve_batch"):
+                 "scg_solve_batch", "scg_server_create", "scg_server_submit", "scg_server_step",
+                 "scg_server_pending", "scg_server_destroy"):
         getattr(L, name).restype = i
     _lib = L
     return L
@@ -110,12 +128,15 @@ def _check(rc: int, what: str, ok=(0,)):
         raise ScgError(f"{what} failed: {rc} ({msg})")
 
 
+def _prec_of(dtype) -> int:
+    p = {torch.float64: F64, torch.float32: F32, torch.float16: F16, torch.bfloat16: BF16}.get(dtype)
+    if p is None:
+        raise ScgError(f"unsupported dtype {dtype}")
+    return p
+
+
 def _prec(t: torch.Tensor) -> int:
-    if t.dtype == torch.float64:
-        return F64
-    if t.dtype == torch.float32:
-        return F32
-    raise ScgError(f"unsupported dtype {t.dtype}")
+    return _prec_of(t.dtype)
 
 
 def _dev_ptr(t: torch.Tensor, name: str) -> int:
@@ -349,7 +370,7 @@ def batch_workspace_bytes(shapes, variant: str = "S-CG", dtype=torch.float32) ->
     arr = (Problem * len(shapes))()
     for q, (n, na, nbins) in enumerate(shapes):
         arr[q].geometry = geometry(n, na, nbins)
-    prec = F64 if dtype == torch.float64 else F32
+    prec = _prec_of(dtype)
     return int(load().scg_batch_workspace_bytes(arr, len(shapes), VARIANTS[variant], prec))
 
 
@@ -385,3 +406,83 @@ def scg_solve_batch(ys, ns, variant: str = "S-CG", eps=1.0, x0s=None, outs=None,
     return [SolveResult(outs[q], r.iters, r.k_final, STATUS.get(r.status, str(r.status)), r.status,
                         r.f_final, r.tv_final, r.ell, r.gamma0_used, r.kernel_launches,
                         r.body_launches, r.device_loop) for q, r in enumerate(res)]
+
+
+def server_footprint(n: int, n_angles: int, n_bins: int, variant: str = "S-CG",
+                     dtype=torch.float32) -> int:
+    """Pool bytes one resident request of this geometry holds (scg_server_footprint)."""
+    g = geometry(n, n_angles, n_bins)
+    prec = _prec_of(dtype)
+    return int(load().scg_server_footprint(ctypes.byref(g), VARIANTS[variant], prec))
+
+
+def _result(r: Result, x) -> SolveResult:
+    return SolveResult(x, r.iters, r.k_final, STATUS.get(r.status, str(r.status)), r.status, r.f_final,
+                       r.tv_final, r.ell, r.gamma0_used, r.kernel_launches, r.body_launches,
+                       r.device_loop)
+
+
+class Server:
+    """Continuous-batching request server (scg_server_*).  The pool is one
+    device tensor of ``pool_bytes``; submitted tensors are kept alive until
+    their completion is returned by :meth:`step`."""
+
+    def __init__(self, variant: str = "S-CG", dtype=torch.float32, pool_bytes: int = 1 << 30,
+                 max_active: int = 64, bodies_per_step: int = 1, device="cuda:0", **params):
+        L = load()
+        self.variant, self.dtype, self.device = variant, dtype, torch.device(device)
+        self.pool = torch.empty(int(pool_bytes), dtype=torch.uint8, device=self.device)
+        cfg = ServerConfig(VARIANTS[variant], _prec_of(dtype),
+                           _params(default_params(**params)), self.pool.data_ptr(), self.pool.numel(),
+                           int(max_active), int(bodies_per_step))
+        h = ctypes.c_void_p()
+        _check(L.scg_server_create(ctypes.byref(cfg), ctypes.byref(h)), "scg_server_create")
+        self._h = h
+        self._live = {}
+        self._next = 0
+        self._buf = (Completion * int(max_active))()   # a step finishes at most max_active
+
+    def submit(self, y: torch.Tensor, n: int, eps: float, x0=None, out=None, tag=None) -> int:
+        if y.dtype != self.dtype:
+            raise ScgError("sinogram dtype differs from the server's")
+        if x0 is not None:
+            x0 = x0.to(dtype=self.dtype).contiguous()
+        if out is None:
+            out = torch.empty((n, n), dtype=self.dtype, device=y.device)
+        if tag is None:
+            tag = self._next
+        self._next = max(self._next, int(tag)) + 1
+        arr = _problems([y], [n], [eps], [x0], [out])
+        _check(load().scg_server_submit(self._h, arr, int(tag)), "scg_server_submit")
+        self._live[int(tag)] = (y, x0, out)
+        return int(tag)
+
+    def step(self) -> list:
+        """Advance the server one step; returns [(tag, SolveResult)] of the
+        requests that finished."""
+        nd = ctypes.c_int(0)
+        rc = load().scg_server_step(self._h, _stream(self.device), self._buf, len(self._buf), ctypes.byref(nd))
+        _check(rc, "scg_server_step")
+        got = []
+        for q in range(nd.value):
+            c = self._buf[q]
+            _, _, out = self._live.pop(int(c.tag))
+            got.append((int(c.tag), _result(c.result, out)))
+        return got
+
+    def pending(self):
+        q, a = ctypes.c_int(0), ctypes.c_int(0)
+        _check(load().scg_server_pending(self._h, ctypes.byref(q), ctypes.byref(a)), "scg_server_pending")
+        return q.value, a.value
+
+    def close(self):
+        if self._h:
+            load().scg_server_destroy(self._h)
+            self._h = None
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

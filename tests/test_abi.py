@@ -105,3 +105,54 @@ def test_batch_workspace_query_and_validation(lib):
     arr[1].y = 256
     hl = scg._params(scg.default_params(host_loop=1))
     assert lib.scg_solve_batch(arr, 2, 2, scg.F32, ctypes.byref(hl), fake, 1 << 30, res, None) == -5
+
+
+def test_server_host_side(lib):
+    # create / submit / pending / destroy touch no device memory until the first step
+    fp = scg.server_footprint(64, 90, 95, "S-CG", torch.float32)
+    assert fp >= lib.scg_solve_workspace_bytes(ctypes.byref(scg.geometry(64, 90, 95)), 2, scg.F32)
+    assert scg.server_footprint(64, 90, 95, "S-PCG", torch.float32) > fp     # filter buffers
+    assert scg.server_footprint(1, 90, 95) == 0
+    p = scg._params(scg.default_params())
+    cfg = scg.ServerConfig(2, scg.F32, p, 1 << 20, 3 * fp, 4, 1)
+    h = ctypes.c_void_p()
+    assert lib.scg_server_create(ctypes.byref(cfg), ctypes.byref(h)) == 0
+    arr = (scg.Problem * 1)()
+    arr[0].geometry = scg.geometry(64, 90, 95)
+    arr[0].eps = 1.0
+    arr[0].y = 256
+    arr[0].x_out = 512
+    assert lib.scg_server_submit(h, arr, 7) == 0
+    assert lib.scg_server_submit(h, arr, 8) == 0
+    big = (scg.Problem * 1)()
+    big[0].geometry = scg.geometry(1024, 1440, 1449)
+    big[0].eps = 1.0
+    big[0].y = 256
+    big[0].x_out = 512
+    assert lib.scg_server_submit(h, big, 9) == -3           # can never fit this pool
+    arr[0].eps = -1.0
+    assert lib.scg_server_submit(h, arr, 10) == -1
+    q, a = ctypes.c_int(), ctypes.c_int()
+    assert lib.scg_server_pending(h, ctypes.byref(q), ctypes.byref(a)) == 0
+    assert (q.value, a.value) == (2, 0)
+    assert lib.scg_server_destroy(h) == 0
+    # invalid configurations
+    for bad in (scg.ServerConfig(2, scg.F32, p, 1 << 20, 3 * fp, 0, 1),
+                scg.ServerConfig(2, scg.F32, p, 1 << 20, 3 * fp, 4, 0),
+                scg.ServerConfig(9, scg.F32, p, 1 << 20, 3 * fp, 4, 1),
+                scg.ServerConfig(2, scg.F32, p, None, 3 * fp, 4, 1),
+                scg.ServerConfig(2, scg.F32, p, 1 << 20, 64, 4, 1)):
+        assert lib.scg_server_create(ctypes.byref(bad), ctypes.byref(h)) in (-1, -3)
+
+
+def test_reduced_storage_workspaces(lib):
+    g = scg.geometry(512, 720, 725)
+    b32 = lib.scg_solve_workspace_bytes(ctypes.byref(g), 2, scg.F32)
+    b16 = lib.scg_solve_workspace_bytes(ctypes.byref(g), 2, scg.F16)
+    bb16 = lib.scg_solve_workspace_bytes(ctypes.byref(g), 2, scg.BF16)
+    assert 0 < b16 == bb16 < 0.6 * b32                 # vectors and views at 2 bytes
+    for v in (0, 1):                                   # CG, PCG: recursive updates, FP32/FP64 only
+        assert lib.scg_solve_workspace_bytes(ctypes.byref(g), v, scg.F16) == 0
+        assert lib.scg_solve_workspace_bytes(ctypes.byref(g), v, scg.BF16) == 0
+    assert lib.scg_op_workspace_bytes(ctypes.byref(g), scg.F16) > 0
+    assert lib.scg_solve_workspace_bytes(ctypes.byref(g), 2, 4) == 0
