@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--serve-warmup", type=float, default=5.0, help="warm-up seconds in --mode serving")
     ap.add_argument("--max-active", type=int, default=64)
     ap.add_argument("--pool-gb", type=float, default=16.0)
+    ap.add_argument("--dtype", default=None, choices=["f32", "f16", "bf16", "f64"],
+                    help="storage precision in --mode batch (default f32) and --mode serving (default f16)")
     ap.add_argument("--host-loop", action="store_true",
                     help="run the while loop as host-polled per-body graphs (same kernels); "
                          "lets a profiler list every kernel launch")
@@ -382,6 +384,20 @@ def run_ours(args, work, rank, local_rank, world):
 
 
 # ---------------------------------------------------------------------------
+def _dtypes():
+    import torch
+    return {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16, "f64": torch.float64}
+
+
+class _LazyDtypes(dict):
+    def __missing__(self, key):
+        self.update(_dtypes())
+        return dict.__getitem__(self, key)
+
+
+DTYPES = _LazyDtypes()
+
+
 def _gpu_problems(works, seed, dev):
     import torch
 
@@ -411,12 +427,14 @@ def run_batch(args, rank, local_rank, world):
     kw = dict(gamma0_rel=args.gamma0_rel, max_iter=100)
     if variant in ("CG", "PCG"):
         kw["perturb"] = "none"
+    dtype = DTYPES[args.dtype or "f32"]
     works = inputs.batch_workloads(args.batch, args.seed + rank)
     probs, ys = _gpu_problems(works, 1000 * (args.seed + rank), dev)
+    ys = [y.to(dtype) for y in ys]
     ns = [w.n for w in works]
     eps = [p.eps for p in probs]
-    outs = [torch.empty((n, n), dtype=torch.float32, device=dev) for n in ns]
-    nbytes = scg.batch_workspace_bytes([(w.n, w.n_angles, w.n_bins) for w in works], variant, torch.float32)
+    outs = [torch.empty((n, n), dtype=dtype, device=dev) for n in ns]
+    nbytes = scg.batch_workspace_bytes([(w.n, w.n_angles, w.n_bins) for w in works], variant, dtype)
     wsp = torch.empty(nbytes, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -439,7 +457,7 @@ def run_batch(args, rank, local_rank, world):
     clk = clocks.stop()
     t_batch = float(np.mean(ms)) / 1e3
     # the same problems one by one (warm first: one graph per geometry)
-    wsolo = torch.empty(max(scg.solve_workspace_bytes(w.n, w.n_angles, w.n_bins, variant, scg.F32)
+    wsolo = torch.empty(max(scg.solve_workspace_bytes(w.n, w.n_angles, w.n_bins, variant, scg._prec_of(dtype))
                             for w in works), dtype=torch.uint8, device=dev)
     for q in range(len(works)):
         scg.scg_solve(ys[q], ns[q], variant, eps[q], out=outs[q], work=wsolo, **kw)
@@ -457,7 +475,7 @@ def run_batch(args, rank, local_rank, world):
         line = {"metric": "batched recon/s", "value": len(works) * world / t_batch, "unit": UNIT,
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * t_batch, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "vs_baseline": None, "dtype": args.dtype or "f32", "data": "synthetic",
                 "config": {"workload": f"uneven_batch{len(works)}", "variant": variant,
                            "sizes": "N in {128,...,768}, angles in {60,...,720}, bins ceil(sqrt2 N)",
                            "workspace_bytes": nbytes, "parallelism": f"replicas x{world}",
@@ -485,10 +503,12 @@ def run_serving(args, rank, local_rank, world):
     kw = dict(gamma0_rel=args.gamma0_rel, max_iter=100)
     if variant in ("CG", "PCG"):
         kw["perturb"] = "none"
+    dtype = DTYPES[args.dtype or "f16"]
     uniq = inputs.serving_workloads(64, args.seed + rank)
-    probs, ys = _gpu_problems(uniq, 5000 * (args.seed + rank), dev)
-    outs = [torch.empty((w.n, w.n), dtype=torch.float32, device=dev) for w in uniq]
-    srv = scg.Server(variant, torch.float32, pool_bytes=int(args.pool_gb * (1 << 30)),
+    probs, ys32 = _gpu_problems(uniq, 5000 * (args.seed + rank), dev)
+    ys = [y.to(dtype) for y in ys32]
+    outs = [torch.empty((w.n, w.n), dtype=dtype, device=dev) for w in uniq]
+    srv = scg.Server(variant, dtype, pool_bytes=int(args.pool_gb * (1 << 30)),
                      max_active=args.max_active, device=dev, **kw)
 
     def submit(q, tag):
@@ -497,25 +517,32 @@ def run_serving(args, rank, local_rank, world):
 
     # saturated throughput: 2 x 64 requests at once (first pass also warms graphs)
     sat = []
+    served = {}
     for rep in range(2):
         t0 = time.perf_counter()
         for q in range(2 * len(uniq)):
             submit(q, q)
         got = 0
         while got < 2 * len(uniq):
-            got += len(srv.step())
+            for tag, r in srv.step():
+                served[tag % len(uniq)] = r
+                got += 1
         sat.append(2 * len(uniq) / (time.perf_counter() - t0))
-    # solo: the same requests one by one through scg_solve
+    # solo: the same requests one by one through scg_solve, plain FP32
     wsolo = torch.empty(max(scg.solve_workspace_bytes(w.n, w.n_angles, w.n_bins, variant, scg.F32)
                             for w in uniq), dtype=torch.uint8, device=dev)
+    o32 = [torch.empty((w.n, w.n), dtype=torch.float32, device=dev) for w in uniq]
     for q in range(len(uniq)):
-        scg.scg_solve(ys[q], uniq[q].n, variant, probs[q].eps, out=outs[q], work=wsolo, **kw)
+        scg.scg_solve(ys32[q], uniq[q].n, variant, probs[q].eps, out=o32[q], work=wsolo, **kw)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    solo_res = []
     for q in range(len(uniq)):
-        scg.scg_solve(ys[q], uniq[q].n, variant, probs[q].eps, out=outs[q], work=wsolo, **kw)
+        solo_res.append(scg.scg_solve(ys32[q], uniq[q].n, variant, probs[q].eps, out=o32[q], work=wsolo, **kw))
     torch.cuda.synchronize()
     solo = len(uniq) / (time.perf_counter() - t0)
+    tv_diff = max(abs(served[q].tv_final - solo_res[q].tv_final) / solo_res[q].tv_final for q in range(len(uniq)))
+    all_ok = all(served[q].status == "ok" and served[q].f_final <= probs[q].eps for q in range(len(uniq)))
     # the Poisson stream
     total = args.serve_warmup + args.duration
     arrivals = inputs.poisson_arrivals(int(args.rate * total * 1.5) + 16, args.rate, args.seed + 7)
@@ -553,7 +580,7 @@ def run_serving(args, rank, local_rank, world):
     if rank == 0:
         line = {"metric": "served recon/s (Poisson)", "value": thr * world, "unit": UNIT, "n_gpus": world,
                 "steps": steps, "warmup": 0, "ms_per_step": None, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": args.dtype or "f16", "data": "synthetic",
                 "config": {"workload": "serving_poisson", "variant": variant, "rate": args.rate,
                            "duration_s": args.duration, "warmup_s": args.serve_warmup,
                            "requests": len(served), "max_active": args.max_active,
@@ -561,7 +588,10 @@ def run_serving(args, rank, local_rank, world):
                            "sizes": "N ~ U{128..1024 step 64}, 30..180 angles, eps 1.02-1.2 x noise floor"},
                 "latency_ms": {"p50": float(np.percentile(L, 50)), "p99": float(np.percentile(L, 99)),
                                "mean": float(np.mean(L))},
-                "saturated_recon_per_s": max(sat), "solo_recon_per_s": solo, "clocks": clk}
+                "saturated_recon_per_s": max(sat), "solo_fp32_recon_per_s": solo,
+                "served_vs_solo_fp32": max(sat) / solo,
+                "equal_eps_and_tv": {"all_f_le_eps": bool(all_ok), "max_tv_rel_diff_vs_fp32": tv_diff},
+                "clocks": clk}
         print(json.dumps(line), flush=True)
     return 0
 
