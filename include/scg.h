@@ -303,7 +303,9 @@ int scg_server_create(const scg_server_config* cfg, scg_server** out);
 int scg_server_submit(scg_server* srv, const scg_problem* req, unsigned long long tag);
 
 /* One step: admit queued requests that fit (in submission order; a request
- * that does not fit yet waits, and so do the ones behind it), advance every
+ * that does not fit yet waits, and so do the ones behind it; one that cannot
+ * fit even with nothing resident completes at once with status
+ * SCG_ERR_WORKSPACE), advance every
  * resident request by bodies_per_step loop bodies, finish the ones that
  * stopped and write up to max_done completions to done[] (*n_done gets the
  * count; completions beyond max_done are kept for the next step).  Blocking:

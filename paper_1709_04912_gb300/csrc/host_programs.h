@@ -77,8 +77,27 @@ struct Plan {
     size_t sino[SB_COUNT];
     size_t total;
     int S, SB, cnt_ray, cnt_img, cnt_row, tiles_x, ray_blocks, filt_blocks, P;
-    int cnt_proj, proj_blocks;
+    int cnt_proj, proj_blocks, proj_shift;
+    int cnt_bp;
 };
+
+// Projector items for the block shape 2^(8-shift) angles x 2^shift rays.
+inline void set_proj_shape(Plan& p, int na, int nb, int shift) {
+    const int R = 1 << shift, A = kProjThreads >> shift;
+    p.proj_shift = shift;
+    p.proj_blocks = (nb + R - 1) / R;
+    p.cnt_proj = ((na + A - 1) / A) * p.proj_blocks;
+}
+constexpr int kProjShiftMin = 5, kProjShiftMax = 8;   // 8 x 32 ... 1 x 256
+inline int max_proj_items(int na, int nb) {
+    Plan p;
+    int m = 0;
+    for (int sh = kProjShiftMin; sh <= kProjShiftMax; ++sh) {
+        set_proj_shape(p, na, nb, sh);
+        if (p.cnt_proj > m) m = p.cnt_proj;
+    }
+    return m;
+}
 
 enum PlanKind { PLAN_OP = 0, PLAN_SOLVE = 1 };
 
@@ -95,8 +114,11 @@ inline Plan make_plan(const scg_geometry& g, int variant, int precision, int kin
     p.cnt_img = ((N + kTileH - 1) / kTileH) * p.tiles_x;
     p.filt_blocks = (nb + kFilterBlock - 1) / kFilterBlock;
     p.cnt_row = na * p.filt_blocks;
-    p.proj_blocks = (nb + kProjRays - 1) / kProjRays;
-    p.cnt_proj = ((na + kProjAngles - 1) / kProjAngles) * p.proj_blocks;
+    // partials are sized for the largest item count of any projector shape
+    const int max_proj = max_proj_items(na, nb);
+    set_proj_shape(p, na, nb, kProjShiftDefault);
+    const int bp_th = precision == SCG_F64 ? kBpTileH64 : kBpTileH32;
+    p.cnt_bp = ((N + bp_th - 1) / bp_th) * p.tiles_x;
     p.P = filter_length(nb);
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, kAlign); return o; };
@@ -107,7 +129,8 @@ inline Plan make_plan(const scg_geometry& g, int variant, int precision, int kin
     p.taps = take(csize * (2 * (size_t)nb - 1));
     int maxcnt = p.cnt_ray > p.cnt_img ? p.cnt_ray : p.cnt_img;
     if (p.cnt_row > maxcnt) maxcnt = p.cnt_row;
-    if (p.cnt_proj > maxcnt) maxcnt = p.cnt_proj;
+    if (max_proj > maxcnt) maxcnt = max_proj;
+    if (p.cnt_bp > maxcnt) maxcnt = p.cnt_bp;
     p.partials = take(sizeof(double) * kSlots * (size_t)maxcnt);
     p.counter = take(sizeof(unsigned) * 4);
     p.view_rm = take(2 * tsize * (size_t)N * p.S);
@@ -156,6 +179,7 @@ void fill_angles(std::vector<Angle<T>>& out, int na, int n, double scale = 1.0) 
         g.c = (T)c;
         g.s = (T)s;
         g.inv_m = (T)(scale / m);
+        g.m_w = (T)(m / scale);
         if (mn == 0.0) {
             g.k2 = (T)1.0; g.h2 = (T)1.0; g.h2p = (T)2.0;
             g.kb = (T)1.0; g.hb0 = (T)1.0; g.hb1 = (T)0.0;
@@ -210,6 +234,8 @@ Prob<T> make_prob(const scg_geometry& g, const Plan& pl, unsigned char* base, do
     P.filt_blocks = pl.filt_blocks;
     P.cnt_proj = pl.cnt_proj;
     P.proj_blocks = pl.proj_blocks;
+    P.proj_shift = pl.proj_shift;
+    P.cnt_bp = pl.cnt_bp;
     P.P = pl.P;
     P.off_n = (C)(0.5 * (g.n - 1));
     P.off_b = (C)(0.5 * (g.n_bins - 1));
@@ -248,9 +274,11 @@ struct Runner {
     const Item* i_img = nullptr;
     const Item* i_row = nullptr;
     const Item* i_proj = nullptr;
+    int g_bp = 0;                      // backprojector tiles
+    const Item* i_bp = nullptr;
     void project(int dst, int mode, int step) { ++launches; launch_project<T>(d, i_proj, g_proj, dst, mode, step, s); }
-    void back1(int src, int dst, int step) { ++launches; launch_backproject<T>(d, i_img, g_img, 1, src, src, dst, dst, step, s); }
-    void back2(int s0, int s1, int d0, int d1, int step) { ++launches; launch_backproject<T>(d, i_img, g_img, 2, s0, s1, d0, d1, step, s); }
+    void back1(int src, int dst, int step) { ++launches; launch_backproject<T>(d, i_bp, g_bp, 1, src, src, dst, dst, step, s); }
+    void back2(int s0, int s1, int d0, int d1, int step) { ++launches; launch_backproject<T>(d, i_bp, g_bp, 2, s0, s1, d0, d1, step, s); }
     void vec(int op, int sel, int step) { ++launches; launch_vec<T>(d, i_img, g_img, op, sel, step, s); }
     void tvgrad(int src, int fuse, int wg, int step) { ++launches; launch_tvgrad<T>(d, i_img, g_img, src, fuse, wg, step, s); }
     void trial() { ++launches; launch_trial<T>(d, i_img, g_img, s); }
@@ -355,6 +383,53 @@ void run_resume(Runner<T>& R, const Program& pg) {
     R.tvgrad(IB_X, 0, 1, FIN_END);                     // dTV(x_k); loop test
 }
 
+// ---------------------------------------------------------------------------
+// Projector block-shape tuner.  The best shape depends on the geometry (how
+// long the rays are, how many angles share image spans); it is measured once
+// per geometry bucket (two buckets per octave of N, n_angles and n_bins) and
+// precision on each device, and cached for the life of the process.  The
+// choice changes only the block decomposition: every ray's value is computed
+// identically, and only the order in which the blocks' partial sums of r^2 are
+// added differs.  FP64 solves keep the default shape.
+int proj_shape_lookup(int dev, int precision, const scg_geometry& g);   // -1 if not tuned
+void proj_shape_store(int dev, int precision, const scg_geometry& g, int shift);
+
+// Time the candidate shapes on problem slot d (a solve plan, DevState not
+// stopped, angles uploaded; the SB_Q view is overwritten) and leave the best
+// one in P, pl and the slot.
+template <typename T>
+int tune_proj_shape(Prob<T>& P, Plan& pl, Prob<T>* d, const scg_geometry& g, cudaStream_t s) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SCG_ERR_CUDA;
+    int best = prec_of<T>() == SCG_F64 ? kProjShiftDefault : proj_shape_lookup(dev, prec_of<T>(), g);
+    if (best < 0) {
+        cudaEvent_t e0, e1;
+        if (cudaEventCreate(&e0) != cudaSuccess) return SCG_ERR_CUDA;
+        if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return SCG_ERR_CUDA; }
+        float best_ms = 1e30f;
+        for (int sh = kProjShiftMin; sh <= kProjShiftMax; ++sh) {
+            set_proj_shape(pl, g.n_angles, g.n_bins, sh);
+            P.cnt_proj = pl.cnt_proj; P.proj_blocks = pl.proj_blocks; P.proj_shift = sh;
+            if (cudaMemcpyAsync(d, &P, sizeof(P), cudaMemcpyHostToDevice, s) != cudaSuccess) break;
+            launch_project<T>(d, nullptr, pl.cnt_proj, SB_Q, PROJ_PLAIN, FIN_NONE, s);
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < 3; ++r) launch_project<T>(d, nullptr, pl.cnt_proj, SB_Q, PROJ_PLAIN, FIN_NONE, s);
+            cudaEventRecord(e1, s);
+            float ms = 1e30f;
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) break;
+            if (ms < best_ms) { best_ms = ms; best = sh; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (cudaGetLastError() != cudaSuccess || best < 0) return SCG_ERR_CUDA;
+        proj_shape_store(dev, prec_of<T>(), g, best);
+    }
+    set_proj_shape(pl, g.n_angles, g.n_bins, best);
+    P.cnt_proj = pl.cnt_proj; P.proj_blocks = pl.proj_blocks; P.proj_shift = best;
+    if (cudaMemcpyAsync(d, &P, sizeof(P), cudaMemcpyHostToDevice, s) != cudaSuccess) return SCG_ERR_CUDA;
+    return SCG_OK;
+}
+
 // Initial device state of one solve.
 inline DevState initial_state(const scg_params* prm, double eps, int variant) {
     DevState st;
@@ -386,13 +461,14 @@ inline Program make_program(const scg_params* prm, int variant) {
 // Work items of batched launches, one list per launch kind.  A problem's
 // items keep the (u, v) and block index (local) of its own single-problem
 // launch, so its reductions add in the single-problem order.
-enum { K_PROJ = 0, K_IMG = 1, K_RAY = 2, K_ROW = 3, K_COUNT = 4 };
+enum { K_PROJ = 0, K_IMG = 1, K_RAY = 2, K_ROW = 3, K_BP = 4, K_COUNT = 5 };
 
 inline void append_items(const Plan& pl, int prob, std::vector<Item>* lists) {
     for (int q = 0; q < pl.cnt_proj; ++q) lists[K_PROJ].push_back(Item{prob, q / pl.proj_blocks, q % pl.proj_blocks, q});
     for (int q = 0; q < pl.cnt_img; ++q) lists[K_IMG].push_back(Item{prob, q / pl.tiles_x, q % pl.tiles_x, q});
     for (int q = 0; q < pl.cnt_ray; ++q) lists[K_RAY].push_back(Item{prob, q / pl.ray_blocks, q % pl.ray_blocks, q});
     for (int q = 0; q < pl.cnt_row; ++q) lists[K_ROW].push_back(Item{prob, q / pl.filt_blocks, q % pl.filt_blocks, q});
+    for (int q = 0; q < pl.cnt_bp; ++q) lists[K_BP].push_back(Item{prob, q / pl.tiles_x, q % pl.tiles_x, q});
 }
 
 // List lengths rounded up to eight steps per octave (<= 12.5 % padding), so

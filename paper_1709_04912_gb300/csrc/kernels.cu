@@ -32,14 +32,16 @@ __device__ __forceinline__ Item decode_item(const Prob<T>* probs, const Item* it
     if (kind == 0) { it.u = blockIdx.x / P.ray_blocks; it.v = blockIdx.x % P.ray_blocks; }
     else if (kind == 1) { it.u = blockIdx.x / P.tiles_x; it.v = blockIdx.x % P.tiles_x; }
     else if (kind == 2) { it.u = blockIdx.x / P.filt_blocks; it.v = blockIdx.x % P.filt_blocks; }
-    else { it.u = blockIdx.x / P.proj_blocks; it.v = blockIdx.x % P.proj_blocks; }
+    else if (kind == 3) { it.u = blockIdx.x / P.proj_blocks; it.v = blockIdx.x % P.proj_blocks; }
+    else { it.u = blockIdx.x / P.tiles_x; it.v = blockIdx.x % P.tiles_x; }   // backprojector tiles
     return it;
 }
 
 // ---------------------------------------------------------------------------
-// Forward projector.  One thread per ray (a, b); a block holds kProjAngles
-// adjacent angles x kProjRays consecutive bins, so sinogram writes are
-// coalesced and the block's warps read nearly the same image spans.  The ray
+// Forward projector.  One thread per ray (a, b); a block holds
+// 2^(8-proj_shift) adjacent angles x 2^proj_shift consecutive bins, so
+// sinogram writes are coalesced and the block's warps read nearly the same
+// image spans.  The ray
 // is walked along its driving axis (columns when |sin| >= |cos|, else rows);
 // in each strip its chord is 1/m and falls on the two pixels nearest the
 // crossing, split u : (1-u) by one saturating FMA of the crossing's
@@ -53,57 +55,46 @@ __device__ __forceinline__ Item decode_item(const Prob<T>* probs, const Item* it
 // D carries the view element index of the pair at the crossing in its high
 // word (line t*S, pad kPad, floor(c*)) and the crossing's fraction in its low
 // word; adding DL = slope + S (both in 32.32) steps to the next strip.
-template <typename V2>
-__device__ __forceinline__ void strip(const V2* view, long long D, float k2, float h2p,
-                                      float& u, float& y) {
-    const float2 v = to_c2(__ldg(view + (int)(D >> 32)));
-    const float f1 = __int_as_float(0x3F800000 | ((unsigned)D >> 9));   // 1 + fraction
-    u = fmaf(__saturatef(fmaf(-f1, k2, h2p)), v.x - v.y, u);
-    y += v.y;
-}
-
-// The walk is software-pipelined: the loads of the next four strips are in
-// flight while the current four are summed.  Every index read lies inside the
-// view because [tlo, thi] holds exactly the strips whose crossing satisfies
-// -1 <= floor(c*) <= N-1 (kPad >= 1).
+// The walk is software-pipelined in two register groups of four strips that
+// take turns: while one group's loads are in flight the other's are summed,
+// with no register copies between iterations.  Every index read lies inside
+// the view because [tlo, thi] holds exactly the strips whose crossing
+// satisfies -1 <= floor(c*) <= N-1 (kPad >= 1), and no load runs ahead of
+// strip n-1.
+#define SCG_STRIP(V_, D_, U_, Y_)                                                                 \
+    U_ = fmaf(__saturatef(fmaf(-__int_as_float(0x3F800000 | ((unsigned)(D_) >> 9)), k2, h2p)),    \
+              V_.x - V_.y, U_);                                                                   \
+    Y_ += V_.y;
+#define SCG_LD(D_) to_c2(__ldg(view + (int)((D_) >> 32)))
 template <typename V2>
 __device__ __forceinline__ float walk_ray_f32(const V2* view, int n, long long D, long long DL,
                                               float k2, float h2p) {
     float u0 = 0.f, u1 = 0.f, y0 = 0.f, y1 = 0.f;
     int t = 0;
-    if (n >= 4) {
-        long long Da = D, Db = D + DL, Dc = D + 2 * DL, Dd = D + 3 * DL;
-        float2 va = to_c2(__ldg(view + (int)(Da >> 32))), vb = to_c2(__ldg(view + (int)(Db >> 32)));
-        float2 vc = to_c2(__ldg(view + (int)(Dc >> 32))), vd = to_c2(__ldg(view + (int)(Dd >> 32)));
-        for (t = 4; t + 4 <= n; t += 4) {
-            const long long Na = Dd + DL, Nb = Dd + 2 * DL, Nc = Dd + 3 * DL, Nd = Dd + 4 * DL;
-            const float2 wa = to_c2(__ldg(view + (int)(Na >> 32))), wb = to_c2(__ldg(view + (int)(Nb >> 32)));
-            const float2 wc = to_c2(__ldg(view + (int)(Nc >> 32))), wd = to_c2(__ldg(view + (int)(Nd >> 32)));
-#define SCG_STRIP(V_, D_, U_, Y_)                                                                 \
-    U_ = fmaf(__saturatef(fmaf(-__int_as_float(0x3F800000 | ((unsigned)(D_) >> 9)), k2, h2p)),    \
-              V_.x - V_.y, U_);                                                                   \
-    Y_ += V_.y;
-            SCG_STRIP(va, Da, u0, y0)
-            SCG_STRIP(vb, Db, u1, y1)
-            SCG_STRIP(vc, Dc, u0, y0)
-            SCG_STRIP(vd, Dd, u1, y1)
-            va = wa; vb = wb; vc = wc; vd = wd;
-            Da = Na; Db = Nb; Dc = Nc; Dd = Nd;
+    if (n >= 8) {
+        // group a holds strips t-4 .. t-1 (loaded) at the top of each iteration
+        long long A0 = D, A1 = D + DL, A2 = D + 2 * DL, A3 = D + 3 * DL;
+        float2 a0 = SCG_LD(A0), a1 = SCG_LD(A1), a2 = SCG_LD(A2), a3 = SCG_LD(A3);
+        for (t = 4; t + 8 <= n; t += 8) {
+            const long long B0 = A3 + DL, B1 = A3 + 2 * DL, B2 = A3 + 3 * DL, B3 = A3 + 4 * DL;
+            const float2 b0 = SCG_LD(B0), b1 = SCG_LD(B1), b2 = SCG_LD(B2), b3 = SCG_LD(B3);
+            SCG_STRIP(a0, A0, u0, y0) SCG_STRIP(a1, A1, u1, y1) SCG_STRIP(a2, A2, u0, y0) SCG_STRIP(a3, A3, u1, y1)
+            A0 = B3 + DL; A1 = B3 + 2 * DL; A2 = B3 + 3 * DL; A3 = B3 + 4 * DL;
+            a0 = SCG_LD(A0); a1 = SCG_LD(A1); a2 = SCG_LD(A2); a3 = SCG_LD(A3);
+            SCG_STRIP(b0, B0, u0, y0) SCG_STRIP(b1, B1, u1, y1) SCG_STRIP(b2, B2, u0, y0) SCG_STRIP(b3, B3, u1, y1)
         }
-        SCG_STRIP(va, Da, u0, y0)
-        SCG_STRIP(vb, Db, u1, y1)
-        SCG_STRIP(vc, Dc, u0, y0)
-        SCG_STRIP(vd, Dd, u1, y1)
-#undef SCG_STRIP
-        D = Dd + DL;
+        SCG_STRIP(a0, A0, u0, y0) SCG_STRIP(a1, A1, u1, y1) SCG_STRIP(a2, A2, u0, y0) SCG_STRIP(a3, A3, u1, y1)
+        D = A3 + DL;
     }
     for (; t < n; ++t) {
-        strip(view, D, k2, h2p, u0, y0);
+        const float2 v = SCG_LD(D);
+        SCG_STRIP(v, D, u0, y0)
         D += DL;
     }
     return (u0 + u1) + (y0 + y1);
 }
-
+#undef SCG_LD
+#undef SCG_STRIP
 
 // Strips t in [0, N) whose crossing C(t) = C0 + t*SL (32.32) has floor in
 // [-1, N-1]: a FP32 estimate, then corrected exactly in integer arithmetic.
@@ -178,10 +169,11 @@ __device__ __forceinline__ typename Tr<T>::C project_ray(const Prob<T>& P, const
     else return project_ray_f32(P, g, b);
 }
 
-// One block: kProjAngles adjacent angles x kProjRays consecutive bins; each
-// warp walks 32 rays of one angle.  Rays of neighbouring angles cross the
-// image almost together, so the warps of a block read nearly the same view
-// spans and most of those reads hit L1.
+// One block: 2^(8-proj_shift) adjacent angles x 2^proj_shift consecutive bins
+// (the shape is tuned per geometry on the host); each warp walks 32 rays of
+// one angle.  Rays of neighbouring angles cross the image almost together, so
+// the warps of a block read nearly the same view spans and most of those
+// reads hit L1.
 template <typename T>
 __global__ void __launch_bounds__(kProjThreads, 5)
 k_project(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int dst_sel,
@@ -190,8 +182,9 @@ k_project(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int
     const Prob<T>& P = probs[it.prob];
     if (P.st->done) return;
     const int nb = P.nb;
-    const int a = it.u * kProjAngles + threadIdx.x / kProjRays;
-    const int b = it.v * kProjRays + threadIdx.x % kProjRays;
+    const int sh = P.proj_shift;
+    const int a = (it.u << (kProjLog2 - sh)) + (threadIdx.x >> sh);
+    const int b = (it.v << sh) + (threadIdx.x & ((1 << sh) - 1));
     using C = typename Tr<T>::C;
     Acc<T> v[1];
     acc_zero(v[0]);
@@ -201,30 +194,38 @@ k_project(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int
         // (y_scale is 1 except for half/bfloat16 storage; the product is exact)
         if (mode == PROJ_RESIDUAL) out = out - to_c(P.y[(size_t)a * nb + b]) * P.y_scale;
         if (mode == PROJ_PLAIN_OUT) P.user_out[(size_t)a * nb + b] = to_s<typename Tr<T>::S>(out);
-        else store_pair<T>(P.sino[dst_sel] + (size_t)a * P.SB + kSPad, b, out);
+        else store_pair<T>(P.sino[dst_sel] + (size_t)a * P.SB + kSPad, b, out * g.inv_m);   // weighted view
         v[0] = acc_prod(out, out);
     }
     if (step != FIN_NONE) reduce_and_finalize<T, 1, true>(v, P, it.local, P.cnt_proj, step);
 }
 
 // ---------------------------------------------------------------------------
-// Backprojector: two pixels per thread (rows ty and ty + kTileH/2 of a
-// kTileW x kTileH tile), all angles.  A pixel whose centre projects to bin
-// coordinate cb can only meet bins floor(cb) and floor(cb)+1 ((m+n)/2 <=
-// 1/sqrt(2)); their weights are two saturating FMAs of cb's fractional part
-// (see Angle), and the two bins are one pair-layout load.
+// Backprojector: a 32 x TH tile per block of 128 threads, PIX pixels per
+// thread (rows ty, ty + TH/PIX, ...), all angles.  A pixel whose centre
+// projects to bin coordinate cb can only meet bins floor(cb) and floor(cb)+1
+// ((m+n)/2 <= 1/sqrt(2)); their weights are two saturating FMAs of cb's
+// fractional part (see Angle), and the two bins are one pair-layout load.  The
+// sinogram views hold r[a,b] / m_a (the chord factor 1/m of the angle is
+// applied when a view is written), so the gather is two FMAs per pixel.
 //
-// Angles are processed in chunks (16 in FP32, 8 in FP64).  For each angle the band of
-// sinogram pairs the tile can touch (<= 31|c| + 7|s| + 4 < kBand slots) is
-// copied into shared memory with cp.async, double-buffered so the next
-// chunk's copies overlap this chunk's arithmetic; parts of a band beyond the
-// detector are zero-filled by the copy itself, so the inner loop needs no
-// bounds test.  The projection of the tile's first pixel comes from 32.32
-// fixed point (FP64 in the FP64 kernel), split into integer + fraction; each
-// pixel adds only its small in-tile offset.
+// Angles are processed in chunks.  For each angle the band of sinogram pairs
+// the tile can touch (<= 31|c| + (TH-1)|s| + 4 < kBand slots) is copied into
+// shared memory with cp.async, double-buffered so the next chunk's copies
+// overlap this chunk's arithmetic; parts of a band beyond the detector are
+// zero-filled by the copy itself, so the inner loop needs no bounds test.  The
+// projection of the tile's first pixel comes from 32.32 fixed point (FP64 in
+// the FP64 kernel), split into integer + fraction; each pixel adds only its
+// small in-tile offset (8.24 fixed point in the FP32 kernel).
 constexpr int kBand = 48;
-template <typename T> struct BpChunk { static constexpr int value = 16; };   // FP32 arithmetic
-template <> struct BpChunk<double> { static constexpr int value = 8; };   // 48 KB static limit
+// tile height, pixels per thread, angles per chunk (FP32 arithmetic) ...
+template <typename T, int NRHS> struct BpCfg {
+    static constexpr int TH = kBpTileH32, PIX = 4, CH = NRHS == 1 ? 32 : 16;
+};
+// ... and FP64 (48 KB static shared memory)
+template <int NRHS> struct BpCfg<double, NRHS> {
+    static constexpr int TH = kBpTileH64, PIX = 2, CH = 8;
+};
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -238,12 +239,12 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 struct __align__(16) BpRowF {
     int base;        // band index of the tile origin's projection, in 8.24 fixed point
     int c24, s24;    // cos, sin in 8.24
-    float kb, hb0p, hb1p, inv_m;
-    int pad_;
+    float kb, hb0p, hb1p;
+    int pad_[2];
 };
 // Per-angle row of the FP64 gather.
 struct __align__(16) BpRowD {
-    double c, s, kb, hb0, hb1, inv_m, frac;
+    double c, s, kb, hb0, hb1, frac;
     int rel;
 };
 
@@ -261,29 +262,29 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
     using C = typename Tr<T>::C;
     using Row = typename std::conditional<std::is_same<C, float>::value, BpRowF, BpRowD>::type;
     constexpr bool kF32 = std::is_same<C, float>::value;
+    constexpr int TH = BpCfg<T, NRHS>::TH, PIX = BpCfg<T, NRHS>::PIX, CH = BpCfg<T, NRHS>::CH;
+    constexpr int kStep = TH / PIX;                   // rows between a thread's pixels
+    static_assert(kTileW * kStep == kBackThreads, "one thread per column and row group");
     constexpr int kSlotsPerSeg = 16 / (int)sizeof(S2);
     constexpr int kSegs = kBand / kSlotsPerSeg;       // 16-byte copies per band
-    constexpr int kHalf = kTileH / 2;
-    constexpr int kBpChunk = BpChunk<T>::value;
-    const Item it = decode_item(probs, items, 1);
+    const Item it = decode_item(probs, items, 4);
     const Prob<T>& P = probs[it.prob];
     if (P.st->done) return;
-    __shared__ Row rows[2][kBpChunk];
-    __shared__ int slo[2][kBpChunk];            // first slot of each band in its sinogram row
-    __shared__ __align__(16) S2 band[2][NRHS][kBpChunk][kBand];
+    __shared__ Row rows[2][CH];
+    __shared__ int slo[2][CH];                  // first slot of each band in its sinogram row
+    __shared__ __align__(16) S2 band[2][NRHS][CH][kBand];
     const int N = P.n, na = P.na, nb = P.nb, SB = P.SB;
-    const int ti0 = it.u * kTileH, tj0 = it.v * kTileW;
+    const int ti0 = it.u * TH, tj0 = it.v * kTileW;
     const int tx = threadIdx.x % kTileW, ty = threadIdx.x / kTileW;
-    const int i1 = ti0 + ty, i2 = ti0 + ty + kHalf, j = tj0 + tx;
-    const bool in1 = (i1 < N) && (j < N), in2 = (i2 < N) && (j < N);
+    const int j = tj0 + tx;
     const int X2 = 2 * tj0 - (N - 1), Y2 = 2 * ti0 - (N - 1);
     const S2* R[2] = {P.sino[src0], NRHS == 2 ? P.sino[src1] : P.sino[src0]};
-    const int nchunks = (na + kBpChunk - 1) / kBpChunk;
+    const int nchunks = (na + CH - 1) / CH;
 
     auto stage_rows = [&](int ch) {
         const int q = threadIdx.x;
-        const int a = ch * kBpChunk + q;
-        if (q < kBpChunk && a < na) {
+        const int a = ch * CH + q;
+        if (q < CH && a < na) {
             const Angle<C> g = P.ang[a];
             // band: slots the tile can touch, from floor(projection of the origin)
             // + floor((kTileW-1) min(c, 0)) - 1, rounded down to a 16-byte boundary
@@ -296,8 +297,8 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
                 // 8.24: integer part = band index of floor(cb), fraction = cb's
                 r.base = ((I + kSPad - s_lo) << 24) | (int)((unsigned)cb >> 8);
                 r.c24 = g.c24; r.s24 = g.s24;
-                r.kb = g.kb; r.hb0p = g.hb0p; r.hb1p = g.hb1p; r.inv_m = g.inv_m;
-                r.pad_ = 0;
+                r.kb = g.kb; r.hb0p = g.hb0p; r.hb1p = g.hb1p;
+                r.pad_[0] = r.pad_[1] = 0;
                 rows[ch & 1][q] = r;
                 slo[ch & 1][q] = s_lo;
             } else {
@@ -306,7 +307,7 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
                 const int I = (int)fl;
                 const int s_lo = (I + kSPad + lo) & ~(kSlotsPerSeg - 1);
                 BpRowD r;
-                r.c = g.c; r.s = g.s; r.kb = g.kb; r.hb0 = g.hb0; r.hb1 = g.hb1; r.inv_m = g.inv_m;
+                r.c = g.c; r.s = g.s; r.kb = g.kb; r.hb0 = g.hb0; r.hb1 = g.hb1;
                 r.frac = cbt - fl;
                 r.rel = I + kSPad - s_lo;
                 rows[ch & 1][q] = r;
@@ -315,8 +316,8 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
         }
     };
     auto stage_copy = [&](int ch) {
-        const int a0 = ch * kBpChunk;
-        const int cnt = min(kBpChunk, na - a0);
+        const int a0 = ch * CH;
+        const int cnt = min(CH, na - a0);
 #pragma unroll
         for (int h = 0; h < NRHS; ++h) {
             for (int sg = threadIdx.x; sg < cnt * kSegs; sg += blockDim.x) {
@@ -330,7 +331,11 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
         cp_async_commit();
     };
 
-    C a1 = C(0), a2 = C(0), b1 = C(0), b2 = C(0);
+    C acc[NRHS][PIX];
+#pragma unroll
+    for (int h = 0; h < NRHS; ++h)
+#pragma unroll
+        for (int k = 0; k < PIX; ++k) acc[h][k] = C(0);
     stage_rows(0);
     __syncthreads();
     stage_copy(0);
@@ -341,57 +346,47 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
         if (more) { stage_copy(ch + 1); cp_async_wait<1>(); }
         else cp_async_wait<0>();
         __syncthreads();
-        const int cnt = min(kBpChunk, na - ch * kBpChunk);
+        const int cnt = min(CH, na - ch * CH);
         const int buf = ch & 1;
-        if (in1) {
+        if (j < N && ti0 + ty < N) {
             if constexpr (kF32) {
-#pragma unroll 4
+#pragma unroll 2
                 for (int q = 0; q < cnt; ++q) {
                     const BpRowF g = rows[buf][q];
-                    // 8.24 position of both pixels in band coordinates (always > 0)
-                    const int p1 = g.base + tx * g.c24 + ty * g.s24;
-                    const int p2 = p1 + kHalf * g.s24;
-                    // 1 + fraction as a float in [1, 2)
-                    const float f1 = __int_as_float(0x3F800000 | (((unsigned)p1 & 0xFFFFFFu) >> 1));
-                    const float f2 = __int_as_float(0x3F800000 | (((unsigned)p2 & 0xFFFFFFu) >> 1));
-                    const float w10 = __saturatef(fmaf(-f1, g.kb, g.hb0p)), w11 = __saturatef(fmaf(f1, g.kb, g.hb1p));
-                    const float w20 = __saturatef(fmaf(-f2, g.kb, g.hb0p)), w21 = __saturatef(fmaf(f2, g.kb, g.hb1p));
-                    const S2* bq = &band[buf][0][q][0];
-                    const float2 e1 = to_c2(bq[p1 >> 24]);
-                    const float2 e2 = to_c2(bq[p2 >> 24]);
-                    a1 = fmaf(g.inv_m, fmaf(w10, e1.x, w11 * e1.y), a1);
-                    a2 = fmaf(g.inv_m, fmaf(w20, e2.x, w21 * e2.y), a2);
-                    if (NRHS == 2) {
-                        const S2* zq = &band[buf][NRHS - 1][q][0];
-                        const float2 z1 = to_c2(zq[p1 >> 24]);
-                        const float2 z2 = to_c2(zq[p2 >> 24]);
-                        b1 = fmaf(g.inv_m, fmaf(w10, z1.x, w11 * z1.y), b1);
-                        b2 = fmaf(g.inv_m, fmaf(w20, z2.x, w21 * z2.y), b2);
+                    // 8.24 position of the thread's first pixel in band coordinates (> 0)
+                    const int p0 = g.base + tx * g.c24 + ty * g.s24;
+                    const int dp = kStep * g.s24;
+#pragma unroll
+                    for (int k = 0; k < PIX; ++k) {
+                        const int p = p0 + k * dp;
+                        // 1 + fraction as a float in [1, 2)
+                        const float f = __int_as_float(0x3F800000 | (((unsigned)p & 0xFFFFFFu) >> 1));
+                        const float w0 = __saturatef(fmaf(-f, g.kb, g.hb0p));
+                        const float w1 = __saturatef(fmaf(f, g.kb, g.hb1p));
+#pragma unroll
+                        for (int h = 0; h < NRHS; ++h) {
+                            const float2 e = to_c2(band[buf][h][q][p >> 24]);
+                            acc[h][k] = fmaf(w0, e.x, fmaf(w1, e.y, acc[h][k]));
+                        }
                     }
                 }
             } else {
-                const double dj = double(tx), di1 = double(ty), di2 = double(ty + kHalf);
+                const double dj = double(tx);
                 for (int q = 0; q < cnt; ++q) {
                     const BpRowD& g = *reinterpret_cast<const BpRowD*>(&rows[buf][q]);
                     const double djc = dj * g.c;
-                    const double v1 = g.frac + fma(di1, g.s, djc);
-                    const double v2 = g.frac + fma(di2, g.s, djc);
-                    int q1, q2;
-                    const double f1 = v1 - floor_split(v1, q1);
-                    const double f2 = v2 - floor_split(v2, q2);
-                    const unsigned k1 = min((unsigned)(q1 + g.rel), (unsigned)(kBand - 2));
-                    const unsigned k2 = min((unsigned)(q2 + g.rel), (unsigned)(kBand - 2));
-                    const double w10 = sat(fma(-f1, g.kb, g.hb0)), w11 = sat(fma(f1, g.kb, g.hb1));
-                    const double w20 = sat(fma(-f2, g.kb, g.hb0)), w21 = sat(fma(f2, g.kb, g.hb1));
-                    const double2 e1 = to_c2(band[buf][0][q][k1]);
-                    const double2 e2 = to_c2(band[buf][0][q][k2]);
-                    a1 = fma(g.inv_m, fma(w10, e1.x, w11 * e1.y), a1);
-                    a2 = fma(g.inv_m, fma(w20, e2.x, w21 * e2.y), a2);
-                    if (NRHS == 2) {
-                        const double2 z1 = to_c2(band[buf][NRHS - 1][q][k1]);
-                        const double2 z2 = to_c2(band[buf][NRHS - 1][q][k2]);
-                        b1 = fma(g.inv_m, fma(w10, z1.x, w11 * z1.y), b1);
-                        b2 = fma(g.inv_m, fma(w20, z2.x, w21 * z2.y), b2);
+#pragma unroll
+                    for (int k = 0; k < PIX; ++k) {
+                        const double v = g.frac + fma(double(ty + k * kStep), g.s, djc);
+                        int qi;
+                        const double f = v - floor_split(v, qi);
+                        const unsigned kk = min((unsigned)(qi + g.rel), (unsigned)(kBand - 2));
+                        const double w0 = sat(fma(-f, g.kb, g.hb0)), w1 = sat(fma(f, g.kb, g.hb1));
+#pragma unroll
+                        for (int h = 0; h < NRHS; ++h) {
+                            const double2 e = to_c2(band[buf][h][q][kk]);
+                            acc[h][k] = fma(w0, e.x, fma(w1, e.y, acc[h][k]));
+                        }
                     }
                 }
             }
@@ -399,26 +394,22 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
         __syncthreads();
     }
     using S = typename Tr<T>::S;
-    const size_t idx1 = (size_t)i1 * N + j, idx2 = (size_t)i2 * N + j;
-    // the dots below use the stored (rounded) values
-    a1 = rnd<T>(a1); a2 = rnd<T>(a2); b1 = rnd<T>(b1); b2 = rnd<T>(b2);
-    if (in1) {
-        P.img[dst0][idx1] = to_s<S>(a1);
-        if (NRHS == 2) P.img[dst1][idx1] = to_s<S>(b1);
-    }
-    if (in2) {
-        P.img[dst0][idx2] = to_s<S>(a2);
-        if (NRHS == 2) P.img[dst1][idx2] = to_s<S>(b2);
-    }
-    if (step == FIN_NONE) return;
+    const int dst[2] = {dst0, dst1};
     Acc<T> v[3];
     acc_zero(v[0]); acc_zero(v[1]); acc_zero(v[2]);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const bool in = h ? in2 : in1;
-        if (!in) continue;
-        const size_t idx = h ? idx2 : idx1;
-        const C g0 = h ? a2 : a1, g1 = h ? b2 : b1;
+    for (int k = 0; k < PIX; ++k) {
+        const int i = ti0 + ty + k * kStep;
+        if (i >= N || j >= N) continue;
+        const size_t idx = (size_t)i * N + j;
+        // stored values are rounded to the storage format; the dots use them
+#pragma unroll
+        for (int h = 0; h < NRHS; ++h) {
+            acc[h][k] = rnd<T>(acc[h][k]);
+            P.img[dst[h]][idx] = to_s<S>(acc[h][k]);
+        }
+        if (step == FIN_NONE) continue;
+        const C g0 = acc[0][k], g1 = acc[NRHS - 1][k];
         if (step == FIN_BETA) {
             v[0] = acc_add(v[0], acc_prod(NRHS == 2 ? g1 : g0, to_c(P.img[IB_H][idx])));  // g'^T h (z'^T h)
             v[1] = acc_add(v[1], acc_prod(g0, g0));                                       // ||g'||^2
@@ -426,11 +417,12 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
         } else if (step == FIN_ALPHA || step == FIN_CG_ALPHA) {
             v[0] = acc_add(v[0], acc_prod(to_c(P.img[IB_P][idx]), g0));                   // p^T h
         } else if (step == FIN_CG_DELTA) {
-            v[0] = acc_add(v[0], acc_prod(g0, g0));                                 // ||g||^2
-            v[1] = acc_add(v[1], acc_prod(g0, g1));                                 // g^T z
+            v[0] = acc_add(v[0], acc_prod(g0, g0));                                       // ||g||^2
+            v[1] = acc_add(v[1], acc_prod(g0, g1));                                       // g^T z
         }
     }
-    reduce_and_finalize<T, 3>(v, P, it.local, P.cnt_img, step);
+    if (step == FIN_NONE) return;
+    reduce_and_finalize<T, 3>(v, P, it.local, P.cnt_bp, step);
 }
 
 // ---------------------------------------------------------------------------
@@ -700,33 +692,41 @@ k_trial(const Prob<T>* __restrict__ probs, const Item* __restrict__ items) {
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    // last block: slot = tid % NS, items tid / NS, tid / NS + NW, ... (fixed order)
-    const int slot = threadIdx.x % NS, lane_grp = threadIdx.x / NS;
-    A acc;
-    acc_zero(acc);
-    for (int q = lane_grp; q < P.cnt_img; q += NW) {
-        const A* src = parts + (size_t)q * kSlots + slot;
-        A x;
-        if constexpr (std::is_same<A, double>::value) {
-            x = __ldcg(reinterpret_cast<const double*>(src));
-        } else {
-            const float2 w = __ldcg(reinterpret_cast<const float2*>(src));
-            x.hi = w.x;
-            x.lo = w.y;
+    // last block: each thread adds the partials of items tid, tid + 256, ...
+    // for eight slots at a time (independent 16-byte loads, all in flight),
+    // then the block adds the per-thread sums in a fixed order
+    __shared__ A red[32 * 8];
+    double sums[NS];
+#pragma unroll 1
+    for (int g8 = 0; g8 < NS / 8; ++g8) {
+        A acc[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc_zero(acc[k]);
+        for (int q = threadIdx.x; q < P.cnt_img; q += kTileThreads) {
+            const A* src = parts + (size_t)q * kSlots + g8 * 8;
+#pragma unroll
+            for (int k = 0; k < 8; k += 2) {
+                A x0, x1;
+                if constexpr (std::is_same<A, double>::value) {
+                    const double2 w = __ldcg(reinterpret_cast<const double2*>(src + k));
+                    x0 = w.x; x1 = w.y;
+                } else {
+                    const float4 w = __ldcg(reinterpret_cast<const float4*>(src + k));
+                    x0.hi = w.x; x0.lo = w.y; x1.hi = w.z; x1.lo = w.w;
+                }
+                acc[k] = acc_add(acc[k], x0);
+                acc[k + 1] = acc_add(acc[k + 1], x1);
+            }
         }
-        acc = acc_add(acc, x);
+        block_sum<A, 8>(acc, red);
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) sums[g8 * 8 + k] = acc_to_double(acc[k]);
+        }
     }
-    wsum[lane_grp][slot] = acc;
-    __syncthreads();
     if (threadIdx.x == 0) {
         *P.counter = 0u;
-        double S[NS];
-        for (int t = 0; t < NS; ++t) {
-            A sum = wsum[0][t];
-            for (int w = 1; w < NW; ++w) sum = acc_add(sum, wsum[w][t]);
-            S[t] = acc_to_double(sum);
-        }
-        finalize<T>(FIN_TRIAL, P, S);
+        finalize<T>(FIN_TRIAL, P, sums);
     }
 }
 
@@ -747,9 +747,11 @@ k_sino_axpy(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, i
         // reads the first half of slot b, writes it and the second half of
         // slot b-1: no other thread touches those words
         using C = typename Tr<T>::C;
+        // weighted views (r / m_a): the update is linear; ||r'||^2 unweights
         const C r = rnd<T>(fma((C)st.alpha, to_c(P.sino[SB_Q][o + b].x), to_c(P.sino[SB_R][o + b].x)));
         store_pair<T>(P.sino[SB_R] + o, b, r);
-        v[0] = acc_prod(r, r);
+        const C ru = r * P.ang[a].m_w;
+        v[0] = acc_prod(ru, ru);
     }
     reduce_and_finalize<T, 1, true>(v, P, it.local, P.cnt_ray, step);
 }
@@ -761,7 +763,8 @@ k_sino_pairs(const Prob<T>* __restrict__ probs, int dst) {
     const Prob<T>& P = probs[0];
     const int a = blockIdx.x / P.ray_blocks, b = (blockIdx.x % P.ray_blocks) * kRayBlock + threadIdx.x;
     if (b < P.nb)
-        store_pair<T>(P.sino[dst] + (size_t)a * P.SB + kSPad, b, to_c(P.user_in[(size_t)a * P.nb + b]));
+        store_pair<T>(P.sino[dst] + (size_t)a * P.SB + kSPad, b,
+                      to_c(P.user_in[(size_t)a * P.nb + b]) * P.ang[a].inv_m);   // weighted view
 }
 
 // ---------------------------------------------------------------------------

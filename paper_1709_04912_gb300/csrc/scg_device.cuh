@@ -17,7 +17,9 @@
 //                      one short contiguous span of a line.
 //   sinogram views     [angle][kSPad + bin] rows of SB pairs with zero pads, so
 //                      the backprojector's two candidate bins are one load and
-//                      never need a bounds test (a clamped pair reads pads).
+//                      never need a bounds test (a clamped pair reads pads);
+//                      a view holds v[a,b] * inv_m(a) (the angle's chord factor,
+//                      applied once when the view is written).
 //   partials           kSlots doubles per work item, summed in a fixed order
 //                      by the last item of a launch (no atomics on data).
 #pragma once
@@ -40,11 +42,13 @@ constexpr int kTrials = 31;      // TV trial candidates per pass (+1 baseline sl
 constexpr int kTileW = 32;       // image tile width (pixels) = one warp
 constexpr int kTileH = 8;        // image tile height
 constexpr int kTileThreads = kTileW * kTileH;
-constexpr int kBackThreads = kTileThreads / 2;   // backprojector: two pixels per thread
+constexpr int kBackThreads = 128;               // backprojector block: 32 x kBpTileH pixels ...
+constexpr int kBpTileH32 = 16;                  // ... 4 per thread (FP32 arithmetic)
+constexpr int kBpTileH64 = 8;                   // ... 2 per thread (FP64)
 constexpr int kRayBlock = 128;   // rays per sinogram-row work item (axpy, pairs)
-constexpr int kProjAngles = 4;   // projector block: adjacent angles ...
-constexpr int kProjRays = 64;    // ... x consecutive rays (they read nearly the same image spans)
-constexpr int kProjThreads = kProjAngles * kProjRays;
+constexpr int kProjLog2 = 8;     // projector block: 2^8 threads = adjacent angles x consecutive
+constexpr int kProjThreads = 1 << kProjLog2;   // rays (2^proj_shift rays of each angle; they read
+constexpr int kProjShiftDefault = 6;           // nearly the same image spans): 4 x 64 by default
 constexpr int kFilterBlock = 128;// output bins per filter work item
 
 enum ImgBuf { IB_X = 0, IB_XH, IB_P, IB_H, IB_G, IB_Z, IB_TVG, IB_AUX, IB_COUNT };
@@ -83,6 +87,7 @@ struct Angle {
     long long c_fx, s_fx;     // 32.32 fixed point (FP32 kernels)
     int c24, s24;             // cos, sin in 8.24 fixed point (in-tile offsets of the gather)
     T hb0p, hb1p;             // hb0 + kb, hb1 - kb (gather weights from g1 = g + 1 in [1, 2))
+    T m_w;                    // 1 / inv_m: undoes the chord factor of a sinogram view
     long long inv_fx, c0_off_fx, slope_fx;
 };
 
@@ -181,6 +186,8 @@ struct Prob {
     int SB;                 // sinogram-view row stride (elements)
     int cnt_ray, cnt_img, cnt_row;   // items per launch kind
     int cnt_proj, proj_blocks;       // projector items; bin blocks per angle group
+    int proj_shift;                  // projector block = 2^(8-shift) angles x 2^shift rays
+    int cnt_bp;                      // backprojector tiles (32 x kBpTileH32 or kBpTileH64)
     int tiles_x;            // image tiles per row of tiles
     int ray_blocks;         // projector items per angle
     int filt_blocks;        // filter items per row
@@ -385,7 +392,8 @@ __device__ void reduce_and_finalize(Acc<T> (&v)[NS], const Prob<T>& P, int local
     A acc[NS];
 #pragma unroll
     for (int k = 0; k < NS; ++k) acc_zero(acc[k]);
-    for (int it = threadIdx.x; it < total; it += blockDim.x) {
+#pragma unroll 4
+    for (int it = threadIdx.x; it < total; it += blockDim.x) {      // loads of 4 items in flight
         const A* src = parts + (size_t)it * kSlots;
 #pragma unroll
         for (int k = 0; k < NS; ++k) {

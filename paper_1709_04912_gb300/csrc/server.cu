@@ -128,8 +128,19 @@ struct ServerBase {
     virtual void pending(int* queued, int* active) const = 0;
 };
 
-size_t list_bytes(const Plan& pl) {
-    return sizeof(Item) * (size_t)(pl.cnt_proj + pl.cnt_img + pl.cnt_ray + pl.cnt_row);
+// Pool bytes of one resident request: its solve region, and its share of the
+// active (rounded up) and set-up/final work lists.
+size_t footprint_bytes(const Plan& pl, const scg_geometry& g) {
+    int n[K_COUNT];
+    n[K_PROJ] = max_proj_items(g.n_angles, g.n_bins);
+    n[K_IMG] = pl.cnt_img;
+    n[K_RAY] = pl.cnt_ray;
+    n[K_ROW] = pl.cnt_row;
+    n[K_BP] = pl.cnt_bp;
+    size_t b = align_up(pl.total, kAlign);
+    for (int k = 0; k < K_COUNT; ++k)
+        b += align_up(sizeof(Item) * (size_t)round_up_bucket(n[k]), kAlign) + align_up(sizeof(Item) * (size_t)n[k], kAlign);
+    return b;
 }
 
 template <typename T>
@@ -172,7 +183,7 @@ public:
         r->slot = -1;
         r->bodies = 0;
         // region plus its share of the work lists (active and set-up/final)
-        if (align_up(r->plan.total, kAlign) + 2 * list_bytes(r->plan) > reserved_) {
+        if (footprint_bytes(r->plan, req->geometry) > reserved_) {
             delete r;
             return SCG_ERR_WORKSPACE;
         }
@@ -245,6 +256,22 @@ private:
         return SCG_OK;
     }
 
+    // Free every work list now (only when no request is resident and nothing
+    // is in flight); cached graphs name list addresses, so they go too.
+    void drop_lists() {
+        for (auto& f : deferred_free_) alloc_.release(f.first, f.second);
+        deferred_free_.clear();
+        for (int k = 0; k < K_COUNT; ++k) {
+            if (active_lists_[k].cap) alloc_.release(active_lists_[k].off, sizeof(Item) * (size_t)active_lists_[k].cap);
+            if (aux_lists_[k].cap) alloc_.release(aux_lists_[k].off, sizeof(Item) * (size_t)aux_lists_[k].cap);
+            active_lists_[k] = DevList();
+            aux_lists_[k] = DevList();
+        }
+        for (auto& g : graphs_) cudaGraphExecDestroy(g.second.exec);
+        graphs_.clear();
+        graphs_dirty_ = true;
+    }
+
     // Upload work lists over the given slots; `bucket` pads each list with
     // placeholder items to its rounded length.  Returns the launch grids.
     int build_lists(const std::vector<int>& slots, DevList* lists, bool bucket, int* grid, int* nb_max) {
@@ -273,14 +300,61 @@ private:
         R.i_img = list_ptr(lists[K_IMG]);
         R.i_row = list_ptr(lists[K_ROW]);
         R.i_proj = list_ptr(lists[K_PROJ]);
+        R.g_bp = grid[K_BP];
+        R.i_bp = list_ptr(lists[K_BP]);
         return R;
     }
 
+    // Work items of each kind one request can add (projector: its largest shape).
+    static void request_items(const Request* r, int* n) {
+        n[K_PROJ] = max_proj_items(r->p.geometry.n_angles, r->p.geometry.n_bins);
+        n[K_IMG] = r->plan.cnt_img;
+        n[K_RAY] = r->plan.cnt_ray;
+        n[K_ROW] = r->plan.cnt_row;
+        n[K_BP] = r->plan.cnt_bp;
+    }
+
     int admit(std::vector<int>* newcomers) {
+        // items of the resident requests, and of this step's newcomers
+        int act[K_COUNT] = {0, 0, 0, 0, 0}, fresh[K_COUNT] = {0, 0, 0, 0, 0}, n[K_COUNT];
+        for (Request* q : slots_) {
+            if (!q) continue;
+            request_items(q, n);
+            for (int k = 0; k < K_COUNT; ++k) act[k] += n[k];
+        }
+        bool lists_dropped = false;
         while (!queue_.empty() && n_active_ < cfg_.max_active) {
             Request* r = queue_.front();
+            // the work lists must hold the newcomer before its state is placed
+            request_items(r, n);
+            bool ok = true;
+            for (int k = 0; k < K_COUNT && ok; ++k)
+                ok = reserve_list(active_lists_[k], round_up_bucket(act[k] + n[k])) == SCG_OK &&
+                     reserve_list(aux_lists_[k], fresh[k] + n[k]) == SCG_OK;
             size_t off = 0;
-            if (!alloc_.alloc(r->plan.total, &off)) break;
+            if (ok) ok = alloc_.alloc(r->plan.total, &off);
+            if (!ok) {
+                if (n_active_ > 0 || !newcomers->empty()) break;   // wait for memory to free up
+                // nothing resident and nothing in flight: drop the work lists (they
+                // only grow) and retry once; a request that still does not fit can
+                // never run, and completes with SCG_ERR_WORKSPACE
+                if (!lists_dropped) {
+                    drop_lists();
+                    lists_dropped = true;
+                    continue;
+                }
+                scg_completion c;
+                memset(&c, 0, sizeof(c));
+                c.tag = r->tag;
+                c.result.status = SCG_ERR_WORKSPACE;
+                completions_.push_back(c);
+                queue_.pop_front();
+                delete r;
+                lists_dropped = false;
+                continue;
+            }
+            lists_dropped = false;
+            for (int k = 0; k < K_COUNT; ++k) { act[k] += n[k]; fresh[k] += n[k]; }
             int slot = 0;
             while (slots_[slot]) ++slot;
             r->off = off;
@@ -304,6 +378,10 @@ private:
                                cfg_.params.filter_gain, stream_);
             }
             SCK(upload(probs() + slot, &P, sizeof(P)));
+            {
+                const int rc = tune_proj_shape<T>(P, r->plan, probs() + slot, r->p.geometry, stream_);
+                if (rc != SCG_OK) return rc;
+            }
             slots_[slot] = r;
             ++n_active_;
             queue_.pop_front();
@@ -318,9 +396,10 @@ private:
         int grid[K_COUNT];
         int nb;
         bool operator<(const Key& o) const {
-            return std::tie(off[0], off[1], off[2], off[3], grid[0], grid[1], grid[2], grid[3], nb) <
-                   std::tie(o.off[0], o.off[1], o.off[2], o.off[3], o.grid[0], o.grid[1], o.grid[2],
-                            o.grid[3], o.nb);
+            return std::tie(off[0], off[1], off[2], off[3], off[4], grid[0], grid[1], grid[2], grid[3], grid[4],
+                            nb) <
+                   std::tie(o.off[0], o.off[1], o.off[2], o.off[3], o.off[4], o.grid[0], o.grid[1], o.grid[2],
+                            o.grid[3], o.grid[4], o.nb);
         }
     };
     struct Graph {
@@ -472,7 +551,7 @@ private:
     std::vector<Request*> slots_;
     int n_active_ = 0;
     DevList active_lists_[K_COUNT], aux_lists_[K_COUNT];
-    int active_grid_[K_COUNT] = {0, 0, 0, 0};
+    int active_grid_[K_COUNT] = {0, 0, 0, 0, 0};
     int active_nb_ = 128;
     bool membership_changed_ = true, graphs_dirty_ = true;
     std::vector<std::pair<size_t, size_t>> deferred_free_;
@@ -502,7 +581,7 @@ size_t scg_server_footprint(const scg_geometry* g, int variant, int precision) {
         !solve_supported(variant, precision))
         return 0;
     const Plan pl = make_plan(*g, variant, precision, PLAN_SOLVE);
-    return align_up(pl.total, kAlign) + 2 * list_bytes(pl);
+    return footprint_bytes(pl, *g);
 }
 
 int scg_server_create(const scg_server_config* cfg, scg_server** out) {

@@ -27,11 +27,11 @@ namespace {
 struct GraphKey {
     int dev;
     const void* work;
-    int prec, variant, trial_passes, ksteps, n, na, nb, host_loop;
+    int prec, variant, trial_passes, ksteps, n, na, nb, host_loop, proj_shift;
     bool operator<(const GraphKey& o) const {
-        return std::tie(dev, work, prec, variant, trial_passes, ksteps, n, na, nb, host_loop) <
+        return std::tie(dev, work, prec, variant, trial_passes, ksteps, n, na, nb, host_loop, proj_shift) <
                std::tie(o.dev, o.work, o.prec, o.variant, o.trial_passes, o.ksteps, o.n, o.na, o.nb,
-                        o.host_loop);
+                        o.host_loop, o.proj_shift);
     }
 };
 
@@ -43,6 +43,19 @@ struct BodyGraph {
 
 std::mutex g_mu;
 std::map<GraphKey, BodyGraph> g_graphs;
+
+struct ShapeKey {
+    int dev, prec, bn, ba, bb;
+    bool operator<(const ShapeKey& o) const {
+        return std::tie(dev, prec, bn, ba, bb) < std::tie(o.dev, o.prec, o.bn, o.ba, o.bb);
+    }
+};
+std::mutex g_shape_mu;
+std::map<ShapeKey, int> g_shapes;
+ShapeKey shape_key(int dev, int precision, const scg_geometry& g) {
+    auto bucket = [](int v) { return (int)lround(2.0 * log2((double)v)); };
+    return ShapeKey{dev, precision, bucket(g.n), bucket(g.n_angles), bucket(g.n_bins)};
+}
 std::map<int, cudaStream_t> g_streams;
 std::map<int, int*> g_pinned;
 
@@ -72,7 +85,7 @@ int solve_impl(const scg_geometry* g, int variant, int precision, const scg_para
                scg_state* final_state, cudaStream_t user_stream) {
     using E = typename Tr<T>::S;
     using C = typename Tr<T>::C;
-    const Plan pl = make_plan(*g, variant, prec_of<T>(), PLAN_SOLVE);
+    Plan pl = make_plan(*g, variant, prec_of<T>(), PLAN_SOLVE);
     if (work_bytes < pl.total || ((uintptr_t)work & 15u)) return SCG_ERR_WORKSPACE;
     unsigned char* base = (unsigned char*)work;
     const int N = g->n, fam = family_of(variant);
@@ -115,8 +128,13 @@ int solve_impl(const scg_geometry* g, int variant, int precision, const scg_para
         size_t smem = (size_t)(3 * g->n_bins) * sizeof(C);
         if (smem > 227 * 1024) return SCG_ERR_UNSUPPORTED;
     }
+    {
+        const int rc = tune_proj_shape<T>(P, pl, reinterpret_cast<Prob<T>*>(base + pl.prob), *g, s);
+        if (rc != SCG_OK) return rc;
+    }
     Runner<T> R{reinterpret_cast<const Prob<T>*>(base + pl.prob), pl.cnt_ray, pl.cnt_img, pl.cnt_row,
                 pl.cnt_proj, g->n_bins, s, 0};
+    R.g_bp = pl.cnt_bp;
     const Program pg = make_program(prm, variant);
 
     if (resumed) {
@@ -137,7 +155,7 @@ int solve_impl(const scg_geometry* g, int variant, int precision, const scg_para
     // device after every body (no host round trip per iteration).  Fallback:
     // one graph per body, launched in batches and polled one batch ahead.
     GraphKey key{dev, work, precision, variant, pg.trial_passes, pg.ksteps, g->n, g->n_angles, g->n_bins,
-                 prm->host_loop ? 1 : 0};
+                 prm->host_loop ? 1 : 0, pl.proj_shift};
     BodyGraph bg{nullptr, 0, false};
     {
         std::lock_guard<std::mutex> lk(g_mu);
@@ -379,7 +397,7 @@ int backproject_impl(const scg_geometry& g, const void* r, void* x, void* work, 
     if (rc) return rc;
     const Prob<T>* d = reinterpret_cast<const Prob<T>*>(base + pl.prob);
     launch_sino_pairs<T>(d, pl.cnt_ray, SB_R, s);
-    launch_backproject<T>(d, nullptr, pl.cnt_img, 1, SB_R, SB_R, IB_AUX, IB_AUX, FIN_NONE, s);
+    launch_backproject<T>(d, nullptr, pl.cnt_bp, 1, SB_R, SB_R, IB_AUX, IB_AUX, FIN_NONE, s);
     CK(cudaGetLastError());
     return SCG_OK;
 }
@@ -464,10 +482,11 @@ BatchPlan make_batch_plan(const scg_problem* pr, int count, int variant, int pre
     b.plans.resize(count);
     for (int i = 0; i < count; ++i) {
         b.plans[i] = make_plan(pr[i].geometry, variant, precision, PLAN_SOLVE);
-        b.n_items[K_PROJ] += b.plans[i].cnt_proj;
+        b.n_items[K_PROJ] += max_proj_items(pr[i].geometry.n_angles, pr[i].geometry.n_bins);
         b.n_items[K_IMG] += b.plans[i].cnt_img;
         b.n_items[K_RAY] += b.plans[i].cnt_ray;
         b.n_items[K_ROW] += b.plans[i].cnt_row;
+        b.n_items[K_BP] += b.plans[i].cnt_bp;
         if (pr[i].geometry.n_bins > max_nb) max_nb = pr[i].geometry.n_bins;
     }
     b.nb_cap = (max_nb + 127) / 128 * 128;
@@ -488,9 +507,9 @@ struct BatchKey {
     int cap_items[K_COUNT];
     bool operator<(const BatchKey& o) const {
         return std::tie(dev, work, prec, variant, trial_passes, ksteps, cap_probs, nb_cap, cap_items[0],
-                        cap_items[1], cap_items[2], cap_items[3]) <
+                        cap_items[1], cap_items[2], cap_items[3], cap_items[4]) <
                std::tie(o.dev, o.work, o.prec, o.variant, o.trial_passes, o.ksteps, o.cap_probs, o.nb_cap,
-                        o.cap_items[0], o.cap_items[1], o.cap_items[2], o.cap_items[3]);
+                        o.cap_items[0], o.cap_items[1], o.cap_items[2], o.cap_items[3], o.cap_items[4]);
     }
 };
 std::map<BatchKey, BodyGraph> g_batch_graphs;
@@ -500,7 +519,7 @@ int batch_impl(const scg_problem* pr, int count, int variant, int precision, con
                void* work, size_t work_bytes, scg_result* results, cudaStream_t user_stream) {
     using E = typename Tr<T>::S;
     using C = typename Tr<T>::C;
-    const BatchPlan bp = make_batch_plan(pr, count, variant, prec_of<T>());
+    BatchPlan bp = make_batch_plan(pr, count, variant, prec_of<T>());
     if (work_bytes < bp.total || ((uintptr_t)work & 15u)) return SCG_ERR_WORKSPACE;
     if (uses_filter(variant) && (size_t)(3 * bp.nb_cap) * sizeof(C) > 227 * 1024) return SCG_ERR_UNSUPPORTED;
     unsigned char* base = (unsigned char*)work;
@@ -521,16 +540,15 @@ int batch_impl(const scg_problem* pr, int count, int variant, int precision, con
     std::vector<std::vector<Item>> items(K_COUNT);
     for (int k = 0; k < K_COUNT; ++k) items[k].reserve(bp.cap_items[k]);
     CK(cudaMemsetAsync(base, 0, bp.total, s));
+    Prob<T>* slots = reinterpret_cast<Prob<T>*>(base + bp.probs);
     for (int i = 0; i < count; ++i) {
-        const Plan& pl = bp.plans[i];
+        Plan& pl = bp.plans[i];
         unsigned char* rb = base + bp.region[i];
         const double scale = system_scale(pr[i].geometry, prec_of<T>());
         scales[i] = scale;
         Prob<T> P = make_prob<T>(pr[i].geometry, pl, rb, scale);
         P.y = (const E*)pr[i].y;
         P.img[IB_AUX] = (E*)pr[i].x0;
-        probs[i] = P;
-        append_items(pl, i, items.data());
         DevState st = initial_state(prm, pr[i].eps * scale * scale, variant);
         CK(cudaMemcpyAsync(rb + pl.state, &st, sizeof(st), cudaMemcpyHostToDevice, s));
         std::vector<Angle<C>> ang;
@@ -540,6 +558,11 @@ int batch_impl(const scg_problem* pr, int count, int variant, int precision, con
             const double mu = prm->mu > 0.0 ? prm->mu : 2.0 * M_PI / pl.P;
             launch_taps<C>(reinterpret_cast<C*>(rb + pl.taps), pr[i].geometry.n_bins, pl.P, mu, prm->filter_gain, s);
         }
+        // the problem's own slot serves the shape tuner (a single-problem launch)
+        const int rc = tune_proj_shape<T>(P, pl, slots + i, pr[i].geometry, s);
+        if (rc != SCG_OK) return rc;
+        probs[i] = P;
+        append_items(pl, i, items.data());
         // (pageable host sources are staged before cudaMemcpyAsync returns,
         // so st and ang may be reused for the next problem)
     }
@@ -549,29 +572,33 @@ int batch_impl(const scg_problem* pr, int count, int variant, int precision, con
     stopped.done = 1;
     CK(cudaMemcpyAsync(base + bp.dummy, &stopped, sizeof(stopped), cudaMemcpyHostToDevice, s));
     for (int i = count; i < bp.cap_probs; ++i) probs[i].st = reinterpret_cast<DevState*>(base + bp.dummy);
+    // projector items depend on the tuned shapes: launch their rounded count
+    int grid[K_COUNT];
+    for (int k = 0; k < K_COUNT; ++k) grid[k] = k == K_PROJ ? round_up_bucket((int)items[k].size()) : bp.cap_items[k];
     for (int k = 0; k < K_COUNT; ++k)
-        while ((int)items[k].size() < bp.cap_items[k]) items[k].push_back(Item{count, 0, 0, 0});
+        while ((int)items[k].size() < grid[k]) items[k].push_back(Item{count, 0, 0, 0});
     BatchState bs{0, prm->max_iter + 2, count, 0};
     CK(cudaMemcpyAsync(base + bp.state, &bs, sizeof(bs), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(base + bp.probs, probs.data(), sizeof(Prob<T>) * bp.cap_probs, cudaMemcpyHostToDevice, s));
     for (int k = 0; k < K_COUNT; ++k)
-        if (bp.cap_items[k])
-            CK(cudaMemcpyAsync(base + bp.items[k], items[k].data(), sizeof(Item) * bp.cap_items[k],
+        if (grid[k])
+            CK(cudaMemcpyAsync(base + bp.items[k], items[k].data(), sizeof(Item) * grid[k],
                                cudaMemcpyHostToDevice, s));
     const Prob<T>* d = reinterpret_cast<const Prob<T>*>(base + bp.probs);
-    Runner<T> R{d, bp.cap_items[K_RAY], bp.cap_items[K_IMG], bp.cap_items[K_ROW], bp.cap_items[K_PROJ],
-                bp.nb_cap, s, 0};
+    Runner<T> R{d, grid[K_RAY], grid[K_IMG], grid[K_ROW], grid[K_PROJ], bp.nb_cap, s, 0};
     R.i_ray = reinterpret_cast<const Item*>(base + bp.items[K_RAY]);
     R.i_img = reinterpret_cast<const Item*>(base + bp.items[K_IMG]);
     R.i_row = reinterpret_cast<const Item*>(base + bp.items[K_ROW]);
     R.i_proj = reinterpret_cast<const Item*>(base + bp.items[K_PROJ]);
+    R.g_bp = grid[K_BP];
+    R.i_bp = reinterpret_cast<const Item*>(base + bp.items[K_BP]);
     const Program pg = make_program(prm, variant);
     run_init<T>(R, pg);
     CK(cudaGetLastError());
 
     BatchState* bsd = reinterpret_cast<BatchState*>(base + bp.state);
     BatchKey key{dev, work, precision, variant, pg.trial_passes, pg.ksteps, bp.cap_probs, bp.nb_cap,
-                 {bp.cap_items[0], bp.cap_items[1], bp.cap_items[2], bp.cap_items[3]}};
+                 {grid[0], grid[1], grid[2], grid[3], grid[4]}};
     BodyGraph bg{nullptr, 0, false};
     {
         std::lock_guard<std::mutex> lk(g_mu);
@@ -677,6 +704,20 @@ int batch_impl(const scg_problem* pr, int count, int variant, int precision, con
      : (p) == SCG_F16 ? F<__half>(__VA_ARGS__) : F<__nv_bfloat16>(__VA_ARGS__))
 
 }  // namespace
+
+namespace scg {
+namespace host {
+int proj_shape_lookup(int dev, int precision, const scg_geometry& g) {
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    auto it = g_shapes.find(shape_key(dev, precision, g));
+    return it == g_shapes.end() ? -1 : it->second;
+}
+void proj_shape_store(int dev, int precision, const scg_geometry& g, int shift) {
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    g_shapes[shape_key(dev, precision, g)] = shift;
+}
+}  // namespace host
+}  // namespace scg
 
 extern "C" {
 
