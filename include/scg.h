@@ -180,6 +180,28 @@ int scg_project(const scg_geometry* g, int precision, const void* x, void* y,
 int scg_backproject(const scg_geometry* g, int precision, const void* r, void* x,
                     void* work, size_t work_bytes, void* stream);
 
+/* ---- Prepared operator pair ------------------------------------------------
+ * For callers that apply A and A^T many times with one geometry (their own
+ * iterative methods): the angle table, descriptors and zero pads are placed in
+ * the workspace once, so each application is only device work (a descriptor
+ * update and two kernels), asynchronous and capturable in a CUDA graph.  The
+ * workspace (scg_op_workspace_bytes) belongs to the operator until
+ * scg_operator_destroy; applications through one operator must not overlap in
+ * time (they share its workspace).  The paper has no counterpart. */
+typedef struct scg_operator scg_operator;    /* opaque */
+
+/* Prepare (blocking: returns after the workspace is set up).  Returns
+ * SCG_ERR_INVALID / SCG_ERR_UNSUPPORTED / SCG_ERR_WORKSPACE as scg_project. */
+int scg_operator_create(const scg_geometry* g, int precision, void* work, size_t work_bytes,
+                        void* stream, scg_operator** out);
+/* y = A x, as scg_project (stream-ordered, asynchronous). */
+int scg_operator_project(scg_operator* op, const void* x, void* y, void* stream);
+/* x = A^T r, as scg_backproject (stream-ordered, asynchronous). */
+int scg_operator_backproject(scg_operator* op, const void* r, void* x, void* stream);
+/* Release the host handle (the workspace is the caller's again once the
+ * stream work issued through the operator has completed). */
+int scg_operator_destroy(scg_operator* op);
+
 /* *tv_out (device double) = TV(x), the secondary criterion: isotropic forward
  * differences over the (N-1)^2 interior terms (the paper names TV without a
  * formula; Sec. 1).  Summed in FP64. */

@@ -552,6 +552,21 @@ k_vec(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int op,
 // tile first forms x_{k+1} = x_{k+1/2} + alpha p' (written to X) and takes the
 // stencil of that.  src selects the image when not fused; write_grad = 0 only
 // sums TV.
+// Norms of the TV terms.  FP32: the hardware square-root approximations
+// (relative error below 2^-22, against twice the instructions for the
+// correctly rounded forms); FP64: sqrt and division, as the definition reads.
+__device__ __forceinline__ float tv_norm(float v) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ float tv_rsqrt(float v) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ double tv_norm(double v) { return sqrt(v); }
+
 template <typename T>
 __global__ void __launch_bounds__(kTileThreads)
 k_tvgrad(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int src,
@@ -592,8 +607,16 @@ k_tvgrad(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int 
         if (gi >= 0 && gi < N - 1 && gj >= 0 && gj < N - 1) {
             const C x0 = xs[ii][jj];
             const C du = xs[ii + 1][jj] - x0, dv = xs[ii][jj + 1] - x0;
-            const C nrm = tsqrt(du * du + dv * dv);
-            if (nrm > C(0)) { a = du / nrm; c = dv / nrm; }
+            const C n2 = du * du + dv * dv;
+            if (n2 > C(0)) {
+                if constexpr (std::is_same<C, double>::value) {
+                    const C nrm = sqrt(n2);
+                    a = du / nrm; c = dv / nrm;
+                } else {
+                    const C r = tv_rsqrt(n2);
+                    a = du * r; c = dv * r;
+                }
+            }
         }
         tu[ii][jj] = a;
         tv[ii][jj] = c;
@@ -609,7 +632,7 @@ k_tvgrad(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int 
         if (fuse_update) P.img[IB_X][g] = to_s<S>(x);
         if (i < N - 1 && j < N - 1) {         // this tile's own term (i, j)
             const C du = xs[ty + 2][tx + 1] - x, dv = xs[ty + 1][tx + 2] - x;
-            v[0] = acc_val(tsqrt(du * du + dv * dv));
+            v[0] = acc_val(tv_norm(du * du + dv * dv));
         }
         const C gr = rnd<T>(-(tu[ty + 1][tx + 1] + tv[ty + 1][tx + 1]) + tu[ty][tx + 1] + tv[ty + 1][tx]);
         if (write_grad) P.img[IB_TVG][g] = to_s<S>(gr);
@@ -624,15 +647,24 @@ k_tvgrad(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int 
 // and x itself, their TVs summed in one pass over x and dTV.  The accepted
 // point is later formed by k_vec(VEC_PERTURB) with the same coefficient and
 // the same fma, so the stored x_{k+1/2} is exactly the point that was tested.
+// Blocks take the backprojector's tiles (32 x kBpTileH, 128 threads), each
+// thread TH/4 pixels of one column, so a thread adds its pixels' terms before
+// the warp-level sums.  The FP32 kernel takes each term's square root with the
+// hardware approximation (relative error below 2^-22, where the correctly
+// rounded sqrtf costs half the pass): every TV this pass compares -- the
+// candidates' and x's own -- is summed the same way, so the acceptance test
+// TV(z) <= TV(x) compares like with like.
 template <typename T>
-__global__ void __launch_bounds__(kTileThreads)
+__global__ void __launch_bounds__(kBackThreads)
 k_trial(const Prob<T>* __restrict__ probs, const Item* __restrict__ items) {
     using A = Acc<T>;
     using C = typename Tr<T>::C;
     using S = typename Tr<T>::S;
     constexpr int NS = kTrials + 1;                 // 31 candidates + x itself
-    constexpr int NW = kTileThreads / 32;
-    const Item it = decode_item(probs, items, 1);
+    constexpr int NW = kBackThreads / 32;
+    constexpr int TH = std::is_same<T, double>::value ? kBpTileH64 : kBpTileH32;
+    constexpr int PIX = TH / NW, kStep = NW;        // pixels per thread, row step
+    const Item it = decode_item(probs, items, 4);
     const Prob<T>& P = probs[it.prob];
     const DevState& st = *P.st;
     if (st.done || st.accepted != 0) return;
@@ -643,40 +675,50 @@ k_trial(const Prob<T>* __restrict__ probs, const Item* __restrict__ items) {
     if (threadIdx.x < kTrials) coef_s[threadIdx.x] = (C)st.trial_coef[threadIdx.x];
     __syncthreads();
     const int N = P.n;
-    const int i = it.u * kTileH + threadIdx.x / kTileW;
-    const int j = it.v * kTileW + threadIdx.x % kTileW;
-    const bool in = (i < N - 1) && (j < N - 1);
-    C x0 = C(0), xu = C(0), xv = C(0), q0 = C(0), qu = C(0), qv = C(0);
-    if (in) {
-        const S* X = P.img[IB_X];
-        const S* G = P.img[IB_TVG];
-        const size_t g0 = (size_t)i * N + j;
-        x0 = to_c(X[g0]); xu = to_c(X[g0 + N]); xv = to_c(X[g0 + 1]);
-        q0 = to_c(G[g0]); qu = to_c(G[g0 + N]); qv = to_c(G[g0 + 1]);
+    const int j = it.v * kTileW + lane;
+    C x0[PIX], xu[PIX], xv[PIX], q0[PIX], qu[PIX], qv[PIX];
+    bool in[PIX];
+#pragma unroll
+    for (int k = 0; k < PIX; ++k) {
+        const int i = it.u * TH + warp + k * kStep;
+        in[k] = (i < N - 1) && (j < N - 1);
+        x0[k] = xu[k] = xv[k] = q0[k] = qu[k] = qv[k] = C(0);
+        if (in[k]) {
+            const S* X = P.img[IB_X];
+            const S* G = P.img[IB_TVG];
+            const size_t g0 = (size_t)i * N + j;
+            x0[k] = to_c(X[g0]); xu[k] = to_c(X[g0 + N]); xv[k] = to_c(X[g0 + 1]);
+            q0[k] = to_c(G[g0]); qu[k] = to_c(G[g0 + N]); qv[k] = to_c(G[g0 + 1]);
+        }
     }
 #pragma unroll
     for (int grp = 0; grp < NS / 8; ++grp) {
         A v[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int t = grp * 8 + k;
-            C du, dv;
-            if (t < kTrials) {
-                // trial points as they would be stored (VEC_PERTURB rounds the same way)
-                const C c = coef_s[t];
-                const C z0 = rnd<T>(fma_rn(c, q0, x0)), zu = rnd<T>(fma_rn(c, qu, xu)),
-                        zv = rnd<T>(fma_rn(c, qv, xv));
-                du = zu - z0; dv = zv - z0;
-            } else {
-                du = xu - x0; dv = xv - x0;
+        for (int kk = 0; kk < 8; ++kk) {
+            const int t = grp * 8 + kk;
+            C sum = C(0);                          // this thread's pixels: non-negative terms
+#pragma unroll
+            for (int k = 0; k < PIX; ++k) {
+                C du, dv;
+                if (t < kTrials) {
+                    // trial points as they would be stored (VEC_PERTURB rounds the same way)
+                    const C c = coef_s[t];
+                    const C z0 = rnd<T>(fma_rn(c, q0[k], x0[k])), zu = rnd<T>(fma_rn(c, qu[k], xu[k])),
+                            zv = rnd<T>(fma_rn(c, qv[k], xv[k]));
+                    du = zu - z0; dv = zv - z0;
+                } else {
+                    du = xu[k] - x0[k]; dv = xv[k] - x0[k];
+                }
+                sum += in[k] ? tv_norm(du * du + dv * dv) : C(0);
             }
-            v[k] = acc_val(in ? tsqrt(du * du + dv * dv) : C(0));
+            v[kk] = acc_val(sum);
         }
 #pragma unroll
-        for (int k = 0; k < 8; ++k) v[k] = warp_sum<true>(v[k]);
+        for (int kk = 0; kk < 8; ++kk) v[kk] = warp_sum<true>(v[kk]);
         if (lane == 0) {
 #pragma unroll
-            for (int k = 0; k < 8; ++k) wsum[warp][grp * 8 + k] = v[k];
+            for (int kk = 0; kk < 8; ++kk) wsum[warp][grp * 8 + kk] = v[kk];
         }
     }
     __syncthreads();
@@ -688,43 +730,49 @@ k_trial(const Prob<T>* __restrict__ probs, const Item* __restrict__ items) {
         __threadfence();
     }
     __syncthreads();
-    if (threadIdx.x == 0) s_last = (atomicAdd(P.counter, 1u) + 1u == (unsigned)P.cnt_img);
+    if (threadIdx.x == 0) s_last = (atomicAdd(P.counter, 1u) + 1u == (unsigned)P.cnt_bp);
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    // last block: each thread adds the partials of items tid, tid + 256, ...
-    // for eight slots at a time (independent 16-byte loads, all in flight),
-    // then the block adds the per-thread sums in a fixed order
-    __shared__ A red[32 * 8];
-    double sums[NS];
-#pragma unroll 1
-    for (int g8 = 0; g8 < NS / 8; ++g8) {
+    // last block: warp w adds slots 8w .. 8w+7 over all items (lane l takes
+    // items l, l+32, ...; independent 16-byte loads), then across its lanes in a
+    // fixed order; thread 0 collects the four warps' results
+    static_assert(NW * 8 == NS, "one warp per eight slots");
+    __shared__ double red[NS];
+    {
         A acc[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) acc_zero(acc[k]);
-        for (int q = threadIdx.x; q < P.cnt_img; q += kTileThreads) {
-            const A* src = parts + (size_t)q * kSlots + g8 * 8;
+        for (int q = lane; q < P.cnt_bp; q += 32) {
+            const A* src = parts + (size_t)q * kSlots + warp * 8;
 #pragma unroll
             for (int k = 0; k < 8; k += 2) {
-                A x0, x1;
+                A y0, y1;
                 if constexpr (std::is_same<A, double>::value) {
                     const double2 w = __ldcg(reinterpret_cast<const double2*>(src + k));
-                    x0 = w.x; x1 = w.y;
+                    y0 = w.x; y1 = w.y;
                 } else {
                     const float4 w = __ldcg(reinterpret_cast<const float4*>(src + k));
-                    x0.hi = w.x; x0.lo = w.y; x1.hi = w.z; x1.lo = w.w;
+                    y0.hi = w.x; y0.lo = w.y; y1.hi = w.z; y1.lo = w.w;
                 }
-                acc[k] = acc_add(acc[k], x0);
-                acc[k + 1] = acc_add(acc[k + 1], x1);
+                acc[k] = acc_add(acc[k], y0);
+                acc[k + 1] = acc_add(acc[k + 1], y1);
             }
         }
-        block_sum<A, 8>(acc, red);
-        if (threadIdx.x == 0) {
 #pragma unroll
-            for (int k = 0; k < 8; ++k) sums[g8 * 8 + k] = acc_to_double(acc[k]);
+        for (int k = 0; k < 8; ++k) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc[k] = acc_add(acc[k], acc_shfl_down(acc[k], o));
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) red[warp * 8 + k] = acc_to_double(acc[k]);
         }
     }
+    __syncthreads();
     if (threadIdx.x == 0) {
+        double sums[NS];
+        for (int t = 0; t < NS; ++t) sums[t] = red[t];
         *P.counter = 0u;
         finalize<T>(FIN_TRIAL, P, sums);
     }
@@ -847,6 +895,22 @@ void launch_loop_cond(DevState* st, cudaGraphConditionalHandle h, cudaStream_t s
     k_loop_cond<<<1, 32, 0, s>>>(st, h);
 }
 
+// Point a prepared operator's descriptor at the caller's buffers (one thread;
+// keeps every application stream-ordered and free of host copies).
+template <typename T>
+__global__ void k_set_io(Prob<T>* d, const typename Tr<T>::S* in_sino, typename Tr<T>::S* out_sino,
+                         typename Tr<T>::S* image) {
+    if (threadIdx.x != 0) return;
+    d->user_in = in_sino;
+    d->user_out = out_sino;
+    d->img[IB_AUX] = image;
+}
+template <typename T>
+void launch_set_io(Prob<T>* d, const typename Tr<T>::S* in_sino, typename Tr<T>::S* out_sino,
+                   typename Tr<T>::S* image, cudaStream_t s) {
+    k_set_io<T><<<1, 32, 0, s>>>(d, in_sino, out_sino, image);
+}
+
 // Set every problem's stop flag (used around the final kernels of a batch).
 template <typename T>
 __global__ void k_set_done(const Prob<T>* probs, int count, int value) {
@@ -926,7 +990,7 @@ void launch_tvgrad(const Prob<T>* d, const Item* items, int grid, int src, int f
 }
 template <typename T>
 void launch_trial(const Prob<T>* d, const Item* items, int grid, cudaStream_t s) {
-    k_trial<T><<<grid, kTileThreads, 0, s>>>(d, items);
+    k_trial<T><<<grid, kBackThreads, 0, s>>>(d, items);
 }
 template <typename T>
 void launch_sino_axpy(const Prob<T>* d, const Item* items, int grid, int step, cudaStream_t s) {
@@ -962,6 +1026,8 @@ void launch_taps(T* taps, int nb, int P, double mu, double gain, cudaStream_t s)
                                           cudaStream_t);                                          \
     template void launch_sino_pairs<T>(const Prob<T>*, int, int, cudaStream_t);                   \
     template void launch_set_done<T>(const Prob<T>*, int, int, cudaStream_t);                     \
+    template void launch_set_io<T>(Prob<T>*, const typename Tr<T>::S*, typename Tr<T>::S*,          \
+                                   typename Tr<T>::S*, cudaStream_t);                            \
     template void launch_slots_done<T>(const Prob<T>*, const int*, int, int*, int, int, cudaStream_t); \
     template void launch_loop_cond_batch<T>(const Prob<T>*, BatchState*, cudaGraphConditionalHandle, \
                                             cudaStream_t);

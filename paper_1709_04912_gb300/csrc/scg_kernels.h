@@ -43,6 +43,9 @@ template <typename T>
 void launch_sino_pairs(const Prob<T>* d, int grid, int dst, cudaStream_t s);
 void launch_loop_cond(DevState* st, cudaGraphConditionalHandle h, cudaStream_t s);
 template <typename T>
+void launch_set_io(Prob<T>* d, const typename Tr<T>::S* in_sino, typename Tr<T>::S* out_sino,
+                   typename Tr<T>::S* image, cudaStream_t s);
+template <typename T>
 void launch_set_done(const Prob<T>* d, int count, int value, cudaStream_t s);
 template <typename T>
 void launch_slots_done(const Prob<T>* d, const int* slots, int count, int* out, int set, int value,

@@ -447,6 +447,64 @@ int filter_impl(const scg_geometry& g, double mu, double gain, const void* r, vo
 }
 
 // ---------------------------------------------------------------------------
+// Prepared operator pair: set up once, then each application is device work
+// only (descriptor update by a one-thread kernel, view or pair-row pass, and
+// the projector or backprojector).
+struct OperatorBase {
+    virtual ~OperatorBase() {}
+    virtual int project(const void* x, void* y, cudaStream_t s) = 0;
+    virtual int backproject(const void* r, void* x, cudaStream_t s) = 0;
+};
+
+template <typename T>
+struct Operator final : OperatorBase {
+    using E = typename Tr<T>::S;
+    scg_geometry g;
+    Plan pl;
+    Prob<T>* d = nullptr;
+
+    int init(const scg_geometry& geo, void* work, size_t wb, cudaStream_t s) {
+        g = geo;
+        Prob<T> P;
+        int rc = op_setup<T>(g, work, wb, s, &pl, &P);
+        if (rc) return rc;
+        // projector shape: the one tuned for this geometry bucket, if any (an
+        // operator workspace has no scratch sinogram to tune on)
+        int dev = 0;
+        CK(cudaGetDevice(&dev));
+        const int sh = prec_of<T>() == SCG_F64 ? -1 : proj_shape_lookup(dev, prec_of<T>(), g);
+        if (sh >= 0) {
+            set_proj_shape(pl, g.n_angles, g.n_bins, sh);
+            P.cnt_proj = pl.cnt_proj; P.proj_blocks = pl.proj_blocks; P.proj_shift = sh;
+        }
+        unsigned char* base = (unsigned char*)work;
+        // zero pads of the views and of the pair rows, once
+        CK(cudaMemsetAsync(base + pl.view_rm, 0, 2 * sizeof(E) * (size_t)g.n * pl.S, s));
+        CK(cudaMemsetAsync(base + pl.view_cm, 0, 2 * sizeof(E) * (size_t)g.n * pl.S, s));
+        CK(cudaMemsetAsync(base + pl.sino[SB_R], 0, 2 * sizeof(E) * (size_t)g.n_angles * pl.SB, s));
+        rc = upload_prob<T>(P, pl, work, s);
+        if (rc) return rc;
+        d = reinterpret_cast<Prob<T>*>(base + pl.prob);
+        CK(cudaStreamSynchronize(s));
+        return SCG_OK;
+    }
+    int project(const void* x, void* y, cudaStream_t s) override {
+        launch_set_io<T>(d, nullptr, (E*)y, (E*)const_cast<void*>(x), s);
+        launch_vec<T>(d, nullptr, pl.cnt_img, VEC_VIEWS, IB_AUX, FIN_NONE, s);
+        launch_project<T>(d, nullptr, pl.cnt_proj, SB_Q, PROJ_PLAIN_OUT, FIN_NONE, s);
+        CK(cudaGetLastError());
+        return SCG_OK;
+    }
+    int backproject(const void* r, void* x, cudaStream_t s) override {
+        launch_set_io<T>(d, (const E*)r, nullptr, (E*)x, s);
+        launch_sino_pairs<T>(d, pl.cnt_ray, SB_R, s);
+        launch_backproject<T>(d, nullptr, pl.cnt_bp, 1, SB_R, SB_R, IB_AUX, IB_AUX, FIN_NONE, s);
+        CK(cudaGetLastError());
+        return SCG_OK;
+    }
+};
+
+// ---------------------------------------------------------------------------
 // Batched solves.  Workspace: [BatchState][an always-stopped DevState][Prob x
 // capacity][item lists for the projector, image-tile, sinogram-row and
 // filter-row kinds][one single-solve region per problem].  Items carry
@@ -821,6 +879,49 @@ int scg_solve(const scg_geometry* g, int variant, int precision, const scg_param
                           work_bytes, res, trace, trace_rows, resume, final_state, s);
     if (rc < 0 && rc != SCG_ERR_BREAKDOWN) res->status = rc;
     return rc;
+}
+
+}  // extern "C"
+
+struct scg_operator {
+    OperatorBase* impl;
+};
+
+extern "C" {
+
+int scg_operator_create(const scg_geometry* g, int precision, void* work, size_t work_bytes, void* stream,
+                        scg_operator** out) {
+    if (!valid_geometry(g) || !work || !out) return SCG_ERR_INVALID;
+    if (!valid_prec(precision)) return SCG_ERR_UNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    OperatorBase* impl = nullptr;
+    int rc;
+    switch (precision) {
+    case SCG_F64: { auto* o = new Operator<double>(); rc = o->init(*g, work, work_bytes, s); impl = o; break; }
+    case SCG_F32: { auto* o = new Operator<float>(); rc = o->init(*g, work, work_bytes, s); impl = o; break; }
+    case SCG_F16: { auto* o = new Operator<__half>(); rc = o->init(*g, work, work_bytes, s); impl = o; break; }
+    default: { auto* o = new Operator<__nv_bfloat16>(); rc = o->init(*g, work, work_bytes, s); impl = o; break; }
+    }
+    if (rc != SCG_OK) { delete impl; return rc; }
+    *out = new scg_operator{impl};
+    return SCG_OK;
+}
+
+int scg_operator_project(scg_operator* op, const void* x, void* y, void* stream) {
+    if (!op || !x || !y) return SCG_ERR_INVALID;
+    return op->impl->project(x, y, (cudaStream_t)stream);
+}
+
+int scg_operator_backproject(scg_operator* op, const void* r, void* x, void* stream) {
+    if (!op || !r || !x) return SCG_ERR_INVALID;
+    return op->impl->backproject(r, x, (cudaStream_t)stream);
+}
+
+int scg_operator_destroy(scg_operator* op) {
+    if (!op) return SCG_ERR_INVALID;
+    delete op->impl;
+    delete op;
+    return SCG_OK;
 }
 
 size_t scg_batch_workspace_bytes(const scg_problem* problems, int count, int variant, int precision) {

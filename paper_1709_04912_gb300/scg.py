@@ -107,6 +107,13 @@ def load(build_if_needed: bool = True):
     L.scg_batch_workspace_bytes.restype = sz
     L.scg_batch_workspace_bytes.argtypes = [pp, i, i, i]
     L.scg_solve_batch.argtypes = [pp, i, i, i, ctypes.POINTER(Params), vp, sz, ctypes.POINTER(Result), vp]
+    L.scg_operator_create.argtypes = [gp, i, vp, sz, vp, ctypes.POINTER(vp)]
+    L.scg_operator_project.argtypes = [vp, vp, vp, vp]
+    L.scg_operator_backproject.argtypes = [vp, vp, vp, vp]
+    L.scg_operator_destroy.argtypes = [vp]
+    for name in ("scg_operator_create", "scg_operator_project", "scg_operator_backproject",
+                 "scg_operator_destroy"):
+        getattr(L, name).restype = i
     L.scg_server_footprint.restype = sz
     L.scg_server_footprint.argtypes = [gp, i, i]
     L.scg_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
@@ -480,6 +487,50 @@ class Server:
             load().scg_server_destroy(self._h)
             self._h = None
             self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Operator:
+    """Prepared A / A^T pair for one geometry and precision (scg_operator_*):
+    each application is device work only, so it is asynchronous and can be
+    captured in a CUDA graph."""
+
+    def __init__(self, n: int, n_angles: int, n_bins: int, dtype=torch.float32, device="cuda:0"):
+        L = load()
+        self.n, self.na, self.nb = int(n), int(n_angles), int(n_bins)
+        self.dtype, self.device = dtype, torch.device(device)
+        prec = _prec_of(dtype)
+        g = geometry(n, n_angles, n_bins)
+        nbytes = L.scg_op_workspace_bytes(ctypes.byref(g), prec)
+        self.work = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=self.device)
+        h = ctypes.c_void_p()
+        _check(L.scg_operator_create(ctypes.byref(g), prec, self.work.data_ptr(), self.work.numel(),
+                                     _stream(self.device), ctypes.byref(h)), "scg_operator_create")
+        self._h = h
+
+    def project(self, x: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty((self.na, self.nb), dtype=self.dtype, device=self.device)
+        _check(load().scg_operator_project(self._h, _dev_ptr(x, "x"), _dev_ptr(out, "y"),
+                                           _stream(self.device)), "scg_operator_project")
+        return out
+
+    def backproject(self, r: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty((self.n, self.n), dtype=self.dtype, device=self.device)
+        _check(load().scg_operator_backproject(self._h, _dev_ptr(r, "r"), _dev_ptr(out, "x"),
+                                               _stream(self.device)), "scg_operator_backproject")
+        return out
+
+    def close(self):
+        if self._h:
+            load().scg_operator_destroy(self._h)
+            self._h = None
 
     def __del__(self):
         try:

@@ -156,3 +156,14 @@ def test_reduced_storage_workspaces(lib):
         assert lib.scg_solve_workspace_bytes(ctypes.byref(g), v, scg.BF16) == 0
     assert lib.scg_op_workspace_bytes(ctypes.byref(g), scg.F16) > 0
     assert lib.scg_solve_workspace_bytes(ctypes.byref(g), 2, 4) == 0
+
+
+def test_operator_rejects_bad_arguments_without_device_work(lib):
+    h = ctypes.c_void_p()
+    fake = ctypes.c_void_p(256)
+    bad = scg.geometry(1, 90, 95)
+    assert lib.scg_operator_create(ctypes.byref(bad), scg.F32, fake, 1 << 20, None, ctypes.byref(h)) == -1
+    g = scg.geometry(64, 90, 95)
+    assert lib.scg_operator_create(ctypes.byref(g), 7, fake, 1 << 20, None, ctypes.byref(h)) == -5
+    assert lib.scg_operator_project(None, fake, fake, None) == -1
+    assert lib.scg_operator_destroy(None) == -1

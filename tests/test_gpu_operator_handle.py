@@ -1,0 +1,54 @@
+"""The prepared operator pair (scg_operator_*): same values as the one-shot
+entry points, repeated applications, and capture in a CUDA graph."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1709_04912_gb300 import inputs, scg
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    assert torch.cuda.is_available()
+    return scg.load()
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64, torch.float16, torch.bfloat16])
+@pytest.mark.parametrize("n,na,nb", [(64, 90, 95), (77, 33, 110), (130, 181, 185)])
+def test_operator_equals_one_shot_entry_points(n, na, nb, dtype):
+    op = scg.Operator(n, na, nb, dtype)
+    for seed in range(2):                       # repeated applications on one workspace
+        x = torch.tensor(inputs.normal(seed, "x", n * n).reshape(n, n), dtype=torch.float32).to(dtype).to(DEV)
+        r = torch.tensor(inputs.normal(seed, "r", na * nb).reshape(na, nb), dtype=torch.float32).to(dtype).to(DEV)
+        assert torch.equal(op.project(x), scg.scg_project(x, na, nb))
+        assert torch.equal(op.backproject(r), scg.scg_backproject(r, n))
+    op.close()
+
+
+def test_operator_in_a_cuda_graph():
+    n, na, nb = 96, 120, 137
+    op = scg.Operator(n, na, nb, torch.float32)
+    x = torch.tensor(inputs.ellipse_phantom(n, 6, 1), dtype=torch.float32, device=DEV)
+    y = torch.empty((na, nb), dtype=torch.float32, device=DEV)
+    z = torch.empty((n, n), dtype=torch.float32, device=DEV)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):                  # warm up off the default stream before capture
+        op.project(x, y)
+        op.backproject(y, z)
+    torch.cuda.current_stream().wait_stream(s)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        op.project(x, y)
+        op.backproject(y, z)                    # A^T A x
+    x.copy_(torch.tensor(inputs.ellipse_phantom(n, 6, 2), dtype=torch.float32, device=DEV))
+    graph.replay()
+    torch.cuda.synchronize()
+    ref = oracle.backproject(oracle.project(x.double().cpu().numpy(), na, nb), n)
+    got = z.double().cpu().numpy()
+    assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
+    op.close()
