@@ -189,8 +189,8 @@ void fill_angles(std::vector<Angle<T>>& out, int na, int n, double scale = 1.0) 
             g.kb = (T)(1.0 / mn); g.hb0 = (T)(hs / mn); g.hb1 = (T)((hs - 1.0) / mn);
             g.hb0p = (T)(hs / mn + 1.0 / mn); g.hb1p = (T)((hs - 1.0) / mn - 1.0 / mn);
         }
-        g.c24 = (int)llrint(c * 16777216.0);
-        g.s24 = (int)llrint(s * 16777216.0);
+        g.c23 = (int)llrint(c * 8388608.0);
+        g.s23 = (int)llrint(s * 8388608.0);
         g.col_driven = as >= ac ? 1 : 0;
         const double inv = g.col_driven ? 1.0 / s : 1.0 / c;
         const double e = g.col_driven ? c : s;

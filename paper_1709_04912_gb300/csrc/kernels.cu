@@ -216,15 +216,19 @@ k_project(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int
 // zero-filled by the copy itself, so the inner loop needs no bounds test.  The
 // projection of the tile's first pixel comes from 32.32 fixed point (FP64 in
 // the FP64 kernel), split into integer + fraction; each pixel adds only its
-// small in-tile offset (8.24 fixed point in the FP32 kernel).
+// small in-tile offset (9.23 fixed point in the FP32 kernel: the fraction
+// bits are directly a float mantissa).
 constexpr int kBand = 48;
-// tile height, pixels per thread, angles per chunk (FP32 arithmetic) ...
+// Tile height, pixels per thread, angles per chunk, and angle groups per
+// block (SPLIT groups of 128 threads take consecutive parts of the angles of
+// one tile and add their sums at the end; measured on GB300 at 512^2 / 720
+// angles, two groups ran 3-5 % slower than one, so one it is) ...
 template <typename T, int NRHS> struct BpCfg {
-    static constexpr int TH = kBpTileH32, PIX = 4, CH = NRHS == 1 ? 32 : 16;
+    static constexpr int TH = kBpTileH32, PIX = 4, CH = NRHS == 1 ? 32 : 16, SPLIT = 1;
 };
 // ... and FP64 (48 KB static shared memory)
 template <int NRHS> struct BpCfg<double, NRHS> {
-    static constexpr int TH = kBpTileH64, PIX = 2, CH = 8;
+    static constexpr int TH = kBpTileH64, PIX = 2, CH = 8, SPLIT = 1;
 };
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
@@ -237,8 +241,8 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 // Per-angle row of the FP32 gather (two 16-byte shared loads).
 struct __align__(16) BpRowF {
-    int base;        // band index of the tile origin's projection, in 8.24 fixed point
-    int c24, s24;    // cos, sin in 8.24
+    int base;        // band index of the tile origin's projection, in 9.23 fixed point
+    int c23, s23;    // cos, sin in 9.23
     float kb, hb0p, hb1p;
     int pad_[2];
 };
@@ -255,7 +259,7 @@ __device__ __forceinline__ long long tile_origin_fx(const Angle<float>& g, int X
 }
 
 template <typename T, int NRHS>
-__global__ void __launch_bounds__(kBackThreads)
+__global__ void __launch_bounds__(kBackThreads * BpCfg<T, NRHS>::SPLIT)
 k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int src0,
               int src1, int dst0, int dst1, int step) {
     using S2 = typename Tr<T>::S2;
@@ -263,6 +267,7 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
     using Row = typename std::conditional<std::is_same<C, float>::value, BpRowF, BpRowD>::type;
     constexpr bool kF32 = std::is_same<C, float>::value;
     constexpr int TH = BpCfg<T, NRHS>::TH, PIX = BpCfg<T, NRHS>::PIX, CH = BpCfg<T, NRHS>::CH;
+    constexpr int SPLIT = BpCfg<T, NRHS>::SPLIT;
     constexpr int kStep = TH / PIX;                   // rows between a thread's pixels
     static_assert(kTileW * kStep == kBackThreads, "one thread per column and row group");
     constexpr int kSlotsPerSeg = 16 / (int)sizeof(S2);
@@ -270,21 +275,24 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
     const Item it = decode_item(probs, items, 4);
     const Prob<T>& P = probs[it.prob];
     if (P.st->done) return;
-    __shared__ Row rows[2][CH];
-    __shared__ int slo[2][CH];                  // first slot of each band in its sinogram row
-    __shared__ __align__(16) S2 band[2][NRHS][CH][kBand];
+    __shared__ Row rows[SPLIT][2][CH];
+    __shared__ int slo[SPLIT][2][CH];           // first slot of each band in its sinogram row
+    __shared__ __align__(16) S2 band[SPLIT][2][NRHS][CH][kBand];
     const int N = P.n, na = P.na, nb = P.nb, SB = P.SB;
+    const int part = threadIdx.x / kBackThreads, tl = threadIdx.x % kBackThreads;
+    const int nap = (na + SPLIT - 1) / SPLIT;    // angles of each group
+    const int a_begin = part * nap, a_end = min(na, a_begin + nap);
     const int ti0 = it.u * TH, tj0 = it.v * kTileW;
-    const int tx = threadIdx.x % kTileW, ty = threadIdx.x / kTileW;
+    const int tx = tl % kTileW, ty = tl / kTileW;
     const int j = tj0 + tx;
     const int X2 = 2 * tj0 - (N - 1), Y2 = 2 * ti0 - (N - 1);
     const S2* R[2] = {P.sino[src0], NRHS == 2 ? P.sino[src1] : P.sino[src0]};
-    const int nchunks = (na + CH - 1) / CH;
+    const int nchunks = (nap + CH - 1) / CH;     // the same for every group
 
     auto stage_rows = [&](int ch) {
-        const int q = threadIdx.x;
-        const int a = ch * CH + q;
-        if (q < CH && a < na) {
+        const int q = tl;
+        const int a = a_begin + ch * CH + q;
+        if (q < CH && a < a_end) {
             const Angle<C> g = P.ang[a];
             // band: slots the tile can touch, from floor(projection of the origin)
             // + floor((kTileW-1) min(c, 0)) - 1, rounded down to a 16-byte boundary
@@ -294,13 +302,13 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
                 const int I = (int)(cb >> 32);
                 const int s_lo = (I + kSPad + lo) & ~(kSlotsPerSeg - 1);
                 BpRowF r;
-                // 8.24: integer part = band index of floor(cb), fraction = cb's
-                r.base = ((I + kSPad - s_lo) << 24) | (int)((unsigned)cb >> 8);
-                r.c24 = g.c24; r.s24 = g.s24;
+                // 9.23: integer part = band index of floor(cb), fraction = cb's
+                r.base = ((I + kSPad - s_lo) << 23) | (int)((unsigned)cb >> 9);
+                r.c23 = g.c23; r.s23 = g.s23;
                 r.kb = g.kb; r.hb0p = g.hb0p; r.hb1p = g.hb1p;
                 r.pad_[0] = r.pad_[1] = 0;
-                rows[ch & 1][q] = r;
-                slo[ch & 1][q] = s_lo;
+                rows[part][ch & 1][q] = r;
+                slo[part][ch & 1][q] = s_lo;
             } else {
                 const double cbt = 0.5 * (double)(nb - 1) + 0.5 * (double)X2 * g.c_d + 0.5 * (double)Y2 * g.s_d;
                 const double fl = floor(cbt);
@@ -310,22 +318,22 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
                 r.c = g.c; r.s = g.s; r.kb = g.kb; r.hb0 = g.hb0; r.hb1 = g.hb1;
                 r.frac = cbt - fl;
                 r.rel = I + kSPad - s_lo;
-                rows[ch & 1][q] = r;
-                slo[ch & 1][q] = s_lo;
+                rows[part][ch & 1][q] = r;
+                slo[part][ch & 1][q] = s_lo;
             }
         }
     };
     auto stage_copy = [&](int ch) {
-        const int a0 = ch * CH;
-        const int cnt = min(CH, na - a0);
+        const int a0 = a_begin + ch * CH;
+        const int cnt = min(CH, a_end - a0);
 #pragma unroll
         for (int h = 0; h < NRHS; ++h) {
-            for (int sg = threadIdx.x; sg < cnt * kSegs; sg += blockDim.x) {
+            for (int sg = tl; sg < cnt * kSegs; sg += kBackThreads) {
                 const int q = sg / kSegs, k = sg - q * kSegs;
-                const int slot = slo[ch & 1][q] + k * kSlotsPerSeg;
+                const int slot = slo[part][ch & 1][q] + k * kSlotsPerSeg;
                 const S2* row = R[h] + (size_t)(a0 + q) * SB;
                 const bool ok = slot >= 0 && slot + kSlotsPerSeg <= SB;
-                cp_async16(&band[ch & 1][h][q][k * kSlotsPerSeg], ok ? row + slot : row, ok ? 16 : 0);
+                cp_async16(&band[part][ch & 1][h][q][k * kSlotsPerSeg], ok ? row + slot : row, ok ? 16 : 0);
             }
         }
         cp_async_commit();
@@ -346,26 +354,26 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
         if (more) { stage_copy(ch + 1); cp_async_wait<1>(); }
         else cp_async_wait<0>();
         __syncthreads();
-        const int cnt = min(CH, na - ch * CH);
+        const int cnt = min(CH, a_end - (a_begin + ch * CH));
         const int buf = ch & 1;
         if (j < N && ti0 + ty < N) {
             if constexpr (kF32) {
 #pragma unroll 2
                 for (int q = 0; q < cnt; ++q) {
-                    const BpRowF g = rows[buf][q];
-                    // 8.24 position of the thread's first pixel in band coordinates (> 0)
-                    const int p0 = g.base + tx * g.c24 + ty * g.s24;
-                    const int dp = kStep * g.s24;
+                    const BpRowF g = rows[part][buf][q];
+                    // 9.23 position of the thread's first pixel in band coordinates (> 0)
+                    const int p0 = g.base + tx * g.c23 + ty * g.s23;
+                    const int dp = kStep * g.s23;
 #pragma unroll
                     for (int k = 0; k < PIX; ++k) {
                         const int p = p0 + k * dp;
-                        // 1 + fraction as a float in [1, 2)
-                        const float f = __int_as_float(0x3F800000 | (((unsigned)p & 0xFFFFFFu) >> 1));
+                        // 1 + fraction as a float in [1, 2): the fraction bits are the mantissa
+                        const float f = __int_as_float(0x3F800000 | ((unsigned)p & 0x7FFFFFu));
                         const float w0 = __saturatef(fmaf(-f, g.kb, g.hb0p));
                         const float w1 = __saturatef(fmaf(f, g.kb, g.hb1p));
 #pragma unroll
                         for (int h = 0; h < NRHS; ++h) {
-                            const float2 e = to_c2(band[buf][h][q][p >> 24]);
+                            const float2 e = to_c2(band[part][buf][h][q][p >> 23]);
                             acc[h][k] = fmaf(w0, e.x, fmaf(w1, e.y, acc[h][k]));
                         }
                     }
@@ -373,7 +381,7 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
             } else {
                 const double dj = double(tx);
                 for (int q = 0; q < cnt; ++q) {
-                    const BpRowD& g = *reinterpret_cast<const BpRowD*>(&rows[buf][q]);
+                    const BpRowD& g = *reinterpret_cast<const BpRowD*>(&rows[part][buf][q]);
                     const double djc = dj * g.c;
 #pragma unroll
                     for (int k = 0; k < PIX; ++k) {
@@ -384,7 +392,7 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
                         const double w0 = sat(fma(-f, g.kb, g.hb0)), w1 = sat(fma(f, g.kb, g.hb1));
 #pragma unroll
                         for (int h = 0; h < NRHS; ++h) {
-                            const double2 e = to_c2(band[buf][h][q][kk]);
+                            const double2 e = to_c2(band[part][buf][h][q][kk]);
                             acc[h][k] = fma(w0, e.x, fma(w1, e.y, acc[h][k]));
                         }
                     }
@@ -393,6 +401,24 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
         }
         __syncthreads();
     }
+    if constexpr (SPLIT == 2) {
+        // the second angle group hands its sums to the first (fixed order: first + second)
+        C* xs = reinterpret_cast<C*>(&band[0][0][0][0][0]);    // band storage is free now
+        static_assert(sizeof(C) * NRHS * PIX * kBackThreads <= sizeof(band), "hand-over fits");
+        if (part == 1) {
+#pragma unroll
+            for (int h = 0; h < NRHS; ++h)
+#pragma unroll
+                for (int k = 0; k < PIX; ++k) xs[(h * PIX + k) * kBackThreads + tl] = acc[h][k];
+        }
+        __syncthreads();
+        if (part == 0) {
+#pragma unroll
+            for (int h = 0; h < NRHS; ++h)
+#pragma unroll
+                for (int k = 0; k < PIX; ++k) acc[h][k] = acc[h][k] + xs[(h * PIX + k) * kBackThreads + tl];
+        }
+    }
     using S = typename Tr<T>::S;
     const int dst[2] = {dst0, dst1};
     Acc<T> v[3];
@@ -400,7 +426,7 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
 #pragma unroll
     for (int k = 0; k < PIX; ++k) {
         const int i = ti0 + ty + k * kStep;
-        if (i >= N || j >= N) continue;
+        if (part != 0 || i >= N || j >= N) continue;
         const size_t idx = (size_t)i * N + j;
         // stored values are rounded to the storage format; the dots use them
 #pragma unroll
@@ -971,8 +997,10 @@ void launch_project(const Prob<T>* d, const Item* items, int grid, int dst, int 
 template <typename T>
 void launch_backproject(const Prob<T>* d, const Item* items, int grid, int nrhs, int src0,
                         int src1, int dst0, int dst1, int step, cudaStream_t s) {
-    if (nrhs == 2) k_backproject<T, 2><<<grid, kBackThreads, 0, s>>>(d, items, src0, src1, dst0, dst1, step);
-    else k_backproject<T, 1><<<grid, kBackThreads, 0, s>>>(d, items, src0, src1, dst0, dst1, step);
+    if (nrhs == 2)
+        k_backproject<T, 2><<<grid, kBackThreads * BpCfg<T, 2>::SPLIT, 0, s>>>(d, items, src0, src1, dst0, dst1, step);
+    else
+        k_backproject<T, 1><<<grid, kBackThreads * BpCfg<T, 1>::SPLIT, 0, s>>>(d, items, src0, src1, dst0, dst1, step);
 }
 template <typename T>
 void launch_sino_pairs(const Prob<T>* d, int grid, int dst, cudaStream_t s) {

@@ -85,7 +85,7 @@ struct Angle {
     double c_d, s_d;          // FP64 copies (FP64 kernels)
     double inv_d, c0_off_d, slope_d;
     long long c_fx, s_fx;     // 32.32 fixed point (FP32 kernels)
-    int c24, s24;             // cos, sin in 8.24 fixed point (in-tile offsets of the gather)
+    int c23, s23;             // cos, sin in 9.23 fixed point (in-tile offsets of the gather)
     T hb0p, hb1p;             // hb0 + kb, hb1 - kb (gather weights from g1 = g + 1 in [1, 2))
     T m_w;                    // 1 / inv_m: undoes the chord factor of a sinogram view
     long long inv_fx, c0_off_fx, slope_fx;
