@@ -51,7 +51,8 @@ __device__ __forceinline__ Item decode_item(const Prob<T>* probs, const Item* it
 //
 // FP32 walk: c* is carried in 32.32 fixed point C, so every increment is
 // exact; the high word is floor(c*) and the fraction's top 23 bits become a
-// float in [1, 2) by an OR into the mantissa.
+// float in [1, 2) as the mantissa under the exponent of 1 (an add of the
+// shifted word, which cannot carry into the exponent).
 // D carries the view element index of the pair at the crossing in its high
 // word (line t*S, pad kPad, floor(c*)) and the crossing's fraction in its low
 // word; adding DL = slope + S (both in 32.32) steps to the next strip.
@@ -62,7 +63,7 @@ __device__ __forceinline__ Item decode_item(const Prob<T>* probs, const Item* it
 // satisfies -1 <= floor(c*) <= N-1 (kPad >= 1), and no load runs ahead of
 // strip n-1.
 #define SCG_STRIP(V_, D_, U_, Y_)                                                                 \
-    U_ = fmaf(__saturatef(fmaf(-__int_as_float(0x3F800000 | ((unsigned)(D_) >> 9)), k2, h2p)),    \
+    U_ = fmaf(__saturatef(fmaf(-__int_as_float(0x3F800000u + ((unsigned)(D_) >> 9)), k2, h2p)),   \
               V_.x - V_.y, U_);                                                                   \
     Y_ += V_.y;
 #define SCG_LD(D_) to_c2(__ldg(view + (int)((D_) >> 32)))
