@@ -77,6 +77,30 @@ def dist_env():
             int(os.environ.get("WORLD_SIZE", 1)))
 
 
+def barrier(world):
+    """Every rank reaches this point before any goes on (no-op for one rank)."""
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(t_local: float, world: int, device=None) -> float:
+    """The slowest rank's time: the whole job's time for replicas that each
+    process their own problems."""
+    if world == 1:
+        return float(t_local)
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([float(t_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_rate(units_per_rank: int, world: int, t_max: float) -> float:
+    """Units all ranks processed per second of the slowest rank's time."""
+    return units_per_rank * world / t_max
+
+
 # ---------------------------------------------------------------------------
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
@@ -244,8 +268,7 @@ def run_ours(args, work, rank, local_rank, world):
     for _ in range(args.warmup):
         r = solve()
     torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    barrier(world)
     clocks = ClockSampler(local_rank)
     clocks.start()
     ms = []
@@ -266,12 +289,9 @@ def run_ours(args, work, rank, local_rank, world):
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
     clk = clocks.stop()
-    t_total = sum(ms) / 1e3
-    if world > 1:
-        tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_total = float(tt.item())
-    value = args.steps * world / t_total
+    barrier(world)
+    t_total = max_over_ranks(sum(ms) / 1e3, world, dev)
+    value = job_rate(args.steps, world, t_total)
     last = results[-1]
 
     # end to end through the public API with host buffers: pinned y in, x out
@@ -455,6 +475,7 @@ def run_batch(args, rank, local_rank, world):
     for _ in range(args.warmup):
         rb = batch()
     torch.cuda.synchronize()
+    barrier(world)
     clocks = ClockSampler(local_rank)
     clocks.start()
     ms = []
@@ -466,7 +487,8 @@ def run_batch(args, rank, local_rank, world):
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
     clk = clocks.stop()
-    t_batch = float(np.mean(ms)) / 1e3
+    barrier(world)
+    t_batch = max_over_ranks(float(np.mean(ms)) / 1e3, world, dev)
     # the same problems one by one (warm first: one graph per geometry)
     wsolo = torch.empty(max(scg.solve_workspace_bytes(w.n, w.n_angles, w.n_bins, variant, scg._prec_of(dtype))
                             for w in works), dtype=torch.uint8, device=dev)
@@ -483,7 +505,7 @@ def run_batch(args, rank, local_rank, world):
     e1.synchronize()
     t_solo = e0.elapsed_time(e1) / 1e3
     if rank == 0:
-        line = {"metric": "batched recon/s", "value": len(works) * world / t_batch, "unit": UNIT,
+        line = {"metric": "batched recon/s", "value": job_rate(len(works), world, t_batch), "unit": UNIT,
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * t_batch, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": args.dtype or "f32", "data": "synthetic",

@@ -180,6 +180,14 @@ int scg_project(const scg_geometry* g, int precision, const void* x, void* y,
 int scg_backproject(const scg_geometry* g, int precision, const void* r, void* x,
                     void* work, size_t work_bytes, void* stream);
 
+/* Release the library's host-side caches: the CUDA graphs captured for earlier
+ * solves and batches (keyed by workspace address and geometry) and the
+ * per-device side streams and pinned flags; they are rebuilt on the next call.
+ * The tuned projector shapes are kept.  No library call may be running or
+ * have work in flight.  The library holds no device memory of its own beyond
+ * what these objects use. */
+int scg_release(void);
+
 /* ---- Prepared operator pair ------------------------------------------------
  * For callers that apply A and A^T many times with one geometry (their own
  * iterative methods): the angle table, descriptors and zero pads are placed in

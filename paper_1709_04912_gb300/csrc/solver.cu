@@ -889,6 +889,24 @@ struct scg_operator {
 
 extern "C" {
 
+int scg_release(void) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    int rc = SCG_OK;
+    for (auto& kv : g_streams)
+        if (cudaStreamSynchronize(kv.second) != cudaSuccess) rc = SCG_ERR_CUDA;
+    for (auto& kv : g_graphs)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    g_graphs.clear();
+    for (auto& kv : g_batch_graphs)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    g_batch_graphs.clear();
+    for (auto& kv : g_streams) cudaStreamDestroy(kv.second);
+    g_streams.clear();
+    for (auto& kv : g_pinned) cudaFreeHost(kv.second);
+    g_pinned.clear();
+    return rc;
+}
+
 int scg_operator_create(const scg_geometry* g, int precision, void* work, size_t work_bytes, void* stream,
                         scg_operator** out) {
     if (!valid_geometry(g) || !work || !out) return SCG_ERR_INVALID;

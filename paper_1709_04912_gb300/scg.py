@@ -107,6 +107,8 @@ def load(build_if_needed: bool = True):
     L.scg_batch_workspace_bytes.restype = sz
     L.scg_batch_workspace_bytes.argtypes = [pp, i, i, i]
     L.scg_solve_batch.argtypes = [pp, i, i, i, ctypes.POINTER(Params), vp, sz, ctypes.POINTER(Result), vp]
+    L.scg_release.argtypes = []
+    L.scg_release.restype = i
     L.scg_operator_create.argtypes = [gp, i, vp, sz, vp, ctypes.POINTER(vp)]
     L.scg_operator_project.argtypes = [vp, vp, vp, vp]
     L.scg_operator_backproject.argtypes = [vp, vp, vp, vp]
@@ -537,3 +539,8 @@ class Operator:
             self.close()
         except Exception:
             pass
+
+
+def release() -> None:
+    """Free the library's cached graphs, side streams and pinned flags (scg_release)."""
+    _check(load().scg_release(), "scg_release")

@@ -52,3 +52,12 @@ def test_operator_in_a_cuda_graph():
     got = z.double().cpu().numpy()
     assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
     op.close()
+
+
+def test_release_then_solve_again_gives_the_same_result():
+    prob = inputs.make_problem(inputs.SMALL_FP64, 0, oracle.project)
+    y = torch.tensor(prob.y, dtype=torch.float32, device=DEV)
+    a = scg.scg_solve(y, prob.work.n, "S-CG", prob.eps, gamma0_rel=0.05)
+    scg.release()
+    b = scg.scg_solve(y, prob.work.n, "S-CG", prob.eps, gamma0_rel=0.05)
+    assert a.iters == b.iters and torch.equal(a.x, b.x)
