@@ -45,7 +45,7 @@ WORKLOADS = {w.name: w for w in (inputs.SINGLE_512, inputs.SMALL_FP64, inputs.MI
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--variant", default="S-CG")
@@ -375,7 +375,11 @@ def run_ours(args, work, rank, local_rank, world):
                 "ms_per_launch": {"project": t_proj, "backproject": t_back},
                 "hbm_gbs_algorithmic": {"project": bytes_pass / (t_proj * 1e-3) / 1e9,
                                         "backproject": bytes_pass / (t_back * 1e-3) / 1e9,
-                                        "peak": peaks.get("hbm_gbs")}}
+                                        "peak": peaks.get("hbm_gbs")},
+                # the rate a stored-matrix SpMV would need (8 B per nonzero: value + index)
+                # to match this matrix-free pass
+                "spmv_equivalent_gbs": {"project": 8 * nnz / (t_proj * 1e-3) / 1e9,
+                                        "backproject": 8 * nnz / (t_back * 1e-3) / 1e9}}
 
     # CPU baseline: the oracle on a bounded sample of the same workload
     cpu = None

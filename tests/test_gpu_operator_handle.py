@@ -61,3 +61,17 @@ def test_release_then_solve_again_gives_the_same_result():
     scg.release()
     b = scg.scg_solve(y, prob.work.n, "S-CG", prob.eps, gamma0_rel=0.05)
     assert a.iters == b.iters and torch.equal(a.x, b.x)
+
+
+def test_projector_output_does_not_depend_on_the_tuned_shape():
+    # a solve tunes the projector shape of this geometry bucket; a prepared
+    # operator then uses the tuned shape while scg_project keeps the default
+    # one: every ray is computed identically, so the sinograms are equal
+    prob = inputs.make_problem(inputs.SMALL_FP64, 3, oracle.project)
+    n, na, nb = prob.work.n, prob.work.n_angles, prob.work.n_bins
+    y = torch.tensor(prob.y, dtype=torch.float32, device=DEV)
+    scg.scg_solve(y, n, "S-CG", prob.eps, gamma0_rel=0.05, max_iter=2)
+    op = scg.Operator(n, na, nb, torch.float32)
+    x = torch.tensor(inputs.normal(5, "x", n * n).reshape(n, n), dtype=torch.float32, device=DEV)
+    assert torch.equal(op.project(x), scg.scg_project(x, na, nb))
+    op.close()
