@@ -347,7 +347,11 @@ int scg_server_step(scg_server* srv, void* stream, scg_completion* done, int max
 int scg_server_pending(const scg_server* srv, int* queued, int* active);
 
 /* Destroy the server (pending requests are dropped).  The pool is the
- * caller's to free afterwards. */
+ * caller's to free afterwards.
+ *
+ * A server is driven by one host thread at a time.  After a step returns an
+ * error (SCG_ERR_CUDA, SCG_ERR_WORKSPACE) its requests' states are undefined:
+ * destroy it. */
 int scg_server_destroy(scg_server* srv);
 
 #ifdef __cplusplus
