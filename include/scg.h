@@ -225,6 +225,7 @@ int scg_tv(int n, int precision, const void* x, double* tv_out,
  * memory; every GPU that loads the library holds it until the process exits.
  * Limits and behaviour:
  *   n must be 2 .. 1024 (larger n returns SCG_ERR_UNSUPPORTED);
+ *   precision SCG_F32 or SCG_F64 (the storage formats return SCG_ERR_UNSUPPORTED);
  *   allocates nothing (no cudaMalloc/cudaFree, no allocating library call);
  *   the first call on a device looks up the array's device address with that
  *   device current -- make that first call before any stream capture;
