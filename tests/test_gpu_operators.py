@@ -28,6 +28,7 @@ CASES = [
     (33, 4, 47),        # angles 0, 45, 90, 135 degrees only
     (40, 1, 57),        # a single angle (theta = 0: every ray on pixel edges)
     (2, 3, 3),          # smallest image
+    (16, 7, 1),         # a single detector bin
 ]
 
 
@@ -158,3 +159,26 @@ def test_full_size_operators_on_sampled_outputs(work):
     j[:2] = [0, n - 1]
     refp = oracle.backproject_pixels(r, n, i, j)
     assert rel(g[i, j], refp) <= 1e-5
+
+
+def test_largest_image_side_on_sampled_outputs():
+    # N = 8192 (the largest side the boundary accepts) with a few angles and a
+    # detector wide enough for every ray: sampled rays and pixels against the
+    # oracle evaluated one by one (the index arithmetic's extreme range)
+    n, na, nb = 8192, 6, 11587
+    x = torch.randn((n, n), dtype=torch.float32, device=DEV, generator=torch.Generator(DEV).manual_seed(3))
+    y = scg.scg_project(x, na, nb).cpu().numpy()
+    xh = x.double().cpu().numpy()
+    rng = np.random.default_rng(4)
+    a = rng.integers(0, na, 16)              # each sampled ray costs the oracle N^2 weights
+    b = rng.integers(0, nb, 16)
+    a[:3] = [0, na // 2, na // 3]
+    b[:3] = [nb // 2, 0, nb - 1]
+    assert rel(y[a, b], oracle.project_rays(xh, na, nb, a, b)) <= 1e-5
+    r = torch.randn((na, nb), dtype=torch.float32, device=DEV, generator=torch.Generator(DEV).manual_seed(5))
+    g = scg.scg_backproject(r, n).cpu().numpy()
+    i = rng.integers(0, n, 40)
+    j = rng.integers(0, n, 40)
+    i[:2] = [0, n - 1]
+    j[:2] = [n - 1, 0]
+    assert rel(g[i, j], oracle.backproject_pixels(r.double().cpu().numpy(), n, i, j)) <= 1e-5
