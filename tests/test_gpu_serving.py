@@ -7,6 +7,7 @@ request alone, bit for bit (output image, iterations, status, final f and
 TV, perturbation count): the work items keep each request's single-solve
 block order, so being in a mix changes no rounding.
 """
+import numpy as np
 import pytest
 import torch
 
@@ -134,3 +135,22 @@ def test_request_stopping_at_max_iter_and_at_x0(requests):
     assert done[tags[0]].status == "max_iter" and done[tags[1]].iters == 0
     for q in range(3):
         same(done[tags[q]], scg.scg_solve(ys[q], requests[q].work.n, "S-CG", eps[q], gamma0_rel=0.05, max_iter=10))
+
+
+def test_serving_workload_sizes_in_binary16():
+    # requests drawn from the serving recipe (N up to 1024, 30..180 angles,
+    # eps factor 1.02..1.2): each served result equals its solo FP16 solve and
+    # meets its eps under the oracle's A
+    ws = inputs.serving_workloads(5, 11)
+    probs = [inputs.make_problem(w, 300 + q, oracle.project) for q, w in enumerate(ws)]
+    ys = [torch.tensor(p.y, dtype=torch.float32).to(torch.float16).to(DEV) for p in probs]
+    srv = scg.Server("S-CG", torch.float16, pool_bytes=1 << 30, max_active=8, gamma0_rel=0.05)
+    done = serve(srv, probs, ys, [[0, 1], [2], [3, 4]])
+    srv.close()
+    for q, p in enumerate(probs):
+        solo = scg.scg_solve(ys[q], p.work.n, "S-CG", p.eps, gamma0_rel=0.05)
+        same(done[q], solo)
+        assert done[q].status == "ok"
+        yq = ys[q].double().cpu().numpy()
+        r = oracle.project(done[q].x.double().cpu().numpy(), p.work.n_angles, p.work.n_bins) - yq
+        assert 0.5 * float(np.sum(r * r)) <= p.eps * (1 + 1e-3)
