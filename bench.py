@@ -648,6 +648,8 @@ def main():
             if rank != 0:
                 return 0
         else:
+            import torch
+            torch.cuda.set_device(local_rank)          # each rank's collectives on its own GPU
             dist.init_process_group("nccl", init_method="env://")
     if args.impl == "reference":
         return run_reference(args, work, rank, world)
