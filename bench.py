@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--max-active", type=int, default=64)
     ap.add_argument("--pool-gb", type=float, default=16.0)
     ap.add_argument("--dtype", default=None, choices=["f32", "f16", "bf16", "f64"],
-                    help="storage precision in --mode batch (default f32) and --mode serving (default f16)")
+                    help="storage precision: single and batch modes default to f32, serving to f16")
     ap.add_argument("--host-loop", action="store_true",
                     help="run the while loop as host-polled per-body graphs (same kernels); "
                          "lets a profiler list every kernel launch")
@@ -255,9 +255,11 @@ def run_ours(args, work, rank, local_rank, world):
         return scg.scg_project(xt, na, nb).double().cpu().numpy()
 
     prob = inputs.make_problem(work, args.seed + rank, gpu_project)
-    y = torch.tensor(prob.y, dtype=torch.float32, device=dev)
-    out = torch.empty((work.n, work.n), dtype=torch.float32, device=dev)
-    nbytes = scg.solve_workspace_bytes(work.n, work.n_angles, work.n_bins, variant, scg.F32)
+    dtype = DTYPES[args.dtype or "f32"]
+    esize = torch.tensor([], dtype=dtype).element_size()
+    y = torch.tensor(prob.y, dtype=torch.float32).to(dtype).to(dev)
+    out = torch.empty((work.n, work.n), dtype=dtype, device=dev)
+    nbytes = scg.solve_workspace_bytes(work.n, work.n_angles, work.n_bins, variant, scg._prec_of(dtype))
     wsp = torch.empty(nbytes, dtype=torch.uint8, device=dev)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -297,8 +299,8 @@ def run_ours(args, work, rank, local_rank, world):
     # end to end through the public API with host buffers: pinned y in, x out
     e2e = None
     if not args.no_e2e:
-        y_host = torch.tensor(prob.y, dtype=torch.float32).pin_memory()
-        x_host = torch.empty((work.n, work.n), dtype=torch.float32).pin_memory()
+        y_host = torch.tensor(prob.y, dtype=torch.float32).to(dtype).pin_memory()
+        x_host = torch.empty((work.n, work.n), dtype=dtype).pin_memory()
         y_dev = torch.empty_like(y)
         t_e2e = 0.0
         for q in range(args.warmup + args.steps):
@@ -312,8 +314,8 @@ def run_ours(args, work, rank, local_rank, world):
             if q >= args.warmup:
                 t_e2e += time.perf_counter() - t0
         e2e = {"value": args.steps / t_e2e, "unit": UNIT,
-               "h2d_bytes_per_step": int(y_host.numel() * 4),
-               "d2h_bytes_per_step": int(x_host.numel() * 4 + 64)}
+               "h2d_bytes_per_step": int(y_host.numel() * esize),
+               "d2h_bytes_per_step": int(x_host.numel() * esize + 64)}
 
     # dominant kernels timed alone (CUDA events on the launching stream)
     peaks, peak_kind = measured_peaks()
@@ -321,13 +323,13 @@ def run_ours(args, work, rank, local_rank, world):
     sms = props.multi_processor_count
     nnz = nnz_of(work)
     xk = out.clone()
-    rk = torch.randn((work.n_angles, work.n_bins), dtype=torch.float32, device=dev)
+    rk = torch.randn((work.n_angles, work.n_bins), dtype=torch.float32, device=dev).to(dtype)
 
     # the operator pair prepared once (scg_operator_*): each application is
     # device work only -- a one-thread descriptor update, the view (or
     # pair-row) pass and the projector (or backprojector); L2 is flushed
     # before every application and the events bracket the application alone
-    op = scg.Operator(work.n, work.n_angles, work.n_bins, torch.float32, dev)
+    op = scg.Operator(work.n, work.n_angles, work.n_bins, dtype, dev)
 
     def time_op(fn, reps=20):
         for _ in range(3):
@@ -352,7 +354,7 @@ def run_ours(args, work, rank, local_rank, world):
     dom = "backproject" if t_back >= t_proj else "project"
     t_dom = max(t_back, t_proj)
     achieved = OPS_PER_NNZ * nnz / (t_dom * 1e-3) / 1e12
-    bytes_pass = 4 * (work.J + 2 * work.L)
+    bytes_pass = esize * (work.J + 2 * work.L)
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tpath):
@@ -404,7 +406,7 @@ def run_ours(args, work, rank, local_rank, world):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype or "f32",
                 "data": "synthetic",
                 "config": {"workload": work.name, "variant": variant, "n": work.n,
                            "n_angles": work.n_angles, "n_bins": work.n_bins, "eps": prob.eps,
