@@ -67,10 +67,14 @@ __device__ __forceinline__ Item decode_item(const Prob<T>* probs, const Item* it
               V_.x - V_.y, U_);                                                                   \
     Y_ += V_.y;
 #define SCG_LD(D_) to_c2(__ldg(view + (int)((D_) >> 32)))
+// Sums go to two accumulator pairs by the parity of the ABSOLUTE strip index
+// (u0, y0: even strips; u1, y1: odd), each receiving its strips in increasing
+// order, so a ray's value does not depend on how its strips are split between
+// the unmasked walk and the masked edges (that split follows the warp's lanes).
+// The walk starts on an even strip.
 template <typename V2>
-__device__ __forceinline__ float walk_ray_f32(const V2* view, int n, long long D, long long DL,
-                                              float k2, float h2p) {
-    float u0 = 0.f, u1 = 0.f, y0 = 0.f, y1 = 0.f;
+__device__ __forceinline__ void walk_ray_f32(const V2* view, int n, long long D, long long DL,
+                                             float k2, float h2p, float& u0, float& u1, float& y0, float& y1) {
     int t = 0;
     if (n >= 8) {
         // group a holds strips t-4 .. t-1 (loaded) at the top of each iteration
@@ -87,12 +91,20 @@ __device__ __forceinline__ float walk_ray_f32(const V2* view, int n, long long D
         SCG_STRIP(a0, A0, u0, y0) SCG_STRIP(a1, A1, u1, y1) SCG_STRIP(a2, A2, u0, y0) SCG_STRIP(a3, A3, u1, y1)
         D = A3 + DL;
     }
-    for (; t < n; ++t) {
-        const float2 v = SCG_LD(D);
-        SCG_STRIP(v, D, u0, y0)
-        D += DL;
+    // at most 7 strips left (t even): every load issued before the first sum
+    float2 v[7];
+    long long Dk[7];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        Dk[k] = D + k * DL;
+        v[k] = t + k < n ? SCG_LD(Dk[k]) : make_float2(0.f, 0.f);
     }
-    return (u0 + u1) + (y0 + y1);
+#pragma unroll
+    for (int k = 0; k < 7; ++k)
+        if (t + k < n) {
+            if (k & 1) { SCG_STRIP(v[k], Dk[k], u1, y1) }
+            else { SCG_STRIP(v[k], Dk[k], u0, y0) }
+        }
 }
 #undef SCG_LD
 #undef SCG_STRIP
@@ -121,19 +133,68 @@ __device__ __forceinline__ void walk_range(long long C0, long long SL, int N, fl
     if (tlo > thi || !ok(tlo) || !ok(thi)) { tlo = 0; thi = -1; }
 }
 
-// FP32 arithmetic (float, half and bfloat16 storage).
+// FP32 arithmetic (float, half and bfloat16 storage).  The 32 rays of a warp
+// walk the same absolute strip t together: the lanes' loads then fall in one
+// line of the view, a short contiguous span (walking each ray from its own
+// first strip puts the lanes in different lines wherever rays enter through
+// the image's far sides).  Strips are taken in pairs (even t, t+1).  The pairs
+// inside every non-empty lane's range [tlo, thi] run unmasked through the
+// pipelined walk; the pairs before and after run masked, each lane loading
+// only inside its own range (a masked strip adds an exact zero).  A lane with
+// no strip (ray misses the image, or past the last bin) walks element kPad of
+// each line of the warp's union -- always in bounds -- and discards the sum.
+// Every lane of the warp must call this (warp shuffles).
 template <typename T>
-__device__ __forceinline__ float project_ray_f32(const Prob<T>& P, const Angle<float>& g, int b) {
+__device__ __forceinline__ float project_ray_f32(const Prob<T>& P, const Angle<float>& g, int b, bool valid) {
     const int N = P.n, B2 = 2 * b - (P.nb - 1);           // 2 (b - (nb-1)/2)
     const long long C0 = (((long long)B2 * g.inv_fx) >> 1) + g.c0_off_fx;
     const float c0f = fmaf(0.5f * (float)B2, g.inv_drive, g.c0_off);
-    int tlo, thi;
-    walk_range(C0, g.slope_fx, N, c0f, g.inv_slope, tlo, thi);
-    if (thi < tlo) return 0.f;
+    int tlo = 0, thi = -1;
+    if (valid) walk_range(C0, g.slope_fx, N, c0f, g.inv_slope, tlo, thi);
+    const bool empty = thi < tlo;
+    int mlo = empty ? 0x7fffffff : tlo, mhi = empty ? -1 : thi;          // union of the lanes' ranges
+    int ilo = empty ? -1 : tlo, ihi = empty ? 0x7fffffff : thi;          // intersection (non-empty lanes)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mlo = min(mlo, __shfl_xor_sync(0xffffffffu, mlo, o));
+        mhi = max(mhi, __shfl_xor_sync(0xffffffffu, mhi, o));
+        ilo = max(ilo, __shfl_xor_sync(0xffffffffu, ilo, o));
+        ihi = min(ihi, __shfl_xor_sync(0xffffffffu, ihi, o));
+    }
+    if (mhi < mlo) return 0.f;                            // the whole warp misses the image
+    mlo &= ~1;                                            // first pair
+    ilo += ilo & 1;                                       // whole pairs inside the intersection
+    ihi -= (ihi & 1) ^ 1;
+    const int mend = mhi | 1;                             // last strip of the last pair
+    const bool shared = ilo < ihi;
+    const int m0 = shared ? ilo : mend + 1, m1 = shared ? ihi : mend;   // unmasked pairs [m0, m1]
     const long long S32 = (long long)P.S << 32;
-    const long long D = C0 + (long long)tlo * g.slope_fx + (long long)tlo * S32 + ((long long)kPad << 32);
-    const auto* V = g.col_driven ? P.view_cm : P.view_rm;
-    return walk_ray_f32(V, thi - tlo + 1, D, g.slope_fx + S32, g.k2, g.h2p) * g.inv_m;
+    const long long DL = empty ? S32 : g.slope_fx + S32;
+    long long D = (empty ? 0 : C0 + (long long)mlo * g.slope_fx) + (long long)mlo * S32 + ((long long)kPad << 32);
+    const auto* view = g.col_driven ? P.view_cm : P.view_rm;
+    const float k2 = g.k2, h2p = g.h2p;
+    const int lo = empty ? mlo : tlo;                     // the strips this lane loads: [lo, lo + span]
+    const unsigned span = empty ? (unsigned)(mhi - mlo) : (unsigned)(thi - tlo);
+    float uE = 0.f, uO = 0.f, yE = 0.f, yO = 0.f;        // even / odd strips (see walk_ray_f32)
+    auto edge = [&](int t, int tend) {                    // pairs [t, tend), masked
+        for (; t < tend; t += 2, D += 2 * DL) {
+            const long long D1 = D + DL;
+            const float2 v0 = (unsigned)(t - lo) <= span ? to_c2(__ldg(view + (int)(D >> 32))) : make_float2(0.f, 0.f);
+            const float2 v1 = (unsigned)(t + 1 - lo) <= span ? to_c2(__ldg(view + (int)(D1 >> 32))) : make_float2(0.f, 0.f);
+            uE = fmaf(__saturatef(fmaf(-__int_as_float(0x3F800000u + ((unsigned)D >> 9)), k2, h2p)), v0.x - v0.y, uE);
+            yE += v0.y;
+            uO = fmaf(__saturatef(fmaf(-__int_as_float(0x3F800000u + ((unsigned)D1 >> 9)), k2, h2p)), v1.x - v1.y, uO);
+            yO += v1.y;
+        }
+    };
+    edge(mlo, m0);
+    if (shared) {
+        const int n = m1 - m0 + 1;
+        walk_ray_f32(view, n, D, DL, k2, h2p, uE, uO, yE, yO);
+        D += (long long)n * DL;
+    }
+    edge(m1 + 1, mend + 1);
+    return empty ? 0.f : ((uE + uO) + (yE + yO)) * g.inv_m;
 }
 
 __device__ __forceinline__ double project_ray_f64(const Prob<double>& P, const Angle<double>& g, int b) {
@@ -165,33 +226,47 @@ __device__ __forceinline__ double project_ray_f64(const Prob<double>& P, const A
 }
 
 template <typename T>
-__device__ __forceinline__ typename Tr<T>::C project_ray(const Prob<T>& P, const Angle<typename Tr<T>::C>& g, int b) {
-    if constexpr (std::is_same<T, double>::value) return project_ray_f64(P, g, b);
-    else return project_ray_f32(P, g, b);
+__device__ __forceinline__ typename Tr<T>::C project_ray(const Prob<T>& P, const Angle<typename Tr<T>::C>& g, int b,
+                                                         bool valid) {
+    if constexpr (std::is_same<T, double>::value) return valid ? project_ray_f64(P, g, b) : 0.0;
+    else return project_ray_f32(P, g, b, valid);
 }
 
+// Resident projector blocks per SM the register allocation is sized for: at
+// 4 (64 registers) the walk keeps more loads in flight than at 5 (48), which
+// measured 15-20 % slower on GB300 at 512^2 and 1024^2.
+constexpr int kProjMinBlocks = 4;
+
 // One block: 2^(8-proj_shift) adjacent angles x 2^proj_shift consecutive bins
-// (the shape is tuned per geometry on the host); each warp walks 32 rays of
-// one angle.  Rays of neighbouring angles cross the image almost together, so
-// the warps of a block read nearly the same view spans and most of those
-// reads hit L1.
+// (the shape is tuned per geometry on the host).  Rays of neighbouring angles
+// cross the image almost together, so the warps of a block read nearly the
+// same view spans and most of those reads hit L1.
 template <typename T>
-__global__ void __launch_bounds__(kProjThreads, 5)
+__global__ void __launch_bounds__(kProjThreads, kProjMinBlocks)
 k_project(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int dst_sel,
           int mode, int step) {
     const Item it = decode_item(probs, items, 3);
     const Prob<T>& P = probs[it.prob];
     if (P.st->done) return;
     const int nb = P.nb;
+    // block: AB = 2^(8-sh) angles x R = 2^sh rays; warp: AW adjacent angles x
+    // 32/AW consecutive rays (AW = min(4, AB)), so the lanes' rays cross the
+    // image close together and their loads share cache lines
     const int sh = P.proj_shift;
-    const int a = (it.u << (kProjLog2 - sh)) + (threadIdx.x >> sh);
-    const int b = (it.v << sh) + (threadIdx.x & ((1 << sh) - 1));
+    const int lab = kProjLog2 - sh;                      // log2 angles per block
+    const int law = lab < 2 ? lab : 2;                   // log2 angles per warp
+    const int lrw = 5 - law;                             // log2 rays per warp
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lwpr = sh - lrw;                           // log2 warps along the rays
+    const int a = (it.u << lab) + ((warp >> lwpr) << law) + (lane >> lrw);
+    const int b = (it.v << sh) + ((warp & ((1 << lwpr) - 1)) << lrw) + (lane & ((1 << lrw) - 1));
     using C = typename Tr<T>::C;
     Acc<T> v[1];
     acc_zero(v[0]);
-    if (a < P.na && b < nb) {
-        const Angle<C> g = P.ang[a];
-        C out = project_ray<T>(P, g, b);
+    const bool valid = a < P.na && b < nb;
+    const Angle<C> g = P.ang[valid ? a : 0];
+    C out = project_ray<T>(P, g, b, valid);                // every lane: the FP32 walk is warp-wide
+    if (valid) {
         // (y_scale is 1 except for half/bfloat16 storage; the product is exact)
         if (mode == PROJ_RESIDUAL) out = out - to_c(P.y[(size_t)a * nb + b]) * P.y_scale;
         if (mode == PROJ_PLAIN_OUT) P.user_out[(size_t)a * nb + b] = to_s<typename Tr<T>::S>(out);
