@@ -16,24 +16,29 @@
 //   k_taps         the taps, in FP64
 //   k_sino_pairs   a caller's plain sinogram into the pair layout
 // No kernel uses atomics on data; reductions are deterministic.
+#include <cstring>
 #include <type_traits>
 
 #include "scg_kernels.h"
 
 namespace scg {
 
+// Work item `bid` (normally the block index) of a launch: from the caller's
+// item list, or computed from the single problem's shape.
 template <typename T>
-__device__ __forceinline__ Item decode_item(const Prob<T>* probs, const Item* items, int kind) {
-    if (items) return items[blockIdx.x];
+__device__ __forceinline__ Item decode_item(const Prob<T>* probs, const Item* items, int kind,
+                                            int bid = -1) {
+    if (bid < 0) bid = blockIdx.x;
+    if (items) return items[bid];
     const Prob<T>& P = probs[0];
     Item it;
     it.prob = 0;
-    it.local = blockIdx.x;
-    if (kind == 0) { it.u = blockIdx.x / P.ray_blocks; it.v = blockIdx.x % P.ray_blocks; }
-    else if (kind == 1) { it.u = blockIdx.x / P.tiles_x; it.v = blockIdx.x % P.tiles_x; }
-    else if (kind == 2) { it.u = blockIdx.x / P.filt_blocks; it.v = blockIdx.x % P.filt_blocks; }
-    else if (kind == 3) { it.u = blockIdx.x / P.proj_blocks; it.v = blockIdx.x % P.proj_blocks; }
-    else { it.u = blockIdx.x / P.tiles_x; it.v = blockIdx.x % P.tiles_x; }   // backprojector tiles
+    it.local = bid;
+    if (kind == 0) { it.u = bid / P.ray_blocks; it.v = bid % P.ray_blocks; }
+    else if (kind == 1) { it.u = bid / P.tiles_x; it.v = bid % P.tiles_x; }
+    else if (kind == 2) { it.u = bid / P.filt_blocks; it.v = bid % P.filt_blocks; }
+    else if (kind == 3) { it.u = bid / P.proj_blocks; it.v = bid % P.proj_blocks; }
+    else { it.u = bid / P.tiles_x; it.v = bid % P.tiles_x; }   // backprojector tiles
     return it;
 }
 
@@ -277,8 +282,8 @@ k_project(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int
 }
 
 // ---------------------------------------------------------------------------
-// Backprojector: a 32 x TH tile per block of 128 threads, PIX pixels per
-// thread (rows ty, ty + TH/PIX, ...), all angles.  A pixel whose centre
+// Backprojector: a 32 x TH tile per cluster of CL blocks of 128 threads, PIX
+// pixels per thread (rows ty, ty + TH/PIX, ...), each block 1/CL of the angles.  A pixel whose centre
 // projects to bin coordinate cb can only meet bins floor(cb) and floor(cb)+1
 // ((m+n)/2 <= 1/sqrt(2)); their weights are two saturating FMAs of cb's
 // fractional part (see Angle), and the two bins are one pair-layout load.  The
@@ -295,16 +300,18 @@ k_project(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int
 // small in-tile offset (9.23 fixed point in the FP32 kernel: the fraction
 // bits are directly a float mantissa).
 constexpr int kBand = 48;
-// Tile height, pixels per thread, angles per chunk, and angle groups per
-// block (SPLIT groups of 128 threads take consecutive parts of the angles of
-// one tile and add their sums at the end; measured on GB300 at 512^2 / 720
-// angles, two groups ran 3-5 % slower than one, so one it is) ...
+// Tile height, pixels per thread, angles per chunk, and blocks per tile (CL
+// blocks -- a thread-block cluster -- take consecutive parts of the angles of
+// one tile; the second hands its sums to the first through distributed shared
+// memory).  The gather is issue-bound, and at 512^2 one block per tile leaves
+// only 3.4 blocks per SM, unevenly spread; two per tile measured 19 % faster
+// there on GB300 (8 % at 1024^2) ...
 template <typename T, int NRHS> struct BpCfg {
-    static constexpr int TH = kBpTileH32, PIX = 4, CH = NRHS == 1 ? 32 : 16, SPLIT = 1;
+    static constexpr int TH = kBpTileH32, PIX = 4, CH = NRHS == 1 ? 32 : 16, CL = 2;
 };
 // ... and FP64 (48 KB static shared memory)
 template <int NRHS> struct BpCfg<double, NRHS> {
-    static constexpr int TH = kBpTileH64, PIX = 2, CH = 8, SPLIT = 1;
+    static constexpr int TH = kBpTileH64, PIX = 2, CH = 8, CL = 1;
 };
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
@@ -335,7 +342,7 @@ __device__ __forceinline__ long long tile_origin_fx(const Angle<float>& g, int X
 }
 
 template <typename T, int NRHS>
-__global__ void __launch_bounds__(kBackThreads * BpCfg<T, NRHS>::SPLIT)
+__global__ void __launch_bounds__(kBackThreads)
 k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int src0,
               int src1, int dst0, int dst1, int step) {
     using S2 = typename Tr<T>::S2;
@@ -343,21 +350,24 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
     using Row = typename std::conditional<std::is_same<C, float>::value, BpRowF, BpRowD>::type;
     constexpr bool kF32 = std::is_same<C, float>::value;
     constexpr int TH = BpCfg<T, NRHS>::TH, PIX = BpCfg<T, NRHS>::PIX, CH = BpCfg<T, NRHS>::CH;
-    constexpr int SPLIT = BpCfg<T, NRHS>::SPLIT;
+    constexpr int CL = BpCfg<T, NRHS>::CL;
     constexpr int kStep = TH / PIX;                   // rows between a thread's pixels
     static_assert(kTileW * kStep == kBackThreads, "one thread per column and row group");
     constexpr int kSlotsPerSeg = 16 / (int)sizeof(S2);
     constexpr int kSegs = kBand / kSlotsPerSeg;       // 16-byte copies per band
-    const Item it = decode_item(probs, items, 4);
+    // launched in clusters of CL blocks along x: block rank blockIdx.x % CL
+    const int part = CL == 2 ? (int)(blockIdx.x & 1) : 0;
+    const Item it = decode_item(probs, items, 4, CL == 2 ? (int)(blockIdx.x >> 1) : (int)blockIdx.x);
     const Prob<T>& P = probs[it.prob];
-    if (P.st->done) return;
-    __shared__ Row rows[SPLIT][2][CH];
-    __shared__ int slo[SPLIT][2][CH];           // first slot of each band in its sinogram row
-    __shared__ __align__(16) S2 band[SPLIT][2][NRHS][CH][kBand];
+    if (P.st->done) return;                      // the same flag for both blocks of a cluster
+    __shared__ Row rows[2][CH];
+    __shared__ int slo[2][CH];                   // first slot of each band in its sinogram row
+    __shared__ __align__(16) S2 band[2][NRHS][CH][kBand];
+    __shared__ C xs[CL == 2 ? NRHS * PIX * kBackThreads : 1];   // the second block's sums
     const int N = P.n, na = P.na, nb = P.nb, SB = P.SB;
-    const int part = threadIdx.x / kBackThreads, tl = threadIdx.x % kBackThreads;
-    const int nap = (na + SPLIT - 1) / SPLIT;    // angles of each group
-    const int a_begin = part * nap, a_end = min(na, a_begin + nap);
+    const int tl = threadIdx.x;
+    const int nap = (na + CL - 1) / CL;          // angles of each block
+    const int a_begin = min(na, part * nap), a_end = min(na, a_begin + nap);
     const int ti0 = it.u * TH, tj0 = it.v * kTileW;
     const int tx = tl % kTileW, ty = tl / kTileW;
     const int j = tj0 + tx;
@@ -383,8 +393,8 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
                 r.c23 = g.c23; r.s23 = g.s23;
                 r.kb = g.kb; r.hb0p = g.hb0p; r.hb1p = g.hb1p;
                 r.pad_[0] = r.pad_[1] = 0;
-                rows[part][ch & 1][q] = r;
-                slo[part][ch & 1][q] = s_lo;
+                rows[ch & 1][q] = r;
+                slo[ch & 1][q] = s_lo;
             } else {
                 const double cbt = 0.5 * (double)(nb - 1) + 0.5 * (double)X2 * g.c_d + 0.5 * (double)Y2 * g.s_d;
                 const double fl = floor(cbt);
@@ -394,8 +404,8 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
                 r.c = g.c; r.s = g.s; r.kb = g.kb; r.hb0 = g.hb0; r.hb1 = g.hb1;
                 r.frac = cbt - fl;
                 r.rel = I + kSPad - s_lo;
-                rows[part][ch & 1][q] = r;
-                slo[part][ch & 1][q] = s_lo;
+                rows[ch & 1][q] = r;
+                slo[ch & 1][q] = s_lo;
             }
         }
     };
@@ -406,10 +416,10 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
         for (int h = 0; h < NRHS; ++h) {
             for (int sg = tl; sg < cnt * kSegs; sg += kBackThreads) {
                 const int q = sg / kSegs, k = sg - q * kSegs;
-                const int slot = slo[part][ch & 1][q] + k * kSlotsPerSeg;
+                const int slot = slo[ch & 1][q] + k * kSlotsPerSeg;
                 const S2* row = R[h] + (size_t)(a0 + q) * SB;
                 const bool ok = slot >= 0 && slot + kSlotsPerSeg <= SB;
-                cp_async16(&band[part][ch & 1][h][q][k * kSlotsPerSeg], ok ? row + slot : row, ok ? 16 : 0);
+                cp_async16(&band[ch & 1][h][q][k * kSlotsPerSeg], ok ? row + slot : row, ok ? 16 : 0);
             }
         }
         cp_async_commit();
@@ -436,7 +446,7 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
             if constexpr (kF32) {
 #pragma unroll 2
                 for (int q = 0; q < cnt; ++q) {
-                    const BpRowF g = rows[part][buf][q];
+                    const BpRowF g = rows[buf][q];
                     // 9.23 position of the thread's first pixel in band coordinates (> 0)
                     const int p0 = g.base + tx * g.c23 + ty * g.s23;
                     const int dp = kStep * g.s23;
@@ -449,7 +459,7 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
                         const float w1 = __saturatef(fmaf(f, g.kb, g.hb1p));
 #pragma unroll
                         for (int h = 0; h < NRHS; ++h) {
-                            const float2 e = to_c2(band[part][buf][h][q][p >> 23]);
+                            const float2 e = to_c2(band[buf][h][q][p >> 23]);
                             acc[h][k] = fmaf(w0, e.x, fmaf(w1, e.y, acc[h][k]));
                         }
                     }
@@ -457,7 +467,7 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
             } else {
                 const double dj = double(tx);
                 for (int q = 0; q < cnt; ++q) {
-                    const BpRowD& g = *reinterpret_cast<const BpRowD*>(&rows[part][buf][q]);
+                    const BpRowD& g = *reinterpret_cast<const BpRowD*>(&rows[buf][q]);
                     const double djc = dj * g.c;
 #pragma unroll
                     for (int k = 0; k < PIX; ++k) {
@@ -468,7 +478,7 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
                         const double w0 = sat(fma(-f, g.kb, g.hb0)), w1 = sat(fma(f, g.kb, g.hb1));
 #pragma unroll
                         for (int h = 0; h < NRHS; ++h) {
-                            const double2 e = to_c2(band[part][buf][h][q][kk]);
+                            const double2 e = to_c2(band[buf][h][q][kk]);
                             acc[h][k] = fma(w0, e.x, fma(w1, e.y, acc[h][k]));
                         }
                     }
@@ -477,23 +487,27 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
         }
         __syncthreads();
     }
-    if constexpr (SPLIT == 2) {
-        // the second angle group hands its sums to the first (fixed order: first + second)
-        C* xs = reinterpret_cast<C*>(&band[0][0][0][0][0]);    // band storage is free now
-        static_assert(sizeof(C) * NRHS * PIX * kBackThreads <= sizeof(band), "hand-over fits");
+    if constexpr (CL == 2) {
+        // the second block writes its sums into the first block's xs; one
+        // cluster barrier (release / acquire) orders the writes before the
+        // first block's reads.  Fixed order: first half + second half.
         if (part == 1) {
+            const unsigned local = (unsigned)__cvta_generic_to_shared(&xs[tl]);
+            unsigned remote;
+            asm volatile("mapa.shared::cluster.u32 %0, %1, 0;" : "=r"(remote) : "r"(local));
 #pragma unroll
             for (int h = 0; h < NRHS; ++h)
 #pragma unroll
-                for (int k = 0; k < PIX; ++k) xs[(h * PIX + k) * kBackThreads + tl] = acc[h][k];
+                for (int k = 0; k < PIX; ++k)
+                    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(remote + (unsigned)(sizeof(C) * (h * PIX + k) * kBackThreads)),
+                                 "f"((float)acc[h][k]) : "memory");
         }
-        __syncthreads();
-        if (part == 0) {
+        asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+        if (part == 1) return;
 #pragma unroll
-            for (int h = 0; h < NRHS; ++h)
+        for (int h = 0; h < NRHS; ++h)
 #pragma unroll
-                for (int k = 0; k < PIX; ++k) acc[h][k] = acc[h][k] + xs[(h * PIX + k) * kBackThreads + tl];
-        }
+            for (int k = 0; k < PIX; ++k) acc[h][k] = acc[h][k] + xs[(h * PIX + k) * kBackThreads + tl];
     }
     using S = typename Tr<T>::S;
     const int dst[2] = {dst0, dst1};
@@ -502,7 +516,7 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
 #pragma unroll
     for (int k = 0; k < PIX; ++k) {
         const int i = ti0 + ty + k * kStep;
-        if (part != 0 || i >= N || j >= N) continue;
+        if (i >= N || j >= N) continue;
         const size_t idx = (size_t)i * N + j;
         // stored values are rounded to the storage format; the dots use them
 #pragma unroll
@@ -1070,13 +1084,30 @@ void launch_project(const Prob<T>* d, const Item* items, int grid, int dst, int 
                     cudaStream_t s) {
     k_project<T><<<grid, kProjThreads, 0, s>>>(d, items, dst, mode, step);
 }
+// `grid` tiles (work items), each taken by a cluster of BpCfg::CL blocks.
+template <typename T, int NRHS>
+void launch_bp(const Prob<T>* d, const Item* items, int grid, int src0, int src1, int dst0, int dst1,
+               int step, cudaStream_t s) {
+    constexpr int CL = BpCfg<T, NRHS>::CL;
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3((unsigned)(grid * CL));
+    cfg.blockDim = dim3(kBackThreads);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_backproject<T, NRHS>, d, items, src0, src1, dst0, dst1, step);
+}
 template <typename T>
 void launch_backproject(const Prob<T>* d, const Item* items, int grid, int nrhs, int src0,
                         int src1, int dst0, int dst1, int step, cudaStream_t s) {
-    if (nrhs == 2)
-        k_backproject<T, 2><<<grid, kBackThreads * BpCfg<T, 2>::SPLIT, 0, s>>>(d, items, src0, src1, dst0, dst1, step);
-    else
-        k_backproject<T, 1><<<grid, kBackThreads * BpCfg<T, 1>::SPLIT, 0, s>>>(d, items, src0, src1, dst0, dst1, step);
+    if (nrhs == 2) launch_bp<T, 2>(d, items, grid, src0, src1, dst0, dst1, step, s);
+    else launch_bp<T, 1>(d, items, grid, src0, src1, dst0, dst1, step, s);
 }
 template <typename T>
 void launch_sino_pairs(const Prob<T>* d, int grid, int dst, cudaStream_t s) {
