@@ -442,6 +442,9 @@ inline DevState initial_state(const scg_params* prm, double eps, int variant) {
     st.gamma_fixed = prm->gamma0 > 0.0 ? 1 : 0;
     st.gamma0_rel = prm->gamma0_rel;
     st.a = prm->a;
+    st.a_ell = 1.0;                                  // ell = 0
+    st.apow[0] = 1.0;
+    for (int t = 1; t < kTrials; ++t) st.apow[t] = st.apow[t - 1] * prm->a;
     st.max_trials = prm->max_trials;
     st.variant = variant;
     st.family = fam;

@@ -788,7 +788,7 @@ k_trial(const Prob<T>* __restrict__ probs, const Item* __restrict__ items) {
     __shared__ C coef_s[kTrials];
     __shared__ unsigned s_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x < kTrials) coef_s[threadIdx.x] = (C)st.trial_coef[threadIdx.x];
+    if (threadIdx.x < kTrials) coef_s[threadIdx.x] = (C)(st.trial_c0 * st.apow[threadIdx.x]);
     __syncthreads();
     const int N = P.n;
     const int j = it.v * kTileW + lane;
@@ -843,13 +843,13 @@ k_trial(const Prob<T>* __restrict__ probs, const Item* __restrict__ items) {
         A b = wsum[0][threadIdx.x];
         for (int w = 1; w < NW; ++w) b = acc_add(b, wsum[w][threadIdx.x]);
         parts[(size_t)it.local * kSlots + threadIdx.x] = b;
-        __threadfence();
     }
     __syncthreads();
-    if (threadIdx.x == 0) s_last = (atomicAdd(P.counter, 1u) + 1u == (unsigned)P.cnt_bp);
+    if (threadIdx.x == 0) s_last = arrive_last(P.counter, (unsigned)P.cnt_bp);
     __syncthreads();
     if (!s_last) return;
-    __threadfence();
+    StateCopy sc;
+    sc.load(P.st);                                    // in flight during the sums below
     // last block: warp w adds slots 8w .. 8w+7 over all items (lane l takes
     // items l, l+32, ...; independent 16-byte loads), then across its lanes in a
     // fixed order; thread 0 collects the four warps' results
@@ -859,7 +859,8 @@ k_trial(const Prob<T>* __restrict__ probs, const Item* __restrict__ items) {
         A acc[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) acc_zero(acc[k]);
-        for (int q = lane; q < P.cnt_bp; q += 32) {
+#pragma unroll 4
+        for (int q = lane; q < P.cnt_bp; q += 32) {      // loads of 4 items in flight
             const A* src = parts + (size_t)q * kSlots + warp * 8;
 #pragma unroll
             for (int k = 0; k < 8; k += 2) {
@@ -885,13 +886,15 @@ k_trial(const Prob<T>* __restrict__ probs, const Item* __restrict__ items) {
             for (int k = 0; k < 8; ++k) red[warp * 8 + k] = acc_to_double(acc[k]);
         }
     }
+    __shared__ DevState sst;
+    sc.to_smem(sst);
     __syncthreads();
     if (threadIdx.x == 0) {
-        double sums[NS];
-        for (int t = 0; t < NS; ++t) sums[t] = red[t];
         *P.counter = 0u;
-        finalize<T>(FIN_TRIAL, P, sums);
+        finalize<T>(FIN_TRIAL, P, sst, red);          // the sums, from shared memory
     }
+    __syncthreads();
+    StateCopy::store(sst, P.st);
 }
 
 // ---------------------------------------------------------------------------

@@ -115,7 +115,9 @@ struct DevState {
     double tv_x, gnorm2, xnorm2;
     double gamma0, gamma0_rel, a;
     double coef;            // applied perturbation: x_{k+1/2} = x_k + coef * dTV(x_k)
-    double trial_coef[kTrials];
+    double trial_c0;        // coefficient of the first pending trial: -gamma0 a^ell / ||dTV||
+    double a_ell;           // a^ell, kept by multiplication as ell advances
+    double apow[kTrials];   // a^t, t = 0 .. kTrials-1 (set on the host); trial t: trial_c0 * apow[t]
     double margin;
     double f_final, tv_final;
     long long ell;
@@ -364,7 +366,42 @@ __device__ __forceinline__ void block_sum(A (&v)[NS], A* smem /* >= 32*NS */) {
     }
 }
 
-template <typename T> __device__ void finalize(int step, const Prob<T>& P, const double* S);
+template <typename T> __device__ void finalize(int step, const Prob<T>& P, DevState& st, const double* S);
+
+// The finalising block works on a shared-memory copy of the problem's state:
+// the copy is loaded by the block's threads in parallel (one 8-byte word
+// each), the state machine runs on it in one thread, and the block writes it
+// back -- instead of one dependent global round trip per state field.
+static_assert(sizeof(DevState) % 8 == 0, "state copied as 8-byte words");
+constexpr int kStateWords = (int)(sizeof(DevState) / 8);
+static_assert(kStateWords <= 128, "one word per thread: every finalising block has >= 128 threads");
+struct StateCopy {
+    unsigned long long w;
+    __device__ __forceinline__ void load(const DevState* g) {
+        if ((int)threadIdx.x < kStateWords) w = __ldcg(reinterpret_cast<const unsigned long long*>(g) + threadIdx.x);
+    }
+    __device__ __forceinline__ void to_smem(DevState& sst) const {
+        if ((int)threadIdx.x < kStateWords) reinterpret_cast<unsigned long long*>(&sst)[threadIdx.x] = w;
+    }
+    __device__ __forceinline__ static void store(const DevState& sst, DevState* g) {
+        if ((int)threadIdx.x < kStateWords)
+            reinterpret_cast<unsigned long long*>(g)[threadIdx.x] = reinterpret_cast<const unsigned long long*>(&sst)[threadIdx.x];
+    }
+};
+
+// One work item's arrival at the end of a launch: an acquire-release atomic
+// increment at GPU scope.  Release: the partial sums this block wrote before
+// it (by any of its threads, ordered before the calling thread by a block
+// barrier) are visible to whoever observes the increment.  Acquire: the block
+// that sees the count reach `total` sees every other item's partials (its
+// other threads after a block barrier).  Returns true for that last item.
+// (No separate __threadfence: a sequentially consistent fence per block, and
+// one per thread of the last block, cost several microseconds per launch.)
+__device__ __forceinline__ bool arrive_last(unsigned* counter, unsigned total) {
+    unsigned prev;
+    asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(prev) : "l"(counter) : "memory");
+    return prev + 1u == total;
+}
 
 // Publish this item's partial sums; the block that completes the problem's
 // last item sums all partials in item order and runs the step's finaliser.
@@ -382,13 +419,12 @@ __device__ void reduce_and_finalize(Acc<T> (&v)[NS], const Prob<T>& P, int local
         A* dst = parts + (size_t)local * kSlots;
 #pragma unroll
         for (int k = 0; k < NS; ++k) dst[k] = v[k];
-        __threadfence();
-        unsigned prev = atomicAdd(P.counter, 1u);
-        s_last = (prev + 1u == (unsigned)total);
+        s_last = arrive_last(P.counter, (unsigned)total);
     }
     __syncthreads();
     if (!s_last) return;
-    __threadfence();
+    StateCopy sc;
+    sc.load(P.st);                                    // in flight during the sums below
     A acc[NS];
 #pragma unroll
     for (int k = 0; k < NS; ++k) acc_zero(acc[k]);
@@ -409,13 +445,18 @@ __device__ void reduce_and_finalize(Acc<T> (&v)[NS], const Prob<T>& P, int local
         }
     }
     block_sum<A, NS>(acc, red);
+    __shared__ DevState sst;
+    sc.to_smem(sst);
+    __syncthreads();
     if (threadIdx.x == 0) {
         *P.counter = 0u;
         double S[NS < 4 ? 4 : NS];
 #pragma unroll
         for (int k = 0; k < (NS < 4 ? 4 : NS); ++k) S[k] = k < NS ? acc_to_double(acc[k]) : 0.0;
-        finalize<T>(step, P, S);
+        finalize<T>(step, P, sst, S);
     }
+    __syncthreads();
+    StateCopy::store(sst, P.st);
 }
 
 // ---------------------------------------------------------------------------
@@ -448,29 +489,20 @@ __device__ __forceinline__ double* trace_row(const Prob<T>& P, int it) {
 }
 
 // Finish a loop body: the algorithm's k <- k+1.
-template <typename T>
-__device__ void end_body(const Prob<T>& P) {
-    DevState& st = *P.st;
+__device__ __forceinline__ void end_body(DevState& st) {
     st.k += 1;
     st.iters += 1;
 }
 
-template <typename T>
-__device__ void set_trial_coefs(const Prob<T>& P) {
-    DevState& st = *P.st;
-    // coef_t = -gamma0 a^(l+t) / ||dTV||, t = 0 .. kTrials-1
-    double c = -st.gamma0 * pow(st.a, (double)st.ell) / sqrt(st.gnorm2);
-    for (int t = 0; t < kTrials; ++t) {
-        st.trial_coef[t] = c;
-        c *= st.a;
-    }
+// First pending trial coefficient -gamma0 a^ell / ||dTV||; trial t of the
+// pass uses trial_c0 * a^t.
+__device__ __forceinline__ void set_trial_coefs(DevState& st) {
+    st.trial_c0 = -st.gamma0 * st.a_ell / sqrt(st.gnorm2);
 }
-
 // Top of the while loop: test f(x_{k-1/2}) > eps (f(x_k) for CG/PCG) and the
 // iteration cap, open the trace row and prepare the perturbation of x_k.
 template <typename T>
-__device__ void top_of_loop(const Prob<T>& P) {
-    DevState& st = *P.st;
+__device__ void top_of_loop(const Prob<T>& P, DevState& st) {
     if (st.done) return;
     if (!(st.f_half > st.eps)) { st.done = 1; st.status = SCG_OK; return; }
     if (st.iters >= st.max_iter) { st.done = 1; st.status = SCG_WARN_MAX_ITER; return; }
@@ -492,24 +524,21 @@ __device__ void top_of_loop(const Prob<T>& P) {
             st.gamma_fixed = 1;
         }
         st.accepted = 0;              // trials pending
-        set_trial_coefs(P);
+        set_trial_coefs(st);
     } else {
         st.accepted = -1;             // no perturbation this k
         if (row) { row[TR_TV_AFTER] = st.tv_x; row[TR_ELL] = (double)st.ell; }
     }
 }
 
-template <typename T>
-__device__ void breakdown(const Prob<T>& P) {
-    DevState& st = *P.st;
+__device__ __forceinline__ void breakdown(DevState& st) {
     st.done = 1;
     st.status = SCG_ERR_BREAKDOWN;
-    end_body(P);
+    end_body(st);
 }
 
 template <typename T>
-__device__ void finalize(int step, const Prob<T>& P, const double* S) {
-    DevState& st = *P.st;
+__device__ void finalize(int step, const Prob<T>& P, DevState& st, const double* S) {
     double* row = trace_row(P, st.iters);
     switch (step) {
     case FIN_F:
@@ -518,7 +547,7 @@ __device__ void finalize(int step, const Prob<T>& P, const double* S) {
             if (row) row[TR_F_AFTER] = st.f_half;
             // f(x_{k+1/2}) <= eps ends the loop at the next test; the rest of
             // this step only produces x_{k+1}, which is never used.
-            if (!(st.f_half > st.eps)) { st.done = 1; st.status = SCG_OK; end_body(P); }
+            if (!(st.f_half > st.eps)) { st.done = 1; st.status = SCG_OK; end_body(st); }
         }
         break;
     case FIN_BETA: {
@@ -526,7 +555,7 @@ __device__ void finalize(int step, const Prob<T>& P, const double* S) {
         if (st.in_init) { st.beta = 0.0; break; }
         if (st.variant == SCG_S_CG_CD) {
             if (S[1] == 0.0) st.beta = 0.0;
-            else if (!(st.gTp < 0.0) || !isfinite(st.gTp)) { breakdown(P); break; }
+            else if (!(st.gTp < 0.0) || !isfinite(st.gTp)) { breakdown(st); break; }
             else st.beta = -S[1] / st.gTp;               // beta = -||g'||^2 / g^T p
         } else {
             st.beta = S[0] / st.pTh;                     // beta = g'^T h / p^T h (z'^T h for S-PCG)
@@ -541,7 +570,7 @@ __device__ void finalize(int step, const Prob<T>& P, const double* S) {
     case FIN_ALPHA:
         if (finite_pos(S[0])) st.alpha = -st.num / S[0]; // alpha = -g'^T p' / p'^T h'
         else if (st.gg == 0.0) st.alpha = 0.0;
-        else { breakdown(P); break; }
+        else { breakdown(st); break; }
         st.pTh = S[0];
         if (row && !st.in_init) row[TR_ALPHA] = st.alpha;
         break;
@@ -550,8 +579,8 @@ __device__ void finalize(int step, const Prob<T>& P, const double* S) {
         st.gnorm2 = S[1];
         st.xnorm2 = S[2];
         if (st.in_init) st.in_init = 0;
-        else end_body(P);
-        top_of_loop(P);
+        else end_body(st);
+        top_of_loop(P, st);
         break;
     case FIN_TRIAL: {
         const double base = S[kTrials];
@@ -564,19 +593,22 @@ __device__ void finalize(int step, const Prob<T>& P, const double* S) {
             if (S[t] <= base) { acc = t; break; }
         }
         if (acc >= 0) {
-            st.coef = st.trial_coef[acc];
+            st.coef = st.trial_c0 * st.apow[acc];       // the coefficient k_trial tested
+            const double gamma = st.gamma0 * st.a_ell * st.apow[acc];
+            st.a_ell = st.a_ell * st.apow[acc] * st.a;   // a^(ell + acc + 1)
             st.ell += acc + 1;
             st.trials += acc + 1;
             st.accepted = 1;
             if (row) {
                 row[TR_TRIALS] = st.trials;
                 row[TR_ACCEPTED] = 1.0;
-                row[TR_GAMMA] = st.gamma0 * pow(st.a, (double)(st.ell - 1));
+                row[TR_GAMMA] = gamma;
                 row[TR_TV_AFTER] = S[acc];
                 row[TR_ELL] = (double)st.ell;
                 row[TR_MARGIN] = st.margin;
             }
         } else {
+            if (valid > 0) st.a_ell = st.a_ell * st.apow[valid - 1] * st.a;   // a^(ell + valid)
             st.ell += valid;
             st.trials += valid;
             if (st.trials >= st.max_trials) {
@@ -590,7 +622,7 @@ __device__ void finalize(int step, const Prob<T>& P, const double* S) {
                     row[TR_MARGIN] = st.margin;
                 }
             } else {
-                set_trial_coefs(P);
+                set_trial_coefs(st);
             }
         }
         break;
@@ -606,7 +638,7 @@ __device__ void finalize(int step, const Prob<T>& P, const double* S) {
             st.alpha = 0.0;
             st.inner_stop = 1;
             if (st.family == FAM_CG) { st.done = 1; st.status = SCG_OK; }
-        } else { breakdown(P); break; }
+        } else { breakdown(st); break; }
         if (row && st.family == FAM_CG) row[TR_ALPHA] = st.alpha;
         break;
     case FIN_CG_F:
@@ -622,8 +654,8 @@ __device__ void finalize(int step, const Prob<T>& P, const double* S) {
     }
     case FIN_CG_END:
         if (st.in_init) st.in_init = 0;
-        else end_body(P);
-        top_of_loop(P);
+        else end_body(st);
+        top_of_loop(P, st);
         break;
     case FIN_RESUME:
         st.pTh = S[0];

@@ -113,6 +113,7 @@ int solve_impl(const scg_geometry* g, int variant, int precision, const scg_para
     if (resumed) {
         st.k = resume->k;
         st.ell = resume->ell;
+        st.a_ell = pow(prm->a, (double)resume->ell);
         st.gamma0 = resume->gamma0;
         st.gamma_fixed = resume->gamma_fixed;
         st.delta = resume->delta;
