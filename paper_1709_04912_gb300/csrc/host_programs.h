@@ -281,7 +281,7 @@ struct Runner {
     void back2(int s0, int s1, int d0, int d1, int step) { ++launches; launch_backproject<T>(d, i_bp, g_bp, 2, s0, s1, d0, d1, step, s); }
     void vec(int op, int sel, int step) { ++launches; launch_vec<T>(d, i_img, g_img, op, sel, step, s); }
     void tvgrad(int src, int fuse, int wg, int step) { ++launches; launch_tvgrad<T>(d, i_img, g_img, src, fuse, wg, step, s); }
-    void trial() { ++launches; launch_trial<T>(d, i_bp, g_bp, s); }
+    void trial(int ncand) { ++launches; launch_trial<T>(d, i_bp, g_bp, ncand, s); }
     void axpy(int step) { ++launches; launch_sino_axpy<T>(d, i_ray, g_ray, step, s); }
     void filter(int src, int dst) { ++launches; launch_filter<T>(d, i_row, g_row, nb, src, dst, 0, s); }
 };
@@ -335,7 +335,8 @@ void run_body(Runner<T>& R, const Program& pg) {
         R.vec(VEC_FORM_P, dsel, FIN_CG_END);           // p' = -g' (-z') + beta p; k = k+1; loop test
         return;
     }
-    for (int t = 0; t < pg.trial_passes; ++t) R.trial();  // TV trials of x_k + gamma_l v
+    for (int t = 0; t < pg.trial_passes; ++t)             // TV trials of x_k + gamma_l v
+        R.trial(t == 0 ? kTrialsFirst : kTrials);
     R.vec(VEC_PERTURB, 0, FIN_NONE);                   // x_{k+1/2} = perturbed(x_k)
     R.project(SB_R, PROJ_RESIDUAL, FIN_F);             // A x_{k+1/2} - y, f(x_{k+1/2})
     if (pre) R.filter(SB_R, SB_W);
@@ -456,7 +457,7 @@ inline DevState initial_state(const scg_params* prm, double eps, int variant) {
 inline Program make_program(const scg_params* prm, int variant) {
     Program pg;
     pg.variant = variant;
-    pg.trial_passes = prm->perturb == SCG_PERTURB_GAMMA ? (prm->max_trials + kTrials - 1) / kTrials : 0;
+    pg.trial_passes = prm->perturb == SCG_PERTURB_GAMMA ? trial_passes_for(prm->max_trials) : 0;
     pg.ksteps = prm->K + (prm->k_inclusive ? 1 : 0);
     return pg;
 }

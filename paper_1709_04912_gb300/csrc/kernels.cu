@@ -759,10 +759,13 @@ k_tvgrad(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int 
 }
 
 // ---------------------------------------------------------------------------
-// kTrials trial points z_t = x + coef_t * dTV(x) (coef_t = -gamma_{l+t}/||dTV||)
-// and x itself, their TVs summed in one pass over x and dTV.  The accepted
-// point is later formed by k_vec(VEC_PERTURB) with the same coefficient and
-// the same fma, so the stored x_{k+1/2} is exactly the point that was tested.
+// NC trial points z_t = x + coef_t * dTV(x) (coef_t = -gamma_{l+t}/||dTV||)
+// and x itself, their TVs summed in one pass over x and dTV.  A step's first
+// pass tries kTrialsFirst candidates (after the first steps the first one is
+// normally accepted); the passes after it, which run only while nothing has
+// been accepted, try kTrials each.  The accepted point is later formed by
+// k_vec(VEC_PERTURB) with the same coefficient and the same fma, so the stored
+// x_{k+1/2} is exactly the point that was tested.
 // Blocks take the backprojector's tiles (32 x kBpTileH, 128 threads), each
 // thread TH/4 pixels of one column, so a thread adds its pixels' terms before
 // the warp-level sums.  The FP32 kernel takes each term's square root with the
@@ -770,14 +773,30 @@ k_tvgrad(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int 
 // rounded sqrtf costs half the pass): every TV this pass compares -- the
 // candidates' and x's own -- is summed the same way, so the acceptance test
 // TV(z) <= TV(x) compares like with like.
-template <typename T>
+template <typename A>
+__device__ __forceinline__ A ld_acc(const A* p) {
+    if constexpr (std::is_same<A, double>::value) return __ldcg(p);
+    else {
+        const float2 w = __ldcg(reinterpret_cast<const float2*>(p));
+        A r;
+        r.hi = w.x; r.lo = w.y;
+        return r;
+    }
+}
+
+template <typename T, int NC>
 __global__ void __launch_bounds__(kBackThreads)
 k_trial(const Prob<T>* __restrict__ probs, const Item* __restrict__ items) {
     using A = Acc<T>;
     using C = typename Tr<T>::C;
     using S = typename Tr<T>::S;
-    constexpr int NS = kTrials + 1;                 // 31 candidates + x itself
+    static_assert(NC >= 1 && NC <= kTrials, "candidates per pass");
+    constexpr int NS = NC + 1;                      // candidates + x itself
+    constexpr int G = NS < 8 ? NS : 8;              // sums reduced together
+    static_assert(NS % G == 0, "whole groups");
     constexpr int NW = kBackThreads / 32;
+    constexpr int SPW = NS / NW;                    // slots per warp in the final sum
+    static_assert(SPW * NW == NS, "the final sum splits the slots evenly over the warps");
     constexpr int TH = std::is_same<T, double>::value ? kBpTileH64 : kBpTileH32;
     constexpr int PIX = TH / NW, kStep = NW;        // pixels per thread, row step
     const Item it = decode_item(probs, items, 4);
@@ -785,10 +804,10 @@ k_trial(const Prob<T>* __restrict__ probs, const Item* __restrict__ items) {
     const DevState& st = *P.st;
     if (st.done || st.accepted != 0) return;
     __shared__ A wsum[NW][NS];
-    __shared__ C coef_s[kTrials];
+    __shared__ C coef_s[NC];
     __shared__ unsigned s_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x < kTrials) coef_s[threadIdx.x] = (C)(st.trial_c0 * st.apow[threadIdx.x]);
+    if (threadIdx.x < NC) coef_s[threadIdx.x] = (C)(st.trial_c0 * st.apow[threadIdx.x]);
     __syncthreads();
     const int N = P.n;
     const int j = it.v * kTileW + lane;
@@ -801,23 +820,23 @@ k_trial(const Prob<T>* __restrict__ probs, const Item* __restrict__ items) {
         x0[k] = xu[k] = xv[k] = q0[k] = qu[k] = qv[k] = C(0);
         if (in[k]) {
             const S* X = P.img[IB_X];
-            const S* G = P.img[IB_TVG];
+            const S* Gr = P.img[IB_TVG];
             const size_t g0 = (size_t)i * N + j;
             x0[k] = to_c(X[g0]); xu[k] = to_c(X[g0 + N]); xv[k] = to_c(X[g0 + 1]);
-            q0[k] = to_c(G[g0]); qu[k] = to_c(G[g0 + N]); qv[k] = to_c(G[g0 + 1]);
+            q0[k] = to_c(Gr[g0]); qu[k] = to_c(Gr[g0 + N]); qv[k] = to_c(Gr[g0 + 1]);
         }
     }
 #pragma unroll
-    for (int grp = 0; grp < NS / 8; ++grp) {
-        A v[8];
+    for (int grp = 0; grp < NS / G; ++grp) {
+        A v[G];
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk) {
-            const int t = grp * 8 + kk;
+        for (int kk = 0; kk < G; ++kk) {
+            const int t = grp * G + kk;
             C sum = C(0);                          // this thread's pixels: non-negative terms
 #pragma unroll
             for (int k = 0; k < PIX; ++k) {
                 C du, dv;
-                if (t < kTrials) {
+                if (t < NC) {
                     // trial points as they would be stored (VEC_PERTURB rounds the same way)
                     const C c = coef_s[t];
                     const C z0 = rnd<T>(fma_rn(c, q0[k], x0[k])), zu = rnd<T>(fma_rn(c, qu[k], xu[k])),
@@ -831,10 +850,10 @@ k_trial(const Prob<T>* __restrict__ probs, const Item* __restrict__ items) {
             v[kk] = acc_val(sum);
         }
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk) v[kk] = warp_sum<true>(v[kk]);
+        for (int kk = 0; kk < G; ++kk) v[kk] = warp_sum<true>(v[kk]);
         if (lane == 0) {
 #pragma unroll
-            for (int kk = 0; kk < 8; ++kk) wsum[warp][grp * 8 + kk] = v[kk];
+            for (int kk = 0; kk < G; ++kk) wsum[warp][grp * G + kk] = v[kk];
         }
     }
     __syncthreads();
@@ -850,40 +869,28 @@ k_trial(const Prob<T>* __restrict__ probs, const Item* __restrict__ items) {
     if (!s_last) return;
     StateCopy sc;
     sc.load(P.st);                                    // in flight during the sums below
-    // last block: warp w adds slots 8w .. 8w+7 over all items (lane l takes
-    // items l, l+32, ...; independent 16-byte loads), then across its lanes in a
-    // fixed order; thread 0 collects the four warps' results
-    static_assert(NW * 8 == NS, "one warp per eight slots");
+    // last block: warp w adds slots SPW*w .. SPW*w+SPW-1 over all items (lane l
+    // takes items l, l+32, ...), then across its lanes in a fixed order;
+    // thread 0 collects the warps' results
     __shared__ double red[NS];
     {
-        A acc[8];
+        A acc[SPW];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) acc_zero(acc[k]);
+        for (int k = 0; k < SPW; ++k) acc_zero(acc[k]);
 #pragma unroll 4
         for (int q = lane; q < P.cnt_bp; q += 32) {      // loads of 4 items in flight
-            const A* src = parts + (size_t)q * kSlots + warp * 8;
+            const A* src = parts + (size_t)q * kSlots + warp * SPW;
 #pragma unroll
-            for (int k = 0; k < 8; k += 2) {
-                A y0, y1;
-                if constexpr (std::is_same<A, double>::value) {
-                    const double2 w = __ldcg(reinterpret_cast<const double2*>(src + k));
-                    y0 = w.x; y1 = w.y;
-                } else {
-                    const float4 w = __ldcg(reinterpret_cast<const float4*>(src + k));
-                    y0.hi = w.x; y0.lo = w.y; y1.hi = w.z; y1.lo = w.w;
-                }
-                acc[k] = acc_add(acc[k], y0);
-                acc[k + 1] = acc_add(acc[k + 1], y1);
-            }
+            for (int k = 0; k < SPW; ++k) acc[k] = acc_add(acc[k], ld_acc(src + k));
         }
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < SPW; ++k) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) acc[k] = acc_add(acc[k], acc_shfl_down(acc[k], o));
         }
         if (lane == 0) {
 #pragma unroll
-            for (int k = 0; k < 8; ++k) red[warp * 8 + k] = acc_to_double(acc[k]);
+            for (int k = 0; k < SPW; ++k) red[warp * SPW + k] = acc_to_double(acc[k]);
         }
     }
     __shared__ DevState sst;
@@ -891,6 +898,7 @@ k_trial(const Prob<T>* __restrict__ probs, const Item* __restrict__ items) {
     __syncthreads();
     if (threadIdx.x == 0) {
         *P.counter = 0u;
+        sst.pass_cands = NC;
         finalize<T>(FIN_TRIAL, P, sst, red);          // the sums, from shared memory
     }
     __syncthreads();
@@ -1127,8 +1135,9 @@ void launch_tvgrad(const Prob<T>* d, const Item* items, int grid, int src, int f
     k_tvgrad<T><<<grid, kTileThreads, 0, s>>>(d, items, src, fuse, write_grad, step);
 }
 template <typename T>
-void launch_trial(const Prob<T>* d, const Item* items, int grid, cudaStream_t s) {
-    k_trial<T><<<grid, kBackThreads, 0, s>>>(d, items);
+void launch_trial(const Prob<T>* d, const Item* items, int grid, int ncand, cudaStream_t s) {
+    if (ncand == kTrialsFirst) k_trial<T, kTrialsFirst><<<grid, kBackThreads, 0, s>>>(d, items);
+    else k_trial<T, kTrials><<<grid, kBackThreads, 0, s>>>(d, items);
 }
 template <typename T>
 void launch_sino_axpy(const Prob<T>* d, const Item* items, int grid, int step, cudaStream_t s) {
@@ -1158,7 +1167,7 @@ void launch_taps(T* taps, int nb, int P, double mu, double gain, cudaStream_t s)
     template void launch_vec<T>(const Prob<T>*, const Item*, int, int, int, int, cudaStream_t);     \
     template void launch_tvgrad<T>(const Prob<T>*, const Item*, int, int, int, int, int,          \
                                    cudaStream_t);                                                 \
-    template void launch_trial<T>(const Prob<T>*, const Item*, int, cudaStream_t);                \
+    template void launch_trial<T>(const Prob<T>*, const Item*, int, int, cudaStream_t);                \
     template void launch_sino_axpy<T>(const Prob<T>*, const Item*, int, int, cudaStream_t);       \
     template cudaError_t launch_filter<T>(const Prob<T>*, const Item*, int, int, int, int, int,   \
                                           cudaStream_t);                                          \

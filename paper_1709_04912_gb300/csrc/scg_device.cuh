@@ -38,7 +38,12 @@ namespace scg {
 constexpr int kPad = 2;          // zero elements on each side of an image-view line
 constexpr int kSPad = 2;         // zero elements on each side of a sinogram-view row
 constexpr int kSlots = 32;       // FP64 partial sums per work item (at most)
-constexpr int kTrials = 31;      // TV trial candidates per pass (+1 baseline slot)
+constexpr int kTrials = 31;      // TV trial candidates per pass (+1 baseline slot) ...
+constexpr int kTrialsFirst = 3;  // ... except a step's first pass
+// trial passes in a loop body for a budget of max_trials candidates per step
+__host__ __device__ constexpr int trial_passes_for(int max_trials) {
+    return max_trials <= kTrialsFirst ? 1 : 1 + (max_trials - kTrialsFirst + kTrials - 1) / kTrials;
+}
 constexpr int kTileW = 32;       // image tile width (pixels) = one warp
 constexpr int kTileH = 8;        // image tile height
 constexpr int kTileThreads = kTileW * kTileH;
@@ -125,6 +130,7 @@ struct DevState {
     int perturb, gamma_fixed, max_trials, trials, accepted;
     int in_init, variant, inner_stop, family;
     int bodies, max_bodies;  // loop bodies started by the device loop, and its hard cap
+    int pass_cands;          // candidates of the trial pass being finalised
 };
 
 enum Family { FAM_CG = 0, FAM_S_PR = 1, FAM_S_K = 2 };
@@ -468,7 +474,7 @@ enum Step {
     FIN_NUM,          // new direction formed: S0 = g'^T p'
     FIN_ALPHA,        // h' backprojection: S0 = p'^T h'  ->  alpha = -g'^T p' / p'^T h'
     FIN_END,          // TV gradient of the new iterate: S0 = TV, S1 = ||dTV||^2, S2 = ||x||^2
-    FIN_TRIAL,        // trial pass: S0..S6 = TV of candidates, S7 = TV(x)
+    FIN_TRIAL,        // trial pass: S0..S(nc-1) = TV of the candidates, S(nc) = TV(x)
     FIN_CG_DELTA,     // CG(-K) start: S0 = ||g||^2, S1 = g^T z
     FIN_CG_ALPHA,     // CG-STEP: S0 = p^T h -> alpha = delta / p^T h
     FIN_CG_F,         // recursive residual: f = S0/2
@@ -583,9 +589,10 @@ __device__ void finalize(int step, const Prob<T>& P, DevState& st, const double*
         top_of_loop(P, st);
         break;
     case FIN_TRIAL: {
-        const double base = S[kTrials];
+        const int nc = st.pass_cands;
+        const double base = S[nc];
         int valid = st.max_trials - st.trials;
-        if (valid > kTrials) valid = kTrials;
+        if (valid > nc) valid = nc;
         int acc = -1;
         for (int t = 0; t < valid; ++t) {
             double rel = fabs(S[t] - base) / (base > 0.0 ? base : 1.0);

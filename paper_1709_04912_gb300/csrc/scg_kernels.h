@@ -31,7 +31,7 @@ template <typename T>
 void launch_tvgrad(const Prob<T>* d, const Item* items, int grid, int src, int fuse,
                    int write_grad, int step, cudaStream_t s);
 template <typename T>
-void launch_trial(const Prob<T>* d, const Item* items, int grid, cudaStream_t s);
+void launch_trial(const Prob<T>* d, const Item* items, int grid, int ncand, cudaStream_t s);
 template <typename T>
 void launch_sino_axpy(const Prob<T>* d, const Item* items, int grid, int step, cudaStream_t s);
 template <typename T>
