@@ -283,31 +283,42 @@ k_project(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int
 
 // ---------------------------------------------------------------------------
 // Backprojector: a 32 x TH tile per cluster of CL blocks of 128 threads, PIX
-// pixels per thread (rows ty, ty + TH/PIX, ...), each block 1/CL of the angles.  A pixel whose centre
-// projects to bin coordinate cb can only meet bins floor(cb) and floor(cb)+1
+// pixels per thread (rows ty, ty + TH/PIX, ...), each block 1/CL of the
+// angles.  A pixel whose centre projects to bin coordinate cb can only meet
+// bins floor(cb) and floor(cb)+1
 // ((m+n)/2 <= 1/sqrt(2)); their weights are two saturating FMAs of cb's
 // fractional part (see Angle), and the two bins are one pair-layout load.  The
 // sinogram views hold r[a,b] / m_a (the chord factor 1/m of the angle is
 // applied when a view is written), so the gather is two FMAs per pixel.
 //
 // Angles are processed in chunks.  For each angle the band of sinogram pairs
-// the tile can touch (<= 31|c| + (TH-1)|s| + 4 < kBand slots) is copied into
-// shared memory with cp.async, double-buffered so the next chunk's copies
-// overlap this chunk's arithmetic; parts of a band beyond the detector are
-// zero-filled by the copy itself, so the inner loop needs no bounds test.  The
-// projection of the tile's first pixel comes from 32.32 fixed point (FP64 in
-// the FP64 kernel), split into integer + fraction; each pixel adds only its
-// small in-tile offset (9.23 fixed point in the FP32 kernel: the fraction
-// bits are directly a float mantissa).
-constexpr int kBand = 48;
+// the tile can touch is copied into shared memory with cp.async,
+// double-buffered so the next chunk's copies overlap this chunk's arithmetic;
+// parts of a band beyond the detector are zero-filled by the copy itself, so
+// the inner loop needs no bounds test.  A band starts at the slot of
+// floor(projection of the tile origin) + floor(31 min(c, 0)) - 1, rounded
+// down to a 16-byte boundary (g slots of g = 16 / sizeof(pair)), and the
+// tile's pixels then reach at most 31 (|c| + |s|) + g + 2 < 44 + g + 2 slots
+// further (|c| + |s| <= sqrt 2, 32 x 32 tile): kBand = 48 slots for FP32
+// pairs (g = 2), 52 for 16-bit pairs (g = 4).  The projection of the tile's
+// first pixel comes from 32.32 fixed point (FP64 in the FP64 kernel), split
+// into integer + fraction; each pixel adds only its small in-tile offset
+// (9.23 fixed point in the FP32 kernel: the fraction bits are directly a
+// float mantissa).
+template <typename S2> constexpr int band_slots() { return sizeof(S2) >= 8 ? 48 : 52; }
 // Tile height, pixels per thread, angles per chunk, and blocks per tile (CL
 // blocks -- a thread-block cluster -- take consecutive parts of the angles of
-// one tile; the second hands its sums to the first through distributed shared
-// memory).  The gather is issue-bound, and at 512^2 one block per tile leaves
-// only 3.4 blocks per SM, unevenly spread; two per tile measured 19 % faster
-// there on GB300 (8 % at 1024^2) ...
+// one tile; blocks 1..CL-1 hand their sums to block 0 through distributed
+// shared memory).  32 x 32 tiles with 8 pixels per thread spread each angle's
+// set-up (row of constants, tile-origin position, chunk copies) over twice
+// the pixels of 32 x 16 tiles; four blocks per tile keep 1024 blocks in
+// flight at 512^2.  Measured on GB300 (one right-hand side): 32 x 16 tiles in
+// clusters of 2 -> 32 x 32 in clusters of 4: 97.8 -> 86.1 us at 512^2 / 720
+// angles, 664 -> 610 us at 1024^2 / 1440 ...
 template <typename T, int NRHS> struct BpCfg {
-    static constexpr int TH = kBpTileH32, PIX = 4, CH = NRHS == 1 ? 32 : 16, CL = 2;
+    static constexpr int TH = kBpTileH32, PIX = 8, CL = 4;
+    // the hand-over of three blocks' sums reuses the band storage
+    static constexpr int CH = (NRHS == 1 || sizeof(typename Tr<T>::S2) == 4) ? 32 : 16;
 };
 // ... and FP64 (48 KB static shared memory)
 template <int NRHS> struct BpCfg<double, NRHS> {
@@ -353,17 +364,18 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
     constexpr int CL = BpCfg<T, NRHS>::CL;
     constexpr int kStep = TH / PIX;                   // rows between a thread's pixels
     static_assert(kTileW * kStep == kBackThreads, "one thread per column and row group");
+    constexpr int kBand = band_slots<S2>();
     constexpr int kSlotsPerSeg = 16 / (int)sizeof(S2);
+    static_assert(kBand % kSlotsPerSeg == 0, "whole 16-byte copies");
     constexpr int kSegs = kBand / kSlotsPerSeg;       // 16-byte copies per band
     // launched in clusters of CL blocks along x: block rank blockIdx.x % CL
-    const int part = CL == 2 ? (int)(blockIdx.x & 1) : 0;
-    const Item it = decode_item(probs, items, 4, CL == 2 ? (int)(blockIdx.x >> 1) : (int)blockIdx.x);
+    const int part = (int)(blockIdx.x % CL);
+    const Item it = decode_item(probs, items, 4, (int)(blockIdx.x / CL));
     const Prob<T>& P = probs[it.prob];
     if (P.st->done) return;                      // the same flag for both blocks of a cluster
     __shared__ Row rows[2][CH];
     __shared__ int slo[2][CH];                   // first slot of each band in its sinogram row
     __shared__ __align__(16) S2 band[2][NRHS][CH][kBand];
-    __shared__ C xs[CL == 2 ? NRHS * PIX * kBackThreads : 1];   // the second block's sums
     const int N = P.n, na = P.na, nb = P.nb, SB = P.SB;
     const int tl = threadIdx.x;
     const int nap = (na + CL - 1) / CL;          // angles of each block
@@ -487,11 +499,15 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
         }
         __syncthreads();
     }
-    if constexpr (CL == 2) {
-        // the second block writes its sums into the first block's xs; one
-        // cluster barrier (release / acquire) orders the writes before the
-        // first block's reads.  Fixed order: first half + second half.
-        if (part == 1) {
+    if constexpr (CL > 1) {
+        // blocks 1..CL-1 write their sums into block 0's band storage (free once
+        // every block of the cluster has passed the first cluster barrier;
+        // release / acquire), and block 0 adds them in rank order after the
+        // second: first part of the angles + second + ...
+        C* xs = reinterpret_cast<C*>(&band[0][0][0][0]);
+        static_assert(sizeof(C) * (CL - 1) * NRHS * PIX * kBackThreads <= sizeof(band), "hand-over fits");
+        asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+        if (part != 0) {
             const unsigned local = (unsigned)__cvta_generic_to_shared(&xs[tl]);
             unsigned remote;
             asm volatile("mapa.shared::cluster.u32 %0, %1, 0;" : "=r"(remote) : "r"(local));
@@ -499,15 +515,19 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
             for (int h = 0; h < NRHS; ++h)
 #pragma unroll
                 for (int k = 0; k < PIX; ++k)
-                    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(remote + (unsigned)(sizeof(C) * (h * PIX + k) * kBackThreads)),
+                    asm volatile("st.shared::cluster.f32 [%0], %1;"
+                                 ::"r"(remote + (unsigned)(sizeof(C) * (((part - 1) * NRHS + h) * PIX + k) * kBackThreads)),
                                  "f"((float)acc[h][k]) : "memory");
         }
         asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-        if (part == 1) return;
+        if (part != 0) return;
 #pragma unroll
-        for (int h = 0; h < NRHS; ++h)
+        for (int r = 1; r < CL; ++r)
 #pragma unroll
-            for (int k = 0; k < PIX; ++k) acc[h][k] = acc[h][k] + xs[(h * PIX + k) * kBackThreads + tl];
+            for (int h = 0; h < NRHS; ++h)
+#pragma unroll
+                for (int k = 0; k < PIX; ++k)
+                    acc[h][k] = acc[h][k] + xs[(((r - 1) * NRHS + h) * PIX + k) * kBackThreads + tl];
     }
     using S = typename Tr<T>::S;
     const int dst[2] = {dst0, dst1};

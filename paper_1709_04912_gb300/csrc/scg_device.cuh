@@ -48,7 +48,7 @@ constexpr int kTileW = 32;       // image tile width (pixels) = one warp
 constexpr int kTileH = 8;        // image tile height
 constexpr int kTileThreads = kTileW * kTileH;
 constexpr int kBackThreads = 128;               // backprojector block: 32 x kBpTileH pixels ...
-constexpr int kBpTileH32 = 16;                  // ... 4 per thread (FP32 arithmetic)
+constexpr int kBpTileH32 = 32;                  // ... 8 per thread (FP32 arithmetic)
 constexpr int kBpTileH64 = 8;                   // ... 2 per thread (FP64)
 constexpr int kRayBlock = 128;   // rays per sinogram-row work item (axpy, pairs)
 constexpr int kProjLog2 = 8;     // projector block: 2^8 threads = adjacent angles x consecutive
