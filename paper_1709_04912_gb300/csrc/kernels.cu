@@ -372,7 +372,7 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
     const int part = (int)(blockIdx.x % CL);
     const Item it = decode_item(probs, items, 4, (int)(blockIdx.x / CL));
     const Prob<T>& P = probs[it.prob];
-    if (P.st->done) return;                      // the same flag for both blocks of a cluster
+    if (P.st->done) return;                      // the same flag for every block of a cluster
     __shared__ Row rows[2][CH];
     __shared__ int slo[2][CH];                   // first slot of each band in its sinogram row
     __shared__ __align__(16) S2 band[2][NRHS][CH][kBand];
@@ -385,7 +385,7 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
     const int j = tj0 + tx;
     const int X2 = 2 * tj0 - (N - 1), Y2 = 2 * ti0 - (N - 1);
     const S2* R[2] = {P.sino[src0], NRHS == 2 ? P.sino[src1] : P.sino[src0]};
-    const int nchunks = (nap + CH - 1) / CH;     // the same for every group
+    const int nchunks = (nap + CH - 1) / CH;     // the same for every block of the cluster
 
     auto stage_rows = [&](int ch) {
         const int q = tl;
