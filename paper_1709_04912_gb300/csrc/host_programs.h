@@ -79,6 +79,7 @@ struct Plan {
     int S, SB, cnt_ray, cnt_img, cnt_row, tiles_x, ray_blocks, filt_blocks, P;
     int cnt_proj, proj_blocks, proj_shift;
     int cnt_bp;
+    int part_cap;           // work items the partial-sum buffer holds per slot
 };
 
 // Projector items for the block shape 2^(8-shift) angles x 2^shift rays.
@@ -132,6 +133,7 @@ inline Plan make_plan(const scg_geometry& g, int variant, int precision, int kin
     if (max_proj > maxcnt) maxcnt = max_proj;
     if (p.cnt_bp > maxcnt) maxcnt = p.cnt_bp;
     p.partials = take(sizeof(double) * kSlots * (size_t)maxcnt);
+    p.part_cap = maxcnt;
     p.counter = take(sizeof(unsigned) * 4);
     p.view_rm = take(2 * tsize * (size_t)N * p.S);
     p.view_cm = take(2 * tsize * (size_t)N * p.S);
@@ -249,6 +251,7 @@ Prob<T> make_prob(const scg_geometry& g, const Plan& pl, unsigned char* base, do
     P.view_rm = reinterpret_cast<E2*>(base + pl.view_rm);
     P.view_cm = reinterpret_cast<E2*>(base + pl.view_cm);
     P.partials = reinterpret_cast<double*>(base + pl.partials);
+    P.part_cap = pl.part_cap;
     P.counter = reinterpret_cast<unsigned*>(base + pl.counter);
     P.st = reinterpret_cast<DevState*>(base + pl.state);
     P.trace = pl.trace == (size_t)-1 ? nullptr : reinterpret_cast<double*>(base + pl.trace);

@@ -881,7 +881,7 @@ k_trial(const Prob<T>* __restrict__ probs, const Item* __restrict__ items) {
     if (threadIdx.x < NS) {
         A b = wsum[0][threadIdx.x];
         for (int w = 1; w < NW; ++w) b = acc_add(b, wsum[w][threadIdx.x]);
-        parts[(size_t)it.local * kSlots + threadIdx.x] = b;
+        parts[(size_t)threadIdx.x * P.part_cap + it.local] = b;
     }
     __syncthreads();
     if (threadIdx.x == 0) s_last = arrive_last(P.counter, (unsigned)P.cnt_bp);
@@ -899,9 +899,9 @@ k_trial(const Prob<T>* __restrict__ probs, const Item* __restrict__ items) {
         for (int k = 0; k < SPW; ++k) acc_zero(acc[k]);
 #pragma unroll 4
         for (int q = lane; q < P.cnt_bp; q += 32) {      // loads of 4 items in flight
-            const A* src = parts + (size_t)q * kSlots + warp * SPW;
 #pragma unroll
-            for (int k = 0; k < SPW; ++k) acc[k] = acc_add(acc[k], ld_acc(src + k));
+            for (int k = 0; k < SPW; ++k)
+                acc[k] = acc_add(acc[k], ld_acc(parts + (size_t)(warp * SPW + k) * P.part_cap + q));
         }
 #pragma unroll
         for (int k = 0; k < SPW; ++k) {

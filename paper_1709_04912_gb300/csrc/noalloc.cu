@@ -78,6 +78,7 @@ int tv_static_impl(int n, const void* x, double* tv_out, cudaStream_t s) {
     P.cnt_img = ((n + kTileH - 1) / kTileH) * P.tiles_x;
     P.img[IB_AUX] = const_cast<T*>(static_cast<const T*>(x));
     P.partials = reinterpret_cast<double*>(base + kOffPartials);
+    P.part_cap = kStaticTiles;
     P.counter = reinterpret_cast<unsigned*>(base + kOffCounter);
     P.st = reinterpret_cast<DevState*>(base + kOffState);
     P.trace = tv_out;

@@ -20,8 +20,10 @@
 //                      never need a bounds test (a clamped pair reads pads);
 //                      a view holds v[a,b] * inv_m(a) (the angle's chord factor,
 //                      applied once when the view is written).
-//   partials           kSlots doubles per work item, summed in a fixed order
-//                      by the last item of a launch (no atomics on data).
+//   partials           up to kSlots sums per work item, slot-major (slot k of
+//                      item i at k * part_cap + i, so the final sum reads
+//                      consecutive items), summed in a fixed order by the last
+//                      item of a launch (no atomics on data).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -37,7 +39,7 @@ namespace scg {
 
 constexpr int kPad = 2;          // zero elements on each side of an image-view line
 constexpr int kSPad = 2;         // zero elements on each side of a sinogram-view row
-constexpr int kSlots = 32;       // FP64 partial sums per work item (at most)
+constexpr int kSlots = 32;       // FP64 partial sums per work item (at most); stored slot-major
 constexpr int kTrials = 31;      // TV trial candidates per pass (+1 baseline slot) ...
 constexpr int kTrialsFirst = 3;  // ... except a step's first pass
 // trial passes in a loop body for a budget of max_trials candidates per step
@@ -216,7 +218,7 @@ struct Prob {
     DevState* st;
     double* trace;
     int trace_rows;
-    int pad_;
+    int part_cap;           // items per slot of `partials` (slot-major: partials[k * part_cap + item])
 };
 
 // ---------------------------------------------------------------------------
@@ -422,9 +424,8 @@ __device__ void reduce_and_finalize(Acc<T> (&v)[NS], const Prob<T>& P, int local
     block_sum<A, NS, kPositive>(v, red);
     A* parts = reinterpret_cast<A*>(P.partials);
     if (threadIdx.x == 0) {
-        A* dst = parts + (size_t)local * kSlots;
 #pragma unroll
-        for (int k = 0; k < NS; ++k) dst[k] = v[k];
+        for (int k = 0; k < NS; ++k) parts[(size_t)k * P.part_cap + local] = v[k];
         s_last = arrive_last(P.counter, (unsigned)total);
     }
     __syncthreads();
@@ -436,16 +437,16 @@ __device__ void reduce_and_finalize(Acc<T> (&v)[NS], const Prob<T>& P, int local
     for (int k = 0; k < NS; ++k) acc_zero(acc[k]);
 #pragma unroll 4
     for (int it = threadIdx.x; it < total; it += blockDim.x) {      // loads of 4 items in flight
-        const A* src = parts + (size_t)it * kSlots;
 #pragma unroll
         for (int k = 0; k < NS; ++k) {
+            const A* src = parts + (size_t)k * P.part_cap + it;   // consecutive items: coalesced
             A x;
             if constexpr (sizeof(A) == 8 && !std::is_same<A, double>::value) {
-                const float2 w = __ldcg(reinterpret_cast<const float2*>(src + k));
+                const float2 w = __ldcg(reinterpret_cast<const float2*>(src));
                 x.hi = w.x;
                 x.lo = w.y;
             } else {
-                x = __ldcg(reinterpret_cast<const double*>(src + k));
+                x = __ldcg(reinterpret_cast<const double*>(src));
             }
             acc[k] = acc_add(acc[k], x);
         }
