@@ -293,6 +293,14 @@ struct Program {
     int variant, trial_passes, ksteps;
 };
 
+// g'^T p' for the step length: FIN_BETA derives it from the gradient pass's
+// sums (-g'^T d + beta g'^T p, exact for the unrounded p'); with 16-bit
+// storage p' is rounded to 11 or 8 bits, and the dot is taken again on the
+// stored p' when it is formed, so that alpha is the exact line search along
+// the direction actually used.
+template <typename T>
+constexpr int num_step() { return sizeof(typename Tr<T>::S) < 4 ? FIN_NUM : FIN_NONE; }
+
 // The algorithms' set-up steps (before the first loop test).
 template <typename T>
 void run_init(Runner<T>& R, const Program& pg) {
@@ -314,7 +322,7 @@ void run_init(Runner<T>& R, const Program& pg) {
     }
     if (pre) R.back2(SB_R, SB_W, IB_G, IB_Z, FIN_BETA);
     else R.back1(SB_R, IB_G, FIN_BETA);                // g0 = A^T (A x0 - y)
-    R.vec(VEC_FORM_P0, dsel, FIN_NUM);                 // p0 = -g0 (-z0), g0^T p0
+    R.vec(VEC_FORM_P0, dsel, num_step<T>());           // p0 = -g0 (-z0) (g0^T p0: see num_step)
     R.project(SB_Q, PROJ_PLAIN, FIN_NONE);             // A p0
     R.back1(SB_Q, IB_H, FIN_ALPHA);                    // h0 = A^T A p0, alpha
     R.tvgrad(IB_X, 1, 1, FIN_END);                     // x1 = x0 + alpha p0 (+ dTV(x1)); k = 1; loop test
@@ -364,7 +372,7 @@ void run_body(Runner<T>& R, const Program& pg) {
     // CG-PR-STEP / CG-CD-STEP / PCG-PR-STEP
     if (pre) R.back2(SB_R, SB_W, IB_G, IB_Z, FIN_BETA);   // g', z' = M g'
     else R.back1(SB_R, IB_G, FIN_BETA);                // g' = A^T (A x - y), beta
-    R.vec(VEC_FORM_P, dsel, FIN_NUM);                  // p' = -g' (-z') + beta p, g'^T p'
+    R.vec(VEC_FORM_P, dsel, num_step<T>());            // p' = -g' (-z') + beta p (g'^T p': see num_step)
     R.project(SB_Q, PROJ_PLAIN, FIN_NONE);             // A p'
     R.back1(SB_Q, IB_H, FIN_ALPHA);                    // h' = A^T A p', alpha
     R.tvgrad(IB_X, 1, 1, FIN_END);                     // x' = x + alpha p' (+ dTV); k = k+1; loop test

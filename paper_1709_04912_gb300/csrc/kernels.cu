@@ -531,8 +531,10 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
     }
     using S = typename Tr<T>::S;
     const int dst[2] = {dst0, dst1};
-    Acc<T> v[3];
-    acc_zero(v[0]); acc_zero(v[1]); acc_zero(v[2]);
+    constexpr int NSUM = NRHS == 2 ? 4 : 3;
+    Acc<T> v[NSUM];
+#pragma unroll
+    for (int q = 0; q < NSUM; ++q) acc_zero(v[q]);
 #pragma unroll
     for (int k = 0; k < PIX; ++k) {
         const int i = ti0 + ty + k * kStep;
@@ -550,6 +552,7 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
             v[0] = acc_add(v[0], acc_prod(NRHS == 2 ? g1 : g0, to_c(P.img[IB_H][idx])));  // g'^T h (z'^T h)
             v[1] = acc_add(v[1], acc_prod(g0, g0));                                       // ||g'||^2
             v[2] = acc_add(v[2], acc_prod(g0, to_c(P.img[IB_P][idx])));                   // g'^T p
+            if constexpr (NRHS == 2) v[NSUM - 1] = acc_add(v[NSUM - 1], acc_prod(g0, g1)); // g'^T z'
         } else if (step == FIN_ALPHA || step == FIN_CG_ALPHA) {
             v[0] = acc_add(v[0], acc_prod(to_c(P.img[IB_P][idx]), g0));                   // p^T h
         } else if (step == FIN_CG_DELTA) {
@@ -558,7 +561,7 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
         }
     }
     if (step == FIN_NONE) return;
-    reduce_and_finalize<T, 3>(v, P, it.local, P.cnt_bp, step);
+    reduce_and_finalize<T, NSUM>(v, P, it.local, P.cnt_bp, step);
 }
 
 // ---------------------------------------------------------------------------

@@ -471,8 +471,9 @@ __device__ void reduce_and_finalize(Acc<T> (&v)[NS], const Prob<T>& P, int local
 enum Step {
     FIN_NONE = 0,
     FIN_F,            // residual projection: f = S0/2 at the point just projected
-    FIN_BETA,         // gradient backprojection (S-variants): S0 = g'^T h (or z'^T h), S1 = ||g'||^2
-    FIN_NUM,          // new direction formed: S0 = g'^T p'
+    FIN_BETA,         // gradient backprojection (S-variants): S0 = g'^T h (or z'^T h), S1 = ||g'||^2,
+                      // S2 = g'^T p, S3 = g'^T z' (S-PCG)
+    FIN_NUM,          // new direction formed: S0 = g'^T p' (16-bit storage; FIN_BETA otherwise)
     FIN_ALPHA,        // h' backprojection: S0 = p'^T h'  ->  alpha = -g'^T p' / p'^T h'
     FIN_END,          // TV gradient of the new iterate: S0 = TV, S1 = ||dTV||^2, S2 = ||x||^2
     FIN_TRIAL,        // trial pass: S0..S(nc-1) = TV of the candidates, S(nc) = TV(x)
@@ -559,15 +560,23 @@ __device__ void finalize(int step, const Prob<T>& P, DevState& st, const double*
         break;
     case FIN_BETA: {
         st.gg = S[1];
-        if (st.in_init) { st.beta = 0.0; break; }
-        if (st.variant == SCG_S_CG_CD) {
+        if (st.in_init) {
+            st.beta = 0.0;
+        } else if (st.variant == SCG_S_CG_CD) {
             if (S[1] == 0.0) st.beta = 0.0;
             else if (!(st.gTp < 0.0) || !isfinite(st.gTp)) { breakdown(st); break; }
             else st.beta = -S[1] / st.gTp;               // beta = -||g'||^2 / g^T p
         } else {
             st.beta = S[0] / st.pTh;                     // beta = g'^T h / p^T h (z'^T h for S-PCG)
         }
-        if (row) row[TR_BETA] = st.beta;
+        if (row && !st.in_init) row[TR_BETA] = st.beta;
+        // g'^T p' of the direction formed next, p' = -d + beta p (d = g', or z'
+        // for S-PCG): -g'^T d + beta g'^T p from this pass's sums, so forming p'
+        // needs no reduction of its own.  (16-bit storage recomputes it from the
+        // rounded p' in that pass: FIN_NUM.)
+        const double gd = st.variant == SCG_S_PCG ? S[3] : S[1];
+        st.num = -gd + st.beta * S[2];
+        if (st.variant == SCG_S_CG_CD) st.gTp = st.num;
         break;
     }
     case FIN_NUM:
