@@ -101,6 +101,24 @@ def test_fp32_whole_solve_matches_oracle(small, variant):
     assert r.tv_final == pytest.approx(ro["tv_final"], rel=2e-2 if variant == "CG" else 1e-3)
 
 
+# Perturbation settings whose steps accept inside the first trial pass (three
+# candidates), at its last candidate, inside a later pass, or reject every
+# candidate of two or three passes.  Oracle traces (trials, accepted) on this
+# workload: (0.5, 0.975, 31): (31,0) (31,0) (21,1) (4,1) (1,1) (5,1) ...;
+# (0.05, 0.5, 31): (3,1) (1,1) ...; (2.0, 0.975, 40): (40,0) x3 (5,1) (6,1) (1,1)
+# (8,1) ...; smallest TV margin of a decision 2e-4, so FP32 decides alike.
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("gamma0_rel,a,max_trials", [(0.5, 0.975, 31), (0.05, 0.5, 31), (2.0, 0.975, 40)])
+def test_trial_passes_decide_like_the_oracle(small, gamma0_rel, a, max_trials, dtype):
+    kw = kw_for("S-CG", small, gamma0_rel=gamma0_rel, a=a, max_trials=max_trials)
+    xo, ro, to = oracle.solve(small.y, small.work.n, **kw)
+    assert np.all(to[:, 10] > 1e-5)
+    r = gpu_solve(small, dtype, **kw)
+    assert r.status == ro["status"] and r.iters == ro["iters"] and r.ell == ro["ell"]
+    np.testing.assert_array_equal(r.trace[:, DECISION], to[:, DECISION])
+    assert rel(r.x.cpu().numpy(), xo) <= (1e-9 if dtype == torch.float64 else FP32_BOUND["S-CG"])
+
+
 @pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-11), (torch.float32, 1e-5)])
 @pytest.mark.parametrize("variant", VARIANTS)
 def test_single_loop_body_from_oracle_state(small, variant, dtype, tol):
