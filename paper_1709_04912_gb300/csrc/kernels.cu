@@ -270,10 +270,13 @@ k_project(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int
     acc_zero(v[0]);
     const bool valid = a < P.na && b < nb;
     const Angle<C> g = P.ang[valid ? a : 0];
+    // the residual's data value, loaded before the walk so that its latency is
+    // hidden (y_scale is 1 except for half/bfloat16 storage; the product is exact)
+    C yv = C(0);
+    if (valid && mode == PROJ_RESIDUAL) yv = to_c(P.y[(size_t)a * nb + b]) * P.y_scale;
     C out = project_ray<T>(P, g, b, valid);                // every lane: the FP32 walk is warp-wide
     if (valid) {
-        // (y_scale is 1 except for half/bfloat16 storage; the product is exact)
-        if (mode == PROJ_RESIDUAL) out = out - to_c(P.y[(size_t)a * nb + b]) * P.y_scale;
+        if (mode == PROJ_RESIDUAL) out = out - yv;
         if (mode == PROJ_PLAIN_OUT) P.user_out[(size_t)a * nb + b] = to_s<typename Tr<T>::S>(out);
         else store_pair<T>(P.sino[dst_sel] + (size_t)a * P.SB + kSPad, b, out * g.inv_m);   // weighted view
         v[0] = acc_prod(out, out);
