@@ -502,6 +502,19 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
         }
         __syncthreads();
     }
+    // block 0's epilogue operands (h and p for the fused dots), loaded before
+    // the cluster barriers so that their latency overlaps the hand-over
+    const bool want_h = step == FIN_BETA;
+    const bool want_p = step == FIN_BETA || step == FIN_ALPHA || step == FIN_CG_ALPHA;
+    C hv[PIX], pv[PIX];
+#pragma unroll
+    for (int k = 0; k < PIX; ++k) {
+        const int i = ti0 + ty + k * kStep;
+        const bool in = part == 0 && i < N && j < N;
+        const size_t idx = (size_t)i * N + j;
+        hv[k] = in && want_h ? to_c(P.img[IB_H][idx]) : C(0);
+        pv[k] = in && want_p ? to_c(P.img[IB_P][idx]) : C(0);
+    }
     if constexpr (CL > 1) {
         // blocks 1..CL-1 write their sums into block 0's band storage (free once
         // every block of the cluster has passed the first cluster barrier;
@@ -552,12 +565,12 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
         if (step == FIN_NONE) continue;
         const C g0 = acc[0][k], g1 = acc[NRHS - 1][k];
         if (step == FIN_BETA) {
-            v[0] = acc_add(v[0], acc_prod(NRHS == 2 ? g1 : g0, to_c(P.img[IB_H][idx])));  // g'^T h (z'^T h)
+            v[0] = acc_add(v[0], acc_prod(NRHS == 2 ? g1 : g0, hv[k]));                   // g'^T h (z'^T h)
             v[1] = acc_add(v[1], acc_prod(g0, g0));                                       // ||g'||^2
-            v[2] = acc_add(v[2], acc_prod(g0, to_c(P.img[IB_P][idx])));                   // g'^T p
+            v[2] = acc_add(v[2], acc_prod(g0, pv[k]));                                    // g'^T p
             if constexpr (NRHS == 2) v[NSUM - 1] = acc_add(v[NSUM - 1], acc_prod(g0, g1)); // g'^T z'
         } else if (step == FIN_ALPHA || step == FIN_CG_ALPHA) {
-            v[0] = acc_add(v[0], acc_prod(to_c(P.img[IB_P][idx]), g0));                   // p^T h
+            v[0] = acc_add(v[0], acc_prod(pv[k], g0));                                    // p^T h
         } else if (step == FIN_CG_DELTA) {
             v[0] = acc_add(v[0], acc_prod(g0, g0));                                       // ||g||^2
             v[1] = acc_add(v[1], acc_prod(g0, g1));                                       // g^T z
