@@ -382,7 +382,9 @@ template <typename T> __device__ void finalize(int step, const Prob<T>& P, DevSt
 // back -- instead of one dependent global round trip per state field.
 static_assert(sizeof(DevState) % 8 == 0, "state copied as 8-byte words");
 constexpr int kStateWords = (int)(sizeof(DevState) / 8);
-static_assert(kStateWords <= 128, "one word per thread: every finalising block has >= 128 threads");
+// one word per thread: every kernel that finalises runs blocks of at least this many threads
+static_assert(kStateWords <= kBackThreads && kStateWords <= kTileThreads && kStateWords <= kRayBlock &&
+              kStateWords <= kProjThreads, "state words per finalising block");
 struct StateCopy {
     unsigned long long w;
     __device__ __forceinline__ void load(const DevState* g) {
@@ -403,8 +405,8 @@ struct StateCopy {
 // barrier) are visible to whoever observes the increment.  Acquire: the block
 // that sees the count reach `total` sees every other item's partials (its
 // other threads after a block barrier).  Returns true for that last item.
-// (No separate __threadfence: a sequentially consistent fence per block, and
-// one per thread of the last block, cost several microseconds per launch.)
+// (It takes the place of a sequentially consistent __threadfence in every
+// block and in every thread of the last block.)
 __device__ __forceinline__ bool arrive_last(unsigned* counter, unsigned total) {
     unsigned prev;
     asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(prev) : "l"(counter) : "memory");
