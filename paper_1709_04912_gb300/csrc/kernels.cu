@@ -644,22 +644,22 @@ k_vec(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int op,
         write_views(P, it.u, it.v, val, in);
         break;
     }
-    case VEC_FORM_P: {          // p' = -d + beta p (d = g' or z'), views; S0 = g'^T p'
+    case VEC_FORM_P: {          // p' = -d + beta p (d = g' or z'), views; S0 = g'^T p' (if summed)
         const C beta = (C)st.beta;
         if (in) {
             const C d = to_c(P.img[sel][idx]);
             val = rnd<T>(fma(beta, to_c(P.img[IB_P][idx]), -d));
             P.img[IB_P][idx] = to_s<S>(val);
-            v[0] = acc_prod(to_c(P.img[IB_G][idx]), val);
+            if (step != FIN_NONE) v[0] = acc_prod(to_c(P.img[IB_G][idx]), val);
         }
         write_views(P, it.u, it.v, val, in);
         break;
     }
-    case VEC_FORM_P0: {         // p_0 = -d (first direction), views; S0 = g^T p_0
+    case VEC_FORM_P0: {         // p_0 = -d (first direction), views; S0 = g^T p_0 (if summed)
         if (in) {
             val = -to_c(P.img[sel][idx]);
             P.img[IB_P][idx] = to_s<S>(val);
-            v[0] = acc_prod(to_c(P.img[IB_G][idx]), val);
+            if (step != FIN_NONE) v[0] = acc_prod(to_c(P.img[IB_G][idx]), val);
         }
         write_views(P, it.u, it.v, val, in);
         break;
