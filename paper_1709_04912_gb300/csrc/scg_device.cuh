@@ -13,8 +13,9 @@
 //                      (view_rm[i*S + kPad + j]) for angles whose rays are
 //                      walked row by row, column-major lines
 //                      (view_cm[j*S + kPad + i]) for angles walked column by
-//                      column, so the lanes of a warp (consecutive rays) read
-//                      one short contiguous span of a line.
+//                      column, so the lanes of a warp (consecutive rays of a
+//                      few adjacent angles, walking the same strip together)
+//                      read a few short spans of one line.
 //   sinogram views     [angle][kSPad + bin] rows of SB pairs with zero pads, so
 //                      the backprojector's two candidate bins are one load and
 //                      never need a bounds test (a clamped pair reads pads);
