@@ -103,8 +103,9 @@ typedef struct {
                             perturbed (default 0)                                */
     double gamma0_rel;   /* default 0.05                                         */
     double a;            /* gamma_l = gamma_0 a^l; 0 < a < 1; default 0.975 (Sec. 4) */
-    int max_trials;      /* TV-acceptance trials per perturbation; default 31 (one
-                            pass of the trial kernel evaluates 31 candidates)   */
+    int max_trials;      /* TV-acceptance trials per perturbation; default 31 (a
+                            step's first trial pass evaluates 3 candidates, each
+                            later pass, run only while none is accepted, 31)    */
     int K;               /* CG-K/PCG-K inner steps (S-CG-K, S-PCG-K), 1 .. 1000;
                             default 2                                             */
     int k_inclusive;     /* 1: the printed loop "while k <= K" (K+1 steps); default 0 */
