@@ -37,7 +37,10 @@ from paper_1709_04912_gb300 import inputs  # noqa: E402
 
 METRIC = "S-CG recon/s at fixed eps"
 UNIT = "recon/s"
-OPS_PER_NNZ = 7           # FP32 lane operations per nonzero ray-pixel weight
+# FP32 lane operations per nonzero ray-pixel weight: the minimum for one
+# chord-weighted multiply-add (crossing position 2, its distance 1, the weight 3,
+# the accumulation 1)
+OPS_PER_NNZ = 7
 WORKLOADS = {w.name: w for w in (inputs.SINGLE_512, inputs.SMALL_FP64, inputs.MIXED_1024,
                                   inputs.PAPER_512)}
 
