@@ -103,9 +103,10 @@ typedef struct {
                             perturbed (default 0)                                */
     double gamma0_rel;   /* default 0.05                                         */
     double a;            /* gamma_l = gamma_0 a^l; 0 < a < 1; default 0.975 (Sec. 4) */
-    int max_trials;      /* TV-acceptance trials per perturbation; default 31 (a
+    int max_trials;      /* TV-acceptance trials per perturbation; default 32 (a
                             step's first trial pass evaluates 3 candidates, each
-                            later pass, run only while none is accepted, 31)    */
+                            later pass, run only while none is accepted, up to
+                            31)                                                   */
     int K;               /* CG-K/PCG-K inner steps (S-CG-K, S-PCG-K), 1 .. 1000;
                             default 2                                             */
     int k_inclusive;     /* 1: the printed loop "while k <= K" (K+1 steps); default 0 */
@@ -184,8 +185,9 @@ int scg_backproject(const scg_geometry* g, int precision, const void* r, void* x
 /* Release the library's host-side caches: the CUDA graphs captured for earlier
  * solves and batches (keyed by workspace address and geometry) and the
  * per-device side streams and pinned flags; they are rebuilt on the next call.
- * The tuned projector shapes are kept.  No library call may be running or
- * have work in flight.  The library holds no device memory of its own beyond
+ * The tuned projector shapes are kept; scg_tv_static's cached scratch
+ * addresses are forgotten.  No library call may be running or have work in
+ * flight.  The library holds no device memory of its own beyond
  * what these objects use. */
 int scg_release(void);
 
@@ -229,7 +231,10 @@ int scg_tv(int n, int precision, const void* x, double* tv_out,
  *   precision SCG_F32 or SCG_F64 (the storage formats return SCG_ERR_UNSUPPORTED);
  *   allocates nothing (no cudaMalloc/cudaFree, no allocating library call);
  *   the first call on a device looks up the array's device address with that
- *   device current -- make that first call before any stream capture;
+ *   device current -- make that first call before any stream capture; the
+ *   address belongs to that device's current context: after the context is
+ *   destroyed (cudaDeviceReset), call scg_release() before the next call so
+ *   that the address is looked up again;
  *   all calls share the array: calls that may overlap on the GPU (e.g. from
  *   two streams at once) race and give undefined results. */
 int scg_tv_static(int n, int precision, const void* x, double* tv_out, void* stream);

@@ -140,6 +140,8 @@ def lib():
         L.orc_filter_rows.argtypes = [i, i, d, d, dp, dp]
         L.orc_norm_A.argtypes = [i, i, i, i]
         L.orc_norm_A.restype = d
+        L.orc_perturb_gamma.argtypes = [i, dp, d, d, i, ctypes.POINTER(ctypes.c_longlong), dp, dp, ip]
+        L.orc_perturb_gamma.restype = i
         L.orc_solve.argtypes = [i, i, i, dp, dp, ctypes.POINTER(Params), dp,
                                 ctypes.POINTER(Result), dp, i, ITER_CB, ctypes.c_void_p,
                                 ctypes.POINTER(State), ctypes.POINTER(State)]
@@ -259,9 +261,24 @@ def norm_A(n: int, n_angles: int, n_bins: int, iters: int = 50) -> float:
     return float(lib().orc_norm_A(n, n_angles, n_bins, iters))
 
 
+def perturb_gamma(x: np.ndarray, gamma0: float, a: float, max_trials: int, ell: int = 0):
+    """One perturbation of the gamma rule from global index ``ell``: returns
+    (x_half, ell after, accepted gamma or 0, trials, outcome) with outcome 1
+    accepted, 0 every trial rejected (x kept), -1 zero subgradient."""
+    x = _f64(x)
+    n = x.shape[0]
+    xh = np.zeros_like(x)
+    e = ctypes.c_longlong(int(ell))
+    g = ctypes.c_double(0.0)
+    t = ctypes.c_int(0)
+    rc = lib().orc_perturb_gamma(n, _dp(x), float(gamma0), float(a), int(max_trials), ctypes.byref(e),
+                                 _dp(xh), ctypes.byref(g), ctypes.byref(t))
+    return xh, int(e.value), float(g.value), int(t.value), int(rc)
+
+
 def default_params(**kw) -> dict:
     p = dict(variant="S-CG", eps=1.0, perturb="gamma", gamma0=0.0, gamma0_rel=0.05,
-             a=0.975, max_trials=31, eta0=0.0, K=2, k_inclusive=0, mu=0.0,
+             a=0.975, max_trials=32, eta0=0.0, K=2, k_inclusive=0, mu=0.0,
              filter_gain=1.0, filter_identity=0, max_iter=100)
     p.update(kw)
     return p

@@ -535,6 +535,40 @@ static void perturb(orc_ctx* C, const double* xk, double* xh, double* trow)
     }
 }
 
+/* One perturbation step of the gamma rule on its own, for checking the rule
+ * against hand-worked cases: x_half = perturbed(x) with the global index l
+ * starting at *ell (updated on return), gamma_0 = gamma0 and kernel a.  Runs
+ * the same perturb() the solvers call.  *gamma_out = the accepted gamma (0 if
+ * none), *trials_out = trials taken, return value = 1 accepted, 0 all
+ * rejected (x kept), -1 no perturbation (zero subgradient). */
+int orc_perturb_gamma(int n, const double* x, double gamma0, double a, int max_trials,
+                      long long* ell, double* x_half, double* gamma_out, int* trials_out)
+{
+    orc_ctx C;
+    memset(&C, 0, sizeof(C));
+    C.n = n;
+    C.J = (size_t)n * n;
+    C.prm.perturb = ORC_PERTURB_GAMMA;
+    C.prm.a = a;
+    C.prm.max_trials = max_trials;
+    C.gamma0 = gamma0;
+    C.gamma_fixed = 1;
+    C.ell = *ell;
+    C.tvg = vec(C.J);
+    C.vdir = vec(C.J);
+    C.ztrial = vec(C.J);
+    double row[ORC_NF];
+    for (int q = 0; q < ORC_NF; ++q) row[q] = 0.0;
+    perturb(&C, x, x_half, row);
+    *ell = C.ell;
+    *gamma_out = row[ORC_T_ACCEPTED] == 1 ? row[ORC_T_GAMMA] : 0.0;
+    *trials_out = (int)row[ORC_T_TRIALS];
+    free(C.tvg);
+    free(C.vdir);
+    free(C.ztrial);
+    return (int)row[ORC_T_ACCEPTED];
+}
+
 /* Working vectors of one solve; also the exported/imported state. */
 typedef struct {
     int k;

@@ -128,6 +128,9 @@ void   orc_filter_rows(int na, int nb, double mu, double gain, const double* r, 
 
 double orc_norm_A(int n, int na, int nb, int iters);
 
+int orc_perturb_gamma(int n, const double* x, double gamma0, double a, int max_trials,
+                      long long* ell, double* x_half, double* gamma_out, int* trials_out);
+
 int orc_solve(int n, int na, int nb, const double* y, const double* x0,
               const orc_params* prm, double* x_out, orc_result* res,
               double* trace, int trace_rows, orc_iter_cb cb, void* user,

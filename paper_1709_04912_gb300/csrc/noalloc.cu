@@ -22,7 +22,10 @@
 // names a stand-in object, and a kernel given that address would fault or, on
 // systems where the GPU can reach host memory, silently use the wrong memory.
 // The device address is therefore fetched with cudaGetSymbolAddress, once per
-// device, with that device current, on the first call made on the device.
+// device, with that device current, on the first call made on the device.  The
+// address belongs to the device's current context: scg_release() forgets it,
+// so after a context is destroyed (cudaDeviceReset) the caller calls
+// scg_release() and the next call looks the address up again.
 #include <string.h>
 
 #include <mutex>
@@ -63,6 +66,18 @@ int scratch_address(unsigned char** out) {
     *out = g_scratch_dev[dev];
     return SCG_OK;
 }
+
+}  // namespace
+
+namespace scg {
+// Forget the cached scratch addresses (called by scg_release).
+void noalloc_forget() {
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (int d = 0; d < kMaxDevices; ++d) g_scratch_dev[d] = nullptr;
+}
+}  // namespace scg
+
+namespace {
 
 template <typename T>
 int tv_static_impl(int n, const void* x, double* tv_out, cudaStream_t s) {

@@ -42,6 +42,7 @@ void launch_taps(T* taps, int nb, int P, double mu, double gain, cudaStream_t s)
 template <typename T>
 void launch_sino_pairs(const Prob<T>* d, int grid, int dst, cudaStream_t s);
 void launch_loop_cond(DevState* st, cudaGraphConditionalHandle h, cudaStream_t s);
+void noalloc_forget();   // scg_tv_static's cached scratch addresses (noalloc.cu)
 template <typename T>
 void launch_set_io(Prob<T>* d, const typename Tr<T>::S* in_sino, typename Tr<T>::S* out_sino,
                    typename Tr<T>::S* image, cudaStream_t s);

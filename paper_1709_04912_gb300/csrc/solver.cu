@@ -799,7 +799,7 @@ void scg_default_params(scg_params* p) {
     p->gamma0 = 0.0;
     p->gamma0_rel = 0.05;
     p->a = 0.975;
-    p->max_trials = 31;
+    p->max_trials = 32;
     p->K = 2;
     p->k_inclusive = 0;
     p->mu = 0.0;
@@ -905,6 +905,7 @@ int scg_release(void) {
     g_streams.clear();
     for (auto& kv : g_pinned) cudaFreeHost(kv.second);
     g_pinned.clear();
+    scg::noalloc_forget();
     return rc;
 }
 

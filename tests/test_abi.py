@@ -45,7 +45,7 @@ def test_strerror_and_defaults(lib):
     assert lib.scg_strerror(0) == b"ok"
     assert b"invalid" in lib.scg_strerror(-1)
     p = scg.default_params()
-    assert p["a"] == 0.975 and p["max_trials"] == 31 and p["K"] == 2 and p["max_iter"] == 100
+    assert p["a"] == 0.975 and p["max_trials"] == 32 and p["K"] == 2 and p["max_iter"] == 100
 
 
 def test_workspace_queries(lib):

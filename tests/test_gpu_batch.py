@@ -126,3 +126,26 @@ def test_full_size_batch_of_uneven_problems():
         r = oracle.project(g.x.double().cpu().numpy(), p.work.n_angles, p.work.n_bins) - p.y
         assert 0.5 * float(np.sum(r * r)) <= p.eps * (1 + 1e-4)
         same(g, scg.scg_solve(y, p.work.n, "S-CG", p.eps, gamma0_rel=0.05, max_iter=100))
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.mark.parametrize("variant", ["CG", "PCG", "S-CG", "S-CG-CD", "S-CG-K", "S-PCG", "S-PCG-K"])
+def test_batch_members_match_the_oracle(variant):
+    # every member of an FP64 batch against the oracle's solve of that problem
+    # alone: same status, iteration count, perturbation index l, output within
+    # 1e-9 relative L2 (the FP64 single-solve bar)
+    probs = problems(MIX_A + MIX_B[:2], 80)
+    ys = [torch.tensor(p.y, dtype=torch.float64, device=DEV) for p in probs]
+    kw = params_for(variant)
+    got = scg.scg_solve_batch(ys, [p.work.n for p in probs], variant, [p.eps for p in probs], **kw)
+    for p, g in zip(probs, got):
+        xo, ro, to = oracle.solve(p.y, p.work.n, variant=variant, eps=p.eps, **kw)
+        assert g.status == ro["status"] and g.iters == ro["iters"] and g.ell == ro["ell"], p.work.name
+        assert rel(g.x.cpu().numpy(), xo) <= 1e-9, p.work.name
+        assert g.tv_final == pytest.approx(ro["tv_final"], rel=1e-9)
+        assert g.f_final == pytest.approx(ro["f_final"], rel=1e-9)

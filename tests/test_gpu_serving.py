@@ -154,3 +154,26 @@ def test_serving_workload_sizes_in_binary16():
         yq = ys[q].double().cpu().numpy()
         r = oracle.project(done[q].x.double().cpu().numpy(), p.work.n_angles, p.work.n_bins) - yq
         assert 0.5 * float(np.sum(r * r)) <= p.eps * (1 + 1e-3)
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.mark.parametrize("variant", ["CG", "S-CG", "S-CG-CD", "S-PCG-K"])
+def test_served_results_match_the_oracle(requests, variant):
+    # an FP64 server: every completion against the oracle's solve of that
+    # request alone (status, iterations, l, output within 1e-9 relative L2)
+    ys = [torch.tensor(p.y, dtype=torch.float64, device=DEV) for p in requests]
+    kw = params_for(variant)
+    srv = scg.Server(variant, torch.float64, pool_bytes=256 << 20, max_active=4, **kw)
+    done = serve(srv, requests, ys, [[0, 1, 2], [3], [4, 5], [], [6]])
+    srv.close()
+    for q, p in enumerate(requests):
+        xo, ro, _ = oracle.solve(p.y, p.work.n, variant=variant, eps=p.eps, **kw)
+        g = done[q]
+        assert g.status == ro["status"] and g.iters == ro["iters"] and g.ell == ro["ell"], p.work.name
+        assert rel(g.x.cpu().numpy(), xo) <= 1e-9, p.work.name
+        assert g.tv_final == pytest.approx(ro["tv_final"], rel=1e-9)

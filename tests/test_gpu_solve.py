@@ -218,3 +218,26 @@ def test_device_loop_and_host_loop_agree(small, variant):
     assert d.device_loop == 1 and h.device_loop == 0
     assert d.iters == h.iters and d.status == h.status
     assert torch.equal(d.x, h.x)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("ell_in,trials,ell_out,gamma", [(0, 3, 3, 2.0 * 0.9 ** 2), (1, 2, 3, 2.0 * 0.9 ** 2),
+                                                         (3, 1, 4, 2.0 * 0.9 ** 3)])
+def test_gamma_schedule_hand_worked(dtype, ell_in, trials, ell_out, gamma):
+    # The 2 x 2 image [[0, 1], [1, 5]] has TV(x + gamma v) <= TV(x) exactly for
+    # gamma <= 4/sqrt 6 = 1.633 (worked out in tests/test_oracle_gamma.py), so
+    # with gamma_0 = 2 and a = 0.9 the trials 2, 1.8 are rejected and 1.62 is
+    # accepted.  The device takes one perturbation from a resumed state whose
+    # x_k is that image and whose global index l is ell_in.
+    x = torch.tensor([[0.0, 1.0], [1.0, 5.0]], dtype=dtype, device=DEV)
+    y = torch.ones((2, 3), dtype=dtype, device=DEV)
+    st = dict(k=5, ell=ell_in, gamma0=2.0, gamma_fixed=1, delta=0.0, x=x, x_half=x.clone())
+    r = scg.scg_solve(y, 2, "S-CG-K", 1e-12, resume=st, trace=True, max_iter=1, gamma0=2.0, a=0.9,
+                      max_trials=32)
+    assert r.iters == 1
+    t = r.trace[0]
+    assert int(t[4]) == trials and int(t[5]) == 1 and int(t[6]) == ell_out and r.ell == ell_out
+    assert t[7] == pytest.approx(gamma, rel=1e-12)
+    v = np.array([[np.sqrt(2.0 / 3.0), -1.0 / np.sqrt(6.0)], [-1.0 / np.sqrt(6.0), 0.0]])
+    assert t[3] == pytest.approx(oracle.tv(np.array([[0.0, 1.0], [1.0, 5.0]]) + gamma * v),
+                                 rel=1e-12 if dtype == torch.float64 else 1e-6)

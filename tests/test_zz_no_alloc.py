@@ -4,9 +4,11 @@ Such callers (a plug-in inside a host program whose memory pool owns the
 device, a real-time loop that forbids allocator calls, a fixed memory budget)
 cannot provide the workspace scg_tv needs, so this entry point keeps its
 scratch in a fixed device array inside the library.  The test calls it through
-the C ABI and checks it against scg_tv, within the same tolerance as the other
-TV tests, on two calls in a row (the second call must not see the first one's
-leftovers), and checks that sizes beyond its limit are refused.  This file is
+the C ABI and checks it against scg_tv and against the FP64 oracle's TV,
+within the same tolerances as the other TV tests, on two calls in a row (the
+second call must not see the first one's leftovers); after scg_release() (which
+makes the next call look up the scratch address again) it must still agree;
+and sizes beyond its limit are refused.  This file is
 collected last so that a run stopping at its first failure has run every other
 test already.
 """
@@ -16,6 +18,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_1709_04912_gb300 import inputs, scg
 
 pytestmark = pytest.mark.gpu
@@ -41,8 +44,11 @@ def test_static_scratch_tv_matches_workspace_tv_twice(dtype, n, tol):
     fn = _entry()
     prec = scg.F64 if dtype == torch.float64 else scg.F32
     stream = torch.cuda.current_stream().cuda_stream
-    for call, seed in enumerate((1, 2)):          # two calls in a row, different images
-        x = torch.tensor(_image(n, seed + n), dtype=dtype, device=DEV)
+    for call, seed in enumerate((1, 2, 3)):       # two calls in a row, different images ...
+        if call == 2:
+            scg.release()                         # ... then one after the address was forgotten
+        img = _image(n, seed + n)
+        x = torch.tensor(img, dtype=dtype, device=DEV)
         ref = float(scg.scg_tv(x))
         out = torch.full((), -1.0, dtype=torch.float64, device=DEV)
         rc = fn(n, prec, x.data_ptr(), out.data_ptr(), stream)
@@ -50,6 +56,9 @@ def test_static_scratch_tv_matches_workspace_tv_twice(dtype, n, tol):
         torch.cuda.synchronize()
         got = float(out)
         assert abs(got - ref) <= tol * abs(ref), (call, got, ref)
+        # the oracle's TV of the same stored image
+        orc = oracle.tv(x.double().cpu().numpy())
+        assert abs(got - orc) <= tol * abs(orc), (call, got, orc)
 
 
 def test_static_scratch_refuses_oversize():
