@@ -246,11 +246,28 @@ int scg_tv_grad(int n, int precision, const void* x, void* grad, double* tv_out,
                 void* work, size_t work_bytes, void* stream);
 
 /* out = F^T C F r row by row: the filtering part of the preconditioner
- * z = A^T F^T C F (A x - y) of Sec. 3, c(w) = (|w| + mu)(0.54 + 0.46 cos w) on a
- * unitary DFT of each row zero-padded to P = 2^ceil(log2(2 n_bins)).
- * mu <= 0 selects 2*pi/P. */
+ * z = A^T F^T C F (A x - y) of Sec. 3, c(w) = gain (|w| + mu)(0.54 + 0.46 cos w)
+ * on a unitary DFT of each row zero-padded to P = 2^ceil(log2(2 n_bins)), w the
+ * DFT frequency 2 pi k / P folded into [-pi, pi].  mu <= 0 selects 2*pi/P;
+ * gain > 0.  r, out: n_angles*n_bins (device).  The FFT of a padded row pair is
+ * held in shared memory: n_bins above 8192 (FP32, FP16, BF16) or 4096 (FP64)
+ * returns SCG_ERR_UNSUPPORTED (the same limit applies to the preconditioned
+ * solvers, and to scg_fbp). */
 int scg_filter(const scg_geometry* g, int precision, double mu, double gain,
                const void* r, void* out, void* work, size_t work_bytes, void* stream);
+
+/* x = filtered backprojection of the sinogram y: the reconstruction Sec. 4
+ * shows as its visual reference (the method of Herman's textbook, Ch. 8, with
+ * the Hamming-windowed ramp Sec. 3 names).  The parallel-beam inversion
+ * x(s) = int_0^pi (p_theta * q)(s) d theta with the ramp q = |nu| (nu in cycles
+ * per bin width), discretised: each row is filtered as scg_filter does with
+ * mu = 0 and gain 1/(2 n_angles) (= the angle step pi/n_angles over the 2 pi
+ * between w and nu), and x = A^T of the filtered rows (A^T spreads each
+ * angle's value over a pixel with weights adding up to the pixel area).
+ * y: n_angles*n_bins, x: N*N (device); workspace scg_op_workspace_bytes;
+ * stream-ordered and asynchronous; n_bins limit as scg_filter. */
+int scg_fbp(const scg_geometry* g, int precision, const void* y, void* x,
+            void* work, size_t work_bytes, void* stream);
 
 /* Bytes of device workspace for scg_solve with this geometry and variant. */
 size_t scg_solve_workspace_bytes(const scg_geometry* g, int variant, int precision);

@@ -138,6 +138,7 @@ def lib():
         L.orc_filter_factor.argtypes = [d, d]
         L.orc_filter_factor.restype = d
         L.orc_filter_rows.argtypes = [i, i, d, d, dp, dp]
+        L.orc_fbp.argtypes = [i, i, i, dp, dp]
         L.orc_norm_A.argtypes = [i, i, i, i]
         L.orc_norm_A.restype = d
         L.orc_perturb_gamma.argtypes = [i, dp, d, d, i, ctypes.POINTER(ctypes.c_longlong), dp, dp, ip]
@@ -255,6 +256,16 @@ def filter_rows(r: np.ndarray, mu: float = 0.0, gain: float = 1.0) -> np.ndarray
     out = np.zeros_like(r)
     lib().orc_filter_rows(r.shape[0], r.shape[1], mu, gain, _dp(r), _dp(out))
     return out
+
+
+def fbp(y: np.ndarray, n: int) -> np.ndarray:
+    """Filtered backprojection: A^T of the ramp-filtered (Hamming-windowed) rows,
+    gain 1/(2 n_angles)."""
+    y = _f64(y)
+    na, nb = y.shape
+    x = np.zeros((n, n))
+    lib().orc_fbp(n, na, nb, _dp(y), _dp(x))
+    return x
 
 
 def norm_A(n: int, n_angles: int, n_bins: int, iters: int = 50) -> float:

@@ -307,10 +307,20 @@ double orc_filter_factor(double omega, double mu)
     return (fabs(omega) + mu) * (0.54 + 0.46 * cos(omega));
 }
 
+/* The filtering of each row with the factors c(w) of the given mu, exactly
+ * as written (mu = 0 allowed). */
+static void filter_rows_mu(int na, int nb, double mu, double gain, const double* r, double* out);
+
 void orc_filter_rows(int na, int nb, double mu, double gain, const double* r, double* out)
 {
     int P = orc_filter_length(nb);
     if (!(mu > 0.0)) mu = 2.0 * ORC_PI / (double)P;
+    filter_rows_mu(na, nb, mu, gain, r, out);
+}
+
+static void filter_rows_mu(int na, int nb, double mu, double gain, const double* r, double* out)
+{
+    int P = orc_filter_length(nb);
     double* cw = (double*)malloc(sizeof(double) * (size_t)P);
     double* sw = (double*)malloc(sizeof(double) * (size_t)P);
     double* cf = (double*)malloc(sizeof(double) * (size_t)P);
@@ -379,6 +389,31 @@ double orc_norm_A(int n, int na, int nb, int iters)
     free(w);
     free(q);
     return sqrt(lam);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Filtered backprojection (Sec. 4 shows an FBP reconstruction as the visual  */
+/* reference; it names the method of Herman's textbook, Ch. 8, and Sec. 3    */
+/* says the preconditioner's Hamming-windowed factors are those commonly     */
+/* used there).  Parallel-beam inversion: x(s) = int_0^pi (p_theta * q)(s)   */
+/* dtheta with q the ramp |nu| (nu in cycles per bin width).  Discretised:   */
+/* each row is filtered by the padded unitary DFT with the factors           */
+/*   |nu| (0.54 + 0.46 cos w) = |w|/(2 pi) (0.54 + 0.46 cos w),              */
+/* w = 2 pi nu in [-pi, pi]; the angle integral becomes (pi / n_angles)      */
+/* times the sum over angles, and that sum at each pixel is A^T (whose       */
+/* weights of one pixel and angle add up to the pixel area 1).  In terms of  */
+/* the Sec. 3 factors c(w) = (|w| + mu)(0.54 + 0.46 cos w) with mu = 0 this  */
+/* is x = A^T F^T (g C) F y with gain g = (pi / n_angles)/(2 pi)             */
+/* = 1 / (2 n_angles).                                                       */
+/* Pinned by: a numpy FFT route for the filtering, the reconstruction of a   */
+/* uniform disk.                                                             */
+/* ------------------------------------------------------------------------ */
+void orc_fbp(int n, int na, int nb, const double* y, double* x)
+{
+    double* q = (double*)malloc(sizeof(double) * (size_t)na * nb);
+    filter_rows_mu(na, nb, 0.0, 1.0 / (2.0 * (double)na), y, q);
+    orc_backproject(n, na, nb, q, x);
+    free(q);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -128,6 +128,8 @@ void   orc_filter_rows(int na, int nb, double mu, double gain, const double* r, 
 
 double orc_norm_A(int n, int na, int nb, int iters);
 
+void orc_fbp(int n, int na, int nb, const double* y, double* x);
+
 int orc_perturb_gamma(int n, const double* x, double gamma0, double a, int max_trials,
                       long long* ell, double* x_half, double* gamma_out, int* trials_out);
 

@@ -24,11 +24,7 @@ inline bool valid_geometry(const scg_geometry* g) {
            g->n_bins >= 1 && g->n_bins <= 16384;
 }
 
-inline int filter_length(int nb) {
-    int P = 1;
-    while (P < 2 * nb) P *= 2;
-    return P;
-}
+inline int filter_length(int nb) { return filter_length_of(nb); }
 
 inline int family_of(int v) {
     if (v == SCG_CG || v == SCG_PCG) return FAM_CG;
@@ -37,6 +33,30 @@ inline int family_of(int v) {
 }
 
 inline bool uses_filter(int v) { return v == SCG_PCG || v == SCG_S_PCG || v == SCG_S_PCG_K; }
+
+// The row filter holds a whole padded row pair's FFT in shared memory.
+inline bool filter_fits(int nb, int precision) {
+    return (precision == SCG_F64 ? filter_smem_bytes<double>(nb) : filter_smem_bytes<float>(nb)) <= kFilterSmemMax;
+}
+
+// Filter tables of one geometry (Sec. 3, Eq. filter_factors_pre): P factors
+// gain c(w_k) / P with c(w) = (|w| + mu)(0.54 + 0.46 cos w), w_k = 2 pi k / P
+// folded into [-pi, pi] (the 1/P completes the unitary transform pair), then
+// the twiddles exp(-2 pi i j / P), j < P/2, as (cos, -sin) pairs; all in FP64,
+// rounded once to the arithmetic type.
+template <typename C>
+void fill_filter_tables(std::vector<C>& out, int P, double mu, double gain) {
+    out.assign(2 * (size_t)P, C(0));
+    for (int k = 0; k < P; ++k) {
+        const double w = (k <= P / 2) ? 2.0 * M_PI * k / P : 2.0 * M_PI * (k - P) / P;
+        out[k] = (C)(gain * (fabs(w) + mu) * (0.54 + 0.46 * cos(w)) / (double)P);
+    }
+    for (int j = 0; j < P / 2; ++j) {
+        const double a = 2.0 * M_PI * (double)j / (double)P;
+        out[P + 2 * j] = (C)cos(a);
+        out[P + 2 * j + 1] = (C)(-sin(a));
+    }
+}
 
 inline bool valid_prec(int p) { return p == SCG_F32 || p == SCG_F64 || p == SCG_F16 || p == SCG_BF16; }
 // bytes of one stored element, and of one arithmetic value
@@ -113,8 +133,8 @@ inline Plan make_plan(const scg_geometry& g, int variant, int precision, int kin
     p.tiles_x = (N + kTileW - 1) / kTileW;
     p.cnt_ray = na * p.ray_blocks;
     p.cnt_img = ((N + kTileH - 1) / kTileH) * p.tiles_x;
-    p.filt_blocks = (nb + kFilterBlock - 1) / kFilterBlock;
-    p.cnt_row = na * p.filt_blocks;
+    p.filt_blocks = 1;                      // one item per pair of rows
+    p.cnt_row = (na + 1) / 2;
     // partials are sized for the largest item count of any projector shape
     const int max_proj = max_proj_items(na, nb);
     set_proj_shape(p, na, nb, kProjShiftDefault);
@@ -127,7 +147,7 @@ inline Plan make_plan(const scg_geometry& g, int variant, int precision, int kin
     p.state = take(sizeof(DevState));
     p.prob = take(sizeof(Prob<double>));
     p.ang = take(sizeof(Angle<double>) * na);
-    p.taps = take(csize * (2 * (size_t)nb - 1));
+    p.taps = take(csize * 2 * (size_t)p.P);
     int maxcnt = p.cnt_ray > p.cnt_img ? p.cnt_ray : p.cnt_img;
     if (p.cnt_row > maxcnt) maxcnt = p.cnt_row;
     if (max_proj > maxcnt) maxcnt = max_proj;
@@ -286,7 +306,7 @@ struct Runner {
     void tvgrad(int src, int fuse, int wg, int step) { ++launches; launch_tvgrad<T>(d, i_img, g_img, src, fuse, wg, step, s); }
     void trial(int ncand) { ++launches; launch_trial<T>(d, i_bp, g_bp, ncand, s); }
     void axpy(int step) { ++launches; launch_sino_axpy<T>(d, i_ray, g_ray, step, s); }
-    void filter(int src, int dst) { ++launches; launch_filter<T>(d, i_row, g_row, nb, src, dst, 0, s); }
+    void filter(int src, int dst) { ++launches; launch_filter<T>(d, i_row, g_row, nb, src, dst, FILT_VIEW, s); }
 };
 
 struct Program {

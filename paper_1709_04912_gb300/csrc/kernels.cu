@@ -11,9 +11,8 @@
 //   k_trial        TV of several trial points x + gamma_l v in one pass
 //                  (Eq. gamma_sequence, acceptance TV(z) <= TV(x))
 //   k_sino_axpy    recursive residual r' = r + alpha A p (CG/PCG)
-//   k_filter       row filter of the preconditioner (Sec. 3) as a Toeplitz
-//                  product with taps h = IDFT(c)
-//   k_taps         the taps, in FP64
+//   k_filter       row filter of the preconditioner (Sec. 3): radix-2 FFT of
+//                  two rows at once in shared memory, factors, inverse FFT
 //   k_sino_pairs   a caller's plain sinogram into the pair layout
 // No kernel uses atomics on data; reductions are deterministic.
 #include <cstring>
@@ -982,66 +981,110 @@ k_sino_pairs(const Prob<T>* __restrict__ probs, int dst) {
 }
 
 // ---------------------------------------------------------------------------
-// Row filter: w[a,b] = sum_b' h[b - b'] r[a,b'], the zero-padded circular
-// convolution of Sec. 3's filter restricted to the row (P >= 2 nb, so nothing
-// wraps).  One block per (row, 128 outputs); the row and the taps are staged
-// in shared memory.
+// Row filter of Sec. 3 (Filters for Preconditioning): each sinogram row r is
+// zero-padded to P (a power of two >= 2 n_bins, so the circular product does
+// not wrap), transformed by a DFT, multiplied by the real factors
+// fac[k] = gain c(w_k) / P (c(w) = (|w| + mu)(0.54 + 0.46 cos w), w_k = 2 pi
+// k / P folded into [-pi, pi]; the 1/P is the unitary pair F^T ... F), and
+// transformed back; the first n_bins outputs are kept.
+//
+// One block per pair of rows: rows 2u and 2u+1 are the real and imaginary
+// parts of one complex sequence z = a + i b.  The factors are real and even
+// (fac[k] = fac[P-k]), so filtering z filters a and b separately: the result
+// is filter(a) + i filter(b), one complex FFT pair for two rows.  The FFT is
+// radix-2 in shared memory: the forward transform decimates in time (input
+// loaded in bit-reversed order, output in natural order), the multiplication
+// by fac is done in place, and the inverse transform decimates in frequency
+// with conjugate twiddles (natural order in, bit-reversed order out), so no
+// reordering pass is needed: rows are read and written through the bit
+// reversal of their index.  Twiddles tw[j] = exp(-2 pi i j / P), j < P/2, and
+// the factors come from a table the host fills in FP64 once per problem.
+//
+// mode: FILT_VIEW  pair view src -> pair view dst (the solvers' sinograms)
+//       FILT_PLAIN the caller's plain rows user_in -> user_out
+//       FILT_FBP   the caller's plain rows user_in -> pair view dst, scaled by
+//                  the angle's chord factor like every sinogram view
 template <typename T>
-__global__ void __launch_bounds__(kFilterBlock)
-k_filter(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int src, int dst,
-         int plain) {
+__global__ void __launch_bounds__(kFilterThreads)
+k_filter(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int src, int dst, int mode) {
+    using C = typename Tr<T>::C;
+    using C2 = typename Vec2<C>::type;
     const Item it = decode_item(probs, items, 2);
     const Prob<T>& P = probs[it.prob];
     if (P.st->done) return;
-    using C = typename Tr<T>::C;
-    extern __shared__ unsigned char smem_raw[];
-    C* row = reinterpret_cast<C*>(smem_raw);
-    C* taps = row + P.nb;
-    const int nb = P.nb, a = it.u;
-    if (plain) {
-        const typename Tr<T>::S* R = P.user_in + (size_t)a * nb;
-        for (int q = threadIdx.x; q < nb; q += blockDim.x) row[q] = to_c(R[q]);
-    } else {
-        const typename Tr<T>::S2* R = P.sino[src] + (size_t)a * P.SB + kSPad;
-        for (int q = threadIdx.x; q < nb; q += blockDim.x) row[q] = to_c(R[q].x);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C2* z = reinterpret_cast<C2*>(smem_raw);
+    const int nb = P.nb, na = P.na, L = P.P;
+    const int lg = 31 - __clz(L);
+    const int ra = 2 * it.u, rb = ra + 1;                 // the block's two rows (rb may be past the end)
+    const bool has_b = rb < na;
+    const C* fac = P.taps;                                // [L] factors
+    const C2* tw = reinterpret_cast<const C2*>(P.taps + L);   // [L/2] twiddles
+    for (int q = threadIdx.x; q < L; q += blockDim.x) {
+        C va = C(0), vb = C(0);
+        if (q < nb) {
+            if (mode == FILT_VIEW) {
+                const typename Tr<T>::S2* R = P.sino[src] + kSPad;
+                va = to_c(R[(size_t)ra * P.SB + q].x);
+                if (has_b) vb = to_c(R[(size_t)rb * P.SB + q].x);
+            } else {
+                va = to_c(P.user_in[(size_t)ra * nb + q]);
+                if (has_b) vb = to_c(P.user_in[(size_t)rb * nb + q]);
+            }
+        }
+        C2 v;
+        v.x = va;
+        v.y = vb;
+        z[__brev((unsigned)q) >> (32 - lg)] = v;
     }
-    for (int q = threadIdx.x; q < 2 * nb - 1; q += blockDim.x) taps[q] = P.taps[q];
     __syncthreads();
-    const int b = it.v * kFilterBlock + threadIdx.x;
-    if (b >= nb) return;
-    // taps[nb - 1 + k] = h[k]
-    const C* tb = taps + (nb - 1) + b;
-    C acc0 = C(0), acc1 = C(0);
-    int q = 0;
-    for (; q + 1 < nb; q += 2) {
-        acc0 = fma(tb[-q], row[q], acc0);
-        acc1 = fma(tb[-q - 1], row[q + 1], acc1);
+    // forward: decimation in time, stages of length 2, 4, ..., L
+    for (int s = 1; s <= lg; ++s) {
+        const int half = 1 << (s - 1);
+        for (int t = threadIdx.x; t < (L >> 1); t += blockDim.x) {
+            const int pos = t & (half - 1);
+            const int i0 = ((t >> (s - 1)) << s) + pos, i1 = i0 + half;
+            const C2 w = tw[pos << (lg - s)];
+            const C2 u = z[i0], v = z[i1];
+            const C vr = v.x * w.x - v.y * w.y, vi = v.x * w.y + v.y * w.x;
+            z[i0] = C2{u.x + vr, u.y + vi};
+            z[i1] = C2{u.x - vr, u.y - vi};
+        }
+        __syncthreads();
     }
-    if (q < nb) acc0 = fma(tb[-q], row[q], acc0);
-    const C out = acc0 + acc1;
-    if (plain) P.user_out[(size_t)a * nb + b] = to_s<typename Tr<T>::S>(out);
-    else store_pair<T>(P.sino[dst] + (size_t)a * P.SB + kSPad, b, out);
-}
-
-// Taps h[k] = gain/P * sum_m c(w_m) cos(2 pi m k / P), k = 0..nb-1, stored
-// symmetrically; one block per k, FP64.
-template <typename T>
-__global__ void k_taps(T* taps, int nb, int P, double mu, double gain) {
-    const int k = blockIdx.x;
-    double acc = 0.0;
-    for (int m = threadIdx.x; m < P; m += blockDim.x) {
-        const double w = (m <= P / 2) ? 2.0 * M_PI * m / P : 2.0 * M_PI * (m - P) / P;
-        const double c = (fabs(w) + mu) * (0.54 + 0.46 * cos(w));
-        const long long mk = ((long long)m * k) % P;
-        acc += c * cos(2.0 * M_PI * (double)mk / (double)P);
+    for (int q = threadIdx.x; q < L; q += blockDim.x) {
+        const C f = fac[q];
+        const C2 v = z[q];
+        z[q] = C2{v.x * f, v.y * f};
     }
-    __shared__ double red[32];
-    double v[1] = {acc};
-    block_sum<double, 1>(v, red);
-    if (threadIdx.x == 0) {
-        const T h = (T)(gain * v[0] / (double)P);
-        taps[nb - 1 + k] = h;
-        taps[nb - 1 - k] = h;
+    __syncthreads();
+    // inverse: decimation in frequency with conjugate twiddles, stages L ... 2
+    for (int s = lg; s >= 1; --s) {
+        const int half = 1 << (s - 1);
+        for (int t = threadIdx.x; t < (L >> 1); t += blockDim.x) {
+            const int pos = t & (half - 1);
+            const int i0 = ((t >> (s - 1)) << s) + pos, i1 = i0 + half;
+            const C2 w = tw[pos << (lg - s)];
+            const C2 u = z[i0], v = z[i1];
+            const C dr = u.x - v.x, di = u.y - v.y;
+            z[i0] = C2{u.x + v.x, u.y + v.y};
+            z[i1] = C2{dr * w.x + di * w.y, di * w.x - dr * w.y};   // (u - v) conj(w)
+        }
+        __syncthreads();
+    }
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        const C2 v = z[__brev((unsigned)b) >> (32 - lg)];
+        if (mode == FILT_PLAIN) {
+            P.user_out[(size_t)ra * nb + b] = to_s<typename Tr<T>::S>(v.x);
+            if (has_b) P.user_out[(size_t)rb * nb + b] = to_s<typename Tr<T>::S>(v.y);
+        } else {
+            const C sa = mode == FILT_FBP ? P.ang[ra].inv_m : C(1);
+            store_pair<T>(P.sino[dst] + (size_t)ra * P.SB + kSPad, b, v.x * sa);
+            if (has_b) {
+                const C sb = mode == FILT_FBP ? P.ang[rb].inv_m : C(1);
+                store_pair<T>(P.sino[dst] + (size_t)rb * P.SB + kSPad, b, v.y * sb);
+            }
+        }
     }
 }
 
@@ -1184,19 +1227,15 @@ void launch_sino_axpy(const Prob<T>* d, const Item* items, int grid, int step, c
 }
 template <typename T>
 cudaError_t launch_filter(const Prob<T>* d, const Item* items, int grid, int max_nb, int src,
-                          int dst, int plain, cudaStream_t s) {
-    size_t smem = (size_t)(3 * max_nb) * sizeof(typename Tr<T>::C);
+                          int dst, int mode, cudaStream_t s) {
+    const size_t smem = filter_smem_bytes<typename Tr<T>::C>(max_nb);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_filter<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_filter<T><<<grid, kFilterBlock, smem, s>>>(d, items, src, dst, plain);
+    k_filter<T><<<grid, kFilterThreads, smem, s>>>(d, items, src, dst, mode);
     return cudaSuccess;
-}
-template <typename T>
-void launch_taps(T* taps, int nb, int P, double mu, double gain, cudaStream_t s) {
-    k_taps<T><<<nb, 256, 0, s>>>(taps, nb, P, mu, gain);
 }
 
 #define SCG_INSTANTIATE(T)                                                                        \
@@ -1222,7 +1261,5 @@ SCG_INSTANTIATE(float)
 SCG_INSTANTIATE(double)
 SCG_INSTANTIATE(__half)
 SCG_INSTANTIATE(__nv_bfloat16)
-template void launch_taps<float>(float*, int, int, double, double, cudaStream_t);
-template void launch_taps<double>(double*, int, int, double, double, cudaStream_t);
 
 }  // namespace scg

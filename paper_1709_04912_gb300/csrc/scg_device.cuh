@@ -57,7 +57,16 @@ constexpr int kRayBlock = 128;   // rays per sinogram-row work item (axpy, pairs
 constexpr int kProjLog2 = 8;     // projector block: 2^8 threads = adjacent angles x consecutive
 constexpr int kProjThreads = 1 << kProjLog2;   // rays (2^proj_shift rays of each angle; they read
 constexpr int kProjShiftDefault = 6;           // nearly the same image spans): 4 x 64 by default
-constexpr int kFilterBlock = 128;// output bins per filter work item
+constexpr int kFilterThreads = 256; // filter block: two sinogram rows, one complex FFT pair
+// filter length P (a power of two >= 2 n_bins) and the shared memory of its FFT
+__host__ __device__ constexpr int filter_length_of(int nb) {
+    int P = 1;
+    while (P < 2 * nb) P *= 2;
+    return P;
+}
+template <typename C>
+__host__ __device__ constexpr size_t filter_smem_bytes(int nb) { return 2 * sizeof(C) * (size_t)filter_length_of(nb); }
+constexpr size_t kFilterSmemMax = 160 * 1024;   // largest FFT held in shared memory (FP32: n_bins <= 8192, FP64: 4096)
 
 enum ImgBuf { IB_X = 0, IB_XH, IB_P, IB_H, IB_G, IB_Z, IB_TVG, IB_AUX, IB_COUNT };
 enum SinoBuf { SB_R = 0, SB_Q, SB_W, SB_COUNT };
@@ -201,7 +210,7 @@ struct Prob {
     int cnt_bp;                      // backprojector tiles (32 x kBpTileH32 or kBpTileH64)
     int tiles_x;            // image tiles per row of tiles
     int ray_blocks;         // projector items per angle
-    int filt_blocks;        // filter items per row
+    int filt_blocks;        // filter items per row pair (1)
     int P;                  // filter length (power of two >= 2 nb)
     calc_t off_n, off_b;    // (N-1)/2, (nb-1)/2
     calc_t y_scale;         // scale c of the solved system c A x ~ c y (a power of two; see Angle.inv_m)
@@ -213,7 +222,7 @@ struct Prob {
     pair_t* view_cm;
     const elem_t* user_in;  // caller's plain sinogram (operator entry points)
     elem_t* user_out;
-    const calc_t* taps;     // Toeplitz filter taps h[-(nb-1) .. nb-1]
+    const calc_t* taps;     // filter tables: P factors gain c(w_k)/P, then P/2 twiddles exp(-2 pi i j/P)
     double* partials;
     unsigned* counter;
     DevState* st;

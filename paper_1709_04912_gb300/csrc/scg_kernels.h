@@ -6,6 +6,7 @@
 namespace scg {
 
 enum ProjMode { PROJ_PLAIN = 0, PROJ_RESIDUAL = 1, PROJ_PLAIN_OUT = 2 };
+enum FiltMode { FILT_VIEW = 0, FILT_PLAIN = 1, FILT_FBP = 2 };
 
 enum VecOp {
     VEC_INIT = 0,          // X = XH = x0 (AUX or zeros); views
@@ -34,11 +35,10 @@ template <typename T>
 void launch_trial(const Prob<T>* d, const Item* items, int grid, int ncand, cudaStream_t s);
 template <typename T>
 void launch_sino_axpy(const Prob<T>* d, const Item* items, int grid, int step, cudaStream_t s);
+// mode: FILT_VIEW / FILT_PLAIN / FILT_FBP (see k_filter)
 template <typename T>
 cudaError_t launch_filter(const Prob<T>* d, const Item* items, int grid, int max_nb, int src,
-                          int dst, int plain, cudaStream_t s);
-template <typename T>
-void launch_taps(T* taps, int nb, int P, double mu, double gain, cudaStream_t s);
+                          int dst, int mode, cudaStream_t s);
 template <typename T>
 void launch_sino_pairs(const Prob<T>* d, int grid, int dst, cudaStream_t s);
 void launch_loop_cond(DevState* st, cudaGraphConditionalHandle h, cudaStream_t s);

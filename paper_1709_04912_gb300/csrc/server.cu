@@ -177,6 +177,10 @@ public:
         Request* r = new Request();
         r->p = *req;
         r->tag = tag;
+        if (uses_filter(cfg_.variant) && !filter_fits(req->geometry.n_bins, prec_of<T>())) {
+            delete r;
+            return SCG_ERR_UNSUPPORTED;
+        }
         r->plan = make_plan(req->geometry, cfg_.variant, prec_of<T>(), PLAN_SOLVE);
         r->scale = system_scale(req->geometry, prec_of<T>());
         r->off = 0;
@@ -374,8 +378,9 @@ private:
             SCK(upload(rb + pl.ang, ang.data(), sizeof(Angle<C>) * ang.size()));
             if (uses_filter(cfg_.variant)) {
                 const double mu = cfg_.params.mu > 0.0 ? cfg_.params.mu : 2.0 * M_PI / pl.P;
-                launch_taps<C>(reinterpret_cast<C*>(rb + pl.taps), r->p.geometry.n_bins, pl.P, mu,
-                               cfg_.params.filter_gain, stream_);
+                std::vector<C> ftab;
+                fill_filter_tables<C>(ftab, pl.P, mu, cfg_.params.filter_gain);
+                SCK(upload(rb + pl.taps, ftab.data(), sizeof(C) * ftab.size()));
             }
             SCK(upload(probs() + slot, &P, sizeof(P)));
             {

@@ -87,6 +87,7 @@ int solve_impl(const scg_geometry* g, int variant, int precision, const scg_para
     using C = typename Tr<T>::C;
     Plan pl = make_plan(*g, variant, prec_of<T>(), PLAN_SOLVE);
     if (work_bytes < pl.total || ((uintptr_t)work & 15u)) return SCG_ERR_WORKSPACE;
+    if (uses_filter(variant) && !filter_fits(g->n_bins, prec_of<T>())) return SCG_ERR_UNSUPPORTED;
     unsigned char* base = (unsigned char*)work;
     const int N = g->n, fam = family_of(variant);
     const double scale = system_scale(*g, prec_of<T>()), s2 = scale * scale;
@@ -123,11 +124,11 @@ int solve_impl(const scg_geometry* g, int variant, int precision, const scg_para
     CK(cudaMemcpyAsync(base + pl.state, &st, sizeof(st), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(base + pl.prob, &P, sizeof(P), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(base + pl.ang, ang.data(), sizeof(Angle<C>) * ang.size(), cudaMemcpyHostToDevice, s));
+    std::vector<C> ftab;
     if (uses_filter(variant)) {
         const double mu = prm->mu > 0.0 ? prm->mu : 2.0 * M_PI / pl.P;
-        launch_taps<C>(reinterpret_cast<C*>(base + pl.taps), g->n_bins, pl.P, mu, prm->filter_gain, s);
-        size_t smem = (size_t)(3 * g->n_bins) * sizeof(C);
-        if (smem > 227 * 1024) return SCG_ERR_UNSUPPORTED;
+        fill_filter_tables<C>(ftab, pl.P, mu, prm->filter_gain);
+        CK(cudaMemcpyAsync(base + pl.taps, ftab.data(), sizeof(C) * ftab.size(), cudaMemcpyHostToDevice, s));
     }
     {
         const int rc = tune_proj_shape<T>(P, pl, reinterpret_cast<Prob<T>*>(base + pl.prob), *g, s);
@@ -433,16 +434,46 @@ int filter_impl(const scg_geometry& g, double mu, double gain, const void* r, vo
     if (rc) return rc;
     using E = typename Tr<T>::S;
     using C = typename Tr<T>::C;
-    if ((size_t)(3 * g.n_bins) * sizeof(C) > 227 * 1024) return SCG_ERR_UNSUPPORTED;
     unsigned char* base = (unsigned char*)work;
     P.user_in = (const E*)r;
     P.user_out = (E*)out;
     rc = upload_prob<T>(P, pl, work, s);
     if (rc) return rc;
     const double mu_eff = mu > 0.0 ? mu : 2.0 * M_PI / pl.P;
-    launch_taps<C>(reinterpret_cast<C*>(base + pl.taps), g.n_bins, pl.P, mu_eff, gain, s);
+    std::vector<C> ftab;
+    fill_filter_tables<C>(ftab, pl.P, mu_eff, gain);
+    CK(cudaMemcpyAsync(base + pl.taps, ftab.data(), sizeof(C) * ftab.size(), cudaMemcpyHostToDevice, s));
     const Prob<T>* d = reinterpret_cast<const Prob<T>*>(base + pl.prob);
-    CK(launch_filter<T>(d, nullptr, pl.cnt_row, g.n_bins, SB_R, SB_W, 1, s));
+    CK(launch_filter<T>(d, nullptr, pl.cnt_row, g.n_bins, SB_R, SB_W, FILT_PLAIN, s));
+    CK(cudaGetLastError());
+    return SCG_OK;
+}
+
+// Filtered backprojection: the rows filtered with the Hamming-windowed ramp
+// (mu = 0, gain 1/(2 n_angles): the angle step pi/n_angles over the 2 pi that
+// turns the radian factors into the ramp |nu|), written into the pair view the
+// gather reads, then A^T.
+template <typename T>
+int fbp_impl(const scg_geometry& g, const void* y, void* x, void* work, size_t wb, cudaStream_t s) {
+    if (!filter_fits(g.n_bins, prec_of<T>())) return SCG_ERR_UNSUPPORTED;
+    Plan pl;
+    Prob<T> P;
+    int rc = op_setup<T>(g, work, wb, s, &pl, &P);
+    if (rc) return rc;
+    unsigned char* base = (unsigned char*)work;
+    using E = typename Tr<T>::S;
+    using C = typename Tr<T>::C;
+    CK(cudaMemsetAsync(base + pl.sino[SB_R], 0, 2 * sizeof(E) * (size_t)g.n_angles * pl.SB, s));
+    P.img[IB_AUX] = (E*)x;
+    P.user_in = (const E*)y;
+    rc = upload_prob<T>(P, pl, work, s);
+    if (rc) return rc;
+    std::vector<C> ftab;
+    fill_filter_tables<C>(ftab, pl.P, 0.0, 1.0 / (2.0 * (double)g.n_angles));
+    CK(cudaMemcpyAsync(base + pl.taps, ftab.data(), sizeof(C) * ftab.size(), cudaMemcpyHostToDevice, s));
+    const Prob<T>* d = reinterpret_cast<const Prob<T>*>(base + pl.prob);
+    CK(launch_filter<T>(d, nullptr, pl.cnt_row, g.n_bins, SB_R, SB_R, FILT_FBP, s));
+    launch_backproject<T>(d, nullptr, pl.cnt_bp, 1, SB_R, SB_R, IB_AUX, IB_AUX, FIN_NONE, s);
     CK(cudaGetLastError());
     return SCG_OK;
 }
@@ -580,7 +611,7 @@ int batch_impl(const scg_problem* pr, int count, int variant, int precision, con
     using C = typename Tr<T>::C;
     BatchPlan bp = make_batch_plan(pr, count, variant, prec_of<T>());
     if (work_bytes < bp.total || ((uintptr_t)work & 15u)) return SCG_ERR_WORKSPACE;
-    if (uses_filter(variant) && (size_t)(3 * bp.nb_cap) * sizeof(C) > 227 * 1024) return SCG_ERR_UNSUPPORTED;
+    if (uses_filter(variant) && !filter_fits(bp.nb_cap, prec_of<T>())) return SCG_ERR_UNSUPPORTED;
     unsigned char* base = (unsigned char*)work;
     const int fam = family_of(variant);
     int dev = 0;
@@ -615,7 +646,9 @@ int batch_impl(const scg_problem* pr, int count, int variant, int precision, con
         CK(cudaMemcpyAsync(rb + pl.ang, ang.data(), sizeof(Angle<C>) * ang.size(), cudaMemcpyHostToDevice, s));
         if (uses_filter(variant)) {
             const double mu = prm->mu > 0.0 ? prm->mu : 2.0 * M_PI / pl.P;
-            launch_taps<C>(reinterpret_cast<C*>(rb + pl.taps), pr[i].geometry.n_bins, pl.P, mu, prm->filter_gain, s);
+            std::vector<C> ftab;
+            fill_filter_tables<C>(ftab, pl.P, mu, prm->filter_gain);
+            CK(cudaMemcpyAsync(rb + pl.taps, ftab.data(), sizeof(C) * ftab.size(), cudaMemcpyHostToDevice, s));
         }
         // the problem's own slot serves the shape tuner (a single-problem launch)
         const int rc = tune_proj_shape<T>(P, pl, slots + i, pr[i].geometry, s);
@@ -854,10 +887,18 @@ int scg_tv_grad(int n, int precision, const void* x, void* grad, double* tv_out,
 
 int scg_filter(const scg_geometry* g, int precision, double mu, double gain, const void* r, void* out,
                void* work, size_t work_bytes, void* stream) {
-    if (!valid_geometry(g) || !r || !out || !work) return SCG_ERR_INVALID;
-    if (!valid_prec(precision)) return SCG_ERR_UNSUPPORTED;
+    if (!valid_geometry(g) || !r || !out || !work || !(gain > 0.0) || !isfinite(mu)) return SCG_ERR_INVALID;
+    if (!valid_prec(precision) || !filter_fits(g->n_bins, precision)) return SCG_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     return SCG_DISPATCH(precision, filter_impl, *g, mu, gain, r, out, work, work_bytes, s);
+}
+
+int scg_fbp(const scg_geometry* g, int precision, const void* y, void* x, void* work, size_t work_bytes,
+            void* stream) {
+    if (!valid_geometry(g) || !y || !x || !work) return SCG_ERR_INVALID;
+    if (!valid_prec(precision)) return SCG_ERR_UNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    return SCG_DISPATCH(precision, fbp_impl, *g, y, x, work, work_bytes, s);
 }
 
 int scg_solve(const scg_geometry* g, int variant, int precision, const scg_params* prm, double eps,

@@ -100,6 +100,7 @@ def load(build_if_needed: bool = True):
     L.scg_tv.argtypes = [i, i, vp, vp, vp, sz, vp]
     L.scg_tv_grad.argtypes = [i, i, vp, vp, vp, vp, sz, vp]
     L.scg_filter.argtypes = [gp, i, d, d, vp, vp, vp, sz, vp]
+    L.scg_fbp.argtypes = [gp, i, vp, vp, vp, sz, vp]
     L.scg_solve.argtypes = [gp, i, i, ctypes.POINTER(Params), d, vp, vp, vp, vp, sz,
                             ctypes.POINTER(Result), ctypes.POINTER(ctypes.c_double), i,
                             ctypes.POINTER(State), ctypes.POINTER(State), vp]
@@ -123,7 +124,7 @@ def load(build_if_needed: bool = True):
     L.scg_server_step.argtypes = [vp, vp, ctypes.POINTER(Completion), i, ctypes.POINTER(i)]
     L.scg_server_pending.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i)]
     L.scg_server_destroy.argtypes = [vp]
-    for name in ("scg_project", "scg_backproject", "scg_tv", "scg_tv_grad", "scg_filter", "scg_solve",
+    for name in ("scg_project", "scg_backproject", "scg_tv", "scg_tv_grad", "scg_filter", "scg_fbp", "scg_solve",
                  "scg_solve_batch", "scg_server_create", "scg_server_submit", "scg_server_step",
                  "scg_server_pending", "scg_server_destroy"):
         getattr(L, name).restype = i
@@ -257,6 +258,21 @@ def scg_filter(r: torch.Tensor, mu: float = 0.0, gain: float = 1.0) -> torch.Ten
     rc = load().scg_filter(ctypes.byref(g), prec, float(mu), float(gain), _dev_ptr(r, "r"),
                            out.data_ptr(), w.data_ptr(), w.numel(), _stream(r.device))
     _check(rc, "scg_filter")
+    return out
+
+
+def scg_fbp(y: torch.Tensor, n: int, out: torch.Tensor | None = None) -> torch.Tensor:
+    """Filtered backprojection of the n_angles x n_bins sinogram ``y`` (N x N image)."""
+    na, nbins = y.shape
+    prec = _prec(y)
+    if out is None:
+        out = torch.empty((n, n), dtype=y.dtype, device=y.device)
+    g = geometry(n, na, nbins)
+    nb = load().scg_op_workspace_bytes(ctypes.byref(g), prec)
+    w = workspace(nb, y.device, "op")
+    rc = load().scg_fbp(ctypes.byref(g), prec, _dev_ptr(y, "y"), _dev_ptr(out, "x"), w.data_ptr(), w.numel(),
+                        _stream(y.device))
+    _check(rc, "scg_fbp")
     return out
 
 

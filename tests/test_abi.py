@@ -78,6 +78,25 @@ def test_invalid_arguments_rejected_before_any_launch(lib):
                          1 << 30, ctypes.byref(res), None, 0, None, None, None) == -1
 
 
+def test_filter_length_limit_rejected_before_any_launch(lib):
+    # the row filter holds a padded row pair's FFT in shared memory: n_bins above
+    # 8192 (FP32 arithmetic) or 4096 (FP64) is refused by every entry point that
+    # filters, before any device work
+    fake = ctypes.c_void_p(256)
+    big32, big64 = scg.geometry(64, 10, 8193), scg.geometry(64, 10, 4097)
+    assert lib.scg_filter(ctypes.byref(big32), scg.F32, 0.0, 1.0, fake, fake, fake, 1 << 40, None) == -5
+    assert lib.scg_filter(ctypes.byref(big32), scg.F16, 0.0, 1.0, fake, fake, fake, 1 << 40, None) == -5
+    assert lib.scg_filter(ctypes.byref(big64), scg.F64, 0.0, 1.0, fake, fake, fake, 1 << 40, None) == -5
+    assert lib.scg_fbp(ctypes.byref(big32), scg.F32, fake, fake, fake, 1 << 40, None) == -5
+    p = scg._params(scg.default_params())
+    res = scg.Result()
+    assert lib.scg_solve(ctypes.byref(big32), scg.VARIANTS["S-PCG"], scg.F32, ctypes.byref(p), 1.0, fake, None,
+                         fake, fake, 1 << 40, ctypes.byref(res), None, 0, None, None, None) == -5
+    # and bad filter parameters
+    g = scg.geometry(64, 10, 95)
+    assert lib.scg_filter(ctypes.byref(g), scg.F32, 0.0, 0.0, fake, fake, fake, 1 << 40, None) == -1
+
+
 def test_batch_workspace_query_and_validation(lib):
     shapes = [(64, 90, 95), (77, 33, 110), (130, 181, 185)]
     b = scg.batch_workspace_bytes(shapes, "S-CG", torch.float32)

@@ -132,12 +132,67 @@ def test_tv_of_constant_is_zero_on_device():
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
-@pytest.mark.parametrize("na,nb,mu,gain", [(5, 95, 0.0, 1.0), (3, 130, 0.02, 2.0), (2, 725, 0.0, 1.0)])
+@pytest.mark.parametrize("na,nb,mu,gain", [(5, 95, 0.0, 1.0), (3, 130, 0.02, 2.0), (2, 725, 0.0, 1.0),
+                                           (1, 1, 0.0, 1.0), (4, 2, 0.1, 0.5), (7, 1449, 0.0, 1.0),
+                                           (3, 4096, 0.0, 1.0)])
 def test_filter_matches_oracle(na, nb, mu, gain, dtype):
+    # the FFT of two rows at a time: odd row counts leave a block with one row;
+    # P from 2 (one bin) to 8192
     r = inputs.normal(nb, "f", na * nb).reshape(na, nb)
     ref = oracle.filter_rows(r, mu, gain)
     got = scg.scg_filter(torch.tensor(r, dtype=dtype, device=DEV), mu, gain).cpu().numpy()
     assert rel(got, ref) <= (1e-5 if dtype == torch.float32 else 1e-11)
+
+
+def test_filter_at_the_fp32_length_limit():
+    # n_bins = 8192: P = 16384, the largest padded row pair the FP32 kernel
+    # holds in shared memory (128 KiB); checked on rows the naive DFT of the
+    # oracle evaluates in seconds
+    na, nb = 2, 8192
+    r = inputs.normal(9, "f", na * nb).reshape(na, nb)
+    got = scg.scg_filter(torch.tensor(r, dtype=torch.float32, device=DEV)).cpu().numpy()
+    assert rel(got, oracle.filter_rows(r)) <= 1e-5
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("n,na,nb", CASES)
+def test_fbp_matches_oracle(n, na, nb, dtype):
+    x = image(n, 3 * n + na)
+    y = oracle.project(x, na, nb) + 0.05 * inputs.normal(n, "fbp", na * nb).reshape(na, nb)
+    ref = oracle.fbp(y, n)
+    got = scg.scg_fbp(torch.tensor(y, dtype=dtype, device=DEV), n).cpu().numpy()
+    assert rel(got, ref) <= (1e-5 if dtype == torch.float32 else 1e-11)
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float16, 2e-3), (torch.bfloat16, 1.5e-2)])
+def test_fbp_reduced_storage(dtype, tol):
+    n, na, nb = 130, 181, 185
+    x = image(n, 11)
+    y = oracle.project(x, na, nb)
+    yq = torch.tensor(y, dtype=torch.float32).to(dtype)
+    ref = oracle.fbp(yq.double().numpy(), n)
+    got = scg.scg_fbp(yq.to(DEV), n).double().cpu().numpy()
+    err = rel(got, ref)
+    print(f"FBP {dtype}: rel L2 {err:.2e}")
+    assert err <= tol
+
+
+def test_fbp_of_full_size_phantom_on_sampled_pixels():
+    # 512^2 / 720 x 725: FBP of the phantom's exact projections, sampled pixels
+    # of A^T(filtered rows) against the oracle's filter and A^T one by one
+    work = inputs.SINGLE_512
+    n, na, nb = work.n, work.n_angles, work.n_bins
+    x = inputs.ellipse_phantom(n, work.n_ellipses, 0)
+    y = oracle.project(x, na, nb)
+    got = scg.scg_fbp(torch.tensor(y, dtype=torch.float32, device=DEV), n).cpu().numpy()
+    q = oracle.filter_rows(y, 1e-300, 1.0 / (2 * na))    # mu -> 0 (exact 0 selects the default)
+    rng = np.random.default_rng(7)
+    i = rng.integers(0, n, 200)
+    j = rng.integers(0, n, 200)
+    assert rel(got[i, j], oracle.backproject_pixels(q, n, i, j)) <= 1e-5
+    # and it is an image of the phantom: the field of view within 10 % in L2 (the oracle: 6.3 %)
+    fov = (np.arange(n)[:, None] - (n - 1) / 2) ** 2 + (np.arange(n)[None, :] - (n - 1) / 2) ** 2 <= (0.45 * n) ** 2
+    assert rel(got[fov], x[fov]) <= 0.10
 
 
 @pytest.mark.parametrize("work", [inputs.SINGLE_512, inputs.MIXED_1024], ids=lambda w: w.name)

@@ -5,14 +5,22 @@ C ABI (scg_solve).
   same status, same perturbation decisions (trials, accepted, l) and output x
   within 1e-9 relative L2 (the oracle's own sensitivity to a 1e-13 data
   perturbation on this workload is <= 5e-11).
-* FP32, same workload: same decisions where the oracle's TV margin exceeds
-  1e-5, and output within a per-variant bound.  The bound is the FP32 error
-  of one loop body (~1e-6, see the single-body test) times the solve's
-  amplification of a rounding-level perturbation, which the oracle measures
-  on this workload (y perturbed by 1e-13: CG 450x, S-CG-K 38x, S-CG-CD 5x,
-  the others <= 3x), with a factor-10 margin.  Plain CG and PCG update the
-  gradient recursively (Eq. recursive), so in FP32 their gradient error does
-  not shrink with the gradient; their bound is looser.
+* FP32, same workload: every TV decision of the seed has a relative margin
+  above 1e-5 (asserted), so the decisions and the iteration count must be
+  the oracle's; the output within a per-variant bound of about 3x the error
+  measured on a GB300 (CG 1.7e-3, PCG 5.4e-7, S-CG 2.2e-6, S-CG-CD 1.6e-5,
+  S-CG-K 4.8e-5, S-PCG 2.2e-6, S-PCG-K 7.6e-7).  FP32 operators differ from
+  the FP64 ones by ~1e-7 relative per output; a solve carries that difference
+  into x amplified by how far into the Krylov space it goes (the error grows
+  with the number of operator applications: S-CG-K's 28 against S-PCG-K's 6),
+  and plain CG / PCG update the gradient recursively (Eq. recursive), so
+  their gradient error does not shrink with the gradient.
+* 512x512 / 720 x 725 (the benchmarked workload): FP64 S-CG equal to the
+  oracle (iterations, decisions, x within 1e-9); FP32 S-CG, S-CG-CD, S-PCG,
+  S-PCG-K with the oracle's iteration count and decisions and x within ~3x
+  the measured error (S-CG 1.1e-4, S-CG-CD 2.0e-4, S-PCG 4.5e-6, S-PCG-K
+  3.0e-6: more iterations, more amplification, as above; rounding the data
+  alone to FP32 moves the oracle's S-CG output by 4.8e-6 here).
 * One loop body from a state the oracle exported (k = 4): every vector of the
   new state within 1e-5 (FP32) / 1e-11 (FP64).
 * Resume from an exported GPU state is bit-exact.
@@ -20,6 +28,7 @@ C ABI (scg_solve).
   perturbation (S-CG reproduces CG's first iterates).
 * Full-size 512x512 / 720 x 725 S-CG: f(output) <= eps checked with the
   oracle's A, lower TV than CG at the same eps.
+* The gamma schedule on a hand-worked 2 x 2 case (accepted gamma and l).
 """
 import numpy as np
 import pytest
@@ -40,8 +49,9 @@ def rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
-FP32_BOUND = {"CG": 2e-2, "PCG": 2e-5, "S-CG": 3e-5, "S-CG-CD": 5e-5, "S-CG-K": 4e-4,
-              "S-PCG": 5e-5, "S-PCG-K": 3e-5}
+FP32_BOUND = {"CG": 5e-3, "PCG": 2e-6, "S-CG": 7e-6, "S-CG-CD": 5e-5, "S-CG-K": 1.5e-4,
+              "S-PCG": 7e-6, "S-PCG-K": 2.5e-6}
+FP32_TV = {"CG": 1e-2, "PCG": 1e-5}                    # others: 1e-5 (measured <= 1.5e-6)
 
 
 def kw_for(variant, prob, **extra):
@@ -92,13 +102,13 @@ def test_fp32_whole_solve_matches_oracle(small, variant):
     print(f"{variant}: iters gpu {r.iters} oracle {ro['iters']}  rel L2 {err:.2e}  "
           f"tv {r.tv_final:.4f}/{ro['tv_final']:.4f}")
     assert r.status == ro["status"]
-    robust = np.all(to[:, 10] > 1e-5)                 # no near-tie TV decision
-    if robust:
-        assert r.iters == ro["iters"]
-        np.testing.assert_array_equal(r.trace[:, DECISION], to[:, DECISION])
-        assert err <= FP32_BOUND[variant]
+    if variant not in ("CG", "PCG"):
+        assert np.all(to[:, 10] > 1e-5)               # the seed has no near-tie TV decision
+    assert r.iters == ro["iters"]
+    np.testing.assert_array_equal(r.trace[:, DECISION], to[:, DECISION])
+    assert err <= FP32_BOUND[variant]
     assert r.f_final <= small.eps
-    assert r.tv_final == pytest.approx(ro["tv_final"], rel=2e-2 if variant == "CG" else 1e-3)
+    assert r.tv_final == pytest.approx(ro["tv_final"], rel=FP32_TV.get(variant, 1e-5))
 
 
 # Perturbation settings whose steps accept inside the first trial pass (three
@@ -241,3 +251,47 @@ def test_gamma_schedule_hand_worked(dtype, ell_in, trials, ell_out, gamma):
     v = np.array([[np.sqrt(2.0 / 3.0), -1.0 / np.sqrt(6.0)], [-1.0 / np.sqrt(6.0), 0.0]])
     assert t[3] == pytest.approx(oracle.tv(np.array([[0.0, 1.0], [1.0, 5.0]]) + gamma * v),
                                  rel=1e-12 if dtype == torch.float64 else 1e-6)
+
+
+# ---------------------------------------------------------------------------
+# The benchmarked workload (512^2, 720 angles x 725 bins) against the oracle.
+C2_FP32 = {"S-CG": (3.2e-4, 6e-5), "S-CG-CD": (6e-4, 2e-4), "S-PCG": (1.5e-5, 3e-6), "S-PCG-K": (1e-5, 6e-6)}
+_c2_cache = {}
+
+
+@pytest.fixture(scope="module")
+def config2():
+    return inputs.make_problem(inputs.SINGLE_512, 0, oracle.project)
+
+
+def c2_oracle(prob, variant):
+    if variant not in _c2_cache:
+        _c2_cache[variant] = oracle.solve(prob.y, prob.work.n, **kw_for(variant, prob))
+    return _c2_cache[variant]
+
+
+def test_config2_fp64_s_cg_equals_the_oracle(config2):
+    xo, ro, to = c2_oracle(config2, "S-CG")
+    r = gpu_solve(config2, torch.float64, **kw_for("S-CG", config2))
+    assert r.status == ro["status"] == "ok" and r.iters == ro["iters"] and r.ell == ro["ell"]
+    np.testing.assert_array_equal(r.trace[:, DECISION], to[:, DECISION])
+    assert rel(r.x.cpu().numpy(), xo) <= 1e-9
+    assert r.tv_final == pytest.approx(ro["tv_final"], rel=1e-9)
+
+
+@pytest.mark.parametrize("variant", sorted(C2_FP32))
+def test_config2_fp32_matches_the_oracle(config2, variant):
+    xo, ro, to = c2_oracle(config2, variant)
+    assert np.all(to[:, 10] > 1e-5)                   # no near-tie TV decision on this seed
+    r = gpu_solve(config2, torch.float32, **kw_for(variant, config2))
+    err = rel(r.x.cpu().numpy(), xo)
+    print(f"{variant} 512^2: iters {r.iters}/{ro['iters']} rel L2 {err:.2e} "
+          f"TV {r.tv_final:.3f}/{ro['tv_final']:.3f}")
+    assert r.status == ro["status"] == "ok" and r.iters == ro["iters"] and r.ell == ro["ell"]
+    np.testing.assert_array_equal(r.trace[:, DECISION], to[:, DECISION])
+    bx, btv = C2_FP32[variant]
+    assert err <= bx
+    assert r.tv_final == pytest.approx(ro["tv_final"], rel=btv)
+    x = r.x.cpu().numpy().astype(np.float64)
+    f = 0.5 * np.sum((config2.y - oracle.project(x, config2.work.n_angles, config2.work.n_bins)) ** 2)
+    assert f <= config2.eps * (1 + 1e-5)
