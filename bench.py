@@ -13,8 +13,19 @@ storage/arithmetic with FP64 reductions and scalars, variant S-CG.  The
 problem state (~20 MB) fits in L2, so the L2 is flushed (a 512 MiB write)
 before every timed step, outside the step's event pair.
 
+The sinogram of both arms is built with the FP64 oracle's projector (the
+same y, eps and config for ``--impl ours`` and ``--impl reference``).
+
+Beside the headline the line carries a ``batch`` block (the 256-problem
+uneven batch recipe through scg_solve_batch in binary16 storage, against the
+same problems solved one by one on the plain FP32 single-solve path) and a
+``serving`` block (a Poisson stream of few-view requests through the
+continuous-batching server in binary16: achieved rate, p50/p99 latency, the
+saturated rate against FP32 solo solves), each with its own clocks.
+
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
-oracle instead, on bounded samples of the same workload.
+oracle instead: whole solves of the same problem, as many as fit a bounded
+CPU budget.
 """
 from __future__ import annotations
 
@@ -37,10 +48,16 @@ from paper_1709_04912_gb300 import inputs  # noqa: E402
 
 METRIC = "S-CG recon/s at fixed eps"
 UNIT = "recon/s"
-# FP32 lane operations per nonzero ray-pixel weight: the minimum for one
-# chord-weighted multiply-add (crossing position 2, its distance 1, the weight 3,
-# the accumulation 1)
-OPS_PER_NNZ = 7
+# FP32 lane operations per nonzero ray-pixel weight of the projector pair's
+# roofline: 10, the cost of evaluating one chord weight from its definition and
+# accumulating it (signed distance of the pixel centre from the ray 2, |d| 1, the
+# two clips of the trapezoid 2, the scale 1/(m n) 1, the select of the
+# axis-aligned case 1, the multiply-add into the ray sum 1, the index 2).  The
+# kernels need fewer (the walk makes the distance an increment and the clips one
+# saturate); the line also reports the fraction at the minimum of 7 (position 2,
+# distance 1, weight 3, accumulation 1).
+OPS_PER_NNZ = 10
+OPS_PER_NNZ_MIN = 7
 WORKLOADS = {w.name: w for w in (inputs.SINGLE_512, inputs.SMALL_FP64, inputs.MIXED_1024,
                                   inputs.PAPER_512)}
 
@@ -57,14 +74,21 @@ def parse():
     ap.add_argument("--gamma0-rel", type=float, default=0.05)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="leave the batch block out of the line")
+    ap.add_argument("--no-serving", action="store_true", help="leave the serving block out of the line")
+    ap.add_argument("--ref-budget", type=float, default=150.0,
+                    help="CPU seconds the reference arm spends on timed oracle solves")
     ap.add_argument("--mode", default="single", choices=["single", "batch", "serving"],
                     help="single: the headline solve; batch: uneven batch through scg_solve_batch "
                          "vs the same solves one by one; serving: Poisson request stream through "
                          "the continuous-batching server")
     ap.add_argument("--batch", type=int, default=256, help="problems in --mode batch")
-    ap.add_argument("--rate", type=float, default=50.0, help="requests/s in --mode serving")
-    ap.add_argument("--duration", type=float, default=20.0, help="measured seconds in --mode serving")
-    ap.add_argument("--serve-warmup", type=float, default=5.0, help="warm-up seconds in --mode serving")
+    ap.add_argument("--rate", type=float, default=None,
+                    help="requests/s of the Poisson stream (--mode serving 50, serving block 200)")
+    ap.add_argument("--duration", type=float, default=None,
+                    help="measured seconds of the Poisson stream (--mode serving 20, serving block 8)")
+    ap.add_argument("--serve-warmup", type=float, default=None,
+                    help="warm-up seconds of the Poisson stream (--mode serving 5, serving block 2)")
     ap.add_argument("--max-active", type=int, default=64)
     ap.add_argument("--pool-gb", type=float, default=16.0)
     ap.add_argument("--dtype", default=None, choices=["f32", "f16", "bf16", "f64"],
@@ -195,47 +219,56 @@ def nnz_of(work) -> int:
 
 
 # ---------------------------------------------------------------------------
+def time_oracle_solves(prob, work, variant, gamma0_rel, budget_s, max_solves):
+    """Whole oracle solves of ``prob`` (FP64, on the host cores), timed one by
+    one until ``budget_s`` seconds or ``max_solves`` solves.  Returns the times,
+    the iteration count and the thread count."""
+    import oracle
+    kw = dict(variant=variant, gamma0_rel=gamma0_rel, eps=prob.eps, max_iter=work.max_iter)
+    if variant in ("CG", "PCG"):
+        kw["perturb"] = "none"
+    oracle.solve(prob.y, work.n, **dict(kw, max_iter=0))      # loads the library
+    times, iters = [], 0
+    t_all = time.perf_counter()
+    while len(times) < max(1, max_solves):
+        t0 = time.perf_counter()
+        _, res, _ = oracle.solve(prob.y, work.n, **kw)
+        times.append(time.perf_counter() - t0)
+        iters = res["iters"]
+        if time.perf_counter() - t_all >= budget_s:
+            break
+    return times, iters, oracle.num_threads()
+
+
 def run_reference(args, work, rank, world):
-    """The FP64 CPU oracle on bounded samples of the same workload."""
+    """The FP64 CPU oracle: whole solves of the same problem as ours."""
     if rank != 0:
         return 0
     import oracle
     variant = args.variant
-    kw = dict(variant=variant, gamma0_rel=args.gamma0_rel)
-    if variant in ("CG", "PCG"):
-        kw["perturb"] = "none"
     prob = inputs.make_problem(work, args.seed, oracle.project)
-    # iteration count to eps: one full oracle solve (untimed; also the warm-up)
-    _, full, _ = oracle.solve(prob.y, work.n, eps=prob.eps, max_iter=work.max_iter, **kw)
-    iters = max(full["iters"], 1)
-    samples = []
-    for step in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        oracle.solve(prob.y, work.n, eps=prob.eps, max_iter=0, **kw)
-        t1 = time.perf_counter()
-        oracle.solve(prob.y, work.n, eps=prob.eps, max_iter=1, **kw)
-        t2 = time.perf_counter()
-        t_setup = t1 - t0
-        t_body = max((t2 - t1) - t_setup, 0.0)
-        if step >= args.warmup:
-            samples.append(t_setup + iters * t_body)
-    t_solve = float(np.mean(samples))
+    times, iters, cores = time_oracle_solves(prob, work, variant, args.gamma0_rel, args.ref_budget, args.steps)
+    t_solve = float(np.mean(times))
     value = 1.0 / t_solve
-    cores = oracle.num_threads()
-    sample = (f"per step: oracle {variant} set-up alone and set-up + 1 loop body on the full "
-              f"workload; solve time = set-up + {iters} bodies (the oracle's own iteration "
-              f"count to eps)")
+    sample = (f"{len(times)} whole oracle {variant} solves of this workload ({iters} iterations to eps each), "
+              f"timed one by one, as many as fit {args.ref_budget:.0f} s of CPU time (no warm-up solve: "
+              f"the oracle has nothing to warm)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_solve,
+            "steps": len(times), "warmup": 0, "ms_per_step": 1e3 * t_solve,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": work.name, "variant": variant,
-                                            "n": work.n, "n_angles": work.n_angles,
-                                            "n_bins": work.n_bins, "eps": prob.eps},
+            "data": "synthetic", "config": dict(config_of(work, variant, prob, iters), parallelism=f"replicas x{world}"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def config_of(work, variant, prob, iters):
+    """The workload as both arms name it."""
+    return {"workload": work.name, "variant": variant, "n": work.n, "n_angles": work.n_angles,
+            "n_bins": work.n_bins, "eps": prob.eps, "iters": iters, "data_projector": "oracle (FP64)",
+            "l2": "flushed (512 MiB write) before each step", "per_gpu_problems": 1}
 
 
 # ---------------------------------------------------------------------------
@@ -253,11 +286,8 @@ def run_ours(args, work, rank, local_rank, world):
     if variant in ("CG", "PCG"):
         kw["perturb"] = "none"
 
-    def gpu_project(x, na, nb):
-        xt = torch.tensor(x, dtype=torch.float32, device=dev)
-        return scg.scg_project(xt, na, nb).double().cpu().numpy()
-
-    prob = inputs.make_problem(work, args.seed + rank, gpu_project)
+    import oracle
+    prob = inputs.make_problem(work, args.seed + rank, oracle.project)
     dtype = DTYPES[args.dtype or "f32"]
     esize = torch.tensor([], dtype=dtype).element_size()
     y = torch.tensor(prob.y, dtype=torch.float32).to(dtype).to(dev)
@@ -376,7 +406,8 @@ def run_ours(args, work, rank, local_rank, world):
                 "achieved": achieved, "peak": peak_ops,
                 "unit": "Top/s (FP32 lane ops)", "frac": achieved / peak_ops, "traffic": traffic,
                 "peak_source": f"{sms} SMs x 128 FP32 lanes x {clock_mhz:.0f} MHz ({peak_kind} clock)",
-                "ops_per_launch": OPS_PER_NNZ * nnz, "nnz": nnz,
+                "ops_per_nnz": OPS_PER_NNZ, "ops_per_launch": OPS_PER_NNZ * nnz, "nnz": nnz,
+                "frac_at_min_ops": OPS_PER_NNZ_MIN * nnz / (t_dom * 1e-3) / 1e12 / peak_ops,
                 "ms_per_launch": {"project": t_proj, "backproject": t_back},
                 "hbm_gbs_algorithmic": {"project": bytes_pass / (t_proj * 1e-3) / 1e9,
                                         "backproject": bytes_pass / (t_back * 1e-3) / 1e9,
@@ -386,39 +417,34 @@ def run_ours(args, work, rank, local_rank, world):
                 "spmv_equivalent_gbs": {"project": 8 * nnz / (t_proj * 1e-3) / 1e9,
                                         "backproject": 8 * nnz / (t_back * 1e-3) / 1e9}}
 
-    # CPU baseline: the oracle on a bounded sample of the same workload
+    # CPU baseline: whole oracle solves of the same problem, timed
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        import oracle
-        okw = dict(variant=variant, gamma0_rel=args.gamma0_rel)
-        if variant in ("CG", "PCG"):
-            okw["perturb"] = "none"
-        t0 = time.perf_counter()
-        oracle.solve(prob.y, work.n, eps=prob.eps, max_iter=0, **okw)
-        t1 = time.perf_counter()
-        oracle.solve(prob.y, work.n, eps=prob.eps, max_iter=1, **okw)
-        t2 = time.perf_counter()
-        t_setup = t1 - t0
-        t_body = max((t2 - t1) - t_setup, 0.0)
-        t_solve = t_setup + max(last.iters, 1) * t_body
-        cpu = {"value": 1.0 / t_solve, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-               "sample": (f"oracle {variant} set-up alone and set-up + 1 loop body on the same "
-                          f"workload ({t2 - t0:.1f} s of CPU work), extrapolated to "
-                          f"{max(last.iters, 1)} bodies (this run's GPU iteration count)")}
+        times, o_iters, cores = time_oracle_solves(prob, work, variant, args.gamma0_rel, 30.0, 1)
+        cpu = {"value": 1.0 / float(np.mean(times)), "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": (f"{len(times)} whole oracle {variant} solve(s) of this workload "
+                          f"({o_iters} iterations to eps), timed")}
+
+    blocks = {}
+    if not args.no_batch:
+        blocks["batch"] = batch_block(args, dev, rank, world, count=args.batch, dtype_name="f16", steps=3,
+                                      warmup=1)
+    if not args.no_serving and world == 1:
+        blocks["serving"] = serving_block(args, dev, rank, rate=args.rate or 200.0,
+                                          duration=args.duration or 8.0, warm=args.serve_warmup or 2.0,
+                                          dtype_name="f16")
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype or "f32",
                 "data": "synthetic",
-                "config": {"workload": work.name, "variant": variant, "n": work.n,
-                           "n_angles": work.n_angles, "n_bins": work.n_bins, "eps": prob.eps,
-                           "iters": last.iters, "status": last.status, "tv_final": last.tv_final,
-                           "f_final": last.f_final, "l2": "flushed (512 MiB write) before each step",
-                           "per_gpu_problems": 1, "parallelism": f"replicas x{world}"},
+                "config": dict(config_of(work, variant, prob, last.iters), parallelism=f"replicas x{world}"),
+                "result": {"status": last.status, "tv_final": last.tv_final, "f_final": last.f_final},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "device_loop": bool(last.device_loop), "clocks": clk,
                 "step_ms": ms}
+        line.update(blocks)
         print(json.dumps(line), flush=True)
     return 0
 
@@ -452,25 +478,39 @@ def _gpu_problems(works, seed, dev):
     return probs, ys
 
 
-def run_batch(args, rank, local_rank, world):
-    """Uneven batch (sizes {128..768}^2, 60..720 angles, 1 % noise): the whole
-    batch through scg_solve_batch, against the same problems solved one by one
-    with scg_solve.  Results are bit-identical both ways."""
+def _solve_kw(args, variant):
+    kw = dict(gamma0_rel=args.gamma0_rel, max_iter=100)
+    if variant in ("CG", "PCG"):
+        kw["perturb"] = "none"
+    return kw
+
+
+def _same_eps_tv(res, ref, eps):
+    """How results of one precision compare with plain-FP32 solo results of the
+    same problems: every result within its eps, iteration counts, relative TV
+    differences."""
+    tv = np.array([abs(a.tv_final - b.tv_final) / max(abs(b.tv_final), 1e-300) for a, b in zip(res, ref)])
+    return {"all_f_le_eps": bool(all(r.status == "ok" and r.f_final <= e for r, e in zip(res, eps))),
+            "iters_equal": int(sum(a.iters == b.iters for a, b in zip(res, ref))), "problems": len(res),
+            "tv_rel_diff_vs_fp32": {"median": float(np.median(tv)), "p95": float(np.percentile(tv, 95)),
+                                    "max": float(tv.max()), "within_1pct": int(np.sum(tv <= 0.01))}}
+
+
+def batch_block(args, dev, rank, world, count, dtype_name, steps, warmup):
+    """The uneven batch recipe (N in {128..768}, 60..720 angles, bins
+    ceil(sqrt2 N), 1 % noise): ``count`` problems through scg_solve_batch in
+    ``dtype_name`` storage, against the same problems one by one through
+    scg_solve in that storage and in plain FP32."""
     import torch
 
     from paper_1709_04912_gb300 import scg
 
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    scg.load()
     variant = args.variant
-    kw = dict(gamma0_rel=args.gamma0_rel, max_iter=100)
-    if variant in ("CG", "PCG"):
-        kw["perturb"] = "none"
-    dtype = DTYPES[args.dtype or "f32"]
-    works = inputs.batch_workloads(args.batch, args.seed + rank)
-    probs, ys = _gpu_problems(works, 1000 * (args.seed + rank), dev)
-    ys = [y.to(dtype) for y in ys]
+    kw = _solve_kw(args, variant)
+    dtype = DTYPES[dtype_name]
+    works = inputs.batch_workloads(count, args.seed + rank)
+    probs, ys32 = _gpu_problems(works, 1000 * (args.seed + rank), dev)
+    ys = [y.to(dtype) for y in ys32]
     ns = [w.n for w in works]
     eps = [p.eps for p in probs]
     outs = [torch.empty((n, n), dtype=dtype, device=dev) for n in ns]
@@ -481,14 +521,14 @@ def run_batch(args, rank, local_rank, world):
     def batch():
         return scg.scg_solve_batch(ys, ns, variant, eps, outs=outs, work=wsp, **kw)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         rb = batch()
     torch.cuda.synchronize()
     barrier(world)
-    clocks = ClockSampler(local_rank)
+    clocks = ClockSampler(dev.index)
     clocks.start()
     ms = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         rb = batch()
@@ -498,69 +538,67 @@ def run_batch(args, rank, local_rank, world):
     clk = clocks.stop()
     barrier(world)
     t_batch = max_over_ranks(float(np.mean(ms)) / 1e3, world, dev)
-    # the same problems one by one (warm first: one graph per geometry)
-    wsolo = torch.empty(max(scg.solve_workspace_bytes(w.n, w.n_angles, w.n_bins, variant, scg._prec_of(dtype))
-                            for w in works), dtype=torch.uint8, device=dev)
-    for q in range(len(works)):
-        scg.scg_solve(ys[q], ns[q], variant, eps[q], out=outs[q], work=wsolo, **kw)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    same = True
-    for q in range(len(works)):
-        r = scg.scg_solve(ys[q], ns[q], variant, eps[q], out=outs[q], work=wsolo, **kw)
-        same = same and r.iters == rb[q].iters and r.tv_final == rb[q].tv_final
-    e1.record(stream)
-    e1.synchronize()
-    t_solo = e0.elapsed_time(e1) / 1e3
-    if rank == 0:
-        line = {"metric": "batched recon/s", "value": job_rate(len(works), world, t_batch), "unit": UNIT,
-                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": 1e3 * t_batch, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": args.dtype or "f32", "data": "synthetic",
-                "config": {"workload": f"uneven_batch{len(works)}", "variant": variant,
-                           "sizes": "N in {128,...,768}, angles in {60,...,720}, bins ceil(sqrt2 N)",
-                           "workspace_bytes": nbytes, "parallelism": f"replicas x{world}",
-                           "total_iters": int(sum(r.iters for r in rb)),
-                           "body_launches": rb[0].body_launches},
-                "solo": {"value": len(works) / t_solo, "unit": UNIT, "ms": 1e3 * t_solo,
-                         "same_iters_and_tv": bool(same)},
-                "speedup_vs_solo": t_solo / t_batch, "clocks": clk, "step_ms": ms}
-        print(json.dumps(line), flush=True)
-    return 0
+
+    def one_by_one(yl, dt):
+        w = torch.empty(max(scg.solve_workspace_bytes(wk.n, wk.n_angles, wk.n_bins, variant, scg._prec_of(dt))
+                            for wk in works), dtype=torch.uint8, device=dev)
+        o = [torch.empty((n, n), dtype=dt, device=dev) for n in ns]
+        for q in range(len(works)):                      # warm: one graph per geometry
+            scg.scg_solve(yl[q], ns[q], variant, eps[q], out=o[q], work=w, **kw)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = [scg.scg_solve(yl[q], ns[q], variant, eps[q], out=o[q], work=w, **kw) for q in range(len(works))]
+        e1.record(stream)
+        e1.synchronize()
+        return res, e0.elapsed_time(e1) / 1e3
+
+    solo, t_solo = one_by_one(ys, dtype)
+    same = all(a.iters == b.iters and a.tv_final == b.tv_final for a, b in zip(rb, solo))
+    if dtype == torch.float32:
+        solo32, t_solo32 = solo, t_solo
+    else:
+        solo32, t_solo32 = one_by_one(ys32, torch.float32)
+    value = job_rate(len(works), world, t_batch)
+    return {"metric": "batched recon/s", "value": value, "unit": UNIT, "dtype": dtype_name,
+            "ms_per_batch": 1e3 * t_batch, "steps": steps, "warmup": warmup, "step_ms": ms,
+            "config": {"workload": f"uneven_batch{len(works)}", "variant": variant,
+                       "sizes": "N in {128,...,768}, angles in {60,...,720}, bins ceil(sqrt2 N), 1 % noise",
+                       "data_projector": "libscg FP32", "workspace_bytes": nbytes,
+                       "total_iters": int(sum(r.iters for r in rb)), "body_launches": rb[0].body_launches},
+            "solo_same_storage": {"value": len(works) / t_solo, "unit": UNIT, "same_iters_and_tv": bool(same)},
+            "solo_fp32": {"value": len(works) / t_solo32, "unit": UNIT},
+            "speedup_vs_fp32_solo": t_solo32 / t_batch,
+            "equal_eps_and_tv": _same_eps_tv(rb, solo32, eps), "clocks": clk}
 
 
-def run_serving(args, rank, local_rank, world):
-    """Poisson stream of few-view requests (N ~ U{128..1024 step 64}, 30..180
+def serving_block(args, dev, rank, rate, duration, warm, dtype_name):
+    """A Poisson stream of few-view requests (N ~ U{128..1024 step 64}, 30..180
     angles, eps factor U[1.02, 1.2], 1 % noise) through the continuous-batching
-    server; latency is arrival to completion on the host clock."""
+    server; latency is arrival to completion on the host clock.  Also the
+    saturated rate (128 requests queued at once) and the same requests solved
+    one by one on the plain FP32 single-solve path."""
     import torch
 
     from paper_1709_04912_gb300 import scg
 
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    scg.load()
     variant = args.variant
-    kw = dict(gamma0_rel=args.gamma0_rel, max_iter=100)
-    if variant in ("CG", "PCG"):
-        kw["perturb"] = "none"
-    dtype = DTYPES[args.dtype or "f16"]
+    kw = _solve_kw(args, variant)
+    dtype = DTYPES[dtype_name]
     uniq = inputs.serving_workloads(64, args.seed + rank)
     probs, ys32 = _gpu_problems(uniq, 5000 * (args.seed + rank), dev)
     ys = [y.to(dtype) for y in ys32]
     outs = [torch.empty((w.n, w.n), dtype=dtype, device=dev) for w in uniq]
-    srv = scg.Server(variant, dtype, pool_bytes=int(args.pool_gb * (1 << 30)),
-                     max_active=args.max_active, device=dev, **kw)
+    srv = scg.Server(variant, dtype, pool_bytes=int(args.pool_gb * (1 << 30)), max_active=args.max_active,
+                     device=dev, **kw)
 
     def submit(q, tag):
         u = q % len(uniq)
         srv.submit(ys[u], uniq[u].n, probs[u].eps, out=outs[u], tag=tag)
 
-    # saturated throughput: 2 x 64 requests at once (first pass also warms graphs)
     sat = []
     served = {}
-    for rep in range(2):
+    for _ in range(2):                                   # the first pass also captures the graphs
         t0 = time.perf_counter()
         for q in range(2 * len(uniq)):
             submit(q, q)
@@ -570,7 +608,6 @@ def run_serving(args, rank, local_rank, world):
                 served[tag % len(uniq)] = r
                 got += 1
         sat.append(2 * len(uniq) / (time.perf_counter() - t0))
-    # solo: the same requests one by one through scg_solve, plain FP32
     wsolo = torch.empty(max(scg.solve_workspace_bytes(w.n, w.n_angles, w.n_bins, variant, scg.F32)
                             for w in uniq), dtype=torch.uint8, device=dev)
     o32 = [torch.empty((w.n, w.n), dtype=torch.float32, device=dev) for w in uniq]
@@ -578,24 +615,16 @@ def run_serving(args, rank, local_rank, world):
         scg.scg_solve(ys32[q], uniq[q].n, variant, probs[q].eps, out=o32[q], work=wsolo, **kw)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    solo_res = []
-    for q in range(len(uniq)):
-        solo_res.append(scg.scg_solve(ys32[q], uniq[q].n, variant, probs[q].eps, out=o32[q], work=wsolo, **kw))
+    solo_res = [scg.scg_solve(ys32[q], uniq[q].n, variant, probs[q].eps, out=o32[q], work=wsolo, **kw)
+                for q in range(len(uniq))]
     torch.cuda.synchronize()
     solo = len(uniq) / (time.perf_counter() - t0)
-    tv_diffs = np.array([abs(served[q].tv_final - solo_res[q].tv_final) / solo_res[q].tv_final
-                         for q in range(len(uniq))])
-    tv_diff = {"max": float(tv_diffs.max()), "median": float(np.median(tv_diffs)),
-               "p95": float(np.percentile(tv_diffs, 95)), "within_1pct": int(np.sum(tv_diffs <= 0.01)),
-               "requests": int(len(tv_diffs)),
-               "iters_equal": int(sum(served[q].iters == solo_res[q].iters for q in range(len(uniq))))}
-    all_ok = all(served[q].status == "ok" and served[q].f_final <= probs[q].eps for q in range(len(uniq)))
-    # the Poisson stream
-    total = args.serve_warmup + args.duration
-    arrivals = inputs.poisson_arrivals(int(args.rate * total * 1.5) + 16, args.rate, args.seed + 7)
+    same = _same_eps_tv([served[q] for q in range(len(uniq))], solo_res, [p.eps for p in probs])
+    total = warm + duration
+    arrivals = inputs.poisson_arrivals(int(rate * total * 1.5) + 16, rate, args.seed + 7)
     arrivals = arrivals[arrivals < total]
     lat, done_t = {}, {}
-    clocks = ClockSampler(local_rank)
+    clocks = ClockSampler(dev.index)
     clocks.start()
     t_start = time.perf_counter()
     nxt = 0
@@ -619,26 +648,54 @@ def run_serving(args, rank, local_rank, world):
         steps += 1
     clk = clocks.stop()
     srv.close()
-    window = [q for q in lat if args.serve_warmup <= arrivals[q] < total]
-    served = [q for q in window]
-    L = np.array([lat[q] for q in served]) * 1e3 if served else np.array([float("nan")])
-    t_end = max(done_t[q] for q in served) if served else total
-    thr = len(served) / max(t_end - args.serve_warmup, 1e-9)
+    window = [q for q in lat if warm <= arrivals[q] < total]
+    L = np.array([lat[q] for q in window]) * 1e3 if window else np.array([float("nan")])
+    t_end = max(done_t[q] for q in window) if window else total
+    thr = len(window) / max(t_end - warm, 1e-9)
+    return {"metric": "served recon/s (Poisson)", "value": thr, "unit": UNIT, "dtype": dtype_name,
+            "steps": steps,
+            "config": {"workload": "serving_poisson", "variant": variant, "rate": rate, "duration_s": duration,
+                       "warmup_s": warm, "requests": len(window), "max_active": args.max_active,
+                       "pool_gb": args.pool_gb, "data_projector": "libscg FP32",
+                       "sizes": "N ~ U{128..1024 step 64}, 30..180 angles, eps 1.02-1.2 x noise floor"},
+            "latency_ms": {"p50": float(np.percentile(L, 50)), "p99": float(np.percentile(L, 99)),
+                           "mean": float(np.mean(L))},
+            "saturated_recon_per_s": max(sat), "solo_fp32_recon_per_s": solo,
+            "saturated_vs_fp32_solo": max(sat) / solo, "equal_eps_and_tv": same, "clocks": clk}
+
+
+def run_batch(args, rank, local_rank, world):
+    """--mode batch: the batch block alone, as its own line."""
+    import torch
+
+    from paper_1709_04912_gb300 import scg
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    scg.load()
+    b = batch_block(args, dev, rank, world, args.batch, args.dtype or "f32", args.steps, args.warmup)
     if rank == 0:
-        line = {"metric": "served recon/s (Poisson)", "value": thr * world, "unit": UNIT, "n_gpus": world,
-                "steps": steps, "warmup": 0, "ms_per_step": None, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": args.dtype or "f16", "data": "synthetic",
-                "config": {"workload": "serving_poisson", "variant": variant, "rate": args.rate,
-                           "duration_s": args.duration, "warmup_s": args.serve_warmup,
-                           "requests": len(served), "max_active": args.max_active,
-                           "pool_gb": args.pool_gb,
-                           "sizes": "N ~ U{128..1024 step 64}, 30..180 angles, eps 1.02-1.2 x noise floor"},
-                "latency_ms": {"p50": float(np.percentile(L, 50)), "p99": float(np.percentile(L, 99)),
-                               "mean": float(np.mean(L))},
-                "saturated_recon_per_s": max(sat), "solo_fp32_recon_per_s": solo,
-                "served_vs_solo_fp32": max(sat) / solo,
-                "equal_eps_and_tv": {"all_f_le_eps": bool(all_ok), "tv_rel_diff_vs_fp32": tv_diff},
-                "clocks": clk}
+        line = dict(b, n_gpus=world, higher_is_better=True, scaling="weak", vs_baseline=None, data="synthetic")
+        line["config"]["parallelism"] = f"replicas x{world}"
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serving(args, rank, local_rank, world):
+    """--mode serving: the serving block alone, as its own line."""
+    import torch
+
+    from paper_1709_04912_gb300 import scg
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    scg.load()
+    b = serving_block(args, dev, rank, args.rate or 50.0, args.duration or 20.0, args.serve_warmup or 5.0,
+                      args.dtype or "f16")
+    if rank == 0:
+        line = dict(b, n_gpus=world, warmup=0, ms_per_step=None, higher_is_better=True, scaling="weak",
+                    vs_baseline=None, data="synthetic")
+        line["value"] = b["value"] * world
         print(json.dumps(line), flush=True)
     return 0
 

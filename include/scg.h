@@ -85,7 +85,15 @@ typedef enum {
 
 typedef enum {
     SCG_PERTURB_NONE = 0,   /* no superiorization step (x_{k+1/2} = x_k)          */
-    SCG_PERTURB_GAMMA = 1   /* gamma_l = gamma0 a^l with TV acceptance (Sec. 3)   */
+    SCG_PERTURB_GAMMA = 1,  /* gamma_l = gamma0 a^l with TV acceptance (Sec. 3)   */
+    SCG_PERTURB_ETA = 2     /* the Appendix's rule (Eq. up bnd u_k):
+                               x_{k+1/2} = x_k + u_k, u_k = eta0 ||g_k|| v_k with
+                               g_k = A^T (A x_k - y) and v_k = -dTV/||dTV||, no TV
+                               test; with 0 < eta0 <= min(1/(4c^2), eta2) (c =
+                               ||A||_2, eta2 the positive root of
+                               (2 + c^2 eta) eta = 1/(32 c^2)) the Lemma bounds
+                               2f(x_k) - 2f(x_{k+1}) >= ||g_k||^2 / (32 c^2).
+                               Costs one extra A and A^T pass per loop body.   */
 } scg_perturb;
 
 typedef struct {
@@ -118,6 +126,7 @@ typedef struct {
                             1: one graph per loop body, launched in batches
                             and polled by the host (same kernels; for tools
                             that profile kernels one launch at a time)          */
+    double eta0;         /* SCG_PERTURB_ETA only: eta0 > 0 (default 0)          */
 } scg_params;
 
 typedef struct {

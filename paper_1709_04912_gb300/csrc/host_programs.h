@@ -58,6 +58,15 @@ void fill_filter_tables(std::vector<C>& out, int P, double mu, double gain) {
     }
 }
 
+// Parameter ranges shared by every solving entry point.
+inline bool valid_params(const scg_params* p) {
+    if (p->max_iter < 0 || p->max_iter > 10000000 || p->max_trials < 1 || p->max_trials > 100000 || p->K < 1 ||
+        p->K > 1000 || !(p->a > 0.0 && p->a < 1.0) || !(p->filter_gain > 0.0))
+        return false;
+    if (p->perturb == SCG_PERTURB_ETA) return p->eta0 > 0.0 && isfinite(p->eta0);
+    return p->perturb == SCG_PERTURB_NONE || p->perturb == SCG_PERTURB_GAMMA;
+}
+
 inline bool valid_prec(int p) { return p == SCG_F32 || p == SCG_F64 || p == SCG_F16 || p == SCG_BF16; }
 // bytes of one stored element, and of one arithmetic value
 inline size_t elem_size(int p) { return p == SCG_F64 ? 8 : p == SCG_F32 ? 4 : 2; }
@@ -311,6 +320,7 @@ struct Runner {
 
 struct Program {
     int variant, trial_passes, ksteps;
+    bool eta;          // Appendix rule: the gradient at x_k sizes the perturbation
 };
 
 // g'^T p' for the step length: FIN_BETA derives it from the gradient pass's
@@ -368,6 +378,11 @@ void run_body(Runner<T>& R, const Program& pg) {
     }
     for (int t = 0; t < pg.trial_passes; ++t)             // TV trials of x_k + gamma_l v
         R.trial(t == 0 ? kTrialsFirst : kTrials);
+    if (pg.eta) {                                      // ||g_k||, g_k = A^T (A x_k - y)
+        R.vec(VEC_VIEWS, IB_X, FIN_NONE);
+        R.project(SB_R, PROJ_RESIDUAL, FIN_NONE);
+        R.back1(SB_R, IB_G, FIN_ETA);
+    }
     R.vec(VEC_PERTURB, 0, FIN_NONE);                   // x_{k+1/2} = perturbed(x_k)
     R.project(SB_R, PROJ_RESIDUAL, FIN_F);             // A x_{k+1/2} - y, f(x_{k+1/2})
     if (pre) R.filter(SB_R, SB_W);
@@ -478,6 +493,7 @@ inline DevState initial_state(const scg_params* prm, double eps, int variant) {
     st.apow[0] = 1.0;
     for (int t = 1; t < kTrials; ++t) st.apow[t] = st.apow[t - 1] * prm->a;
     st.max_trials = prm->max_trials;
+    st.eta0 = prm->eta0;
     st.variant = variant;
     st.family = fam;
     st.in_init = 1;
@@ -490,6 +506,7 @@ inline Program make_program(const scg_params* prm, int variant) {
     pg.variant = variant;
     pg.trial_passes = prm->perturb == SCG_PERTURB_GAMMA ? trial_passes_for(prm->max_trials) : 0;
     pg.ksteps = prm->K + (prm->k_inclusive ? 1 : 0);
+    pg.eta = prm->perturb == SCG_PERTURB_ETA && family_of(variant) != FAM_CG;
     return pg;
 }
 

@@ -573,6 +573,8 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
         } else if (step == FIN_CG_DELTA) {
             v[0] = acc_add(v[0], acc_prod(g0, g0));                                       // ||g||^2
             v[1] = acc_add(v[1], acc_prod(g0, g1));                                       // g^T z
+        } else if (step == FIN_ETA) {
+            v[0] = acc_add(v[0], acc_prod(g0, g0));                                       // ||g_k||^2
         }
     }
     if (step == FIN_NONE) return;

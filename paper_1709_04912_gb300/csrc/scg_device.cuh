@@ -137,6 +137,7 @@ struct DevState {
     double apow[kTrials];   // a^t, t = 0 .. kTrials-1 (set on the host); trial t: trial_c0 * apow[t]
     double margin;
     double f_final, tv_final;
+    double eta0;            // Appendix rule: ||u_k|| = eta0 ||g_k||
     long long ell;
     int k, iters, max_iter, done, status;
     int perturb, gamma_fixed, max_trials, trials, accepted;
@@ -497,7 +498,8 @@ enum Step {
     FIN_RESUME,       // resumed state: S0 = p^T h, S1 = g^T p
     FIN_TV,           // standalone TV: S0 -> trace slot 0
     FIN_FINAL_F,      // f of the output
-    FIN_FINAL_TV      // TV of the output
+    FIN_FINAL_TV,     // TV of the output
+    FIN_ETA           // gradient at x_k (Appendix rule): S0 = ||g_k||^2 -> the perturbation's size
 };
 
 __device__ __forceinline__ bool finite_pos(double v) { return v > 0.0 && isfinite(v); }
@@ -545,6 +547,8 @@ __device__ void top_of_loop(const Prob<T>& P, DevState& st) {
         }
         st.accepted = 0;              // trials pending
         set_trial_coefs(st);
+    } else if (st.family != FAM_CG && st.perturb == SCG_PERTURB_ETA && st.gnorm2 > 0.0) {
+        st.accepted = 3;              // size pending: ||g_k|| from this body's first passes
     } else {
         st.accepted = -1;             // no perturbation this k
         if (row) { row[TR_TV_AFTER] = st.tv_x; row[TR_ELL] = (double)st.ell; }
@@ -698,6 +702,22 @@ __device__ void finalize(int step, const Prob<T>& P, DevState& st, const double*
         break;
     case FIN_FINAL_TV:
         st.tv_final = S[0];
+        break;
+    case FIN_ETA:
+        // Appendix, Eq. up bnd u_k: u_k = eta0 ||g_k|| v_k with v_k = -dTV/||dTV||
+        // and g_k = A^T(A x_k - y); on the scaled system c A x ~ c y the sum is
+        // c^4 ||g_k||^2.  No TV test: x_{k+1/2} = x_k + u_k.
+        if (st.accepted == 3) {
+            const double ys = (double)P.y_scale;
+            const double un = st.eta0 * sqrt(S[0]) / (ys * ys);
+            st.coef = -un / sqrt(st.gnorm2);
+            st.accepted = 1;
+            if (row) {
+                row[TR_ACCEPTED] = 1.0;
+                row[TR_GAMMA] = un;
+                row[TR_ELL] = (double)st.ell;
+            }
+        }
         break;
     default:
         break;

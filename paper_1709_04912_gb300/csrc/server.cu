@@ -566,13 +566,6 @@ private:
     cudaEvent_t ev_ = nullptr;
 };
 
-bool valid_params(const scg_params* prm) {
-    return prm->max_iter >= 0 && prm->max_iter <= 10000000 && prm->max_trials >= 1 &&
-           prm->max_trials <= 100000 && prm->K >= 1 && prm->K <= 1000 && prm->a > 0.0 && prm->a < 1.0 &&
-           prm->filter_gain > 0.0 &&
-           (prm->perturb == SCG_PERTURB_NONE || prm->perturb == SCG_PERTURB_GAMMA);
-}
-
 }  // namespace
 
 struct scg_server {

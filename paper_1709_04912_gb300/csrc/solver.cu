@@ -27,11 +27,11 @@ namespace {
 struct GraphKey {
     int dev;
     const void* work;
-    int prec, variant, trial_passes, ksteps, n, na, nb, host_loop, proj_shift;
+    int prec, variant, trial_passes, ksteps, n, na, nb, host_loop, proj_shift, eta;
     bool operator<(const GraphKey& o) const {
-        return std::tie(dev, work, prec, variant, trial_passes, ksteps, n, na, nb, host_loop, proj_shift) <
+        return std::tie(dev, work, prec, variant, trial_passes, ksteps, n, na, nb, host_loop, proj_shift, eta) <
                std::tie(o.dev, o.work, o.prec, o.variant, o.trial_passes, o.ksteps, o.n, o.na, o.nb,
-                        o.host_loop, o.proj_shift);
+                        o.host_loop, o.proj_shift, o.eta);
     }
 };
 
@@ -157,7 +157,7 @@ int solve_impl(const scg_geometry* g, int variant, int precision, const scg_para
     // device after every body (no host round trip per iteration).  Fallback:
     // one graph per body, launched in batches and polled one batch ahead.
     GraphKey key{dev, work, precision, variant, pg.trial_passes, pg.ksteps, g->n, g->n_angles, g->n_bins,
-                 prm->host_loop ? 1 : 0, pl.proj_shift};
+                 prm->host_loop ? 1 : 0, pl.proj_shift, pg.eta ? 1 : 0};
     BodyGraph bg{nullptr, 0, false};
     {
         std::lock_guard<std::mutex> lk(g_mu);
@@ -593,12 +593,12 @@ BatchPlan make_batch_plan(const scg_problem* pr, int count, int variant, int pre
 struct BatchKey {
     int dev;
     const void* work;
-    int prec, variant, trial_passes, ksteps, cap_probs, nb_cap;
+    int prec, variant, trial_passes, ksteps, cap_probs, nb_cap, eta;
     int cap_items[K_COUNT];
     bool operator<(const BatchKey& o) const {
-        return std::tie(dev, work, prec, variant, trial_passes, ksteps, cap_probs, nb_cap, cap_items[0],
+        return std::tie(dev, work, prec, variant, trial_passes, ksteps, cap_probs, nb_cap, eta, cap_items[0],
                         cap_items[1], cap_items[2], cap_items[3], cap_items[4]) <
-               std::tie(o.dev, o.work, o.prec, o.variant, o.trial_passes, o.ksteps, o.cap_probs, o.nb_cap,
+               std::tie(o.dev, o.work, o.prec, o.variant, o.trial_passes, o.ksteps, o.cap_probs, o.nb_cap, o.eta,
                         o.cap_items[0], o.cap_items[1], o.cap_items[2], o.cap_items[3], o.cap_items[4]);
     }
 };
@@ -690,7 +690,7 @@ int batch_impl(const scg_problem* pr, int count, int variant, int precision, con
 
     BatchState* bsd = reinterpret_cast<BatchState*>(base + bp.state);
     BatchKey key{dev, work, precision, variant, pg.trial_passes, pg.ksteps, bp.cap_probs, bp.nb_cap,
-                 {grid[0], grid[1], grid[2], grid[3], grid[4]}};
+                 pg.eta ? 1 : 0, {grid[0], grid[1], grid[2], grid[3], grid[4]}};
     BodyGraph bg{nullptr, 0, false};
     {
         std::lock_guard<std::mutex> lk(g_mu);
@@ -839,6 +839,7 @@ void scg_default_params(scg_params* p) {
     p->filter_gain = 1.0;
     p->max_iter = 100;
     p->host_loop = 0;
+    p->eta0 = 0.0;
 }
 
 size_t scg_op_workspace_bytes(const scg_geometry* g, int precision) {
@@ -907,11 +908,7 @@ int scg_solve(const scg_geometry* g, int variant, int precision, const scg_param
               scg_state* final_state, void* stream) {
     if (!valid_geometry(g) || !prm || !y || !x_out || !work || !res) return SCG_ERR_INVALID;
     if (variant < SCG_CG || variant > SCG_S_PCG_K) return SCG_ERR_INVALID;
-    if (!(eps > 0.0) || !isfinite(eps) || prm->max_iter < 0 || prm->max_iter > 10000000 ||
-        prm->max_trials < 1 || prm->max_trials > 100000 || prm->K < 1 || prm->K > 1000 ||
-        !(prm->a > 0.0 && prm->a < 1.0) || !(prm->filter_gain > 0.0))
-        return SCG_ERR_INVALID;
-    if (prm->perturb != SCG_PERTURB_NONE && prm->perturb != SCG_PERTURB_GAMMA) return SCG_ERR_INVALID;
+    if (!(eps > 0.0) || !isfinite(eps) || !valid_params(prm)) return SCG_ERR_INVALID;
     if (prm->host_loop != 0 && prm->host_loop != 1) return SCG_ERR_INVALID;
     if (resume && resume->valid != 1) return SCG_ERR_INVALID;
     if (!valid_prec(precision) || !solve_supported(variant, precision)) return SCG_ERR_UNSUPPORTED;
@@ -999,10 +996,7 @@ int scg_solve_batch(const scg_problem* problems, int count, int variant, int pre
                     void* stream) {
     if (!problems || count < 1 || count > 65536 || !prm || !work || !results) return SCG_ERR_INVALID;
     if (variant < SCG_CG || variant > SCG_S_PCG_K) return SCG_ERR_INVALID;
-    if (prm->max_iter < 0 || prm->max_iter > 10000000 || prm->max_trials < 1 || prm->max_trials > 100000 ||
-        prm->K < 1 || prm->K > 1000 || !(prm->a > 0.0 && prm->a < 1.0) || !(prm->filter_gain > 0.0))
-        return SCG_ERR_INVALID;
-    if (prm->perturb != SCG_PERTURB_NONE && prm->perturb != SCG_PERTURB_GAMMA) return SCG_ERR_INVALID;
+    if (!valid_params(prm)) return SCG_ERR_INVALID;
     if (prm->host_loop != 0) return SCG_ERR_UNSUPPORTED;
     for (int i = 0; i < count; ++i) {
         const scg_problem& p = problems[i];

@@ -16,7 +16,7 @@ from . import build as _build
 
 F64, F32, F16, BF16 = 0, 1, 2, 3
 VARIANTS = {"CG": 0, "PCG": 1, "S-CG": 2, "S-CG-CD": 3, "S-CG-K": 4, "S-PCG": 5, "S-PCG-K": 6}
-PERTURB = {"none": 0, "gamma": 1}
+PERTURB = {"none": 0, "gamma": 1, "eta": 2}
 STATUS = {0: "ok", 1: "max_iter", -1: "invalid", -2: "cuda", -3: "workspace", -4: "breakdown",
           -5: "unsupported"}
 TRACE_FIELDS = ("k", "f_test", "tv_before", "tv_after", "trials", "accepted", "ell",
@@ -36,7 +36,7 @@ class Params(ctypes.Structure):
                 ("gamma0_rel", ctypes.c_double), ("a", ctypes.c_double),
                 ("max_trials", ctypes.c_int), ("K", ctypes.c_int), ("k_inclusive", ctypes.c_int),
                 ("mu", ctypes.c_double), ("filter_gain", ctypes.c_double),
-                ("max_iter", ctypes.c_int), ("host_loop", ctypes.c_int)]
+                ("max_iter", ctypes.c_int), ("host_loop", ctypes.c_int), ("eta0", ctypes.c_double)]
 
 
 class Result(ctypes.Structure):
@@ -280,7 +280,7 @@ def default_params(**kw) -> dict:
     p = Params()
     load().scg_default_params(ctypes.byref(p))
     d = {name: getattr(p, name) for name, _ in Params._fields_}
-    d["perturb"] = "gamma" if d["perturb"] == 1 else "none"
+    d["perturb"] = {v: k for k, v in PERTURB.items()}[d["perturb"]]
     d.update(kw)
     return d
 
@@ -288,7 +288,7 @@ def default_params(**kw) -> dict:
 def _params(d: dict) -> Params:
     return Params(PERTURB[d["perturb"]], float(d["gamma0"]), float(d["gamma0_rel"]), float(d["a"]),
                   int(d["max_trials"]), int(d["K"]), int(d["k_inclusive"]), float(d["mu"]),
-                  float(d["filter_gain"]), int(d["max_iter"]), int(d["host_loop"]))
+                  float(d["filter_gain"]), int(d["max_iter"]), int(d["host_loop"]), float(d["eta0"]))
 
 
 @dataclass

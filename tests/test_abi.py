@@ -78,6 +78,24 @@ def test_invalid_arguments_rejected_before_any_launch(lib):
                          1 << 30, ctypes.byref(res), None, 0, None, None, None) == -1
 
 
+def test_eta_rule_needs_a_positive_eta0(lib):
+    g = scg.geometry(64, 90, 95)
+    fake = ctypes.c_void_p(256)
+    res = scg.Result()
+    for e0 in (0.0, -1.0, float("inf")):
+        p = scg._params(scg.default_params(perturb="eta", eta0=e0))
+        assert lib.scg_solve(ctypes.byref(g), scg.VARIANTS["S-CG"], scg.F32, ctypes.byref(p), 1.0, fake, None,
+                             fake, fake, 1 << 40, ctypes.byref(res), None, 0, None, None, None) == -1
+    p = scg._params(scg.default_params(perturb="eta", eta0=0.0))
+    pr = (scg.Problem * 1)()
+    pr[0].geometry = g
+    pr[0].eps = 1.0
+    pr[0].y = fake
+    pr[0].x_out = fake
+    assert lib.scg_solve_batch(pr, 1, scg.VARIANTS["S-CG"], scg.F32, ctypes.byref(p), fake, 1 << 40,
+                               (scg.Result * 1)(), None) == -1
+
+
 def test_filter_length_limit_rejected_before_any_launch(lib):
     # the row filter holds a padded row pair's FFT in shared memory: n_bins above
     # 8192 (FP32 arithmetic) or 4096 (FP64) is refused by every entry point that

@@ -126,7 +126,8 @@ def test_trial_passes_decide_like_the_oracle(small, gamma0_rel, a, max_trials, d
     r = gpu_solve(small, dtype, **kw)
     assert r.status == ro["status"] and r.iters == ro["iters"] and r.ell == ro["ell"]
     np.testing.assert_array_equal(r.trace[:, DECISION], to[:, DECISION])
-    assert rel(r.x.cpu().numpy(), xo) <= (1e-9 if dtype == torch.float64 else FP32_BOUND["S-CG"])
+    # FP32: ~3x the 1.0e-5 measured for (0.5, 0.975, 31), whose first steps reject whole passes
+    assert rel(r.x.cpu().numpy(), xo) <= (1e-9 if dtype == torch.float64 else 3e-5)
 
 
 @pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-11), (torch.float32, 1e-5)])
