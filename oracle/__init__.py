@@ -143,6 +143,9 @@ def lib():
         L.orc_norm_A.restype = d
         L.orc_perturb_gamma.argtypes = [i, dp, d, d, i, ctypes.POINTER(ctypes.c_longlong), dp, dp, ip]
         L.orc_perturb_gamma.restype = i
+        L.orc_tv_prox.argtypes = [i, dp, d, i, i, dp, dp, dp]
+        L.orc_fista.argtypes = [i, i, i, dp, dp, d, d, d, i, i, i, dp, ctypes.POINTER(Result), dp, i]
+        L.orc_fista.restype = i
         L.orc_solve.argtypes = [i, i, i, dp, dp, ctypes.POINTER(Params), dp,
                                 ctypes.POINTER(Result), dp, i, ITER_CB, ctypes.c_void_p,
                                 ctypes.POINTER(State), ctypes.POINTER(State)]
@@ -285,6 +288,40 @@ def perturb_gamma(x: np.ndarray, gamma0: float, a: float, max_trials: int, ell: 
     rc = lib().orc_perturb_gamma(n, _dp(x), float(gamma0), float(a), int(max_trials), ctypes.byref(e),
                                  _dp(xh), ctypes.byref(g), ctypes.byref(t))
     return xh, int(e.value), float(g.value), int(t.value), int(rc)
+
+
+def tv_prox(b: np.ndarray, alpha: float, iters: int, accel: bool = True, want_dual: bool = False):
+    """prox of alpha TV at b by ``iters`` FGP steps (plain gradient projection
+    with ``accel=False``); with ``want_dual`` also the dual field (p, q) on the
+    (N-1)^2 interior terms."""
+    b = _f64(b)
+    n = b.shape[0]
+    x = np.zeros_like(b)
+    p = np.zeros((n - 1, n - 1))
+    q = np.zeros((n - 1, n - 1))
+    lib().orc_tv_prox(n, _dp(b), float(alpha), int(iters), int(bool(accel)), _dp(x), _dp(p), _dp(q))
+    return (x, p, q) if want_dual else x
+
+
+def fista(y: np.ndarray, n: int, eps: float, lam: float, c2: float, prox_iters: int = 20,
+          accel: bool = True, max_iter: int = 100, x0=None):
+    """FISTA (ISTA with ``accel=False``) with the TV prox; returns (x, result
+    dict, trace [iters, 12]: k, -, -, TV(x_k), -, -, -, -, t_k, beta)."""
+    y = _f64(y)
+    na, nb = y.shape
+    x = np.zeros((n, n))
+    res = Result()
+    rows = max(int(max_iter), 1)
+    trace = np.zeros((rows, len(TRACE_FIELDS)))
+    x0p = _dp(_f64(x0)) if x0 is not None else None
+    keep = _f64(x0) if x0 is not None else None
+    if keep is not None:
+        x0p = _dp(keep)
+    rc = lib().orc_fista(n, na, nb, _dp(y), x0p, float(eps), float(lam), float(c2), int(prox_iters),
+                         int(bool(accel)), int(max_iter), _dp(x), ctypes.byref(res), _dp(trace), rows)
+    out = dict(iters=res.iters, status=STATUS.get(res.status, res.status), f_final=res.f_final,
+               tv_final=res.tv_final, rc=rc)
+    return x, out, trace[: min(res.iters, rows)].copy()
 
 
 def default_params(**kw) -> dict:

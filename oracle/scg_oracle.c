@@ -932,3 +932,175 @@ int orc_solve(int n, int na, int nb, const double* y, const double* x0,
     free(xz);
     return st;
 }
+
+/* ------------------------------------------------------------------------ */
+/* FISTA with a TV proximal operator (Sec. 2: Eq. prox, Eq. FISTA,           */
+/* Eq. FISTA-u), the paper's comparison method.                              */
+/*                                                                           */
+/* TV as a maximum over a dual field: with the interior terms               */
+/* (i, j), i, j < N-1, and L x = (x[i+1,j] - x[i,j], x[i,j+1] - x[i,j]) per  */
+/* term, TV(x) = max <L x, w> over fields w = (p, q) with p^2 + q^2 <= 1 at  */
+/* every term.  The prox of alpha TV at b is then x = b - alpha L^T w*, where */
+/* w* minimises ||b - alpha L^T w||^2 over that set: the fast gradient      */
+/* projection (FGP) of Beck and Teboulle (2009) solves this dual with a      */
+/* gradient step 1/(8 alpha) (||L||^2 <= 8), projection of each term's (p,q) */
+/* onto the unit disk, and Nesterov momentum, starting from w = 0.           */
+/* Pinned by: a hand-worked 2 x 2 prox in closed form, the duality gap of    */
+/* a long FGP run, plain gradient projection converging to the same point.   */
+/* ------------------------------------------------------------------------ */
+/* L x at every interior term: p = vertical, q = horizontal difference;
+ * arrays of (n-1)^2 terms, row-major. */
+static void tv_L(int n, const double* x, double* p, double* q)
+{
+    int m = n - 1;
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) {
+            double x0 = x[(size_t)i * n + j];
+            p[(size_t)i * m + j] = x[(size_t)(i + 1) * n + j] - x0;
+            q[(size_t)i * m + j] = x[(size_t)i * n + j + 1] - x0;
+        }
+}
+
+/* L^T (p, q): each term sends -(p + q) to its pixel, +p to the pixel below,
+ * +q to the pixel on the right. */
+static void tv_LT(int n, const double* p, const double* q, double* out)
+{
+    int m = n - 1;
+    for (size_t k = 0; k < (size_t)n * n; ++k) out[k] = 0.0;
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) {
+            double pv = p[(size_t)i * m + j], qv = q[(size_t)i * m + j];
+            out[(size_t)i * n + j] -= pv + qv;
+            out[(size_t)(i + 1) * n + j] += pv;
+            out[(size_t)i * n + j + 1] += qv;
+        }
+}
+
+/* prox_{alpha TV}(b) by `iters` FGP steps (accel = 1) or plain gradient
+ * projection steps (accel = 0).  The final dual field is returned in
+ * p_out, q_out when they are not NULL. */
+void orc_tv_prox(int n, const double* b, double alpha, int iters, int accel, double* x_out,
+                 double* p_out, double* q_out)
+{
+    size_t J = (size_t)n * n, T = (size_t)(n - 1) * (n - 1);
+    if (!(alpha > 0.0) || n < 2) {
+        memcpy(x_out, b, sizeof(double) * J);
+        if (p_out) memset(p_out, 0, sizeof(double) * T);
+        if (q_out) memset(q_out, 0, sizeof(double) * T);
+        return;
+    }
+    double* p = vec(T);      /* w_k          */
+    double* q = vec(T);
+    double* pr = vec(T);     /* r_k: the point the gradient step is taken from */
+    double* qr = vec(T);
+    double* pn = vec(T);
+    double* qn = vec(T);
+    double* lp = vec(T);
+    double* lq = vec(T);
+    double* w = vec(J);
+    double t = 1.0;
+    for (int k = 0; k < iters; ++k) {
+        tv_LT(n, pr, qr, w);                                  /* w = b - alpha L^T r */
+        for (size_t e = 0; e < J; ++e) w[e] = b[e] - alpha * w[e];
+        tv_L(n, w, lp, lq);
+        for (size_t e = 0; e < T; ++e) {                      /* gradient step, projection */
+            double a = pr[e] + lp[e] / (8.0 * alpha);
+            double c = qr[e] + lq[e] / (8.0 * alpha);
+            double nrm = sqrt(a * a + c * c);
+            double s = nrm > 1.0 ? nrm : 1.0;
+            pn[e] = a / s;
+            qn[e] = c / s;
+        }
+        if (accel) {
+            double t1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+            double beta = (t - 1.0) / t1;
+            for (size_t e = 0; e < T; ++e) {
+                pr[e] = pn[e] + beta * (pn[e] - p[e]);
+                qr[e] = qn[e] + beta * (qn[e] - q[e]);
+            }
+            t = t1;
+        } else {
+            memcpy(pr, pn, sizeof(double) * T);
+            memcpy(qr, qn, sizeof(double) * T);
+        }
+        memcpy(p, pn, sizeof(double) * T);
+        memcpy(q, qn, sizeof(double) * T);
+    }
+    tv_LT(n, p, q, w);                                        /* x = b - alpha L^T w */
+    for (size_t e = 0; e < J; ++e) x_out[e] = b[e] - alpha * w[e];
+    if (p_out) memcpy(p_out, p, sizeof(double) * T);
+    if (q_out) memcpy(q_out, q, sizeof(double) * T);
+    free(p); free(q); free(pr); free(qr); free(pn); free(qn); free(lp); free(lq); free(w);
+}
+
+/* FISTA (Eq. FISTA, Eq. FISTA-u):
+ *   x_k = prox_{lambda/c^2, TV}(u_k + (1/c^2) A^T (y - A u_k)),
+ *   u_{k+1} = x_k + ((t_k - 1)/t_{k+1}) (x_k - x_{k-1}),
+ *   t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2,  t_1 = 1,  u_1 = x_0,
+ * stopped, like the other methods of Sec. 4, at the first x_k with
+ * f(x_k) <= eps (or after max_iter iterations); the output is that x_k.
+ * c2 = c^2 = ||A||_2^2.  accel = 0 drops the momentum (ISTA, Eq. ISTA).
+ * Trace rows (ORC_NF): k, f(x_k), TV(x_k), t_k, beta = (t_k-1)/t_{k+1}. */
+int orc_fista(int n, int na, int nb, const double* y, const double* x0, double eps, double lambda,
+              double c2, int prox_iters, int accel, int max_iter, double* x_out, orc_result* res,
+              double* trace, int trace_rows)
+{
+    if (n < 2 || na <= 0 || nb <= 0 || !y || !x_out || !res || !(c2 > 0.0) || lambda < 0.0 ||
+        prox_iters < 0 || max_iter < 0 || !(eps > 0.0))
+        return ORC_ERR_INVALID;
+    size_t J = (size_t)n * n, L = (size_t)na * nb;
+    double* x = vec(J);        /* x_k      */
+    double* xp = vec(J);       /* x_{k-1}  */
+    double* u = vec(J);
+    double* g = vec(J);
+    double* bvec = vec(J);
+    double* sino = vec(L);
+    memset(res, 0, sizeof(*res));
+    if (x0) memcpy(x, x0, sizeof(double) * J);
+    memcpy(u, x, sizeof(double) * J);                        /* u_1 = x_0 */
+    double t = 1.0;
+    int it = 0, status = ORC_OK;
+    for (;;) {
+        orc_project(n, na, nb, x, sino);                      /* f(x_k) */
+        double f = 0.0;
+        for (size_t e = 0; e < L; ++e) {
+            double r = y[e] - sino[e];
+            f += r * r;
+        }
+        f *= 0.5;
+        if (!(f > eps)) break;
+        if (it >= max_iter) { status = ORC_MAX_ITER; break; }
+        orc_project(n, na, nb, u, sino);                      /* A^T (y - A u_k) */
+        for (size_t e = 0; e < L; ++e) sino[e] = y[e] - sino[e];
+        orc_backproject(n, na, nb, sino, g);
+        for (size_t e = 0; e < J; ++e) bvec[e] = u[e] + g[e] / c2;
+        memcpy(xp, x, sizeof(double) * J);
+        orc_tv_prox(n, bvec, lambda / c2, prox_iters, 1, x, NULL, NULL);   /* x_k */
+        double t1 = accel ? 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t)) : 1.0;
+        double beta = accel ? (t - 1.0) / t1 : 0.0;
+        for (size_t e = 0; e < J; ++e) u[e] = x[e] + beta * (x[e] - xp[e]);   /* u_{k+1} */
+        double* tr = row_of(trace, trace_rows, it);
+        if (tr) {
+            tr[ORC_T_K] = it + 1;
+            tr[ORC_T_TV_AFTER] = orc_tv(n, x);
+            tr[ORC_T_ALPHA] = t;
+            tr[ORC_T_BETA] = beta;
+        }
+        t = t1;
+        ++it;
+    }
+    memcpy(x_out, x, sizeof(double) * J);
+    res->iters = it;
+    res->k_final = it;
+    res->status = status;
+    orc_project(n, na, nb, x, sino);
+    double f = 0.0;
+    for (size_t e = 0; e < L; ++e) {
+        double r = y[e] - sino[e];
+        f += r * r;
+    }
+    res->f_final = 0.5 * f;
+    res->tv_final = orc_tv(n, x);
+    free(x); free(xp); free(u); free(g); free(bvec); free(sino);
+    return status;
+}

@@ -133,6 +133,12 @@ void orc_fbp(int n, int na, int nb, const double* y, double* x);
 int orc_perturb_gamma(int n, const double* x, double gamma0, double a, int max_trials,
                       long long* ell, double* x_half, double* gamma_out, int* trials_out);
 
+void orc_tv_prox(int n, const double* b, double alpha, int iters, int accel, double* x_out,
+                 double* p_out, double* q_out);
+int orc_fista(int n, int na, int nb, const double* y, const double* x0, double eps, double lambda,
+              double c2, int prox_iters, int accel, int max_iter, double* x_out, orc_result* res,
+              double* trace, int trace_rows);
+
 int orc_solve(int n, int na, int nb, const double* y, const double* x0,
               const orc_params* prm, double* x_out, orc_result* res,
               double* trace, int trace_rows, orc_iter_cb cb, void* user,
