@@ -555,10 +555,31 @@ def batch_block(args, dev, rank, world, count, dtype_name, steps, warmup):
 
     solo, t_solo = one_by_one(ys, dtype)
     same = all(a.iters == b.iters and a.tv_final == b.tv_final for a, b in zip(rb, solo))
+    fp32_batch = None
     if dtype == torch.float32:
         solo32, t_solo32 = solo, t_solo
     else:
         solo32, t_solo32 = one_by_one(ys32, torch.float32)
+        # the same batch in FP32 storage: results bit-identical to the FP32 solo solves
+        nb32 = scg.batch_workspace_bytes([(w.n, w.n_angles, w.n_bins) for w in works], variant, torch.float32)
+        wsp32 = torch.empty(nb32, dtype=torch.uint8, device=dev)
+        o32 = [torch.empty((n, n), dtype=torch.float32, device=dev) for n in ns]
+        r32 = scg.scg_solve_batch(ys32, ns, variant, eps, outs=o32, work=wsp32, **kw)
+        torch.cuda.synchronize()
+        ms32 = []
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r32 = scg.scg_solve_batch(ys32, ns, variant, eps, outs=o32, work=wsp32, **kw)
+            e1.record(stream)
+            e1.synchronize()
+            ms32.append(e0.elapsed_time(e1))
+        t32 = max_over_ranks(float(np.mean(ms32)) / 1e3, world, dev)
+        fp32_batch = {"value": job_rate(len(works), world, t32), "unit": UNIT, "ms_per_batch": 1e3 * t32,
+                      "speedup_vs_fp32_solo": t_solo32 / t32,
+                      "same_iters_and_tv_as_fp32_solo": bool(all(a.iters == b.iters and a.tv_final == b.tv_final
+                                                                 for a, b in zip(r32, solo32)))}
+        del wsp32
     value = job_rate(len(works), world, t_batch)
     return {"metric": "batched recon/s", "value": value, "unit": UNIT, "dtype": dtype_name,
             "ms_per_batch": 1e3 * t_batch, "steps": steps, "warmup": warmup, "step_ms": ms,
@@ -569,7 +590,7 @@ def batch_block(args, dev, rank, world, count, dtype_name, steps, warmup):
             "solo_same_storage": {"value": len(works) / t_solo, "unit": UNIT, "same_iters_and_tv": bool(same)},
             "solo_fp32": {"value": len(works) / t_solo32, "unit": UNIT},
             "speedup_vs_fp32_solo": t_solo32 / t_batch,
-            "equal_eps_and_tv": _same_eps_tv(rb, solo32, eps), "clocks": clk}
+            "equal_eps_and_tv": _same_eps_tv(rb, solo32, eps), "fp32_batch": fp32_batch, "clocks": clk}
 
 
 def serving_block(args, dev, rank, rate, duration, warm, dtype_name):

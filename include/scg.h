@@ -65,7 +65,20 @@ typedef enum {
     SCG_S_CG_CD = 3,  /* Algorithm 9 (steps: CG-CD-STEP, Algorithm 10)           */
     SCG_S_CG_K = 4,   /* Algorithm 5 (calls CG-K, Algorithm 6)                   */
     SCG_S_PCG = 5,    /* Algorithm 13 (steps: PCG-PR-STEP, Algorithm 14)         */
-    SCG_S_PCG_K = 6   /* Algorithm 11 (calls PCG-K, Algorithm 12)                */
+    SCG_S_PCG_K = 6,  /* Algorithm 11 (calls PCG-K, Algorithm 12)                */
+    SCG_FISTA = 7     /* the comparison method of Sec. 4: FISTA (Sec. 2, Eq. FISTA
+                         and Eq. FISTA-u) for f(x) + lambda TV(x),
+                         x_k = prox_{lambda/c^2, TV}(u_k + A^T(y - A u_k)/c^2),
+                         u_{k+1} = x_k + ((t_k - 1)/t_{k+1})(x_k - x_{k-1}),
+                         t_{k+1} = (1 + sqrt(1 + 4 t_k^2))/2, t_1 = 1, u_1 = x_0;
+                         the prox (Eq. prox) by prox_iters steps of Beck and
+                         Teboulle's fast gradient projection on TV's dual, from
+                         zero; stopped at the first x_k with f(x_k) <= eps (as
+                         the paper's Sec. 4 stops every method) or max_iter.
+                         scg_solve only (FP32/FP64; no resume, no final_state);
+                         scg_solve_batch and the server return
+                         SCG_ERR_UNSUPPORTED.  Trace rows: k, f(x_k) in field
+                         11, t_k in field 8, (t_k - 1)/t_{k+1} in field 9.   */
 } scg_variant;
 
 typedef enum {
@@ -127,6 +140,12 @@ typedef struct {
                             and polled by the host (same kernels; for tools
                             that profile kernels one launch at a time)          */
     double eta0;         /* SCG_PERTURB_ETA only: eta0 > 0 (default 0)          */
+    double lambda;       /* SCG_FISTA: weight of TV, >= 0 (default 0: no prox)  */
+    int prox_iters;      /* SCG_FISTA: FGP steps per prox, 0 .. 100000 (default 20) */
+    double lipschitz;    /* SCG_FISTA: c^2 = ||A||_2^2 (Appendix, Eq. lambda);
+                            <= 0 (default): estimated on the device by 100 power
+                            iterations on A^T A from 1 + 0.001 (index mod 7) and
+                            cached per device, precision and geometry           */
 } scg_params;
 
 typedef struct {
@@ -143,6 +162,7 @@ typedef struct {
                             launched after the stop flag return at once)         */
     int device_loop;     /* 1: the loop ran as one CUDA graph whose conditional
                             node the device steers; 0: host-polled graph launches */
+    double lipschitz_used; /* SCG_FISTA: the c^2 the solve used (else 0)       */
 } scg_result;
 
 /* Solver state, for exact checkpoint/resume and for single-step checks.  The

@@ -29,8 +29,10 @@ inline int filter_length(int nb) { return filter_length_of(nb); }
 inline int family_of(int v) {
     if (v == SCG_CG || v == SCG_PCG) return FAM_CG;
     if (v == SCG_S_CG_K || v == SCG_S_PCG_K) return FAM_S_K;
+    if (v == SCG_FISTA) return FAM_FISTA;
     return FAM_S_PR;
 }
+inline bool valid_variant(int v) { return v >= SCG_CG && v <= SCG_FISTA; }
 
 inline bool uses_filter(int v) { return v == SCG_PCG || v == SCG_S_PCG || v == SCG_S_PCG_K; }
 
@@ -63,6 +65,9 @@ inline bool valid_params(const scg_params* p) {
     if (p->max_iter < 0 || p->max_iter > 10000000 || p->max_trials < 1 || p->max_trials > 100000 || p->K < 1 ||
         p->K > 1000 || !(p->a > 0.0 && p->a < 1.0) || !(p->filter_gain > 0.0))
         return false;
+    if (!(p->lambda >= 0.0) || !isfinite(p->lambda) || p->prox_iters < 0 || p->prox_iters > 100000 ||
+        !isfinite(p->lipschitz))
+        return false;
     if (p->perturb == SCG_PERTURB_ETA) return p->eta0 > 0.0 && isfinite(p->eta0);
     return p->perturb == SCG_PERTURB_NONE || p->perturb == SCG_PERTURB_GAMMA;
 }
@@ -83,7 +88,7 @@ template <> constexpr int prec_of<__nv_bfloat16>() { return SCG_BF16; }
 // mantissa the cancellation in that update loses the gradient.
 inline bool solve_supported(int variant, int precision) {
     if (precision == SCG_F32 || precision == SCG_F64) return true;
-    return variant != SCG_CG && variant != SCG_PCG;
+    return variant != SCG_CG && variant != SCG_PCG && variant != SCG_FISTA;
 }
 
 // Scale c of the system a solve works on: c A x ~ c y, f scaled by c^2.  CG's
@@ -102,6 +107,7 @@ inline double system_scale(const scg_geometry& g, int precision) {
 struct Plan {
     size_t state, prob, ang, taps, partials, counter, trace;
     size_t img[IB_COUNT];
+    size_t dual[4];
     size_t view_rm, view_cm;
     size_t sino[SB_COUNT];
     size_t total;
@@ -109,6 +115,7 @@ struct Plan {
     int cnt_proj, proj_blocks, proj_shift;
     int cnt_bp;
     int part_cap;           // work items the partial-sum buffer holds per slot
+    int nb;                 // detector bins (the projector's item order depends on them)
 };
 
 // Projector items for the block shape 2^(8-shift) angles x 2^shift rays.
@@ -136,6 +143,7 @@ inline Plan make_plan(const scg_geometry& g, int variant, int precision, int kin
     Plan p;
     memset(&p, 0, sizeof(p));
     const int N = g.n, na = g.n_angles, nb = g.n_bins;
+    p.nb = nb;
     p.S = round_up4(N + 2 * kPad);          // pairs per view line
     p.SB = round_up4(nb + 2 * kSPad);       // pairs per sinogram-view row
     p.ray_blocks = (nb + kRayBlock - 1) / kRayBlock;
@@ -169,12 +177,28 @@ inline Plan make_plan(const scg_geometry& g, int variant, int precision, int kin
     const size_t sino_bytes = 2 * tsize * (size_t)na * p.SB;
     for (int q = 0; q < IB_COUNT; ++q) p.img[q] = (size_t)-1;
     for (int q = 0; q < SB_COUNT; ++q) p.sino[q] = (size_t)-1;
+    for (int q = 0; q < 4; ++q) p.dual[q] = (size_t)-1;
     if (kind == PLAN_OP) {
         p.trace = (size_t)-1;
         p.sino[SB_R] = take(sino_bytes);
     } else {
         p.trace = take(sizeof(double) * TR_NF * kMaxTraceRows);
         const int fam = family_of(variant);
+        if (fam == FAM_FISTA) {                 // x in three slots, b, A^T r, the dual fields, A x in three slots
+            p.img[IB_X] = take(tsize * J);
+            p.img[IB_XH] = take(tsize * J);
+            p.img[IB_P] = take(tsize * J);
+            p.img[IB_H] = take(tsize * J);
+            p.img[IB_G] = take(tsize * J);
+            p.img[IB_Z] = take(tsize * J);
+            for (int q = 0; q < 4; ++q) p.dual[q] = take(2 * tsize * J);
+            p.sino[SB_R] = take(sino_bytes);
+            p.sino[SB_Q] = take(sino_bytes);
+            p.sino[SB_W] = take(sino_bytes);
+            p.sino[SB_V] = take(sino_bytes);
+            p.total = off;
+            return p;
+        }
         p.img[IB_X] = take(tsize * J);
         p.img[IB_P] = take(tsize * J);
         p.img[IB_H] = take(tsize * J);
@@ -277,6 +301,8 @@ Prob<T> make_prob(const scg_geometry& g, const Plan& pl, unsigned char* base, do
         P.img[q] = pl.img[q] == (size_t)-1 ? nullptr : reinterpret_cast<E*>(base + pl.img[q]);
     for (int q = 0; q < SB_COUNT; ++q)
         P.sino[q] = pl.sino[q] == (size_t)-1 ? nullptr : reinterpret_cast<E2*>(base + pl.sino[q]);
+    for (int q = 0; q < 4; ++q)
+        P.dual[q] = pl.dual[q] == (size_t)-1 ? nullptr : reinterpret_cast<E2*>(base + pl.dual[q]);
     P.view_rm = reinterpret_cast<E2*>(base + pl.view_rm);
     P.view_cm = reinterpret_cast<E2*>(base + pl.view_cm);
     P.partials = reinterpret_cast<double*>(base + pl.partials);
@@ -316,11 +342,14 @@ struct Runner {
     void trial(int ncand) { ++launches; launch_trial<T>(d, i_bp, g_bp, ncand, s); }
     void axpy(int step) { ++launches; launch_sino_axpy<T>(d, i_ray, g_ray, step, s); }
     void filter(int src, int dst) { ++launches; launch_filter<T>(d, i_row, g_row, nb, src, dst, FILT_VIEW, s); }
+    void sino_comb(int cur, int prev) { ++launches; launch_sino_comb<T>(d, i_ray, g_ray, cur, prev, s); }
+    void fgp(int j, double beta) { ++launches; launch_fgp<T>(d, i_img, g_img, j, beta, s); }
 };
 
 struct Program {
     int variant, trial_passes, ksteps;
     bool eta;          // Appendix rule: the gradient at x_k sizes the perturbation
+    int prox_iters;    // FISTA: FGP steps per prox (0 when lambda = 0: the prox is the identity)
 };
 
 // g'^T p' for the step length: FIN_BETA derives it from the gradient pass's
@@ -331,12 +360,52 @@ struct Program {
 template <typename T>
 constexpr int num_step() { return sizeof(typename Tr<T>::S) < 4 ? FIN_NUM : FIN_NONE; }
 
+// Power iteration for c^2 = ||A^T A||_2 (Appendix, Eq. lambda and Eq. gamma):
+// p <- A^T A p / ||A^T A p|| from the start vector 1 + 0.001 (index mod 7);
+// the device keeps the Rayleigh quotient p^T A^T A p / ||p||^2 as c^2.
+template <typename T>
+void run_power(Runner<T>& R, int iters) {
+    R.vec(VEC_POWER_START, 0, FIN_POWER_NORM);
+    for (int q = 0; q < iters; ++q) {
+        R.project(SB_Q, PROJ_PLAIN, FIN_NONE);         // A p (views written by the vector pass)
+        R.back1(SB_Q, IB_H, FIN_POWER);                // h = A^T A p, c^2, 1/||h||
+        R.vec(VEC_NORMALIZE, 0, FIN_POWER_NORM);       // p = h / ||h||
+    }
+}
+
+// FISTA (Eq. FISTA, Eq. FISTA-u): x_0 is projected once; each iteration forms
+// A u_k - y from the two latest projections, backprojects it, takes the
+// gradient step, the prox by FGP, and projects x_k (stop test, t_{k+1},
+// beta_k).  x_k lives in kFistaX[k % 3] and A x_k in kFistaQ[k % 3]; a loop
+// body holds three iterations so that every buffer choice is static.
+template <typename T>
+void run_fista_iteration(Runner<T>& R, const Program& pg, int k3) {
+    const int cur = (k3 + 2) % 3, prev = (k3 + 1) % 3;    // x_{k-1}, x_{k-2}
+    R.sino_comb(kFistaQ[cur], kFistaQ[prev]);          // A u_k - y
+    R.back1(SB_R, IB_G, FIN_NONE);                     // A^T (A u_k - y)
+    R.vec(VEC_FISTA_B, kFistaX[cur] | (kFistaX[prev] << 4), FIN_NONE);   // b = u_k - A^T(A u_k - y)/c^2
+    double t = 1.0;
+    for (int j = 0; j < pg.prox_iters; ++j) {          // FGP: momentum (t_j - 1)/t_{j+1}, t_1 = 1
+        const double t1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+        R.fgp(j, (t - 1.0) / t1);
+        t = t1;
+    }
+    const int w = pg.prox_iters > 0 ? (pg.prox_iters - 1) & 1 : 2;
+    R.vec(VEC_FGP_FINAL, kFistaX[k3] | (w << 4), FIN_NONE);              // x_k = prox(b), views
+    R.project(kFistaQ[k3], PROJ_FISTA, FIN_FISTA_F);  // A x_k, f(x_k)
+}
+
 // The algorithms' set-up steps (before the first loop test).
 template <typename T>
 void run_init(Runner<T>& R, const Program& pg) {
     const int v = pg.variant, fam = family_of(v);
     const bool pre = uses_filter(v);
     const int dsel = pre ? IB_Z : IB_G;
+    if (fam == FAM_FISTA) {
+        R.vec(VEC_INIT, 0, FIN_NONE);                  // x_0 (u_1 = x_0), views
+        R.project(kFistaQ[0], PROJ_FISTA, FIN_FISTA_F);   // A x_0, f(x_0): first loop test
+        return;
+    }
     R.vec(VEC_INIT, 0, FIN_NONE);                      // x_{1/2} = x0 (S-CG family), x_{-1/2} = x0 (S-K)
     R.project(SB_R, PROJ_RESIDUAL, FIN_F);             // r = A x0 - y, f(x0)
     if (fam == FAM_S_K) {
@@ -358,12 +427,16 @@ void run_init(Runner<T>& R, const Program& pg) {
     R.tvgrad(IB_X, 1, 1, FIN_END);                     // x1 = x0 + alpha p0 (+ dTV(x1)); k = 1; loop test
 }
 
-// One loop body of the variant's while loop.
+// One loop body of the variant's while loop (FISTA: three iterations).
 template <typename T>
 void run_body(Runner<T>& R, const Program& pg) {
     const int v = pg.variant, fam = family_of(v);
     const bool pre = uses_filter(v);
     const int dsel = pre ? IB_Z : IB_G;
+    if (fam == FAM_FISTA) {
+        for (int k3 = 1; k3 <= 3; ++k3) run_fista_iteration<T>(R, pg, k3 % 3);
+        return;
+    }
     if (fam == FAM_CG) {                               // CG-STEP / PCG-STEP
         R.project(SB_Q, PROJ_PLAIN, FIN_NONE);         // A p
         R.back1(SB_Q, IB_H, FIN_CG_ALPHA);             // h = A^T A p, alpha = delta / p^T h
@@ -494,6 +567,9 @@ inline DevState initial_state(const scg_params* prm, double eps, int variant) {
     for (int t = 1; t < kTrials; ++t) st.apow[t] = st.apow[t - 1] * prm->a;
     st.max_trials = prm->max_trials;
     st.eta0 = prm->eta0;
+    st.lam = prm->lambda;
+    st.c2 = prm->lipschitz > 0.0 ? prm->lipschitz : 0.0;
+    st.tk = 1.0;
     st.variant = variant;
     st.family = fam;
     st.in_init = 1;
@@ -506,7 +582,9 @@ inline Program make_program(const scg_params* prm, int variant) {
     pg.variant = variant;
     pg.trial_passes = prm->perturb == SCG_PERTURB_GAMMA ? trial_passes_for(prm->max_trials) : 0;
     pg.ksteps = prm->K + (prm->k_inclusive ? 1 : 0);
-    pg.eta = prm->perturb == SCG_PERTURB_ETA && family_of(variant) != FAM_CG;
+    pg.eta = prm->perturb == SCG_PERTURB_ETA && family_of(variant) != FAM_CG && family_of(variant) != FAM_FISTA;
+    pg.prox_iters = prm->lambda > 0.0 ? prm->prox_iters : 0;
+    if (family_of(variant) == FAM_FISTA) pg.trial_passes = 0;
     return pg;
 }
 
@@ -516,7 +594,11 @@ inline Program make_program(const scg_params* prm, int variant) {
 enum { K_PROJ = 0, K_IMG = 1, K_RAY = 2, K_ROW = 3, K_BP = 4, K_COUNT = 5 };
 
 inline void append_items(const Plan& pl, int prob, std::vector<Item>* lists) {
-    for (int q = 0; q < pl.cnt_proj; ++q) lists[K_PROJ].push_back(Item{prob, q / pl.proj_blocks, q % pl.proj_blocks, q});
+    for (int q = 0; q < pl.cnt_proj; ++q) {            // the single-problem launch's order (proj_item_of)
+        Item it{prob, 0, 0, q};
+        proj_item_of(q, pl.cnt_proj / pl.proj_blocks, pl.proj_blocks, pl.nb, pl.proj_shift, it.u, it.v);
+        lists[K_PROJ].push_back(it);
+    }
     for (int q = 0; q < pl.cnt_img; ++q) lists[K_IMG].push_back(Item{prob, q / pl.tiles_x, q % pl.tiles_x, q});
     for (int q = 0; q < pl.cnt_ray; ++q) lists[K_RAY].push_back(Item{prob, q / pl.ray_blocks, q % pl.ray_blocks, q});
     for (int q = 0; q < pl.cnt_row; ++q) lists[K_ROW].push_back(Item{prob, q / pl.filt_blocks, q % pl.filt_blocks, q});

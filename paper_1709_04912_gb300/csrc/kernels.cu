@@ -36,7 +36,7 @@ __device__ __forceinline__ Item decode_item(const Prob<T>* probs, const Item* it
     if (kind == 0) { it.u = bid / P.ray_blocks; it.v = bid % P.ray_blocks; }
     else if (kind == 1) { it.u = bid / P.tiles_x; it.v = bid % P.tiles_x; }
     else if (kind == 2) { it.u = bid / P.filt_blocks; it.v = bid % P.filt_blocks; }
-    else if (kind == 3) { it.u = bid / P.proj_blocks; it.v = bid % P.proj_blocks; }
+    else if (kind == 3) proj_item_of(bid, P.cnt_proj / P.proj_blocks, P.proj_blocks, P.nb, P.proj_shift, it.u, it.v);
     else { it.u = bid / P.tiles_x; it.v = bid % P.tiles_x; }   // backprojector tiles
     return it;
 }
@@ -272,12 +272,13 @@ k_project(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int
     // the residual's data value, loaded before the walk so that its latency is
     // hidden (y_scale is 1 except for half/bfloat16 storage; the product is exact)
     C yv = C(0);
-    if (valid && mode == PROJ_RESIDUAL) yv = to_c(P.y[(size_t)a * nb + b]) * P.y_scale;
+    if (valid && (mode == PROJ_RESIDUAL || mode == PROJ_FISTA)) yv = to_c(P.y[(size_t)a * nb + b]) * P.y_scale;
     C out = project_ray<T>(P, g, b, valid);                // every lane: the FP32 walk is warp-wide
     if (valid) {
         if (mode == PROJ_RESIDUAL) out = out - yv;
         if (mode == PROJ_PLAIN_OUT) P.user_out[(size_t)a * nb + b] = to_s<typename Tr<T>::S>(out);
         else store_pair<T>(P.sino[dst_sel] + (size_t)a * P.SB + kSPad, b, out * g.inv_m);   // weighted view
+        if (mode == PROJ_FISTA) out = out - yv;          // A x kept, f(x) summed
         v[0] = acc_prod(out, out);
     }
     if (step != FIN_NONE) reduce_and_finalize<T, 1, true>(v, P, it.local, P.cnt_proj, step);
@@ -504,7 +505,7 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
     // block 0's epilogue operands (h and p for the fused dots), loaded before
     // the cluster barriers so that their latency overlaps the hand-over
     const bool want_h = step == FIN_BETA;
-    const bool want_p = step == FIN_BETA || step == FIN_ALPHA || step == FIN_CG_ALPHA;
+    const bool want_p = step == FIN_BETA || step == FIN_ALPHA || step == FIN_CG_ALPHA || step == FIN_POWER;
     C hv[PIX], pv[PIX];
 #pragma unroll
     for (int k = 0; k < PIX; ++k) {
@@ -575,6 +576,9 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
             v[1] = acc_add(v[1], acc_prod(g0, g1));                                       // g^T z
         } else if (step == FIN_ETA) {
             v[0] = acc_add(v[0], acc_prod(g0, g0));                                       // ||g_k||^2
+        } else if (step == FIN_POWER) {
+            v[0] = acc_add(v[0], acc_prod(g0, g0));                                       // ||h||^2
+            v[1] = acc_add(v[1], acc_prod(pv[k], g0));                                    // p^T h
         }
     }
     if (step == FIN_NONE) return;
@@ -692,6 +696,60 @@ k_vec(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int op,
             const C p = to_c(P.img[IB_P][idx]);
             if (P.img[IB_H]) v[0] = acc_prod(p, to_c(P.img[IB_H][idx]));
             if (P.img[IB_G]) v[1] = acc_prod(p, to_c(P.img[IB_G][idx]));
+        }
+        break;
+    }
+    case VEC_POWER_START: {     // the power iteration's start vector 1 + 0.001 (index mod 7)
+        if (in) {
+            val = C(1) + C(0.001) * C((int)(idx % 7));
+            P.img[IB_P][idx] = to_s<S>(val);
+            v[0] = acc_prod(val, val);
+        }
+        write_views(P, it.u, it.v, val, in);
+        break;
+    }
+    case VEC_NORMALIZE: {       // p = h / ||h||
+        const C c = (C)st.coef;
+        if (in) {
+            val = rnd<T>(to_c(P.img[IB_H][idx]) * c);
+            P.img[IB_P][idx] = to_s<S>(val);
+            v[0] = acc_prod(val, val);
+        }
+        write_views(P, it.u, it.v, val, in);
+        break;
+    }
+    case VEC_FISTA_B: {         // b = u_k + A^T (y - A u_k) / c^2, u_k = x_{k-1} + beta (x_{k-1} - x_{k-2})
+        if (in) {
+            const C xc = to_c(P.img[sel & 15][idx]), xp = to_c(P.img[sel >> 4][idx]);
+            const C u = fma((C)st.beta, xc - xp, xc);
+            P.img[IB_Z][idx] = to_s<S>(u - to_c(P.img[IB_G][idx]) * (C)(1.0 / st.c2));
+        }
+        break;
+    }
+    case VEC_FGP_FINAL: {       // x_k = b - (lambda / c^2) L^T w (the prox of Eq. FISTA)
+        const int w = sel >> 4;
+        if (in) {
+            val = to_c(P.img[IB_Z][idx]);
+            if (w < 2) {
+                const auto* D = P.dual[w];
+                const int m = N - 1;
+                C lt = C(0);                                        // (L^T w) at pixel (i, j)
+                if (i < m && j < m) { const auto e = D[idx]; lt -= to_c(e.x) + to_c(e.y); }
+                if (i > 0 && j < m) lt += to_c(D[idx - N].x);
+                if (j > 0 && i < m) lt += to_c(D[idx - 1].y);
+                val = fma(-(C)(st.lam / st.c2), lt, val);
+            }
+            P.img[sel & 15][idx] = to_s<S>(val);
+        }
+        write_views(P, it.u, it.v, val, in);
+        break;
+    }
+    case VEC_FISTA_OUT: {       // the output x_k, from the buffer of k mod 3
+        if (in) {
+            const int ks = st.k % 3;
+            const S xv = P.img[ks == 0 ? IB_X : ks == 1 ? IB_XH : IB_P][idx];   // kFistaX[k % 3]
+            P.img[IB_Z][idx] = xv;
+            if (P.user_out) P.user_out[idx] = xv;
         }
         break;
     }
@@ -971,6 +1029,107 @@ k_sino_axpy(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, i
     reduce_and_finalize<T, 1, true>(v, P, it.local, P.cnt_ray, step);
 }
 
+// FISTA's gradient residual A u_k - y on the sinogram views, without
+// projecting u_k: u_k = x_{k-1} + beta (x_{k-1} - x_{k-2}) is linear in the
+// iterates, so A u_k = (1 + beta) A x_{k-1} - beta A x_{k-2} from the two
+// projections already taken (views hold v / m_a, so y is weighted alike).
+template <typename T>
+__global__ void __launch_bounds__(kRayBlock)
+k_sino_comb(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int cur, int prev) {
+    const Item it = decode_item(probs, items, 0);
+    const Prob<T>& P = probs[it.prob];
+    const DevState& st = *P.st;
+    if (st.done) return;
+    using C = typename Tr<T>::C;
+    const int a = it.u, b = it.v * kRayBlock + threadIdx.x;
+    if (b >= P.nb) return;
+    const size_t o = (size_t)a * P.SB + kSPad;
+    const C beta = (C)st.beta;
+    const C qc = to_c(P.sino[cur][o + b].x), qp = to_c(P.sino[prev][o + b].x);
+    const C yw = to_c(P.y[(size_t)a * P.nb + b]) * P.y_scale * P.ang[a].inv_m;
+    store_pair<T>(P.sino[SB_R] + o, b, fma(beta, qc - qp, qc) - yw);
+}
+
+// One step of the fast gradient projection (Beck and Teboulle) for the dual
+// of FISTA's TV prox at b (= img[IB_Z]) with alpha = lambda / c^2: with r the
+// momentum point, w = b - alpha L^T r at every pixel, then per interior term
+// w_j = proj_{|.| <= 1}(r + L w / (8 alpha)) and the next momentum point
+// r' = w_j + beta_j (w_j - w_{j-1}).  dual[j % 2] receives w_j (w_{j-1} is
+// read from the other), dual[2 + (j+1) % 2] receives r' (r is read from
+// dual[2 + j % 2]); step j = 0 starts from r = w_{-1} = 0.  A block takes the
+// 8 x 32 terms of an image tile; r is staged with a one-term halo and w on the
+// tile's pixels plus one row and column.
+template <typename T>
+__global__ void __launch_bounds__(kTileThreads)
+k_fgp(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int j, typename Tr<T>::C beta) {
+    using C = typename Tr<T>::C;
+    using C2 = typename Vec2<C>::type;
+    if constexpr (!std::is_same<typename Tr<T>::S, C>::value) {
+        return;                                              // FISTA runs in FP32 / FP64 storage only
+    } else {
+    const Item it = decode_item(probs, items, 1);
+    const Prob<T>& P = probs[it.prob];
+    const DevState& st = *P.st;
+    if (st.done) return;
+    __shared__ C2 rs[kTileH + 2][kTileW + 2];
+    __shared__ C ws[kTileH + 1][kTileW + 1];
+    const int N = P.n, m = N - 1;
+    const int i0 = it.u * kTileH, j0 = it.v * kTileW;
+    const C alpha = (C)(st.lam / st.c2);
+    const C inv8a = C(1) / (C(8) * alpha);
+    const bool start = j == 0;
+    const C2* R = reinterpret_cast<const C2*>(P.dual[2 + (j & 1)]);
+    const C2* Wold = reinterpret_cast<const C2*>(P.dual[(j + 1) & 1]);
+    C2* Wnew = reinterpret_cast<C2*>(P.dual[j & 1]);
+    C2* Rnext = reinterpret_cast<C2*>(P.dual[2 + ((j + 1) & 1)]);
+    for (int q = threadIdx.x; q < (kTileH + 2) * (kTileW + 2); q += kTileThreads) {
+        const int ii = q / (kTileW + 2), jj = q % (kTileW + 2);
+        const int ti = i0 - 1 + ii, tj = j0 - 1 + jj;
+        C2 v;
+        v.x = C(0);
+        v.y = C(0);
+        if (!start && ti >= 0 && ti < m && tj >= 0 && tj < m) v = R[(size_t)ti * N + tj];
+        rs[ii][jj] = v;
+    }
+    __syncthreads();
+    const C* B = P.img[IB_Z];
+    for (int q = threadIdx.x; q < (kTileH + 1) * (kTileW + 1); q += kTileThreads) {
+        const int ii = q / (kTileW + 1), jj = q % (kTileW + 1);
+        const int a = i0 + ii, b = j0 + jj;
+        C w = C(0);
+        if (a < N && b < N) {
+            // (L^T r) at pixel (a, b): -(p + q) of term (a, b), +p of (a-1, b), +q of (a, b-1)
+            const C lt = -(rs[ii + 1][jj + 1].x + rs[ii + 1][jj + 1].y) + rs[ii][jj + 1].x + rs[ii + 1][jj].y;
+            w = fma(-alpha, lt, B[(size_t)a * N + b]);
+        }
+        ws[ii][jj] = w;
+    }
+    __syncthreads();
+    const int ty = threadIdx.x / kTileW, tx = threadIdx.x % kTileW;
+    const int i = i0 + ty, jc = j0 + tx;
+    if (i >= m || jc >= m) return;
+    const C w0 = ws[ty][tx];
+    const C2 r = rs[ty + 1][tx + 1];
+    const C ax = fma(ws[ty + 1][tx] - w0, inv8a, r.x);      // r + (L w) / (8 alpha)
+    const C ay = fma(ws[ty][tx + 1] - w0, inv8a, r.y);
+    const C nrm = sqrt(ax * ax + ay * ay);
+    const C sc = nrm > C(1) ? C(1) / nrm : C(1);
+    C2 wn;
+    wn.x = ax * sc;
+    wn.y = ay * sc;
+    const size_t idx = (size_t)i * N + jc;
+    C2 wo;
+    wo.x = C(0);
+    wo.y = C(0);
+    if (!start) wo = Wold[idx];
+    C2 rn;
+    rn.x = fma(beta, wn.x - wo.x, wn.x);
+    rn.y = fma(beta, wn.y - wo.y, wn.y);
+    Wnew[idx] = wn;
+    Rnext[idx] = rn;
+    }
+}
+
 // Caller's plain sinogram [na][nb] into the pair view sino[dst].
 template <typename T>
 __global__ void __launch_bounds__(kRayBlock)
@@ -1205,6 +1364,14 @@ void launch_backproject(const Prob<T>* d, const Item* items, int grid, int nrhs,
     else launch_bp<T, 1>(d, items, grid, src0, src1, dst0, dst1, step, s);
 }
 template <typename T>
+void launch_sino_comb(const Prob<T>* d, const Item* items, int grid, int cur, int prev, cudaStream_t s) {
+    k_sino_comb<T><<<grid, kRayBlock, 0, s>>>(d, items, cur, prev);
+}
+template <typename T>
+void launch_fgp(const Prob<T>* d, const Item* items, int grid, int j, double beta, cudaStream_t s) {
+    k_fgp<T><<<grid, kTileThreads, 0, s>>>(d, items, j, (typename Tr<T>::C)beta);
+}
+template <typename T>
 void launch_sino_pairs(const Prob<T>* d, int grid, int dst, cudaStream_t s) {
     k_sino_pairs<T><<<grid, kRayBlock, 0, s>>>(d, dst);
 }
@@ -1252,6 +1419,8 @@ cudaError_t launch_filter(const Prob<T>* d, const Item* items, int grid, int max
     template cudaError_t launch_filter<T>(const Prob<T>*, const Item*, int, int, int, int, int,   \
                                           cudaStream_t);                                          \
     template void launch_sino_pairs<T>(const Prob<T>*, int, int, cudaStream_t);                   \
+    template void launch_sino_comb<T>(const Prob<T>*, const Item*, int, int, int, cudaStream_t);    \
+    template void launch_fgp<T>(const Prob<T>*, const Item*, int, int, double, cudaStream_t);       \
     template void launch_set_done<T>(const Prob<T>*, int, int, cudaStream_t);                     \
     template void launch_set_io<T>(Prob<T>*, const typename Tr<T>::S*, typename Tr<T>::S*,          \
                                    typename Tr<T>::S*, cudaStream_t);                            \

@@ -69,7 +69,10 @@ __host__ __device__ constexpr size_t filter_smem_bytes(int nb) { return 2 * size
 constexpr size_t kFilterSmemMax = 160 * 1024;   // largest FFT held in shared memory (FP32: n_bins <= 8192, FP64: 4096)
 
 enum ImgBuf { IB_X = 0, IB_XH, IB_P, IB_H, IB_G, IB_Z, IB_TVG, IB_AUX, IB_COUNT };
-enum SinoBuf { SB_R = 0, SB_Q, SB_W, SB_COUNT };
+enum SinoBuf { SB_R = 0, SB_Q, SB_W, SB_V, SB_COUNT };
+// FISTA keeps x_k in FISTA_X[k % 3] and A x_k in FISTA_Q[k % 3]
+constexpr int kFistaX[3] = {IB_X, IB_XH, IB_P};
+constexpr int kFistaQ[3] = {SB_Q, SB_W, SB_V};
 
 // Per-angle constants (host computes them in FP64).  With m = max(|c|,|s|),
 // n = min(|c|,|s|), the chord of a ray through a unit pixel whose centre is at
@@ -116,6 +119,23 @@ struct Item {
     int local;     // index of this item among the problem's items of this kind
 };
 
+// Projector work item number q -> (angle group u, bin block v), longest rays
+// first: bin blocks are taken centre-out (the block holding the detector's
+// middle bin, then its neighbours alternately, then the rest of the longer
+// side), and for each bin block every angle group in turn.  Rays near the
+// detector's middle cross the whole image and rays near its ends only a corner,
+// so launching blocks in this order lets the short blocks fill the last wave.
+__host__ __device__ inline void proj_item_of(int q, int n_groups, int proj_blocks, int nb, int shift,
+                                             int& u, int& v) {
+    const int r = q / n_groups;
+    u = q - r * n_groups;
+    const int c = ((nb - 1) >> 1) >> shift;                // block of the middle bin
+    const int lo = c, hi = proj_blocks - 1 - c;
+    const int m = lo < hi ? lo : hi;
+    if (r <= 2 * m) v = (r & 1) ? c + ((r + 1) >> 1) : c - (r >> 1);
+    else v = hi > lo ? c + (r - m) : c - (r - m);
+}
+
 // Trace row fields (SCG_TRACE_FIELDS).
 enum { TR_K = 0, TR_FTEST, TR_TV_BEFORE, TR_TV_AFTER, TR_TRIALS, TR_ACCEPTED, TR_ELL,
        TR_GAMMA, TR_ALPHA, TR_BETA, TR_MARGIN, TR_F_AFTER, TR_NF };
@@ -138,6 +158,9 @@ struct DevState {
     double margin;
     double f_final, tv_final;
     double eta0;            // Appendix rule: ||u_k|| = eta0 ||g_k||
+    double c2;              // FISTA: c^2 = ||A||_2^2 (given, or the power iteration's estimate)
+    double tk;              // FISTA: t_k of Eq. FISTA-u
+    double lam;             // FISTA: lambda of the prox step lambda / c^2
     long long ell;
     int k, iters, max_iter, done, status;
     int perturb, gamma_fixed, max_trials, trials, accepted;
@@ -146,7 +169,7 @@ struct DevState {
     int pass_cands;          // candidates of the trial pass being finalised
 };
 
-enum Family { FAM_CG = 0, FAM_S_PR = 1, FAM_S_K = 2 };
+enum Family { FAM_CG = 0, FAM_S_PR = 1, FAM_S_K = 2, FAM_FISTA = 3 };
 
 // Loop bookkeeping of a batched solve (the problems' own states are DevState).
 struct BatchState {
@@ -221,6 +244,8 @@ struct Prob {
     pair_t* sino[SB_COUNT]; // pair views of the sinogram-sized vectors
     pair_t* view_rm;
     pair_t* view_cm;
+    pair_t* dual[4];        // FISTA's TV prox: dual fields w_j (0, 1) and momentum points (2, 3), one
+                            // (p, q) pair per interior term (i, j) at i*N + j
     const elem_t* user_in;  // caller's plain sinogram (operator entry points)
     elem_t* user_out;
     const calc_t* taps;     // filter tables: P factors gain c(w_k)/P, then P/2 twiddles exp(-2 pi i j/P)
@@ -499,7 +524,10 @@ enum Step {
     FIN_TV,           // standalone TV: S0 -> trace slot 0
     FIN_FINAL_F,      // f of the output
     FIN_FINAL_TV,     // TV of the output
-    FIN_ETA           // gradient at x_k (Appendix rule): S0 = ||g_k||^2 -> the perturbation's size
+    FIN_ETA,          // gradient at x_k (Appendix rule): S0 = ||g_k||^2 -> the perturbation's size
+    FIN_POWER,        // power iteration: S0 = ||h||^2, S1 = p^T h with h = A^T A p
+    FIN_POWER_NORM,   // power iteration: S0 = ||p||^2
+    FIN_FISTA_F       // FISTA: A x_k projected, S0 = ||A x_k - y||^2 -> stop test, t_{k+1}, beta_k
 };
 
 __device__ __forceinline__ bool finite_pos(double v) { return v > 0.0 && isfinite(v); }
@@ -702,6 +730,33 @@ __device__ void finalize(int step, const Prob<T>& P, DevState& st, const double*
         break;
     case FIN_FINAL_TV:
         st.tv_final = S[0];
+        break;
+    case FIN_POWER:
+        st.c2 = S[1] / st.xnorm2;                        // Rayleigh quotient of A^T A at p
+        st.coef = 1.0 / sqrt(S[0]);
+        break;
+    case FIN_POWER_NORM:
+        st.xnorm2 = S[0];
+        break;
+    case FIN_FISTA_F:
+        st.f_half = 0.5 * S[0];                          // f(x_k)
+        if (st.in_init) {
+            st.in_init = 0;                              // x_0: t_1 = 1, u_1 = x_0
+        } else {
+            const double t1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * st.tk * st.tk));
+            if (row) {
+                row[TR_K] = st.iters + 1;
+                row[TR_ALPHA] = st.tk;
+                row[TR_BETA] = (st.tk - 1.0) / t1;
+                row[TR_F_AFTER] = st.f_half;
+            }
+            st.beta = (st.tk - 1.0) / t1;                // u_{k+1} = x_k + beta (x_k - x_{k-1})
+            st.tk = t1;
+            st.iters += 1;
+            st.k += 1;
+        }
+        if (!(st.f_half > st.eps)) { st.done = 1; st.status = SCG_OK; }
+        else if (st.iters >= st.max_iter) { st.done = 1; st.status = SCG_WARN_MAX_ITER; }
         break;
     case FIN_ETA:
         // Appendix, Eq. up bnd u_k: u_k = eta0 ||g_k|| v_k with v_k = -dTV/||dTV||

@@ -5,7 +5,7 @@
 
 namespace scg {
 
-enum ProjMode { PROJ_PLAIN = 0, PROJ_RESIDUAL = 1, PROJ_PLAIN_OUT = 2 };
+enum ProjMode { PROJ_PLAIN = 0, PROJ_RESIDUAL = 1, PROJ_PLAIN_OUT = 2, PROJ_FISTA = 3 };
 enum FiltMode { FILT_VIEW = 0, FILT_PLAIN = 1, FILT_FBP = 2 };
 
 enum VecOp {
@@ -16,7 +16,12 @@ enum VecOp {
     VEC_FORM_P0 = 4,       // P = -img[sel]; views; S0 = G^T P
     VEC_FORM_P_NOVIEW = 5, // P = -img[sel] + beta P
     VEC_CG_UPDATE = 6,     // X = img[sel] + alpha P; G += alpha H; S0 = ||G||^2, S1 = G^T Z
-    VEC_DOTS_RESUME = 7    // S0 = P^T H, S1 = G^T P
+    VEC_DOTS_RESUME = 7,   // S0 = P^T H, S1 = G^T P
+    VEC_POWER_START = 8,   // P = start vector of the power iteration; views; S0 = ||P||^2
+    VEC_NORMALIZE = 9,     // P = coef H; views; S0 = ||P||^2
+    VEC_FISTA_B = 10,      // Z = u - G / c^2, u = img[c] + beta (img[c] - img[p]); sel = c | p << 4
+    VEC_FGP_FINAL = 11,    // img[d] = Z - (lambda/c^2) L^T dual[w]; views; sel = d | w << 4 (w = 2: none)
+    VEC_FISTA_OUT = 12     // Z = user_out = x_k (buffer chosen by the device's k)
 };
 
 template <typename T>
@@ -41,6 +46,10 @@ cudaError_t launch_filter(const Prob<T>* d, const Item* items, int grid, int max
                           int dst, int mode, cudaStream_t s);
 template <typename T>
 void launch_sino_pairs(const Prob<T>* d, int grid, int dst, cudaStream_t s);
+template <typename T>
+void launch_sino_comb(const Prob<T>* d, const Item* items, int grid, int cur, int prev, cudaStream_t s);
+template <typename T>
+void launch_fgp(const Prob<T>* d, const Item* items, int grid, int j, double beta, cudaStream_t s);
 void launch_loop_cond(DevState* st, cudaGraphConditionalHandle h, cudaStream_t s);
 void noalloc_forget();   // scg_tv_static's cached scratch addresses (noalloc.cu)
 template <typename T>

@@ -27,11 +27,12 @@ namespace {
 struct GraphKey {
     int dev;
     const void* work;
-    int prec, variant, trial_passes, ksteps, n, na, nb, host_loop, proj_shift, eta;
+    int prec, variant, trial_passes, ksteps, n, na, nb, host_loop, proj_shift, eta, prox_iters;
     bool operator<(const GraphKey& o) const {
-        return std::tie(dev, work, prec, variant, trial_passes, ksteps, n, na, nb, host_loop, proj_shift, eta) <
+        return std::tie(dev, work, prec, variant, trial_passes, ksteps, n, na, nb, host_loop, proj_shift, eta,
+                        prox_iters) <
                std::tie(o.dev, o.work, o.prec, o.variant, o.trial_passes, o.ksteps, o.n, o.na, o.nb,
-                        o.host_loop, o.proj_shift, o.eta);
+                        o.host_loop, o.proj_shift, o.eta, o.prox_iters);
     }
 };
 
@@ -55,6 +56,18 @@ std::map<ShapeKey, int> g_shapes;
 ShapeKey shape_key(int dev, int precision, const scg_geometry& g) {
     auto bucket = [](int v) { return (int)lround(2.0 * log2((double)v)); };
     return ShapeKey{dev, precision, bucket(g.n), bucket(g.n_angles), bucket(g.n_bins)};
+}
+// FISTA's c^2 estimates, per device, precision and exact geometry
+std::map<std::tuple<int, int, int, int, int>, double> g_lipschitz;
+constexpr int kPowerIters = 100;
+double lipschitz_lookup(int dev, int precision, const scg_geometry& g) {
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    auto it = g_lipschitz.find(std::make_tuple(dev, precision, g.n, g.n_angles, g.n_bins));
+    return it == g_lipschitz.end() ? 0.0 : it->second;
+}
+void lipschitz_store(int dev, int precision, const scg_geometry& g, double c2) {
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    g_lipschitz[std::make_tuple(dev, precision, g.n, g.n_angles, g.n_bins)] = c2;
 }
 std::map<int, cudaStream_t> g_streams;
 std::map<int, int*> g_pinned;
@@ -106,10 +119,18 @@ int solve_impl(const scg_geometry* g, int variant, int precision, const scg_para
     Prob<T> P = make_prob<T>(*g, pl, base, scale);
     P.y = (const E*)y;
     P.img[IB_AUX] = (E*)x0;
+    if (fam == FAM_FISTA) P.user_out = (E*)x_out;        // written by the output pass
     std::vector<Angle<C>> ang;
     fill_angles<C>(ang, g->n_angles, g->n, scale);
 
     DevState st = initial_state(prm, eps * s2, variant);
+    // FISTA's c^2: given, cached for this geometry, or estimated below
+    bool need_power = false;
+    if (fam == FAM_FISTA && !(prm->lipschitz > 0.0)) {
+        const double c2 = lipschitz_lookup(dev, prec_of<T>(), *g);
+        if (c2 > 0.0) st.c2 = c2;
+        else need_power = true;
+    }
     const bool resumed = resume && resume->valid == 1;
     if (resumed) {
         st.k = resume->k;
@@ -148,6 +169,7 @@ int solve_impl(const scg_geometry* g, int variant, int precision, const scg_para
         if (resume->g) CK(cudaMemcpyAsync(P.img[IB_G], resume->g, vb, cudaMemcpyDeviceToDevice, s));
         run_resume<T>(R, pg);
     } else {
+        if (need_power) run_power<T>(R, kPowerIters);
         run_init<T>(R, pg);
     }
     CK(cudaGetLastError());
@@ -157,7 +179,7 @@ int solve_impl(const scg_geometry* g, int variant, int precision, const scg_para
     // device after every body (no host round trip per iteration).  Fallback:
     // one graph per body, launched in batches and polled one batch ahead.
     GraphKey key{dev, work, precision, variant, pg.trial_passes, pg.ksteps, g->n, g->n_angles, g->n_bins,
-                 prm->host_loop ? 1 : 0, pl.proj_shift, pg.eta ? 1 : 0};
+                 prm->host_loop ? 1 : 0, pl.proj_shift, pg.eta ? 1 : 0, pg.prox_iters};
     BodyGraph bg{nullptr, 0, false};
     {
         std::lock_guard<std::mutex> lk(g_mu);
@@ -229,7 +251,8 @@ int solve_impl(const scg_geometry* g, int variant, int precision, const scg_para
     }
 
     const DevState* dst = reinterpret_cast<const DevState*>(base + pl.state);
-    const int max_bodies = prm->max_iter + 2;
+    // (a FISTA body holds three iterations)
+    const int max_bodies = (fam == FAM_FISTA ? prm->max_iter / 3 : prm->max_iter) + 2;
     int launched = 0;
     if (bg.device_loop) {
         int mb[2] = {0, max_bodies};                // bodies, max_bodies
@@ -272,11 +295,12 @@ int solve_impl(const scg_geometry* g, int variant, int precision, const scg_para
     const int body_kernels = bg.kernels;
 
     // output, f and TV of the output
-    const int out_sel = fam == FAM_CG ? IB_X : IB_XH;
-    CK(cudaMemcpyAsync(x_out, P.img[out_sel], sizeof(E) * J, cudaMemcpyDeviceToDevice, s));
+    const int out_sel = fam == FAM_CG ? IB_X : fam == FAM_FISTA ? IB_Z : IB_XH;
+    if (fam != FAM_FISTA) CK(cudaMemcpyAsync(x_out, P.img[out_sel], sizeof(E) * J, cudaMemcpyDeviceToDevice, s));
     DevState* dstm = reinterpret_cast<DevState*>(base + pl.state);
     int zero = 0;
     CK(cudaMemcpyAsync(&dstm->done, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
+    if (fam == FAM_FISTA) R.vec(VEC_FISTA_OUT, 0, FIN_NONE);   // x_k of the device's k, to Z and x_out
     R.tvgrad(out_sel, 0, 0, FIN_FINAL_TV);
     if (fam == FAM_CG) {
         R.vec(VEC_VIEWS, IB_X, FIN_NONE);
@@ -318,6 +342,8 @@ int solve_impl(const scg_geometry* g, int variant, int precision, const scg_para
     res->tv_final = hs.tv_final;
     res->ell = hs.ell;
     res->gamma0_used = hs.gamma0;
+    res->lipschitz_used = hs.c2;
+    if (need_power && hs.c2 > 0.0) lipschitz_store(dev, prec_of<T>(), *g, hs.c2);
     if (bg.device_loop) {
         res->body_launches = hs.bodies;
         res->kernel_launches = R.launches + 1 + hs.bodies * (body_kernels + 1);
@@ -840,6 +866,9 @@ void scg_default_params(scg_params* p) {
     p->max_iter = 100;
     p->host_loop = 0;
     p->eta0 = 0.0;
+    p->lambda = 0.0;
+    p->prox_iters = 20;
+    p->lipschitz = 0.0;
 }
 
 size_t scg_op_workspace_bytes(const scg_geometry* g, int precision) {
@@ -848,7 +877,7 @@ size_t scg_op_workspace_bytes(const scg_geometry* g, int precision) {
 }
 
 size_t scg_solve_workspace_bytes(const scg_geometry* g, int variant, int precision) {
-    if (!valid_geometry(g) || !valid_prec(precision) || variant < SCG_CG || variant > SCG_S_PCG_K ||
+    if (!valid_geometry(g) || !valid_prec(precision) || !valid_variant(variant) ||
         !solve_supported(variant, precision))
         return 0;
     return make_plan(*g, variant, precision, PLAN_SOLVE).total;
@@ -907,7 +936,8 @@ int scg_solve(const scg_geometry* g, int variant, int precision, const scg_param
               scg_result* res, double* trace, int trace_rows, const scg_state* resume,
               scg_state* final_state, void* stream) {
     if (!valid_geometry(g) || !prm || !y || !x_out || !work || !res) return SCG_ERR_INVALID;
-    if (variant < SCG_CG || variant > SCG_S_PCG_K) return SCG_ERR_INVALID;
+    if (!valid_variant(variant)) return SCG_ERR_INVALID;
+    if (variant == SCG_FISTA && resume) return SCG_ERR_UNSUPPORTED;
     if (!(eps > 0.0) || !isfinite(eps) || !valid_params(prm)) return SCG_ERR_INVALID;
     if (prm->host_loop != 0 && prm->host_loop != 1) return SCG_ERR_INVALID;
     if (resume && resume->valid != 1) return SCG_ERR_INVALID;
@@ -995,6 +1025,7 @@ int scg_solve_batch(const scg_problem* problems, int count, int variant, int pre
                     const scg_params* prm, void* work, size_t work_bytes, scg_result* results,
                     void* stream) {
     if (!problems || count < 1 || count > 65536 || !prm || !work || !results) return SCG_ERR_INVALID;
+    if (variant == SCG_FISTA) return SCG_ERR_UNSUPPORTED;          // FISTA: scg_solve only
     if (variant < SCG_CG || variant > SCG_S_PCG_K) return SCG_ERR_INVALID;
     if (!valid_params(prm)) return SCG_ERR_INVALID;
     if (prm->host_loop != 0) return SCG_ERR_UNSUPPORTED;

@@ -15,7 +15,7 @@ import torch
 from . import build as _build
 
 F64, F32, F16, BF16 = 0, 1, 2, 3
-VARIANTS = {"CG": 0, "PCG": 1, "S-CG": 2, "S-CG-CD": 3, "S-CG-K": 4, "S-PCG": 5, "S-PCG-K": 6}
+VARIANTS = {"CG": 0, "PCG": 1, "S-CG": 2, "S-CG-CD": 3, "S-CG-K": 4, "S-PCG": 5, "S-PCG-K": 6, "FISTA": 7}
 PERTURB = {"none": 0, "gamma": 1, "eta": 2}
 STATUS = {0: "ok", 1: "max_iter", -1: "invalid", -2: "cuda", -3: "workspace", -4: "breakdown",
           -5: "unsupported"}
@@ -36,7 +36,8 @@ class Params(ctypes.Structure):
                 ("gamma0_rel", ctypes.c_double), ("a", ctypes.c_double),
                 ("max_trials", ctypes.c_int), ("K", ctypes.c_int), ("k_inclusive", ctypes.c_int),
                 ("mu", ctypes.c_double), ("filter_gain", ctypes.c_double),
-                ("max_iter", ctypes.c_int), ("host_loop", ctypes.c_int), ("eta0", ctypes.c_double)]
+                ("max_iter", ctypes.c_int), ("host_loop", ctypes.c_int), ("eta0", ctypes.c_double),
+                ("lambda_", ctypes.c_double), ("prox_iters", ctypes.c_int), ("lipschitz", ctypes.c_double)]
 
 
 class Result(ctypes.Structure):
@@ -44,7 +45,7 @@ class Result(ctypes.Structure):
                 ("f_final", ctypes.c_double), ("tv_final", ctypes.c_double),
                 ("ell", ctypes.c_longlong), ("gamma0_used", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int), ("body_launches", ctypes.c_int),
-                ("device_loop", ctypes.c_int)]
+                ("device_loop", ctypes.c_int), ("lipschitz_used", ctypes.c_double)]
 
 
 class Problem(ctypes.Structure):
@@ -288,7 +289,8 @@ def default_params(**kw) -> dict:
 def _params(d: dict) -> Params:
     return Params(PERTURB[d["perturb"]], float(d["gamma0"]), float(d["gamma0_rel"]), float(d["a"]),
                   int(d["max_trials"]), int(d["K"]), int(d["k_inclusive"]), float(d["mu"]),
-                  float(d["filter_gain"]), int(d["max_iter"]), int(d["host_loop"]), float(d["eta0"]))
+                  float(d["filter_gain"]), int(d["max_iter"]), int(d["host_loop"]), float(d["eta0"]),
+                  float(d["lambda_"]), int(d["prox_iters"]), float(d["lipschitz"]))
 
 
 @dataclass
@@ -305,6 +307,7 @@ class SolveResult:
     kernel_launches: int = 0
     body_launches: int = 0
     device_loop: int = 0
+    lipschitz_used: float = 0.0
     trace: object = None
     state: dict | None = None
 
@@ -368,7 +371,7 @@ def scg_solve(y: torch.Tensor, n: int, variant: str = "S-CG", eps: float = 1.0, 
     _check(rc, "scg_solve", ok=(0, 1, -4))
     out_res = SolveResult(out, res.iters, res.k_final, STATUS.get(res.status, str(res.status)),
                           res.status, res.f_final, res.tv_final, res.ell, res.gamma0_used,
-                          res.kernel_launches, res.body_launches, res.device_loop)
+                          res.kernel_launches, res.body_launches, res.device_loop, res.lipschitz_used)
     if trace:
         out_res.trace = tr[: min(res.iters, rows)].copy()
     if want_state:
