@@ -234,6 +234,17 @@ typedef struct scg_operator scg_operator;    /* opaque */
  * SCG_ERR_INVALID / SCG_ERR_UNSUPPORTED / SCG_ERR_WORKSPACE as scg_project. */
 int scg_operator_create(const scg_geometry* g, int precision, void* work, size_t work_bytes,
                         void* stream, scg_operator** out);
+/* A prepared operator for one block of consecutive angles of a scan: the rows
+ * a_begin .. a_begin + a_count - 1 of A for the scan g (angle a_begin + a of
+ * g->n_angles is the operator's angle a).  Projections write a_count x n_bins
+ * sinograms; backprojections read them and give that block's share of A^T r
+ * (the shares of a partition of the angles add up to A^T r).  This is the
+ * local operator of an angle-sharded solve, where each GPU holds one block of
+ * the data.  Workspace: scg_op_workspace_bytes of {n, a_count, n_bins}.
+ * Returns SCG_ERR_INVALID unless 0 <= a_begin, 1 <= a_count and
+ * a_begin + a_count <= g->n_angles.  The paper has no counterpart. */
+int scg_operator_create_angles(const scg_geometry* g, int a_begin, int a_count, int precision, void* work,
+                               size_t work_bytes, void* stream, scg_operator** out);
 /* y = A x, as scg_project (stream-ordered, asynchronous). */
 int scg_operator_project(scg_operator* op, const void* x, void* y, void* stream);
 /* x = A^T r, as scg_backproject (stream-ordered, asynchronous). */

@@ -217,15 +217,20 @@ inline Plan make_plan(const scg_geometry& g, int variant, int precision, int kin
 }
 
 // Per-angle constants; `scale` multiplies every chord (1/m), i.e. A -> scale A.
+// Entry a describes angle a_begin + a of a scan of na_total angles (a block of
+// consecutive angles for an angle-sharded operator; by default the whole scan).
 template <typename T>
-void fill_angles(std::vector<Angle<T>>& out, int na, int n, double scale = 1.0) {
+void fill_angles(std::vector<Angle<T>>& out, int na, int n, double scale = 1.0, int a_begin = 0,
+                 int na_total = -1) {
     out.resize(na);
+    if (na_total < 0) na_total = na;
     const double off_n = 0.5 * (n - 1);
     for (int a = 0; a < na; ++a) {
+        const int ga = a_begin + a;
         double c, s;
-        if (a == 0) { c = 1.0; s = 0.0; }
-        else if (2 * a == na) { c = 0.0; s = 1.0; }
-        else { const double th = M_PI * (double)a / (double)na; c = cos(th); s = sin(th); }
+        if (ga == 0) { c = 1.0; s = 0.0; }
+        else if (2 * ga == na_total) { c = 0.0; s = 1.0; }
+        else { const double th = M_PI * (double)ga / (double)na_total; c = cos(th); s = sin(th); }
         const double ac = fabs(c), as = fabs(s);
         const double m = ac > as ? ac : as, mn = ac > as ? as : ac;
         const double hs = 0.5 * (m + mn);

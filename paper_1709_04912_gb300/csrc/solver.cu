@@ -365,16 +365,19 @@ int solve_impl(const scg_geometry* g, int variant, int precision, const scg_para
 
 // ---------------------------------------------------------------------------
 // Operator entry points share this set-up.
+// `g` is the geometry the operator applies (for an angle block: n_angles =
+// the block's angles), angle a of it is angle a_begin + a of a scan of
+// na_total angles.
 template <typename T>
 int op_setup(const scg_geometry& g, void* work, size_t work_bytes, cudaStream_t s, Plan* pl_out,
-             Prob<T>* P_out) {
+             Prob<T>* P_out, int a_begin = 0, int na_total = -1) {
     using C = typename Tr<T>::C;
     const Plan pl = make_plan(g, SCG_S_CG, prec_of<T>(), PLAN_OP);
     if (work_bytes < pl.total || ((uintptr_t)work & 15u)) return SCG_ERR_WORKSPACE;
     unsigned char* base = (unsigned char*)work;
     Prob<T> P = make_prob<T>(g, pl, base);
     std::vector<Angle<C>> ang;
-    fill_angles<C>(ang, g.n_angles, g.n);
+    fill_angles<C>(ang, g.n_angles, g.n, 1.0, a_begin, na_total);
     CK(cudaMemsetAsync(base + pl.state, 0, sizeof(DevState), s));
     CK(cudaMemsetAsync(base + pl.counter, 0, 16, s));
     CK(cudaMemcpyAsync(base + pl.ang, ang.data(), sizeof(Angle<C>) * ang.size(), cudaMemcpyHostToDevice, s));
@@ -521,10 +524,10 @@ struct Operator final : OperatorBase {
     Plan pl;
     Prob<T>* d = nullptr;
 
-    int init(const scg_geometry& geo, void* work, size_t wb, cudaStream_t s) {
+    int init(const scg_geometry& geo, void* work, size_t wb, cudaStream_t s, int a_begin = 0, int na_total = -1) {
         g = geo;
         Prob<T> P;
-        int rc = op_setup<T>(g, work, wb, s, &pl, &P);
+        int rc = op_setup<T>(g, work, wb, s, &pl, &P, a_begin, na_total);
         if (rc) return rc;
         // projector shape: the one tuned for this geometry bucket, if any (an
         // operator workspace has no scratch sinogram to tune on)
@@ -977,22 +980,30 @@ int scg_release(void) {
     return rc;
 }
 
-int scg_operator_create(const scg_geometry* g, int precision, void* work, size_t work_bytes, void* stream,
-                        scg_operator** out) {
-    if (!valid_geometry(g) || !work || !out) return SCG_ERR_INVALID;
+int scg_operator_create_angles(const scg_geometry* g, int a_begin, int a_count, int precision, void* work,
+                               size_t work_bytes, void* stream, scg_operator** out) {
+    if (!valid_geometry(g) || !work || !out || a_begin < 0 || a_count < 1 || a_begin + a_count > g->n_angles)
+        return SCG_ERR_INVALID;
     if (!valid_prec(precision)) return SCG_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
+    const scg_geometry gl{g->n, a_count, g->n_bins};       // the block as the operator's own scan
     OperatorBase* impl = nullptr;
     int rc;
     switch (precision) {
-    case SCG_F64: { auto* o = new Operator<double>(); rc = o->init(*g, work, work_bytes, s); impl = o; break; }
-    case SCG_F32: { auto* o = new Operator<float>(); rc = o->init(*g, work, work_bytes, s); impl = o; break; }
-    case SCG_F16: { auto* o = new Operator<__half>(); rc = o->init(*g, work, work_bytes, s); impl = o; break; }
-    default: { auto* o = new Operator<__nv_bfloat16>(); rc = o->init(*g, work, work_bytes, s); impl = o; break; }
+    case SCG_F64: { auto* o = new Operator<double>(); rc = o->init(gl, work, work_bytes, s, a_begin, g->n_angles); impl = o; break; }
+    case SCG_F32: { auto* o = new Operator<float>(); rc = o->init(gl, work, work_bytes, s, a_begin, g->n_angles); impl = o; break; }
+    case SCG_F16: { auto* o = new Operator<__half>(); rc = o->init(gl, work, work_bytes, s, a_begin, g->n_angles); impl = o; break; }
+    default: { auto* o = new Operator<__nv_bfloat16>(); rc = o->init(gl, work, work_bytes, s, a_begin, g->n_angles); impl = o; break; }
     }
     if (rc != SCG_OK) { delete impl; return rc; }
     *out = new scg_operator{impl};
     return SCG_OK;
+}
+
+int scg_operator_create(const scg_geometry* g, int precision, void* work, size_t work_bytes, void* stream,
+                        scg_operator** out) {
+    if (!valid_geometry(g)) return SCG_ERR_INVALID;
+    return scg_operator_create_angles(g, 0, g->n_angles, precision, work, work_bytes, stream, out);
 }
 
 int scg_operator_project(scg_operator* op, const void* x, void* y, void* stream) {

@@ -112,6 +112,8 @@ def load(build_if_needed: bool = True):
     L.scg_release.argtypes = []
     L.scg_release.restype = i
     L.scg_operator_create.argtypes = [gp, i, vp, sz, vp, ctypes.POINTER(vp)]
+    L.scg_operator_create_angles.argtypes = [gp, i, i, i, vp, sz, vp, ctypes.POINTER(vp)]
+    L.scg_operator_create_angles.restype = i
     L.scg_operator_project.argtypes = [vp, vp, vp, vp]
     L.scg_operator_backproject.argtypes = [vp, vp, vp, vp]
     L.scg_operator_destroy.argtypes = [vp]
@@ -521,17 +523,24 @@ class Operator:
     each application is device work only, so it is asynchronous and can be
     captured in a CUDA graph."""
 
-    def __init__(self, n: int, n_angles: int, n_bins: int, dtype=torch.float32, device="cuda:0"):
+    def __init__(self, n: int, n_angles: int, n_bins: int, dtype=torch.float32, device="cuda:0",
+                 angles: tuple | None = None):
+        """``angles=(a_begin, a_count)``: the operator of that block of the
+        scan's angles (scg_operator_create_angles); sinograms are then
+        a_count x n_bins."""
         L = load()
-        self.n, self.na, self.nb = int(n), int(n_angles), int(n_bins)
+        a0, na_loc = (0, int(n_angles)) if angles is None else (int(angles[0]), int(angles[1]))
+        self.n, self.na, self.nb = int(n), na_loc, int(n_bins)
         self.dtype, self.device = dtype, torch.device(device)
         prec = _prec_of(dtype)
         g = geometry(n, n_angles, n_bins)
-        nbytes = L.scg_op_workspace_bytes(ctypes.byref(g), prec)
+        gl = geometry(n, na_loc, n_bins)
+        nbytes = L.scg_op_workspace_bytes(ctypes.byref(gl), prec)
         self.work = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=self.device)
         h = ctypes.c_void_p()
-        _check(L.scg_operator_create(ctypes.byref(g), prec, self.work.data_ptr(), self.work.numel(),
-                                     _stream(self.device), ctypes.byref(h)), "scg_operator_create")
+        _check(L.scg_operator_create_angles(ctypes.byref(g), a0, na_loc, prec, self.work.data_ptr(),
+                                            self.work.numel(), _stream(self.device), ctypes.byref(h)),
+               "scg_operator_create_angles")
         self._h = h
 
     def project(self, x: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
