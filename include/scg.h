@@ -32,7 +32,8 @@
  *
  * Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  Operator
  * calls are asynchronous and stream-ordered.  scg_solve returns when the solve
- * has finished (it reads the device's stop flag).
+ * has finished (it reads the device's stop flag); scg_solve_async enqueues the
+ * same solve and returns, its result written by the device.
  *
  * Errors: every entry point returns an int status (scg_status).  Nothing
  * prints, aborts or throws; scg_strerror() names a code.  Invalid arguments
@@ -325,6 +326,24 @@ int scg_solve(const scg_geometry* g, int variant, int precision, const scg_param
               void* work, size_t work_bytes, scg_result* res,
               double* trace, int trace_rows,
               const scg_state* resume, scg_state* final_state, void* stream);
+
+/* scg_solve, stream-ordered and asynchronous: the solve is enqueued on
+ * `stream` and the call returns; the device writes *res when the stream gets
+ * there (its status field then holds the solve's own status, as scg_solve
+ * returns it), and x_out is ordered before later work on `stream`.
+ *   res   device-accessible memory: device memory, or pinned host memory
+ *         (cudaMallocHost / cudaHostAlloc), read after the stream has passed;
+ *   no trace and no exported state (use scg_solve for those); host_loop must
+ *   be 0 (SCG_ERR_UNSUPPORTED otherwise).
+ * Returns SCG_OK once enqueued, or an error found before any launch.  The
+ * first call for a geometry bucket and precision times the projector shapes
+ * and captures the loop graph, which blocks; later calls do not (a FISTA solve
+ * with lipschitz <= 0 estimates c^2 on the device every time: the estimate is
+ * not read back here). */
+int scg_solve_async(const scg_geometry* g, int variant, int precision, const scg_params* prm,
+                    double eps, const void* y, const void* x0, void* x_out,
+                    void* work, size_t work_bytes, scg_result* res,
+                    const scg_state* resume, void* stream);
 
 /* One problem of a batched solve: its geometry, threshold and buffers (device
  * pointers as for scg_solve; x0 may be NULL). */

@@ -115,7 +115,6 @@ struct Plan {
     int cnt_proj, proj_blocks, proj_shift;
     int cnt_bp;
     int part_cap;           // work items the partial-sum buffer holds per slot
-    int nb;                 // detector bins (the projector's item order depends on them)
 };
 
 // Projector items for the block shape 2^(8-shift) angles x 2^shift rays.
@@ -143,7 +142,6 @@ inline Plan make_plan(const scg_geometry& g, int variant, int precision, int kin
     Plan p;
     memset(&p, 0, sizeof(p));
     const int N = g.n, na = g.n_angles, nb = g.n_bins;
-    p.nb = nb;
     p.S = round_up4(N + 2 * kPad);          // pairs per view line
     p.SB = round_up4(nb + 2 * kSPad);       // pairs per sinogram-view row
     p.ray_blocks = (nb + kRayBlock - 1) / kRayBlock;
@@ -349,6 +347,7 @@ struct Runner {
     void filter(int src, int dst) { ++launches; launch_filter<T>(d, i_row, g_row, nb, src, dst, FILT_VIEW, s); }
     void sino_comb(int cur, int prev) { ++launches; launch_sino_comb<T>(d, i_ray, g_ray, cur, prev, s); }
     void fgp(int j, double beta) { ++launches; launch_fgp<T>(d, i_img, g_img, j, beta, s); }
+    void sino_norm(int src, int step) { ++launches; launch_sino_norm<T>(d, i_ray, g_ray, src, step, s); }
 };
 
 struct Program {
@@ -373,20 +372,22 @@ void run_power(Runner<T>& R, int iters) {
     R.vec(VEC_POWER_START, 0, FIN_POWER_NORM);
     for (int q = 0; q < iters; ++q) {
         R.project(SB_Q, PROJ_PLAIN, FIN_NONE);         // A p (views written by the vector pass)
-        R.back1(SB_Q, IB_H, FIN_POWER);                // h = A^T A p, c^2, 1/||h||
+        R.back1(SB_Q, IB_H, FIN_NONE);                 // h = A^T A p
+        R.vec(VEC_POWER_DOTS, 0, FIN_POWER);           // c^2 = p^T h / ||p||^2, 1/||h||
         R.vec(VEC_NORMALIZE, 0, FIN_POWER_NORM);       // p = h / ||h||
     }
 }
 
 // FISTA (Eq. FISTA, Eq. FISTA-u): x_0 is projected once; each iteration forms
-// A u_k - y from the two latest projections, backprojects it, takes the
-// gradient step, the prox by FGP, and projects x_k (stop test, t_{k+1},
-// beta_k).  x_k lives in kFistaX[k % 3] and A x_k in kFistaQ[k % 3]; a loop
-// body holds three iterations so that every buffer choice is static.
+// A u_k - y from the two latest residuals, backprojects it, takes the gradient
+// step, the prox by FGP, and projects x_k (its residual r_k = A x_k - y, the
+// stop test, t_{k+1}, beta_k).  x_k lives in kFistaX[k % 3] and r_k in
+// kFistaQ[k % 3]; a loop body holds three iterations so that every buffer
+// choice is static.
 template <typename T>
 void run_fista_iteration(Runner<T>& R, const Program& pg, int k3) {
     const int cur = (k3 + 2) % 3, prev = (k3 + 1) % 3;    // x_{k-1}, x_{k-2}
-    R.sino_comb(kFistaQ[cur], kFistaQ[prev]);          // A u_k - y
+    R.sino_comb(kFistaQ[cur], kFistaQ[prev]);          // A u_k - y = (1 + beta) r_{k-1} - beta r_{k-2}
     R.back1(SB_R, IB_G, FIN_NONE);                     // A^T (A u_k - y)
     R.vec(VEC_FISTA_B, kFistaX[cur] | (kFistaX[prev] << 4), FIN_NONE);   // b = u_k - A^T(A u_k - y)/c^2
     double t = 1.0;
@@ -397,7 +398,8 @@ void run_fista_iteration(Runner<T>& R, const Program& pg, int k3) {
     }
     const int w = pg.prox_iters > 0 ? (pg.prox_iters - 1) & 1 : 2;
     R.vec(VEC_FGP_FINAL, kFistaX[k3] | (w << 4), FIN_NONE);              // x_k = prox(b), views
-    R.project(kFistaQ[k3], PROJ_FISTA, FIN_FISTA_F);  // A x_k, f(x_k)
+    R.project(kFistaQ[k3], PROJ_RESIDUAL, FIN_NONE);  // r_k = A x_k - y
+    R.sino_norm(kFistaQ[k3], FIN_FISTA_F);             // f(x_k): stop test, t_{k+1}, beta_k
 }
 
 // The algorithms' set-up steps (before the first loop test).
@@ -408,7 +410,8 @@ void run_init(Runner<T>& R, const Program& pg) {
     const int dsel = pre ? IB_Z : IB_G;
     if (fam == FAM_FISTA) {
         R.vec(VEC_INIT, 0, FIN_NONE);                  // x_0 (u_1 = x_0), views
-        R.project(kFistaQ[0], PROJ_FISTA, FIN_FISTA_F);   // A x_0, f(x_0): first loop test
+        R.project(kFistaQ[0], PROJ_RESIDUAL, FIN_NONE);  // r_0 = A x_0 - y
+        R.sino_norm(kFistaQ[0], FIN_FISTA_F);          // f(x_0): first loop test
         return;
     }
     R.vec(VEC_INIT, 0, FIN_NONE);                      // x_{1/2} = x0 (S-CG family), x_{-1/2} = x0 (S-K)
@@ -459,7 +462,8 @@ void run_body(Runner<T>& R, const Program& pg) {
     if (pg.eta) {                                      // ||g_k||, g_k = A^T (A x_k - y)
         R.vec(VEC_VIEWS, IB_X, FIN_NONE);
         R.project(SB_R, PROJ_RESIDUAL, FIN_NONE);
-        R.back1(SB_R, IB_G, FIN_ETA);
+        R.back1(SB_R, IB_G, FIN_NONE);
+        R.vec(VEC_NORM_G, 0, FIN_ETA_SIZE);
     }
     R.vec(VEC_PERTURB, 0, FIN_NONE);                   // x_{k+1/2} = perturbed(x_k)
     R.project(SB_R, PROJ_RESIDUAL, FIN_F);             // A x_{k+1/2} - y, f(x_{k+1/2})
@@ -568,13 +572,16 @@ inline DevState initial_state(const scg_params* prm, double eps, int variant) {
     st.gamma0_rel = prm->gamma0_rel;
     st.a = prm->a;
     st.a_ell = 1.0;                                  // ell = 0
-    st.apow[0] = 1.0;
-    for (int t = 1; t < kTrials; ++t) st.apow[t] = st.apow[t - 1] * prm->a;
+    if (prm->perturb == SCG_PERTURB_ETA || fam == FAM_FISTA) {   // no gamma trials: the table holds these
+        st.ex.eta0 = prm->eta0;
+        st.ex.lam = prm->lambda;
+        st.ex.c2 = prm->lipschitz > 0.0 ? prm->lipschitz : 0.0;
+        st.ex.tk = 1.0;
+    } else {
+        st.apow[0] = 1.0;
+        for (int t = 1; t < kTrials; ++t) st.apow[t] = st.apow[t - 1] * prm->a;
+    }
     st.max_trials = prm->max_trials;
-    st.eta0 = prm->eta0;
-    st.lam = prm->lambda;
-    st.c2 = prm->lipschitz > 0.0 ? prm->lipschitz : 0.0;
-    st.tk = 1.0;
     st.variant = variant;
     st.family = fam;
     st.in_init = 1;
@@ -599,11 +606,7 @@ inline Program make_program(const scg_params* prm, int variant) {
 enum { K_PROJ = 0, K_IMG = 1, K_RAY = 2, K_ROW = 3, K_BP = 4, K_COUNT = 5 };
 
 inline void append_items(const Plan& pl, int prob, std::vector<Item>* lists) {
-    for (int q = 0; q < pl.cnt_proj; ++q) {            // the single-problem launch's order (proj_item_of)
-        Item it{prob, 0, 0, q};
-        proj_item_of(q, pl.cnt_proj / pl.proj_blocks, pl.proj_blocks, pl.nb, pl.proj_shift, it.u, it.v);
-        lists[K_PROJ].push_back(it);
-    }
+    for (int q = 0; q < pl.cnt_proj; ++q) lists[K_PROJ].push_back(Item{prob, q / pl.proj_blocks, q % pl.proj_blocks, q});
     for (int q = 0; q < pl.cnt_img; ++q) lists[K_IMG].push_back(Item{prob, q / pl.tiles_x, q % pl.tiles_x, q});
     for (int q = 0; q < pl.cnt_ray; ++q) lists[K_RAY].push_back(Item{prob, q / pl.ray_blocks, q % pl.ray_blocks, q});
     for (int q = 0; q < pl.cnt_row; ++q) lists[K_ROW].push_back(Item{prob, q / pl.filt_blocks, q % pl.filt_blocks, q});

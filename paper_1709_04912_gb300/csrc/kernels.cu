@@ -36,7 +36,7 @@ __device__ __forceinline__ Item decode_item(const Prob<T>* probs, const Item* it
     if (kind == 0) { it.u = bid / P.ray_blocks; it.v = bid % P.ray_blocks; }
     else if (kind == 1) { it.u = bid / P.tiles_x; it.v = bid % P.tiles_x; }
     else if (kind == 2) { it.u = bid / P.filt_blocks; it.v = bid % P.filt_blocks; }
-    else if (kind == 3) proj_item_of(bid, P.cnt_proj / P.proj_blocks, P.proj_blocks, P.nb, P.proj_shift, it.u, it.v);
+    else if (kind == 3) { it.u = bid / P.proj_blocks; it.v = bid % P.proj_blocks; }
     else { it.u = bid / P.tiles_x; it.v = bid % P.tiles_x; }   // backprojector tiles
     return it;
 }
@@ -272,13 +272,12 @@ k_project(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int
     // the residual's data value, loaded before the walk so that its latency is
     // hidden (y_scale is 1 except for half/bfloat16 storage; the product is exact)
     C yv = C(0);
-    if (valid && (mode == PROJ_RESIDUAL || mode == PROJ_FISTA)) yv = to_c(P.y[(size_t)a * nb + b]) * P.y_scale;
+    if (valid && mode == PROJ_RESIDUAL) yv = to_c(P.y[(size_t)a * nb + b]) * P.y_scale;
     C out = project_ray<T>(P, g, b, valid);                // every lane: the FP32 walk is warp-wide
     if (valid) {
         if (mode == PROJ_RESIDUAL) out = out - yv;
         if (mode == PROJ_PLAIN_OUT) P.user_out[(size_t)a * nb + b] = to_s<typename Tr<T>::S>(out);
         else store_pair<T>(P.sino[dst_sel] + (size_t)a * P.SB + kSPad, b, out * g.inv_m);   // weighted view
-        if (mode == PROJ_FISTA) out = out - yv;          // A x kept, f(x) summed
         v[0] = acc_prod(out, out);
     }
     if (step != FIN_NONE) reduce_and_finalize<T, 1, true>(v, P, it.local, P.cnt_proj, step);
@@ -505,7 +504,7 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
     // block 0's epilogue operands (h and p for the fused dots), loaded before
     // the cluster barriers so that their latency overlaps the hand-over
     const bool want_h = step == FIN_BETA;
-    const bool want_p = step == FIN_BETA || step == FIN_ALPHA || step == FIN_CG_ALPHA || step == FIN_POWER;
+    const bool want_p = step == FIN_BETA || step == FIN_ALPHA || step == FIN_CG_ALPHA;
     C hv[PIX], pv[PIX];
 #pragma unroll
     for (int k = 0; k < PIX; ++k) {
@@ -574,11 +573,6 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
         } else if (step == FIN_CG_DELTA) {
             v[0] = acc_add(v[0], acc_prod(g0, g0));                                       // ||g||^2
             v[1] = acc_add(v[1], acc_prod(g0, g1));                                       // g^T z
-        } else if (step == FIN_ETA) {
-            v[0] = acc_add(v[0], acc_prod(g0, g0));                                       // ||g_k||^2
-        } else if (step == FIN_POWER) {
-            v[0] = acc_add(v[0], acc_prod(g0, g0));                                       // ||h||^2
-            v[1] = acc_add(v[1], acc_prod(pv[k], g0));                                    // p^T h
         }
     }
     if (step == FIN_NONE) return;
@@ -708,6 +702,21 @@ k_vec(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int op,
         write_views(P, it.u, it.v, val, in);
         break;
     }
+    case VEC_NORM_G: {          // S0 = ||g||^2
+        if (in) {
+            const C g = to_c(P.img[IB_G][idx]);
+            v[0] = acc_prod(g, g);
+        }
+        break;
+    }
+    case VEC_POWER_DOTS: {      // S0 = ||h||^2, S1 = p^T h (h = A^T A p)
+        if (in) {
+            const C h = to_c(P.img[IB_H][idx]);
+            v[0] = acc_prod(h, h);
+            v[1] = acc_prod(to_c(P.img[IB_P][idx]), h);
+        }
+        break;
+    }
     case VEC_NORMALIZE: {       // p = h / ||h||
         const C c = (C)st.coef;
         if (in) {
@@ -722,7 +731,7 @@ k_vec(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int op,
         if (in) {
             const C xc = to_c(P.img[sel & 15][idx]), xp = to_c(P.img[sel >> 4][idx]);
             const C u = fma((C)st.beta, xc - xp, xc);
-            P.img[IB_Z][idx] = to_s<S>(u - to_c(P.img[IB_G][idx]) * (C)(1.0 / st.c2));
+            P.img[IB_Z][idx] = to_s<S>(u - to_c(P.img[IB_G][idx]) * (C)(1.0 / st.ex.c2));
         }
         break;
     }
@@ -737,7 +746,7 @@ k_vec(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int op,
                 if (i < m && j < m) { const auto e = D[idx]; lt -= to_c(e.x) + to_c(e.y); }
                 if (i > 0 && j < m) lt += to_c(D[idx - N].x);
                 if (j > 0 && i < m) lt += to_c(D[idx - 1].y);
-                val = fma(-(C)(st.lam / st.c2), lt, val);
+                val = fma(-(C)(st.ex.lam / st.ex.c2), lt, val);
             }
             P.img[sel & 15][idx] = to_s<S>(val);
         }
@@ -756,7 +765,8 @@ k_vec(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int op,
     default:
         break;
     }
-    if (step != FIN_NONE) reduce_and_finalize<T, 2>(v, P, it.local, P.cnt_img, step);
+    if (step >= kFirstRareStep) reduce_and_finalize<T, 2, false, true>(v, P, it.local, P.cnt_img, step);
+    else if (step != FIN_NONE) reduce_and_finalize<T, 2>(v, P, it.local, P.cnt_img, step);
 }
 
 // ---------------------------------------------------------------------------
@@ -1031,8 +1041,8 @@ k_sino_axpy(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, i
 
 // FISTA's gradient residual A u_k - y on the sinogram views, without
 // projecting u_k: u_k = x_{k-1} + beta (x_{k-1} - x_{k-2}) is linear in the
-// iterates, so A u_k = (1 + beta) A x_{k-1} - beta A x_{k-2} from the two
-// projections already taken (views hold v / m_a, so y is weighted alike).
+// iterates, so A u_k - y = (1 + beta) r_{k-1} - beta r_{k-2} from the residuals
+// r_j = A x_j - y of the two projections already taken.
 template <typename T>
 __global__ void __launch_bounds__(kRayBlock)
 k_sino_comb(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int cur, int prev) {
@@ -1046,8 +1056,26 @@ k_sino_comb(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, i
     const size_t o = (size_t)a * P.SB + kSPad;
     const C beta = (C)st.beta;
     const C qc = to_c(P.sino[cur][o + b].x), qp = to_c(P.sino[prev][o + b].x);
-    const C yw = to_c(P.y[(size_t)a * P.nb + b]) * P.y_scale * P.ang[a].inv_m;
-    store_pair<T>(P.sino[SB_R] + o, b, fma(beta, qc - qp, qc) - yw);
+    store_pair<T>(P.sino[SB_R] + o, b, fma(beta, qc - qp, qc));
+}
+
+// ||r||^2 of a residual view (r / m_a stored; the chord factor is undone), for
+// FISTA's f(x_k) = ||A x_k - y||^2 / 2.
+template <typename T>
+__global__ void __launch_bounds__(kRayBlock)
+k_sino_norm(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int src, int step) {
+    const Item it = decode_item(probs, items, 0);
+    const Prob<T>& P = probs[it.prob];
+    if (P.st->done) return;
+    using C = typename Tr<T>::C;
+    const int a = it.u, b = it.v * kRayBlock + threadIdx.x;
+    Acc<T> v[1];
+    acc_zero(v[0]);
+    if (b < P.nb) {
+        const C r = to_c(P.sino[src][(size_t)a * P.SB + kSPad + b].x) * P.ang[a].m_w;
+        v[0] = acc_prod(r, r);
+    }
+    reduce_and_finalize<T, 1, true, true>(v, P, it.local, P.cnt_ray, step);
 }
 
 // One step of the fast gradient projection (Beck and Teboulle) for the dual
@@ -1075,7 +1103,7 @@ k_fgp(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int j, 
     __shared__ C ws[kTileH + 1][kTileW + 1];
     const int N = P.n, m = N - 1;
     const int i0 = it.u * kTileH, j0 = it.v * kTileW;
-    const C alpha = (C)(st.lam / st.c2);
+    const C alpha = (C)(st.ex.lam / st.ex.c2);
     const C inv8a = C(1) / (C(8) * alpha);
     const bool start = j == 0;
     const C2* R = reinterpret_cast<const C2*>(P.dual[2 + (j & 1)]);
@@ -1265,6 +1293,29 @@ void launch_loop_cond(DevState* st, cudaGraphConditionalHandle h, cudaStream_t s
     k_loop_cond<<<1, 32, 0, s>>>(st, h);
 }
 
+// The result of an asynchronous solve, written by the device from its state
+// when the stream reaches it (f is reported on the unscaled system).
+__global__ void k_write_result(const DevState* st, scg_result* res, double s2, int cg_family, int base_launches,
+                               int body_kernels) {
+    const bool fista = st->family == FAM_FISTA;
+    if (threadIdx.x != 0) return;
+    res->iters = st->iters;
+    res->k_final = st->k;
+    res->status = st->status;
+    res->f_final = (cg_family ? st->f_final : st->f_half) / s2;
+    res->tv_final = st->tv_final;
+    res->ell = st->ell;
+    res->gamma0_used = st->gamma0;
+    res->kernel_launches = base_launches + st->bodies * (body_kernels + 1);
+    res->body_launches = st->bodies;
+    res->device_loop = 1;
+    res->lipschitz_used = fista ? st->ex.c2 : 0.0;
+}
+void launch_write_result(const DevState* st, scg_result* res, double s2, int cg_family, int base_launches,
+                         int body_kernels, cudaStream_t s) {
+    k_write_result<<<1, 32, 0, s>>>(st, res, s2, cg_family, base_launches, body_kernels);
+}
+
 // Point a prepared operator's descriptor at the caller's buffers (one thread;
 // keeps every application stream-ordered and free of host copies).
 template <typename T>
@@ -1368,6 +1419,10 @@ void launch_sino_comb(const Prob<T>* d, const Item* items, int grid, int cur, in
     k_sino_comb<T><<<grid, kRayBlock, 0, s>>>(d, items, cur, prev);
 }
 template <typename T>
+void launch_sino_norm(const Prob<T>* d, const Item* items, int grid, int src, int step, cudaStream_t s) {
+    k_sino_norm<T><<<grid, kRayBlock, 0, s>>>(d, items, src, step);
+}
+template <typename T>
 void launch_fgp(const Prob<T>* d, const Item* items, int grid, int j, double beta, cudaStream_t s) {
     k_fgp<T><<<grid, kTileThreads, 0, s>>>(d, items, j, (typename Tr<T>::C)beta);
 }
@@ -1421,6 +1476,7 @@ cudaError_t launch_filter(const Prob<T>* d, const Item* items, int grid, int max
     template void launch_sino_pairs<T>(const Prob<T>*, int, int, cudaStream_t);                   \
     template void launch_sino_comb<T>(const Prob<T>*, const Item*, int, int, int, cudaStream_t);    \
     template void launch_fgp<T>(const Prob<T>*, const Item*, int, int, double, cudaStream_t);       \
+    template void launch_sino_norm<T>(const Prob<T>*, const Item*, int, int, int, cudaStream_t);    \
     template void launch_set_done<T>(const Prob<T>*, int, int, cudaStream_t);                     \
     template void launch_set_io<T>(Prob<T>*, const typename Tr<T>::S*, typename Tr<T>::S*,          \
                                    typename Tr<T>::S*, cudaStream_t);                            \

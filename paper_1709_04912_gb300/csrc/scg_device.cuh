@@ -70,7 +70,7 @@ constexpr size_t kFilterSmemMax = 160 * 1024;   // largest FFT held in shared me
 
 enum ImgBuf { IB_X = 0, IB_XH, IB_P, IB_H, IB_G, IB_Z, IB_TVG, IB_AUX, IB_COUNT };
 enum SinoBuf { SB_R = 0, SB_Q, SB_W, SB_V, SB_COUNT };
-// FISTA keeps x_k in FISTA_X[k % 3] and A x_k in FISTA_Q[k % 3]
+// FISTA keeps x_k in kFistaX[k % 3] and its residual A x_k - y in kFistaQ[k % 3]
 constexpr int kFistaX[3] = {IB_X, IB_XH, IB_P};
 constexpr int kFistaQ[3] = {SB_Q, SB_W, SB_V};
 
@@ -119,23 +119,6 @@ struct Item {
     int local;     // index of this item among the problem's items of this kind
 };
 
-// Projector work item number q -> (angle group u, bin block v), longest rays
-// first: bin blocks are taken centre-out (the block holding the detector's
-// middle bin, then its neighbours alternately, then the rest of the longer
-// side), and for each bin block every angle group in turn.  Rays near the
-// detector's middle cross the whole image and rays near its ends only a corner,
-// so launching blocks in this order lets the short blocks fill the last wave.
-__host__ __device__ inline void proj_item_of(int q, int n_groups, int proj_blocks, int nb, int shift,
-                                             int& u, int& v) {
-    const int r = q / n_groups;
-    u = q - r * n_groups;
-    const int c = ((nb - 1) >> 1) >> shift;                // block of the middle bin
-    const int lo = c, hi = proj_blocks - 1 - c;
-    const int m = lo < hi ? lo : hi;
-    if (r <= 2 * m) v = (r & 1) ? c + ((r + 1) >> 1) : c - (r >> 1);
-    else v = hi > lo ? c + (r - m) : c - (r - m);
-}
-
 // Trace row fields (SCG_TRACE_FIELDS).
 enum { TR_K = 0, TR_FTEST, TR_TV_BEFORE, TR_TV_AFTER, TR_TRIALS, TR_ACCEPTED, TR_ELL,
        TR_GAMMA, TR_ALPHA, TR_BETA, TR_MARGIN, TR_F_AFTER, TR_NF };
@@ -154,13 +137,18 @@ struct DevState {
     double coef;            // applied perturbation: x_{k+1/2} = x_k + coef * dTV(x_k)
     double trial_c0;        // coefficient of the first pending trial: -gamma0 a^ell / ||dTV||
     double a_ell;           // a^ell, kept by multiplication as ell advances
-    double apow[kTrials];   // a^t, t = 0 .. kTrials-1 (set on the host); trial t: trial_c0 * apow[t]
+    union {
+        double apow[kTrials];   // gamma rule: a^t, t = 0 .. kTrials-1 (set on the host); trial t: trial_c0 * apow[t]
+        struct {                // FISTA and the Appendix rule, which take no gamma trials (sharing the
+                                // table keeps the state, which every finalising block copies, its size)
+            double eta0;        // Appendix rule: ||u_k|| = eta0 ||g_k||
+            double c2;          // FISTA: c^2 = ||A||_2^2 (given, or the power iteration's estimate)
+            double tk;          // FISTA: t_k of Eq. FISTA-u
+            double lam;         // FISTA: lambda of the prox step lambda / c^2
+        } ex;
+    };
     double margin;
     double f_final, tv_final;
-    double eta0;            // Appendix rule: ||u_k|| = eta0 ||g_k||
-    double c2;              // FISTA: c^2 = ||A||_2^2 (given, or the power iteration's estimate)
-    double tk;              // FISTA: t_k of Eq. FISTA-u
-    double lam;             // FISTA: lambda of the prox step lambda / c^2
     long long ell;
     int k, iters, max_iter, done, status;
     int perturb, gamma_fixed, max_trials, trials, accepted;
@@ -244,8 +232,6 @@ struct Prob {
     pair_t* sino[SB_COUNT]; // pair views of the sinogram-sized vectors
     pair_t* view_rm;
     pair_t* view_cm;
-    pair_t* dual[4];        // FISTA's TV prox: dual fields w_j (0, 1) and momentum points (2, 3), one
-                            // (p, q) pair per interior term (i, j) at i*N + j
     const elem_t* user_in;  // caller's plain sinogram (operator entry points)
     elem_t* user_out;
     const calc_t* taps;     // filter tables: P factors gain c(w_k)/P, then P/2 twiddles exp(-2 pi i j/P)
@@ -255,6 +241,8 @@ struct Prob {
     double* trace;
     int trace_rows;
     int part_cap;           // items per slot of `partials` (slot-major: partials[k * part_cap + item])
+    pair_t* dual[4];        // FISTA's TV prox: dual fields w_j (0, 1) and momentum points (2, 3), one
+                            // (p, q) pair per interior term (i, j) at i*N + j
 };
 
 // ---------------------------------------------------------------------------
@@ -411,6 +399,7 @@ __device__ __forceinline__ void block_sum(A (&v)[NS], A* smem /* >= 32*NS */) {
 }
 
 template <typename T> __device__ void finalize(int step, const Prob<T>& P, DevState& st, const double* S);
+template <typename T> __device__ __noinline__ void finalize_rare(int step, const Prob<T>& P, DevState& st, const double* S);
 
 // The finalising block works on a shared-memory copy of the problem's state:
 // the copy is loaded by the block's threads in parallel (one 8-byte word
@@ -453,7 +442,7 @@ __device__ __forceinline__ bool arrive_last(unsigned* counter, unsigned total) {
 // last item sums all partials in item order and runs the step's finaliser.
 // Must be called by every thread of the block (uniform control flow).
 // Partials are stored as the accumulator type (8 bytes either way).
-template <typename T, int NS, bool kPositive = false>
+template <typename T, int NS, bool kPositive = false, bool kRare = false>
 __device__ void reduce_and_finalize(Acc<T> (&v)[NS], const Prob<T>& P, int local, int total,
                                     int step) {
     using A = Acc<T>;
@@ -498,7 +487,8 @@ __device__ void reduce_and_finalize(Acc<T> (&v)[NS], const Prob<T>& P, int local
         double S[NS < 4 ? 4 : NS];
 #pragma unroll
         for (int k = 0; k < (NS < 4 ? 4 : NS); ++k) S[k] = k < NS ? acc_to_double(acc[k]) : 0.0;
-        finalize<T>(step, P, sst, S);
+        if constexpr (kRare) finalize_rare<T>(step, P, sst, S);
+        else finalize<T>(step, P, sst, S);
     }
     __syncthreads();
     StateCopy::store(sst, P.st);
@@ -524,11 +514,13 @@ enum Step {
     FIN_TV,           // standalone TV: S0 -> trace slot 0
     FIN_FINAL_F,      // f of the output
     FIN_FINAL_TV,     // TV of the output
-    FIN_ETA,          // gradient at x_k (Appendix rule): S0 = ||g_k||^2 -> the perturbation's size
-    FIN_POWER,        // power iteration: S0 = ||h||^2, S1 = p^T h with h = A^T A p
+    FIN_POWER,        // power iteration: S0 = ||h||^2, S1 = p^T h with h = A^T A p (vector pass)
     FIN_POWER_NORM,   // power iteration: S0 = ||p||^2
-    FIN_FISTA_F       // FISTA: A x_k projected, S0 = ||A x_k - y||^2 -> stop test, t_{k+1}, beta_k
+    FIN_FISTA_F,      // FISTA: residual of x_k, S0 = ||A x_k - y||^2 -> stop test, t_{k+1}, beta_k
+    FIN_ETA_SIZE      // Appendix rule: S0 = ||g_k||^2 -> the perturbation's size
 };
+// Steps at or after FIN_POWER are finalised by finalize_rare (see there).
+constexpr int kFirstRareStep = FIN_POWER;
 
 __device__ __forceinline__ bool finite_pos(double v) { return v > 0.0 && isfinite(v); }
 
@@ -575,8 +567,6 @@ __device__ void top_of_loop(const Prob<T>& P, DevState& st) {
         }
         st.accepted = 0;              // trials pending
         set_trial_coefs(st);
-    } else if (st.family != FAM_CG && st.perturb == SCG_PERTURB_ETA && st.gnorm2 > 0.0) {
-        st.accepted = 3;              // size pending: ||g_k|| from this body's first passes
     } else {
         st.accepted = -1;             // no perturbation this k
         if (row) { row[TR_TV_AFTER] = st.tv_x; row[TR_ELL] = (double)st.ell; }
@@ -587,6 +577,66 @@ __device__ __forceinline__ void breakdown(DevState& st) {
     st.done = 1;
     st.status = SCG_ERR_BREAKDOWN;
     end_body(st);
+}
+
+
+// Steps that only the power iteration, FISTA and the Appendix rule take,
+// finalised by the vector and sinogram passes that sum them (never by the
+// projector or the gather), so that the finaliser those kernels inline holds
+// only the steps of Algorithms 1-14.
+template <typename T>
+__device__ __noinline__ void finalize_rare(int step, const Prob<T>& P, DevState& st, const double* S) {
+    double* row = trace_row(P, st.iters);
+    switch (step) {
+    case FIN_ETA_SIZE: {
+        // the Appendix rule's gradient at x_k:
+        // u_k = eta0 ||g_k|| v_k with v_k = -dTV/||dTV|| (Eq. up bnd u_k); on
+        // the scaled system c A x ~ c y, S0 = c^4 ||g_k||^2.  No TV test:
+        // x_{k+1/2} = x_k + u_k.
+        const double ys = (double)P.y_scale;
+        const double un = st.ex.eta0 * sqrt(S[0]) / (ys * ys);
+        // (the loop test left accepted = -1: no gamma trials under this rule)
+        if (!st.done && st.family != FAM_CG && st.perturb == SCG_PERTURB_ETA && st.gnorm2 > 0.0) {
+            st.coef = -un / sqrt(st.gnorm2);
+            st.accepted = 1;
+            if (row) {
+                row[TR_ACCEPTED] = 1.0;
+                row[TR_GAMMA] = un;
+                row[TR_ELL] = (double)st.ell;
+            }
+        }
+        break;
+    }
+    case FIN_POWER:
+        st.ex.c2 = S[1] / st.xnorm2;                        // Rayleigh quotient of A^T A at p
+        st.coef = 1.0 / sqrt(S[0]);
+        break;
+    case FIN_POWER_NORM:
+        st.xnorm2 = S[0];
+        break;
+    case FIN_FISTA_F:
+        st.f_half = 0.5 * S[0];                          // f(x_k)
+        if (st.in_init) {
+            st.in_init = 0;                              // x_0: t_1 = 1, u_1 = x_0
+        } else {
+            const double t1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * st.ex.tk * st.ex.tk));
+            if (row) {
+                row[TR_K] = st.iters + 1;
+                row[TR_ALPHA] = st.ex.tk;
+                row[TR_BETA] = (st.ex.tk - 1.0) / t1;
+                row[TR_F_AFTER] = st.f_half;
+            }
+            st.beta = (st.ex.tk - 1.0) / t1;                // u_{k+1} = x_k + beta (x_k - x_{k-1})
+            st.ex.tk = t1;
+            st.iters += 1;
+            st.k += 1;
+        }
+        if (!(st.f_half > st.eps)) { st.done = 1; st.status = SCG_OK; }
+        else if (st.iters >= st.max_iter) { st.done = 1; st.status = SCG_WARN_MAX_ITER; }
+        break;
+    default:
+        break;
+    }
 }
 
 template <typename T>
@@ -730,49 +780,6 @@ __device__ void finalize(int step, const Prob<T>& P, DevState& st, const double*
         break;
     case FIN_FINAL_TV:
         st.tv_final = S[0];
-        break;
-    case FIN_POWER:
-        st.c2 = S[1] / st.xnorm2;                        // Rayleigh quotient of A^T A at p
-        st.coef = 1.0 / sqrt(S[0]);
-        break;
-    case FIN_POWER_NORM:
-        st.xnorm2 = S[0];
-        break;
-    case FIN_FISTA_F:
-        st.f_half = 0.5 * S[0];                          // f(x_k)
-        if (st.in_init) {
-            st.in_init = 0;                              // x_0: t_1 = 1, u_1 = x_0
-        } else {
-            const double t1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * st.tk * st.tk));
-            if (row) {
-                row[TR_K] = st.iters + 1;
-                row[TR_ALPHA] = st.tk;
-                row[TR_BETA] = (st.tk - 1.0) / t1;
-                row[TR_F_AFTER] = st.f_half;
-            }
-            st.beta = (st.tk - 1.0) / t1;                // u_{k+1} = x_k + beta (x_k - x_{k-1})
-            st.tk = t1;
-            st.iters += 1;
-            st.k += 1;
-        }
-        if (!(st.f_half > st.eps)) { st.done = 1; st.status = SCG_OK; }
-        else if (st.iters >= st.max_iter) { st.done = 1; st.status = SCG_WARN_MAX_ITER; }
-        break;
-    case FIN_ETA:
-        // Appendix, Eq. up bnd u_k: u_k = eta0 ||g_k|| v_k with v_k = -dTV/||dTV||
-        // and g_k = A^T(A x_k - y); on the scaled system c A x ~ c y the sum is
-        // c^4 ||g_k||^2.  No TV test: x_{k+1/2} = x_k + u_k.
-        if (st.accepted == 3) {
-            const double ys = (double)P.y_scale;
-            const double un = st.eta0 * sqrt(S[0]) / (ys * ys);
-            st.coef = -un / sqrt(st.gnorm2);
-            st.accepted = 1;
-            if (row) {
-                row[TR_ACCEPTED] = 1.0;
-                row[TR_GAMMA] = un;
-                row[TR_ELL] = (double)st.ell;
-            }
-        }
         break;
     default:
         break;

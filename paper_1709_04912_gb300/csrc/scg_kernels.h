@@ -5,7 +5,7 @@
 
 namespace scg {
 
-enum ProjMode { PROJ_PLAIN = 0, PROJ_RESIDUAL = 1, PROJ_PLAIN_OUT = 2, PROJ_FISTA = 3 };
+enum ProjMode { PROJ_PLAIN = 0, PROJ_RESIDUAL = 1, PROJ_PLAIN_OUT = 2 };
 enum FiltMode { FILT_VIEW = 0, FILT_PLAIN = 1, FILT_FBP = 2 };
 
 enum VecOp {
@@ -21,7 +21,9 @@ enum VecOp {
     VEC_NORMALIZE = 9,     // P = coef H; views; S0 = ||P||^2
     VEC_FISTA_B = 10,      // Z = u - G / c^2, u = img[c] + beta (img[c] - img[p]); sel = c | p << 4
     VEC_FGP_FINAL = 11,    // img[d] = Z - (lambda/c^2) L^T dual[w]; views; sel = d | w << 4 (w = 2: none)
-    VEC_FISTA_OUT = 12     // Z = user_out = x_k (buffer chosen by the device's k)
+    VEC_FISTA_OUT = 12,    // Z = user_out = x_k (buffer chosen by the device's k)
+    VEC_POWER_DOTS = 13,   // S0 = ||H||^2, S1 = P^T H
+    VEC_NORM_G = 14        // S0 = ||G||^2
 };
 
 template <typename T>
@@ -50,7 +52,11 @@ template <typename T>
 void launch_sino_comb(const Prob<T>* d, const Item* items, int grid, int cur, int prev, cudaStream_t s);
 template <typename T>
 void launch_fgp(const Prob<T>* d, const Item* items, int grid, int j, double beta, cudaStream_t s);
+template <typename T>
+void launch_sino_norm(const Prob<T>* d, const Item* items, int grid, int src, int step, cudaStream_t s);
 void launch_loop_cond(DevState* st, cudaGraphConditionalHandle h, cudaStream_t s);
+void launch_write_result(const DevState* st, scg_result* res, double s2, int cg_family, int base_launches,
+                         int body_kernels, cudaStream_t s);
 void noalloc_forget();   // scg_tv_static's cached scratch addresses (noalloc.cu)
 template <typename T>
 void launch_set_io(Prob<T>* d, const typename Tr<T>::S* in_sino, typename Tr<T>::S* out_sino,

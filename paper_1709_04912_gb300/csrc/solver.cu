@@ -95,7 +95,7 @@ template <typename T>
 int solve_impl(const scg_geometry* g, int variant, int precision, const scg_params* prm, double eps,
                const void* y, const void* x0, void* x_out, void* work, size_t work_bytes,
                scg_result* res, double* trace, int trace_rows, const scg_state* resume,
-               scg_state* final_state, cudaStream_t user_stream) {
+               scg_state* final_state, cudaStream_t user_stream, scg_result* res_async = nullptr) {
     using E = typename Tr<T>::S;
     using C = typename Tr<T>::C;
     Plan pl = make_plan(*g, variant, prec_of<T>(), PLAN_SOLVE);
@@ -128,7 +128,7 @@ int solve_impl(const scg_geometry* g, int variant, int precision, const scg_para
     bool need_power = false;
     if (fam == FAM_FISTA && !(prm->lipschitz > 0.0)) {
         const double c2 = lipschitz_lookup(dev, prec_of<T>(), *g);
-        if (c2 > 0.0) st.c2 = c2;
+        if (c2 > 0.0) st.ex.c2 = c2;
         else need_power = true;
     }
     const bool resumed = resume && resume->valid == 1;
@@ -307,6 +307,15 @@ int solve_impl(const scg_geometry* g, int variant, int precision, const scg_para
         R.project(SB_Q, PROJ_RESIDUAL, FIN_FINAL_F);
     }
     CK(cudaGetLastError());
+    if (res_async) {
+        // stream-ordered: the device writes the result when it gets there
+        launch_write_result(dstm, res_async, s2, fam == FAM_CG ? 1 : 0, R.launches + 1, body_kernels, s);
+        CK(cudaGetLastError());
+        CK(cudaEventRecord(ev, s));
+        CK(cudaStreamWaitEvent(user_stream, ev, 0));
+        cudaEventDestroy(ev);
+        return SCG_OK;
+    }
     DevState hs;
     CK(cudaMemcpyAsync(&hs, dstm, sizeof(hs), cudaMemcpyDeviceToHost, s));
     if (trace && trace_rows > 0) {
@@ -342,8 +351,8 @@ int solve_impl(const scg_geometry* g, int variant, int precision, const scg_para
     res->tv_final = hs.tv_final;
     res->ell = hs.ell;
     res->gamma0_used = hs.gamma0;
-    res->lipschitz_used = hs.c2;
-    if (need_power && hs.c2 > 0.0) lipschitz_store(dev, prec_of<T>(), *g, hs.c2);
+    res->lipschitz_used = fam == FAM_FISTA ? hs.ex.c2 : 0.0;
+    if (need_power && hs.ex.c2 > 0.0) lipschitz_store(dev, prec_of<T>(), *g, hs.ex.c2);
     if (bg.device_loop) {
         res->body_launches = hs.bodies;
         res->kernel_launches = R.launches + 1 + hs.bodies * (body_kernels + 1);
@@ -924,6 +933,21 @@ int scg_filter(const scg_geometry* g, int precision, double mu, double gain, con
     if (!valid_prec(precision) || !filter_fits(g->n_bins, precision)) return SCG_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     return SCG_DISPATCH(precision, filter_impl, *g, mu, gain, r, out, work, work_bytes, s);
+}
+
+int scg_solve_async(const scg_geometry* g, int variant, int precision, const scg_params* prm, double eps,
+                    const void* y, const void* x0, void* x_out, void* work, size_t work_bytes, scg_result* res,
+                    const scg_state* resume, void* stream) {
+    if (!valid_geometry(g) || !prm || !y || !x_out || !work || !res) return SCG_ERR_INVALID;
+    if (!valid_variant(variant)) return SCG_ERR_INVALID;
+    if (!(eps > 0.0) || !isfinite(eps) || !valid_params(prm)) return SCG_ERR_INVALID;
+    if (resume && resume->valid != 1) return SCG_ERR_INVALID;
+    if (prm->host_loop != 0 || (variant == SCG_FISTA && resume)) return SCG_ERR_UNSUPPORTED;
+    if (!valid_prec(precision) || !solve_supported(variant, precision)) return SCG_ERR_UNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    scg_result dummy;
+    return SCG_DISPATCH(precision, solve_impl, g, variant, precision, prm, eps, y, x0, x_out, work, work_bytes,
+                        &dummy, nullptr, 0, resume, nullptr, s, res);
 }
 
 int scg_fbp(const scg_geometry* g, int precision, const void* y, void* x, void* work, size_t work_bytes,

@@ -105,6 +105,9 @@ def load(build_if_needed: bool = True):
     L.scg_solve.argtypes = [gp, i, i, ctypes.POINTER(Params), d, vp, vp, vp, vp, sz,
                             ctypes.POINTER(Result), ctypes.POINTER(ctypes.c_double), i,
                             ctypes.POINTER(State), ctypes.POINTER(State), vp]
+    L.scg_solve_async.argtypes = [gp, i, i, ctypes.POINTER(Params), d, vp, vp, vp, vp, sz, vp,
+                                  ctypes.POINTER(State), vp]
+    L.scg_solve_async.restype = i
     pp = ctypes.POINTER(Problem)
     L.scg_batch_workspace_bytes.restype = sz
     L.scg_batch_workspace_bytes.argtypes = [pp, i, i, i]
@@ -381,6 +384,48 @@ def scg_solve(y: torch.Tensor, n: int, variant: str = "S-CG", eps: float = 1.0, 
         st.update(fs_t)
         out_res.state = st
     return out_res
+
+
+class AsyncSolve:
+    """A solve enqueued by scg_solve_async: ``x`` is ordered before later work
+    on the stream; :meth:`result` waits for the stream and reads the result the
+    device wrote into pinned host memory."""
+
+    def __init__(self, x, res_buf, stream):
+        self.x, self._buf, self._stream = x, res_buf, stream
+
+    def result(self) -> SolveResult:
+        self._stream.synchronize()
+        r = Result.from_address(self._buf.data_ptr())
+        return SolveResult(self.x, r.iters, r.k_final, STATUS.get(r.status, str(r.status)), r.status,
+                           r.f_final, r.tv_final, r.ell, r.gamma0_used, r.kernel_launches, r.body_launches,
+                           r.device_loop, r.lipschitz_used)
+
+
+def scg_solve_async(y: torch.Tensor, n: int, variant: str = "S-CG", eps: float = 1.0, x0=None,
+                    out: torch.Tensor | None = None, work: torch.Tensor | None = None, **params) -> AsyncSolve:
+    """Enqueue one solve on the current stream (scg_solve_async) and return at once."""
+    L = load()
+    na, nbins = y.shape
+    prec = _prec(y)
+    g = geometry(n, na, nbins)
+    p = _params(default_params(**params))
+    nbytes = L.scg_solve_workspace_bytes(ctypes.byref(g), VARIANTS[variant], prec)
+    if work is None:
+        work = workspace(nbytes, y.device, "solve")
+    if out is None:
+        out = torch.empty((n, n), dtype=y.dtype, device=y.device)
+    x0p = None
+    if x0 is not None:
+        x0 = x0.to(dtype=y.dtype).contiguous()
+        x0p = _dev_ptr(x0, "x0")
+    buf = torch.zeros(ctypes.sizeof(Result), dtype=torch.uint8).pin_memory()
+    stream = torch.cuda.current_stream(y.device)
+    rc = L.scg_solve_async(ctypes.byref(g), VARIANTS[variant], prec, ctypes.byref(p), float(eps),
+                           _dev_ptr(y, "y"), x0p, _dev_ptr(out, "x_out"), work.data_ptr(), work.numel(),
+                           buf.data_ptr(), None, stream.cuda_stream)
+    _check(rc, "scg_solve_async")
+    return AsyncSolve(out, buf, stream)
 
 
 def _problems(ys, ns, eps, x0s, outs):

@@ -296,3 +296,25 @@ def test_config2_fp32_matches_the_oracle(config2, variant):
     x = r.x.cpu().numpy().astype(np.float64)
     f = 0.5 * np.sum((config2.y - oracle.project(x, config2.work.n_angles, config2.work.n_bins)) ** 2)
     assert f <= config2.eps * (1 + 1e-5)
+
+
+@pytest.mark.parametrize("variant", ["S-CG", "CG", "S-PCG-K", "FISTA"])
+def test_async_solve_equals_the_blocking_one(small, variant):
+    # scg_solve_async enqueues the same solve and returns; the device writes the
+    # result into pinned host memory and the output is ordered before later work
+    # on the stream (a copy taken right after the call sees the final image)
+    kw = kw_for(variant, small)
+    kw.pop("variant")
+    eps = kw.pop("eps")
+    if variant == "FISTA":
+        c = oracle.norm_A(small.work.n, small.work.n_angles, small.work.n_bins, 100)
+        kw = dict(lambda_=1.0, lipschitz=c * c, prox_iters=10, max_iter=300)
+    y = torch.tensor(small.y, dtype=torch.float32, device=DEV)
+    ref = scg.scg_solve(y, small.work.n, variant, eps, **kw)
+    h = scg.scg_solve_async(y, small.work.n, variant, eps, **kw)
+    x_after = h.x.clone()
+    r = h.result()
+    assert r.status == ref.status and r.iters == ref.iters and r.k_final == ref.k_final and r.ell == ref.ell
+    assert r.f_final == ref.f_final and r.tv_final == ref.tv_final
+    assert r.kernel_launches == ref.kernel_launches and r.device_loop == 1
+    assert torch.equal(x_after, ref.x)
