@@ -520,8 +520,27 @@ int fbp_impl(const scg_geometry& g, const void* y, void* x, void* work, size_t w
 // Prepared operator pair: set up once, then each application is device work
 // only (descriptor update by a one-thread kernel, view or pair-row pass, and
 // the projector or backprojector).
+// Each application records CUDA events on its stream around the projector (or
+// gather) kernel alone -- not while the stream is being captured into a graph
+// -- so that scg_operator_kernel_ms can report that kernel's device time.
 struct OperatorBase {
-    virtual ~OperatorBase() {}
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // project start/end, backproject start/end
+    bool timed[2] = {false, false};
+    virtual ~OperatorBase() {
+        for (auto e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+    int make_events() {
+        for (auto& e : ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return SCG_ERR_CUDA;
+        return SCG_OK;
+    }
+    // record event i on s unless s is capturing; returns whether it was recorded
+    bool mark(int i, cudaStream_t s) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return false;
+        return cudaEventRecord(ev[i], s) == cudaSuccess;
+    }
     virtual int project(const void* x, void* y, cudaStream_t s) = 0;
     virtual int backproject(const void* r, void* x, cudaStream_t s) = 0;
 };
@@ -561,14 +580,18 @@ struct Operator final : OperatorBase {
     int project(const void* x, void* y, cudaStream_t s) override {
         launch_set_io<T>(d, nullptr, (E*)y, (E*)const_cast<void*>(x), s);
         launch_vec<T>(d, nullptr, pl.cnt_img, VEC_VIEWS, IB_AUX, FIN_NONE, s);
+        const bool t0 = mark(0, s);
         launch_project<T>(d, nullptr, pl.cnt_proj, SB_Q, PROJ_PLAIN_OUT, FIN_NONE, s);
+        timed[0] = t0 && mark(1, s);
         CK(cudaGetLastError());
         return SCG_OK;
     }
     int backproject(const void* r, void* x, cudaStream_t s) override {
         launch_set_io<T>(d, (const E*)r, nullptr, (E*)x, s);
         launch_sino_pairs<T>(d, pl.cnt_ray, SB_R, s);
+        const bool t0 = mark(2, s);
         launch_backproject<T>(d, nullptr, pl.cnt_bp, 1, SB_R, SB_R, IB_AUX, IB_AUX, FIN_NONE, s);
+        timed[1] = t0 && mark(3, s);
         CK(cudaGetLastError());
         return SCG_OK;
     }
@@ -1019,8 +1042,24 @@ int scg_operator_create_angles(const scg_geometry* g, int a_begin, int a_count, 
     case SCG_F16: { auto* o = new Operator<__half>(); rc = o->init(gl, work, work_bytes, s, a_begin, g->n_angles); impl = o; break; }
     default: { auto* o = new Operator<__nv_bfloat16>(); rc = o->init(gl, work, work_bytes, s, a_begin, g->n_angles); impl = o; break; }
     }
+    if (rc == SCG_OK) rc = impl->make_events();
     if (rc != SCG_OK) { delete impl; return rc; }
     *out = new scg_operator{impl};
+    return SCG_OK;
+}
+
+int scg_operator_kernel_ms(scg_operator* op, float* project_ms, float* backproject_ms) {
+    if (!op || (!project_ms && !backproject_ms)) return SCG_ERR_INVALID;
+    OperatorBase* o = op->impl;
+    if ((project_ms && !o->timed[0]) || (backproject_ms && !o->timed[1])) return SCG_ERR_INVALID;
+    if (project_ms) {
+        if (cudaEventSynchronize(o->ev[1]) != cudaSuccess) return SCG_ERR_CUDA;
+        if (cudaEventElapsedTime(project_ms, o->ev[0], o->ev[1]) != cudaSuccess) return SCG_ERR_CUDA;
+    }
+    if (backproject_ms) {
+        if (cudaEventSynchronize(o->ev[3]) != cudaSuccess) return SCG_ERR_CUDA;
+        if (cudaEventElapsedTime(backproject_ms, o->ev[2], o->ev[3]) != cudaSuccess) return SCG_ERR_CUDA;
+    }
     return SCG_OK;
 }
 

@@ -120,6 +120,8 @@ def load(build_if_needed: bool = True):
     L.scg_operator_project.argtypes = [vp, vp, vp, vp]
     L.scg_operator_backproject.argtypes = [vp, vp, vp, vp]
     L.scg_operator_destroy.argtypes = [vp]
+    L.scg_operator_kernel_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
+    L.scg_operator_kernel_ms.restype = i
     for name in ("scg_operator_create", "scg_operator_project", "scg_operator_backproject",
                  "scg_operator_destroy"):
         getattr(L, name).restype = i
@@ -601,6 +603,17 @@ class Operator:
         _check(load().scg_operator_backproject(self._h, _dev_ptr(r, "r"), _dev_ptr(out, "x"),
                                                _stream(self.device)), "scg_operator_backproject")
         return out
+
+    def kernel_ms(self):
+        """(projector, gather) kernel device times of the last project / backproject
+        calls (scg_operator_kernel_ms); None for a kernel not yet timed."""
+        out = []
+        for which in (0, 1):
+            f = ctypes.c_float(0.0)
+            args = (ctypes.byref(f), None) if which == 0 else (None, ctypes.byref(f))
+            rc = load().scg_operator_kernel_ms(self._h, *args)
+            out.append(float(f.value) if rc == 0 else None)
+        return tuple(out)
 
     def close(self):
         if self._h:

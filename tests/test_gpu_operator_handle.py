@@ -75,3 +75,20 @@ def test_projector_output_does_not_depend_on_the_tuned_shape():
     x = torch.tensor(inputs.normal(5, "x", n * n).reshape(n, n), dtype=torch.float32, device=DEV)
     assert torch.equal(op.project(x), scg.scg_project(x, na, nb))
     op.close()
+
+
+def test_operator_kernel_times_are_recorded():
+    # scg_operator_kernel_ms: the projector's and the gather's own device time
+    # from events the library records around the kernel alone; a call captured
+    # into a graph records none
+    n, na, nb = 128, 90, 183
+    op = scg.Operator(n, na, nb, torch.float32, DEV)
+    assert op.kernel_ms() == (None, None)
+    x = torch.rand((n, n), device=DEV)
+    y = op.project(x)
+    tp, tb = op.kernel_ms()
+    assert tp is not None and tp > 0.0 and tb is None
+    op.backproject(y)
+    tp2, tb2 = op.kernel_ms()
+    assert tp2 == tp and tb2 is not None and tb2 > 0.0
+    op.close()
