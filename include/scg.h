@@ -147,6 +147,11 @@ typedef struct {
                             <= 0 (default): estimated on the device by 100 power
                             iterations on A^T A from 1 + 0.001 (index mod 7) and
                             cached per device, precision and geometry           */
+    int proj_shape;      /* 0 (default): the projector's block shape is the one the
+                            library's tuner measured fastest for this geometry
+                            bucket; 5..8: blocks of 2^(8-s) angles x 2^s rays,
+                            untimed.  Results do not depend on it: every ray is
+                            computed alike and f is summed in a fixed order    */
 } scg_params;
 
 typedef struct {

@@ -60,6 +60,8 @@ void fill_filter_tables(std::vector<C>& out, int P, double mu, double gain) {
     }
 }
 
+constexpr int kProjShiftMin = 5, kProjShiftMax = 8;   // projector blocks 8 x 32 ... 1 x 256
+
 // Parameter ranges shared by every solving entry point.
 inline bool valid_params(const scg_params* p) {
     if (p->max_iter < 0 || p->max_iter > 10000000 || p->max_trials < 1 || p->max_trials > 100000 || p->K < 1 ||
@@ -68,6 +70,7 @@ inline bool valid_params(const scg_params* p) {
     if (!(p->lambda >= 0.0) || !isfinite(p->lambda) || p->prox_iters < 0 || p->prox_iters > 100000 ||
         !isfinite(p->lipschitz))
         return false;
+    if (p->proj_shape != 0 && (p->proj_shape < kProjShiftMin || p->proj_shape > kProjShiftMax)) return false;
     if (p->perturb == SCG_PERTURB_ETA) return p->eta0 > 0.0 && isfinite(p->eta0);
     return p->perturb == SCG_PERTURB_NONE || p->perturb == SCG_PERTURB_GAMMA;
 }
@@ -124,7 +127,6 @@ inline void set_proj_shape(Plan& p, int na, int nb, int shift) {
     p.proj_blocks = (nb + R - 1) / R;
     p.cnt_proj = ((na + A - 1) / A) * p.proj_blocks;
 }
-constexpr int kProjShiftMin = 5, kProjShiftMax = 8;   // 8 x 32 ... 1 x 256
 inline int max_proj_items(int na, int nb) {
     Plan p;
     int m = 0;
@@ -337,7 +339,13 @@ struct Runner {
     const Item* i_proj = nullptr;
     int g_bp = 0;                      // backprojector tiles
     const Item* i_bp = nullptr;
-    void project(int dst, int mode, int step) { ++launches; launch_project<T>(d, i_proj, g_proj, dst, mode, step, s); }
+    // a projection; with a step, f = ||residual||^2 / 2 is then summed by k_sino_norm in
+    // (angle, bin-block) order, independent of the projector's tuned block shape
+    void project(int dst, int mode, int step) {
+        ++launches;
+        launch_project<T>(d, i_proj, g_proj, dst, mode, s);
+        if (step != FIN_NONE) sino_norm(dst, step);
+    }
     void back1(int src, int dst, int step) { ++launches; launch_backproject<T>(d, i_bp, g_bp, 1, src, src, dst, dst, step, s); }
     void back2(int s0, int s1, int d0, int d1, int step) { ++launches; launch_backproject<T>(d, i_bp, g_bp, 2, s0, s1, d0, d1, step, s); }
     void vec(int op, int sel, int step) { ++launches; launch_vec<T>(d, i_img, g_img, op, sel, step, s); }
@@ -527,10 +535,11 @@ void proj_shape_store(int dev, int precision, const scg_geometry& g, int shift);
 // stopped, angles uploaded; the SB_Q view is overwritten) and leave the best
 // one in P, pl and the slot.
 template <typename T>
-int tune_proj_shape(Prob<T>& P, Plan& pl, Prob<T>* d, const scg_geometry& g, cudaStream_t s) {
+int tune_proj_shape(Prob<T>& P, Plan& pl, Prob<T>* d, const scg_geometry& g, cudaStream_t s, int forced = 0) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return SCG_ERR_CUDA;
     int best = prec_of<T>() == SCG_F64 ? kProjShiftDefault : proj_shape_lookup(dev, prec_of<T>(), g);
+    if (forced >= kProjShiftMin && forced <= kProjShiftMax) best = forced;     // the caller's shape
     if (best < 0) {
         cudaEvent_t e0, e1;
         if (cudaEventCreate(&e0) != cudaSuccess) return SCG_ERR_CUDA;
@@ -540,9 +549,9 @@ int tune_proj_shape(Prob<T>& P, Plan& pl, Prob<T>* d, const scg_geometry& g, cud
             set_proj_shape(pl, g.n_angles, g.n_bins, sh);
             P.cnt_proj = pl.cnt_proj; P.proj_blocks = pl.proj_blocks; P.proj_shift = sh;
             if (cudaMemcpyAsync(d, &P, sizeof(P), cudaMemcpyHostToDevice, s) != cudaSuccess) break;
-            launch_project<T>(d, nullptr, pl.cnt_proj, SB_Q, PROJ_PLAIN, FIN_NONE, s);
+            launch_project<T>(d, nullptr, pl.cnt_proj, SB_Q, PROJ_PLAIN, s);
             cudaEventRecord(e0, s);
-            for (int r = 0; r < 3; ++r) launch_project<T>(d, nullptr, pl.cnt_proj, SB_Q, PROJ_PLAIN, FIN_NONE, s);
+            for (int r = 0; r < 3; ++r) launch_project<T>(d, nullptr, pl.cnt_proj, SB_Q, PROJ_PLAIN, s);
             cudaEventRecord(e1, s);
             float ms = 1e30f;
             if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) break;

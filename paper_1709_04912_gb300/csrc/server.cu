@@ -384,7 +384,8 @@ private:
             }
             SCK(upload(probs() + slot, &P, sizeof(P)));
             {
-                const int rc = tune_proj_shape<T>(P, r->plan, probs() + slot, r->p.geometry, stream_);
+                const int rc = tune_proj_shape<T>(P, r->plan, probs() + slot, r->p.geometry, stream_,
+                                                  cfg_.params.proj_shape);
                 if (rc != SCG_OK) return rc;
             }
             slots_[slot] = r;

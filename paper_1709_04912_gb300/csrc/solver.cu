@@ -152,7 +152,7 @@ int solve_impl(const scg_geometry* g, int variant, int precision, const scg_para
         CK(cudaMemcpyAsync(base + pl.taps, ftab.data(), sizeof(C) * ftab.size(), cudaMemcpyHostToDevice, s));
     }
     {
-        const int rc = tune_proj_shape<T>(P, pl, reinterpret_cast<Prob<T>*>(base + pl.prob), *g, s);
+        const int rc = tune_proj_shape<T>(P, pl, reinterpret_cast<Prob<T>*>(base + pl.prob), *g, s, prm->proj_shape);
         if (rc != SCG_OK) return rc;
     }
     Runner<T> R{reinterpret_cast<const Prob<T>*>(base + pl.prob), pl.cnt_ray, pl.cnt_img, pl.cnt_row,
@@ -417,7 +417,7 @@ int project_impl(const scg_geometry& g, const void* x, void* y, void* work, size
     if (rc) return rc;
     const Prob<T>* d = reinterpret_cast<const Prob<T>*>(base + pl.prob);
     launch_vec<T>(d, nullptr, pl.cnt_img, VEC_VIEWS, IB_AUX, FIN_NONE, s);
-    launch_project<T>(d, nullptr, pl.cnt_proj, SB_Q, PROJ_PLAIN_OUT, FIN_NONE, s);
+    launch_project<T>(d, nullptr, pl.cnt_proj, SB_Q, PROJ_PLAIN_OUT, s);
     CK(cudaGetLastError());
     return SCG_OK;
 }
@@ -581,7 +581,7 @@ struct Operator final : OperatorBase {
         launch_set_io<T>(d, nullptr, (E*)y, (E*)const_cast<void*>(x), s);
         launch_vec<T>(d, nullptr, pl.cnt_img, VEC_VIEWS, IB_AUX, FIN_NONE, s);
         const bool t0 = mark(0, s);
-        launch_project<T>(d, nullptr, pl.cnt_proj, SB_Q, PROJ_PLAIN_OUT, FIN_NONE, s);
+        launch_project<T>(d, nullptr, pl.cnt_proj, SB_Q, PROJ_PLAIN_OUT, s);
         timed[0] = t0 && mark(1, s);
         CK(cudaGetLastError());
         return SCG_OK;
@@ -712,7 +712,7 @@ int batch_impl(const scg_problem* pr, int count, int variant, int precision, con
             CK(cudaMemcpyAsync(rb + pl.taps, ftab.data(), sizeof(C) * ftab.size(), cudaMemcpyHostToDevice, s));
         }
         // the problem's own slot serves the shape tuner (a single-problem launch)
-        const int rc = tune_proj_shape<T>(P, pl, slots + i, pr[i].geometry, s);
+        const int rc = tune_proj_shape<T>(P, pl, slots + i, pr[i].geometry, s, prm->proj_shape);
         if (rc != SCG_OK) return rc;
         probs[i] = P;
         append_items(pl, i, items.data());
@@ -904,6 +904,7 @@ void scg_default_params(scg_params* p) {
     p->lambda = 0.0;
     p->prox_iters = 20;
     p->lipschitz = 0.0;
+    p->proj_shape = 0;
 }
 
 size_t scg_op_workspace_bytes(const scg_geometry* g, int precision) {

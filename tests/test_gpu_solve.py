@@ -318,3 +318,17 @@ def test_async_solve_equals_the_blocking_one(small, variant):
     assert r.f_final == ref.f_final and r.tv_final == ref.tv_final
     assert r.kernel_launches == ref.kernel_launches and r.device_loop == 1
     assert torch.equal(x_after, ref.x)
+
+
+@pytest.mark.parametrize("dtype,variant", [(torch.float32, "S-CG"), (torch.float32, "CG"),
+                                           (torch.float32, "S-PCG"), (torch.float16, "S-CG-K")])
+def test_solves_do_not_depend_on_the_projector_block_shape(small, dtype, variant):
+    # every ray is computed alike in any block shape and f is summed in a fixed
+    # (angle, bin-block) order, so the tuned shape -- which may differ between
+    # processes -- and each forced shape give the same solve bit for bit
+    kw = kw_for(variant, small)
+    runs = [gpu_solve(small, dtype, proj_shape=s, **dict(kw)) for s in (0, 5, 6, 7, 8)]
+    for r in runs[1:]:
+        assert r.iters == runs[0].iters and r.status == runs[0].status
+        assert r.f_final == runs[0].f_final and r.tv_final == runs[0].tv_final
+        assert torch.equal(r.x, runs[0].x)
