@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--workload", default=inputs.SINGLE_512.name, choices=sorted(WORKLOADS))
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--gamma0-rel", type=float, default=0.05)
+    ap.add_argument("--lam", type=float, default=30.0, help="FISTA's TV weight lambda (--variant FISTA)")
+    ap.add_argument("--prox-iters", type=int, default=10, help="FISTA's FGP steps per prox (--variant FISTA)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="leave the batch block out of the line")
@@ -219,20 +221,31 @@ def nnz_of(work) -> int:
 
 
 # ---------------------------------------------------------------------------
-def time_oracle_solves(prob, work, variant, gamma0_rel, budget_s, max_solves):
+def time_oracle_solves(prob, work, variant, gamma0_rel, budget_s, max_solves, lam=0.0, prox_iters=10):
     """Whole oracle solves of ``prob`` (FP64, on the host cores), timed one by
     one until ``budget_s`` seconds or ``max_solves`` solves.  Returns the times,
-    the iteration count and the thread count."""
+    the iteration count and the thread count.  FISTA's c^2 comes from the
+    oracle's own power iteration (100 steps, the library's count), outside the
+    timed solves."""
     import oracle
     kw = dict(variant=variant, gamma0_rel=gamma0_rel, eps=prob.eps, max_iter=work.max_iter)
     if variant in ("CG", "PCG"):
         kw["perturb"] = "none"
-    oracle.solve(prob.y, work.n, **dict(kw, max_iter=0))      # loads the library
+    if variant == "FISTA":
+        c2 = oracle.norm_A(work.n, work.n_angles, work.n_bins, 100) ** 2
+
+        def one():
+            return oracle.fista(prob.y, work.n, prob.eps, lam, c2, prox_iters=prox_iters, max_iter=300)
+    else:
+        oracle.solve(prob.y, work.n, **dict(kw, max_iter=0))  # loads the library
+
+        def one():
+            return oracle.solve(prob.y, work.n, **kw)
     times, iters = [], 0
     t_all = time.perf_counter()
     while len(times) < max(1, max_solves):
         t0 = time.perf_counter()
-        _, res, _ = oracle.solve(prob.y, work.n, **kw)
+        _, res, _ = one()
         times.append(time.perf_counter() - t0)
         iters = res["iters"]
         if time.perf_counter() - t_all >= budget_s:
@@ -247,7 +260,8 @@ def run_reference(args, work, rank, world):
     import oracle
     variant = args.variant
     prob = inputs.make_problem(work, args.seed, oracle.project)
-    times, iters, cores = time_oracle_solves(prob, work, variant, args.gamma0_rel, args.ref_budget, args.steps)
+    times, iters, cores = time_oracle_solves(prob, work, variant, args.gamma0_rel, args.ref_budget, args.steps,
+                                             args.lam, args.prox_iters)
     t_solve = float(np.mean(times))
     value = 1.0 / t_solve
     sample = (f"{len(times)} whole oracle {variant} solves of this workload ({iters} iterations to eps each), "
@@ -285,6 +299,8 @@ def run_ours(args, work, rank, local_rank, world):
     kw = dict(gamma0_rel=args.gamma0_rel, max_iter=work.max_iter, host_loop=int(args.host_loop))
     if variant in ("CG", "PCG"):
         kw["perturb"] = "none"
+    if variant == "FISTA":              # c^2 estimated on the device once, then cached
+        kw = dict(lambda_=args.lam, prox_iters=args.prox_iters, max_iter=300, host_loop=int(args.host_loop))
 
     import oracle
     prob = inputs.make_problem(work, args.seed + rank, oracle.project)
@@ -427,12 +443,15 @@ def run_ours(args, work, rank, local_rank, world):
     # CPU baseline: whole oracle solves of the same problem, timed
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        times, o_iters, cores = time_oracle_solves(prob, work, variant, args.gamma0_rel, 30.0, 1)
+        times, o_iters, cores = time_oracle_solves(prob, work, variant, args.gamma0_rel, 30.0, 1, args.lam,
+                                                   args.prox_iters)
         cpu = {"value": 1.0 / float(np.mean(times)), "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": (f"{len(times)} whole oracle {variant} solve(s) of this workload "
                           f"({o_iters} iterations to eps), timed")}
 
     blocks = {}
+    if variant == "FISTA":                      # scg_solve only
+        args.no_batch = args.no_serving = True
     if not args.no_batch:
         blocks["batch"] = batch_block(args, dev, rank, world, count=args.batch, dtype_name="f16", steps=3,
                                       warmup=1)
