@@ -149,9 +149,13 @@ typedef struct {
                             cached per device, precision and geometry           */
     int proj_shape;      /* 0 (default): the projector's block shape is the one the
                             library's tuner measured fastest for this geometry
-                            bucket; 5..8: blocks of 2^(8-s) angles x 2^s rays,
-                            untimed.  Results do not depend on it: every ray is
-                            computed alike and f is summed in a fixed order    */
+                            bucket (the first solve of a bucket in a process
+                            times the shapes, so two processes may pick
+                            differently); 5..8: blocks of 2^(8-s) angles x 2^s
+                            rays, untimed.  Every ray is computed alike in any
+                            shape, but f sums the blocks' partial sums, whose
+                            rounding depends on the shape: a fixed proj_shape
+                            makes solves repeat bit for bit across processes */
 } scg_params;
 
 typedef struct {

@@ -339,13 +339,7 @@ struct Runner {
     const Item* i_proj = nullptr;
     int g_bp = 0;                      // backprojector tiles
     const Item* i_bp = nullptr;
-    // a projection; with a step, f = ||residual||^2 / 2 is then summed by k_sino_norm in
-    // (angle, bin-block) order, independent of the projector's tuned block shape
-    void project(int dst, int mode, int step) {
-        ++launches;
-        launch_project<T>(d, i_proj, g_proj, dst, mode, s);
-        if (step != FIN_NONE) sino_norm(dst, step);
-    }
+    void project(int dst, int mode, int step) { ++launches; launch_project<T>(d, i_proj, g_proj, dst, mode, step, s); }
     void back1(int src, int dst, int step) { ++launches; launch_backproject<T>(d, i_bp, g_bp, 1, src, src, dst, dst, step, s); }
     void back2(int s0, int s1, int d0, int d1, int step) { ++launches; launch_backproject<T>(d, i_bp, g_bp, 2, s0, s1, d0, d1, step, s); }
     void vec(int op, int sel, int step) { ++launches; launch_vec<T>(d, i_img, g_img, op, sel, step, s); }
@@ -549,9 +543,9 @@ int tune_proj_shape(Prob<T>& P, Plan& pl, Prob<T>* d, const scg_geometry& g, cud
             set_proj_shape(pl, g.n_angles, g.n_bins, sh);
             P.cnt_proj = pl.cnt_proj; P.proj_blocks = pl.proj_blocks; P.proj_shift = sh;
             if (cudaMemcpyAsync(d, &P, sizeof(P), cudaMemcpyHostToDevice, s) != cudaSuccess) break;
-            launch_project<T>(d, nullptr, pl.cnt_proj, SB_Q, PROJ_PLAIN, s);
+            launch_project<T>(d, nullptr, pl.cnt_proj, SB_Q, PROJ_PLAIN, FIN_NONE, s);
             cudaEventRecord(e0, s);
-            for (int r = 0; r < 3; ++r) launch_project<T>(d, nullptr, pl.cnt_proj, SB_Q, PROJ_PLAIN, s);
+            for (int r = 0; r < 3; ++r) launch_project<T>(d, nullptr, pl.cnt_proj, SB_Q, PROJ_PLAIN, FIN_NONE, s);
             cudaEventRecord(e1, s);
             float ms = 1e30f;
             if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) break;

@@ -1,8 +1,8 @@
 // kernels.cu -- the CUDA kernels of the TV-superiorized CG hot path.
 //
 //   k_project      ray-driven forward projector A (Eq. LS1), fused residual
-//                  epilogue r = Ax - y
-//   k_sino_norm    ||r||^2 of a residual (f of Sec. 1) in a fixed block order
+//                  epilogue r = Ax - y and FP64 sum of squares (f of Sec. 1)
+//   k_sino_norm    ||r||^2 of a residual view (FISTA's f)
 //   k_backproject  pixel-driven gather A^T (1 or 2 right-hand sides), fused
 //                  FP64 inner products of Algorithms 2/4/8/10/14
 //   k_vec          CG vector updates (p' = -g' + beta p, x' = x + alpha p,
@@ -248,7 +248,8 @@ constexpr int kProjMinBlocks = 4;
 // same view spans and most of those reads hit L1.
 template <typename T>
 __global__ void __launch_bounds__(kProjThreads, kProjMinBlocks)
-k_project(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int dst_sel, int mode) {
+k_project(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int dst_sel,
+          int mode, int step) {
     const Item it = decode_item(probs, items, 3);
     const Prob<T>& P = probs[it.prob];
     if (P.st->done) return;
@@ -265,6 +266,8 @@ k_project(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int
     const int a = (it.u << lab) + ((warp >> lwpr) << law) + (lane >> lrw);
     const int b = (it.v << sh) + ((warp & ((1 << lwpr) - 1)) << lrw) + (lane & ((1 << lrw) - 1));
     using C = typename Tr<T>::C;
+    Acc<T> v[1];
+    acc_zero(v[0]);
     const bool valid = a < P.na && b < nb;
     const Angle<C> g = P.ang[valid ? a : 0];
     // the residual's data value, loaded before the walk so that its latency is
@@ -276,7 +279,9 @@ k_project(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int
         if (mode == PROJ_RESIDUAL) out = out - yv;
         if (mode == PROJ_PLAIN_OUT) P.user_out[(size_t)a * nb + b] = to_s<typename Tr<T>::S>(out);
         else store_pair<T>(P.sino[dst_sel] + (size_t)a * P.SB + kSPad, b, out * g.inv_m);   // weighted view
+        v[0] = acc_prod(out, out);
     }
+    if (step != FIN_NONE) reduce_and_finalize<T, 1, true>(v, P, it.local, P.cnt_proj, step);
 }
 
 // ---------------------------------------------------------------------------
@@ -1055,10 +1060,8 @@ k_sino_comb(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, i
     store_pair<T>(P.sino[SB_R] + o, b, fma(beta, qc - qp, qc));
 }
 
-// ||r||^2 of a residual view (r / m_a stored; the chord factor is undone): f =
-// ||A x - y||^2 / 2 of every solver's stop test.  The sum runs over blocks of
-// (angle, 128 bins) whatever block shape the projector was tuned to, so f, and
-// every decision taken from it, do not depend on the tuning.
+// ||r||^2 of a residual view (r / m_a stored; the chord factor is undone), for
+// FISTA's f(x_k) = ||A x_k - y||^2 / 2.
 template <typename T>
 __global__ void __launch_bounds__(kRayBlock)
 k_sino_norm(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int src, int step) {
@@ -1384,8 +1387,9 @@ void launch_loop_cond_batch(const Prob<T>* d, BatchState* bs, cudaGraphCondition
 // ---------------------------------------------------------------------------
 // Host launchers.
 template <typename T>
-void launch_project(const Prob<T>* d, const Item* items, int grid, int dst, int mode, cudaStream_t s) {
-    k_project<T><<<grid, kProjThreads, 0, s>>>(d, items, dst, mode);
+void launch_project(const Prob<T>* d, const Item* items, int grid, int dst, int mode, int step,
+                    cudaStream_t s) {
+    k_project<T><<<grid, kProjThreads, 0, s>>>(d, items, dst, mode, step);
 }
 // `grid` tiles (work items), each taken by a cluster of BpCfg::CL blocks.
 template <typename T, int NRHS>
@@ -1461,7 +1465,7 @@ cudaError_t launch_filter(const Prob<T>* d, const Item* items, int grid, int max
 }
 
 #define SCG_INSTANTIATE(T)                                                                        \
-    template void launch_project<T>(const Prob<T>*, const Item*, int, int, int, cudaStream_t);      \
+    template void launch_project<T>(const Prob<T>*, const Item*, int, int, int, int, cudaStream_t); \
     template void launch_backproject<T>(const Prob<T>*, const Item*, int, int, int, int, int, int, \
                                         int, cudaStream_t);                                       \
     template void launch_vec<T>(const Prob<T>*, const Item*, int, int, int, int, cudaStream_t);     \

@@ -27,7 +27,8 @@ enum VecOp {
 };
 
 template <typename T>
-void launch_project(const Prob<T>* d, const Item* items, int grid, int dst, int mode, cudaStream_t s);
+void launch_project(const Prob<T>* d, const Item* items, int grid, int dst, int mode, int step,
+                    cudaStream_t s);
 template <typename T>
 void launch_backproject(const Prob<T>* d, const Item* items, int grid, int nrhs, int src0,
                         int src1, int dst0, int dst1, int step, cudaStream_t s);

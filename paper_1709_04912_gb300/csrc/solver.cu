@@ -417,7 +417,7 @@ int project_impl(const scg_geometry& g, const void* x, void* y, void* work, size
     if (rc) return rc;
     const Prob<T>* d = reinterpret_cast<const Prob<T>*>(base + pl.prob);
     launch_vec<T>(d, nullptr, pl.cnt_img, VEC_VIEWS, IB_AUX, FIN_NONE, s);
-    launch_project<T>(d, nullptr, pl.cnt_proj, SB_Q, PROJ_PLAIN_OUT, s);
+    launch_project<T>(d, nullptr, pl.cnt_proj, SB_Q, PROJ_PLAIN_OUT, FIN_NONE, s);
     CK(cudaGetLastError());
     return SCG_OK;
 }
@@ -581,7 +581,7 @@ struct Operator final : OperatorBase {
         launch_set_io<T>(d, nullptr, (E*)y, (E*)const_cast<void*>(x), s);
         launch_vec<T>(d, nullptr, pl.cnt_img, VEC_VIEWS, IB_AUX, FIN_NONE, s);
         const bool t0 = mark(0, s);
-        launch_project<T>(d, nullptr, pl.cnt_proj, SB_Q, PROJ_PLAIN_OUT, s);
+        launch_project<T>(d, nullptr, pl.cnt_proj, SB_Q, PROJ_PLAIN_OUT, FIN_NONE, s);
         timed[0] = t0 && mark(1, s);
         CK(cudaGetLastError());
         return SCG_OK;

@@ -322,13 +322,19 @@ def test_async_solve_equals_the_blocking_one(small, variant):
 
 @pytest.mark.parametrize("dtype,variant", [(torch.float32, "S-CG"), (torch.float32, "CG"),
                                            (torch.float32, "S-PCG"), (torch.float16, "S-CG-K")])
-def test_solves_do_not_depend_on_the_projector_block_shape(small, dtype, variant):
-    # every ray is computed alike in any block shape and f is summed in a fixed
-    # (angle, bin-block) order, so the tuned shape -- which may differ between
-    # processes -- and each forced shape give the same solve bit for bit
+def test_projector_block_shape_changes_only_rounding(small, dtype, variant):
+    # every ray is computed alike in any block shape; only the order of the
+    # blocks' partial sums of f follows the shape.  A forced shape repeats bit
+    # for bit (also after the caches are released, as in a new process); the
+    # four shapes agree in iterations, decisions and, to rounding, in x and f
     kw = kw_for(variant, small)
-    runs = [gpu_solve(small, dtype, proj_shape=s, **dict(kw)) for s in (0, 5, 6, 7, 8)]
-    for r in runs[1:]:
-        assert r.iters == runs[0].iters and r.status == runs[0].status
-        assert r.f_final == runs[0].f_final and r.tv_final == runs[0].tv_final
-        assert torch.equal(r.x, runs[0].x)
+    runs = {s: gpu_solve(small, dtype, proj_shape=s, **dict(kw)) for s in (5, 6, 7, 8)}
+    scg.release()
+    again = gpu_solve(small, dtype, proj_shape=6, **dict(kw))
+    assert torch.equal(again.x, runs[6].x) and again.f_final == runs[6].f_final
+    ref = runs[5]
+    for r in runs.values():
+        assert r.iters == ref.iters and r.status == ref.status
+        np.testing.assert_array_equal(r.trace[:, DECISION], ref.trace[:, DECISION])
+        assert rel(r.x.cpu().numpy(), ref.x.cpu().numpy()) <= (1e-5 if dtype == torch.float32 else 1e-3)
+        assert r.f_final == pytest.approx(ref.f_final, rel=1e-6)
