@@ -378,7 +378,7 @@ def run_ours(args, work, rank, local_rank, world):
     # device work only -- a one-thread descriptor update, the view (or
     # pair-row) pass and the projector (or backprojector); L2 is flushed
     # before every application and the events bracket the application alone
-    op = scg.Operator(work.n, work.n_angles, work.n_bins, dtype, dev)
+    op = scg.Operator(work.n, work.n_angles, work.n_bins, dtype, dev, timing=True)
 
     def time_op(fn, which, reps=20):
         # application time (CUDA events around the call) and the kernel's own

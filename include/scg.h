@@ -259,12 +259,18 @@ int scg_operator_create_angles(const scg_geometry* g, int a_begin, int a_count, 
 int scg_operator_project(scg_operator* op, const void* x, void* y, void* stream);
 /* x = A^T r, as scg_backproject (stream-ordered, asynchronous). */
 int scg_operator_backproject(scg_operator* op, const void* r, void* x, void* stream);
+/* Turn kernel timing on (enable != 0) or off (0, the default) for the
+ * operator's later applications.  While it is on, each application records two
+ * CUDA events on its stream immediately before and after the projector (gather)
+ * kernel -- about 4 microseconds of device time per application -- except in
+ * calls made while the stream is being captured into a graph.  Returns
+ * SCG_ERR_INVALID for a NULL operator. */
+int scg_operator_timing(scg_operator* op, int enable);
 /* Device time, in milliseconds, of the projector (gather) kernel alone in the
- * operator's last scg_operator_project (scg_operator_backproject) call, from
- * CUDA events the library records on that call's stream immediately before and
- * after the kernel (not in calls made while the stream is being captured into
- * a graph).  Blocks until that kernel has finished.  Either pointer may be
- * NULL; returns SCG_ERR_INVALID when the requested kernel has no timed call. */
+ * operator's last timed scg_operator_project (scg_operator_backproject) call,
+ * from the events described under scg_operator_timing.  Blocks until that
+ * kernel has finished.  Either pointer may be NULL; returns SCG_ERR_INVALID
+ * when the requested kernel has no timed call. */
 int scg_operator_kernel_ms(scg_operator* op, float* project_ms, float* backproject_ms);
 /* Release the host handle (the workspace is the caller's again once the
  * stream work issued through the operator has completed). */

@@ -6,6 +6,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
+#include <memory>
 #include <vector>
 
 #include "scg_kernels.h"
@@ -43,15 +45,20 @@ inline bool filter_fits(int nb, int precision) {
 
 // Filter tables of one geometry (Sec. 3, Eq. filter_factors_pre): P factors
 // gain c(w_k) / P with c(w) = (|w| + mu)(0.54 + 0.46 cos w), w_k = 2 pi k / P
-// folded into [-pi, pi] (the 1/P completes the unitary transform pair), then
-// the twiddles exp(-2 pi i j / P), j < P/2, as (cos, -sin) pairs; all in FP64,
-// rounded once to the arithmetic type.
+// folded into [-pi, pi] (the 1/P completes the unitary transform pair), stored
+// at the bit reversal of k (the order in which the filter kernel's forward FFT
+// leaves the spectrum), then the twiddles exp(-2 pi i j / P), j < P/2, as
+// (cos, -sin) pairs; all in FP64, rounded once to the arithmetic type.
 template <typename C>
 void fill_filter_tables(std::vector<C>& out, int P, double mu, double gain) {
     out.assign(2 * (size_t)P, C(0));
+    int lg = 0;
+    while ((1 << lg) < P) ++lg;
     for (int k = 0; k < P; ++k) {
         const double w = (k <= P / 2) ? 2.0 * M_PI * k / P : 2.0 * M_PI * (k - P) / P;
-        out[k] = (C)(gain * (fabs(w) + mu) * (0.54 + 0.46 * cos(w)) / (double)P);
+        int r = 0;                                    // k with its lg bits reversed
+        for (int b = 0; b < lg; ++b) r |= ((k >> b) & 1) << (lg - 1 - b);
+        out[r] = (C)(gain * (fabs(w) + mu) * (0.54 + 0.46 * cos(w)) / (double)P);
     }
     for (int j = 0; j < P / 2; ++j) {
         const double a = 2.0 * M_PI * (double)j / (double)P;
@@ -108,7 +115,7 @@ inline double system_scale(const scg_geometry& g, int precision) {
 
 // Workspace plan: byte offsets of every segment.
 struct Plan {
-    size_t state, prob, ang, taps, partials, counter, trace;
+    size_t state, prob, ang, taps, partials, counter, trace, proj_items;
     size_t img[IB_COUNT];
     size_t dual[4];
     size_t view_rm, view_cm;
@@ -171,6 +178,7 @@ inline Plan make_plan(const scg_geometry& g, int variant, int precision, int kin
     if (p.cnt_bp > maxcnt) maxcnt = p.cnt_bp;
     p.partials = take(sizeof(double) * kSlots * (size_t)maxcnt);
     p.part_cap = maxcnt;
+    p.proj_items = take(sizeof(Item) * (size_t)max_proj);
     p.counter = take(sizeof(unsigned) * 4);
     p.view_rm = take(2 * tsize * (size_t)N * p.S);
     p.view_cm = take(2 * tsize * (size_t)N * p.S);
@@ -274,6 +282,78 @@ void fill_angles(std::vector<Angle<T>>& out, int na, int n, double scale = 1.0, 
     }
 }
 
+// Projector work list, longest blocks first.  The blocks of one launch differ
+// widely in work -- rays near the ends of the detector are short or miss the
+// image -- and in block-index order long blocks are still starting when most
+// SMs have run out of work (about a fifth of the launch at 512^2 / 720 x 725,
+// 3.4 waves).  Handing the blocks out longest first (list scheduling) ends the
+// launch close to the mean load of an SM.  A block's cost is the number of
+// strips its warps walk: each warp walks the union of its rays' strip ranges in
+// lockstep, in whole pairs, plus a fixed set-up cost.  Only the order changes:
+// every item keeps its block index (local), so the partial sums are added in
+// the same order and the results are bit-identical to the block-index order.
+struct ProjOrder {
+    std::vector<Item> items;    // longest first
+    std::vector<float> cost;    // strips walked, per item
+};
+constexpr int kWarpSetupStrips = 12;
+
+inline ProjOrder make_proj_order(int n, int nb, int shift, const std::vector<Angle<double>>& ang) {
+    const int na = (int)ang.size();
+    const int lab = kProjLog2 - shift, law = lab < 2 ? lab : 2, lrw = 5 - law, lwpr = shift - lrw;
+    const int ablocks = (na + (1 << lab) - 1) >> lab, bblocks = (nb + (1 << shift) - 1) >> shift;
+    // strip range [lo, hi] of every ray: -1 <= c0 + t slope < n, 0 <= t < n
+    std::vector<int> lo((size_t)na * nb), hi((size_t)na * nb);
+    for (int a = 0; a < na; ++a) {
+        const Angle<double>& g = ang[a];
+        for (int b = 0; b < nb; ++b) {
+            const double c0 = ((double)b - 0.5 * (nb - 1)) * g.inv_d + g.c0_off_d;
+            double t0 = 0.0, t1 = n - 1.0;
+            if (g.slope_d == 0.0) {
+                if (!(c0 >= -1.0 && c0 < (double)n)) { t0 = 1.0; t1 = 0.0; }
+            } else {
+                const double ta = (-1.0 - c0) / g.slope_d, tb = ((double)n - c0) / g.slope_d;
+                t0 = std::max(t0, ceil(std::min(ta, tb)));
+                t1 = std::min(t1, floor(std::max(ta, tb)));
+            }
+            const size_t q = (size_t)a * nb + b;
+            if (t0 > t1) { lo[q] = 1; hi[q] = 0; }
+            else { lo[q] = (int)t0; hi[q] = (int)t1; }
+        }
+    }
+    ProjOrder o;
+    const int cnt = ablocks * bblocks;
+    std::vector<std::pair<float, int>> by_cost(cnt);
+    for (int u = 0; u < ablocks; ++u)
+        for (int v = 0; v < bblocks; ++v) {
+            float c = 0.f;
+            for (int w = 0; w < kProjThreads / 32; ++w) {
+                int mlo = 1 << 30, mhi = -1;
+                for (int lane = 0; lane < 32; ++lane) {
+                    const int a = (u << lab) + ((w >> lwpr) << law) + (lane >> lrw);
+                    const int b = (v << shift) + ((w & ((1 << lwpr) - 1)) << lrw) + (lane & ((1 << lrw) - 1));
+                    if (a >= na || b >= nb) continue;
+                    const size_t q = (size_t)a * nb + b;
+                    if (lo[q] > hi[q]) continue;
+                    mlo = std::min(mlo, lo[q]);
+                    mhi = std::max(mhi, hi[q]);
+                }
+                c += mhi < mlo ? 1.f : (float)((mhi | 1) - (mlo & ~1) + 1 + kWarpSetupStrips);
+            }
+            by_cost[u * bblocks + v] = {c, u * bblocks + v};
+        }
+    std::stable_sort(by_cost.begin(), by_cost.end(),
+                     [](const std::pair<float, int>& x, const std::pair<float, int>& y) { return x.first > y.first; });
+    o.items.resize(cnt);
+    o.cost.resize(cnt);
+    for (int k = 0; k < cnt; ++k) {
+        const int q = by_cost[k].second;
+        o.items[k] = Item{0, q / bblocks, q % bblocks, q};
+        o.cost[k] = by_cost[k].first;
+    }
+    return o;
+}
+
 template <typename T>
 Prob<T> make_prob(const scg_geometry& g, const Plan& pl, unsigned char* base, double scale = 1.0) {
     using E = typename Tr<T>::S;
@@ -324,6 +404,20 @@ Prob<T> make_prob(const scg_geometry& g, const Plan& pl, unsigned char* base, do
         cudaError_t e_ = (call);                   \
         if (e_ != cudaSuccess) return SCG_ERR_CUDA; \
     } while (0)
+
+// The projector work list of one geometry and shape (make_proj_order), cached
+// for the life of the process; a_begin / na_total as for fill_angles.
+std::shared_ptr<const ProjOrder> proj_order(int n, int na, int nb, int shift, int a_begin = 0, int na_total = -1);
+
+// Writes the work list of shape pl.proj_shift to dst (a device array of
+// pl.cnt_proj items, normally base + pl.proj_items).
+inline int upload_proj_order(const Plan& pl, void* dst, const scg_geometry& g, cudaStream_t s, int a_begin = 0,
+                             int na_total = -1) {
+    const auto o = proj_order(g.n, g.n_angles, g.n_bins, pl.proj_shift, a_begin, na_total);
+    if ((int)o->items.size() != pl.cnt_proj) return SCG_ERR_INVALID;
+    CK(cudaMemcpyAsync(dst, o->items.data(), sizeof(Item) * o->items.size(), cudaMemcpyHostToDevice, s));
+    return SCG_OK;
+}
 
 // Kernel launch sequence helper: one problem (item lists null, blocks decode
 // their item from blockIdx) or a batch (explicit item lists over problems).
@@ -526,10 +620,13 @@ int proj_shape_lookup(int dev, int precision, const scg_geometry& g);   // -1 if
 void proj_shape_store(int dev, int precision, const scg_geometry& g, int shift);
 
 // Time the candidate shapes on problem slot d (a solve plan, DevState not
-// stopped, angles uploaded; the SB_Q view is overwritten) and leave the best
-// one in P, pl and the slot.
+// stopped, angles uploaded; the SB_Q view is overwritten), each launched over
+// its longest-first work list in order_dst (pl.cnt_proj items of the problem's
+// workspace), and leave the best shape in P, pl and the slot and its list in
+// order_dst.
 template <typename T>
-int tune_proj_shape(Prob<T>& P, Plan& pl, Prob<T>* d, const scg_geometry& g, cudaStream_t s, int forced = 0) {
+int tune_proj_shape(Prob<T>& P, Plan& pl, Prob<T>* d, const scg_geometry& g, cudaStream_t s, Item* order_dst,
+                    int forced = 0) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return SCG_ERR_CUDA;
     int best = prec_of<T>() == SCG_F64 ? kProjShiftDefault : proj_shape_lookup(dev, prec_of<T>(), g);
@@ -543,9 +640,10 @@ int tune_proj_shape(Prob<T>& P, Plan& pl, Prob<T>* d, const scg_geometry& g, cud
             set_proj_shape(pl, g.n_angles, g.n_bins, sh);
             P.cnt_proj = pl.cnt_proj; P.proj_blocks = pl.proj_blocks; P.proj_shift = sh;
             if (cudaMemcpyAsync(d, &P, sizeof(P), cudaMemcpyHostToDevice, s) != cudaSuccess) break;
-            launch_project<T>(d, nullptr, pl.cnt_proj, SB_Q, PROJ_PLAIN, FIN_NONE, s);
+            if (upload_proj_order(pl, order_dst, g, s) != SCG_OK) break;
+            launch_project<T>(d, order_dst, pl.cnt_proj, SB_Q, PROJ_PLAIN, FIN_NONE, s);
             cudaEventRecord(e0, s);
-            for (int r = 0; r < 3; ++r) launch_project<T>(d, nullptr, pl.cnt_proj, SB_Q, PROJ_PLAIN, FIN_NONE, s);
+            for (int r = 0; r < 3; ++r) launch_project<T>(d, order_dst, pl.cnt_proj, SB_Q, PROJ_PLAIN, FIN_NONE, s);
             cudaEventRecord(e1, s);
             float ms = 1e30f;
             if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) break;
@@ -559,7 +657,7 @@ int tune_proj_shape(Prob<T>& P, Plan& pl, Prob<T>* d, const scg_geometry& g, cud
     set_proj_shape(pl, g.n_angles, g.n_bins, best);
     P.cnt_proj = pl.cnt_proj; P.proj_blocks = pl.proj_blocks; P.proj_shift = best;
     if (cudaMemcpyAsync(d, &P, sizeof(P), cudaMemcpyHostToDevice, s) != cudaSuccess) return SCG_ERR_CUDA;
-    return SCG_OK;
+    return upload_proj_order(pl, order_dst, g, s);
 }
 
 // Initial device state of one solve.
@@ -608,12 +706,35 @@ inline Program make_program(const scg_params* prm, int variant) {
 // launch, so its reductions add in the single-problem order.
 enum { K_PROJ = 0, K_IMG = 1, K_RAY = 2, K_ROW = 3, K_BP = 4, K_COUNT = 5 };
 
-inline void append_items(const Plan& pl, int prob, std::vector<Item>* lists) {
-    for (int q = 0; q < pl.cnt_proj; ++q) lists[K_PROJ].push_back(Item{prob, q / pl.proj_blocks, q % pl.proj_blocks, q});
+// With a work list po, the projector items come from it, and their costs are
+// appended to proj_cost.
+inline void append_items(const Plan& pl, int prob, std::vector<Item>* lists, const ProjOrder* po = nullptr,
+                         std::vector<float>* proj_cost = nullptr) {
+    if (po) {
+        for (size_t q = 0; q < po->items.size(); ++q) {
+            Item it = po->items[q];
+            it.prob = prob;
+            lists[K_PROJ].push_back(it);
+            if (proj_cost) proj_cost->push_back(po->cost[q]);
+        }
+    } else {
+        for (int q = 0; q < pl.cnt_proj; ++q) lists[K_PROJ].push_back(Item{prob, q / pl.proj_blocks, q % pl.proj_blocks, q});
+    }
     for (int q = 0; q < pl.cnt_img; ++q) lists[K_IMG].push_back(Item{prob, q / pl.tiles_x, q % pl.tiles_x, q});
     for (int q = 0; q < pl.cnt_ray; ++q) lists[K_RAY].push_back(Item{prob, q / pl.ray_blocks, q % pl.ray_blocks, q});
     for (int q = 0; q < pl.cnt_row; ++q) lists[K_ROW].push_back(Item{prob, q / pl.filt_blocks, q % pl.filt_blocks, q});
     for (int q = 0; q < pl.cnt_bp; ++q) lists[K_BP].push_back(Item{prob, q / pl.tiles_x, q % pl.tiles_x, q});
+}
+
+// Reorders items (with their costs) longest first; equal costs keep their order.
+inline void sort_longest_first(std::vector<Item>& items, const std::vector<float>& cost) {
+    if (cost.size() != items.size()) return;
+    std::vector<int> idx(items.size());
+    for (size_t q = 0; q < idx.size(); ++q) idx[q] = (int)q;
+    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    std::vector<Item> out(items.size());
+    for (size_t q = 0; q < idx.size(); ++q) out[q] = items[idx[q]];
+    items.swap(out);
 }
 
 // List lengths rounded up to eight steps per octave (<= 12.5 % padding), so

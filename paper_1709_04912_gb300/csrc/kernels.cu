@@ -61,58 +61,74 @@ __device__ __forceinline__ Item decode_item(const Prob<T>* probs, const Item* it
 // D carries the view element index of the pair at the crossing in its high
 // word (line t*S, pad kPad, floor(c*)) and the crossing's fraction in its low
 // word; adding DL = slope + S (both in 32.32) steps to the next strip.
-// The walk is software-pipelined in two register groups of four strips that
-// take turns: while one group's loads are in flight the other's are summed,
-// with no register copies between iterations.  Every index read lies inside
+// The walk is software-pipelined in three register groups of four strips that
+// take turns: a strip's weight is formed when its load is issued (so its 32.32
+// position dies at once), and while two groups' loads are in flight the third
+// group is summed.  Every index read lies inside
 // the view because [tlo, thi] holds exactly the strips whose crossing
 // satisfies -1 <= floor(c*) <= N-1 (kPad >= 1), and no load runs ahead of
 // strip n-1.
-#define SCG_STRIP(V_, D_, U_, Y_)                                                                 \
-    U_ = fmaf(__saturatef(fmaf(-__int_as_float(0x3F800000u + ((unsigned)(D_) >> 9)), k2, h2p)),   \
-              V_.x - V_.y, U_);                                                                   \
-    Y_ += V_.y;
+#define SCG_W(D_) __saturatef(fmaf(-__int_as_float(0x3F800000u + ((unsigned)(D_) >> 9)), k2, h2p))
 #define SCG_LD(D_) to_c2(__ldg(view + (int)((D_) >> 32)))
+#define SCG_ISSUE4(V_, W_)                                                     \
+    V_[0] = SCG_LD(D); W_[0] = SCG_W(D); D += DL;                              \
+    V_[1] = SCG_LD(D); W_[1] = SCG_W(D); D += DL;                              \
+    V_[2] = SCG_LD(D); W_[2] = SCG_W(D); D += DL;                              \
+    V_[3] = SCG_LD(D); W_[3] = SCG_W(D); D += DL;
+#define SCG_SUM4(V_, W_)                                                       \
+    u0 = fmaf(W_[0], V_[0].x - V_[0].y, u0); y0 += V_[0].y;                    \
+    u1 = fmaf(W_[1], V_[1].x - V_[1].y, u1); y1 += V_[1].y;                    \
+    u0 = fmaf(W_[2], V_[2].x - V_[2].y, u0); y0 += V_[2].y;                    \
+    u1 = fmaf(W_[3], V_[3].x - V_[3].y, u1); y1 += V_[3].y;
 // Sums go to two accumulator pairs by the parity of the ABSOLUTE strip index
 // (u0, y0: even strips; u1, y1: odd), each receiving its strips in increasing
 // order, so a ray's value does not depend on how its strips are split between
 // the unmasked walk and the masked edges (that split follows the warp's lanes).
-// The walk starts on an even strip.
+// The walk starts on an even strip, and groups start at multiples of four.
 template <typename V2>
 __device__ __forceinline__ void walk_ray_f32(const V2* view, int n, long long D, long long DL,
                                              float k2, float h2p, float& u0, float& u1, float& y0, float& y1) {
     int t = 0;
+    float2 va[4], vb[4], vc[4];
+    float wa[4], wb[4], wc[4];
     if (n >= 8) {
-        // group a holds strips t-4 .. t-1 (loaded) at the top of each iteration
-        long long A0 = D, A1 = D + DL, A2 = D + 2 * DL, A3 = D + 3 * DL;
-        float2 a0 = SCG_LD(A0), a1 = SCG_LD(A1), a2 = SCG_LD(A2), a3 = SCG_LD(A3);
-        for (t = 4; t + 8 <= n; t += 8) {
-            const long long B0 = A3 + DL, B1 = A3 + 2 * DL, B2 = A3 + 3 * DL, B3 = A3 + 4 * DL;
-            const float2 b0 = SCG_LD(B0), b1 = SCG_LD(B1), b2 = SCG_LD(B2), b3 = SCG_LD(B3);
-            SCG_STRIP(a0, A0, u0, y0) SCG_STRIP(a1, A1, u1, y1) SCG_STRIP(a2, A2, u0, y0) SCG_STRIP(a3, A3, u1, y1)
-            A0 = B3 + DL; A1 = B3 + 2 * DL; A2 = B3 + 3 * DL; A3 = B3 + 4 * DL;
-            a0 = SCG_LD(A0); a1 = SCG_LD(A1); a2 = SCG_LD(A2); a3 = SCG_LD(A3);
-            SCG_STRIP(b0, B0, u0, y0) SCG_STRIP(b1, B1, u1, y1) SCG_STRIP(b2, B2, u0, y0) SCG_STRIP(b3, B3, u1, y1)
+        // at the top of each iteration group a holds strips t-8 .. t-5 and
+        // group b t-4 .. t-1 (issued), and D is strip t
+        SCG_ISSUE4(va, wa)
+        SCG_ISSUE4(vb, wb)
+        for (t = 8; t + 12 <= n; t += 12) {
+            SCG_ISSUE4(vc, wc)
+            SCG_SUM4(va, wa)
+            SCG_ISSUE4(va, wa)
+            SCG_SUM4(vb, wb)
+            SCG_ISSUE4(vb, wb)
+            SCG_SUM4(vc, wc)
         }
-        SCG_STRIP(a0, A0, u0, y0) SCG_STRIP(a1, A1, u1, y1) SCG_STRIP(a2, A2, u0, y0) SCG_STRIP(a3, A3, u1, y1)
-        D = A3 + DL;
+        SCG_SUM4(va, wa)
+        SCG_SUM4(vb, wb)
     }
-    // at most 7 strips left (t even): every load issued before the first sum
-    float2 v[7];
-    long long Dk[7];
-#pragma unroll
-    for (int k = 0; k < 7; ++k) {
-        Dk[k] = D + k * DL;
-        v[k] = t + k < n ? SCG_LD(Dk[k]) : make_float2(0.f, 0.f);
+    // fewer than 12 strips left (t a multiple of four): whole groups, then the rest
+    for (; t + 4 <= n; t += 4) {
+        SCG_ISSUE4(vc, wc)
+        SCG_SUM4(vc, wc)
     }
 #pragma unroll
-    for (int k = 0; k < 7; ++k)
+    for (int k = 0; k < 3; ++k) {
+        vc[k] = t + k < n ? SCG_LD(D) : make_float2(0.f, 0.f);
+        wc[k] = SCG_W(D);
+        D += DL;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
         if (t + k < n) {
-            if (k & 1) { SCG_STRIP(v[k], Dk[k], u1, y1) }
-            else { SCG_STRIP(v[k], Dk[k], u0, y0) }
+            if (k & 1) { u1 = fmaf(wc[k], vc[k].x - vc[k].y, u1); y1 += vc[k].y; }
+            else { u0 = fmaf(wc[k], vc[k].x - vc[k].y, u0); y0 += vc[k].y; }
         }
 }
+#undef SCG_ISSUE4
+#undef SCG_SUM4
+#undef SCG_W
 #undef SCG_LD
-#undef SCG_STRIP
 
 // Strips t in [0, N) whose crossing C(t) = C0 + t*SL (32.32) has floor in
 // [-1, N-1]: a FP32 estimate, then corrected exactly in integer arithmetic.
@@ -1183,13 +1199,17 @@ k_sino_pairs(const Prob<T>* __restrict__ probs, int dst) {
 // parts of one complex sequence z = a + i b.  The factors are real and even
 // (fac[k] = fac[P-k]), so filtering z filters a and b separately: the result
 // is filter(a) + i filter(b), one complex FFT pair for two rows.  The FFT is
-// radix-2 in shared memory: the forward transform decimates in time (input
-// loaded in bit-reversed order, output in natural order), the multiplication
-// by fac is done in place, and the inverse transform decimates in frequency
-// with conjugate twiddles (natural order in, bit-reversed order out), so no
-// reordering pass is needed: rows are read and written through the bit
-// reversal of their index.  Twiddles tw[j] = exp(-2 pi i j / P), j < P/2, and
-// the factors come from a table the host fills in FP64 once per problem.
+// radix-2 in shared memory: the forward transform decimates in frequency
+// (natural order in, spectrum out in bit-reversed order), the factors -- which
+// the host stores in that bit-reversed order -- are applied in place, and the
+// inverse transform decimates in time with conjugate twiddles (bit-reversed
+// order in, natural order out).  So rows are read and written in natural
+// order and no pass touches shared memory through a bit reversal (whose
+// power-of-two strides put a warp's accesses in one bank).  The twiddles
+// w_j = exp(-2 pi i j / P) come from a quarter table staged in shared memory
+// once per block (w_{j + P/4} = -i w_j), not from global memory in every
+// stage.  Twiddles and factors come from a table the host fills in FP64 once
+// per problem.
 //
 // mode: FILT_VIEW  pair view src -> pair view dst (the solvers' sinograms)
 //       FILT_PLAIN the caller's plain rows user_in -> user_out
@@ -1204,13 +1224,16 @@ k_filter(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int 
     const Prob<T>& P = probs[it.prob];
     if (P.st->done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C2* z = reinterpret_cast<C2*>(smem_raw);
     const int nb = P.nb, na = P.na, L = P.P;
     const int lg = 31 - __clz(L);
+    const int quarter = max(L >> 2, 1);
+    C2* z = reinterpret_cast<C2*>(smem_raw);              // [L] the row pair, natural order
+    C2* twq = z + L;                                       // [quarter] w_k = exp(-2 pi i k / L), k < L/4
     const int ra = 2 * it.u, rb = ra + 1;                 // the block's two rows (rb may be past the end)
     const bool has_b = rb < na;
-    const C* fac = P.taps;                                // [L] factors
+    const C* fac = P.taps;                                // [L] factors in bit-reversed order
     const C2* tw = reinterpret_cast<const C2*>(P.taps + L);   // [L/2] twiddles
+    for (int q = threadIdx.x; q < quarter; q += blockDim.x) twq[q] = tw[q];
     for (int q = threadIdx.x; q < L; q += blockDim.x) {
         C va = C(0), vb = C(0);
         if (q < nb) {
@@ -1226,45 +1249,57 @@ k_filter(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int 
         C2 v;
         v.x = va;
         v.y = vb;
-        z[__brev((unsigned)q) >> (32 - lg)] = v;
+        z[q] = v;
     }
     __syncthreads();
-    // forward: decimation in time, stages of length 2, 4, ..., L
-    for (int s = 1; s <= lg; ++s) {
-        const int half = 1 << (s - 1);
+    // w_k for k < L/2 from the quarter table: w_{k + L/4} = -i w_k
+    auto W = [&](int k) -> C2 {
+        if (k < quarter) return twq[k];
+        const C2 a = twq[k - quarter];
+        return C2{a.y, -a.x};
+    };
+    // forward: decimation in frequency (natural order in, bit-reversed out),
+    // spans L, L/2, ..., 2
+    for (int st = lg; st >= 1; --st) {
+        const int half = 1 << (st - 1);
+#pragma unroll 4
         for (int t = threadIdx.x; t < (L >> 1); t += blockDim.x) {
             const int pos = t & (half - 1);
-            const int i0 = ((t >> (s - 1)) << s) + pos, i1 = i0 + half;
-            const C2 w = tw[pos << (lg - s)];
+            const int i0 = ((t >> (st - 1)) << st) + pos, i1 = i0 + half;
+            const C2 w = W(pos << (lg - st));
             const C2 u = z[i0], v = z[i1];
-            const C vr = v.x * w.x - v.y * w.y, vi = v.x * w.y + v.y * w.x;
-            z[i0] = C2{u.x + vr, u.y + vi};
-            z[i1] = C2{u.x - vr, u.y - vi};
+            const C dr = u.x - v.x, di = u.y - v.y;
+            z[i0] = C2{u.x + v.x, u.y + v.y};
+            z[i1] = C2{dr * w.x - di * w.y, dr * w.y + di * w.x};   // (u - v) w
         }
         __syncthreads();
     }
+    // the factors, stored in the spectrum's bit-reversed order
+#pragma unroll 4
     for (int q = threadIdx.x; q < L; q += blockDim.x) {
         const C f = fac[q];
         const C2 v = z[q];
         z[q] = C2{v.x * f, v.y * f};
     }
     __syncthreads();
-    // inverse: decimation in frequency with conjugate twiddles, stages L ... 2
-    for (int s = lg; s >= 1; --s) {
-        const int half = 1 << (s - 1);
+    // inverse: decimation in time with conjugate twiddles (bit-reversed order
+    // in, natural out), spans 2, 4, ..., L
+    for (int st = 1; st <= lg; ++st) {
+        const int half = 1 << (st - 1);
+#pragma unroll 4
         for (int t = threadIdx.x; t < (L >> 1); t += blockDim.x) {
             const int pos = t & (half - 1);
-            const int i0 = ((t >> (s - 1)) << s) + pos, i1 = i0 + half;
-            const C2 w = tw[pos << (lg - s)];
+            const int i0 = ((t >> (st - 1)) << st) + pos, i1 = i0 + half;
+            const C2 w = W(pos << (lg - st));
             const C2 u = z[i0], v = z[i1];
-            const C dr = u.x - v.x, di = u.y - v.y;
-            z[i0] = C2{u.x + v.x, u.y + v.y};
-            z[i1] = C2{dr * w.x + di * w.y, di * w.x - dr * w.y};   // (u - v) conj(w)
+            const C vr = v.x * w.x + v.y * w.y, vi = v.y * w.x - v.x * w.y;   // v conj(w)
+            z[i0] = C2{u.x + vr, u.y + vi};
+            z[i1] = C2{u.x - vr, u.y - vi};
         }
         __syncthreads();
     }
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        const C2 v = z[__brev((unsigned)b) >> (32 - lg)];
+        const C2 v = z[b];
         if (mode == FILT_PLAIN) {
             P.user_out[(size_t)ra * nb + b] = to_s<typename Tr<T>::S>(v.x);
             if (has_b) P.user_out[(size_t)rb * nb + b] = to_s<typename Tr<T>::S>(v.y);

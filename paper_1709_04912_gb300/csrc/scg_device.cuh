@@ -65,7 +65,10 @@ __host__ __device__ constexpr int filter_length_of(int nb) {
     return P;
 }
 template <typename C>
-__host__ __device__ constexpr size_t filter_smem_bytes(int nb) { return 2 * sizeof(C) * (size_t)filter_length_of(nb); }
+// the row pair (P complex values) and the quarter twiddle table (max(P/4, 1))
+__host__ __device__ constexpr size_t filter_smem_bytes(int nb) {
+    return 2 * sizeof(C) * ((size_t)filter_length_of(nb) + (size_t)(filter_length_of(nb) / 4 > 0 ? filter_length_of(nb) / 4 : 1));
+}
 constexpr size_t kFilterSmemMax = 160 * 1024;   // largest FFT held in shared memory (FP32: n_bins <= 8192, FP64: 4096)
 
 enum ImgBuf { IB_X = 0, IB_XH, IB_P, IB_H, IB_G, IB_Z, IB_TVG, IB_AUX, IB_COUNT };

@@ -57,6 +57,16 @@ ShapeKey shape_key(int dev, int precision, const scg_geometry& g) {
     auto bucket = [](int v) { return (int)lround(2.0 * log2((double)v)); };
     return ShapeKey{dev, precision, bucket(g.n), bucket(g.n_angles), bucket(g.n_bins)};
 }
+// Projector work lists (longest blocks first), per exact geometry, shape and
+// angle block
+struct OrderKey {
+    int n, na, nb, shift, a_begin, na_total;
+    bool operator<(const OrderKey& o) const {
+        return std::tie(n, na, nb, shift, a_begin, na_total) < std::tie(o.n, o.na, o.nb, o.shift, o.a_begin, o.na_total);
+    }
+};
+std::mutex g_order_mu;
+std::map<OrderKey, std::shared_ptr<const ProjOrder>> g_orders;
 // FISTA's c^2 estimates, per device, precision and exact geometry
 std::map<std::tuple<int, int, int, int, int>, double> g_lipschitz;
 constexpr int kPowerIters = 100;
@@ -152,12 +162,14 @@ int solve_impl(const scg_geometry* g, int variant, int precision, const scg_para
         CK(cudaMemcpyAsync(base + pl.taps, ftab.data(), sizeof(C) * ftab.size(), cudaMemcpyHostToDevice, s));
     }
     {
-        const int rc = tune_proj_shape<T>(P, pl, reinterpret_cast<Prob<T>*>(base + pl.prob), *g, s, prm->proj_shape);
+        const int rc = tune_proj_shape<T>(P, pl, reinterpret_cast<Prob<T>*>(base + pl.prob), *g, s,
+                                          reinterpret_cast<Item*>(base + pl.proj_items), prm->proj_shape);
         if (rc != SCG_OK) return rc;
     }
     Runner<T> R{reinterpret_cast<const Prob<T>*>(base + pl.prob), pl.cnt_ray, pl.cnt_img, pl.cnt_row,
                 pl.cnt_proj, g->n_bins, s, 0};
     R.g_bp = pl.cnt_bp;
+    R.i_proj = reinterpret_cast<const Item*>(base + pl.proj_items);   // longest first
     const Program pg = make_program(prm, variant);
 
     if (resumed) {
@@ -416,8 +428,11 @@ int project_impl(const scg_geometry& g, const void* x, void* y, void* work, size
     rc = upload_prob<T>(P, pl, work, s);
     if (rc) return rc;
     const Prob<T>* d = reinterpret_cast<const Prob<T>*>(base + pl.prob);
+    rc = upload_proj_order(pl, base + pl.proj_items, g, s);
+    if (rc) return rc;
     launch_vec<T>(d, nullptr, pl.cnt_img, VEC_VIEWS, IB_AUX, FIN_NONE, s);
-    launch_project<T>(d, nullptr, pl.cnt_proj, SB_Q, PROJ_PLAIN_OUT, FIN_NONE, s);
+    launch_project<T>(d, reinterpret_cast<const Item*>(base + pl.proj_items), pl.cnt_proj, SB_Q, PROJ_PLAIN_OUT,
+                      FIN_NONE, s);
     CK(cudaGetLastError());
     return SCG_OK;
 }
@@ -520,12 +535,15 @@ int fbp_impl(const scg_geometry& g, const void* y, void* x, void* work, size_t w
 // Prepared operator pair: set up once, then each application is device work
 // only (descriptor update by a one-thread kernel, view or pair-row pass, and
 // the projector or backprojector).
-// Each application records CUDA events on its stream around the projector (or
-// gather) kernel alone -- not while the stream is being captured into a graph
-// -- so that scg_operator_kernel_ms can report that kernel's device time.
+// With timing on, each application records CUDA events on its stream around
+// the projector (or gather) kernel alone -- not while the stream is being
+// captured into a graph -- so that scg_operator_kernel_ms can report that
+// kernel's device time.  Off by default: the two records cost about 4 us of
+// device time per application.
 struct OperatorBase {
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // project start/end, backproject start/end
     bool timed[2] = {false, false};
+    bool timing = false;
     virtual ~OperatorBase() {
         for (auto e : ev)
             if (e) cudaEventDestroy(e);
@@ -537,6 +555,7 @@ struct OperatorBase {
     }
     // record event i on s unless s is capturing; returns whether it was recorded
     bool mark(int i, cudaStream_t s) {
+        if (!timing) return false;
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return false;
         return cudaEventRecord(ev[i], s) == cudaSuccess;
@@ -551,6 +570,7 @@ struct Operator final : OperatorBase {
     scg_geometry g;
     Plan pl;
     Prob<T>* d = nullptr;
+    const Item* order = nullptr;       // projector blocks, longest first
 
     int init(const scg_geometry& geo, void* work, size_t wb, cudaStream_t s, int a_begin = 0, int na_total = -1) {
         g = geo;
@@ -567,6 +587,9 @@ struct Operator final : OperatorBase {
             P.cnt_proj = pl.cnt_proj; P.proj_blocks = pl.proj_blocks; P.proj_shift = sh;
         }
         unsigned char* base = (unsigned char*)work;
+        order = reinterpret_cast<const Item*>(base + pl.proj_items);
+        rc = upload_proj_order(pl, base + pl.proj_items, g, s, a_begin, na_total);
+        if (rc) return rc;
         // zero pads of the views and of the pair rows, once
         CK(cudaMemsetAsync(base + pl.view_rm, 0, 2 * sizeof(E) * (size_t)g.n * pl.S, s));
         CK(cudaMemsetAsync(base + pl.view_cm, 0, 2 * sizeof(E) * (size_t)g.n * pl.S, s));
@@ -581,8 +604,8 @@ struct Operator final : OperatorBase {
         launch_set_io<T>(d, nullptr, (E*)y, (E*)const_cast<void*>(x), s);
         launch_vec<T>(d, nullptr, pl.cnt_img, VEC_VIEWS, IB_AUX, FIN_NONE, s);
         const bool t0 = mark(0, s);
-        launch_project<T>(d, nullptr, pl.cnt_proj, SB_Q, PROJ_PLAIN_OUT, FIN_NONE, s);
-        timed[0] = t0 && mark(1, s);
+        launch_project<T>(d, order, pl.cnt_proj, SB_Q, PROJ_PLAIN_OUT, FIN_NONE, s);
+        if (t0) timed[0] = mark(1, s);
         CK(cudaGetLastError());
         return SCG_OK;
     }
@@ -591,7 +614,7 @@ struct Operator final : OperatorBase {
         launch_sino_pairs<T>(d, pl.cnt_ray, SB_R, s);
         const bool t0 = mark(2, s);
         launch_backproject<T>(d, nullptr, pl.cnt_bp, 1, SB_R, SB_R, IB_AUX, IB_AUX, FIN_NONE, s);
-        timed[1] = t0 && mark(3, s);
+        if (t0) timed[1] = mark(3, s);
         CK(cudaGetLastError());
         return SCG_OK;
     }
@@ -690,6 +713,7 @@ int batch_impl(const scg_problem* pr, int count, int variant, int precision, con
     memset(probs.data(), 0, sizeof(Prob<T>) * probs.size());
     std::vector<std::vector<Item>> items(K_COUNT);
     for (int k = 0; k < K_COUNT; ++k) items[k].reserve(bp.cap_items[k]);
+    std::vector<float> proj_cost;
     CK(cudaMemsetAsync(base, 0, bp.total, s));
     Prob<T>* slots = reinterpret_cast<Prob<T>*>(base + bp.probs);
     for (int i = 0; i < count; ++i) {
@@ -712,13 +736,16 @@ int batch_impl(const scg_problem* pr, int count, int variant, int precision, con
             CK(cudaMemcpyAsync(rb + pl.taps, ftab.data(), sizeof(C) * ftab.size(), cudaMemcpyHostToDevice, s));
         }
         // the problem's own slot serves the shape tuner (a single-problem launch)
-        const int rc = tune_proj_shape<T>(P, pl, slots + i, pr[i].geometry, s, prm->proj_shape);
+        const int rc = tune_proj_shape<T>(P, pl, slots + i, pr[i].geometry, s,
+                                          reinterpret_cast<Item*>(rb + pl.proj_items), prm->proj_shape);
         if (rc != SCG_OK) return rc;
         probs[i] = P;
-        append_items(pl, i, items.data());
+        const auto po = proj_order(pr[i].geometry.n, pr[i].geometry.n_angles, pr[i].geometry.n_bins, pl.proj_shift);
+        append_items(pl, i, items.data(), po.get(), &proj_cost);
         // (pageable host sources are staged before cudaMemcpyAsync returns,
         // so st and ang may be reused for the next problem)
     }
+    sort_longest_first(items[K_PROJ], proj_cost);     // all problems' projector blocks, longest first
     // placeholder problem for the padding items: stopped for good
     DevState stopped;
     memset(&stopped, 0, sizeof(stopped));
@@ -868,6 +895,19 @@ int proj_shape_lookup(int dev, int precision, const scg_geometry& g) {
 void proj_shape_store(int dev, int precision, const scg_geometry& g, int shift) {
     std::lock_guard<std::mutex> lk(g_shape_mu);
     g_shapes[shape_key(dev, precision, g)] = shift;
+}
+std::shared_ptr<const ProjOrder> proj_order(int n, int na, int nb, int shift, int a_begin, int na_total) {
+    if (na_total < 0) na_total = na;
+    const OrderKey key{n, na, nb, shift, a_begin, na_total};
+    std::lock_guard<std::mutex> lk(g_order_mu);
+    auto it = g_orders.find(key);
+    if (it != g_orders.end()) return it->second;
+    std::vector<Angle<double>> ang;
+    fill_angles<double>(ang, na, n, 1.0, a_begin, na_total);
+    auto o = std::make_shared<const ProjOrder>(make_proj_order(n, nb, shift, ang));
+    if (g_orders.size() >= 256) g_orders.clear();
+    g_orders[key] = o;
+    return o;
 }
 }  // namespace host
 }  // namespace scg
@@ -1025,6 +1065,10 @@ int scg_release(void) {
     for (auto& kv : g_pinned) cudaFreeHost(kv.second);
     g_pinned.clear();
     scg::noalloc_forget();
+    {
+        std::lock_guard<std::mutex> lo(g_order_mu);
+        g_orders.clear();
+    }
     return rc;
 }
 
@@ -1046,6 +1090,12 @@ int scg_operator_create_angles(const scg_geometry* g, int a_begin, int a_count, 
     if (rc == SCG_OK) rc = impl->make_events();
     if (rc != SCG_OK) { delete impl; return rc; }
     *out = new scg_operator{impl};
+    return SCG_OK;
+}
+
+int scg_operator_timing(scg_operator* op, int enable) {
+    if (!op) return SCG_ERR_INVALID;
+    op->impl->timing = enable != 0;
     return SCG_OK;
 }
 

@@ -123,6 +123,8 @@ def load(build_if_needed: bool = True):
     L.scg_operator_destroy.argtypes = [vp]
     L.scg_operator_kernel_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
     L.scg_operator_kernel_ms.restype = i
+    L.scg_operator_timing.argtypes = [vp, i]
+    L.scg_operator_timing.restype = i
     for name in ("scg_operator_create", "scg_operator_project", "scg_operator_backproject",
                  "scg_operator_destroy"):
         getattr(L, name).restype = i
@@ -572,10 +574,12 @@ class Operator:
     captured in a CUDA graph."""
 
     def __init__(self, n: int, n_angles: int, n_bins: int, dtype=torch.float32, device="cuda:0",
-                 angles: tuple | None = None):
+                 angles: tuple | None = None, timing: bool = False):
         """``angles=(a_begin, a_count)``: the operator of that block of the
         scan's angles (scg_operator_create_angles); sinograms are then
-        a_count x n_bins."""
+        a_count x n_bins.  ``timing``: record the kernels' own device times
+        for kernel_ms() (scg_operator_timing; costs a few microseconds per
+        application)."""
         L = load()
         a0, na_loc = (0, int(n_angles)) if angles is None else (int(angles[0]), int(angles[1]))
         self.n, self.na, self.nb = int(n), na_loc, int(n_bins)
@@ -590,6 +594,11 @@ class Operator:
                                             self.work.numel(), _stream(self.device), ctypes.byref(h)),
                "scg_operator_create_angles")
         self._h = h
+        if timing:
+            self.set_timing(True)
+
+    def set_timing(self, enable: bool):
+        _check(load().scg_operator_timing(self._h, int(bool(enable))), "scg_operator_timing")
 
     def project(self, x: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
         if out is None:
@@ -606,8 +615,9 @@ class Operator:
         return out
 
     def kernel_ms(self):
-        """(projector, gather) kernel device times of the last project / backproject
-        calls (scg_operator_kernel_ms); None for a kernel not yet timed."""
+        """(projector, gather) kernel device times of the last timed project /
+        backproject calls (scg_operator_kernel_ms); None for a kernel not yet
+        timed."""
         out = []
         for which in (0, 1):
             f = ctypes.c_float(0.0)

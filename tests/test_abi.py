@@ -204,6 +204,7 @@ def test_operator_rejects_bad_arguments_without_device_work(lib):
     assert lib.scg_operator_create(ctypes.byref(g), 7, fake, 1 << 20, None, ctypes.byref(h)) == -5
     assert lib.scg_operator_project(None, fake, fake, None) == -1
     assert lib.scg_operator_destroy(None) == -1
+    assert lib.scg_operator_timing(None, 1) == -1
 
 
 def test_release_with_nothing_cached(lib):

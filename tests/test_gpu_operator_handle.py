@@ -79,16 +79,22 @@ def test_projector_output_does_not_depend_on_the_tuned_shape():
 
 def test_operator_kernel_times_are_recorded():
     # scg_operator_kernel_ms: the projector's and the gather's own device time
-    # from events the library records around the kernel alone; a call captured
-    # into a graph records none
+    # from events the library records around the kernel alone, once timing is
+    # on; untimed applications and calls captured into a graph record none
     n, na, nb = 128, 90, 183
     op = scg.Operator(n, na, nb, torch.float32, DEV)
-    assert op.kernel_ms() == (None, None)
     x = torch.rand((n, n), device=DEV)
+    y = op.project(x)
+    op.backproject(y)
+    assert op.kernel_ms() == (None, None)
+    op.set_timing(True)
     y = op.project(x)
     tp, tb = op.kernel_ms()
     assert tp is not None and tp > 0.0 and tb is None
     op.backproject(y)
     tp2, tb2 = op.kernel_ms()
     assert tp2 == tp and tb2 is not None and tb2 > 0.0
+    op.set_timing(False)
+    op.project(x)
+    assert op.kernel_ms() == (tp, tb2)          # the last timed calls' values
     op.close()
