@@ -52,7 +52,8 @@ typedef enum {
     SCG_OK = 0,               /* finished; for solves: f(output) <= eps         */
     SCG_WARN_MAX_ITER = 1,    /* solve stopped at max_iter with f > eps          */
     SCG_ERR_INVALID = -1,     /* bad geometry/size/pointer/parameter             */
-    SCG_ERR_CUDA = -2,        /* a CUDA runtime call failed                      */
+    SCG_ERR_CUDA = -2,        /* a CUDA runtime call failed, or a kernel's       */
+                              /* bounded wait for its own copies ran out         */
     SCG_ERR_WORKSPACE = -3,   /* workspace too small or misaligned               */
     SCG_ERR_BREAKDOWN = -4,   /* zero or non-finite CG denominator               */
     SCG_ERR_UNSUPPORTED = -5  /* precision/variant combination not available     */

@@ -10,6 +10,8 @@
 #include <memory>
 #include <vector>
 
+#include <cuda.h>   // CUtensorMap and its encoder's signature (the encoder is resolved at run time)
+
 #include "scg_kernels.h"
 
 namespace scg {
@@ -17,6 +19,7 @@ namespace host {
 
 constexpr int kMaxTraceRows = 4096;
 constexpr size_t kAlign = 256;
+constexpr size_t kMapBytes = kSinoMapBytes;       // one CUtensorMap
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 inline int round_up4(int v) { return (v + 3) / 4 * 4; }
@@ -115,7 +118,7 @@ inline double system_scale(const scg_geometry& g, int precision) {
 
 // Workspace plan: byte offsets of every segment.
 struct Plan {
-    size_t state, prob, ang, taps, partials, counter, trace, proj_items;
+    size_t state, prob, ang, taps, partials, counter, trace, proj_items, maps;
     size_t img[IB_COUNT];
     size_t dual[4];
     size_t view_rm, view_cm;
@@ -179,6 +182,7 @@ inline Plan make_plan(const scg_geometry& g, int variant, int precision, int kin
     p.partials = take(sizeof(double) * kSlots * (size_t)maxcnt);
     p.part_cap = maxcnt;
     p.proj_items = take(sizeof(Item) * (size_t)max_proj);
+    p.maps = take(kMapBytes * SB_COUNT);          // TMA maps of the sinogram views (kAlign >= 128)
     p.counter = take(sizeof(unsigned) * 4);
     p.view_rm = take(2 * tsize * (size_t)N * p.S);
     p.view_cm = take(2 * tsize * (size_t)N * p.S);
@@ -404,6 +408,48 @@ Prob<T> make_prob(const scg_geometry& g, const Plan& pl, unsigned char* base, do
         cudaError_t e_ = (call);                   \
         if (e_ != cudaSuccess) return SCG_ERR_CUDA; \
     } while (0)
+
+// cuTensorMapEncodeTiled, resolved once through the runtime's driver entry
+// point (no link against the driver library); null if unavailable.
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn tensor_map_encoder();
+
+// TMA maps of a problem's sinogram views, written to base + pl.maps and
+// pointed to by P.sino_map (FP32 and 16-bit storage; the FP64 gather copies
+// with cp.async and gets none).  Map q describes sino[q] as na rows of SB
+// pairs, each pair one 8-byte (FP32) or 4-byte (16-bit) element; a box is one
+// row of band_slots pairs, the gather's band of one angle.  Elements outside
+// the view read as zero, as the band's zero-fill requires.  Call after every
+// change of the sinogram views' addresses (a map holds the address).
+template <typename T>
+int upload_sino_maps(Prob<T>& P, const Plan& pl, unsigned char* base, cudaStream_t s) {
+    P.sino_map = nullptr;
+    if constexpr (!std::is_same<T, double>::value) {
+        using S2 = typename Tr<T>::S2;
+        static_assert(sizeof(CUtensorMap) == kMapBytes, "one map per 128 bytes");
+        const EncodeTiledFn enc = tensor_map_encoder();
+        if (!enc) return SCG_ERR_CUDA;
+        CUtensorMap maps[SB_COUNT];
+        memset(maps, 0, sizeof(maps));
+        for (int q = 0; q < SB_COUNT; ++q) {
+            if (!P.sino[q]) continue;
+            const cuuint64_t dims[2] = {(cuuint64_t)P.SB, (cuuint64_t)P.na};
+            const cuuint64_t strides[1] = {(cuuint64_t)P.SB * sizeof(S2)};
+            const cuuint32_t box[2] = {(cuuint32_t)band_slots<S2>(), 1u};
+            const cuuint32_t estr[2] = {1u, 1u};
+            const CUresult r = enc(&maps[q], sizeof(S2) == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32,
+                                   2, (void*)P.sino[q], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return SCG_ERR_CUDA;
+        }
+        CK(cudaMemcpyAsync(base + pl.maps, maps, sizeof(maps), cudaMemcpyHostToDevice, s));
+        P.sino_map = base + pl.maps;
+    }
+    return SCG_OK;
+}
 
 // The projector work list of one geometry and shape (make_proj_order), cached
 // for the life of the process; a_begin / na_total as for fill_angles.

@@ -324,7 +324,6 @@ k_project(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int
 // into integer + fraction; each pixel adds only its small in-tile offset
 // (9.23 fixed point in the FP32 kernel: the fraction bits are directly a
 // float mantissa).
-template <typename S2> constexpr int band_slots() { return sizeof(S2) >= 8 ? 48 : 52; }
 // Tile height, pixels per thread, angles per chunk, and blocks per tile (CL
 // blocks -- a thread-block cluster -- take consecutive parts of the angles of
 // one tile; blocks 1..CL-1 hand their sums to block 0 through distributed
@@ -352,6 +351,35 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
+// TMA and mbarrier (FP32 / 16-bit gather).  One mbarrier per band buffer, one
+// arrival (the expect_tx of the chunk's bytes) per phase.
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned mb) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned mb, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes) : "memory");
+}
+// Waits for the phase of the given parity to complete, for at most about
+// 2^28 SM cycles (~0.13 s); returns false if the wait ran out.
+__device__ __forceinline__ bool mbar_wait(unsigned mb, unsigned parity) {
+    const long long t0 = clock64();
+    for (;;) {
+        unsigned done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(mb), "r"(parity) : "memory");
+        if (done) return true;
+        if (clock64() - t0 > (1LL << 28)) return false;
+    }
+}
+// One box of a 2-D tensor map (x innermost, in elements) into shared memory,
+// completing its bytes on mbarrier mb.
+__device__ __forceinline__ void tma_load_2d(unsigned dst, const void* map, int x, int y, unsigned mb) {
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+                 ::"r"(dst), "l"(map), "r"(x), "r"(y), "r"(mb) : "memory");
+}
+
 // Per-angle row of the FP32 gather (two 16-byte shared loads).
 struct __align__(16) BpRowF {
     int base;        // band index of the tile origin's projection, in 9.23 fixed point
@@ -371,8 +399,13 @@ __device__ __forceinline__ long long tile_origin_fx(const Angle<float>& g, int X
     return ((long long)(nb - 1) << 31) + (((long long)X2 * g.c_fx + (long long)Y2 * g.s_fx) >> 1);
 }
 
+// Gather blocks per SM the register allocation is sized for: seven with one
+// right-hand side (72 registers; at 512^2 the 1024 blocks then run in one wave
+// on 152 SMs), six with two, whose sums need more registers.
+template <int NRHS> constexpr int back_min_blocks() { return NRHS == 1 ? 7 : 6; }
+
 template <typename T, int NRHS>
-__global__ void __launch_bounds__(kBackThreads)
+__global__ void __launch_bounds__(kBackThreads, back_min_blocks<NRHS>())
 k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int src0,
               int src1, int dst0, int dst1, int step) {
     using S2 = typename Tr<T>::S2;
@@ -392,9 +425,13 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
     const Item it = decode_item(probs, items, 4, (int)(blockIdx.x / CL));
     const Prob<T>& P = probs[it.prob];
     if (P.st->done) return;                      // the same flag for every block of a cluster
+    // FP32 / 16-bit: bands arrive by TMA, one box (one angle row of kBand pairs)
+    // per angle into a row padded to 128 bytes; FP64: cp.async, 16 bytes a copy
+    constexpr int kBandS = kF32 ? (kBand * (int)sizeof(S2) + 127) / 128 * 128 / (int)sizeof(S2) : kBand;
     __shared__ Row rows[2][CH];
-    __shared__ int slo[2][CH];                   // first slot of each band in its sinogram row
-    __shared__ __align__(16) S2 band[2][NRHS][CH][kBand];
+    __shared__ int slo[2][CH];                   // first slot of each band in its sinogram row (FP64)
+    __shared__ __align__(128) S2 band[2][NRHS][CH][kBandS];
+    __shared__ __align__(8) unsigned long long mbar[2];   // TMA completion per band buffer
     const int N = P.n, na = P.na, nb = P.nb, SB = P.SB;
     const int tl = threadIdx.x;
     const int nap = (na + CL - 1) / CL;          // angles of each block
@@ -406,27 +443,16 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
     const S2* R[2] = {P.sino[src0], NRHS == 2 ? P.sino[src1] : P.sino[src0]};
     const int nchunks = (nap + CH - 1) / CH;     // the same for every block of the cluster
 
+    // FP64: the row constants of chunk ch (threads q < CH) for the cp.async copies
     auto stage_rows = [&](int ch) {
-        const int q = tl;
-        const int a = a_begin + ch * CH + q;
-        if (q < CH && a < a_end) {
-            const Angle<C> g = P.ang[a];
-            // band: slots the tile can touch, from floor(projection of the origin)
-            // + floor((kTileW-1) min(c, 0)) - 1, rounded down to a 16-byte boundary
-            const int lo = (int)tfloor(C(kTileW - 1) * tmin(g.c, C(0))) - 1;
-            if constexpr (kF32) {
-                const long long cb = tile_origin_fx(g, X2, Y2, nb);
-                const int I = (int)(cb >> 32);
-                const int s_lo = (I + kSPad + lo) & ~(kSlotsPerSeg - 1);
-                BpRowF r;
-                // 9.23: integer part = band index of floor(cb), fraction = cb's
-                r.base = ((I + kSPad - s_lo) << 23) | (int)((unsigned)cb >> 9);
-                r.c23 = g.c23; r.s23 = g.s23;
-                r.kb = g.kb; r.hb0p = g.hb0p; r.hb1p = g.hb1p;
-                r.pad_[0] = r.pad_[1] = 0;
-                rows[ch & 1][q] = r;
-                slo[ch & 1][q] = s_lo;
-            } else {
+        if constexpr (!kF32) {
+            const int q = tl;
+            const int a = a_begin + ch * CH + q;
+            if (q < CH && a < a_end) {
+                const Angle<C> g = P.ang[a];
+                // band: slots the tile can touch, from floor(projection of the origin)
+                // + floor((kTileW-1) min(c, 0)) - 1, rounded down to a 16-byte boundary
+                const int lo = (int)tfloor(C(kTileW - 1) * tmin(g.c, C(0))) - 1;
                 const double cbt = 0.5 * (double)(nb - 1) + 0.5 * (double)X2 * g.c_d + 0.5 * (double)Y2 * g.s_d;
                 const double fl = floor(cbt);
                 const int I = (int)fl;
@@ -437,6 +463,46 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
                 r.rel = I + kSPad - s_lo;
                 rows[ch & 1][q] = r;
                 slo[ch & 1][q] = s_lo;
+            }
+        }
+    };
+    // FP32 / 16-bit: the row constants of chunk ch and the TMA copies of its
+    // bands, spread over the block: lanes 0..CH/4-1 of warp w take the chunk's
+    // angles w*CH/4 .. (w+1)*CH/4-1 (box origin: the band's first slot, rounded
+    // down to a 16-byte boundary as TMA requires; slots beyond the row read as
+    // zero).  Thread 0 adds the chunk's bytes to the barrier's expected count;
+    // a copy may complete before that (the count may go below zero), and the
+    // phase still ends only after thread 0's arrival.
+    auto stage_tma = [&](int ch) {
+        if constexpr (kF32) {
+            constexpr int kPerWarp = CH / 4;
+            static_assert(kBackThreads == 128 && CH % 4 == 0, "four warps share a chunk's rows");
+            const int buf = ch & 1;
+            const int a0 = a_begin + ch * CH;
+            const int cnt = min(CH, a_end - a0);          // may be <= 0 (a part with no angles)
+            const unsigned mb = smem_addr(&mbar[buf]);
+            if (tl == 0) mbar_expect_tx(mb, cnt > 0 ? (unsigned)(cnt * NRHS * kBand * (int)sizeof(S2)) : 0u);
+            const int lane = tl & 31;
+            const int q = (tl >> 5) * kPerWarp + lane;
+            if (lane < kPerWarp && q < cnt) {
+                const Angle<C> g = P.ang[a0 + q];
+                const int lo = (int)tfloor(C(kTileW - 1) * tmin(g.c, C(0))) - 1;
+                const long long cb = tile_origin_fx(g, X2, Y2, nb);
+                const int I = (int)(cb >> 32);
+                const int s_lo = (I + kSPad + lo) & ~(kSlotsPerSeg - 1);
+                BpRowF r;
+                r.base = ((I + kSPad - s_lo) << 23) | (int)((unsigned)cb >> 9);
+                r.c23 = g.c23; r.s23 = g.s23;
+                r.kb = g.kb; r.hb0p = g.hb0p; r.hb1p = g.hb1p;
+                r.pad_[0] = r.pad_[1] = 0;
+                rows[buf][q] = r;
+                // this buffer was last read through the generic proxy (before the
+                // block barrier that ended that chunk); order those reads first
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+#pragma unroll
+                for (int h = 0; h < NRHS; ++h)
+                    tma_load_2d(smem_addr(&band[buf][h][q][0]),
+                                P.sino_map + (size_t)(h == 0 ? src0 : src1) * kSinoMapBytes, s_lo, a0 + q, mb);
             }
         }
     };
@@ -461,19 +527,41 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
     for (int h = 0; h < NRHS; ++h)
 #pragma unroll
         for (int k = 0; k < PIX; ++k) acc[h][k] = C(0);
-    stage_rows(0);
-    __syncthreads();
-    stage_copy(0);
+    bool ok = true;                              // every wait of this thread on its block's copies completed
+    if constexpr (kF32) {
+        if (tl == 0) {
+            mbar_init(smem_addr(&mbar[0]));
+            mbar_init(smem_addr(&mbar[1]));
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+        stage_tma(0);
+        __syncthreads();
+    } else {
+        stage_rows(0);
+        __syncthreads();
+        stage_copy(0);
+    }
     for (int ch = 0; ch < nchunks; ++ch) {
         const bool more = ch + 1 < nchunks;
-        if (more) stage_rows(ch + 1);
-        __syncthreads();
-        if (more) { stage_copy(ch + 1); cp_async_wait<1>(); }
-        else cp_async_wait<0>();
-        __syncthreads();
+        if constexpr (kF32) {
+            // stage the next chunk (rows and copies into the other buffer, free
+            // since the barrier that ended the previous chunk), then wait for this
+            // chunk's bands -- always, even after a wait ran out, so no copy is
+            // still in flight when the block ends
+            if (more) stage_tma(ch + 1);
+            const bool w = mbar_wait(smem_addr(&mbar[ch & 1]), (unsigned)((ch >> 1) & 1));
+            ok = ok && w;
+        } else {
+            if (more) stage_rows(ch + 1);
+            __syncthreads();
+            if (more) { stage_copy(ch + 1); cp_async_wait<1>(); }
+            else cp_async_wait<0>();
+            __syncthreads();
+        }
         const int cnt = min(CH, a_end - (a_begin + ch * CH));
         const int buf = ch & 1;
-        if (j < N && ti0 + ty < N) {
+        if (ok && j < N && ti0 + ty < N) {
             if constexpr (kF32) {
 #pragma unroll 4
                 for (int q = 0; q < cnt; ++q) {              // 4 angles in flight: measured 5 % faster than 2
@@ -517,6 +605,9 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
             }
         }
         __syncthreads();
+    }
+    if constexpr (kF32) {
+        if (!ok) atomicExch(&P.st->dev_error, 1);   // a band never arrived: the sums are not valid
     }
     // block 0's epilogue operands (h and p for the fused dots), loaded before
     // the cluster barriers so that their latency overlaps the hand-over
@@ -1128,6 +1219,27 @@ k_fgp(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int j, 
     const C2* Wold = reinterpret_cast<const C2*>(P.dual[(j + 1) & 1]);
     C2* Wnew = reinterpret_cast<C2*>(P.dual[j & 1]);
     C2* Rnext = reinterpret_cast<C2*>(P.dual[2 + ((j + 1) & 1)]);
+    // the loads that need nothing staged -- b on the w points, the previous dual
+    // field at this thread's term -- are issued first, so that their latency
+    // overlaps the halo's
+    constexpr int kWPts = (kTileH + 1) * (kTileW + 1);
+    constexpr int kWIters = (kWPts + kTileThreads - 1) / kTileThreads;
+    const C* B = P.img[IB_Z];
+    C bv[kWIters];
+#pragma unroll
+    for (int k = 0; k < kWIters; ++k) {
+        const int q = threadIdx.x + k * kTileThreads;
+        const int a = i0 + q / (kTileW + 1), b = j0 + q % (kTileW + 1);
+        bv[k] = q < kWPts && a < N && b < N ? B[(size_t)a * N + b] : C(0);
+    }
+    const int ty = threadIdx.x / kTileW, tx = threadIdx.x % kTileW;
+    const int i = i0 + ty, jc = j0 + tx;
+    const bool term = i < m && jc < m;
+    const size_t idx = (size_t)i * N + jc;
+    C2 wo;
+    wo.x = C(0);
+    wo.y = C(0);
+    if (!start && term) wo = Wold[idx];
     for (int q = threadIdx.x; q < (kTileH + 2) * (kTileW + 2); q += kTileThreads) {
         const int ii = q / (kTileW + 2), jj = q % (kTileW + 2);
         const int ti = i0 - 1 + ii, tj = j0 - 1 + jj;
@@ -1138,22 +1250,22 @@ k_fgp(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int j, 
         rs[ii][jj] = v;
     }
     __syncthreads();
-    const C* B = P.img[IB_Z];
-    for (int q = threadIdx.x; q < (kTileH + 1) * (kTileW + 1); q += kTileThreads) {
+#pragma unroll
+    for (int k = 0; k < kWIters; ++k) {
+        const int q = threadIdx.x + k * kTileThreads;
+        if (q >= kWPts) break;
         const int ii = q / (kTileW + 1), jj = q % (kTileW + 1);
         const int a = i0 + ii, b = j0 + jj;
         C w = C(0);
         if (a < N && b < N) {
             // (L^T r) at pixel (a, b): -(p + q) of term (a, b), +p of (a-1, b), +q of (a, b-1)
             const C lt = -(rs[ii + 1][jj + 1].x + rs[ii + 1][jj + 1].y) + rs[ii][jj + 1].x + rs[ii + 1][jj].y;
-            w = fma(-alpha, lt, B[(size_t)a * N + b]);
+            w = fma(-alpha, lt, bv[k]);
         }
         ws[ii][jj] = w;
     }
     __syncthreads();
-    const int ty = threadIdx.x / kTileW, tx = threadIdx.x % kTileW;
-    const int i = i0 + ty, jc = j0 + tx;
-    if (i >= m || jc >= m) return;
+    if (!term) return;
     const C w0 = ws[ty][tx];
     const C2 r = rs[ty + 1][tx + 1];
     const C ax = fma(ws[ty + 1][tx] - w0, inv8a, r.x);      // r + (L w) / (8 alpha)
@@ -1163,11 +1275,6 @@ k_fgp(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int j, 
     C2 wn;
     wn.x = ax * sc;
     wn.y = ay * sc;
-    const size_t idx = (size_t)i * N + jc;
-    C2 wo;
-    wo.x = C(0);
-    wo.y = C(0);
-    if (!start) wo = Wold[idx];
     C2 rn;
     rn.x = fma(beta, wn.x - wo.x, wn.x);
     rn.y = fma(beta, wn.y - wo.y, wn.y);
@@ -1320,6 +1427,7 @@ k_filter(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int 
 // ends even if the stop flag were never set.
 __global__ void k_loop_cond(DevState* st, cudaGraphConditionalHandle h) {
     if (threadIdx.x != 0) return;
+    if (st->dev_error) st->done = 1;          // a bounded wait ran out: stop (reported as SCG_ERR_CUDA)
     unsigned more = st->done ? 0u : 1u;
     if (st->bodies >= st->max_bodies) more = 0u;
     st->bodies += (int)more;
@@ -1338,7 +1446,7 @@ __global__ void k_write_result(const DevState* st, scg_result* res, double s2, i
     if (threadIdx.x != 0) return;
     res->iters = st->iters;
     res->k_final = st->k;
-    res->status = st->status;
+    res->status = st->dev_error ? SCG_ERR_CUDA : st->status;
     res->f_final = (cg_family ? st->f_final : st->f_half) / s2;
     res->tv_final = st->tv_final;
     res->ell = st->ell;
@@ -1403,8 +1511,11 @@ __global__ void k_loop_cond_batch(const Prob<T>* probs, BatchState* bs, cudaGrap
     __shared__ int any;
     if (threadIdx.x == 0) any = 0;
     __syncthreads();
-    for (int i = threadIdx.x; i < bs->count; i += blockDim.x)
-        if (!probs[i].st->done) atomicOr(&any, 1);
+    for (int i = threadIdx.x; i < bs->count; i += blockDim.x) {
+        DevState* st = probs[i].st;
+        if (st->dev_error) st->done = 1;      // a bounded wait ran out: stop that problem
+        if (!st->done) atomicOr(&any, 1);
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned more = any ? 1u : 0u;

@@ -71,6 +71,11 @@ __host__ __device__ constexpr size_t filter_smem_bytes(int nb) {
 }
 constexpr size_t kFilterSmemMax = 160 * 1024;   // largest FFT held in shared memory (FP32: n_bins <= 8192, FP64: 4096)
 
+// Sinogram pair slots the gather stages per angle for one 32-pixel-wide tile
+// (see k_backproject): 48 for FP32 pairs, 52 for 16-bit pairs.
+template <typename S2> __host__ __device__ constexpr int band_slots() { return sizeof(S2) >= 8 ? 48 : 52; }
+constexpr int kSinoMapBytes = 128;   // one TMA tensor map (CUtensorMap)
+
 enum ImgBuf { IB_X = 0, IB_XH, IB_P, IB_H, IB_G, IB_Z, IB_TVG, IB_AUX, IB_COUNT };
 enum SinoBuf { SB_R = 0, SB_Q, SB_W, SB_V, SB_COUNT };
 // FISTA keeps x_k in kFistaX[k % 3] and its residual A x_k - y in kFistaQ[k % 3]
@@ -158,6 +163,8 @@ struct DevState {
     int in_init, variant, inner_stop, family;
     int bodies, max_bodies;  // loop bodies started by the device loop, and its hard cap
     int pass_cands;          // candidates of the trial pass being finalised
+    int dev_error;           // set when a kernel's bounded wait on its own copies ran out (the solve
+                             // then stops and reports SCG_ERR_CUDA); fills padding, no size change
 };
 
 enum Family { FAM_CG = 0, FAM_S_PR = 1, FAM_S_K = 2, FAM_FISTA = 3 };
@@ -246,6 +253,8 @@ struct Prob {
     int part_cap;           // items per slot of `partials` (slot-major: partials[k * part_cap + item])
     pair_t* dual[4];        // FISTA's TV prox: dual fields w_j (0, 1) and momentum points (2, 3), one
                             // (p, q) pair per interior term (i, j) at i*N + j
+    const unsigned char* sino_map;   // SB_COUNT TMA tensor maps (128 bytes each): map q describes sino[q]
+                                     // as na rows of SB pairs (FP32 / 16-bit storage; null for FP64)
 };
 
 // ---------------------------------------------------------------------------
@@ -409,6 +418,7 @@ template <typename T> __device__ __noinline__ void finalize_rare(int step, const
 // each), the state machine runs on it in one thread, and the block writes it
 // back -- instead of one dependent global round trip per state field.
 static_assert(sizeof(DevState) % 8 == 0, "state copied as 8-byte words");
+static_assert(sizeof(DevState) == 496, "the state's size is part of the finalisers' register budget");
 constexpr int kStateWords = (int)(sizeof(DevState) / 8);
 // one word per thread: every kernel that finalises runs blocks of at least this many threads
 static_assert(kStateWords <= kBackThreads && kStateWords <= kTileThreads && kStateWords <= kRayBlock &&

@@ -375,6 +375,10 @@ private:
             P.y = static_cast<const E*>(r->p.y);
             P.img[IB_AUX] = static_cast<E*>(const_cast<void*>(r->p.x0));
             SCK(cudaMemsetAsync(rb, 0, pl.total, stream_));
+            {
+                const int rc = upload_sino_maps<T>(P, pl, rb, stream_);
+                if (rc != SCG_OK) return rc;
+            }
             DevState st = initial_state(&cfg_.params, r->p.eps * r->scale * r->scale, cfg_.variant);
             SCK(upload(rb + pl.state, &st, sizeof(st)));
             std::vector<Angle<C>> ang;
@@ -534,7 +538,7 @@ private:
             c.tag = r->tag;
             c.result.iters = st.iters;
             c.result.k_final = st.k;
-            c.result.status = st.status;
+            c.result.status = st.dev_error ? SCG_ERR_CUDA : st.status;
             c.result.f_final = (fam_ == FAM_CG ? st.f_final : st.f_half) / (r->scale * r->scale);
             c.result.tv_final = st.tv_final;
             c.result.ell = st.ell;

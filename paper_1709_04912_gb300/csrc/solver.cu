@@ -152,6 +152,10 @@ int solve_impl(const scg_geometry* g, int variant, int precision, const scg_para
     }
 
     CK(cudaMemsetAsync(base, 0, pl.total, s));
+    {
+        const int rc = upload_sino_maps<T>(P, pl, base, s);
+        if (rc != SCG_OK) return rc;
+    }
     CK(cudaMemcpyAsync(base + pl.state, &st, sizeof(st), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(base + pl.prob, &P, sizeof(P), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(base + pl.ang, ang.data(), sizeof(Angle<C>) * ang.size(), cudaMemcpyHostToDevice, s));
@@ -358,7 +362,8 @@ int solve_impl(const scg_geometry* g, int variant, int precision, const scg_para
     }
     res->iters = hs.iters;
     res->k_final = hs.k;
-    res->status = hs.status;
+    const int status = hs.dev_error ? SCG_ERR_CUDA : hs.status;   // dev_error: a device-side wait ran out
+    res->status = status;
     res->f_final = (fam == FAM_CG ? hs.f_final : hs.f_half) / s2;
     res->tv_final = hs.tv_final;
     res->ell = hs.ell;
@@ -381,7 +386,7 @@ int solve_impl(const scg_geometry* g, int variant, int precision, const scg_para
         final_state->gamma_fixed = hs.gamma_fixed;
         final_state->delta = hs.delta;
     }
-    return hs.status;
+    return status;
 }
 
 // ---------------------------------------------------------------------------
@@ -399,6 +404,10 @@ int op_setup(const scg_geometry& g, void* work, size_t work_bytes, cudaStream_t 
     Prob<T> P = make_prob<T>(g, pl, base);
     std::vector<Angle<C>> ang;
     fill_angles<C>(ang, g.n_angles, g.n, 1.0, a_begin, na_total);
+    {
+        const int rc = upload_sino_maps<T>(P, pl, base, s);
+        if (rc != SCG_OK) return rc;
+    }
     CK(cudaMemsetAsync(base + pl.state, 0, sizeof(DevState), s));
     CK(cudaMemsetAsync(base + pl.counter, 0, 16, s));
     CK(cudaMemcpyAsync(base + pl.ang, ang.data(), sizeof(Angle<C>) * ang.size(), cudaMemcpyHostToDevice, s));
@@ -722,6 +731,10 @@ int batch_impl(const scg_problem* pr, int count, int variant, int precision, con
         const double scale = system_scale(pr[i].geometry, prec_of<T>());
         scales[i] = scale;
         Prob<T> P = make_prob<T>(pr[i].geometry, pl, rb, scale);
+        {
+            const int rc = upload_sino_maps<T>(P, pl, rb, s);
+            if (rc != SCG_OK) return rc;
+        }
         P.y = (const E*)pr[i].y;
         P.img[IB_AUX] = (E*)pr[i].x0;
         DevState st = initial_state(prm, pr[i].eps * scale * scale, variant);
@@ -864,7 +877,7 @@ int batch_impl(const scg_problem* pr, int count, int variant, int precision, con
         memset(&r, 0, sizeof(r));
         r.iters = hs[i].iters;
         r.k_final = hs[i].k;
-        r.status = hs[i].status;
+        r.status = hs[i].dev_error ? SCG_ERR_CUDA : hs[i].status;
         r.f_final = (fam == FAM_CG ? hs[i].f_final : hs[i].f_half) / (scales[i] * scales[i]);
         r.tv_final = hs[i].tv_final;
         r.ell = hs[i].ell;
@@ -896,6 +909,18 @@ void proj_shape_store(int dev, int precision, const scg_geometry& g, int shift) 
     std::lock_guard<std::mutex> lk(g_shape_mu);
     g_shapes[shape_key(dev, precision, g)] = shift;
 }
+EncodeTiledFn tensor_map_encoder() {
+    static const EncodeTiledFn fn = []() -> EncodeTiledFn {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
 std::shared_ptr<const ProjOrder> proj_order(int n, int na, int nb, int shift, int a_begin, int na_total) {
     if (na_total < 0) na_total = na;
     const OrderKey key{n, na, nb, shift, a_begin, na_total};
