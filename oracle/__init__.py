@@ -26,7 +26,7 @@ _lib = None
 
 # variant names follow the paper's algorithm names
 VARIANTS = {"CG": 0, "PCG": 1, "S-CG": 2, "S-CG-CD": 3, "S-CG-K": 4, "S-PCG": 5, "S-PCG-K": 6}
-PERTURB = {"none": 0, "gamma": 1, "eta": 2}
+PERTURB = {"none": 0, "gamma": 1, "eta": 2, "prox": 3}
 STATUS = {0: "ok", 1: "max_iter", -1: "invalid", -4: "breakdown"}
 TRACE_FIELDS = ("k", "f_test", "tv_before", "tv_after", "trials", "accepted", "ell",
                 "gamma", "alpha", "beta", "margin", "f_after")
@@ -48,6 +48,7 @@ class Params(ctypes.Structure):
         ("filter_gain", ctypes.c_double),
         ("filter_identity", ctypes.c_int),
         ("max_iter", ctypes.c_int),
+        ("prox_iters", ctypes.c_int),
     ]
 
 
@@ -143,6 +144,8 @@ def lib():
         L.orc_norm_A.restype = d
         L.orc_perturb_gamma.argtypes = [i, dp, d, d, i, ctypes.POINTER(ctypes.c_longlong), dp, dp, ip]
         L.orc_perturb_gamma.restype = i
+        L.orc_perturb_prox.argtypes = [i, dp, d, d, i, ctypes.POINTER(ctypes.c_longlong), dp, dp]
+        L.orc_perturb_prox.restype = i
         L.orc_tv_prox.argtypes = [i, dp, d, i, i, dp, dp, dp]
         L.orc_fista.argtypes = [i, i, i, dp, dp, d, d, d, i, i, i, dp, ctypes.POINTER(Result), dp, i]
         L.orc_fista.restype = i
@@ -290,6 +293,20 @@ def perturb_gamma(x: np.ndarray, gamma0: float, a: float, max_trials: int, ell: 
     return xh, int(e.value), float(g.value), int(t.value), int(rc)
 
 
+def perturb_prox(x: np.ndarray, gamma0: float, a: float, prox_iters: int, ell: int = 0):
+    """One perturbation of the prox rule from global index ``ell``: returns
+    (x_half, ell after, lambda or 0, outcome) with outcome 1 perturbed, -1 zero
+    subgradient (x kept)."""
+    x = _f64(x)
+    n = x.shape[0]
+    xh = np.zeros_like(x)
+    e = ctypes.c_longlong(int(ell))
+    lam = np.zeros(1)
+    rc = lib().orc_perturb_prox(n, _dp(x), float(gamma0), float(a), int(prox_iters), ctypes.byref(e),
+                                _dp(xh), _dp(lam))
+    return xh, int(e.value), float(lam[0]), int(rc)
+
+
 def tv_prox(b: np.ndarray, alpha: float, iters: int, accel: bool = True, want_dual: bool = False):
     """prox of alpha TV at b by ``iters`` FGP steps (plain gradient projection
     with ``accel=False``); with ``want_dual`` also the dual field (p, q) on the
@@ -327,7 +344,7 @@ def fista(y: np.ndarray, n: int, eps: float, lam: float, c2: float, prox_iters: 
 def default_params(**kw) -> dict:
     p = dict(variant="S-CG", eps=1.0, perturb="gamma", gamma0=0.0, gamma0_rel=0.05,
              a=0.975, max_trials=32, eta0=0.0, K=2, k_inclusive=0, mu=0.0,
-             filter_gain=1.0, filter_identity=0, max_iter=100)
+             filter_gain=1.0, filter_identity=0, max_iter=100, prox_iters=20)
     p.update(kw)
     return p
 
@@ -361,7 +378,7 @@ def solve(y: np.ndarray, n: int, x0=None, callback=None, resume: dict | None = N
     prm = Params(VARIANTS[p["variant"]], p["eps"], PERTURB[p["perturb"]], p["gamma0"],
                  p["gamma0_rel"], p["a"], p["max_trials"], p["eta0"], p["K"],
                  p["k_inclusive"], p["mu"], p["filter_gain"], p["filter_identity"],
-                 p["max_iter"])
+                 p["max_iter"], p["prox_iters"])
     res = Result()
     x = np.zeros((n, n))
     rows = max(int(p["max_iter"]), 1)

@@ -507,7 +507,13 @@ static double* row_of(double* trace, int rows, int it)
  *    max_trials rejections x is kept.  Zero subgradient: x is kept, l is
  *    unchanged.
  *  eta rule (Appendix, Eq. up bnd u_k): u = eta0 ||g_k|| v with
- *    g_k = A^T(A x_k - y), applied without a TV test. */
+ *    g_k = A^T(A x_k - y), applied without a TV test.
+ *  prox rule (footnote to Eq. superiorized): x_{k+1/2} =
+ *    prox_{lambda TV}(x_k), the implicit counterpart of the gamma rule's step
+ *    x_k + gamma v = x_k - (gamma / ||dTV||) dTV: lambda = gamma_0 a^l /
+ *    ||dTV(x_k)||, gamma_0 fixed as in the gamma rule, FGP with prox_iters
+ *    steps.  A prox step cannot raise TV, so there is no trial: l <- l+1 once
+ *    per perturbed step.  Zero subgradient: x is kept, l unchanged. */
 static void perturb(orc_ctx* C, const double* xk, double* xh, double* trow)
 {
     size_t J = C->J;
@@ -539,6 +545,19 @@ static void perturb(orc_ctx* C, const double* xk, double* xh, double* trow)
     if (!C->gamma_fixed) {
         C->gamma0 = C->prm.gamma0_rel * sqrt(dot(xk, xk, J));
         C->gamma_fixed = 1;
+    }
+    if (C->prm.perturb == ORC_PERTURB_PROX) {
+        double gamma = C->gamma0 * pow(C->prm.a, (double)C->ell);
+        double lambda = gamma / gn;
+        orc_tv_prox(C->n, xk, lambda, C->prm.prox_iters, 1, xh, NULL, NULL);
+        C->ell += 1;
+        if (trow) {
+            trow[ORC_T_ACCEPTED] = 1;
+            trow[ORC_T_GAMMA] = lambda;
+            trow[ORC_T_TV_AFTER] = orc_tv(C->n, xh);
+            trow[ORC_T_ELL] = (double)C->ell;
+        }
+        return;
     }
     double margin = INFINITY;
     for (int t = 0; t < C->prm.max_trials; ++t) {
@@ -598,6 +617,38 @@ int orc_perturb_gamma(int n, const double* x, double gamma0, double a, int max_t
     *ell = C.ell;
     *gamma_out = row[ORC_T_ACCEPTED] == 1 ? row[ORC_T_GAMMA] : 0.0;
     *trials_out = (int)row[ORC_T_TRIALS];
+    free(C.tvg);
+    free(C.vdir);
+    free(C.ztrial);
+    return (int)row[ORC_T_ACCEPTED];
+}
+
+/* One step of the prox rule on its own (the perturb() the solvers call):
+ * x_half = prox_{lambda TV}(x) with lambda = gamma0 a^l / ||dTV(x)||, l
+ * starting at *ell (advanced by one when x is perturbed).  *lambda_out =
+ * lambda (0 if the subgradient is zero and x is kept).  Returns 1 perturbed,
+ * -1 not (zero subgradient). */
+int orc_perturb_prox(int n, const double* x, double gamma0, double a, int prox_iters,
+                     long long* ell, double* x_half, double* lambda_out)
+{
+    orc_ctx C;
+    memset(&C, 0, sizeof(C));
+    C.n = n;
+    C.J = (size_t)n * n;
+    C.prm.perturb = ORC_PERTURB_PROX;
+    C.prm.a = a;
+    C.prm.prox_iters = prox_iters;
+    C.gamma0 = gamma0;
+    C.gamma_fixed = 1;
+    C.ell = *ell;
+    C.tvg = vec(C.J);
+    C.vdir = vec(C.J);
+    C.ztrial = vec(C.J);
+    double row[ORC_NF];
+    for (int q = 0; q < ORC_NF; ++q) row[q] = 0.0;
+    perturb(&C, x, x_half, row);
+    *ell = C.ell;
+    *lambda_out = row[ORC_T_ACCEPTED] == 1 ? row[ORC_T_GAMMA] : 0.0;
     free(C.tvg);
     free(C.vdir);
     free(C.ztrial);

@@ -32,9 +32,11 @@ enum { ORC_CG = 0, ORC_PCG = 1, ORC_S_CG = 2, ORC_S_CG_CD = 3, ORC_S_CG_K = 4,
        ORC_S_PCG = 5, ORC_S_PCG_K = 6 };
 
 /* perturbation rules: none, the gamma_l = gamma0 * a^l sequence with a TV
- * acceptance test (Eq. gamma_sequence, Sec. 3), and the Appendix's
- * ||u_k|| = eta0 * ||g_k|| rule used by Proposition/Lemma of the Appendix */
-enum { ORC_PERTURB_NONE = 0, ORC_PERTURB_GAMMA = 1, ORC_PERTURB_ETA = 2 };
+ * acceptance test (Eq. gamma_sequence, Sec. 3), the Appendix's
+ * ||u_k|| = eta0 * ||g_k|| rule used by Proposition/Lemma of the Appendix, and
+ * the proximal perturbation of the footnote to Eq. superiorized:
+ * perturbed(x_k) = prox_{lambda_k TV}(x_k) */
+enum { ORC_PERTURB_NONE = 0, ORC_PERTURB_GAMMA = 1, ORC_PERTURB_ETA = 2, ORC_PERTURB_PROX = 3 };
 
 /* status codes */
 enum { ORC_OK = 0, ORC_MAX_ITER = 1, ORC_ERR_INVALID = -1, ORC_ERR_BREAKDOWN = -4 };
@@ -61,6 +63,7 @@ typedef struct {
     int filter_identity; /* 1: c(w) = filter_gain for every w (test special
                             case: PCG then reduces to CG)                      */
     int max_iter;        /* cap on loop bodies                                 */
+    int prox_iters;      /* FGP steps of the proximal perturbation             */
 } orc_params;
 
 typedef struct {
@@ -132,6 +135,8 @@ void orc_fbp(int n, int na, int nb, const double* y, double* x);
 
 int orc_perturb_gamma(int n, const double* x, double gamma0, double a, int max_trials,
                       long long* ell, double* x_half, double* gamma_out, int* trials_out);
+int orc_perturb_prox(int n, const double* x, double gamma0, double a, int prox_iters,
+                     long long* ell, double* x_half, double* lambda_out);
 
 void orc_tv_prox(int n, const double* b, double alpha, int iters, int accel, double* x_out,
                  double* p_out, double* q_out);
