@@ -703,7 +703,10 @@ static int solve_cg(orc_ctx* C, int precond, const double* x0, int resumed, orc_
     double *x = W->x, *g = W->g, *p = W->p, *h = W->h, *z = W->z;
     for (;;) {
         double fx = f_of(C, x);                          /* while f(x_k) > eps */
-        if (!(fx > C->prm.eps)) break;
+        if (!(fx > C->prm.eps)) {                    /* f <= eps; NaN f: breakdown */
+            if (!(fx <= C->prm.eps)) status = ORC_ERR_BREAKDOWN;
+            break;
+        }
         if (it >= C->prm.max_iter) { status = ORC_MAX_ITER; break; }
         double* tr = row_of(trace, rows, it);
         if (tr) {
@@ -799,7 +802,10 @@ static int solve_s_k(orc_ctx* C, int precond, const double* x0, int resumed, orc
     }
     for (;;) {
         double fx = f_of(C, W->xh);                      /* f(x_{k-1/2}) > eps    */
-        if (!(fx > C->prm.eps)) break;
+        if (!(fx > C->prm.eps)) {                    /* f <= eps; NaN f: breakdown */
+            if (!(fx <= C->prm.eps)) status = ORC_ERR_BREAKDOWN;
+            break;
+        }
         if (it >= C->prm.max_iter) { status = ORC_MAX_ITER; break; }
         double* tr = row_of(trace, rows, it);
         if (tr) {
@@ -852,7 +858,10 @@ static int solve_s_pr(orc_ctx* C, int variant, const double* x0, int resumed, or
 
     for (;;) {
         double fx = f_of(C, xh);                         /* while f(x_{k-1/2}) > eps */
-        if (!(fx > C->prm.eps)) break;
+        if (!(fx > C->prm.eps)) {                    /* f <= eps; NaN f: breakdown */
+            if (!(fx <= C->prm.eps)) status = ORC_ERR_BREAKDOWN;
+            break;
+        }
         if (it >= C->prm.max_iter) { status = ORC_MAX_ITER; break; }
         double* tr = row_of(trace, rows, it);
         if (tr) {
@@ -1119,7 +1128,10 @@ int orc_fista(int n, int na, int nb, const double* y, const double* x0, double e
             f += r * r;
         }
         f *= 0.5;
-        if (!(f > eps)) break;
+        if (!(f > eps)) {                            /* f <= eps; NaN f: breakdown */
+            if (!(f <= eps)) status = ORC_ERR_BREAKDOWN;
+            break;
+        }
         if (it >= max_iter) { status = ORC_MAX_ITER; break; }
         orc_project(n, na, nb, u, sino);                      /* A^T (y - A u_k) */
         for (size_t e = 0; e < L; ++e) sino[e] = y[e] - sino[e];
