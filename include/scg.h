@@ -101,7 +101,7 @@ typedef enum {
 typedef enum {
     SCG_PERTURB_NONE = 0,   /* no superiorization step (x_{k+1/2} = x_k)          */
     SCG_PERTURB_GAMMA = 1,  /* gamma_l = gamma0 a^l with TV acceptance (Sec. 3)   */
-    SCG_PERTURB_ETA = 2     /* the Appendix's rule (Eq. up bnd u_k):
+    SCG_PERTURB_ETA = 2,    /* the Appendix's rule (Eq. up bnd u_k):
                                x_{k+1/2} = x_k + u_k, u_k = eta0 ||g_k|| v_k with
                                g_k = A^T (A x_k - y) and v_k = -dTV/||dTV||, no TV
                                test; with 0 < eta0 <= min(1/(4c^2), eta2) (c =
@@ -109,6 +109,15 @@ typedef enum {
                                (2 + c^2 eta) eta = 1/(32 c^2)) the Lemma bounds
                                2f(x_k) - 2f(x_{k+1}) >= ||g_k||^2 / (32 c^2).
                                Costs one extra A and A^T pass per loop body.   */
+    SCG_PERTURB_PROX = 3    /* proximal perturbation (footnote to Eq.
+                               superiorized): x_{k+1/2} = prox_{lambda TV}(x_k)
+                               by prox_iters FGP steps, lambda = gamma_0 a^l /
+                               ||dTV(x_k)|| (gamma_0 as for the gamma rule); no
+                               TV test (a prox step cannot raise TV), l <- l+1
+                               per perturbed step.  S-variants only, FP32/FP64
+                               storage, scg_solve / scg_solve_async only (the
+                               batch and the server return SCG_ERR_UNSUPPORTED);
+                               needs scg_solve_workspace_bytes_p's workspace. */
 } scg_perturb;
 
 typedef struct {
@@ -143,7 +152,8 @@ typedef struct {
                             that profile kernels one launch at a time)          */
     double eta0;         /* SCG_PERTURB_ETA only: eta0 > 0 (default 0)          */
     double lambda;       /* SCG_FISTA: weight of TV, >= 0 (default 0: no prox)  */
-    int prox_iters;      /* SCG_FISTA: FGP steps per prox, 0 .. 100000 (default 20) */
+    int prox_iters;      /* SCG_FISTA and SCG_PERTURB_PROX: FGP steps per prox,
+                            0 .. 100000 (default 20; >= 1 for SCG_PERTURB_PROX) */
     double lipschitz;    /* SCG_FISTA: c^2 = ||A||_2^2 (Appendix, Eq. lambda);
                             <= 0 (default): estimated on the device by 100 power
                             iterations on A^T A from 1 + 0.001 (index mod 7) and
@@ -203,7 +213,9 @@ typedef struct {
  * trace_rows * SCG_TRACE_FIELDS doubles): k, f(x_{k-1/2}) tested at the top of
  * the loop body, TV(x_k), TV(x_{k+1/2}), trials, accepted (1/0, -1 = no
  * perturbation attempted), l after the trials, accepted gamma, alpha, beta,
- * smallest relative TV margin of the trials, f(x_{k+1/2}). */
+ * smallest relative TV margin of the trials, f(x_{k+1/2}).  Under
+ * SCG_PERTURB_PROX the gamma field holds lambda and TV(x_{k+1/2}) is NaN (not
+ * computed). */
 #define SCG_TRACE_FIELDS 12
 
 const char* scg_strerror(int status);
@@ -230,6 +242,17 @@ int scg_backproject(const scg_geometry* g, int precision, const void* r, void* x
  * flight.  The library holds no device memory of its own beyond
  * what these objects use. */
 int scg_release(void);
+
+/* Test hook for the error path of the device's bounded waits (fault injection
+ * on the host; the paper has no counterpart).  With stall != 0, problems set up
+ * afterwards get sinogram copies 16 bytes shorter per angle than the FP32 /
+ * 16-bit gather's barriers expect: the copies all complete, but each wait for a
+ * chunk runs out after its limit (about 0.13 s), the solve stops at
+ * its next loop test and returns SCG_ERR_CUDA (batch and server: that
+ * problem's status).  No fault is raised and the context stays usable; the
+ * gather's results are not valid meanwhile.  stall = 0 (the default) restores
+ * normal operation for problems set up afterwards.  Returns SCG_OK. */
+int scg_test_stall_copies(int stall);
 
 /* ---- Prepared operator pair ------------------------------------------------
  * For callers that apply A and A^T many times with one geometry (their own
@@ -333,8 +356,13 @@ int scg_filter(const scg_geometry* g, int precision, double mu, double gain,
 int scg_fbp(const scg_geometry* g, int precision, const void* y, void* x,
             void* work, size_t work_bytes, void* stream);
 
-/* Bytes of device workspace for scg_solve with this geometry and variant. */
+/* Bytes of device workspace for scg_solve with this geometry and variant
+ * (default parameters: every perturbation rule but SCG_PERTURB_PROX). */
 size_t scg_solve_workspace_bytes(const scg_geometry* g, int variant, int precision);
+/* The same for the given parameters (prm may be NULL: the defaults);
+ * SCG_PERTURB_PROX adds four dual fields of 2 N^2 stored values.  0 on
+ * invalid arguments. */
+size_t scg_solve_workspace_bytes_p(const scg_geometry* g, int variant, int precision, const scg_params* prm);
 
 /* Run one solver of the paper from x0 (NULL = zeros) to f <= eps or max_iter.
  *   y      n_angles*n_bins data (device); x_out  N*N output (device): for the

@@ -82,6 +82,7 @@ inline bool valid_params(const scg_params* p) {
         return false;
     if (p->proj_shape != 0 && (p->proj_shape < kProjShiftMin || p->proj_shape > kProjShiftMax)) return false;
     if (p->perturb == SCG_PERTURB_ETA) return p->eta0 > 0.0 && isfinite(p->eta0);
+    if (p->perturb == SCG_PERTURB_PROX) return p->prox_iters >= 1;
     return p->perturb == SCG_PERTURB_NONE || p->perturb == SCG_PERTURB_GAMMA;
 }
 
@@ -102,6 +103,11 @@ template <> constexpr int prec_of<__nv_bfloat16>() { return SCG_BF16; }
 inline bool solve_supported(int variant, int precision) {
     if (precision == SCG_F32 || precision == SCG_F64) return true;
     return variant != SCG_CG && variant != SCG_PCG && variant != SCG_FISTA;
+}
+// The proximal perturbation runs the FGP kernels, which exist for FP32 and
+// FP64 storage only (as FISTA).
+inline bool perturb_supported(const scg_params* p, int precision) {
+    return p->perturb != SCG_PERTURB_PROX || precision == SCG_F32 || precision == SCG_F64;
 }
 
 // Scale c of the system a solve works on: c A x ~ c y, f scaled by c^2.  CG's
@@ -149,7 +155,8 @@ inline int max_proj_items(int na, int nb) {
 
 enum PlanKind { PLAN_OP = 0, PLAN_SOLVE = 1 };
 
-inline Plan make_plan(const scg_geometry& g, int variant, int precision, int kind) {
+// prox_duals: the proximal perturbation's four dual fields (S-variants).
+inline Plan make_plan(const scg_geometry& g, int variant, int precision, int kind, bool prox_duals = false) {
     const size_t tsize = elem_size(precision), csize = calc_size(precision);
     Plan p;
     memset(&p, 0, sizeof(p));
@@ -220,6 +227,8 @@ inline Plan make_plan(const scg_geometry& g, int variant, int precision, int kin
             p.img[IB_TVG] = take(tsize * J);
         }
         if (uses_filter(variant)) p.img[IB_Z] = take(tsize * J);
+        if (prox_duals && fam != FAM_CG)
+            for (int q = 0; q < 4; ++q) p.dual[q] = take(2 * tsize * J);
         p.sino[SB_R] = take(sino_bytes);
         p.sino[SB_Q] = take(sino_bytes);
         if (uses_filter(variant)) p.sino[SB_W] = take(sino_bytes);
@@ -415,6 +424,7 @@ using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t
                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 EncodeTiledFn tensor_map_encoder();
+bool test_stall_copies();             // scg_test_stall_copies's setting
 
 // TMA maps of a problem's sinogram views, written to base + pl.maps and
 // pointed to by P.sino_map (FP32 and 16-bit storage; the FP64 gather copies
@@ -437,7 +447,10 @@ int upload_sino_maps(Prob<T>& P, const Plan& pl, unsigned char* base, cudaStream
             if (!P.sino[q]) continue;
             const cuuint64_t dims[2] = {(cuuint64_t)P.SB, (cuuint64_t)P.na};
             const cuuint64_t strides[1] = {(cuuint64_t)P.SB * sizeof(S2)};
-            const cuuint32_t box[2] = {(cuuint32_t)band_slots<S2>(), 1u};
+            // (under scg_test_stall_copies the box is 16 bytes narrower than the
+            // band the gather's barrier expects, so no chunk's bytes ever add up)
+            const cuuint32_t box[2] = {(cuuint32_t)(band_slots<S2>() - (test_stall_copies() ? 16 / (int)sizeof(S2) : 0)),
+                                       1u};
             const cuuint32_t estr[2] = {1u, 1u};
             const CUresult r = enc(&maps[q], sizeof(S2) == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32,
                                    2, (void*)P.sino[q], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -488,14 +501,15 @@ struct Runner {
     void axpy(int step) { ++launches; launch_sino_axpy<T>(d, i_ray, g_ray, step, s); }
     void filter(int src, int dst) { ++launches; launch_filter<T>(d, i_row, g_row, nb, src, dst, FILT_VIEW, s); }
     void sino_comb(int cur, int prev) { ++launches; launch_sino_comb<T>(d, i_ray, g_ray, cur, prev, s); }
-    void fgp(int j, double beta) { ++launches; launch_fgp<T>(d, i_img, g_img, j, beta, s); }
+    void fgp(int j, double beta, int mode = 0) { ++launches; launch_fgp<T>(d, i_img, g_img, j, beta, mode, s); }
     void sino_norm(int src, int step) { ++launches; launch_sino_norm<T>(d, i_ray, g_ray, src, step, s); }
 };
 
 struct Program {
     int variant, trial_passes, ksteps;
     bool eta;          // Appendix rule: the gradient at x_k sizes the perturbation
-    int prox_iters;    // FISTA: FGP steps per prox (0 when lambda = 0: the prox is the identity)
+    bool prox;         // proximal perturbation (S-variants): x_{k+1/2} = prox_{lambda_k TV}(x_k)
+    int prox_iters;    // FISTA and the proximal perturbation: FGP steps per prox (0: no prox)
 };
 
 // g'^T p' for the step length: FIN_BETA derives it from the gradient pass's
@@ -599,15 +613,26 @@ void run_body(Runner<T>& R, const Program& pg) {
         R.vec(VEC_FORM_P, dsel, FIN_CG_END);           // p' = -g' (-z') + beta p; k = k+1; loop test
         return;
     }
-    for (int t = 0; t < pg.trial_passes; ++t)             // TV trials of x_k + gamma_l v
-        R.trial(t == 0 ? kTrialsFirst : kTrials);
-    if (pg.eta) {                                      // ||g_k||, g_k = A^T (A x_k - y)
-        R.vec(VEC_VIEWS, IB_X, FIN_NONE);
-        R.project(SB_R, PROJ_RESIDUAL, FIN_NONE);
-        R.back1(SB_R, IB_G, FIN_NONE);
-        R.vec(VEC_NORM_G, 0, FIN_ETA_SIZE);
+    if (pg.prox) {                                     // x_{k+1/2} = prox_{lambda_k TV}(x_k): FGP from a zero dual
+        double t = 1.0;
+        for (int j = 0; j < pg.prox_iters; ++j) {
+            const double t1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+            R.fgp(j, (t - 1.0) / t1, 1);
+            t = t1;
+        }
+        const int w = (pg.prox_iters - 1) & 1;
+        R.vec(VEC_FGP_FINAL, IB_XH | (w << 4) | (1 << 8), FIN_PROX_END);   // x_{k+1/2}, views; l <- l+1
+    } else {
+        for (int t = 0; t < pg.trial_passes; ++t)         // TV trials of x_k + gamma_l v
+            R.trial(t == 0 ? kTrialsFirst : kTrials);
+        if (pg.eta) {                                  // ||g_k||, g_k = A^T (A x_k - y)
+            R.vec(VEC_VIEWS, IB_X, FIN_NONE);
+            R.project(SB_R, PROJ_RESIDUAL, FIN_NONE);
+            R.back1(SB_R, IB_G, FIN_NONE);
+            R.vec(VEC_NORM_G, 0, FIN_ETA_SIZE);
+        }
+        R.vec(VEC_PERTURB, 0, FIN_NONE);               // x_{k+1/2} = perturbed(x_k)
     }
-    R.vec(VEC_PERTURB, 0, FIN_NONE);                   // x_{k+1/2} = perturbed(x_k)
     R.project(SB_R, PROJ_RESIDUAL, FIN_F);             // A x_{k+1/2} - y, f(x_{k+1/2})
     if (pre) R.filter(SB_R, SB_W);
     if (fam == FAM_S_K) {                              // CG-K / PCG-K from x_{k+1/2}
@@ -742,7 +767,9 @@ inline Program make_program(const scg_params* prm, int variant) {
     pg.trial_passes = prm->perturb == SCG_PERTURB_GAMMA ? trial_passes_for(prm->max_trials) : 0;
     pg.ksteps = prm->K + (prm->k_inclusive ? 1 : 0);
     pg.eta = prm->perturb == SCG_PERTURB_ETA && family_of(variant) != FAM_CG && family_of(variant) != FAM_FISTA;
-    pg.prox_iters = prm->lambda > 0.0 ? prm->prox_iters : 0;
+    pg.prox = prm->perturb == SCG_PERTURB_PROX && family_of(variant) != FAM_CG && family_of(variant) != FAM_FISTA;
+    if (family_of(variant) == FAM_FISTA) pg.prox_iters = prm->lambda > 0.0 ? prm->prox_iters : 0;
+    else pg.prox_iters = pg.prox ? prm->prox_iters : 0;
     if (family_of(variant) == FAM_FISTA) pg.trial_passes = 0;
     return pg;
 }

@@ -466,6 +466,7 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
             }
         }
     };
+    bool ok = true;                              // every wait of this thread on its block's copies completed
     // FP32 / 16-bit: the row constants of chunk ch and the TMA copies of its
     // bands, spread over the block: lanes 0..CH/4-1 of warp w take the chunk's
     // angles w*CH/4 .. (w+1)*CH/4-1 (box origin: the band's first slot, rounded
@@ -481,7 +482,9 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
             const int a0 = a_begin + ch * CH;
             const int cnt = min(CH, a_end - a0);          // may be <= 0 (a part with no angles)
             const unsigned mb = smem_addr(&mbar[buf]);
-            if (tl == 0) mbar_expect_tx(mb, cnt > 0 ? (unsigned)(cnt * NRHS * kBand * (int)sizeof(S2)) : 0u);
+            // (only while thread 0's own waits all completed: a barrier phase is the
+            // same for every thread, so it never arrives twice in one phase)
+            if (tl == 0 && ok) mbar_expect_tx(mb, cnt > 0 ? (unsigned)(cnt * NRHS * kBand * (int)sizeof(S2)) : 0u);
             const int lane = tl & 31;
             const int q = (tl >> 5) * kPerWarp + lane;
             if (lane < kPerWarp && q < cnt) {
@@ -527,7 +530,6 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
     for (int h = 0; h < NRHS; ++h)
 #pragma unroll
         for (int k = 0; k < PIX; ++k) acc[h][k] = C(0);
-    bool ok = true;                              // every wait of this thread on its block's copies completed
     if constexpr (kF32) {
         if (tl == 0) {
             mbar_init(smem_addr(&mbar[0]));
@@ -547,8 +549,8 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
         if constexpr (kF32) {
             // stage the next chunk (rows and copies into the other buffer, free
             // since the barrier that ended the previous chunk), then wait for this
-            // chunk's bands -- always, even after a wait ran out, so no copy is
-            // still in flight when the block ends
+            // chunk's bands -- always, even after a wait ran out, so that no copy
+            // is in flight when the block ends
             if (more) stage_tma(ch + 1);
             const bool w = mbar_wait(smem_addr(&mbar[ch & 1]), (unsigned)((ch >> 1) & 1));
             ok = ok && w;
@@ -843,18 +845,21 @@ k_vec(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int op,
         }
         break;
     }
-    case VEC_FGP_FINAL: {       // x_k = b - (lambda / c^2) L^T w (the prox of Eq. FISTA)
-        const int w = sel >> 4;
+    case VEC_FGP_FINAL: {       // x = b - alpha L^T w: the prox of Eq. FISTA (mode 0, b = img[IB_Z],
+                                // alpha = lambda / c^2) or the proximal perturbation (mode 1, b = x_k,
+                                // alpha = prox_lambda); sel = output | w << 4 | mode << 8
+        const int w = (sel >> 4) & 15, mode = sel >> 8;
+        const double a64 = mode ? prox_lambda(st) : st.ex.lam / st.ex.c2;
         if (in) {
-            val = to_c(P.img[IB_Z][idx]);
-            if (w < 2) {
+            val = to_c(P.img[mode ? IB_X : IB_Z][idx]);
+            if (w < 2 && a64 > 0.0) {
                 const auto* D = P.dual[w];
                 const int m = N - 1;
                 C lt = C(0);                                        // (L^T w) at pixel (i, j)
                 if (i < m && j < m) { const auto e = D[idx]; lt -= to_c(e.x) + to_c(e.y); }
                 if (i > 0 && j < m) lt += to_c(D[idx - N].x);
                 if (j > 0 && i < m) lt += to_c(D[idx - 1].y);
-                val = fma(-(C)(st.ex.lam / st.ex.c2), lt, val);
+                val = fma(-(C)a64, lt, val);
             }
             P.img[sel & 15][idx] = to_s<S>(val);
         }
@@ -1188,7 +1193,10 @@ k_sino_norm(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, i
 }
 
 // One step of the fast gradient projection (Beck and Teboulle) for the dual
-// of FISTA's TV prox at b (= img[IB_Z]) with alpha = lambda / c^2: with r the
+// of a TV prox at b with step alpha -- mode 0: FISTA's prox, b = img[IB_Z],
+// alpha = lambda / c^2; mode 1: the proximal perturbation, b = x_k = img[IB_X],
+// alpha = prox_lambda (a block with alpha = 0, zero subgradient, does nothing:
+// the final pass then keeps x_k).  With r the
 // momentum point, w = b - alpha L^T r at every pixel, then per interior term
 // w_j = proj_{|.| <= 1}(r + L w / (8 alpha)) and the next momentum point
 // r' = w_j + beta_j (w_j - w_{j-1}).  dual[j % 2] receives w_j (w_{j-1} is
@@ -1198,7 +1206,8 @@ k_sino_norm(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, i
 // tile's pixels plus one row and column.
 template <typename T>
 __global__ void __launch_bounds__(kTileThreads)
-k_fgp(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int j, typename Tr<T>::C beta) {
+k_fgp(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int j, typename Tr<T>::C beta,
+      int mode) {
     using C = typename Tr<T>::C;
     using C2 = typename Vec2<C>::type;
     if constexpr (!std::is_same<typename Tr<T>::S, C>::value) {
@@ -1212,7 +1221,9 @@ k_fgp(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int j, 
     __shared__ C ws[kTileH + 1][kTileW + 1];
     const int N = P.n, m = N - 1;
     const int i0 = it.u * kTileH, j0 = it.v * kTileW;
-    const C alpha = (C)(st.ex.lam / st.ex.c2);
+    const double a64 = mode ? prox_lambda(st) : st.ex.lam / st.ex.c2;
+    if (!(a64 > 0.0)) return;
+    const C alpha = (C)a64;
     const C inv8a = C(1) / (C(8) * alpha);
     const bool start = j == 0;
     const C2* R = reinterpret_cast<const C2*>(P.dual[2 + (j & 1)]);
@@ -1224,7 +1235,7 @@ k_fgp(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int j, 
     // overlaps the halo's
     constexpr int kWPts = (kTileH + 1) * (kTileW + 1);
     constexpr int kWIters = (kWPts + kTileThreads - 1) / kTileThreads;
-    const C* B = P.img[IB_Z];
+    const C* B = P.img[mode ? IB_X : IB_Z];
     C bv[kWIters];
 #pragma unroll
     for (int k = 0; k < kWIters; ++k) {
@@ -1571,8 +1582,8 @@ void launch_sino_norm(const Prob<T>* d, const Item* items, int grid, int src, in
     k_sino_norm<T><<<grid, kRayBlock, 0, s>>>(d, items, src, step);
 }
 template <typename T>
-void launch_fgp(const Prob<T>* d, const Item* items, int grid, int j, double beta, cudaStream_t s) {
-    k_fgp<T><<<grid, kTileThreads, 0, s>>>(d, items, j, (typename Tr<T>::C)beta);
+void launch_fgp(const Prob<T>* d, const Item* items, int grid, int j, double beta, int mode, cudaStream_t s) {
+    k_fgp<T><<<grid, kTileThreads, 0, s>>>(d, items, j, (typename Tr<T>::C)beta, mode);
 }
 template <typename T>
 void launch_sino_pairs(const Prob<T>* d, int grid, int dst, cudaStream_t s) {
@@ -1623,7 +1634,7 @@ cudaError_t launch_filter(const Prob<T>* d, const Item* items, int grid, int max
                                           cudaStream_t);                                          \
     template void launch_sino_pairs<T>(const Prob<T>*, int, int, cudaStream_t);                   \
     template void launch_sino_comb<T>(const Prob<T>*, const Item*, int, int, int, cudaStream_t);    \
-    template void launch_fgp<T>(const Prob<T>*, const Item*, int, int, double, cudaStream_t);       \
+    template void launch_fgp<T>(const Prob<T>*, const Item*, int, int, double, int, cudaStream_t);  \
     template void launch_sino_norm<T>(const Prob<T>*, const Item*, int, int, int, cudaStream_t);    \
     template void launch_set_done<T>(const Prob<T>*, int, int, cudaStream_t);                     \
     template void launch_set_io<T>(Prob<T>*, const typename Tr<T>::S*, typename Tr<T>::S*,          \

@@ -530,12 +530,29 @@ enum Step {
     FIN_POWER,        // power iteration: S0 = ||h||^2, S1 = p^T h with h = A^T A p (vector pass)
     FIN_POWER_NORM,   // power iteration: S0 = ||p||^2
     FIN_FISTA_F,      // FISTA: residual of x_k, S0 = ||A x_k - y||^2 -> stop test, t_{k+1}, beta_k
-    FIN_ETA_SIZE      // Appendix rule: S0 = ||g_k||^2 -> the perturbation's size
+    FIN_ETA_SIZE,     // Appendix rule: S0 = ||g_k||^2 -> the perturbation's size
+    FIN_PROX_END      // proximal perturbation applied (no sums): fix gamma_0, l <- l+1, trace
 };
 // Steps at or after FIN_POWER are finalised by finalize_rare (see there).
 constexpr int kFirstRareStep = FIN_POWER;
 
 __device__ __forceinline__ bool finite_pos(double v) { return v > 0.0 && isfinite(v); }
+// Step of the proximal perturbation x_{k+1/2} = prox_{lambda TV}(x_k) (the
+// footnote to Eq. superiorized): lambda = gamma_0 a^l / ||dTV(x_k)||, the
+// implicit counterpart of the gamma rule's step x_k + gamma v; gamma_0 as in
+// the gamma rule (gamma0_rel ||x|| of the first perturbed image unless given).
+// 0 when the subgradient is zero (x_k is then kept).
+__device__ __forceinline__ double prox_lambda(const DevState& st) {
+    if (!(st.gnorm2 > 0.0)) return 0.0;
+    const double g0 = st.gamma_fixed ? st.gamma0 : st.gamma0_rel * sqrt(st.xnorm2);
+    return g0 * st.a_ell / sqrt(st.gnorm2);
+}
+
+// Status of a stop at the loop test "while f > eps": f <= eps is success; a
+// non-finite f (NaN data or arithmetic) is a breakdown, not a convergence.
+__device__ __forceinline__ int stop_status(const DevState& st) {
+    return st.f_half <= st.eps ? SCG_OK : SCG_ERR_BREAKDOWN;
+}
 
 template <typename T>
 __device__ __forceinline__ double* trace_row(const Prob<T>& P, int it) {
@@ -559,7 +576,7 @@ __device__ __forceinline__ void set_trial_coefs(DevState& st) {
 template <typename T>
 __device__ void top_of_loop(const Prob<T>& P, DevState& st) {
     if (st.done) return;
-    if (!(st.f_half > st.eps)) { st.done = 1; st.status = SCG_OK; return; }
+    if (!(st.f_half > st.eps)) { st.done = 1; st.status = stop_status(st); return; }
     if (st.iters >= st.max_iter) { st.done = 1; st.status = SCG_WARN_MAX_ITER; return; }
     double* row = trace_row(P, st.iters);
     if (row) {
@@ -620,6 +637,28 @@ __device__ __noinline__ void finalize_rare(int step, const Prob<T>& P, DevState&
         }
         break;
     }
+    case FIN_PROX_END: {
+        // x_{k+1/2} = prox_{lambda TV}(x_k) has been formed: a prox step cannot
+        // raise TV, so there is no trial; l <- l+1 once per perturbed step.  The
+        // TV of x_{k+1/2} is not computed here (the trace's TV-after field is NaN).
+        if (!st.done && st.family != FAM_CG && st.perturb == SCG_PERTURB_PROX && st.gnorm2 > 0.0) {
+            const double lam = prox_lambda(st);
+            if (!st.gamma_fixed) {
+                st.gamma0 = st.gamma0_rel * sqrt(st.xnorm2);
+                st.gamma_fixed = 1;
+            }
+            st.ell += 1;
+            st.a_ell *= st.a;
+            st.accepted = 1;
+            if (row) {
+                row[TR_ACCEPTED] = 1.0;
+                row[TR_GAMMA] = lam;
+                row[TR_ELL] = (double)st.ell;
+                row[TR_TV_AFTER] = __longlong_as_double(0x7ff8000000000000LL);
+            }
+        }
+        break;
+    }
     case FIN_POWER:
         st.ex.c2 = S[1] / st.xnorm2;                        // Rayleigh quotient of A^T A at p
         st.coef = 1.0 / sqrt(S[0]);
@@ -644,7 +683,7 @@ __device__ __noinline__ void finalize_rare(int step, const Prob<T>& P, DevState&
             st.iters += 1;
             st.k += 1;
         }
-        if (!(st.f_half > st.eps)) { st.done = 1; st.status = SCG_OK; }
+        if (!(st.f_half > st.eps)) { st.done = 1; st.status = stop_status(st); }
         else if (st.iters >= st.max_iter) { st.done = 1; st.status = SCG_WARN_MAX_ITER; }
         break;
     default:
@@ -662,7 +701,7 @@ __device__ void finalize(int step, const Prob<T>& P, DevState& st, const double*
             if (row) row[TR_F_AFTER] = st.f_half;
             // f(x_{k+1/2}) <= eps ends the loop at the next test; the rest of
             // this step only produces x_{k+1}, which is never used.
-            if (!(st.f_half > st.eps)) { st.done = 1; st.status = SCG_OK; end_body(st); }
+            if (!(st.f_half > st.eps)) { st.done = 1; st.status = stop_status(st); end_body(st); }
         }
         break;
     case FIN_BETA: {

@@ -51,7 +51,7 @@ void launch_sino_pairs(const Prob<T>* d, int grid, int dst, cudaStream_t s);
 template <typename T>
 void launch_sino_comb(const Prob<T>* d, const Item* items, int grid, int cur, int prev, cudaStream_t s);
 template <typename T>
-void launch_fgp(const Prob<T>* d, const Item* items, int grid, int j, double beta, cudaStream_t s);
+void launch_fgp(const Prob<T>* d, const Item* items, int grid, int j, double beta, int mode, cudaStream_t s);
 template <typename T>
 void launch_sino_norm(const Prob<T>* d, const Item* items, int grid, int src, int step, cudaStream_t s);
 void launch_loop_cond(DevState* st, cudaGraphConditionalHandle h, cudaStream_t s);

@@ -595,6 +595,7 @@ size_t scg_server_footprint(const scg_geometry* g, int variant, int precision) {
 int scg_server_create(const scg_server_config* cfg, scg_server** out) {
     if (!cfg || !out || !cfg->pool || ((uintptr_t)cfg->pool & 15u)) return SCG_ERR_INVALID;
     if (cfg->variant == SCG_FISTA) return SCG_ERR_UNSUPPORTED;     // FISTA: scg_solve only
+    if (cfg->params.perturb == SCG_PERTURB_PROX) return SCG_ERR_UNSUPPORTED;   // scg_solve only
     if (cfg->variant < SCG_CG || cfg->variant > SCG_S_PCG_K) return SCG_ERR_INVALID;
     if (!valid_prec(cfg->precision) || !solve_supported(cfg->variant, cfg->precision)) return SCG_ERR_UNSUPPORTED;
     if (cfg->max_active < 1 || cfg->max_active > 65535 || cfg->bodies_per_step < 1 ||

@@ -13,6 +13,7 @@
 #include <string.h>
 
 #include <map>
+#include <atomic>
 #include <mutex>
 #include <tuple>
 #include <vector>
@@ -108,7 +109,7 @@ int solve_impl(const scg_geometry* g, int variant, int precision, const scg_para
                scg_state* final_state, cudaStream_t user_stream, scg_result* res_async = nullptr) {
     using E = typename Tr<T>::S;
     using C = typename Tr<T>::C;
-    Plan pl = make_plan(*g, variant, prec_of<T>(), PLAN_SOLVE);
+    Plan pl = make_plan(*g, variant, prec_of<T>(), PLAN_SOLVE, prm->perturb == SCG_PERTURB_PROX);
     if (work_bytes < pl.total || ((uintptr_t)work & 15u)) return SCG_ERR_WORKSPACE;
     if (uses_filter(variant) && !filter_fits(g->n_bins, prec_of<T>())) return SCG_ERR_UNSUPPORTED;
     unsigned char* base = (unsigned char*)work;
@@ -909,6 +910,9 @@ void proj_shape_store(int dev, int precision, const scg_geometry& g, int shift) 
     std::lock_guard<std::mutex> lk(g_shape_mu);
     g_shapes[shape_key(dev, precision, g)] = shift;
 }
+std::atomic<int> g_test_stall{0};
+bool test_stall_copies() { return g_test_stall.load() != 0; }
+
 EncodeTiledFn tensor_map_encoder() {
     static const EncodeTiledFn fn = []() -> EncodeTiledFn {
         void* p = nullptr;
@@ -984,6 +988,14 @@ size_t scg_solve_workspace_bytes(const scg_geometry* g, int variant, int precisi
     return make_plan(*g, variant, precision, PLAN_SOLVE).total;
 }
 
+size_t scg_solve_workspace_bytes_p(const scg_geometry* g, int variant, int precision, const scg_params* prm) {
+    if (!prm) return scg_solve_workspace_bytes(g, variant, precision);
+    if (!valid_geometry(g) || !valid_prec(precision) || !valid_variant(variant) ||
+        !solve_supported(variant, precision) || !valid_params(prm) || !perturb_supported(prm, precision))
+        return 0;
+    return make_plan(*g, variant, precision, PLAN_SOLVE, prm->perturb == SCG_PERTURB_PROX).total;
+}
+
 int scg_project(const scg_geometry* g, int precision, const void* x, void* y, void* work,
                 size_t work_bytes, void* stream) {
     if (!valid_geometry(g) || !x || !y || !work) return SCG_ERR_INVALID;
@@ -1032,7 +1044,8 @@ int scg_solve_async(const scg_geometry* g, int variant, int precision, const scg
     if (!(eps > 0.0) || !isfinite(eps) || !valid_params(prm)) return SCG_ERR_INVALID;
     if (resume && resume->valid != 1) return SCG_ERR_INVALID;
     if (prm->host_loop != 0 || (variant == SCG_FISTA && resume)) return SCG_ERR_UNSUPPORTED;
-    if (!valid_prec(precision) || !solve_supported(variant, precision)) return SCG_ERR_UNSUPPORTED;
+    if (!valid_prec(precision) || !solve_supported(variant, precision) || !perturb_supported(prm, precision))
+        return SCG_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     scg_result dummy;
     return SCG_DISPATCH(precision, solve_impl, g, variant, precision, prm, eps, y, x0, x_out, work, work_bytes,
@@ -1057,7 +1070,8 @@ int scg_solve(const scg_geometry* g, int variant, int precision, const scg_param
     if (!(eps > 0.0) || !isfinite(eps) || !valid_params(prm)) return SCG_ERR_INVALID;
     if (prm->host_loop != 0 && prm->host_loop != 1) return SCG_ERR_INVALID;
     if (resume && resume->valid != 1) return SCG_ERR_INVALID;
-    if (!valid_prec(precision) || !solve_supported(variant, precision)) return SCG_ERR_UNSUPPORTED;
+    if (!valid_prec(precision) || !solve_supported(variant, precision) || !perturb_supported(prm, precision))
+        return SCG_ERR_UNSUPPORTED;
     memset(res, 0, sizeof(*res));
     cudaStream_t s = (cudaStream_t)stream;
     int rc = SCG_DISPATCH(precision, solve_impl, g, variant, precision, prm, eps, y, x0, x_out, work,
@@ -1073,6 +1087,11 @@ struct scg_operator {
 };
 
 extern "C" {
+
+int scg_test_stall_copies(int stall) {
+    scg::host::g_test_stall.store(stall ? 1 : 0);
+    return SCG_OK;
+}
 
 int scg_release(void) {
     std::lock_guard<std::mutex> lk(g_mu);
@@ -1178,6 +1197,7 @@ int scg_solve_batch(const scg_problem* problems, int count, int variant, int pre
     if (variant == SCG_FISTA) return SCG_ERR_UNSUPPORTED;          // FISTA: scg_solve only
     if (variant < SCG_CG || variant > SCG_S_PCG_K) return SCG_ERR_INVALID;
     if (!valid_params(prm)) return SCG_ERR_INVALID;
+    if (prm->perturb == SCG_PERTURB_PROX) return SCG_ERR_UNSUPPORTED;   // proximal perturbation: scg_solve only
     if (prm->host_loop != 0) return SCG_ERR_UNSUPPORTED;
     for (int i = 0; i < count; ++i) {
         const scg_problem& p = problems[i];

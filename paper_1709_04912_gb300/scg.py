@@ -16,7 +16,7 @@ from . import build as _build
 
 F64, F32, F16, BF16 = 0, 1, 2, 3
 VARIANTS = {"CG": 0, "PCG": 1, "S-CG": 2, "S-CG-CD": 3, "S-CG-K": 4, "S-PCG": 5, "S-PCG-K": 6, "FISTA": 7}
-PERTURB = {"none": 0, "gamma": 1, "eta": 2}
+PERTURB = {"none": 0, "gamma": 1, "eta": 2, "prox": 3}
 STATUS = {0: "ok", 1: "max_iter", -1: "invalid", -2: "cuda", -3: "workspace", -4: "breakdown",
           -5: "unsupported"}
 TRACE_FIELDS = ("k", "f_test", "tv_before", "tv_after", "trials", "accepted", "ell",
@@ -97,6 +97,8 @@ def load(build_if_needed: bool = True):
     L.scg_op_workspace_bytes.argtypes = [gp, i]
     L.scg_solve_workspace_bytes.restype = sz
     L.scg_solve_workspace_bytes.argtypes = [gp, i, i]
+    L.scg_solve_workspace_bytes_p.restype = sz
+    L.scg_solve_workspace_bytes_p.argtypes = [gp, i, i, ctypes.POINTER(Params)]
     L.scg_project.argtypes = [gp, i, vp, vp, vp, sz, vp]
     L.scg_backproject.argtypes = [gp, i, vp, vp, vp, sz, vp]
     L.scg_tv.argtypes = [i, i, vp, vp, vp, sz, vp]
@@ -115,6 +117,8 @@ def load(build_if_needed: bool = True):
     L.scg_solve_batch.argtypes = [pp, i, i, i, ctypes.POINTER(Params), vp, sz, ctypes.POINTER(Result), vp]
     L.scg_release.argtypes = []
     L.scg_release.restype = i
+    L.scg_test_stall_copies.argtypes = [i]
+    L.scg_test_stall_copies.restype = i
     L.scg_operator_create.argtypes = [gp, i, vp, sz, vp, ctypes.POINTER(vp)]
     L.scg_operator_create_angles.argtypes = [gp, i, i, i, vp, sz, vp, ctypes.POINTER(vp)]
     L.scg_operator_create_angles.restype = i
@@ -336,7 +340,7 @@ def scg_solve(y: torch.Tensor, n: int, variant: str = "S-CG", eps: float = 1.0, 
     prec = _prec(y)
     g = geometry(n, na, nbins)
     p = _params(default_params(**params))
-    nbytes = L.scg_solve_workspace_bytes(ctypes.byref(g), VARIANTS[variant], prec)
+    nbytes = L.scg_solve_workspace_bytes_p(ctypes.byref(g), VARIANTS[variant], prec, ctypes.byref(p))
     if work is None:
         work = workspace(nbytes, y.device, "solve")
     if out is None:
@@ -415,7 +419,7 @@ def scg_solve_async(y: torch.Tensor, n: int, variant: str = "S-CG", eps: float =
     prec = _prec(y)
     g = geometry(n, na, nbins)
     p = _params(default_params(**params))
-    nbytes = L.scg_solve_workspace_bytes(ctypes.byref(g), VARIANTS[variant], prec)
+    nbytes = L.scg_solve_workspace_bytes_p(ctypes.byref(g), VARIANTS[variant], prec, ctypes.byref(p))
     if work is None:
         work = workspace(nbytes, y.device, "solve")
     if out is None:
@@ -636,6 +640,13 @@ class Operator:
             self.close()
         except Exception:
             pass
+
+
+def set_copy_stall(stall: bool) -> None:
+    """Test hook (scg_test_stall_copies): while set, the gathers of problems set
+    up afterwards wait for bytes that never arrive, so their bounded waits run
+    out and solves report SCG_ERR_CUDA."""
+    _check(load().scg_test_stall_copies(int(bool(stall))), "scg_test_stall_copies")
 
 
 def release() -> None:
