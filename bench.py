@@ -73,7 +73,11 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--gamma0-rel", type=float, default=0.05)
     ap.add_argument("--lam", type=float, default=30.0, help="FISTA's TV weight lambda (--variant FISTA)")
-    ap.add_argument("--prox-iters", type=int, default=10, help="FISTA's FGP steps per prox (--variant FISTA)")
+    ap.add_argument("--prox-iters", type=int, default=10,
+                    help="FGP steps per prox (--variant FISTA, --perturb prox)")
+    ap.add_argument("--perturb", default="gamma", choices=["gamma", "prox"],
+                    help="superiorization rule of the S-variants: the gamma rule with its TV test, or the "
+                         "proximal perturbation prox_{lambda TV}(x_k)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="leave the batch block out of the line")
@@ -221,7 +225,8 @@ def nnz_of(work) -> int:
 
 
 # ---------------------------------------------------------------------------
-def time_oracle_solves(prob, work, variant, gamma0_rel, budget_s, max_solves, lam=0.0, prox_iters=10):
+def time_oracle_solves(prob, work, variant, gamma0_rel, budget_s, max_solves, lam=0.0, prox_iters=10,
+                       perturb="gamma"):
     """Whole oracle solves of ``prob`` (FP64, on the host cores), timed one by
     one until ``budget_s`` seconds or ``max_solves`` solves.  Returns the times,
     the iteration count and the thread count.  FISTA's c^2 comes from the
@@ -231,6 +236,8 @@ def time_oracle_solves(prob, work, variant, gamma0_rel, budget_s, max_solves, la
     kw = dict(variant=variant, gamma0_rel=gamma0_rel, eps=prob.eps, max_iter=work.max_iter)
     if variant in ("CG", "PCG"):
         kw["perturb"] = "none"
+    elif perturb == "prox":
+        kw.update(perturb="prox", prox_iters=prox_iters)
     if variant == "FISTA":
         c2 = oracle.norm_A(work.n, work.n_angles, work.n_bins, 100) ** 2
 
@@ -261,7 +268,7 @@ def run_reference(args, work, rank, world):
     variant = args.variant
     prob = inputs.make_problem(work, args.seed, oracle.project)
     times, iters, cores = time_oracle_solves(prob, work, variant, args.gamma0_rel, args.ref_budget, args.steps,
-                                             args.lam, args.prox_iters)
+                                             args.lam, args.prox_iters, args.perturb)
     t_solve = float(np.mean(times))
     value = 1.0 / t_solve
     sample = (f"{len(times)} whole oracle {variant} solves of this workload ({iters} iterations to eps each), "
@@ -270,7 +277,7 @@ def run_reference(args, work, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": len(times), "warmup": 0, "ms_per_step": 1e3 * t_solve,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": dict(config_of(work, variant, prob, iters), parallelism=f"replicas x{world}"),
+            "data": "synthetic", "config": dict(config_of(work, variant, prob, iters, args), parallelism=f"replicas x{world}"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -278,11 +285,14 @@ def run_reference(args, work, rank, world):
     return 0
 
 
-def config_of(work, variant, prob, iters):
+def config_of(work, variant, prob, iters, args=None):
     """The workload as both arms name it."""
-    return {"workload": work.name, "variant": variant, "n": work.n, "n_angles": work.n_angles,
-            "n_bins": work.n_bins, "eps": prob.eps, "iters": iters, "data_projector": "oracle (FP64)",
-            "l2": "flushed (512 MiB write) before each step", "per_gpu_problems": 1}
+    c = {"workload": work.name, "variant": variant, "n": work.n, "n_angles": work.n_angles,
+         "n_bins": work.n_bins, "eps": prob.eps, "iters": iters, "data_projector": "oracle (FP64)",
+         "l2": "flushed (512 MiB write) before each step", "per_gpu_problems": 1}
+    if args is not None and args.perturb == "prox" and variant not in ("CG", "PCG", "FISTA"):
+        c.update(perturb="prox", prox_iters=args.prox_iters)
+    return c
 
 
 # ---------------------------------------------------------------------------
@@ -299,6 +309,8 @@ def run_ours(args, work, rank, local_rank, world):
     kw = dict(gamma0_rel=args.gamma0_rel, max_iter=work.max_iter, host_loop=int(args.host_loop))
     if variant in ("CG", "PCG"):
         kw["perturb"] = "none"
+    elif args.perturb == "prox":
+        kw.update(perturb="prox", prox_iters=args.prox_iters)
     if variant == "FISTA":              # c^2 estimated on the device once, then cached
         kw = dict(lambda_=args.lam, prox_iters=args.prox_iters, max_iter=300, host_loop=int(args.host_loop))
 
@@ -444,7 +456,7 @@ def run_ours(args, work, rank, local_rank, world):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         times, o_iters, cores = time_oracle_solves(prob, work, variant, args.gamma0_rel, 30.0, 1, args.lam,
-                                                   args.prox_iters)
+                                                   args.prox_iters, args.perturb)
         cpu = {"value": 1.0 / float(np.mean(times)), "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": (f"{len(times)} whole oracle {variant} solve(s) of this workload "
                           f"({o_iters} iterations to eps), timed")}
@@ -465,7 +477,7 @@ def run_ours(args, work, rank, local_rank, world):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype or "f32",
                 "data": "synthetic",
-                "config": dict(config_of(work, variant, prob, last.iters), parallelism=f"replicas x{world}"),
+                "config": dict(config_of(work, variant, prob, last.iters, args), parallelism=f"replicas x{world}"),
                 "result": {"status": last.status, "tv_final": last.tv_final, "f_final": last.f_final},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "device_loop": bool(last.device_loop), "clocks": clk,
