@@ -320,7 +320,8 @@ def run_ours(args, work, rank, local_rank, world):
     esize = torch.tensor([], dtype=dtype).element_size()
     y = torch.tensor(prob.y, dtype=torch.float32).to(dtype).to(dev)
     out = torch.empty((work.n, work.n), dtype=dtype, device=dev)
-    nbytes = scg.solve_workspace_bytes(work.n, work.n_angles, work.n_bins, variant, scg._prec_of(dtype))
+    nbytes = scg.solve_workspace_bytes(work.n, work.n_angles, work.n_bins, variant, scg._prec_of(dtype),
+                                       **{k: v for k, v in kw.items() if k != "host_loop"})
     wsp = torch.empty(nbytes, dtype=torch.uint8, device=dev)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)

@@ -198,9 +198,13 @@ def op_workspace_bytes(n: int, n_angles: int, n_bins: int, precision: int) -> in
     return int(load().scg_op_workspace_bytes(ctypes.byref(g), precision))
 
 
-def solve_workspace_bytes(n: int, n_angles: int, n_bins: int, variant: str, precision: int) -> int:
+def solve_workspace_bytes(n: int, n_angles: int, n_bins: int, variant: str, precision: int, **params) -> int:
+    """Workspace bytes of scg_solve for this geometry, variant, precision and
+    parameters (scg_solve_workspace_bytes_p; the proximal perturbation needs
+    more than the defaults)."""
     g = geometry(n, n_angles, n_bins)
-    return int(load().scg_solve_workspace_bytes(ctypes.byref(g), VARIANTS[variant], precision))
+    p = _params(default_params(**params))
+    return int(load().scg_solve_workspace_bytes_p(ctypes.byref(g), VARIANTS[variant], precision, ctypes.byref(p)))
 
 
 def scg_project(x: torch.Tensor, n_angles: int, n_bins: int, out: torch.Tensor | None = None):
