@@ -307,7 +307,6 @@ void fill_angles(std::vector<Angle<T>>& out, int na, int n, double scale = 1.0, 
 // the same order and the results are bit-identical to the block-index order.
 struct ProjOrder {
     std::vector<Item> items;    // longest first
-    std::vector<float> cost;    // strips walked, per item
 };
 constexpr int kWarpSetupStrips = 12;
 
@@ -358,11 +357,9 @@ inline ProjOrder make_proj_order(int n, int nb, int shift, const std::vector<Ang
     std::stable_sort(by_cost.begin(), by_cost.end(),
                      [](const std::pair<float, int>& x, const std::pair<float, int>& y) { return x.first > y.first; });
     o.items.resize(cnt);
-    o.cost.resize(cnt);
     for (int k = 0; k < cnt; ++k) {
         const int q = by_cost[k].second;
         o.items[k] = Item{0, q / bblocks, q % bblocks, q};
-        o.cost[k] = by_cost[k].first;
     }
     return o;
 }
@@ -694,7 +691,8 @@ void proj_shape_store(int dev, int precision, const scg_geometry& g, int shift);
 // stopped, angles uploaded; the SB_Q view is overwritten), each launched over
 // its longest-first work list in order_dst (pl.cnt_proj items of the problem's
 // workspace), and leave the best shape in P, pl and the slot and its list in
-// order_dst.
+// order_dst.  order_dst = nullptr: blocks in index order, no list (batched
+// launches, whose many problems' blocks already fill the last wave).
 template <typename T>
 int tune_proj_shape(Prob<T>& P, Plan& pl, Prob<T>* d, const scg_geometry& g, cudaStream_t s, Item* order_dst,
                     int forced = 0) {
@@ -711,7 +709,7 @@ int tune_proj_shape(Prob<T>& P, Plan& pl, Prob<T>* d, const scg_geometry& g, cud
             set_proj_shape(pl, g.n_angles, g.n_bins, sh);
             P.cnt_proj = pl.cnt_proj; P.proj_blocks = pl.proj_blocks; P.proj_shift = sh;
             if (cudaMemcpyAsync(d, &P, sizeof(P), cudaMemcpyHostToDevice, s) != cudaSuccess) break;
-            if (upload_proj_order(pl, order_dst, g, s) != SCG_OK) break;
+            if (order_dst && upload_proj_order(pl, order_dst, g, s) != SCG_OK) break;
             launch_project<T>(d, order_dst, pl.cnt_proj, SB_Q, PROJ_PLAIN, FIN_NONE, s);
             cudaEventRecord(e0, s);
             for (int r = 0; r < 3; ++r) launch_project<T>(d, order_dst, pl.cnt_proj, SB_Q, PROJ_PLAIN, FIN_NONE, s);
@@ -728,7 +726,7 @@ int tune_proj_shape(Prob<T>& P, Plan& pl, Prob<T>* d, const scg_geometry& g, cud
     set_proj_shape(pl, g.n_angles, g.n_bins, best);
     P.cnt_proj = pl.cnt_proj; P.proj_blocks = pl.proj_blocks; P.proj_shift = best;
     if (cudaMemcpyAsync(d, &P, sizeof(P), cudaMemcpyHostToDevice, s) != cudaSuccess) return SCG_ERR_CUDA;
-    return upload_proj_order(pl, order_dst, g, s);
+    return order_dst ? upload_proj_order(pl, order_dst, g, s) : SCG_OK;
 }
 
 // Initial device state of one solve.
@@ -779,35 +777,12 @@ inline Program make_program(const scg_params* prm, int variant) {
 // launch, so its reductions add in the single-problem order.
 enum { K_PROJ = 0, K_IMG = 1, K_RAY = 2, K_ROW = 3, K_BP = 4, K_COUNT = 5 };
 
-// With a work list po, the projector items come from it, and their costs are
-// appended to proj_cost.
-inline void append_items(const Plan& pl, int prob, std::vector<Item>* lists, const ProjOrder* po = nullptr,
-                         std::vector<float>* proj_cost = nullptr) {
-    if (po) {
-        for (size_t q = 0; q < po->items.size(); ++q) {
-            Item it = po->items[q];
-            it.prob = prob;
-            lists[K_PROJ].push_back(it);
-            if (proj_cost) proj_cost->push_back(po->cost[q]);
-        }
-    } else {
-        for (int q = 0; q < pl.cnt_proj; ++q) lists[K_PROJ].push_back(Item{prob, q / pl.proj_blocks, q % pl.proj_blocks, q});
-    }
+inline void append_items(const Plan& pl, int prob, std::vector<Item>* lists) {
+    for (int q = 0; q < pl.cnt_proj; ++q) lists[K_PROJ].push_back(Item{prob, q / pl.proj_blocks, q % pl.proj_blocks, q});
     for (int q = 0; q < pl.cnt_img; ++q) lists[K_IMG].push_back(Item{prob, q / pl.tiles_x, q % pl.tiles_x, q});
     for (int q = 0; q < pl.cnt_ray; ++q) lists[K_RAY].push_back(Item{prob, q / pl.ray_blocks, q % pl.ray_blocks, q});
     for (int q = 0; q < pl.cnt_row; ++q) lists[K_ROW].push_back(Item{prob, q / pl.filt_blocks, q % pl.filt_blocks, q});
     for (int q = 0; q < pl.cnt_bp; ++q) lists[K_BP].push_back(Item{prob, q / pl.tiles_x, q % pl.tiles_x, q});
-}
-
-// Reorders items (with their costs) longest first; equal costs keep their order.
-inline void sort_longest_first(std::vector<Item>& items, const std::vector<float>& cost) {
-    if (cost.size() != items.size()) return;
-    std::vector<int> idx(items.size());
-    for (size_t q = 0; q < idx.size(); ++q) idx[q] = (int)q;
-    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return cost[x] > cost[y]; });
-    std::vector<Item> out(items.size());
-    for (size_t q = 0; q < idx.size(); ++q) out[q] = items[idx[q]];
-    items.swap(out);
 }
 
 // List lengths rounded up to eight steps per octave (<= 12.5 % padding), so

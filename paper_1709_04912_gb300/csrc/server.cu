@@ -280,15 +280,11 @@ private:
     // placeholder items to its rounded length.  Returns the launch grids.
     int build_lists(const std::vector<int>& slots, DevList* lists, bool bucket, int* grid, int* nb_max) {
         std::vector<Item> v[K_COUNT];
-        std::vector<float> proj_cost;
         *nb_max = 1;
         for (int sl : slots) {
-            const scg_geometry& g = slots_[sl]->p.geometry;
-            const auto po = proj_order(g.n, g.n_angles, g.n_bins, slots_[sl]->plan.proj_shift);
-            append_items(slots_[sl]->plan, sl, v, po.get(), &proj_cost);
-            if (g.n_bins > *nb_max) *nb_max = g.n_bins;
+            append_items(slots_[sl]->plan, sl, v);
+            if (slots_[sl]->p.geometry.n_bins > *nb_max) *nb_max = slots_[sl]->p.geometry.n_bins;
         }
-        sort_longest_first(v[K_PROJ], proj_cost);     // all requests' projector blocks, longest first
         for (int k = 0; k < K_COUNT; ++k) {
             const int n = (int)v[k].size();
             const int g = bucket ? round_up_bucket(n) : n;
@@ -392,8 +388,7 @@ private:
             }
             SCK(upload(probs() + slot, &P, sizeof(P)));
             {
-                const int rc = tune_proj_shape<T>(P, r->plan, probs() + slot, r->p.geometry, stream_,
-                                                  reinterpret_cast<Item*>(rb + r->plan.proj_items),
+                const int rc = tune_proj_shape<T>(P, r->plan, probs() + slot, r->p.geometry, stream_, nullptr,
                                                   cfg_.params.proj_shape);
                 if (rc != SCG_OK) return rc;
             }

@@ -723,7 +723,6 @@ int batch_impl(const scg_problem* pr, int count, int variant, int precision, con
     memset(probs.data(), 0, sizeof(Prob<T>) * probs.size());
     std::vector<std::vector<Item>> items(K_COUNT);
     for (int k = 0; k < K_COUNT; ++k) items[k].reserve(bp.cap_items[k]);
-    std::vector<float> proj_cost;
     CK(cudaMemsetAsync(base, 0, bp.total, s));
     Prob<T>* slots = reinterpret_cast<Prob<T>*>(base + bp.probs);
     for (int i = 0; i < count; ++i) {
@@ -750,16 +749,15 @@ int batch_impl(const scg_problem* pr, int count, int variant, int precision, con
             CK(cudaMemcpyAsync(rb + pl.taps, ftab.data(), sizeof(C) * ftab.size(), cudaMemcpyHostToDevice, s));
         }
         // the problem's own slot serves the shape tuner (a single-problem launch)
-        const int rc = tune_proj_shape<T>(P, pl, slots + i, pr[i].geometry, s,
-                                          reinterpret_cast<Item*>(rb + pl.proj_items), prm->proj_shape);
+        // (blocks in index order: a batch's launch holds many problems' blocks,
+        // so no longest-first list is built for it)
+        const int rc = tune_proj_shape<T>(P, pl, slots + i, pr[i].geometry, s, nullptr, prm->proj_shape);
         if (rc != SCG_OK) return rc;
         probs[i] = P;
-        const auto po = proj_order(pr[i].geometry.n, pr[i].geometry.n_angles, pr[i].geometry.n_bins, pl.proj_shift);
-        append_items(pl, i, items.data(), po.get(), &proj_cost);
+        append_items(pl, i, items.data());
         // (pageable host sources are staged before cudaMemcpyAsync returns,
         // so st and ang may be reused for the next problem)
     }
-    sort_longest_first(items[K_PROJ], proj_cost);     // all problems' projector blocks, longest first
     // placeholder problem for the padding items: stopped for good
     DevState stopped;
     memset(&stopped, 0, sizeof(stopped));
@@ -934,7 +932,7 @@ std::shared_ptr<const ProjOrder> proj_order(int n, int na, int nb, int shift, in
     std::vector<Angle<double>> ang;
     fill_angles<double>(ang, na, n, 1.0, a_begin, na_total);
     auto o = std::make_shared<const ProjOrder>(make_proj_order(n, nb, shift, ang));
-    if (g_orders.size() >= 256) g_orders.clear();
+    if (g_orders.size() >= 1024) g_orders.clear();
     g_orders[key] = o;
     return o;
 }
