@@ -499,6 +499,7 @@ struct Runner {
     void filter(int src, int dst) { ++launches; launch_filter<T>(d, i_row, g_row, nb, src, dst, FILT_VIEW, s); }
     void sino_comb(int cur, int prev) { ++launches; launch_sino_comb<T>(d, i_ray, g_ray, cur, prev, s); }
     void fgp(int j, double beta, int mode = 0) { ++launches; launch_fgp<T>(d, i_img, g_img, j, beta, mode, s); }
+    void fgp2(int p, double b0, double b1, int mode) { ++launches; launch_fgp2<T>(d, i_img, g_img, p, b0, b1, mode, s); }
     void sino_norm(int src, int step) { ++launches; launch_sino_norm<T>(d, i_ray, g_ray, src, step, s); }
 };
 
@@ -531,6 +532,32 @@ void run_power(Runner<T>& R, int iters) {
     }
 }
 
+// The FGP steps of one TV prox (momentum (t_j - 1)/t_{j+1}, t_1 = 1), two per
+// launch (k_fgp2) and a last single step when the count is odd; mode 0 is
+// FISTA's prox, 1 the proximal perturbation.  Returns the dual buffer (0 or 1)
+// that holds the final w, or 2 if no step was taken.
+template <typename T>
+int run_fgp(Runner<T>& R, int iters, int mode) {
+    double t = 1.0;
+    int p = 0;                                        // launch index: selects the buffers
+    for (int j = 0; j < iters; ++p) {
+        const double t1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+        const double b0 = (t - 1.0) / t1;
+        t = t1;
+        if (j + 1 < iters) {
+            const double t2 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+            const double b1 = (t - 1.0) / t2;
+            t = t2;
+            R.fgp2(p, b0, b1, mode);
+            j += 2;
+        } else {
+            R.fgp(p, b0, mode);
+            j += 1;
+        }
+    }
+    return p > 0 ? (p - 1) & 1 : 2;
+}
+
 // FISTA (Eq. FISTA, Eq. FISTA-u): x_0 is projected once; each iteration forms
 // A u_k - y from the two latest residuals, backprojects it, takes the gradient
 // step, the prox by FGP, and projects x_k (its residual r_k = A x_k - y, the
@@ -543,13 +570,7 @@ void run_fista_iteration(Runner<T>& R, const Program& pg, int k3) {
     R.sino_comb(kFistaQ[cur], kFistaQ[prev]);          // A u_k - y = (1 + beta) r_{k-1} - beta r_{k-2}
     R.back1(SB_R, IB_G, FIN_NONE);                     // A^T (A u_k - y)
     R.vec(VEC_FISTA_B, kFistaX[cur] | (kFistaX[prev] << 4), FIN_NONE);   // b = u_k - A^T(A u_k - y)/c^2
-    double t = 1.0;
-    for (int j = 0; j < pg.prox_iters; ++j) {          // FGP: momentum (t_j - 1)/t_{j+1}, t_1 = 1
-        const double t1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
-        R.fgp(j, (t - 1.0) / t1);
-        t = t1;
-    }
-    const int w = pg.prox_iters > 0 ? (pg.prox_iters - 1) & 1 : 2;
+    const int w = run_fgp<T>(R, pg.prox_iters, 0);    // FGP on the prox's dual
     R.vec(VEC_FGP_FINAL, kFistaX[k3] | (w << 4), FIN_NONE);              // x_k = prox(b), views
     R.project(kFistaQ[k3], PROJ_RESIDUAL, FIN_NONE);  // r_k = A x_k - y
     R.sino_norm(kFistaQ[k3], FIN_FISTA_F);             // f(x_k): stop test, t_{k+1}, beta_k
@@ -611,13 +632,7 @@ void run_body(Runner<T>& R, const Program& pg) {
         return;
     }
     if (pg.prox) {                                     // x_{k+1/2} = prox_{lambda_k TV}(x_k): FGP from a zero dual
-        double t = 1.0;
-        for (int j = 0; j < pg.prox_iters; ++j) {
-            const double t1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
-            R.fgp(j, (t - 1.0) / t1, 1);
-            t = t1;
-        }
-        const int w = (pg.prox_iters - 1) & 1;
+        const int w = run_fgp<T>(R, pg.prox_iters, 1);
         R.vec(VEC_FGP_FINAL, IB_XH | (w << 4) | (1 << 8), FIN_PROX_END);   // x_{k+1/2}, views; l <- l+1
     } else {
         for (int t = 0; t < pg.trial_passes; ++t)         // TV trials of x_k + gamma_l v

@@ -1294,6 +1294,147 @@ k_fgp(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int j, 
     }
 }
 
+// Two FGP steps (j, j+1) in one launch, with the buffers of launch index p as
+// k_fgp with j = p (reads dual[2 + (p & 1)] and dual[(p + 1) & 1], writes
+// dual[p & 1] and dual[2 + ((p + 1) & 1)]): step j is computed on the tile
+// grown by one term on every side (from the momentum point with a two-term
+// halo), kept in shared memory, and step j+1 on the tile, so one launch and one
+// round of dual fields through L2 serve two steps.  Every value is formed by the
+// same expressions as in k_fgp, so the iterates are bit-identical.
+template <typename T>
+__global__ void __launch_bounds__(kTileThreads)
+k_fgp2(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int p, typename Tr<T>::C beta0,
+       typename Tr<T>::C beta1, int mode) {
+    using C = typename Tr<T>::C;
+    using C2 = typename Vec2<C>::type;
+    if constexpr (!std::is_same<typename Tr<T>::S, C>::value) {
+        return;                                              // FP32 / FP64 storage only
+    } else {
+    constexpr int H = kTileH, W = kTileW;
+    const Item it = decode_item(probs, items, 1);
+    const Prob<T>& P = probs[it.prob];
+    const DevState& st = *P.st;
+    if (st.done) return;
+    __shared__ C2 rs0[H + 4][W + 4];     // r_j on terms (i0-2+ii, j0-2+jj)
+    __shared__ C bs[H + 3][W + 3];       // b on pixels (i0-1+ii, j0-1+jj)
+    __shared__ C ws0[H + 3][W + 3];      // b - alpha L^T r_j on the same pixels
+    __shared__ C2 w1s[H + 2][W + 2];     // w_j on terms (i0-1+ii, j0-1+jj)
+    __shared__ C2 r1s[H + 2][W + 2];     // r_{j+1} on the same terms
+    __shared__ C ws1[H + 1][W + 1];      // b - alpha L^T r_{j+1} on pixels (i0+ii, j0+jj)
+    const int N = P.n, m = N - 1;
+    const int i0 = it.u * H, j0 = it.v * W;
+    const double a64 = mode ? prox_lambda(st) : st.ex.lam / st.ex.c2;
+    if (!(a64 > 0.0)) return;
+    const C alpha = (C)a64;
+    const C inv8a = C(1) / (C(8) * alpha);
+    const bool start = p == 0;
+    const C2* R = reinterpret_cast<const C2*>(P.dual[2 + (p & 1)]);
+    const C2* Wold = reinterpret_cast<const C2*>(P.dual[(p + 1) & 1]);
+    C2* Wnew = reinterpret_cast<C2*>(P.dual[p & 1]);
+    C2* Rnext = reinterpret_cast<C2*>(P.dual[2 + ((p + 1) & 1)]);
+    const C* B = P.img[mode ? IB_X : IB_Z];
+    const int tl = threadIdx.x;
+    auto valid_term = [&](int ti, int tj) { return ti >= 0 && ti < m && tj >= 0 && tj < m; };
+    constexpr int kR1 = (H + 2) * (W + 2);
+    constexpr int kR1Iters = (kR1 + kTileThreads - 1) / kTileThreads;
+    // every load first: r_j with its two-term halo, b, w_{j-1} on the grown tile
+    for (int q = tl; q < (H + 4) * (W + 4); q += kTileThreads) {
+        const int ii = q / (W + 4), jj = q % (W + 4);
+        const int ti = i0 - 2 + ii, tj = j0 - 2 + jj;
+        C2 v;
+        v.x = C(0);
+        v.y = C(0);
+        if (!start && valid_term(ti, tj)) v = R[(size_t)ti * N + tj];
+        rs0[ii][jj] = v;
+    }
+    for (int q = tl; q < (H + 3) * (W + 3); q += kTileThreads) {
+        const int ii = q / (W + 3), jj = q % (W + 3);
+        const int a = i0 - 1 + ii, b = j0 - 1 + jj;
+        bs[ii][jj] = a >= 0 && a < N && b >= 0 && b < N ? B[(size_t)a * N + b] : C(0);
+    }
+    C2 wo[kR1Iters];
+#pragma unroll
+    for (int k = 0; k < kR1Iters; ++k) {
+        const int q = tl + k * kTileThreads;
+        const int ti = i0 - 1 + q / (W + 2), tj = j0 - 1 + q % (W + 2);
+        wo[k].x = C(0);
+        wo[k].y = C(0);
+        if (q < kR1 && !start && valid_term(ti, tj)) wo[k] = Wold[(size_t)ti * N + tj];
+    }
+    __syncthreads();
+    // w = b - alpha L^T r_j on the pixels of the grown tile plus a row and column
+    for (int q = tl; q < (H + 3) * (W + 3); q += kTileThreads) {
+        const int ii = q / (W + 3), jj = q % (W + 3);
+        const int a = i0 - 1 + ii, b = j0 - 1 + jj;
+        C w = C(0);
+        if (a >= 0 && a < N && b >= 0 && b < N) {
+            // (L^T r) at pixel (a, b): -(p + q) of term (a, b), +p of (a-1, b), +q of (a, b-1)
+            const C lt = -(rs0[ii + 1][jj + 1].x + rs0[ii + 1][jj + 1].y) + rs0[ii][jj + 1].x + rs0[ii + 1][jj].y;
+            w = fma(-alpha, lt, bs[ii][jj]);
+        }
+        ws0[ii][jj] = w;
+    }
+    __syncthreads();
+    // step j on the grown tile: w_j and r_{j+1} (zero on terms outside the image)
+#pragma unroll
+    for (int k = 0; k < kR1Iters; ++k) {
+        const int q = tl + k * kTileThreads;
+        if (q >= kR1) break;
+        const int ii = q / (W + 2), jj = q % (W + 2);
+        const int ti = i0 - 1 + ii, tj = j0 - 1 + jj;
+        C2 wn, rn;
+        wn.x = wn.y = rn.x = rn.y = C(0);
+        if (valid_term(ti, tj)) {
+            const C w0 = ws0[ii][jj];
+            const C2 r = rs0[ii + 1][jj + 1];
+            const C ax = fma(ws0[ii + 1][jj] - w0, inv8a, r.x);      // r + (L w) / (8 alpha)
+            const C ay = fma(ws0[ii][jj + 1] - w0, inv8a, r.y);
+            const C nrm = sqrt(ax * ax + ay * ay);
+            const C sc = nrm > C(1) ? C(1) / nrm : C(1);
+            wn.x = ax * sc;
+            wn.y = ay * sc;
+            rn.x = fma(beta0, wn.x - wo[k].x, wn.x);
+            rn.y = fma(beta0, wn.y - wo[k].y, wn.y);
+        }
+        w1s[ii][jj] = wn;
+        r1s[ii][jj] = rn;
+    }
+    __syncthreads();
+    // w = b - alpha L^T r_{j+1} on the tile's pixels plus a row and column
+    for (int q = tl; q < (H + 1) * (W + 1); q += kTileThreads) {
+        const int ii = q / (W + 1), jj = q % (W + 1);
+        const int a = i0 + ii, b = j0 + jj;
+        C w = C(0);
+        if (a < N && b < N) {
+            const C lt = -(r1s[ii + 1][jj + 1].x + r1s[ii + 1][jj + 1].y) + r1s[ii][jj + 1].x + r1s[ii + 1][jj].y;
+            w = fma(-alpha, lt, bs[ii + 1][jj + 1]);
+        }
+        ws1[ii][jj] = w;
+    }
+    __syncthreads();
+    // step j+1 on the tile
+    const int ty = tl / W, tx = tl % W;
+    const int i = i0 + ty, jc = j0 + tx;
+    if (i >= m || jc >= m) return;
+    const C w0 = ws1[ty][tx];
+    const C2 r = r1s[ty + 1][tx + 1];
+    const C ax = fma(ws1[ty + 1][tx] - w0, inv8a, r.x);
+    const C ay = fma(ws1[ty][tx + 1] - w0, inv8a, r.y);
+    const C nrm = sqrt(ax * ax + ay * ay);
+    const C sc = nrm > C(1) ? C(1) / nrm : C(1);
+    C2 wn;
+    wn.x = ax * sc;
+    wn.y = ay * sc;
+    const C2 wp = w1s[ty + 1][tx + 1];
+    C2 rn;
+    rn.x = fma(beta1, wn.x - wp.x, wn.x);
+    rn.y = fma(beta1, wn.y - wp.y, wn.y);
+    const size_t idx = (size_t)i * N + jc;
+    Wnew[idx] = wn;
+    Rnext[idx] = rn;
+    }
+}
+
 // Caller's plain sinogram [na][nb] into the pair view sino[dst].
 template <typename T>
 __global__ void __launch_bounds__(kRayBlock)
@@ -1586,6 +1727,12 @@ void launch_fgp(const Prob<T>* d, const Item* items, int grid, int j, double bet
     k_fgp<T><<<grid, kTileThreads, 0, s>>>(d, items, j, (typename Tr<T>::C)beta, mode);
 }
 template <typename T>
+void launch_fgp2(const Prob<T>* d, const Item* items, int grid, int p, double beta0, double beta1, int mode,
+                 cudaStream_t s) {
+    using C = typename Tr<T>::C;
+    k_fgp2<T><<<grid, kTileThreads, 0, s>>>(d, items, p, (C)beta0, (C)beta1, mode);
+}
+template <typename T>
 void launch_sino_pairs(const Prob<T>* d, int grid, int dst, cudaStream_t s) {
     k_sino_pairs<T><<<grid, kRayBlock, 0, s>>>(d, dst);
 }
@@ -1635,6 +1782,7 @@ cudaError_t launch_filter(const Prob<T>* d, const Item* items, int grid, int max
     template void launch_sino_pairs<T>(const Prob<T>*, int, int, cudaStream_t);                   \
     template void launch_sino_comb<T>(const Prob<T>*, const Item*, int, int, int, cudaStream_t);    \
     template void launch_fgp<T>(const Prob<T>*, const Item*, int, int, double, int, cudaStream_t);  \
+    template void launch_fgp2<T>(const Prob<T>*, const Item*, int, int, double, double, int, cudaStream_t); \
     template void launch_sino_norm<T>(const Prob<T>*, const Item*, int, int, int, cudaStream_t);    \
     template void launch_set_done<T>(const Prob<T>*, int, int, cudaStream_t);                     \
     template void launch_set_io<T>(Prob<T>*, const typename Tr<T>::S*, typename Tr<T>::S*,          \

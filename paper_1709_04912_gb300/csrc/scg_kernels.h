@@ -53,6 +53,9 @@ void launch_sino_comb(const Prob<T>* d, const Item* items, int grid, int cur, in
 template <typename T>
 void launch_fgp(const Prob<T>* d, const Item* items, int grid, int j, double beta, int mode, cudaStream_t s);
 template <typename T>
+void launch_fgp2(const Prob<T>* d, const Item* items, int grid, int p, double beta0, double beta1, int mode,
+                 cudaStream_t s);
+template <typename T>
 void launch_sino_norm(const Prob<T>* d, const Item* items, int grid, int src, int step, cudaStream_t s);
 void launch_loop_cond(DevState* st, cudaGraphConditionalHandle h, cudaStream_t s);
 void launch_write_result(const DevState* st, scg_result* res, double s2, int cg_family, int base_launches,
