@@ -49,6 +49,7 @@ class Params(ctypes.Structure):
         ("filter_identity", ctypes.c_int),
         ("max_iter", ctypes.c_int),
         ("prox_iters", ctypes.c_int),
+        ("perturb_steps", ctypes.c_int),
     ]
 
 
@@ -344,7 +345,7 @@ def fista(y: np.ndarray, n: int, eps: float, lam: float, c2: float, prox_iters: 
 def default_params(**kw) -> dict:
     p = dict(variant="S-CG", eps=1.0, perturb="gamma", gamma0=0.0, gamma0_rel=0.05,
              a=0.975, max_trials=32, eta0=0.0, K=2, k_inclusive=0, mu=0.0,
-             filter_gain=1.0, filter_identity=0, max_iter=100, prox_iters=20)
+             filter_gain=1.0, filter_identity=0, max_iter=100, prox_iters=20, perturb_steps=1)
     p.update(kw)
     return p
 
@@ -378,7 +379,7 @@ def solve(y: np.ndarray, n: int, x0=None, callback=None, resume: dict | None = N
     prm = Params(VARIANTS[p["variant"]], p["eps"], PERTURB[p["perturb"]], p["gamma0"],
                  p["gamma0_rel"], p["a"], p["max_trials"], p["eta0"], p["K"],
                  p["k_inclusive"], p["mu"], p["filter_gain"], p["filter_identity"],
-                 p["max_iter"], p["prox_iters"])
+                 p["max_iter"], p["prox_iters"], p["perturb_steps"])
     res = Result()
     x = np.zeros((n, n))
     rows = max(int(p["max_iter"]), 1)

@@ -589,6 +589,37 @@ static void perturb(orc_ctx* C, const double* xk, double* xh, double* trow)
     }
 }
 
+/* perturbed(x_k) with several perturbations per step (the superiorization
+ * scheme's N nonascending steps per iteration; the printed algorithms take
+ * one): the rule is applied perturb_steps times in succession, each time from
+ * the current point with its own subgradient; l runs on across the sub-steps
+ * and each sub-step has its own trial budget; a sub-step with a zero
+ * subgradient ends the sequence.  The trace row keeps TV(x_k) from the first
+ * sub-step and the other perturbation fields of the last one.  The eta rule
+ * takes one step only. */
+static void perturb_all(orc_ctx* C, const double* xk, double* xh, double* trow)
+{
+    perturb(C, xk, xh, trow);
+    int steps = C->prm.perturb_steps;
+    if (steps <= 1 || C->prm.perturb == ORC_PERTURB_ETA || C->prm.perturb == ORC_PERTURB_NONE) return;
+    if (trow && trow[ORC_T_ACCEPTED] == -1) return;          /* zero subgradient */
+    double* cur = vec(C->J);
+    double row[ORC_NF];
+    for (int s = 1; s < steps; ++s) {
+        memcpy(cur, xh, sizeof(double) * C->J);
+        for (int q = 0; q < ORC_NF; ++q) row[q] = 0.0;
+        perturb(C, cur, xh, row);
+        if (trow) {
+            double tv0 = trow[ORC_T_TV_BEFORE];
+            for (int q = ORC_T_TV_AFTER; q <= ORC_T_GAMMA; ++q) trow[q] = row[q];
+            trow[ORC_T_MARGIN] = row[ORC_T_MARGIN];
+            trow[ORC_T_TV_BEFORE] = tv0;
+        }
+        if (row[ORC_T_ACCEPTED] == -1) break;
+    }
+    free(cur);
+}
+
 /* One perturbation step of the gamma rule on its own, for checking the rule
  * against hand-worked cases: x_half = perturbed(x) with the global index l
  * starting at *ell (updated on return), gamma_0 = gamma0 and kernel a.  Runs
@@ -812,7 +843,7 @@ static int solve_s_k(orc_ctx* C, int precond, const double* x0, int resumed, orc
             tr[ORC_T_K] = W->k;
             tr[ORC_T_FTEST] = fx;
         }
-        perturb(C, W->x, W->xh, tr);                     /* x_{k+1/2} = perturbed(x_k) */
+        perturb_all(C, W->x, W->xh, tr);                     /* x_{k+1/2} = perturbed(x_k) */
         int st = cg_k(C, precond, W->xh, W->x, W->g, W->p, W->h, W->z); /* x_{k+1} = CG-K(x_{k+1/2}) */
         if (st != ORC_OK) { status = st; ++it; W->k += 1; break; }
         if (cb) cb(it, W->x, W->xh, W->p, W->h, W->g, user);
@@ -868,7 +899,7 @@ static int solve_s_pr(orc_ctx* C, int variant, const double* x0, int resumed, or
             tr[ORC_T_K] = W->k;
             tr[ORC_T_FTEST] = fx;
         }
-        perturb(C, x, xh, tr);                           /* x_{k+1/2} = perturbed(x_k) */
+        perturb_all(C, x, xh, tr);                           /* x_{k+1/2} = perturbed(x_k) */
 
         /* --- the step: CG-PR-STEP / CG-CD-STEP / PCG-PR-STEP --- */
         double f_half = grad_of(C, xh, gn);              /* g' = A^T(A x - y)    */

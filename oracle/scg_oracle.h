@@ -64,6 +64,7 @@ typedef struct {
                             case: PCG then reduces to CG)                      */
     int max_iter;        /* cap on loop bodies                                 */
     int prox_iters;      /* FGP steps of the proximal perturbation             */
+    int perturb_steps;   /* perturbations per step (<= 1: one, as printed)     */
 } orc_params;
 
 typedef struct {
