@@ -75,6 +75,8 @@ def parse():
     ap.add_argument("--lam", type=float, default=30.0, help="FISTA's TV weight lambda (--variant FISTA)")
     ap.add_argument("--prox-iters", type=int, default=10,
                     help="FGP steps per prox (--variant FISTA, --perturb prox)")
+    ap.add_argument("--perturb-steps", type=int, default=1,
+                    help="perturbations per step of the S-variants (scg_params.perturb_steps)")
     ap.add_argument("--perturb", default="gamma", choices=["gamma", "prox"],
                     help="superiorization rule of the S-variants: the gamma rule with its TV test, or the "
                          "proximal perturbation prox_{lambda TV}(x_k)")
@@ -226,7 +228,7 @@ def nnz_of(work) -> int:
 
 # ---------------------------------------------------------------------------
 def time_oracle_solves(prob, work, variant, gamma0_rel, budget_s, max_solves, lam=0.0, prox_iters=10,
-                       perturb="gamma"):
+                       perturb="gamma", perturb_steps=1):
     """Whole oracle solves of ``prob`` (FP64, on the host cores), timed one by
     one until ``budget_s`` seconds or ``max_solves`` solves.  Returns the times,
     the iteration count and the thread count.  FISTA's c^2 comes from the
@@ -238,6 +240,8 @@ def time_oracle_solves(prob, work, variant, gamma0_rel, budget_s, max_solves, la
         kw["perturb"] = "none"
     elif perturb == "prox":
         kw.update(perturb="prox", prox_iters=prox_iters)
+    if variant not in ("CG", "PCG", "FISTA") and perturb_steps > 1:
+        kw["perturb_steps"] = perturb_steps
     if variant == "FISTA":
         c2 = oracle.norm_A(work.n, work.n_angles, work.n_bins, 100) ** 2
 
@@ -268,7 +272,7 @@ def run_reference(args, work, rank, world):
     variant = args.variant
     prob = inputs.make_problem(work, args.seed, oracle.project)
     times, iters, cores = time_oracle_solves(prob, work, variant, args.gamma0_rel, args.ref_budget, args.steps,
-                                             args.lam, args.prox_iters, args.perturb)
+                                             args.lam, args.prox_iters, args.perturb, args.perturb_steps)
     t_solve = float(np.mean(times))
     value = 1.0 / t_solve
     sample = (f"{len(times)} whole oracle {variant} solves of this workload ({iters} iterations to eps each), "
@@ -292,6 +296,8 @@ def config_of(work, variant, prob, iters, args=None):
          "l2": "flushed (512 MiB write) before each step", "per_gpu_problems": 1}
     if args is not None and args.perturb == "prox" and variant not in ("CG", "PCG", "FISTA"):
         c.update(perturb="prox", prox_iters=args.prox_iters)
+    if args is not None and args.perturb_steps > 1 and variant not in ("CG", "PCG", "FISTA"):
+        c["perturb_steps"] = args.perturb_steps
     return c
 
 
@@ -311,6 +317,8 @@ def run_ours(args, work, rank, local_rank, world):
         kw["perturb"] = "none"
     elif args.perturb == "prox":
         kw.update(perturb="prox", prox_iters=args.prox_iters)
+    if variant not in ("CG", "PCG", "FISTA") and args.perturb_steps > 1:
+        kw["perturb_steps"] = args.perturb_steps
     if variant == "FISTA":              # c^2 estimated on the device once, then cached
         kw = dict(lambda_=args.lam, prox_iters=args.prox_iters, max_iter=300, host_loop=int(args.host_loop))
 
@@ -457,7 +465,7 @@ def run_ours(args, work, rank, local_rank, world):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         times, o_iters, cores = time_oracle_solves(prob, work, variant, args.gamma0_rel, 30.0, 1, args.lam,
-                                                   args.prox_iters, args.perturb)
+                                                   args.prox_iters, args.perturb, args.perturb_steps)
         cpu = {"value": 1.0 / float(np.mean(times)), "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": (f"{len(times)} whole oracle {variant} solve(s) of this workload "
                           f"({o_iters} iterations to eps), timed")}

@@ -167,6 +167,13 @@ typedef struct {
                             shape, but f sums the blocks' partial sums, whose
                             rounding depends on the shape: a fixed proj_shape
                             makes solves repeat bit for bit across processes */
+    int perturb_steps;   /* perturbations per step, 1 .. 16 (0 or 1: one, as in
+                            Algorithms 5-14; default 1).  With more, the rule
+                            (SCG_PERTURB_GAMMA or SCG_PERTURB_PROX) is applied
+                            in succession, each time from the current point with
+                            its own subgradient and trial budget, l running on;
+                            the trace row keeps TV(x_k) and the last sub-step's
+                            perturbation fields.  SCG_PERTURB_ETA takes one.  */
 } scg_params;
 
 typedef struct {

@@ -81,7 +81,8 @@ inline bool valid_params(const scg_params* p) {
         !isfinite(p->lipschitz))
         return false;
     if (p->proj_shape != 0 && (p->proj_shape < kProjShiftMin || p->proj_shape > kProjShiftMax)) return false;
-    if (p->perturb == SCG_PERTURB_ETA) return p->eta0 > 0.0 && isfinite(p->eta0);
+    if (p->perturb_steps < 0 || p->perturb_steps > 16) return false;
+    if (p->perturb == SCG_PERTURB_ETA) return p->eta0 > 0.0 && isfinite(p->eta0) && p->perturb_steps <= 1;
     if (p->perturb == SCG_PERTURB_PROX) return p->prox_iters >= 1;
     return p->perturb == SCG_PERTURB_NONE || p->perturb == SCG_PERTURB_GAMMA;
 }
@@ -508,6 +509,7 @@ struct Program {
     bool eta;          // Appendix rule: the gradient at x_k sizes the perturbation
     bool prox;         // proximal perturbation (S-variants): x_{k+1/2} = prox_{lambda_k TV}(x_k)
     int prox_iters;    // FISTA and the proximal perturbation: FGP steps per prox (0: no prox)
+    int pert_steps;    // perturbations per step (S-variants, gamma and prox rules; 1 otherwise)
 };
 
 // g'^T p' for the step length: FIN_BETA derives it from the gradient pass's
@@ -631,19 +633,25 @@ void run_body(Runner<T>& R, const Program& pg) {
         R.vec(VEC_FORM_P, dsel, FIN_CG_END);           // p' = -g' (-z') + beta p; k = k+1; loop test
         return;
     }
-    if (pg.prox) {                                     // x_{k+1/2} = prox_{lambda_k TV}(x_k): FGP from a zero dual
-        const int w = run_fgp<T>(R, pg.prox_iters, 1);
-        R.vec(VEC_FGP_FINAL, IB_XH | (w << 4) | (1 << 8), FIN_PROX_END);   // x_{k+1/2}, views; l <- l+1
-    } else {
-        for (int t = 0; t < pg.trial_passes; ++t)         // TV trials of x_k + gamma_l v
-            R.trial(t == 0 ? kTrialsFirst : kTrials);
-        if (pg.eta) {                                  // ||g_k||, g_k = A^T (A x_k - y)
-            R.vec(VEC_VIEWS, IB_X, FIN_NONE);
-            R.project(SB_R, PROJ_RESIDUAL, FIN_NONE);
-            R.back1(SB_R, IB_G, FIN_NONE);
-            R.vec(VEC_NORM_G, 0, FIN_ETA_SIZE);
+    for (int sub = 0; sub < pg.pert_steps; ++sub) {
+        if (sub > 0) {                                 // the next perturbation starts from x_{k+1/2}
+            R.vec(VEC_COPY_HALF, 0, FIN_NONE);         // (x_k is not used again in the step)
+            R.tvgrad(IB_X, 0, 1, FIN_PERTURB_NEXT);    // its TV and subgradient; trial set-up
         }
-        R.vec(VEC_PERTURB, 0, FIN_NONE);               // x_{k+1/2} = perturbed(x_k)
+        if (pg.prox) {                                 // x_{k+1/2} = prox_{lambda_k TV}(x_k): FGP from a zero dual
+            const int w = run_fgp<T>(R, pg.prox_iters, 1);
+            R.vec(VEC_FGP_FINAL, IB_XH | (w << 4) | (1 << 8), FIN_PROX_END);   // x_{k+1/2}, views; l <- l+1
+        } else {
+            for (int t = 0; t < pg.trial_passes; ++t)     // TV trials of x_k + gamma_l v
+                R.trial(t == 0 ? kTrialsFirst : kTrials);
+            if (pg.eta) {                              // ||g_k||, g_k = A^T (A x_k - y)
+                R.vec(VEC_VIEWS, IB_X, FIN_NONE);
+                R.project(SB_R, PROJ_RESIDUAL, FIN_NONE);
+                R.back1(SB_R, IB_G, FIN_NONE);
+                R.vec(VEC_NORM_G, 0, FIN_ETA_SIZE);
+            }
+            R.vec(VEC_PERTURB, 0, FIN_NONE);           // x_{k+1/2} = perturbed(x_k)
+        }
     }
     R.project(SB_R, PROJ_RESIDUAL, FIN_F);             // A x_{k+1/2} - y, f(x_{k+1/2})
     if (pre) R.filter(SB_R, SB_W);
@@ -783,6 +791,9 @@ inline Program make_program(const scg_params* prm, int variant) {
     pg.prox = prm->perturb == SCG_PERTURB_PROX && family_of(variant) != FAM_CG && family_of(variant) != FAM_FISTA;
     if (family_of(variant) == FAM_FISTA) pg.prox_iters = prm->lambda > 0.0 ? prm->prox_iters : 0;
     else pg.prox_iters = pg.prox ? prm->prox_iters : 0;
+    const bool multi = family_of(variant) != FAM_CG && family_of(variant) != FAM_FISTA &&
+                       (prm->perturb == SCG_PERTURB_GAMMA || prm->perturb == SCG_PERTURB_PROX);
+    pg.pert_steps = multi && prm->perturb_steps > 1 ? prm->perturb_steps : 1;
     if (family_of(variant) == FAM_FISTA) pg.trial_passes = 0;
     return pg;
 }

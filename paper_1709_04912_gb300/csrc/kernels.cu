@@ -866,6 +866,9 @@ k_vec(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int op,
         write_views(P, it.u, it.v, val, in);
         break;
     }
+    case VEC_COPY_HALF:         // x <- x_{k+1/2} (several perturbations per step)
+        if (in) P.img[IB_X][idx] = P.img[IB_XH][idx];
+        break;
     case VEC_FISTA_OUT: {       // the output x_k, from the buffer of k mod 3
         if (in) {
             const int ks = st.k % 3;
@@ -976,7 +979,8 @@ k_tvgrad(const Prob<T>* __restrict__ probs, const Item* __restrict__ items, int 
         v[1] = acc_prod(gr, gr);
         v[2] = acc_prod(x, x);
     }
-    if (step != FIN_NONE) reduce_and_finalize<T, 3, true>(v, P, it.local, P.cnt_img, step);
+    if (step >= kFirstRareStep) reduce_and_finalize<T, 3, true, true>(v, P, it.local, P.cnt_img, step);
+    else if (step != FIN_NONE) reduce_and_finalize<T, 3, true>(v, P, it.local, P.cnt_img, step);
 }
 
 // ---------------------------------------------------------------------------

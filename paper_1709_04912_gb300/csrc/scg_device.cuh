@@ -531,7 +531,9 @@ enum Step {
     FIN_POWER_NORM,   // power iteration: S0 = ||p||^2
     FIN_FISTA_F,      // FISTA: residual of x_k, S0 = ||A x_k - y||^2 -> stop test, t_{k+1}, beta_k
     FIN_ETA_SIZE,     // Appendix rule: S0 = ||g_k||^2 -> the perturbation's size
-    FIN_PROX_END      // proximal perturbation applied (no sums): fix gamma_0, l <- l+1, trace
+    FIN_PROX_END,     // proximal perturbation applied (no sums): fix gamma_0, l <- l+1, trace
+    FIN_PERTURB_NEXT  // a later one of several perturbations per step: S0 = TV, S1 = ||dTV||^2,
+                      // S2 = ||x||^2 of x_{k+1/2} so far -> that sub-step's set-up
 };
 // Steps at or after FIN_POWER are finalised by finalize_rare (see there).
 constexpr int kFirstRareStep = FIN_POWER;
@@ -659,6 +661,32 @@ __device__ __noinline__ void finalize_rare(int step, const Prob<T>& P, DevState&
         }
         break;
     }
+    case FIN_PERTURB_NEXT:
+        // several perturbations per step: a later sub-step starts from x_{k+1/2}
+        // so far (copied into x's buffer) with its own subgradient and trial
+        // budget, l running on; set up as at the top of the loop, without the
+        // loop test.  The trace row keeps TV(x_k) and takes the last sub-step's
+        // perturbation fields.
+        st.tv_x = S[0];
+        st.gnorm2 = S[1];
+        st.xnorm2 = S[2];
+        st.trials = 0;
+        st.margin = __longlong_as_double(0x7ff0000000000000LL);
+        st.coef = 0.0;
+        if (row) {
+            row[TR_TRIALS] = 0.0;
+            row[TR_ACCEPTED] = -1.0;
+            row[TR_GAMMA] = 0.0;
+            row[TR_MARGIN] = st.margin;
+        }
+        if (st.family != FAM_CG && st.perturb == SCG_PERTURB_GAMMA && st.gnorm2 > 0.0) {
+            st.accepted = 0;                                // trials pending
+            set_trial_coefs(st);
+        } else {
+            st.accepted = -1;                               // (the prox rule's step follows)
+            if (row) { row[TR_TV_AFTER] = st.tv_x; row[TR_ELL] = (double)st.ell; }
+        }
+        break;
     case FIN_POWER:
         st.ex.c2 = S[1] / st.xnorm2;                        // Rayleigh quotient of A^T A at p
         st.coef = 1.0 / sqrt(S[0]);

@@ -23,7 +23,8 @@ enum VecOp {
     VEC_FGP_FINAL = 11,    // img[d] = Z - (lambda/c^2) L^T dual[w]; views; sel = d | w << 4 (w = 2: none)
     VEC_FISTA_OUT = 12,    // Z = user_out = x_k (buffer chosen by the device's k)
     VEC_POWER_DOTS = 13,   // S0 = ||H||^2, S1 = P^T H
-    VEC_NORM_G = 14        // S0 = ||G||^2
+    VEC_NORM_G = 14,       // S0 = ||G||^2
+    VEC_COPY_HALF = 15     // X = XH: the next of several perturbations per step starts from x_{k+1/2}
 };
 
 template <typename T>

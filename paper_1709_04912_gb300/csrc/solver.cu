@@ -28,12 +28,12 @@ namespace {
 struct GraphKey {
     int dev;
     const void* work;
-    int prec, variant, trial_passes, ksteps, n, na, nb, host_loop, proj_shift, eta, prox_iters;
+    int prec, variant, trial_passes, ksteps, n, na, nb, host_loop, proj_shift, eta, prox_iters, pert_steps, prox;
     bool operator<(const GraphKey& o) const {
         return std::tie(dev, work, prec, variant, trial_passes, ksteps, n, na, nb, host_loop, proj_shift, eta,
-                        prox_iters) <
+                        prox_iters, pert_steps, prox) <
                std::tie(o.dev, o.work, o.prec, o.variant, o.trial_passes, o.ksteps, o.n, o.na, o.nb,
-                        o.host_loop, o.proj_shift, o.eta, o.prox_iters);
+                        o.host_loop, o.proj_shift, o.eta, o.prox_iters, o.pert_steps, o.prox);
     }
 };
 
@@ -196,7 +196,8 @@ int solve_impl(const scg_geometry* g, int variant, int precision, const scg_para
     // device after every body (no host round trip per iteration).  Fallback:
     // one graph per body, launched in batches and polled one batch ahead.
     GraphKey key{dev, work, precision, variant, pg.trial_passes, pg.ksteps, g->n, g->n_angles, g->n_bins,
-                 prm->host_loop ? 1 : 0, pl.proj_shift, pg.eta ? 1 : 0, pg.prox_iters};
+                 prm->host_loop ? 1 : 0, pl.proj_shift, pg.eta ? 1 : 0, pg.prox_iters, pg.pert_steps,
+                 pg.prox ? 1 : 0};
     BodyGraph bg{nullptr, 0, false};
     {
         std::lock_guard<std::mutex> lk(g_mu);
@@ -687,13 +688,14 @@ BatchPlan make_batch_plan(const scg_problem* pr, int count, int variant, int pre
 struct BatchKey {
     int dev;
     const void* work;
-    int prec, variant, trial_passes, ksteps, cap_probs, nb_cap, eta;
+    int prec, variant, trial_passes, ksteps, cap_probs, nb_cap, eta, pert_steps;
     int cap_items[K_COUNT];
     bool operator<(const BatchKey& o) const {
-        return std::tie(dev, work, prec, variant, trial_passes, ksteps, cap_probs, nb_cap, eta, cap_items[0],
-                        cap_items[1], cap_items[2], cap_items[3], cap_items[4]) <
+        return std::tie(dev, work, prec, variant, trial_passes, ksteps, cap_probs, nb_cap, eta, pert_steps,
+                        cap_items[0], cap_items[1], cap_items[2], cap_items[3], cap_items[4]) <
                std::tie(o.dev, o.work, o.prec, o.variant, o.trial_passes, o.ksteps, o.cap_probs, o.nb_cap, o.eta,
-                        o.cap_items[0], o.cap_items[1], o.cap_items[2], o.cap_items[3], o.cap_items[4]);
+                        o.pert_steps, o.cap_items[0], o.cap_items[1], o.cap_items[2], o.cap_items[3],
+                        o.cap_items[4]);
     }
 };
 std::map<BatchKey, BodyGraph> g_batch_graphs;
@@ -790,7 +792,7 @@ int batch_impl(const scg_problem* pr, int count, int variant, int precision, con
 
     BatchState* bsd = reinterpret_cast<BatchState*>(base + bp.state);
     BatchKey key{dev, work, precision, variant, pg.trial_passes, pg.ksteps, bp.cap_probs, bp.nb_cap,
-                 pg.eta ? 1 : 0, {grid[0], grid[1], grid[2], grid[3], grid[4]}};
+                 pg.eta ? 1 : 0, pg.pert_steps, {grid[0], grid[1], grid[2], grid[3], grid[4]}};
     BodyGraph bg{nullptr, 0, false};
     {
         std::lock_guard<std::mutex> lk(g_mu);
@@ -972,6 +974,7 @@ void scg_default_params(scg_params* p) {
     p->prox_iters = 20;
     p->lipschitz = 0.0;
     p->proj_shape = 0;
+    p->perturb_steps = 1;
 }
 
 size_t scg_op_workspace_bytes(const scg_geometry* g, int precision) {

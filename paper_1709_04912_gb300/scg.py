@@ -38,7 +38,7 @@ class Params(ctypes.Structure):
                 ("mu", ctypes.c_double), ("filter_gain", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("host_loop", ctypes.c_int), ("eta0", ctypes.c_double),
                 ("lambda_", ctypes.c_double), ("prox_iters", ctypes.c_int), ("lipschitz", ctypes.c_double),
-                ("proj_shape", ctypes.c_int)]
+                ("proj_shape", ctypes.c_int), ("perturb_steps", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -308,7 +308,8 @@ def _params(d: dict) -> Params:
     return Params(PERTURB[d["perturb"]], float(d["gamma0"]), float(d["gamma0_rel"]), float(d["a"]),
                   int(d["max_trials"]), int(d["K"]), int(d["k_inclusive"]), float(d["mu"]),
                   float(d["filter_gain"]), int(d["max_iter"]), int(d["host_loop"]), float(d["eta0"]),
-                  float(d["lambda_"]), int(d["prox_iters"]), float(d["lipschitz"]), int(d["proj_shape"]))
+                  float(d["lambda_"]), int(d["prox_iters"]), float(d["lipschitz"]), int(d["proj_shape"]),
+                  int(d["perturb_steps"]))
 
 
 @dataclass
