@@ -41,8 +41,11 @@ void orc_angle(int a, int n_angles, double* c, double* s)
 {
     if (a == 0) { *c = 1.0; *s = 0.0; return; }
     if (2 * a == n_angles) { *c = 0.0; *s = 1.0; return; }
-    double th = ORC_PI * (double)a / (double)n_angles;
-    *c = cos(th);
+    /* theta_a = pi a / n_angles; past pi/2 through cos(pi - t) = -cos t,
+     * sin(pi - t) = sin t, so that theta and pi - theta are exact mirrors */
+    int mirror = 2 * a > n_angles;
+    double th = ORC_PI * (double)(mirror ? n_angles - a : a) / (double)n_angles;
+    *c = mirror ? -cos(th) : cos(th);
     *s = sin(th);
 }
 
