@@ -252,7 +252,14 @@ void fill_angles(std::vector<Angle<T>>& out, int na, int n, double scale = 1.0, 
         double c, s;
         if (ga == 0) { c = 1.0; s = 0.0; }
         else if (2 * ga == na_total) { c = 0.0; s = 1.0; }
-        else { const double th = M_PI * (double)ga / (double)na_total; c = cos(th); s = sin(th); }
+        else {
+            // past pi/2 through cos(pi - t) = -cos t, sin(pi - t) = sin t, so that
+            // theta and pi - theta are exact mirrors (as the oracle computes them)
+            const bool mirror = 2 * ga > na_total;
+            const double th = M_PI * (double)(mirror ? na_total - ga : ga) / (double)na_total;
+            c = mirror ? -cos(th) : cos(th);
+            s = sin(th);
+        }
         const double ac = fabs(c), as = fabs(s);
         const double m = ac > as ? ac : as, mn = ac > as ? as : ac;
         const double hs = 0.5 * (m + mn);
