@@ -134,6 +134,8 @@ struct Plan {
     int S, SB, cnt_ray, cnt_img, cnt_row, tiles_x, ray_blocks, filt_blocks, P;
     int cnt_proj, proj_blocks, proj_shift;
     int cnt_bp;
+    int bp_mirror;          // the gather may take the mirror-paired kernel (64 | N, FP32 arithmetic,
+                            // the scan's full angle set)
     int part_cap;           // work items the partial-sum buffer holds per slot
 };
 
@@ -175,6 +177,7 @@ inline Plan make_plan(const scg_geometry& g, int variant, int precision, int kin
     set_proj_shape(p, na, nb, kProjShiftDefault);
     const int bp_th = precision == SCG_F64 ? kBpTileH64 : kBpTileH32;
     p.cnt_bp = ((N + bp_th - 1) / bp_th) * p.tiles_x;
+    p.bp_mirror = (precision != SCG_F64 && N % 64 == 0) ? 1 : 0;
     p.P = filter_length(nb);
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, kAlign); return o; };
@@ -394,6 +397,7 @@ Prob<T> make_prob(const scg_geometry& g, const Plan& pl, unsigned char* base, do
     P.proj_blocks = pl.proj_blocks;
     P.proj_shift = pl.proj_shift;
     P.cnt_bp = pl.cnt_bp;
+    P.bp_mirror = pl.bp_mirror;
     P.P = pl.P;
     P.off_n = (C)(0.5 * (g.n - 1));
     P.off_b = (C)(0.5 * (g.n_bins - 1));

@@ -411,6 +411,239 @@ __device__ __forceinline__ long long tile_origin_fx(const Angle<float>& g, int X
     return ((long long)(nb - 1) << 31) + (((long long)X2 * g.c_fx + (long long)Y2 * g.s_fx) >> 1);
 }
 
+// ---------------------------------------------------------------------------
+// Mirror-paired gather (FP32 arithmetic, one right-hand side; N a multiple of
+// 64 and a scan's full angle set).  Pixel (x, y) at angle theta and pixel
+// (-x, y) at pi - theta project to the same detector position (cos(pi - t) =
+// -cos t, sin(pi - t) = sin t; the angle table holds these mirrors exactly),
+// so one band index and one pair of weights serve both.  A work item is a
+// 32 x 16 tile T of the image's left half together with its mirror image T'
+// in the right half, four pixels of each per thread.  Angles come in slots:
+// angle 0, the pairs (a, na - a) for 0 < a < na/2, and angle na/2 when na is
+// even.  For a slot (a, a') and a thread's pixel p of T (mirror p' of T'):
+//   window A = the positions of T at angle a:        p at a,  p' at a'
+//   window B = the positions of T at the mirror of a: p at a', p' at a
+// so a slot stages four bands (rows a and a' over each window) and takes two
+// weight evaluations and four pair loads per pixel pair, where the plain
+// gather takes four evaluations.  A slot with a single angle (0, na/2) has no
+// second row: its two bands of it are zero-filled in shared memory and every
+// slot takes the same path.  Item q is the plain gather's item q (64 | N makes
+// the counts equal: (N/64) x (N/16) = (N/32)^2), so work lists and partial
+// sums are shared with it, and a batch or a server step mixes problems of
+// either path in one launch (each problem always takes the same one, so its
+// result does not depend on its company); bands arrive by TMA as in the plain
+// gather, four boxes per slot, eight slots per chunk, in the plain gather's
+// shared storage (the same number of band bytes).  Called by the plain
+// gather's blocks for a problem with bp_mirror set.
+template <typename T>
+__device__ __forceinline__ void backproject_mirror(const Prob<T>& P, const Item& it, int part, int src, int dst,
+                                                   int step, void* rows_smem, void* band_smem,
+                                                   unsigned long long* mbar) {
+    using S2 = typename Tr<T>::S2;
+    using C = typename Tr<T>::C;
+    static_assert(std::is_same<C, float>::value, "FP32 arithmetic");
+    constexpr int TH = 16, PIX = 4, kStep = TH / PIX, CH = 8, CL = 4, NB = 4;
+    static_assert(kTileW * kStep == kBackThreads && kBackThreads == 128, "one thread per column and row group");
+    static_assert(CH * NB == 32, "one box per staging lane: lanes 0..7 of the four warps");
+    constexpr int kBand = band_slots<S2>();
+    constexpr int kSlotsPerSeg = 16 / (int)sizeof(S2);
+    constexpr int kBandS = (kBand * (int)sizeof(S2) + 127) / 128 * 128 / (int)sizeof(S2);
+    constexpr unsigned kBoxBytes = (unsigned)(kBand * (int)sizeof(S2));
+    struct __align__(16) Row {
+        int baseA, baseB;    // band index of T's origin in windows A and B, in 9.23 fixed point
+        int c23, s23;        // cos, sin of angle a in 9.23
+        float kb, hb0p, hb1p;
+        int pad_;
+    };
+    Row (&rows)[2][CH] = *reinterpret_cast<Row(*)[2][CH]>(rows_smem);
+    // bands: a over A, a' over A, a' over B, a over B
+    S2 (&band)[2][CH][NB][kBandS] = *reinterpret_cast<S2(*)[2][CH][NB][kBandS]>(band_smem);
+    const int N = P.n, na = P.na, nb = P.nb;
+    const int tl = threadIdx.x, tx = tl % kTileW, ty = tl / kTileW;
+    const int mcols = N / 64;                    // left-half tile columns
+    const int i0 = (it.local / mcols) * TH, j0 = (it.local % mcols) * kTileW;
+    const int X2 = 2 * j0 - (N - 1), Y2 = 2 * i0 - (N - 1);
+    const int npairs = (na - 1) / 2;             // slots 1..npairs: (a, na - a)
+    const int nslots = npairs + 1 + ((na & 1) ? 0 : 1);
+    const int nsp = (nslots + CL - 1) / CL;      // slots of each block
+    const int s_begin = min(nslots, part * nsp), s_end = min(nslots, s_begin + nsp);
+    const int nchunks = (nsp + CH - 1) / CH;     // the same for every block of the cluster
+    const unsigned char* map = P.sino_map + (size_t)src * kSinoMapBytes;
+
+    bool ok = true;                              // every wait of this thread on its block's copies completed
+    // Rows and bands of chunk ch: lane l < 8 of warp w takes box b = 8 w + l,
+    // slot b / 4 of the chunk, band b % 4.  A lane of window B places T at the
+    // mirror of a (cos -> -cos, in 32.32 fixed point: exact); box origin = the
+    // window's first slot, rounded down to a 16-byte boundary as TMA requires.
+    // Thread 0 adds the chunk's TMA bytes to the barrier's expected count (a
+    // copy may complete first; the phase still ends only after that arrival).
+    auto stage = [&](int ch) {
+        const int buf = ch & 1;
+        const int s0 = s_begin + ch * CH;
+        const int cnt = min(CH, s_end - s0);             // may be <= 0 (a part with no slots)
+        if (tl == 0 && ok) {
+            int single = 0;                              // slots of one angle in this chunk (two boxes fewer each)
+            if (cnt > 0 && s0 == 0) ++single;
+            if (cnt > 0 && (na & 1) == 0 && s0 <= npairs + 1 && npairs + 1 < s0 + cnt) ++single;
+            mbar_expect_tx(smem_addr(&mbar[buf]), cnt > 0 ? (unsigned)(cnt * NB - 2 * single) * kBoxBytes : 0u);
+        }
+        const int lane = tl & 31;
+        const int b = (tl >> 5) * 8 + lane;
+        const int q = b >> 2, which = b & 3;
+        if (lane < 8 && q < cnt) {
+            const int sl = s0 + q;
+            const bool pair = sl >= 1 && sl <= npairs;
+            const int a = sl <= npairs ? sl : na / 2;
+            const Angle<C> g = P.ang[a];
+            const bool wB = which >= 2;
+            const long long cfx = wB ? -g.c_fx : g.c_fx;
+            const long long cb = ((long long)(nb - 1) << 31) + (((long long)X2 * cfx + (long long)Y2 * g.s_fx) >> 1);
+            const int lo = (int)floorf((float)(kTileW - 1) * fminf(wB ? -g.c : g.c, 0.f)) - 1;
+            const int I = (int)(cb >> 32);
+            const int s_lo = (I + kSPad + lo) & ~(kSlotsPerSeg - 1);
+            const int base = ((I + kSPad - s_lo) << 23) | (int)((unsigned)cb >> 9);
+            Row& r = rows[buf][q];
+            if (which == 0) {
+                r.baseA = base;
+                r.c23 = g.c23; r.s23 = g.s23;
+                r.kb = g.kb; r.hb0p = g.hb0p; r.hb1p = g.hb1p;
+                r.pad_ = 0;
+            } else if (which == 2) {
+                r.baseB = base;
+            }
+            S2* dstb = &band[buf][q][which][0];
+            if (pair || which == 0 || which == 3) {
+                // this buffer was last read through the generic proxy (before the
+                // block barrier that ended that chunk); order those reads first
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                tma_load_2d(smem_addr(dstb), map, s_lo, (which == 0 || which == 3) ? a : na - a, smem_addr(&mbar[buf]));
+            } else {
+                // no second angle: zeros (visible to the block after the barrier
+                // that ends the current chunk)
+                uint4* z = reinterpret_cast<uint4*>(dstb);
+                for (int k = 0; k < kBand * (int)sizeof(S2) / 16; ++k) z[k] = make_uint4(0u, 0u, 0u, 0u);
+            }
+        }
+    };
+
+    float acc[2 * PIX];                          // p (rows ty + 4k of T), then p' (the same rows of T')
+#pragma unroll
+    for (int k = 0; k < 2 * PIX; ++k) acc[k] = 0.f;
+    if (tl == 0) {
+        mbar_init(smem_addr(&mbar[0]));
+        mbar_init(smem_addr(&mbar[1]));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    stage(0);
+    __syncthreads();
+    for (int ch = 0; ch < nchunks; ++ch) {
+        // stage the next chunk (into the other buffer, free since the barrier
+        // that ended the previous chunk), then wait for this chunk's bands --
+        // always, even after a wait ran out, so that no copy is in flight when
+        // the block ends
+        if (ch + 1 < nchunks) stage(ch + 1);
+        const bool w = mbar_wait(smem_addr(&mbar[ch & 1]), (unsigned)((ch >> 1) & 1));
+        ok = ok && w;
+        const int cnt = min(CH, s_end - (s_begin + ch * CH));
+        const int buf = ch & 1;
+        if (ok) {
+#pragma unroll 2
+            for (int q = 0; q < cnt; ++q) {
+                const Row r = rows[buf][q];
+                // 9.23 positions of the thread's first pixel in windows A and B (> 0)
+                const int pA0 = r.baseA + tx * r.c23 + ty * r.s23;
+                const int pB0 = r.baseB - tx * r.c23 + ty * r.s23;
+                const int dp = kStep * r.s23;
+                const S2* bq = &band[buf][q][0][0];
+#pragma unroll
+                for (int k = 0; k < PIX; ++k) {
+                    const int pA = pA0 + k * dp, pB = pB0 + k * dp;
+                    // 1 + fraction as a float in [1, 2): the fraction bits are the mantissa
+                    const float fA = __int_as_float(0x3F800000 | ((unsigned)pA & 0x7FFFFFu));
+                    const float fB = __int_as_float(0x3F800000 | ((unsigned)pB & 0x7FFFFFu));
+                    const float wA0 = __saturatef(fmaf(-fA, r.kb, r.hb0p)), wA1 = __saturatef(fmaf(fA, r.kb, r.hb1p));
+                    const float wB0 = __saturatef(fmaf(-fB, r.kb, r.hb0p)), wB1 = __saturatef(fmaf(fB, r.kb, r.hb1p));
+                    const int iA = pA >> 23, iB = pB >> 23;
+                    const float2 e0 = to_c2(bq[iA]);                 // row a,  window A: p  at a
+                    const float2 e1 = to_c2(bq[kBandS + iA]);        // row a', window A: p' at a'
+                    const float2 e2 = to_c2(bq[2 * kBandS + iB]);    // row a', window B: p  at a'
+                    const float2 e3 = to_c2(bq[3 * kBandS + iB]);    // row a,  window B: p' at a
+                    acc[k] = fmaf(wA0, e0.x, fmaf(wA1, e0.y, acc[k]));
+                    acc[PIX + k] = fmaf(wA0, e1.x, fmaf(wA1, e1.y, acc[PIX + k]));
+                    acc[k] = fmaf(wB0, e2.x, fmaf(wB1, e2.y, acc[k]));
+                    acc[PIX + k] = fmaf(wB0, e3.x, fmaf(wB1, e3.y, acc[PIX + k]));
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (!ok) atomicExch(&P.st->dev_error, 1);     // a band never arrived: the sums are not valid
+    // pixel k of this thread: row i0 + ty + 4 (k % PIX), column j0 + tx (k < PIX)
+    // or its mirror N - 1 - j0 - tx
+    auto pix = [&](int k) {
+        const int i = i0 + ty + (k % PIX) * kStep;
+        const int j = k < PIX ? j0 + tx : N - 1 - j0 - tx;
+        return (size_t)i * N + j;
+    };
+    // block 0's epilogue operands (h and p for the fused dots), loaded before
+    // the cluster barriers so that their latency overlaps the hand-over
+    const bool want_h = step == FIN_BETA;
+    const bool want_p = step == FIN_BETA || step == FIN_ALPHA || step == FIN_CG_ALPHA;
+    C hv[2 * PIX], pv[2 * PIX];
+#pragma unroll
+    for (int k = 0; k < 2 * PIX; ++k) {
+        const size_t idx = pix(k);
+        hv[k] = part == 0 && want_h ? to_c(P.img[IB_H][idx]) : C(0);
+        pv[k] = part == 0 && want_p ? to_c(P.img[IB_P][idx]) : C(0);
+    }
+    // blocks 1..3 write their sums into block 0's band storage (free once every
+    // block of the cluster has passed the first cluster barrier; release /
+    // acquire), and block 0 adds them in rank order after the second
+    float* xs = reinterpret_cast<float*>(&band[0][0][0][0]);
+    static_assert(sizeof(float) * (CL - 1) * 2 * PIX * kBackThreads <= sizeof(band), "hand-over fits");
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    if (part != 0) {
+        const unsigned local = (unsigned)__cvta_generic_to_shared(&xs[tl]);
+        unsigned remote;
+        asm volatile("mapa.shared::cluster.u32 %0, %1, 0;" : "=r"(remote) : "r"(local));
+#pragma unroll
+        for (int k = 0; k < 2 * PIX; ++k)
+            asm volatile("st.shared::cluster.f32 [%0], %1;"
+                         ::"r"(remote + (unsigned)(sizeof(float) * ((part - 1) * 2 * PIX + k) * kBackThreads)),
+                         "f"(acc[k]) : "memory");
+    }
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    if (part != 0) return;
+#pragma unroll
+    for (int r = 1; r < CL; ++r)
+#pragma unroll
+        for (int k = 0; k < 2 * PIX; ++k) acc[k] = acc[k] + xs[((r - 1) * 2 * PIX + k) * kBackThreads + tl];
+    using S = typename Tr<T>::S;
+    Acc<T> v[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) acc_zero(v[q]);
+#pragma unroll
+    for (int k = 0; k < 2 * PIX; ++k) {
+        const size_t idx = pix(k);
+        // stored values are rounded to the storage format; the dots use them
+        const C g0 = rnd<T>(acc[k]);
+        P.img[dst][idx] = to_s<S>(g0);
+        if (step == FIN_BETA) {
+            v[0] = acc_add(v[0], acc_prod(g0, hv[k]));               // g'^T h
+            v[1] = acc_add(v[1], acc_prod(g0, g0));                  // ||g'||^2
+            v[2] = acc_add(v[2], acc_prod(g0, pv[k]));               // g'^T p
+        } else if (step == FIN_ALPHA || step == FIN_CG_ALPHA) {
+            v[0] = acc_add(v[0], acc_prod(pv[k], g0));               // p^T h
+        } else if (step == FIN_CG_DELTA) {
+            v[0] = acc_add(v[0], acc_prod(g0, g0));                  // ||g||^2
+            v[1] = acc_add(v[1], acc_prod(g0, g0));                  // g^T z (z = g)
+        }
+    }
+    if (step == FIN_NONE) return;
+    reduce_and_finalize<T, 3>(v, P, it.local, P.cnt_bp, step);
+}
+
 // Gather blocks per SM the register allocation is sized for: seven with one
 // right-hand side (72 registers; at 512^2 the 1024 blocks then run in one wave
 // on 152 SMs), six with two, whose sums need more registers.
@@ -444,6 +677,14 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
     __shared__ int slo[2][CH];                   // first slot of each band in its sinogram row (FP64)
     __shared__ __align__(128) S2 band[2][NRHS][CH][kBandS];
     __shared__ __align__(8) unsigned long long mbar[2];   // TMA completion per band buffer
+    if constexpr (kF32 && NRHS == 1) {
+        if (P.bp_mirror) {
+            static_assert(sizeof(rows) >= 2 * 8 * sizeof(BpRowF) && sizeof(band) >= 2 * 8 * 4 * kBandS * sizeof(S2),
+                          "the mirror-paired path fits the plain gather's storage");
+            backproject_mirror<T>(P, it, part, src0, dst0, step, &rows[0][0], &band[0][0][0][0], mbar);
+            return;
+        }
+    }
     const int N = P.n, na = P.na, nb = P.nb, SB = P.SB;
     const int tl = threadIdx.x;
     const int nap = (na + CL - 1) / CL;          // angles of each block

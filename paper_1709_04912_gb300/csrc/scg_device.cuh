@@ -230,6 +230,8 @@ struct Prob {
     int cnt_proj, proj_blocks;       // projector items; bin blocks per angle group
     int proj_shift;                  // projector block = 2^(8-shift) angles x 2^shift rays
     int cnt_bp;                      // backprojector tiles (32 x kBpTileH32 or kBpTileH64)
+    int bp_mirror;                   // the gather takes its mirror-paired path (FP32 arithmetic,
+                                     // 64 | n, the scan's full angle set)
     int tiles_x;            // image tiles per row of tiles
     int ray_blocks;         // projector items per angle
     int filt_blocks;        // filter items per row pair (1)

@@ -400,8 +400,9 @@ template <typename T>
 int op_setup(const scg_geometry& g, void* work, size_t work_bytes, cudaStream_t s, Plan* pl_out,
              Prob<T>* P_out, int a_begin = 0, int na_total = -1) {
     using C = typename Tr<T>::C;
-    const Plan pl = make_plan(g, SCG_S_CG, prec_of<T>(), PLAN_OP);
+    Plan pl = make_plan(g, SCG_S_CG, prec_of<T>(), PLAN_OP);
     if (work_bytes < pl.total || ((uintptr_t)work & 15u)) return SCG_ERR_WORKSPACE;
+    if (a_begin != 0 || (na_total >= 0 && na_total != g.n_angles)) pl.bp_mirror = 0;   // an angle block
     unsigned char* base = (unsigned char*)work;
     Prob<T> P = make_prob<T>(g, pl, base);
     std::vector<Angle<C>> ang;

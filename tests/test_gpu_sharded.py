@@ -3,8 +3,11 @@
 
 * A block's projection is exactly those rows of the whole scan's projection
   (every ray is computed alike, whatever block it falls in).
-* The blocks' backprojection shares add up to the whole A^T r (to rounding of
-  the order of the sums).
+* The blocks' backprojection shares add up to the whole A^T r: to rounding of
+  the order of the sums in FP64; in FP32 within the operator tolerance, since
+  with 64 | N the whole scan takes the mirror-paired gather and an angle
+  block the plain one (two roundings of the same weights, each within 3.3e-6
+  of the oracle).
 * The sharded driver on one rank with the device operators (FP64) reproduces
   scg_solve's S-CG: iterations, decisions, l, x within 1e-9.
 """
@@ -26,7 +29,7 @@ def rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
-@pytest.mark.parametrize("dtype,tol", [(torch.float32, 1e-6), (torch.float64, 1e-13)])
+@pytest.mark.parametrize("dtype,tol", [(torch.float32, 1e-5), (torch.float64, 1e-13)])
 @pytest.mark.parametrize("n,na,nb,world", [(64, 90, 95, 2), (77, 33, 110, 3), (130, 181, 185, 4)])
 def test_angle_block_operators(n, na, nb, world, dtype, tol):
     x = torch.tensor(inputs.ellipse_phantom(n, 8, n) + 0.1 * inputs.normal(n, "i", n * n).reshape(n, n),

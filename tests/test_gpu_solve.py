@@ -8,8 +8,9 @@ C ABI (scg_solve).
 * FP32, same workload: every TV decision of the seed has a relative margin
   above 1e-5 (asserted), so the decisions and the iteration count must be
   the oracle's; the output within a per-variant bound of about 3x the error
-  measured on a GB300 (CG 1.7e-3, PCG 5.4e-7, S-CG 2.2e-6, S-CG-CD 1.6e-5,
-  S-CG-K 4.8e-5, S-PCG 2.2e-6, S-PCG-K 7.6e-7).  FP32 operators differ from
+  measured on a GB300 with either gather path (CG 1.1e-3 - 1.7e-3, PCG 4.6e-7
+  - 5.4e-7, S-CG 0.9e-6 - 2.2e-6, S-CG-CD 2.2e-6 - 1.6e-5, S-CG-K 4.8e-5 -
+  1.8e-4, S-PCG 1.7e-6 - 2.2e-6, S-PCG-K 5.9e-7 - 7.6e-7).  FP32 operators differ from
   the FP64 ones by ~1e-7 relative per output; a solve carries that difference
   into x amplified by how far into the Krylov space it goes (the error grows
   with the number of operator applications: S-CG-K's 28 against S-PCG-K's 6),
@@ -49,9 +50,14 @@ def rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
-FP32_BOUND = {"CG": 5e-3, "PCG": 2e-6, "S-CG": 7e-6, "S-CG-CD": 5e-5, "S-CG-K": 1.5e-4,
+# ~3x the measured error (both gather paths: S-CG-K 4.8e-5 with the plain one, 1.8e-4 with the
+# mirror-paired one that 64 | N selects -- a more accurate operator, 2.2e-6 against 2.8e-6, whose
+# different rounding the restarted solve amplifies differently)
+FP32_BOUND = {"CG": 5e-3, "PCG": 2e-6, "S-CG": 7e-6, "S-CG-CD": 5e-5, "S-CG-K": 5e-4,
               "S-PCG": 7e-6, "S-PCG-K": 2.5e-6}
-FP32_TV = {"CG": 1e-2, "PCG": 1e-5}                    # others: 1e-5 (measured <= 1.5e-6)
+# final TV, relative: others 1e-5 (measured <= 1.5e-6); S-CG-K ~3x the 3.2e-5 measured with the
+# mirror-paired gather (its x error above)
+FP32_TV = {"CG": 1e-2, "PCG": 1e-5, "S-CG-K": 1e-4}
 
 
 def kw_for(variant, prob, **extra):
@@ -126,8 +132,9 @@ def test_trial_passes_decide_like_the_oracle(small, gamma0_rel, a, max_trials, d
     r = gpu_solve(small, dtype, **kw)
     assert r.status == ro["status"] and r.iters == ro["iters"] and r.ell == ro["ell"]
     np.testing.assert_array_equal(r.trace[:, DECISION], to[:, DECISION])
-    # FP32: ~3x the 1.0e-5 measured for (0.5, 0.975, 31), whose first steps reject whole passes
-    assert rel(r.x.cpu().numpy(), xo) <= (1e-9 if dtype == torch.float64 else 3e-5)
+    # FP32: ~3x the largest measured, 4.0e-5 for (2.0, 0.975, 40) (its first steps reject whole
+    # passes; 1.8e-5 with the plain gather, whose rounding the run amplifies differently)
+    assert rel(r.x.cpu().numpy(), xo) <= (1e-9 if dtype == torch.float64 else 1.2e-4)
 
 
 @pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-11), (torch.float32, 1e-5)])
