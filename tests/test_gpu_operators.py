@@ -4,7 +4,10 @@ A (ray-driven projector), A^T (pixel-driven backprojector), TV, its
 subgradient and the preconditioner's row filter, on seeded inputs.  Small
 cases (several tiles plus ragged tails, axis-aligned and diagonal angles, odd
 and even sizes) are compared element by element; the full-size workloads are
-compared on sampled rays/pixels that the oracle evaluates one by one.
+compared on sampled rays/pixels that the oracle evaluates one by one.  The
+gather's mirror-paired path (64 | N) has its own cases: single and unpaired
+angles, odd counts, narrow and wide detectors, 16-bit storage, and a
+weight-by-weight comparison with the projector.
 
 Tolerances: relative L2 <= 1e-5 for FP32 (FP32 geometry and accumulation over
 at most ~2N weights per ray; the measured error is ~1e-7), <= 1e-12 for FP64.
@@ -152,6 +155,67 @@ def test_filter_at_the_fp32_length_limit():
     r = inputs.normal(9, "f", na * nb).reshape(na, nb)
     got = scg.scg_filter(torch.tensor(r, dtype=torch.float32, device=DEV)).cpu().numpy()
     assert rel(got, oracle.filter_rows(r)) <= 1e-5
+
+
+# Geometries of the gather's mirror-paired path (64 | N, FP32 arithmetic): one
+# angle (slot 0 alone), two (0 and the self-mirrored pi/2: no pair), an odd count
+# (pairs and angle 0), the batch's and server's sizes, a detector narrower than
+# the image (rays and bands beyond it), and a band reaching past both ends.
+MIRROR_CASES = [
+    (64, 1, 91),
+    (64, 2, 91),
+    (64, 7, 91),
+    (128, 33, 182),
+    (192, 120, 272),
+    (64, 90, 20),
+    (256, 61, 400),
+]
+
+
+@pytest.mark.parametrize("n,na,nb", MIRROR_CASES)
+def test_mirror_gather_matches_oracle(n, na, nb):
+    r = inputs.normal(5 * n + na, "msino", na * nb).reshape(na, nb)
+    ref = oracle.backproject(r, n)
+    got = scg.scg_backproject(torch.tensor(r, dtype=torch.float32, device=DEV), n).cpu().numpy()
+    assert rel(got, ref) <= 1e-5
+    # and the pixels of each half: the mirror images of the left half's pixels
+    # are gathered from the other rows of each angle pair
+    assert rel(got[:, n // 2:], ref[:, n // 2:]) <= 1e-5
+    assert rel(got[:, :n // 2], ref[:, :n // 2]) <= 1e-5
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float16, 2e-3), (torch.bfloat16, 1.5e-2)])
+@pytest.mark.parametrize("n,na,nb", [(64, 7, 91), (128, 33, 182)])
+def test_mirror_gather_reduced_storage(n, na, nb, dtype, tol):
+    # 16-bit storage: the sinogram rounded to the format, the gather in FP32
+    r = inputs.normal(3 * n + na, "msino16", na * nb).reshape(na, nb)
+    rq = torch.tensor(r, dtype=torch.float32).to(dtype)
+    ref = oracle.backproject(rq.double().numpy(), n)
+    got = scg.scg_backproject(rq.to(DEV), n).double().cpu().numpy()
+    assert rel(got, ref) <= tol
+
+
+def test_mirror_gather_is_matched_weight_by_weight():
+    # the mirror-paired gather (n = 64) against the projector, weight by
+    # weight: dense A from unit images, dense A^T from unit sinograms, with
+    # angle pairs (1, 5), (2, 4) and the unpaired angles 0 and 3
+    n, na, nb = 64, 6, 91
+    A = np.zeros((na * nb, n * n))
+    for q in range(n * n):
+        e = torch.zeros(n * n, dtype=torch.float32, device=DEV)
+        e[q] = 1
+        A[:, q] = scg.scg_project(e.view(n, n), na, nb).cpu().numpy().ravel()
+    AT = np.zeros((n * n, na * nb))
+    for q in range(na * nb):
+        e = torch.zeros(na * nb, dtype=torch.float32, device=DEV)
+        e[q] = 1
+        AT[:, q] = scg.scg_backproject(e.view(na, nb), n).cpu().numpy().ravel()
+    scale = np.max(np.abs(A))
+    assert np.max(np.abs(A - AT.T)) <= 1e-5 * scale
+    one_sided = (A != 0) != (AT.T != 0)
+    assert np.all(np.abs(A - AT.T)[one_sided] <= 1e-5 * scale)
+    # no ray the projector sees is missing from the gather (a slot's band lost)
+    assert np.all(np.abs(AT).sum(axis=0)[np.abs(A).sum(axis=1) > 0] > 0)
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
