@@ -237,7 +237,11 @@ int scg_project(const scg_geometry* g, int precision, const void* x, void* y,
                 void* work, size_t work_bytes, void* stream);
 
 /* x = A^T r (the backprojection in every step of Algorithms 1-14; pixel-driven
- * gather that evaluates the same weights as scg_project, no atomics). */
+ * gather that evaluates the same weights as scg_project, no atomics).  With
+ * FP32 arithmetic and n a multiple of 64 it pairs each pixel (x, y) with its
+ * mirror (-x, y), which meets angle pi - theta at the same detector position,
+ * so the two share one weight evaluation; results agree with the plain gather
+ * (other n, angle-block operators) to FP32 rounding, not bit for bit. */
 int scg_backproject(const scg_geometry* g, int precision, const void* r, void* x,
                     void* work, size_t work_bytes, void* stream);
 

@@ -4,7 +4,10 @@
 //                  epilogue r = Ax - y and FP64 sum of squares (f of Sec. 1)
 //   k_sino_norm    ||r||^2 of a residual view (FISTA's f)
 //   k_backproject  pixel-driven gather A^T (1 or 2 right-hand sides), fused
-//                  FP64 inner products of Algorithms 2/4/8/10/14
+//                  FP64 inner products of Algorithms 2/4/8/10/14; with one
+//                  right-hand side, 64 | N and a full angle set, a
+//                  mirror-paired path (pixel (x, y) at theta and (-x, y) at
+//                  pi - theta share one band index and weight pair)
 //   k_vec          CG vector updates (p' = -g' + beta p, x' = x + alpha p,
 //                  g' = g + alpha h), perturbation apply, projector views
 //   k_tvgrad       TV, TV subgradient, ||dTV||^2, ||x||^2 (optionally fused
