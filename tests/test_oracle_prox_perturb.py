@@ -9,8 +9,8 @@ cannot raise TV, so no trial is taken and l grows by one per perturbed step;
 a zero subgradient leaves x_k as it is.
 
 The checks below use a TV and a subgradient restated here in numpy (isotropic
-forward differences over the interior terms, the form the paper's TV takes in
-this build), not the oracle's own routines: lambda against gamma_0 a^l, the
+forward differences over the interior terms, the reading of the paper's TV
+that the library and the oracle follow), not the oracle's own routines: lambda against gamma_0 a^l, the
 prox optimality of the result by brute force (no random nearby point has a
 lower lambda TV(z) + ||z - x||^2 / 2), TV not raised, the index, and the
 special cases.
