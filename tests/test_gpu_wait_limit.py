@@ -25,10 +25,13 @@ def lib():
     return scg.load()
 
 
-# 90 angles: one chunk of bands per gather block; 360 angles: three, so after
-# the first wait runs out one more chunk is in flight (waited for, with its
-# limit) and the rest are never issued
-WORKLOADS = {"a90": inputs.SMALL_FP64, "a360": inputs.Workload("ellipse64_a360_b95", 64, 360, 95, 6, 0.01, 1.05, 100)}
+# 64 x 64 takes the gather's mirror-paired path (slots of an angle and its
+# mirror, eight a chunk): 90 angles give each gather block two chunks of bands,
+# 360 angles six, so after the first wait runs out one more chunk is in flight
+# (waited for, with its limit) and the rest are never issued; 77 x 77 takes the
+# plain path (32 angles a chunk: one chunk per block at 90 angles)
+WORKLOADS = {"a90": inputs.SMALL_FP64, "a360": inputs.Workload("ellipse64_a360_b95", 64, 360, 95, 6, 0.01, 1.05, 100),
+             "n77": inputs.Workload("ellipse77_a90_b110", 77, 90, 110, 6, 0.01, 1.05, 100)}
 
 
 def make(name):
@@ -41,7 +44,8 @@ def problem():
     return make("a90")
 
 
-@pytest.mark.parametrize("dtype,name", [(torch.float32, "a90"), (torch.float16, "a90"), (torch.float32, "a360")])
+@pytest.mark.parametrize("dtype,name", [(torch.float32, "a90"), (torch.float16, "a90"), (torch.float32, "a360"),
+                                        (torch.float32, "n77")])
 def test_solve_reports_a_wait_that_ran_out(dtype, name):
     prob, y = make(name)
     y = y.to(dtype)
