@@ -395,6 +395,16 @@ __device__ __forceinline__ void tma_load_2d(unsigned dst, const void* map, int x
                  ::"r"(dst), "l"(map), "r"(x), "r"(y), "r"(mb) : "memory");
 }
 
+// Per-slot row of the mirror-paired gather (below): an angle a and its mirror.
+struct __align__(16) BpRowM {
+    int baseA, baseB;    // band index of the tile's origin in windows A and B, in 9.23 fixed point
+    int c23, s23;        // cos, sin of angle a in 9.23
+    float kb, hb0p, hb1p;
+    int pad_;
+};
+constexpr int kBpMirrorCH = 8;    // slots per chunk of the mirror-paired gather
+constexpr int kBpMirrorNB = 4;    // bands per slot
+
 // Per-angle row of the FP32 gather (two 16-byte shared loads).
 struct __align__(16) BpRowF {
     int base;        // band index of the tile origin's projection, in 9.23 fixed point
@@ -445,19 +455,14 @@ __device__ __forceinline__ void backproject_mirror(const Prob<T>& P, const Item&
     using S2 = typename Tr<T>::S2;
     using C = typename Tr<T>::C;
     static_assert(std::is_same<C, float>::value, "FP32 arithmetic");
-    constexpr int TH = 16, PIX = 4, kStep = TH / PIX, CH = 8, CL = 4, NB = 4;
+    constexpr int TH = 16, PIX = 4, kStep = TH / PIX, CH = kBpMirrorCH, CL = 4, NB = kBpMirrorNB;
     static_assert(kTileW * kStep == kBackThreads && kBackThreads == 128, "one thread per column and row group");
     static_assert(CH * NB == 32, "one box per staging lane: lanes 0..7 of the four warps");
     constexpr int kBand = band_slots<S2>();
     constexpr int kSlotsPerSeg = 16 / (int)sizeof(S2);
     constexpr int kBandS = (kBand * (int)sizeof(S2) + 127) / 128 * 128 / (int)sizeof(S2);
     constexpr unsigned kBoxBytes = (unsigned)(kBand * (int)sizeof(S2));
-    struct __align__(16) Row {
-        int baseA, baseB;    // band index of T's origin in windows A and B, in 9.23 fixed point
-        int c23, s23;        // cos, sin of angle a in 9.23
-        float kb, hb0p, hb1p;
-        int pad_;
-    };
+    using Row = BpRowM;
     Row (&rows)[2][CH] = *reinterpret_cast<Row(*)[2][CH]>(rows_smem);
     // bands: a over A, a' over A, a' over B, a over B
     S2 (&band)[2][CH][NB][kBandS] = *reinterpret_cast<S2(*)[2][CH][NB][kBandS]>(band_smem);
@@ -682,7 +687,8 @@ k_backproject(const Prob<T>* __restrict__ probs, const Item* __restrict__ items,
     __shared__ __align__(8) unsigned long long mbar[2];   // TMA completion per band buffer
     if constexpr (kF32 && NRHS == 1) {
         if (P.bp_mirror) {
-            static_assert(sizeof(rows) >= 2 * 8 * sizeof(BpRowF) && sizeof(band) >= 2 * 8 * 4 * kBandS * sizeof(S2),
+            static_assert(sizeof(rows) >= 2 * kBpMirrorCH * sizeof(BpRowM) &&
+                          sizeof(band) >= 2 * kBpMirrorCH * kBpMirrorNB * kBandS * sizeof(S2),
                           "the mirror-paired path fits the plain gather's storage");
             backproject_mirror<T>(P, it, part, src0, dst0, step, &rows[0][0], &band[0][0][0][0], mbar);
             return;
