@@ -439,8 +439,8 @@ __device__ __forceinline__ long long tile_origin_fx(const Angle<float>& g, int X
 // so a slot stages four bands (rows a and a' over each window) and takes two
 // weight evaluations and four pair loads per pixel pair, where the plain
 // gather takes four evaluations.  A slot with a single angle (0, na/2) has no
-// second row: its two bands of it are zero-filled in shared memory and every
-// slot takes the same path.  Item q is the plain gather's item q (64 | N makes
+// second row: the two bands of the missing row are zero-filled in shared
+// memory, so every slot takes the same path.  Item q is the plain gather's item q (64 | N makes
 // the counts equal: (N/64) x (N/16) = (N/32)^2), so work lists and partial
 // sums are shared with it, and a batch or a server step mixes problems of
 // either path in one launch (each problem always takes the same one, so its
