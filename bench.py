@@ -228,12 +228,12 @@ def nnz_of(work) -> int:
 
 # ---------------------------------------------------------------------------
 def time_oracle_solves(prob, work, variant, gamma0_rel, budget_s, max_solves, lam=0.0, prox_iters=10,
-                       perturb="gamma", perturb_steps=1):
-    """Whole oracle solves of ``prob`` (FP64, on the host cores), timed one by
-    one until ``budget_s`` seconds or ``max_solves`` solves.  Returns the times,
-    the iteration count and the thread count.  FISTA's c^2 comes from the
-    oracle's own power iteration (100 steps, the library's count), outside the
-    timed solves."""
+                       perturb="gamma", perturb_steps=1, warmup=0):
+    """Whole oracle solves of ``prob`` (FP64, on the host cores): ``warmup``
+    untimed ones, then solves timed one by one until ``budget_s`` seconds or
+    ``max_solves`` solves.  Returns the times, the iteration count and the
+    thread count.  FISTA's c^2 comes from the oracle's own power iteration (100
+    steps, the library's count), outside the timed solves."""
     import oracle
     kw = dict(variant=variant, gamma0_rel=gamma0_rel, eps=prob.eps, max_iter=work.max_iter)
     if variant in ("CG", "PCG"):
@@ -252,6 +252,8 @@ def time_oracle_solves(prob, work, variant, gamma0_rel, budget_s, max_solves, la
 
         def one():
             return oracle.solve(prob.y, work.n, **kw)
+    for _ in range(max(0, warmup)):
+        one()
     times, iters = [], 0
     t_all = time.perf_counter()
     while len(times) < max(1, max_solves):
@@ -272,14 +274,15 @@ def run_reference(args, work, rank, world):
     variant = args.variant
     prob = inputs.make_problem(work, args.seed, oracle.project)
     times, iters, cores = time_oracle_solves(prob, work, variant, args.gamma0_rel, args.ref_budget, args.steps,
-                                             args.lam, args.prox_iters, args.perturb, args.perturb_steps)
+                                             args.lam, args.prox_iters, args.perturb, args.perturb_steps,
+                                             warmup=args.warmup)
     t_solve = float(np.mean(times))
     value = 1.0 / t_solve
     sample = (f"{len(times)} whole oracle {variant} solves of this workload ({iters} iterations to eps each), "
-              f"timed one by one, as many as fit {args.ref_budget:.0f} s of CPU time (no warm-up solve: "
-              f"the oracle has nothing to warm)")
+              f"timed one by one after {args.warmup} untimed ones, as many as fit {args.ref_budget:.0f} s "
+              f"of CPU time")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": len(times), "warmup": 0, "ms_per_step": 1e3 * t_solve,
+            "steps": len(times), "warmup": args.warmup, "ms_per_step": 1e3 * t_solve,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": dict(config_of(work, variant, prob, iters, args), parallelism=f"replicas x{world}"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
