@@ -230,9 +230,9 @@ def nnz_of(work) -> int:
 def time_oracle_solves(prob, work, variant, gamma0_rel, budget_s, max_solves, lam=0.0, prox_iters=10,
                        perturb="gamma", perturb_steps=1, warmup=0):
     """Whole oracle solves of ``prob`` (FP64, on the host cores): ``warmup``
-    untimed ones, then solves timed one by one until ``budget_s`` seconds or
-    ``max_solves`` solves.  Returns the times, the iteration count and the
-    thread count.  FISTA's c^2 comes from the oracle's own power iteration (100
+    untimed ones, then solves timed one by one until ``budget_s`` seconds (the
+    warm-up included; at least one timed solve) or ``max_solves`` solves.
+    Returns the times, the iteration count and the thread count.  FISTA's c^2 comes from the oracle's own power iteration (100
     steps, the library's count), outside the timed solves."""
     import oracle
     kw = dict(variant=variant, gamma0_rel=gamma0_rel, eps=prob.eps, max_iter=work.max_iter)
@@ -252,10 +252,10 @@ def time_oracle_solves(prob, work, variant, gamma0_rel, budget_s, max_solves, la
 
         def one():
             return oracle.solve(prob.y, work.n, **kw)
+    t_all = time.perf_counter()
     for _ in range(max(0, warmup)):
         one()
     times, iters = [], 0
-    t_all = time.perf_counter()
     while len(times) < max(1, max_solves):
         t0 = time.perf_counter()
         _, res, _ = one()
@@ -280,7 +280,7 @@ def run_reference(args, work, rank, world):
     value = 1.0 / t_solve
     sample = (f"{len(times)} whole oracle {variant} solves of this workload ({iters} iterations to eps each), "
               f"timed one by one after {args.warmup} untimed ones, as many as fit {args.ref_budget:.0f} s "
-              f"of CPU time")
+              f"of CPU time with the untimed ones")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": len(times), "warmup": args.warmup, "ms_per_step": 1e3 * t_solve,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
